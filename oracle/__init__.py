@@ -1,0 +1,290 @@
+"""CPU oracle for the HDC classification path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline legs of
+``bench.py`` may import this package.  The product library never loads it and
+shares no code with it.
+
+The arithmetic lives in ``hdc_oracle.c`` (plain C, FP64/int64, compiled with
+gcc ``-O2 -ffp-contract=off`` so that FP64 sums are evaluated exactly as
+written on every host).  This module only marshals numpy arrays and strings
+the C steps together in the paper's order (Sec. 2.1: encode -> bundle/retrain
+-> similarity -> nearest class; Listing 1; Sec. 4.2 approximations).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hdc_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+
+ENC_FP32, ENC_BF16, ENC_FP8 = 0, 1, 2
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into oracle/_build/liboracle.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-std=c11", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _L():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_SO)
+            i64, f32, i32, f64 = ctypes.c_int64, ctypes.c_float, ctypes.c_int32, ctypes.c_double
+            P = ctypes.c_void_p
+            sig = {
+                "orc_kept_dims": (i64, [i64, f32, f32, i64, P]),
+                "orc_gather_cols_u8": (None, [P, i64, i64, P, i64, P]),
+                "orc_gather_cols_i64": (None, [P, i64, i64, P, i64, P]),
+                "orc_round_bf16": (f64, [f32]),
+                "orc_round_e4m3": (f64, [f64]),
+                "orc_pow2_scale": (f64, [f64]),
+                "orc_quantise_rows": (None, [P, i64, i64, i32, P, P]),
+                "orc_encode_f64": (None, [P, i64, i64, P, P, i64, P]),
+                "orc_encode_i64": (None, [P, i64, i64, P, P, i64, P]),
+                "orc_encode_absdot_f64": (None, [P, i64, i64, P, P, i64, P]),
+                "orc_binarise_f64": (None, [P, i64, P]),
+                "orc_binarise_i64": (None, [P, i64, P]),
+                "orc_hamming": (None, [P, i64, P, i64, i64, P]),
+                "orc_argmin_i64": (None, [P, i64, i64, P]),
+                "orc_argmax_f64": (None, [P, i64, i64, P]),
+                "orc_bundle": (None, [P, P, i64, i64, i64, P]),
+                "orc_class_bits": (None, [P, i64, i64, P]),
+                "orc_retrain_epoch": (i64, [P, P, i64, i64, i64, P]),
+                "orc_class_quantise": (None, [P, i64, i64, i32, P]),
+                "orc_cosine_scores": (None, [P, i64, P, i64, i64, P]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# --------------------------------------------------------------------- steps
+
+def kept_dims(D: int, start: float = 0.0, end: float = 1.0, stride: int = 1) -> np.ndarray:
+    """Reduction-perforation index set (Sec. 4.2; Listing 1)."""
+    n = _L().orc_kept_dims(D, start, end, stride, None)
+    if n < 0:
+        raise ValueError("invalid perforation (D=%d start=%r end=%r stride=%d)" % (D, start, end, stride))
+    dims = np.empty(max(n, 1), dtype=np.int64)
+    _L().orc_kept_dims(D, start, end, stride, _p(dims))
+    return dims[:n]
+
+
+def gather_cols(a: np.ndarray, dims: np.ndarray) -> np.ndarray:
+    dims = _c(dims, np.int64)
+    if a.dtype == np.uint8:
+        a = _c(a, np.uint8)
+        out = np.empty((a.shape[0], dims.size), dtype=np.uint8)
+        _L().orc_gather_cols_u8(_p(a), a.shape[0], a.shape[1], _p(dims), dims.size, _p(out))
+    else:
+        a = _c(a, np.int64)
+        out = np.empty((a.shape[0], dims.size), dtype=np.int64)
+        _L().orc_gather_cols_i64(_p(a), a.shape[0], a.shape[1], _p(dims), dims.size, _p(out))
+    return out
+
+
+def round_bf16(x) -> np.ndarray:
+    x = np.asarray(x, dtype=np.float32)
+    f = _L().orc_round_bf16
+    return np.array([f(float(v)) for v in x.ravel()], dtype=np.float64).reshape(x.shape)
+
+
+def round_e4m3(x) -> np.ndarray:
+    x = np.asarray(x, dtype=np.float64)
+    f = _L().orc_round_e4m3
+    return np.array([f(float(v)) for v in x.ravel()], dtype=np.float64).reshape(x.shape)
+
+
+def pow2_scale(amax: float) -> float:
+    return _L().orc_pow2_scale(float(amax))
+
+
+def quantise_rows(X: np.ndarray, enc: int):
+    """(values in scaled units as FP64, per-row scales) for ENC_FP32/BF16/FP8."""
+    X = _c(X, np.float32)
+    n, F = X.shape
+    out = np.empty((n, F), dtype=np.float64)
+    sc = np.empty(n, dtype=np.float64)
+    _L().orc_quantise_rows(_p(X), n, F, enc, _p(out), _p(sc))
+    return out, sc
+
+
+def encode_f64(X: np.ndarray, Bt: np.ndarray, dims: np.ndarray) -> np.ndarray:
+    X = _c(X, np.float64); Bt = _c(Bt, np.float64); dims = _c(dims, np.int64)
+    assert X.shape[1] == Bt.shape[1]
+    s = np.empty((X.shape[0], dims.size), dtype=np.float64)
+    _L().orc_encode_f64(_p(X), X.shape[0], X.shape[1], _p(Bt), _p(dims), dims.size, _p(s))
+    return s
+
+
+def encode_i64(X: np.ndarray, Bt: np.ndarray, dims: np.ndarray) -> np.ndarray:
+    X = _c(X, np.int64); Bt = _c(Bt, np.int64); dims = _c(dims, np.int64)
+    assert X.shape[1] == Bt.shape[1]
+    s = np.empty((X.shape[0], dims.size), dtype=np.int64)
+    _L().orc_encode_i64(_p(X), X.shape[0], X.shape[1], _p(Bt), _p(dims), dims.size, _p(s))
+    return s
+
+
+def encode_absdot(X: np.ndarray, Bt: np.ndarray, dims: np.ndarray) -> np.ndarray:
+    X = _c(X, np.float64); Bt = _c(Bt, np.float64); dims = _c(dims, np.int64)
+    s = np.empty((X.shape[0], dims.size), dtype=np.float64)
+    _L().orc_encode_absdot_f64(_p(X), X.shape[0], X.shape[1], _p(Bt), _p(dims), dims.size, _p(s))
+    return s
+
+
+def binarise(s: np.ndarray) -> np.ndarray:
+    out = np.empty(s.shape, dtype=np.uint8)
+    if s.dtype.kind == "i":
+        s = _c(s, np.int64)
+        _L().orc_binarise_i64(_p(s), s.size, _p(out))
+    else:
+        s = _c(s, np.float64)
+        _L().orc_binarise_f64(_p(s), s.size, _p(out))
+    return out
+
+
+def hamming(q: np.ndarray, c: np.ndarray) -> np.ndarray:
+    q = _c(q, np.uint8); c = _c(c, np.uint8)
+    assert q.shape[1] == c.shape[1]
+    d = np.empty((q.shape[0], c.shape[0]), dtype=np.int64)
+    _L().orc_hamming(_p(q), q.shape[0], _p(c), c.shape[0], q.shape[1], _p(d))
+    return d
+
+
+def argmin(v: np.ndarray) -> np.ndarray:
+    v = _c(v, np.int64)
+    out = np.empty(v.shape[0], dtype=np.int32)
+    _L().orc_argmin_i64(_p(v), v.shape[0], v.shape[1], _p(out))
+    return out
+
+
+def argmax(v: np.ndarray) -> np.ndarray:
+    v = _c(v, np.float64)
+    out = np.empty(v.shape[0], dtype=np.int32)
+    _L().orc_argmax_f64(_p(v), v.shape[0], v.shape[1], _p(out))
+    return out
+
+
+def bundle(bits: np.ndarray, y: np.ndarray, C: int) -> np.ndarray:
+    bits = _c(bits, np.uint8); y = _c(y, np.int32)
+    acc = np.empty((C, bits.shape[1]), dtype=np.int64)
+    _L().orc_bundle(_p(bits), _p(y), bits.shape[0], bits.shape[1], C, _p(acc))
+    return acc
+
+
+def class_bits(acc: np.ndarray) -> np.ndarray:
+    acc = _c(acc, np.int64)
+    out = np.empty(acc.shape, dtype=np.uint8)
+    _L().orc_class_bits(_p(acc), acc.shape[0], acc.shape[1], _p(out))
+    return out
+
+
+def retrain_epoch(bits: np.ndarray, y: np.ndarray, acc: np.ndarray) -> int:
+    """One epoch; updates acc (int64, C x D) in place, returns #updates."""
+    bits = _c(bits, np.uint8); y = _c(y, np.int32)
+    assert acc.dtype == np.int64 and acc.flags["C_CONTIGUOUS"]
+    n = _L().orc_retrain_epoch(_p(bits), _p(y), bits.shape[0], bits.shape[1], acc.shape[0], _p(acc))
+    if n < 0:
+        raise MemoryError("oracle retrain epoch: out of memory")
+    return int(n)
+
+
+def class_quantise(acc: np.ndarray, b: int) -> np.ndarray:
+    acc = _c(acc, np.int64)
+    out = np.empty(acc.shape, dtype=np.int64)
+    _L().orc_class_quantise(_p(acc), acc.shape[0], acc.shape[1], b, _p(out))
+    return out
+
+
+def cosine_scores(q: np.ndarray, chat: np.ndarray) -> np.ndarray:
+    q = _c(q, np.uint8); chat = _c(chat, np.int64)
+    assert q.shape[1] == chat.shape[1]
+    s = np.empty((q.shape[0], chat.shape[0]), dtype=np.float64)
+    _L().orc_cosine_scores(_p(q), q.shape[0], _p(chat), chat.shape[0], q.shape[1], _p(s))
+    return s
+
+
+# ---------------------------------------------------------------- pipelines
+
+def encode_bits(X: np.ndarray, Bt: np.ndarray, enc: int, dims: np.ndarray,
+                integer: bool = False):
+    """Quantise -> encode over the kept dims -> binarise.
+
+    Returns (bits N x Dk, scores in units of the row scales, scale_x, scale_b).
+    ``integer=True`` encodes integer-valued inputs exactly in int64.
+    """
+    if integer:
+        s = encode_i64(np.rint(X).astype(np.int64), np.rint(Bt).astype(np.int64), dims)
+        return binarise(s), s, np.ones(X.shape[0]), np.ones(Bt.shape[0])
+    Xq, sx = quantise_rows(X, enc)
+    Bq, sb = quantise_rows(Bt, enc)
+    s = encode_f64(Xq, Bq, dims)
+    return binarise(s), s, sx, sb
+
+
+def train(bits: np.ndarray, y: np.ndarray, C: int, epochs: int):
+    """Bundle (epoch 0) then ``epochs`` retraining epochs; returns (acc, updates)."""
+    acc = bundle(bits, y, C)
+    ups = []
+    for _ in range(epochs):
+        ups.append(retrain_epoch(bits, y, acc))
+    return acc, ups
+
+
+def classify(X: np.ndarray, Bt: np.ndarray, acc: np.ndarray, enc: int = ENC_FP32,
+             start: float = 0.0, end: float = 1.0, stride: int = 1, class_bits_: int = 1,
+             integer: bool = False, threads: int = 1):
+    """End-to-end classification of query rows X (Listing 1 + Sec. 4.2 knobs).
+
+    Returns (labels, similarity N x C) where similarity is the Hamming distance
+    (class_bits_ = 1, arg-min) or the cosine score (class_bits_ > 1, arg-max).
+    ``threads`` > 1 splits the queries over a thread pool (the C steps run
+    without the GIL); the result does not depend on it.
+    """
+    D = Bt.shape[0]
+    dims = kept_dims(D, start, end, stride)
+    if threads > 1 and X.shape[0] > 1:
+        chunks = np.array_split(np.arange(X.shape[0]), threads)
+        with ThreadPoolExecutor(threads) as ex:
+            parts = list(ex.map(lambda idx: classify(X[idx], Bt, acc, enc, start, end, stride,
+                                                     class_bits_, integer, 1), chunks))
+        return (np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]))
+    bits, _, _, _ = encode_bits(X, Bt, enc, dims, integer)
+    if class_bits_ == 1:
+        cb = gather_cols(class_bits(acc), dims)
+        dist = hamming(bits, cb)
+        return argmin(dist), dist
+    chat = gather_cols(class_quantise(acc, class_bits_), dims)
+    sc = cosine_scores(bits, chat)
+    return argmax(sc), sc

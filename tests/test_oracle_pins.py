@@ -1,0 +1,415 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test checks an oracle step against a value the paper prints, a closed
+form, an invariant of the mathematics, a library routine (numpy, scipy,
+torch CPU casts, Python fractions) or brute force on tiny inputs, chosen so
+that a dropped term, a wrong sign or index, or a transposed operand fails.
+No GPU is needed.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import torch
+from scipy.spatial import distance as sdist
+
+from tests._helpers import pack, unpack, words_for
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------- perforation
+
+def test_kept_dims_listing1_golden(orc):
+    # Listing 1 / Sec. 2.2: red_perf(dists, 0.0, 0.5, 1) on D = 2048 keeps
+    # the first 1024 elements.
+    with open(os.path.join(GOLDEN, "red_perf_listing1.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    for D, s, e, st, first, last, cnt in rows:
+        dims = orc.kept_dims(int(D), float(s), float(e), int(st))
+        assert dims.size == int(cnt)
+        assert dims[0] == int(first) and dims[-1] == int(last)
+        assert np.array_equal(dims, np.arange(int(first), int(last) + 1))
+
+
+@pytest.mark.parametrize("D", [1, 31, 2048, 10000, 16384])
+def test_kept_dims_properties(orc, D):
+    full = orc.kept_dims(D)
+    assert np.array_equal(full, np.arange(D))
+    prev = set(full.tolist())
+    for stride in (2, 4, 8):                      # nested strides
+        k = orc.kept_dims(D, 0.0, 1.0, stride)
+        assert k.size == (D + stride - 1) // stride
+        assert set(k.tolist()) <= prev
+        assert np.all(np.diff(k) == stride) or k.size <= 1
+        prev = set(k.tolist())
+    k = orc.kept_dims(D, 0.25, 0.75, 3) if D >= 4 else None
+    if k is not None:
+        lo = math.floor(Fraction(float(np.float32(0.25))) * D)
+        hi = math.floor(Fraction(float(np.float32(0.75))) * D)
+        assert k[0] == lo and k[-1] < hi and k[-1] + 3 >= hi
+
+
+def test_kept_dims_invalid(orc):
+    for args in [(0, 0.0, 1.0, 1), (10, 0.5, 0.5, 1), (10, 0.0, 1.0, 0), (10, -0.1, 1.0, 1),
+                 (10, 0.0, 1.5, 1)]:
+        with pytest.raises(ValueError):
+            orc.kept_dims(*args)
+
+
+# ------------------------------------------------------------ element types
+
+def test_round_bf16_matches_torch(orc):
+    rng = np.random.default_rng(1)
+    v = np.concatenate([rng.standard_normal(4000) * 10.0 ** rng.integers(-30, 30, 4000),
+                        np.array([0.0, -0.0, 1.0, -1.0, 3.0e38, 1e-40])]).astype(np.float32)
+    ours = orc.round_bf16(v)
+    ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(ours, ref)
+
+
+def test_round_bf16_ties_to_even(orc):
+    # 1 + 2^-8 is halfway between 1 and 1 + 2^-7 -> even (1.0);
+    # 1 + 3*2^-8 is halfway between 1 + 2^-7 and 1 + 2^-6 -> even (1 + 2^-6)
+    assert orc.round_bf16(np.float32(1 + 2 ** -8)) == 1.0
+    assert orc.round_bf16(np.float32(1 + 3 * 2 ** -8)) == 1 + 2 ** -6
+
+
+def _e4m3_table():
+    """All finite E4M3 values, decoded from the bit format in this test."""
+    vals = set()
+    for code in range(256):
+        s, e, m = code >> 7, (code >> 3) & 15, code & 7
+        if e == 15 and m == 7:
+            continue                                   # NaN
+        v = (m / 8.0) * 2.0 ** -6 if e == 0 else (1 + m / 8.0) * 2.0 ** (e - 7)
+        vals.add(-v if s else v)
+    return np.array(sorted(vals))
+
+
+def test_e4m3_table_fixed_points(orc):
+    t = _e4m3_table()
+    assert t.max() == 448.0 and t.min() == -448.0 and t.size == 253  # +-0 merge
+    assert np.array_equal(orc.round_e4m3(t), t)
+
+
+def test_round_e4m3_nearest_even_bruteforce(orc):
+    t = _e4m3_table()
+    pos = t[t >= 0]
+    rng = np.random.default_rng(2)
+    v = np.concatenate([rng.uniform(-500, 500, 3000), rng.uniform(-1, 1, 3000),
+                        rng.uniform(-0.02, 0.02, 2000),
+                        (pos[:-1] + pos[1:]) / 2, -(pos[:-1] + pos[1:]) / 2])
+    ours = orc.round_e4m3(v)
+    for x, r in zip(v, ours):
+        a = abs(x)
+        if a >= 448:
+            assert abs(r) == 448.0
+            continue
+        d = np.abs(pos - a)
+        cand = pos[d == d.min()]
+        if cand.size == 1:
+            exp = cand[0]
+        else:                                   # tie: even fraction code wins
+            def code(val):
+                if val < 2.0 ** -6:
+                    return int(round(val / 2.0 ** -9))
+                e = math.floor(math.log2(val))
+                return int(round((val / 2.0 ** e - 1) * 8))
+            exp = [c for c in cand if code(c) % 2 == 0][0]
+        assert abs(r) == exp and (r == 0 or math.copysign(1, r) == math.copysign(1, x))
+
+
+def test_round_e4m3_matches_torch_in_range(orc):
+    rng = np.random.default_rng(3)
+    v = (rng.standard_normal(5000) * 10.0 ** rng.uniform(-4, 2.6, 5000)).clip(-448, 448)
+    ours = orc.round_e4m3(v)
+    ref = torch.from_numpy(v.astype(np.float32)).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(ours, ref)
+
+
+def test_pow2_scale_bruteforce(orc):
+    rng = np.random.default_rng(4)
+    for amax in list(rng.uniform(0, 1, 200) * 10.0 ** rng.integers(-20, 20, 200)) + [448.0, 896.0, 1.0, 3.5]:
+        s = orc.pow2_scale(float(amax))
+        m, e = math.frexp(s)
+        assert m == 0.5                                   # power of two
+        assert Fraction(amax) <= 448 * Fraction(s)
+        assert Fraction(amax) > 224 * Fraction(s)        # s/2 would not do
+    assert orc.pow2_scale(0.0) == 1.0
+
+
+def test_quantise_rows_fp8_in_table(orc):
+    rng = np.random.default_rng(5)
+    X = (rng.standard_normal((16, 100)) * rng.uniform(0.01, 100, (16, 1))).astype(np.float32)
+    X[3] = 0.0
+    q, sc = orc.quantise_rows(X, orc.ENC_FP8)
+    t = set(_e4m3_table().tolist())
+    assert all(v in t for v in q.ravel())
+    assert np.abs(q).max() <= 448
+    assert sc[3] == 1.0 and np.all(q[3] == 0)
+    # relative error of the e4m3 grid is at most 2^-4 for normal values
+    rec = q * sc[:, None]
+    big = np.abs(X) > 2.0 ** -6 * sc[:, None]
+    assert np.all(np.abs(rec - X)[big] <= np.abs(X)[big] * 2.0 ** -4 + 1e-30)
+
+
+# --------------------------------------------------------------- encoding
+
+def test_encode_int_matches_numpy(orc):
+    rng = np.random.default_rng(6)
+    X = rng.integers(-8, 8, (37, 61))
+    Bt = 1 - 2 * rng.integers(0, 2, (300, 61))
+    dims = orc.kept_dims(300, 0.1, 0.9, 3)
+    s = orc.encode_i64(X, Bt, dims)
+    assert np.array_equal(s, (X @ Bt.T)[:, dims])
+
+
+def test_encode_f64_matches_numpy(orc):
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((20, 50))
+    Bt = rng.standard_normal((70, 50))
+    dims = orc.kept_dims(70)
+    s = orc.encode_f64(X, Bt, dims)
+    ab = orc.encode_absdot(X, Bt, dims)
+    assert np.all(np.abs(s - X @ Bt.T) <= 1e-13 * ab)
+    assert np.allclose(ab, np.abs(X) @ np.abs(Bt).T, rtol=1e-13)
+
+
+def test_encode_special_cases(orc):
+    rng = np.random.default_rng(8)
+    F, D = 17, 90
+    Bt = rng.standard_normal((D, F))
+    dims = orc.kept_dims(D)
+    E = np.eye(F)                                   # x = e_f -> h = sign(B row f)
+    bits = orc.binarise(orc.encode_f64(E, Bt, dims))
+    assert np.array_equal(bits, (Bt.T < 0).astype(np.uint8))
+    z = orc.binarise(orc.encode_f64(np.zeros((3, F)), Bt, dims))
+    assert not z.any()                              # sign(0) = +1 -> bit 0
+    x = rng.standard_normal((5, F))
+    for a in (2.0, 0.25, 1024.0):                   # exact positive rescale
+        assert np.array_equal(orc.binarise(orc.encode_f64(a * x, Bt, dims)),
+                              orc.binarise(orc.encode_f64(x, Bt, dims)))
+    assert np.array_equal(orc.binarise(orc.encode_f64(-x, Bt, dims)),
+                          1 - orc.binarise(orc.encode_f64(x, Bt, dims)))
+
+
+def test_encode_simhash_angle(orc):
+    # Random hyperplane hashing: for Gaussian B, P[bit differs] = angle/pi,
+    # so Hamming/D estimates theta/pi (check within 5 binomial sigmas).
+    rng = np.random.default_rng(9)
+    F, D = 40, 10000
+    Bt = rng.standard_normal((D, F))
+    dims = orc.kept_dims(D)
+    for _ in range(6):
+        x, y = rng.standard_normal(F), rng.standard_normal(F)
+        y = x + rng.uniform(0.2, 3) * y
+        bx = orc.binarise(orc.encode_f64(x[None], Bt, dims))
+        by = orc.binarise(orc.encode_f64(y[None], Bt, dims))
+        h = orc.hamming(bx, by)[0, 0]
+        p = math.acos(np.dot(x, y) / np.linalg.norm(x) / np.linalg.norm(y)) / math.pi
+        assert abs(h / D - p) <= 5 * math.sqrt(p * (1 - p) / D)
+
+
+# ----------------------------------------------------------------- Hamming
+
+def test_hamming_axioms_and_scipy(orc):
+    rng = np.random.default_rng(10)
+    Dk = 333
+    a = rng.integers(0, 2, (12, Dk)).astype(np.uint8)
+    d = orc.hamming(a, a)
+    assert np.all(np.diag(d) == 0)
+    assert np.array_equal(d, d.T)
+    assert np.all(orc.hamming(a, 1 - a).diagonal() == Dk)
+    assert d.min() >= 0 and d.max() <= Dk
+    for i in range(12):                              # triangle inequality
+        for j in range(12):
+            assert np.all(d[i, j] <= d[i, :] + d[:, j])
+    ref = sdist.cdist(a, a, "hamming") * Dk
+    assert np.array_equal(d, np.rint(ref).astype(np.int64))
+    pm = 1 - 2 * a.astype(np.int64)                  # (Dk - <q,c>)/2 on +-1
+    assert np.array_equal(d, (Dk - pm @ pm.T) // 2)
+
+
+def test_hamming_perforated_is_subset_distance(orc):
+    rng = np.random.default_rng(11)
+    D = 1000
+    q = rng.integers(0, 2, (5, D)).astype(np.uint8)
+    c = rng.integers(0, 2, (7, D)).astype(np.uint8)
+    tot = np.zeros((5, 7), dtype=np.int64)
+    for r in range(4):                               # residues of stride 4
+        dims = orc.kept_dims(D - r, 0.0, 1.0, 4) + r if r else orc.kept_dims(D, 0.0, 1.0, 4)
+        dq, dc = orc.gather_cols(q, dims), orc.gather_cols(c, dims)
+        part = orc.hamming(dq, dc)
+        assert np.array_equal(part, (q[:, None, dims] != c[None, :, dims]).sum(-1))
+        tot += part
+    assert np.array_equal(tot, orc.hamming(q, c))    # residues add up to stride 1
+
+
+def test_pack_roundtrip():
+    rng = np.random.default_rng(12)
+    for D in (1, 31, 32, 33, 127, 128, 129, 10000):
+        b = rng.integers(0, 2, (3, D)).astype(np.uint8)
+        w = pack(b)
+        assert w.shape[1] == words_for(D) and w.shape[1] % 4 == 0
+        assert np.array_equal(unpack(w, D), b)
+        tail = unpack(w, w.shape[1] * 32)[:, D:]
+        assert not tail.any()
+
+
+# ----------------------------------------------------------- arg-min / max
+
+def test_argmin_argmax_bruteforce(orc):
+    rng = np.random.default_rng(13)
+    v = rng.integers(0, 4, (500, 9))
+    assert np.array_equal(orc.argmin(v), np.argmin(v, axis=1))   # numpy: first minimum
+    f = rng.integers(0, 4, (500, 9)).astype(np.float64)
+    assert np.array_equal(orc.argmax(f), np.argmax(f, axis=1))
+    assert np.all(orc.argmin(np.full((4, 6), 7)) == 0)
+    assert np.all(orc.argmax(np.zeros((4, 6))) == 0)
+
+
+# -------------------------------------------------------- bundle / retrain
+
+def test_bundle_properties(orc):
+    rng = np.random.default_rng(14)
+    N, D, C = 90, 257, 5
+    bits = rng.integers(0, 2, (N, D)).astype(np.uint8)
+    y = rng.integers(0, C, N).astype(np.int32)
+    acc = orc.bundle(bits, y, C)
+    onehot = np.eye(C, dtype=np.int64)[y]
+    assert np.array_equal(acc, onehot.T @ (1 - 2 * bits.astype(np.int64)))
+    n_c = np.bincount(y, minlength=C)
+    assert np.all((acc - n_c[:, None]) % 2 == 0)      # acc = n_c (mod 2)
+    perm = rng.permutation(N)
+    assert np.array_equal(orc.bundle(bits[perm], y[perm], C), acc)
+    one = orc.bundle(bits[:1], np.zeros(1, np.int32), 1)
+    assert np.array_equal(orc.class_bits(one), bits[:1])  # one sample reproduces it
+    two = orc.bundle(np.stack([bits[0], 1 - bits[0]]), np.zeros(2, np.int32), 1)
+    assert not two.any() and not orc.class_bits(two).any()  # h + not h = 0 -> +1
+
+
+def _separable(rng, C=4, D=512, N=200, flip=0.2):
+    protos = rng.integers(0, 2, (C, D)).astype(np.uint8)
+    y = (np.arange(N) % C).astype(np.int32)
+    noise = (rng.random((N, D)) < flip).astype(np.uint8)
+    return protos[y] ^ noise, y
+
+
+def test_retrain_invariants(orc):
+    rng = np.random.default_rng(15)
+    bits, y = _separable(rng, C=6, D=300, N=240, flip=0.42)
+    acc = orc.bundle(bits, y, 6)
+    col = acc.sum(0).copy()
+    for _ in range(4):
+        before = acc.copy()
+        cb = orc.class_bits(before)
+        pred = np.argmin(sdist.cdist(bits, cb, "hamming"), axis=1)
+        wrong = pred != y
+        n = orc.retrain_epoch(bits, y, acc)
+        assert n == int(wrong.sum())
+        assert np.array_equal(acc.sum(0), col)        # updates move mass between classes
+        h = 1 - 2 * bits.astype(np.int64)
+        delta = (np.eye(6, dtype=np.int64)[y[wrong]] - np.eye(6, dtype=np.int64)[pred[wrong]]).T @ h[wrong]
+        assert np.array_equal(acc - before, delta)
+
+
+def test_retrain_converges_on_separable(orc):
+    rng = np.random.default_rng(16)
+    bits, y = _separable(rng, C=4, D=512, N=200, flip=0.3)
+    acc = orc.bundle(bits, y, 4)
+    ups = [orc.retrain_epoch(bits, y, acc) for _ in range(10)]
+    assert ups[-1] == 0
+    frozen = acc.copy()
+    assert orc.retrain_epoch(bits, y, acc) == 0 and np.array_equal(acc, frozen)
+
+
+# --------------------------------------------------------- class quantise
+
+def _round_half_away(fr: Fraction) -> int:
+    s = -1 if fr < 0 else 1
+    a = abs(fr)
+    return s * math.floor(a + Fraction(1, 2))
+
+
+@pytest.mark.parametrize("b", [2, 4, 8])
+def test_class_quantise_exhaustive(orc, b):
+    Q = 2 ** (b - 1) - 1
+    for M in range(1, 40):
+        acc = np.arange(-M, M + 1, dtype=np.int64)[None]
+        chat = orc.class_quantise(acc, b)[0]
+        exp = [_round_half_away(Fraction(int(a) * Q, M)) for a in acc[0]]
+        assert chat.tolist() == exp
+        assert np.abs(chat).max() == Q
+
+
+def test_class_quantise_identity_and_sign(orc):
+    rng = np.random.default_rng(17)
+    acc = rng.integers(-127, 128, (3, 500))
+    acc[:, 0] = 127
+    assert np.array_equal(orc.class_quantise(acc, 8), acc)
+    acc2 = rng.integers(-50, 51, (3, 500))
+    c1 = orc.class_quantise(acc2, 1)
+    assert np.array_equal(c1, np.where(acc2 >= 0, 1, -1))
+    assert not orc.class_quantise(np.zeros((2, 9), np.int64), 4).any()
+
+
+def test_cosine_scores_vs_scipy(orc):
+    rng = np.random.default_rng(18)
+    Dk = 400
+    q = rng.integers(0, 2, (6, Dk)).astype(np.uint8)
+    chat = rng.integers(-7, 8, (5, Dk))
+    chat[2] = 0
+    sc = orc.cosine_scores(q, chat)
+    qpm = 1 - 2 * q.astype(np.float64)
+    for i in range(6):
+        for j in range(5):
+            if j == 2:
+                assert sc[i, j] == 0.0
+                continue
+            cos = 1.0 - sdist.cosine(qpm[i], chat[j].astype(np.float64))
+            assert abs(sc[i, j] - cos * math.sqrt(Dk)) < 1e-9
+
+
+def test_cosine_binary_classes_equals_hamming(orc):
+    # with +-1 classes the score is (Dk - 2*Hamming)/sqrt(Dk): same winner
+    rng = np.random.default_rng(19)
+    Dk = 257
+    q = rng.integers(0, 2, (300, Dk)).astype(np.uint8)
+    cb = rng.integers(0, 2, (9, Dk)).astype(np.uint8)
+    chat = 1 - 2 * cb.astype(np.int64)
+    sc = orc.cosine_scores(q, chat)
+    hd = orc.hamming(q, cb)
+    assert np.allclose(sc, (Dk - 2 * hd) / math.sqrt(Dk), rtol=0, atol=1e-12)
+    assert np.array_equal(orc.argmax(sc), orc.argmin(hd))
+
+
+# ---------------------------------------------------------- end to end
+
+def test_integer_data_three_routes_agree(orc):
+    """Integer features and +-1 base: int64, FP64 of the FP32 values and
+    FP64 of the E4M3-quantised values (pow2 row scales) give the same bits,
+    because every product and partial sum is exact in all three."""
+    from paper_2606_26547_gb300 import synth
+    d = synth.make("int_exact_F617_D2048_C26", n_train=50, n_query=40)
+    dims = orc.kept_dims(2048)
+    b_int, s_int, _, _ = orc.encode_bits(d["Xq"], d["Bt"], orc.ENC_FP32, dims, integer=True)
+    b_f32, s_f32, _, _ = orc.encode_bits(d["Xq"], d["Bt"], orc.ENC_FP32, dims)
+    b_fp8, s_fp8, sx, sb = orc.encode_bits(d["Xq"], d["Bt"], orc.ENC_FP8, dims)
+    b_bf, _, _, _ = orc.encode_bits(d["Xq"], d["Bt"], orc.ENC_BF16, dims)
+    assert np.array_equal(s_int, s_f32)
+    assert np.array_equal(s_fp8 * sx[:, None] * sb[None, :], s_f32)
+    assert np.array_equal(b_int, b_f32) and np.array_equal(b_int, b_fp8) and np.array_equal(b_int, b_bf)
+    assert np.abs(s_int).max() <= 617 * 8
+
+
+def test_classify_threads_invariant(orc):
+    from paper_2606_26547_gb300 import synth
+    d = synth.make("precision_F784_D10000_C10", n_train=40, n_query=30, D=512)
+    bits, _, _, _ = orc.encode_bits(d["Xtr"], d["Bt"], orc.ENC_FP32, orc.kept_dims(512))
+    acc, _ = orc.train(bits, d["ytr"], 10, 2)
+    l1, s1 = orc.classify(d["Xq"], d["Bt"], acc, orc.ENC_BF16, 0.0, 1.0, 2, 1)
+    l4, s4 = orc.classify(d["Xq"], d["Bt"], acc, orc.ENC_BF16, 0.0, 1.0, 2, 1, threads=4)
+    assert np.array_equal(l1, l4) and np.array_equal(s1, s4)
