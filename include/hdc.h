@@ -1,0 +1,207 @@
+/*
+ * hdc.h -- C ABI of libhdc, a GB300 (sm_103a) library for the data-parallel
+ * hot path of hyperdimensional-computing (HDC) classification under the
+ * approximation knobs studied in "Compiler-Driven Approximation Tuning for
+ * Hyperdimensional Computing" (ApproxHDC).
+ *
+ * The path (Sec. 2.1; Listing 1):
+ *   encode   h = sign(x . B)          random projection, __hetero_hdc_matmul
+ *   pack     +-1 -> one bit per dim   Automatic Binarization (Sec. 4.2)
+ *   compare  Hamming distance to C class hypervectors
+ *            (or cosine on b-bit class hypervectors, "Algorithmic Choice")
+ *   choose   arg-min / arg-max        __hetero_hdc_arg_min
+ *   train    bundling + retraining    Sec. 2.1 training stage; TRAIN_ITERATIONS
+ * and the knobs (Sec. 4.2): reduction perforation (start, end, stride) of the
+ * dimension axis, element type of the encoding (FP32, BF16, FP8 E4M3) and of
+ * the class hypervectors (1, 4 or 8 bits).
+ *
+ * CONVENTIONS (all entry points)
+ *  - Every array argument is DEVICE memory owned by the caller unless the
+ *    name says _host.  The library never allocates device memory, never
+ *    frees, never synchronises the stream (except hdc_stream_status and the
+ *    _host entry points, which say so) and keeps no state between calls.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default).
+ *    Results are valid once the stream has reached that point.
+ *  - Row-major throughout.  A packed hypervector of L dimensions occupies
+ *    W(L) = ceil(L/32) rounded up to a multiple of 4 uint32 words: bit d is
+ *    bit (d % 32) of word d / 32, a set bit is the element -1, sign(0) = +1,
+ *    and every bit past L is zero.  Packed rows are 16-byte aligned.
+ *  - Arguments are checked before anything is enqueued: a NULL required
+ *    pointer, a size out of range, a misaligned pointer or a workspace that
+ *    is too small returns an error and enqueues nothing.  A failed launch
+ *    returns HDC_ERR_CUDA.  Device-side failures (a bounded wait that ran out,
+ *    a failed device check) set a device status word that hdc_stream_status
+ *    reports; the library never traps, aborts or throws across this ABI.
+ */
+#ifndef HDC_H
+#define HDC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *hdc_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+    HDC_OK = 0,
+    HDC_ERR_INVALID_ARG = 1, /* NULL pointer, size out of range, misalignment */
+    HDC_ERR_UNSUPPORTED = 2, /* valid but not built (e.g. class_bits = 3)     */
+    HDC_ERR_WORKSPACE = 3,   /* caller buffer smaller than the size query     */
+    HDC_ERR_CUDA = 4,        /* a CUDA runtime call or launch failed          */
+    HDC_ERR_TIMEOUT = 5,     /* a bounded device wait expired                 */
+    HDC_ERR_DEVICE = 6       /* a device-side check failed                    */
+} hdc_status;
+
+/* Element type of the encoding contraction (Sec. 4.2 "Element Type
+ * Representation").  FP32: FFMA on CUDA cores, the plain exact form.
+ * BF16: round-to-nearest-even, tensor cores, FP32 accumulation.
+ * FP8_E4M3: per-row power-of-two scale s = smallest 2^k with amax <= 448*s
+ * (rows of x and rows of B^T alike), round-to-nearest-even with saturation,
+ * tensor cores, FP32 accumulation.  Positive scales leave sign(x.B) as is.  */
+typedef enum {
+    HDC_ENC_FP32 = 0,
+    HDC_ENC_BF16 = 1,
+    HDC_ENC_FP8_E4M3 = 2
+} hdc_enc;
+
+/* One approximation configuration (mirrors the per-operation JSON of
+ * Listing 3: red_perf {base, stride, extent} plus an algorithmic choice).
+ * Kept dimensions K = { s0 + k*stride : s0 + k*stride < e0 } with
+ * s0 = floor(perf_start*D), e0 = floor(perf_end*D), both products in double
+ * (Listing 1: red_perf(dists, 0.0, 0.5, 1) keeps the first half of D).
+ * class_bits 1 = binary class hypervectors, Hamming distance, arg-min;
+ * class_bits 4 or 8 = b-bit class hypervectors, cosine score, arg-max.     */
+typedef struct {
+    uint32_t struct_size; /* = sizeof(hdc_approx_config)                    */
+    float perf_start;     /* in [0, 1)                                      */
+    float perf_end;       /* in (perf_start, 1]                             */
+    uint32_t perf_stride; /* >= 1                                           */
+    int32_t enc;          /* hdc_enc                                        */
+    uint32_t class_bits;  /* 1, 4 or 8                                      */
+    uint32_t flags;       /* HDC_FLAG_* below                               */
+} hdc_approx_config;
+
+/* Force the CUDA-core (FFMA) encoder even for BF16/FP8 inputs.             */
+#define HDC_FLAG_SIMT_ENCODE 0x1u
+
+/* Fill *cfg with the unapproximated configuration: perforation (0, 1, 1),
+ * FP32 encoding, binary class hypervectors.                                */
+void hdc_default_config(hdc_approx_config *cfg);
+
+/* Number of kept dimensions |K| of cfg's perforation on D dims, or -1 if
+ * the perforation arguments are invalid.  Host-only, no CUDA call.          */
+int64_t hdc_kept_dims(int32_t D, const hdc_approx_config *cfg);
+
+/* Words per packed row of L dimensions: ceil(L/32) rounded up to 4.         */
+int32_t hdc_words(int32_t L);
+
+/* A prepared model: views into a caller-owned device buffer filled by
+ * hdc_model_prepare.  Read-only for every other entry point.               */
+typedef struct {
+    uint32_t struct_size;
+    int32_t F;          /* features                                          */
+    int32_t D;          /* full dimensionality                               */
+    int32_t Dk;         /* kept dimensions |K|                               */
+    int32_t C;          /* classes (0 = base only)                           */
+    int32_t enc;        /* hdc_enc of Bq                                     */
+    int32_t ldb;        /* elements per row of Bq (F rounded up, zero pad)   */
+    int32_t class_bits; /* 1, 4 or 8                                         */
+    int32_t W;          /* words per packed hypervector over Dk dims         */
+    uint32_t flags;     /* HDC_FLAG_* of the configuration                   */
+    const void *Bq;     /* Dk x ldb: rows K of B^T in the encoding type      */
+    const float *b_scale;      /* Dk row scales (FP8) or NULL               */
+    const uint32_t *cls;       /* class_bits planes, each C x W words;       */
+                               /* plane j holds bit j of the two's-         */
+                               /* complement class value (1 plane = sign)   */
+    const int32_t *cls_sum;    /* C: sum over K of the class values (b > 1) */
+    const double *cls_norm;    /* C: sqrt(sum over K of class value^2)       */
+} hdc_model;
+
+/* Bytes of device buffer hdc_model_prepare needs for this configuration.  */
+hdc_status hdc_model_bytes(int32_t F, int32_t D, int32_t C,
+                           const hdc_approx_config *cfg, size_t *bytes);
+
+/* Prepare a model for cfg (model load, Sec. 4.2 knobs applied once):
+ *  - rows K of Bt (D x F FP32, the transposed base hypermatrix, Listing 1
+ *    rp_matrix) are gathered, quantised to cfg->enc and zero-padded to ldb;
+ *  - if acc (C x D int32 class accumulators from hdc_train_epoch) is not
+ *    NULL, the class hypervectors are quantised to cfg->class_bits over ALL
+ *    D dims (b = 1: sign; b > 1: per class Q = 2^(b-1)-1, M = max|acc|,
+ *    value = sign(acc)*floor((2|acc|Q + M)/(2M)), 0 if M = 0), restricted
+ *    to K, and stored as bit planes with their sums and norms over K.
+ * buf (>= hdc_model_bytes, 256-byte aligned) receives all data; *out gets
+ * the views.  C may be 0 (with acc NULL) for a base-only model.          */
+hdc_status hdc_model_prepare(const float *Bt, int32_t F, int32_t D,
+                             const int32_t *acc, int32_t C,
+                             const hdc_approx_config *cfg, void *buf,
+                             size_t buf_bytes, hdc_model *out,
+                             hdc_stream_t stream);
+
+/* Workspace bytes for hdc_encode / hdc_classify on N query rows.         */
+hdc_status hdc_workspace_bytes(int64_t N, const hdc_model *m, size_t *bytes);
+
+/* Encode (Listing 1 __hetero_hdc_matmul + Automatic Binarization):
+ * H[i] = pack(sign(X[i] . B[:, K]))  for X (N x F FP32, rows 16-byte
+ * aligned when F % 4 == 0).  H is N x m->W words.  If scores is not NULL
+ * it receives the N x Dk FP32 projections (de-scaled: x . B estimate), for
+ * parity checks.  ws: >= hdc_workspace_bytes(N, m), 256-byte aligned.   */
+hdc_status hdc_encode(const float *X, int64_t N, const hdc_model *m,
+                      uint32_t *H, float *scores, void *ws, size_t ws_bytes,
+                      hdc_stream_t stream);
+
+/* Hamming distance + arg-min (Listing 1: __hetero_hdc_hamming_distance,
+ * red_perf, __hetero_hdc_arg_min) on packed hypervectors of D dims:
+ * dist[i][c] = number of kept dims d in K(cfg, D) with Q[i] and Cls[c]
+ * different; labels[i] = arg-min, lowest class index on ties.  Q is N x
+ * W(D), Cls is C x W(D).  dists (N x C int32) is optional.  Only the
+ * perforation fields of cfg are used (NULL = no perforation).            */
+hdc_status hdc_hamming_argmin(const uint32_t *Q, const uint32_t *Cls,
+                              int64_t N, int32_t C, int32_t D,
+                              const hdc_approx_config *cfg, int32_t *labels,
+                              int32_t *dists, hdc_stream_t stream);
+
+/* Workspace bytes for hdc_train_epoch.                                     */
+hdc_status hdc_train_workspace_bytes(int64_t N, int32_t D, int32_t C,
+                                     size_t *bytes);
+
+/* One training pass over N packed training hypervectors H (N x W(D)) with
+ * labels y (int32 in [0, C); other labels are skipped):
+ *  mode 0 (bundling, Sec. 2.1): acc[c][d] = sum over n with y_n = c of
+ *         (1 - 2*bit[n][d])   (acc is overwritten);
+ *  mode 1 (retraining epoch, TRAIN_ITERATIONS): every sample is classified
+ *         by Hamming arg-min against cls as it is on entry; then, for each
+ *         misclassified n, acc[y_n] += h_n and acc[pred_n] -= h_n with
+ *         h = 1 - 2*bit (perceptron, applied once per epoch).
+ * In both modes cls (C x W(D)) is then rewritten as the sign of acc.
+ * n_updates (one int32, device, optional) receives the number of updates.
+ * acc (C x D int32) must not overflow: |acc| < 2^31.                      */
+hdc_status hdc_train_epoch(const uint32_t *H, const int32_t *y, int64_t N,
+                           int32_t D, int32_t C, int32_t mode, int32_t *acc,
+                           uint32_t *cls, int32_t *n_updates, void *ws,
+                           size_t ws_bytes, hdc_stream_t stream);
+
+/* Classify (Listing 1 end to end under the model's knobs):
+ * labels[i] for X (N x F FP32).  class_bits 1: Hamming arg-min over K,
+ * dists (N x C int32, optional).  class_bits > 1: cosine arg-max with
+ * score = dot(1-2*q, chat) / ||chat|| over K (IEEE FP64, 0 if the norm is
+ * 0), scores (N x C double, optional).  Encoded hypervectors are kept on
+ * chip on the tensor-core path and never written to memory.              */
+hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m,
+                        int32_t *labels, int32_t *dists, double *scores,
+                        void *ws, size_t ws_bytes, hdc_stream_t stream);
+
+/* Waits for `stream`, then reads and clears the library's device status
+ * words: HDC_OK, HDC_ERR_TIMEOUT or HDC_ERR_DEVICE (or HDC_ERR_CUDA if the
+ * stream itself reports an error).                                        */
+hdc_status hdc_stream_status(hdc_stream_t stream);
+
+/* Static English text for a status code.                                   */
+const char *hdc_status_string(hdc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDC_H */

@@ -1,0 +1,328 @@
+// C-ABI entry points of libhdc (declared and documented in include/hdc.h):
+// argument checks, carving of caller-owned buffers, and the launch sequence
+// of each call.  Every step of the path runs in the library's kernels.
+#include <math.h>
+#include <string.h>
+
+#include "hdc_internal.cuh"
+
+namespace hdc {
+
+bool perf_of(int64_t D, const hdc_approx_config *cfg, Perf *p)
+{
+    float st = 0.f, en = 1.f;
+    int64_t stride = 1;
+    if (cfg) {
+        st = cfg->perf_start;
+        en = cfg->perf_end;
+        stride = cfg->perf_stride;
+    }
+    if (D <= 0 || stride < 1 || !(st >= 0.f) || !(en <= 1.f) || !(st < en)) return false;
+    p->s0 = (int64_t)floor((double)st * (double)D);
+    p->e0 = (int64_t)floor((double)en * (double)D);
+    p->stride = stride;
+    p->Dk = p->e0 > p->s0 ? (p->e0 - p->s0 + stride - 1) / stride : 0;
+    return p->Dk > 0;
+}
+
+namespace {
+
+inline bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+bool cfg_ok(const hdc_approx_config *cfg)
+{
+    if (!cfg || cfg->struct_size < sizeof(hdc_approx_config)) return false;
+    if (cfg->enc < HDC_ENC_FP32 || cfg->enc > HDC_ENC_FP8_E4M3) return false;
+    return true;
+}
+
+bool bits_ok(uint32_t b) { return b == 1 || b == 4 || b == 8; }
+
+bool model_ok(const hdc_model *m)
+{
+    return m && m->struct_size >= sizeof(hdc_model) && m->F > 0 && m->D > 0 && m->Dk > 0 && m->Dk <= m->D &&
+           m->C >= 0 && m->Bq && m->ldb >= m->F && m->W == words_for(m->Dk) && bits_ok((uint32_t)m->class_bits) &&
+           m->enc >= HDC_ENC_FP32 && m->enc <= HDC_ENC_FP8_E4M3 && (m->enc != HDC_ENC_FP8_E4M3 || m->b_scale);
+}
+
+struct ModelLayout {
+    size_t bq, bscale, planes, csum, cnorm, total;
+};
+
+ModelLayout model_layout(int F, int Dk, int C, int enc, int bits)
+{
+    ModelLayout L;
+    size_t off = 0;
+    const int ldb = ld_for(enc, F), W = words_for(Dk);
+    L.bq = off;     off = align_up(off + (size_t)Dk * ldb * esize_for(enc), kAlign);
+    L.bscale = off; off = align_up(off + (enc == HDC_ENC_FP8_E4M3 ? (size_t)Dk * 4 : 0), kAlign);
+    L.planes = off; off = align_up(off + (size_t)bits * C * W * 4, kAlign);
+    L.csum = off;   off = align_up(off + (size_t)C * 4, kAlign);
+    L.cnorm = off;  off = align_up(off + (size_t)C * 8, kAlign);
+    L.total = off;
+    return L;
+}
+
+struct WsLayout {
+    size_t xq, sx, h, total;
+};
+
+WsLayout ws_layout(int64_t N, const hdc_model *m)
+{
+    WsLayout L;
+    size_t off = 0;
+    const bool quant = m->enc != HDC_ENC_FP32;
+    const int ldx = ld_for(m->enc, m->F);
+    L.xq = off; off = align_up(off + (quant ? (size_t)N * ldx * esize_for(m->enc) : 0), kAlign);
+    L.sx = off; off = align_up(off + (m->enc == HDC_ENC_FP8_E4M3 ? (size_t)N * 4 : 0), kAlign);
+    L.h = off;  off = align_up(off + (size_t)N * m->W * 4, kAlign);
+    L.total = off;
+    return L;
+}
+
+hdc_status cu(cudaError_t e) { return e == cudaSuccess ? HDC_OK : HDC_ERR_CUDA; }
+
+// Quantise X into the workspace (BF16/FP8); returns the operand to encode.
+hdc_status prepare_queries(const float *X, int64_t N, const hdc_model *m, char *ws, const WsLayout &L,
+                           const void **Xop, int64_t *ldx, const float **sx, cudaStream_t st)
+{
+    if (m->enc == HDC_ENC_FP32) {
+        *Xop = X;
+        *ldx = m->F;
+        *sx = nullptr;
+        return HDC_OK;
+    }
+    const int ld = ld_for(m->enc, m->F);
+    float *scale = m->enc == HDC_ENC_FP8_E4M3 ? (float *)(ws + L.sx) : nullptr;
+    hdc_status s = cu(launch_quant_rows(X, m->F, 0, 1, N, m->F, m->enc, ws + L.xq, ld, scale, st));
+    *Xop = ws + L.xq;
+    *ldx = ld;
+    *sx = scale;
+    return s;
+}
+
+// Tensor-core encoder for BF16/FP8 unless the configuration forces FFMA.
+bool use_tc(const hdc_model *m) { return m->enc != HDC_ENC_FP32 && !(m->flags & HDC_FLAG_SIMT_ENCODE); }
+
+}  // namespace
+}  // namespace hdc
+
+using namespace hdc;
+
+extern "C" {
+
+void hdc_default_config(hdc_approx_config *cfg)
+{
+    if (!cfg) return;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->struct_size = sizeof(*cfg);
+    cfg->perf_start = 0.f;
+    cfg->perf_end = 1.f;
+    cfg->perf_stride = 1;
+    cfg->enc = HDC_ENC_FP32;
+    cfg->class_bits = 1;
+    cfg->flags = 0;
+}
+
+int64_t hdc_kept_dims(int32_t D, const hdc_approx_config *cfg)
+{
+    Perf p;
+    if (cfg && cfg->struct_size < sizeof(hdc_approx_config)) return -1;
+    return perf_of(D, cfg, &p) ? p.Dk : -1;
+}
+
+int32_t hdc_words(int32_t L) { return L < 0 ? -1 : words_for(L); }
+
+hdc_status hdc_model_bytes(int32_t F, int32_t D, int32_t C, const hdc_approx_config *cfg, size_t *bytes)
+{
+    Perf p;
+    if (!bytes || F <= 0 || D <= 0 || C < 0 || !cfg_ok(cfg) || !perf_of(D, cfg, &p)) return HDC_ERR_INVALID_ARG;
+    if (!bits_ok(cfg->class_bits)) return HDC_ERR_UNSUPPORTED;
+    *bytes = model_layout(F, (int)p.Dk, C, cfg->enc, (int)cfg->class_bits).total;
+    return HDC_OK;
+}
+
+hdc_status hdc_model_prepare(const float *Bt, int32_t F, int32_t D, const int32_t *acc, int32_t C,
+                             const hdc_approx_config *cfg, void *buf, size_t buf_bytes, hdc_model *out,
+                             hdc_stream_t stream)
+{
+    Perf p;
+    if (!Bt || !buf || !out || F <= 0 || D <= 0 || C < 0 || (C > 0 && !acc) || !cfg_ok(cfg) ||
+        !perf_of(D, cfg, &p) || !aligned(buf, kAlign))
+        return HDC_ERR_INVALID_ARG;
+    if (!bits_ok(cfg->class_bits)) return HDC_ERR_UNSUPPORTED;
+    const int Dk = (int)p.Dk, enc = cfg->enc, bits = (int)cfg->class_bits;
+    const ModelLayout L = model_layout(F, Dk, C, enc, bits);
+    if (buf_bytes < L.total) return HDC_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *b = (char *)buf;
+    hdc_model m;
+    memset(&m, 0, sizeof(m));
+    m.struct_size = sizeof(hdc_model);
+    m.F = F;
+    m.D = D;
+    m.Dk = Dk;
+    m.C = C;
+    m.enc = enc;
+    m.ldb = ld_for(enc, F);
+    m.class_bits = bits;
+    m.flags = cfg->flags;
+    m.W = words_for(Dk);
+    m.Bq = b + L.bq;
+    m.b_scale = enc == HDC_ENC_FP8_E4M3 ? (const float *)(b + L.bscale) : nullptr;
+    // rows K of B^T: row k of Bq = quantise(Bt[s0 + k*stride])
+    hdc_status s = cu(launch_quant_rows(Bt, F, p.s0, p.stride, Dk, F, enc, b + L.bq, m.ldb,
+                                        (float *)(b + L.bscale), st));
+    if (s != HDC_OK) return s;
+    if (C > 0) {
+        m.cls = (const uint32_t *)(b + L.planes);
+        m.cls_sum = (const int32_t *)(b + L.csum);
+        m.cls_norm = (const double *)(b + L.cnorm);
+        s = cu(launch_class_prepare(acc, C, D, p, bits, (uint32_t *)(b + L.planes), m.W, (int32_t *)(b + L.csum),
+                                    (double *)(b + L.cnorm), st));
+        if (s != HDC_OK) return s;
+    }
+    *out = m;
+    return HDC_OK;
+}
+
+hdc_status hdc_workspace_bytes(int64_t N, const hdc_model *m, size_t *bytes)
+{
+    if (!bytes || N < 0 || !model_ok(m)) return HDC_ERR_INVALID_ARG;
+    *bytes = ws_layout(N, m).total;
+    return HDC_OK;
+}
+
+hdc_status hdc_encode(const float *X, int64_t N, const hdc_model *m, uint32_t *H, float *scores, void *ws,
+                      size_t ws_bytes, hdc_stream_t stream)
+{
+    if (N < 0 || !model_ok(m)) return HDC_ERR_INVALID_ARG;
+    if (N == 0) return HDC_OK;
+    if (!X || !H || !aligned(H, 16) || (ws_bytes && !ws) || (ws && !aligned(ws, kAlign))) return HDC_ERR_INVALID_ARG;
+    const WsLayout L = ws_layout(N, m);
+    if (ws_bytes < L.total) return HDC_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    const void *Xop;
+    int64_t ldx;
+    const float *sx;
+    hdc_status s = prepare_queries(X, N, m, (char *)ws, L, &Xop, &ldx, &sx, st);
+    if (s != HDC_OK) return s;
+    if (use_tc(m)) {
+        TcArgs a = {};
+        a.Xq = Xop; a.N = N; a.ldx = (int)ldx; a.Bq = m->Bq; a.ldb = m->ldb; a.Dk = m->Dk; a.enc = m->enc;
+        a.sx = sx; a.sb = m->b_scale; a.H = H; a.scores = scores; a.W = m->W;
+        if (tc_supported(a)) return cu(launch_tc_encode(a, st));
+    }
+    return cu(launch_encode_simt(Xop, ldx, N, m->F, m->Bq, m->ldb, m->Dk, m->enc, sx, m->b_scale, H, m->W, scores,
+                                 st));
+}
+
+hdc_status hdc_hamming_argmin(const uint32_t *Q, const uint32_t *Cls, int64_t N, int32_t C, int32_t D,
+                              const hdc_approx_config *cfg, int32_t *labels, int32_t *dists, hdc_stream_t stream)
+{
+    Perf p;
+    if (N < 0 || C <= 0 || D <= 0) return HDC_ERR_INVALID_ARG;
+    if (cfg && (cfg->struct_size < sizeof(hdc_approx_config) || !perf_of(D, cfg, &p))) return HDC_ERR_INVALID_ARG;
+    if (N == 0) return HDC_OK;
+    if (!Q || !Cls || !labels || !aligned(Q, 16) || !aligned(Cls, 16)) return HDC_ERR_INVALID_ARG;
+    const bool perforated = cfg && !(p.s0 == 0 && p.e0 == D && p.stride == 1);
+    return cu(launch_similarity(Q, N, Cls, C, words_for(D), 1, D, perforated ? &p : nullptr, nullptr, nullptr,
+                                labels, dists, nullptr, (cudaStream_t)stream));
+}
+
+hdc_status hdc_train_workspace_bytes(int64_t N, int32_t D, int32_t C, size_t *bytes)
+{
+    if (!bytes || N < 0 || D <= 0 || C <= 0) return HDC_ERR_INVALID_ARG;
+    *bytes = align_up((size_t)N * 4, kAlign);
+    return HDC_OK;
+}
+
+hdc_status hdc_train_epoch(const uint32_t *H, const int32_t *y, int64_t N, int32_t D, int32_t C, int32_t mode,
+                           int32_t *acc, uint32_t *cls, int32_t *n_updates, void *ws, size_t ws_bytes,
+                           hdc_stream_t stream)
+{
+    if (N < 0 || D <= 0 || C <= 0 || (mode != 0 && mode != 1) || !acc || !cls || !aligned(cls, 16))
+        return HDC_ERR_INVALID_ARG;
+    if (N > 0 && (!H || !y || !aligned(H, 16))) return HDC_ERR_INVALID_ARG;
+    const int W = words_for(D);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mode == 1 && N > 0) {
+        if (!ws || ws_bytes < (size_t)N * 4) return HDC_ERR_WORKSPACE;
+    }
+    if (n_updates) {
+        hdc_status s = cu(cudaMemsetAsync(n_updates, 0, sizeof(int32_t), st));
+        if (s != HDC_OK) return s;
+    }
+    if (mode == 0) {
+        hdc_status s = cu(cudaMemsetAsync(acc, 0, (size_t)C * D * sizeof(int32_t), st));
+        if (s != HDC_OK) return s;
+        s = cu(launch_train_count(H, W, y, nullptr, N, D, C, 0, acc, nullptr, st));
+        if (s != HDC_OK) return s;
+    } else if (N > 0) {
+        int32_t *pred = (int32_t *)ws;
+        hdc_status s = cu(launch_similarity(H, N, cls, C, W, 1, D, nullptr, nullptr, nullptr, pred, nullptr, nullptr,
+                                            st));
+        if (s != HDC_OK) return s;
+        s = cu(launch_train_count(H, W, y, pred, N, D, C, 1, acc, n_updates, st));
+        if (s != HDC_OK) return s;
+    }
+    return cu(launch_binarise(acc, C, D, cls, W, st));
+}
+
+hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *labels, int32_t *dists,
+                        double *scores, void *ws, size_t ws_bytes, hdc_stream_t stream)
+{
+    if (N < 0 || !model_ok(m) || m->C <= 0 || !m->cls) return HDC_ERR_INVALID_ARG;
+    if (N == 0) return HDC_OK;
+    if (!X || !labels || (ws_bytes && !ws) || (ws && !aligned(ws, kAlign))) return HDC_ERR_INVALID_ARG;
+    const WsLayout L = ws_layout(N, m);
+    if (ws_bytes < L.total) return HDC_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nb = m->class_bits;
+    const void *Xop;
+    int64_t ldx;
+    const float *sx;
+    hdc_status s = prepare_queries(X, N, m, (char *)ws, L, &Xop, &ldx, &sx, st);
+    if (s != HDC_OK) return s;
+    if (use_tc(m)) {
+        TcArgs a = {};
+        a.Xq = Xop; a.N = N; a.ldx = (int)ldx; a.Bq = m->Bq; a.ldb = m->ldb; a.Dk = m->Dk; a.enc = m->enc;
+        a.sx = sx; a.sb = m->b_scale; a.W = m->W;
+        a.planes = m->cls; a.C = m->C; a.nb = nb; a.csum = m->cls_sum; a.cnorm = m->cls_norm;
+        a.labels = labels; a.dists = dists; a.sims = scores;
+        if (tc_supported(a)) return cu(launch_tc_encode(a, st));
+    }
+    uint32_t *Hb = (uint32_t *)((char *)ws + L.h);
+    s = cu(launch_encode_simt(Xop, ldx, N, m->F, m->Bq, m->ldb, m->Dk, m->enc, sx, m->b_scale, Hb, m->W, nullptr,
+                              st));
+    if (s != HDC_OK) return s;
+    return cu(launch_similarity(Hb, N, m->cls, m->C, m->W, nb, m->Dk, nullptr, m->cls_sum, m->cls_norm, labels,
+                                dists, scores, st));
+}
+
+hdc_status hdc_stream_status(hdc_stream_t stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HDC_ERR_CUDA;
+    int status = 0;
+    if (tc_read_status(st, &status) != cudaSuccess) return HDC_ERR_CUDA;
+    if (status == 1) return HDC_ERR_TIMEOUT;
+    if (status != 0) return HDC_ERR_DEVICE;
+    return HDC_OK;
+}
+
+const char *hdc_status_string(hdc_status s)
+{
+    switch (s) {
+    case HDC_OK: return "ok";
+    case HDC_ERR_INVALID_ARG: return "invalid argument";
+    case HDC_ERR_UNSUPPORTED: return "unsupported configuration";
+    case HDC_ERR_WORKSPACE: return "buffer or workspace too small";
+    case HDC_ERR_CUDA: return "CUDA error";
+    case HDC_ERR_TIMEOUT: return "device wait timed out";
+    case HDC_ERR_DEVICE: return "device-side check failed";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// Internal declarations shared by the translation units of libhdc.
+// Not part of the ABI (include/hdc.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hdc.h"
+
+namespace hdc {
+
+constexpr int kAlign = 256;  // alignment of every sub-buffer we carve
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Words per packed row of L dims: ceil(L/32) rounded up to a multiple of 4.
+inline int words_for(int64_t L) { return (int)((((L + 31) / 32) + 3) / 4 * 4); }
+
+// Reduction-perforation index set (Sec. 4.2 "Reduction Perforation";
+// Listing 1 red_perf(start, end, stride) with start/end fractions of D):
+// kept dims are s0, s0+stride, ... below e0.
+struct Perf {
+    int64_t s0, e0, stride, Dk;
+};
+bool perf_of(int64_t D, const hdc_approx_config *cfg, Perf *p);
+
+// Row padding of the quantised operands, in elements: one 128-byte swizzle
+// row of the tensor-core tiles (64 BF16 or 128 FP8), 32 floats for FP32.
+inline int ld_for(int enc, int F) {
+    int q = enc == HDC_ENC_BF16 ? 64 : enc == HDC_ENC_FP8_E4M3 ? 128 : 32;
+    return (F + q - 1) / q * q;
+}
+inline int esize_for(int enc) { return enc == HDC_ENC_BF16 ? 2 : enc == HDC_ENC_FP8_E4M3 ? 1 : 4; }
+
+// ---- launchers (each returns the launch error) -----------------------------
+
+// K1: quantise rows src[row_off + k*row_step] (F floats each, row stride lds)
+// into dst row k (ldd elements, zero padded); FP8 writes the row's power-of-
+// two scale to scale[k].  enc: HDC_ENC_FP32 (copy), BF16, FP8_E4M3.
+cudaError_t launch_quant_rows(const float *src, int64_t lds, int64_t row_off, int64_t row_step,
+                              int64_t nrows, int F, int enc, void *dst, int ldd, float *scale,
+                              cudaStream_t st);
+
+// Class preparation: planes [b][C][W], sums and norms over the kept dims.
+cudaError_t launch_class_prepare(const int32_t *acc, int C, int D, const Perf &p, int b,
+                                 uint32_t *planes, int W, int32_t *csum, double *cnorm,
+                                 cudaStream_t st);
+
+// K0: CUDA-core encode + sign + pack: H (N x W), optional scores (N x Dk).
+// X: N x ldx elements of type enc (FP32 rows may be unpadded: ldx = F),
+// Bq: Dk x ldb elements of type enc.  sx / sb: row scales or NULL.
+cudaError_t launch_encode_simt(const void *X, int64_t ldx, int64_t N, int F, const void *Bq, int ldb,
+                               int Dk, int enc, const float *sx, const float *sb, uint32_t *H, int W,
+                               float *scores, cudaStream_t st);
+
+// K4: similarity + arg-min/arg-max over packed hypervectors.
+//  nb == 1: Hamming distance to plane 0, masked by perforation p over D
+//           (p == NULL: every dim of W words counts), arg-min.
+//  nb  > 1: cosine score from nb two's-complement planes, arg-max.
+cudaError_t launch_similarity(const uint32_t *Q, int64_t N, const uint32_t *planes, int C, int W,
+                              int nb, int64_t D, const Perf *p, const int32_t *csum,
+                              const double *cnorm, int32_t *labels, int32_t *dists, double *scores,
+                              cudaStream_t st);
+
+// K5: signed bit counts of the training rows into acc (C x D int32).
+//  mode 0: row n adds (1-2 bit) to class y_n.
+//  mode 1: rows with pred_n != y_n add to y_n and subtract from pred_n,
+//          and n_updates (if not NULL) counts them.
+cudaError_t launch_train_count(const uint32_t *H, int W, const int32_t *y, const int32_t *pred,
+                               int64_t N, int D, int C, int mode, int32_t *acc, int32_t *n_updates,
+                               cudaStream_t st);
+
+// K6 (binary): cls[c] = pack(acc[c] < 0) over D dims, W words per row.
+cudaError_t launch_binarise(const int32_t *acc, int C, int D, uint32_t *cls, int W, cudaStream_t st);
+
+// Tensor-core (tcgen05) encode, fused with Hamming / cosine and arg-min.
+// Returns cudaErrorNotSupported when the shape is outside what it handles.
+struct TcArgs {
+    const void *Xq;   // N x ldx quantised queries (BF16 or FP8)
+    int64_t N;
+    int ldx;          // elements per row (multiple of the K block)
+    const void *Bq;   // Dk x ldb quantised base rows
+    int ldb;
+    int Dk;
+    int enc;
+    const float *sx, *sb;       // row scales (FP8) or NULL
+    uint32_t *H;                // encode-only output (N x W) or NULL
+    float *scores;              // optional N x Dk projections
+    int W;
+    // fused similarity (classify); planes == NULL for encode-only
+    const uint32_t *planes;
+    int C, nb;
+    const int32_t *csum;
+    const double *cnorm;
+    int32_t *labels, *dists;
+    double *sims;
+};
+cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st);
+bool tc_supported(const TcArgs &a);
+
+// Reads and clears the tensor-core kernels' device status word.
+cudaError_t tc_read_status(cudaStream_t st, int *status);
+
+}  // namespace hdc

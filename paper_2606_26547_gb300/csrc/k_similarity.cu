@@ -1,0 +1,150 @@
+// K4: similarity of packed query hypervectors to C class hypervectors and
+// the nearest class (Listing 1: __hetero_hdc_hamming_distance, red_perf,
+// __hetero_hdc_arg_min; Sec. 4.2 Automatic Binarization: xor + popcount).
+//
+//  NB == 1  Hamming distance, dist = sum_w popc((q ^ c) & mask), arg-min.
+//           The mask selects the kept dims of a perforated reduction
+//           (all ones without perforation; pad bits are zero in q and c).
+//  NB  > 1  cosine on b-bit class hypervectors stored as two's-complement
+//           bit planes: with q_d = 1 - 2*bit_d,
+//             dot_c = sum_d q_d chat_d = S_c - 2 * sum_j w_j popc(plane_j & q)
+//           (S_c = sum_d chat_d, w_j = 2^j, w_{b-1} = -2^{b-1});
+//           score = dot / ||chat|| in IEEE FP64, arg-max.
+// Ties go to the lowest class index.
+//
+// One query per thread, 128 per block; class words are staged through shared
+// memory in chunks of WCH words, partial sums live in shared memory
+// (acc[c][thread]) so C is a runtime value.
+#include "hdc_internal.cuh"
+
+namespace hdc {
+namespace {
+
+constexpr int TPB = 128;
+
+template <int NB>
+__global__ void __launch_bounds__(TPB) similarity_kernel(const uint32_t *__restrict__ Q, int64_t N,
+                                                         const uint32_t *__restrict__ planes, int C, int W, int WCH,
+                                                         int use_mask, int64_t s0, int64_t e0, int64_t stride,
+                                                         const int32_t *__restrict__ csum,
+                                                         const double *__restrict__ cnorm,
+                                                         int32_t *__restrict__ labels, int32_t *__restrict__ dists,
+                                                         double *__restrict__ scores)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    int32_t *acc = reinterpret_cast<int32_t *>(smem);        // C x TPB
+    uint32_t *cw = smem + (size_t)C * TPB;                    // NB x C x WCH
+    uint32_t *mk = cw + (size_t)NB * C * WCH;                 // WCH
+    const int tid = threadIdx.x;
+    const int64_t row = (int64_t)blockIdx.x * TPB + tid;
+    const bool valid = row < N;
+    const uint32_t *qrow = Q + (valid ? row : 0) * (int64_t)W;
+
+    for (int c = 0; c < C; c++) acc[c * TPB + tid] = 0;
+
+    for (int w0 = 0; w0 < W; w0 += WCH) {
+        const int nw = min(WCH, W - w0);
+        __syncthreads();
+        for (int i = tid; i < NB * C * WCH; i += TPB) {
+            const int pc = i / WCH, j = i % WCH;   // pc = plane*C + class
+            cw[i] = j < nw ? planes[(int64_t)pc * W + w0 + j] : 0u;
+        }
+        for (int j = tid; j < WCH; j += TPB) {
+            uint32_t m = 0xffffffffu;
+            if (use_mask) {  // kept dims s0, s0+stride, ... < e0 inside this word
+                m = 0;
+                const int64_t base = (int64_t)(w0 + j) * 32;
+                const int64_t lo = max(s0, base), hi = min(e0, base + 32);
+                if (lo < hi) {
+                    const int64_t r = (lo - s0) % stride;
+                    for (int64_t d = r ? lo + (stride - r) : lo; d < hi; d += stride) m |= 1u << (d - base);
+                }
+            }
+            mk[j] = j < nw ? m : 0u;
+        }
+        __syncthreads();
+        for (int j0 = 0; j0 < nw; j0 += 4) {  // W and WCH are multiples of 4
+            uint4 qv = valid ? *reinterpret_cast<const uint4 *>(qrow + w0 + j0) : make_uint4(0, 0, 0, 0);
+            uint32_t q[4] = {qv.x & mk[j0], qv.y & mk[j0 + 1], qv.z & mk[j0 + 2], qv.w & mk[j0 + 3]};
+            if (NB == 1) {
+                for (int c = 0; c < C; c++) {
+                    const uint4 cv = *reinterpret_cast<const uint4 *>(cw + c * WCH + j0);
+                    const int part = __popc(q[0] ^ (cv.x & mk[j0])) + __popc(q[1] ^ (cv.y & mk[j0 + 1])) +
+                                     __popc(q[2] ^ (cv.z & mk[j0 + 2])) + __popc(q[3] ^ (cv.w & mk[j0 + 3]));
+                    acc[c * TPB + tid] += part;
+                }
+            } else {
+                for (int c = 0; c < C; c++) {
+                    int part = 0;
+#pragma unroll
+                    for (int p = 0; p < NB; p++) {
+                        const uint4 pv = *reinterpret_cast<const uint4 *>(cw + (p * C + c) * WCH + j0);
+                        const int cnt = __popc(q[0] & pv.x) + __popc(q[1] & pv.y) + __popc(q[2] & pv.z) +
+                                        __popc(q[3] & pv.w);
+                        part += (p == NB - 1) ? -(cnt << p) : (cnt << p);
+                    }
+                    acc[c * TPB + tid] += part;
+                }
+            }
+        }
+    }
+    if (!valid) return;
+    if (NB == 1) {
+        int best = 0, bv = acc[tid];
+        for (int c = 0; c < C; c++) {
+            const int v = acc[c * TPB + tid];
+            if (dists) dists[row * C + c] = v;
+            if (v < bv) { bv = v; best = c; }
+        }
+        labels[row] = best;
+    } else {
+        int best = 0;
+        double bs = 0.0;
+        for (int c = 0; c < C; c++) {
+            const double nrm = cnorm[c];
+            const double s = nrm == 0.0 ? 0.0 : (double)(csum[c] - 2 * acc[c * TPB + tid]) / nrm;
+            if (scores) scores[row * C + c] = s;
+            if (c == 0 || s > bs) { bs = s; best = c; }
+        }
+        labels[row] = best;
+    }
+}
+
+template <int NB>
+cudaError_t launch_nb(const uint32_t *Q, int64_t N, const uint32_t *planes, int C, int W, int64_t D, const Perf *p,
+                      const int32_t *csum, const double *cnorm, int32_t *labels, int32_t *dists, double *scores,
+                      cudaStream_t st)
+{
+    // words per staged chunk: multiple of 4 with NB*C*WCH*4 bytes <= 64 KB
+    int WCH = (16384 / (NB * C)) / 4 * 4;
+    if (WCH < 4) return cudaErrorNotSupported;
+    if (WCH > 256) WCH = 256;
+    if (WCH > W) WCH = W;
+    const size_t smem = ((size_t)C * TPB + (size_t)NB * C * WCH + WCH) * sizeof(uint32_t);
+    if (smem > 200 * 1024) return cudaErrorNotSupported;
+    cudaError_t e = cudaFuncSetAttribute(similarity_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int use_mask = p != nullptr;
+    const int64_t s0 = p ? p->s0 : 0, e0 = p ? p->e0 : D, stride = p ? p->stride : 1;
+    const int64_t blocks = (N + TPB - 1) / TPB;
+    similarity_kernel<NB><<<(unsigned)blocks, TPB, smem, st>>>(Q, N, planes, C, W, WCH, use_mask, s0, e0, stride,
+                                                               csum, cnorm, labels, dists, scores);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_similarity(const uint32_t *Q, int64_t N, const uint32_t *planes, int C, int W, int nb, int64_t D,
+                              const Perf *p, const int32_t *csum, const double *cnorm, int32_t *labels,
+                              int32_t *dists, double *scores, cudaStream_t st)
+{
+    if (N <= 0) return cudaSuccess;
+    switch (nb) {
+    case 1: return launch_nb<1>(Q, N, planes, C, W, D, p, csum, cnorm, labels, dists, scores, st);
+    case 4: return launch_nb<4>(Q, N, planes, C, W, D, nullptr, csum, cnorm, labels, dists, scores, st);
+    case 8: return launch_nb<8>(Q, N, planes, C, W, D, nullptr, csum, cnorm, labels, dists, scores, st);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+}  // namespace hdc

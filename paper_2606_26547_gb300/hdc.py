@@ -1,0 +1,254 @@
+"""Thin Python binding of libhdc (include/hdc.h) over torch CUDA tensors.
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the current stream.  If the
+shared library has not been built the import fails loudly; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhdc.so")
+
+ENC = {"fp32": 0, "bf16": 1, "fp8": 2}
+FLAG_SIMT_ENCODE = 0x1
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported configuration", 3: "buffer or workspace too small",
+          4: "CUDA error", 5: "device wait timed out", 6: "device-side check failed"}
+
+
+class HdcError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__("%s failed: %s (%d)" % (fn, STATUS.get(code, "?"), code))
+        self.code = code
+
+
+class ApproxConfigC(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("perf_start", ctypes.c_float), ("perf_end", ctypes.c_float),
+                ("perf_stride", ctypes.c_uint32), ("enc", ctypes.c_int32), ("class_bits", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32)]
+
+
+class ModelC(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("F", ctypes.c_int32), ("D", ctypes.c_int32),
+                ("Dk", ctypes.c_int32), ("C", ctypes.c_int32), ("enc", ctypes.c_int32), ("ldb", ctypes.c_int32),
+                ("class_bits", ctypes.c_int32), ("W", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("Bq", ctypes.c_void_p), ("b_scale", ctypes.c_void_p), ("cls", ctypes.c_void_p),
+                ("cls_sum", ctypes.c_void_p), ("cls_norm", ctypes.c_void_p)]
+
+
+_P, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+_SIGS = {
+    "hdc_default_config": (None, [_P]),
+    "hdc_kept_dims": (_I64, [_I32, _P]),
+    "hdc_words": (_I32, [_I32]),
+    "hdc_model_bytes": (_I32, [_I32, _I32, _I32, _P, _P]),
+    "hdc_model_prepare": (_I32, [_P, _I32, _I32, _P, _I32, _P, _P, _SZ, _P, _P]),
+    "hdc_workspace_bytes": (_I32, [_I64, _P, _P]),
+    "hdc_encode": (_I32, [_P, _I64, _P, _P, _P, _P, _SZ, _P]),
+    "hdc_hamming_argmin": (_I32, [_P, _P, _I64, _I32, _I32, _P, _P, _P, _P]),
+    "hdc_train_workspace_bytes": (_I32, [_I64, _I32, _I32, _P]),
+    "hdc_train_epoch": (_I32, [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
+    "hdc_classify": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _SZ, _P]),
+    "hdc_stream_status": (_I32, [_P]),
+    "hdc_status_string": (ctypes.c_char_p, [_I32]),
+}
+EXPORTED = tuple(_SIGS)
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libhdc.so (raises if it is missing: build it with build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError("libhdc.so not built at %s; run paper_2606_26547_gb300.build.build()" % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _call(name: str, *args) -> None:
+    rc = getattr(load(), name)(*args)
+    if rc != 0:
+        raise HdcError(name, rc)
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclasses.dataclass(frozen=True)
+class ApproxConfig:
+    """Approximation knobs (Sec. 4.2): perforation, encoding type, class bits."""
+    perf_start: float = 0.0
+    perf_end: float = 1.0
+    perf_stride: int = 1
+    enc: str = "fp32"
+    class_bits: int = 1
+    simt: bool = False  # force the CUDA-core encoder
+
+    def c(self) -> ApproxConfigC:
+        cfg = ApproxConfigC()
+        load().hdc_default_config(ctypes.byref(cfg))
+        cfg.perf_start = self.perf_start
+        cfg.perf_end = self.perf_end
+        cfg.perf_stride = self.perf_stride
+        cfg.enc = ENC[self.enc]
+        cfg.class_bits = self.class_bits
+        cfg.flags = FLAG_SIMT_ENCODE if self.simt else 0
+        return cfg
+
+
+def kept_dims(D: int, cfg: ApproxConfig | None = None) -> int:
+    c = cfg.c() if cfg else None
+    return int(load().hdc_kept_dims(D, ctypes.byref(c) if c else None))
+
+
+def words(L: int) -> int:
+    return int(load().hdc_words(L))
+
+
+def _empty_bytes(n: int, device) -> torch.Tensor:
+    # 256-byte aligned device buffer (the caching allocator aligns to 512)
+    return torch.empty(max(int(n), 1), dtype=torch.uint8, device=device)
+
+
+class Model:
+    """A prepared model (hdc_model_prepare): its device buffer and views."""
+
+    def __init__(self, Bt: torch.Tensor, cfg: ApproxConfig, acc: torch.Tensor | None = None,
+                 stream=None):
+        assert Bt.dtype == torch.float32 and Bt.dim() == 2
+        D, F = Bt.shape
+        C = 0 if acc is None else acc.shape[0]
+        if acc is not None:
+            assert acc.dtype == torch.int32 and acc.shape == (C, D)
+        self.cfg = cfg
+        c = cfg.c()
+        nbytes = ctypes.c_size_t()
+        _call("hdc_model_bytes", F, D, C, ctypes.byref(c), ctypes.byref(nbytes))
+        self.buf = _empty_bytes(nbytes.value, Bt.device)
+        self.m = ModelC()
+        _call("hdc_model_prepare", _ptr(Bt), F, D, _ptr(acc), C, ctypes.byref(c), _ptr(self.buf),
+              nbytes.value, ctypes.byref(self.m), _stream(stream))
+        self.device = Bt.device
+
+    @property
+    def W(self) -> int:
+        return self.m.W
+
+    @property
+    def Dk(self) -> int:
+        return self.m.Dk
+
+    @property
+    def C(self) -> int:
+        return self.m.C
+
+    def workspace_bytes(self, N: int) -> int:
+        n = ctypes.c_size_t()
+        _call("hdc_workspace_bytes", N, ctypes.byref(self.m), ctypes.byref(n))
+        return n.value
+
+    def workspace(self, N: int) -> torch.Tensor:
+        return _empty_bytes(self.workspace_bytes(N), self.device)
+
+
+def encode(X: torch.Tensor, model: Model, scores: bool = False, ws: torch.Tensor | None = None,
+           stream=None):
+    """Packed hypervectors (N x W int32 view of uint32 words), [projections]."""
+    assert X.dtype == torch.float32 and X.dim() == 2 and X.shape[1] == model.m.F
+    N = X.shape[0]
+    H = torch.empty((N, model.W), dtype=torch.int32, device=X.device)
+    S = torch.empty((N, model.Dk), dtype=torch.float32, device=X.device) if scores else None
+    ws = model.workspace(N) if ws is None else ws
+    _call("hdc_encode", _ptr(X), N, ctypes.byref(model.m), _ptr(H), _ptr(S), _ptr(ws), ws.numel(),
+          _stream(stream))
+    return (H, S) if scores else H
+
+
+def hamming_argmin(Q: torch.Tensor, Cls: torch.Tensor, D: int, cfg: ApproxConfig | None = None,
+                   dists: bool = False, stream=None):
+    N, C = Q.shape[0], Cls.shape[0]
+    labels = torch.empty(N, dtype=torch.int32, device=Q.device)
+    dd = torch.empty((N, C), dtype=torch.int32, device=Q.device) if dists else None
+    c = cfg.c() if cfg else None
+    _call("hdc_hamming_argmin", _ptr(Q), _ptr(Cls), N, C, D, ctypes.byref(c) if c else None, _ptr(labels),
+          _ptr(dd), _stream(stream))
+    return (labels, dd) if dists else labels
+
+
+def train_epoch(H: torch.Tensor, y: torch.Tensor, D: int, C: int, mode: int, acc: torch.Tensor,
+                cls: torch.Tensor, n_updates: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+                stream=None) -> None:
+    """One bundling (mode 0) or retraining (mode 1) pass; updates acc and cls."""
+    N = H.shape[0]
+    if ws is None:
+        n = ctypes.c_size_t()
+        _call("hdc_train_workspace_bytes", N, D, C, ctypes.byref(n))
+        ws = _empty_bytes(n.value, H.device)
+    _call("hdc_train_epoch", _ptr(H), _ptr(y), N, D, C, mode, _ptr(acc), _ptr(cls), _ptr(n_updates),
+          _ptr(ws), ws.numel(), _stream(stream))
+
+
+def train(H: torch.Tensor, y: torch.Tensor, D: int, C: int, epochs: int, stream=None):
+    """Bundling then ``epochs`` retraining epochs; returns (acc, cls, updates)."""
+    acc = torch.empty((C, D), dtype=torch.int32, device=H.device)
+    cls = torch.empty((C, words(D)), dtype=torch.int32, device=H.device)
+    train_epoch(H, y, D, C, 0, acc, cls, stream=stream)
+    ups = []
+    nu = torch.zeros(1, dtype=torch.int32, device=H.device)
+    for _ in range(epochs):
+        train_epoch(H, y, D, C, 1, acc, cls, n_updates=nu, stream=stream)
+        ups.append(int(nu.item()))
+    return acc, cls, ups
+
+
+def classify(X: torch.Tensor, model: Model, sims: bool = False, ws: torch.Tensor | None = None,
+             labels: torch.Tensor | None = None, stream=None):
+    """Labels (N int32) and optionally the similarity (N x C int32 Hamming
+    distances for binary classes, N x C float64 cosine scores otherwise)."""
+    assert X.dtype == torch.float32 and X.dim() == 2 and X.shape[1] == model.m.F
+    N, C = X.shape[0], model.C
+    if labels is None:
+        labels = torch.empty(N, dtype=torch.int32, device=X.device)
+    dd = sc = None
+    if sims:
+        if model.m.class_bits == 1:
+            dd = torch.empty((N, C), dtype=torch.int32, device=X.device)
+        else:
+            sc = torch.empty((N, C), dtype=torch.float64, device=X.device)
+    ws = model.workspace(N) if ws is None else ws
+    _call("hdc_classify", _ptr(X), N, ctypes.byref(model.m), _ptr(labels), _ptr(dd), _ptr(sc), _ptr(ws),
+          ws.numel(), _stream(stream))
+    if sims:
+        return labels, (dd if dd is not None else sc)
+    return labels
+
+
+def stream_status(stream=None) -> int:
+    """Synchronise the stream and return (and clear) the device status."""
+    return int(load().hdc_stream_status(_stream(stream)))

@@ -1,0 +1,84 @@
+"""Host-side checks of the C ABI: the library loads without a GPU, exports
+every function include/hdc.h declares, and its host-only logic (perforation
+index sets, word counts, argument checks) agrees with the oracle and the
+header.  No kernel is launched."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_26547_gb300 import build, hdc
+    build.build()
+    return hdc.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hdc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hdc_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_2606_26547_gb300 import hdc
+    names = _declared()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(hdc.EXPORTED) | set()
+
+
+def test_kept_dims_matches_oracle(lib, orc):
+    from paper_2606_26547_gb300 import hdc
+    rng = np.random.default_rng(0)
+    cases = [(2048, 0.0, 0.5, 1), (10000, 0.0, 1.0, 2), (16384, 0.0, 1.0, 2), (10000, 0.1, 0.9, 3),
+             (617, 0.3, 0.7, 5), (1, 0.0, 1.0, 1)]
+    for _ in range(200):
+        s, e = sorted(rng.uniform(0, 1, 2))
+        cases.append((int(rng.integers(1, 20000)), float(np.float32(s)), float(np.float32(e)),
+                      int(rng.integers(1, 9))))
+    for D, s, e, st in cases:
+        cfg = hdc.ApproxConfig(perf_start=s, perf_end=e, perf_stride=st)
+        try:
+            n = orc.kept_dims(D, s, e, st).size
+        except ValueError:
+            n = -1
+        got = hdc.kept_dims(D, cfg)
+        assert got == (n if n > 0 else -1), (D, s, e, st)
+
+
+def test_words(lib):
+    from paper_2606_26547_gb300 import hdc
+    from tests._helpers import words_for
+    for L in (1, 31, 32, 33, 128, 129, 1000, 10000, 16384):
+        assert hdc.words(L) == words_for(L)
+
+
+def test_status_strings(lib):
+    for code in range(7):
+        assert lib.hdc_status_string(code)
+
+
+def test_argument_checks_without_gpu(lib):
+    """Invalid arguments are rejected before anything is enqueued."""
+    from paper_2606_26547_gb300 import hdc
+    cfg = hdc.ApproxConfig().c()
+    n = ctypes.c_size_t()
+    assert lib.hdc_model_bytes(0, 10, 2, ctypes.byref(cfg), ctypes.byref(n)) == 1
+    assert lib.hdc_model_bytes(16, 10, 2, None, ctypes.byref(n)) == 1
+    bad = hdc.ApproxConfig(class_bits=3).c()
+    assert lib.hdc_model_bytes(16, 10, 2, ctypes.byref(bad), ctypes.byref(n)) == 2
+    assert lib.hdc_model_bytes(784, 10000, 10, ctypes.byref(cfg), ctypes.byref(n)) == 0 and n.value > 0
+    m = hdc.ModelC()
+    assert lib.hdc_model_prepare(None, 16, 10, None, 0, ctypes.byref(cfg), None, 0, ctypes.byref(m), None) == 1
+    assert lib.hdc_encode(None, 5, ctypes.byref(m), None, None, None, 0, None) == 1
+    assert lib.hdc_hamming_argmin(None, None, 5, 0, 10, None, None, None, None) == 1
+    assert lib.hdc_train_epoch(None, None, 5, 10, 2, 7, None, None, None, None, 0, None) == 1
+    assert lib.hdc_classify(None, 5, ctypes.byref(m), None, None, None, None, 0, None) == 1
+    assert lib.hdc_kept_dims(100, None) == 100

@@ -1,0 +1,250 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer and binary results (packed hypervectors, Hamming distances, labels,
+class accumulators, cosine scores of b-bit classes) must match bit for bit.
+Float encodings are compared with the bound derived from FP32 accumulation:
+|s_gpu - s_q| <= 4*F*2^-24 * sum_f |xq_f * bq_f|, where s_q is the FP64
+projection of the same quantised inputs; packed bits must agree wherever the
+oracle's |s_q| exceeds that bound.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from tests._helpers import pack, unpack, words_for
+
+pytestmark = pytest.mark.gpu
+
+ENCS = {"fp32": orc.ENC_FP32, "bf16": orc.ENC_BF16, "fp8": orc.ENC_FP8}
+
+
+@pytest.fixture(scope="module")
+def hdc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_26547_gb300 import build, hdc as h
+    build.build()
+    h.load()
+    orc.build()
+    return h
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev())
+
+
+def words_np(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def _model_bytes(model, ptr, nbytes):
+    off = ptr - model.buf.data_ptr()
+    return model.buf[off:off + nbytes].cpu().numpy()
+
+
+def decode_bq(model, enc):
+    m = model.m
+    es = {"fp32": 4, "bf16": 2, "fp8": 1}[enc]
+    raw = _model_bytes(model, m.Bq, m.Dk * m.ldb * es)
+    t = torch.from_numpy(raw.copy())
+    if enc == "fp32":
+        v = t.view(torch.float32)
+    elif enc == "bf16":
+        v = t.view(torch.bfloat16)
+    else:
+        v = t.view(torch.float8_e4m3fn)
+    return v.to(torch.float64).numpy().reshape(m.Dk, m.ldb)
+
+
+# ------------------------------------------------------------------ quantise
+
+@pytest.mark.parametrize("enc", ["bf16", "fp8", "fp32"])
+def test_base_quantisation_bit_exact(hdc, enc):
+    rng = np.random.default_rng(1)
+    D, F = 700, 617
+    Bt = (rng.standard_normal((D, F)) * 10.0 ** rng.uniform(-3, 3, (D, 1))).astype(np.float32)
+    Bt[5] = 0.0
+    Bt[9] = (rng.standard_normal(F) * 1e-41).astype(np.float32)   # subnormal row: scale 2^k, k < -126
+    Bt[11, 3] = 3.0e38                                               # huge entry
+    cfg = hdc.ApproxConfig(enc=enc, perf_start=0.0, perf_end=1.0, perf_stride=3)
+    model = hdc.Model(T(Bt), cfg)
+    dims = orc.kept_dims(D, 0.0, 1.0, 3)
+    q, sc = orc.quantise_rows(Bt[dims], ENCS[enc])
+    got = decode_bq(model, enc)
+    assert model.m.Dk == dims.size
+    assert np.array_equal(got[:, :F], q)
+    assert not got[:, F:].any()
+    if enc == "fp8":
+        gs = np.frombuffer(_model_bytes(model, model.m.b_scale, 4 * dims.size).tobytes(), dtype=np.float32)
+        assert np.array_equal(gs.astype(np.float64), sc)
+
+
+# -------------------------------------------------------------------- encode
+
+def _int_data(n, D=2048):
+    from paper_2606_26547_gb300 import synth
+    return synth.make("int_exact_F617_D2048_C26", n_train=n, n_query=8, D=D)
+
+
+@pytest.mark.parametrize("enc", ["fp32", "bf16", "fp8"])
+@pytest.mark.parametrize("simt", [False, True])
+@pytest.mark.parametrize("perf", [(0.0, 1.0, 1), (0.0, 0.5, 1), (0.1, 0.97, 3)])
+def test_encode_integer_bit_exact(hdc, enc, simt, perf):
+    d = _int_data(300)
+    X, Bt = d["Xtr"], d["Bt"]
+    cfg = hdc.ApproxConfig(enc=enc, perf_start=perf[0], perf_end=perf[1], perf_stride=perf[2], simt=simt)
+    model = hdc.Model(T(Bt), cfg)
+    H, S = hdc.encode(T(X), model, scores=True)
+    dims = orc.kept_dims(2048, *perf)
+    bits, s, _, _ = orc.encode_bits(X, Bt, orc.ENC_FP32, dims, integer=True)
+    assert np.array_equal(words_np(H), pack(bits, words_for(dims.size)))
+    assert np.array_equal(S.cpu().numpy().astype(np.float64), s.astype(np.float64))
+
+
+@pytest.mark.parametrize("enc", ["fp32", "bf16", "fp8"])
+@pytest.mark.parametrize("simt", [False, True])
+def test_encode_float_within_bound(hdc, enc, simt):
+    from paper_2606_26547_gb300 import synth
+    d = synth.make("precision_F784_D10000_C10", n_train=300, n_query=4, D=1000)
+    X, Bt = d["Xtr"], d["Bt"]
+    cfg = hdc.ApproxConfig(enc=enc, simt=simt)
+    model = hdc.Model(T(Bt), cfg)
+    H, S = hdc.encode(T(X), model, scores=True)
+    dims = orc.kept_dims(1000)
+    Xq, sx = orc.quantise_rows(X, ENCS[enc])
+    Bq, sb = orc.quantise_rows(Bt, ENCS[enc])
+    scale = sx[:, None] * sb[None, :]
+    sq = orc.encode_f64(Xq, Bq, dims) * scale
+    bound = 4 * 784 * 2.0 ** -24 * orc.encode_absdot(Xq, Bq, dims) * scale
+    err = np.abs(S.cpu().numpy().astype(np.float64) - sq)
+    assert np.all(err <= bound), float((err / np.maximum(bound, 1e-300)).max())
+    gb = unpack(words_np(H), 1000)
+    sure = np.abs(sq) > bound
+    assert np.array_equal(gb[sure], (sq < 0)[sure])
+    assert not unpack(words_np(H), words_for(1000) * 32)[:, 1000:].any()   # pad bits zero
+
+
+# ------------------------------------------------------------ Hamming arg-min
+
+@pytest.mark.parametrize("N,C,D", [(1, 1, 32), (300, 26, 2048), (257, 7, 1000), (129, 100, 16384), (50, 3, 33)])
+@pytest.mark.parametrize("perf", [None, (0.0, 0.5, 1), (0.05, 0.95, 4), (0.0, 1.0, 8)])
+def test_hamming_argmin_bit_exact(hdc, N, C, D, perf):
+    rng = np.random.default_rng(N * 7 + C)
+    q = rng.integers(0, 2, (N, D)).astype(np.uint8)
+    c = rng.integers(0, 2, (C, D)).astype(np.uint8)
+    if C > 2:
+        c[2] = c[1]                      # a guaranteed tie: lowest index wins
+    cfg = hdc.ApproxConfig(perf_start=perf[0], perf_end=perf[1], perf_stride=perf[2]) if perf else None
+    if perf and orc.kept_dims(D, *perf).size == 0:
+        pytest.skip("empty perforation")
+    labels, dd = hdc.hamming_argmin(T(pack(q).view(np.int32)), T(pack(c).view(np.int32)), D, cfg, dists=True)
+    dims = orc.kept_dims(D, *perf) if perf else orc.kept_dims(D)
+    od = orc.hamming(orc.gather_cols(q, dims), orc.gather_cols(c, dims))
+    assert np.array_equal(dd.cpu().numpy().astype(np.int64), od)
+    assert np.array_equal(labels.cpu().numpy(), orc.argmin(od))
+
+
+def test_hamming_all_ties(hdc):
+    q = np.zeros((40, 64), np.uint8)
+    c = np.ones((5, 64), np.uint8)
+    labels = hdc.hamming_argmin(T(pack(q).view(np.int32)), T(pack(c).view(np.int32)), 64)
+    assert not labels.cpu().numpy().any()
+
+
+# -------------------------------------------------------------------- train
+
+@pytest.mark.parametrize("N,D,C", [(500, 2048, 26), (333, 1000, 10), (1, 64, 1), (700, 10000, 6)])
+def test_train_bit_exact(hdc, N, D, C):
+    rng = np.random.default_rng(D + C)
+    protos = rng.integers(0, 2, (C, D)).astype(np.uint8)
+    y = rng.integers(0, C, N).astype(np.int32)
+    bits = protos[y] ^ (rng.random((N, D)) < 0.4).astype(np.uint8)
+    acc, cls, ups = hdc.train(T(pack(bits).view(np.int32)), T(y), D, C, epochs=4)
+    oacc, oups = orc.train(bits, y, C, 4)
+    assert np.array_equal(acc.cpu().numpy().astype(np.int64), oacc)
+    assert ups == oups
+    assert np.array_equal(words_np(cls), pack(orc.class_bits(oacc)))
+
+
+def test_train_skips_out_of_range_labels(hdc):
+    rng = np.random.default_rng(3)
+    bits = rng.integers(0, 2, (64, 96)).astype(np.uint8)
+    y = rng.integers(-1, 5, 64).astype(np.int32)            # -1 and 4 are skipped with C = 4
+    acc, cls, ups = hdc.train(T(pack(bits).view(np.int32)), T(y), 96, 4, epochs=1)
+    keep = (y >= 0) & (y < 4)
+    oacc, oups = orc.train(bits[keep], y[keep], 4, 1)
+    assert np.array_equal(acc.cpu().numpy().astype(np.int64), oacc) and ups == oups
+
+
+# ----------------------------------------------------------------- classify
+
+@pytest.mark.parametrize("enc", ["fp32", "bf16", "fp8"])
+@pytest.mark.parametrize("bits_", [1, 4, 8])
+@pytest.mark.parametrize("perf", [(0.0, 1.0, 1), (0.0, 0.5, 1), (0.0, 1.0, 2)])
+def test_classify_integer_end_to_end(hdc, enc, bits_, perf):
+    d = _int_data(600)
+    dims_full = orc.kept_dims(2048)
+    tb, _, _, _ = orc.encode_bits(d["Xtr"], d["Bt"], orc.ENC_FP32, dims_full, integer=True)
+    oacc, _ = orc.train(tb, d["ytr"], 26, 2)
+    from paper_2606_26547_gb300 import synth
+    Xq, _ = synth.int_mixture(333, 617, 26, 2.0, 77, 1000)
+    cfg = hdc.ApproxConfig(enc=enc, class_bits=bits_, perf_start=perf[0], perf_end=perf[1], perf_stride=perf[2])
+    model = hdc.Model(T(d["Bt"]), cfg, acc=T(oacc.astype(np.int32)))
+    labels, sims = hdc.classify(T(Xq), model, sims=True)
+    ol, osim = orc.classify(Xq, d["Bt"], oacc, orc.ENC_FP32, *perf, bits_, integer=True)
+    assert np.array_equal(labels.cpu().numpy(), ol)
+    if bits_ == 1:
+        assert np.array_equal(sims.cpu().numpy().astype(np.int64), osim)
+    else:
+        assert np.array_equal(sims.cpu().numpy(), osim)      # IEEE FP64 on both sides
+
+
+@pytest.mark.parametrize("enc", ["fp32", "bf16", "fp8"])
+@pytest.mark.parametrize("bits_", [1, 8])
+def test_classify_float_consistent_with_encode(hdc, enc, bits_):
+    """Float encodings: the fused classify equals Hamming/cosine of the
+    hypervectors hdc_encode produces with the same model, and those agree
+    with the FP64 oracle wherever the projection's sign is certain."""
+    from paper_2606_26547_gb300 import synth
+    d = synth.make("precision_F784_D10000_C10", n_train=400, n_query=300, D=1000)
+    dims = orc.kept_dims(1000)
+    tb, _, _, _ = orc.encode_bits(d["Xtr"], d["Bt"], orc.ENC_FP32, dims)
+    oacc, _ = orc.train(tb, d["ytr"], 10, 2)
+    cfg = hdc.ApproxConfig(enc=enc, class_bits=bits_, perf_stride=2)
+    model = hdc.Model(T(d["Bt"]), cfg, acc=T(oacc.astype(np.int32)))
+    labels, sims = hdc.classify(T(d["Xq"]), model, sims=True)
+    H = hdc.encode(T(d["Xq"]), model)
+    kd = orc.kept_dims(1000, 0.0, 1.0, 2)
+    qb = unpack(words_np(H), kd.size)
+    if bits_ == 1:
+        od = orc.hamming(qb, orc.gather_cols(orc.class_bits(oacc), kd))
+        assert np.array_equal(sims.cpu().numpy().astype(np.int64), od)
+        assert np.array_equal(labels.cpu().numpy(), orc.argmin(od))
+    else:
+        sc = orc.cosine_scores(qb, orc.gather_cols(orc.class_quantise(oacc, bits_), kd))
+        assert np.array_equal(sims.cpu().numpy(), sc)
+        assert np.array_equal(labels.cpu().numpy(), orc.argmax(sc))
+    ol, _ = orc.classify(d["Xq"], d["Bt"], oacc, ENCS[enc], 0.0, 1.0, 2, bits_)
+    agree = (labels.cpu().numpy() == ol).mean()
+    assert agree >= 0.99, agree
+
+
+def test_classify_edge_cases(hdc):
+    rng = np.random.default_rng(5)
+    F, D = 33, 100
+    Bt = rng.standard_normal((D, F)).astype(np.float32)
+    acc = np.zeros((1, D), np.int32)                       # C = 1, all classes +1
+    model = hdc.Model(T(Bt), hdc.ApproxConfig(enc="bf16"), acc=T(acc))
+    lab = hdc.classify(T(np.zeros((1, F), np.float32)), model)
+    assert lab.cpu().numpy().tolist() == [0]
+    lab0 = hdc.classify(torch.empty((0, F), dtype=torch.float32, device=dev()), model)
+    assert lab0.numel() == 0
+    H = hdc.encode(T(np.zeros((3, F), np.float32)), model)   # x = 0 -> all +1 -> all bits 0
+    assert not words_np(H).any()
+    torch.cuda.synchronize()
+    assert hdc.stream_status() == 0
