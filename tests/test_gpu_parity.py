@@ -248,3 +248,45 @@ def test_classify_edge_cases(hdc):
     assert not words_np(H).any()
     torch.cuda.synchronize()
     assert hdc.stream_status() == 0
+
+
+# ------------------------------------------- tensor-core path specifics
+
+@pytest.mark.parametrize("enc", ["bf16", "fp8"])
+@pytest.mark.parametrize("C,bits_", [(1, 1), (17, 1), (65, 4), (100, 1), (128, 8), (33, 8)])
+def test_tc_classify_matches_oracle_many_classes(hdc, enc, C, bits_):
+    """Class counts across every register block of the fused epilogue."""
+    rng = np.random.default_rng(C * 10 + bits_)
+    F, D, N = 200, 1300, 260
+    X = rng.integers(-8, 8, (N, F)).astype(np.float32)
+    Bt = (1 - 2 * rng.integers(0, 2, (D, F))).astype(np.float32)
+    acc = rng.integers(-300, 301, (C, D)).astype(np.int64)
+    cfg = hdc.ApproxConfig(enc=enc, class_bits=bits_, perf_stride=1)
+    model = hdc.Model(T(Bt), cfg, acc=T(acc.astype(np.int32)))
+    labels, sims = hdc.classify(T(X), model, sims=True)
+    ol, osim = orc.classify(X, Bt, acc, orc.ENC_FP32, 0.0, 1.0, 1, bits_, integer=True)
+    assert np.array_equal(labels.cpu().numpy(), ol)
+    if bits_ == 1:
+        assert np.array_equal(sims.cpu().numpy().astype(np.int64), osim)
+    else:
+        assert np.array_equal(sims.cpu().numpy(), osim)
+
+
+@pytest.mark.parametrize("enc", ["bf16", "fp8"])
+def test_tc_persistent_many_tiles_matches_simt(hdc, enc):
+    """More query tiles than SMs: every CTA loops over several tiles and
+    both TMEM accumulators; integer data make both encoders exact."""
+    rng = np.random.default_rng(11)
+    F, D, N = 96, 520, 152 * 128 * 2 + 77
+    X = rng.integers(-8, 8, (N, F)).astype(np.float32)
+    Bt = (1 - 2 * rng.integers(0, 2, (D, F))).astype(np.float32)
+    m_tc = hdc.Model(T(Bt), hdc.ApproxConfig(enc=enc))
+    m_si = hdc.Model(T(Bt), hdc.ApproxConfig(enc=enc, simt=True))
+    Xd = T(X)
+    h_tc, h_si = hdc.encode(Xd, m_tc), hdc.encode(Xd, m_si)
+    assert torch.equal(h_tc, h_si)
+    sub = rng.choice(N, 300, replace=False)
+    bits, _, _, _ = orc.encode_bits(X[sub], Bt, orc.ENC_FP32, orc.kept_dims(D), integer=True)
+    assert np.array_equal(words_np(h_tc)[sub], pack(bits, words_for(D)))
+    torch.cuda.synchronize()
+    assert hdc.stream_status() == 0
