@@ -284,18 +284,29 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *
     const float *sx;
     hdc_status s = prepare_queries(X, N, m, (char *)ws, L, &Xop, &ldx, &sx, st);
     if (s != HDC_OK) return s;
+    uint32_t *Hb = (uint32_t *)((char *)ws + L.h);
+    bool encoded = false;
     if (use_tc(m)) {
         TcArgs a = {};
         a.Xq = Xop; a.N = N; a.ldx = (int)ldx; a.Bq = m->Bq; a.ldb = m->ldb; a.Dk = m->Dk; a.enc = m->enc;
         a.sx = sx; a.sb = m->b_scale; a.W = m->W;
         a.planes = m->cls; a.C = m->C; a.nb = nb; a.csum = m->cls_sum; a.cnorm = m->cls_norm;
         a.labels = labels; a.dists = dists; a.sims = scores;
+        // binary classes: fully fused; otherwise tensor-core encode + K4
         if (tc_supported(a)) return cu(launch_tc_encode(a, st));
+        TcArgs e = a;
+        e.planes = nullptr; e.labels = nullptr; e.dists = nullptr; e.sims = nullptr; e.H = Hb;
+        if (tc_supported(e)) {
+            s = cu(launch_tc_encode(e, st));
+            if (s != HDC_OK) return s;
+            encoded = true;
+        }
     }
-    uint32_t *Hb = (uint32_t *)((char *)ws + L.h);
-    s = cu(launch_encode_simt(Xop, ldx, N, m->F, m->Bq, m->ldb, m->Dk, m->enc, sx, m->b_scale, Hb, m->W, nullptr,
-                              st));
-    if (s != HDC_OK) return s;
+    if (!encoded) {
+        s = cu(launch_encode_simt(Xop, ldx, N, m->F, m->Bq, m->ldb, m->Dk, m->enc, sx, m->b_scale, Hb, m->W,
+                                  nullptr, st));
+        if (s != HDC_OK) return s;
+    }
     return cu(launch_similarity(Hb, N, m->cls, m->C, m->W, nb, m->Dk, nullptr, m->cls_sum, m->cls_norm, labels,
                                 dists, scores, st));
 }

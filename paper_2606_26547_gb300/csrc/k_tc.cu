@@ -1,420 +1,14 @@
-// Tensor-core encoder for sm_103a (tcgen05 + TMA + TMEM), fused with sign
-// binarisation, bit packing and -- in classify mode -- Hamming distance (or
-// the b-bit cosine dot product) and arg-min, so encoded hypervectors never
-// reach device memory.
-//
-// What it computes (Listing 1 end to end, Sec. 4.2 knobs):
-//   s[i][k] = sum_f xq[i][f] * bq[k][f]   (BF16 or E4M3 operands, FP32
-//                                          accumulation in tensor memory)
-//   bit[i][k] = s < 0                      (sign(0) = +1)
-//   classify: dist[i][c] = sum_w popc(q_w ^ cls_c,w)      -> arg-min
-//             or dot via bit planes (see k_similarity.cu) -> arg-max
-//   encode:   H[i] = packed bits (and optionally the de-scaled s).
-// The per-row power-of-two scales of FP8 are positive, so they do not change
-// any bit; they are applied only to the optional projection output.
-//
-// Structure (one CTA per SM, persistent over 128-query tiles):
-//   warp 4 lane 0  TMA producer: A tile (128 queries x 128 B of K) and B tile
-//                  (256 dims x 128 B of K) per stage into a 4-stage ring,
-//                  128-byte swizzle, completion on an mbarrier;
-//   warp 5 lane 0  MMA issuer: 4 tcgen05.mma (K = 32 bytes each) per stage
-//                  into one of two 128 x 256 FP32 accumulators in TMEM,
-//                  tcgen05.commit frees the stage / publishes the tile;
-//   warps 0-3      epilogue: tcgen05.ld of the thread's row (TMEM lane),
-//                  32 columns at a time -> one packed word, releases the
-//                  accumulator, then popcounts against the class words.
-// Every wait is bounded by the global timer; on expiry the kernel records
-// status 1 in g_tc_status, stops its loops, drains its own copies and MMAs
-// (again with a bound), frees TMEM and returns.
-#include <cuda.h>
+// Host side of the tensor-core encoder: TMA tensor maps, support checks,
+// grid sizing and dispatch to the per-encoding translation units.
 #include <cudaTypedefs.h>
 
 #include <mutex>
 
-#include "hdc_internal.cuh"
+#include "tc_kernel.cuh"
 
 namespace hdc {
-
-__device__ int g_tc_status;  // 0 ok, 1 a wait timed out
-
 namespace {
 
-constexpr int BM = 128;                      // queries per tile (TMEM lanes)
-constexpr int BN = 256;                      // dims per tile (TMEM columns)
-constexpr int BKB = 128;                     // K bytes per stage row
-constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BKB;            // 16 KB
-constexpr int B_BYTES = BN * BKB;            // 32 KB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int NUM_THREADS = 192;
-constexpr int TMEM_COLS = 2 * BN;            // two accumulators
-constexpr int NUM_BARS = 2 * STAGES + 5;     // full, empty, tfull[2], tempty[2], done
-constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + NUM_BARS * 8 + 16;
-constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
-
-struct Params {
-    int64_t N;
-    int Dk, num_kb, W;
-    const float *sx, *sb;
-    uint32_t *H;
-    float *scores;
-    const uint32_t *planes;
-    int C, nb;
-    const int32_t *csum;
-    const double *cnorm;
-    int32_t *labels, *dists;
-    double *sims;
-};
-
-// ------------------------------------------------------------ PTX wrappers
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long gtimer()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t n)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(n) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity.  Returns false (and
-// raises the CTA's abort flag and the device status) after `limit` ns, or
-// as soon as another role of the CTA has aborted.
-__device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int *abort_flag,
-                                       unsigned long long limit = TIMEOUT_NS)
-{
-    if (mbar_try(a, parity)) return true;
-    const unsigned long long t0 = gtimer();
-    while (true) {
-        for (int i = 0; i < 32; i++)
-            if (mbar_try(a, parity)) return true;
-        if (*abort_flag) return false;
-        if (gtimer() - t0 > limit) {
-            *abort_flag = 1;
-            atomicCAS(&g_tc_status, 0, 1);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t a)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows
-// of 128 bytes, 8-row core groups 1024 bytes apart (SBO), version 1.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr)
-{
-    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1 << 16;           // LBO (ignored for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32; // SBO
-    d |= (uint64_t)1 << 46;           // descriptor version
-    d |= (uint64_t)2 << 61;           // SWIZZLE_128B
-    return d;
-}
-
-// Instruction descriptor: FP32 accumulator, K-major A and B, M = 128, N = 256;
-// operand format BF16 (kind::f16, code 1) or E4M3 (kind::f8f6f4, code 0).
-template <int ENC>
-__device__ __forceinline__ uint32_t idesc()
-{
-    const uint32_t fmt = ENC == HDC_ENC_BF16 ? 1u : 0u;
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-}
-
-template <int ENC>
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t accum)
-{
-    if (ENC == HDC_ENC_BF16)
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-            "l"(a), "l"(b), "r"(id), "r"(accum));
-    else
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-            "l"(a), "l"(b), "r"(id), "r"(accum));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// 32 consecutive FP32 columns of this thread's TMEM lane; the wait names the
-// registers so no use of them is scheduled before the load has landed.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
-                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
-                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
-                 :
-                 : "memory");
-}
-
-// sign(0) = +1: -0.0 and +0.0 both give bit 0.
-__device__ __forceinline__ uint32_t pack_signs(const uint32_t (&r)[32])
-{
-    uint32_t w = 0;
-#pragma unroll
-    for (int j = 0; j < 32; j++) w |= (__uint_as_float(r[j]) < 0.f ? 1u : 0u) << j;
-    return w;
-}
-
-// ------------------------------------------------------------------ kernel
-template <int ENC, int CMAX, bool CLASSIFY>
-__global__ void __launch_bounds__(NUM_THREADS, 1)
-    tc_encode_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p)
-{
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *sA = smem;
-    uint8_t *sB = smem + STAGES * A_BYTES;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + NUM_BARS);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    auto full = [&](int s) { return su32(bars + s); };
-    auto empty = [&](int s) { return su32(bars + STAGES + s); };
-    auto tfull = [&](int a) { return su32(bars + 2 * STAGES + a); };
-    auto tempty = [&](int a) { return su32(bars + 2 * STAGES + 2 + a); };
-    const uint32_t done_bar = su32(bars + 2 * STAGES + 4);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t num_m_tiles = (p.N + BM - 1) / BM;
-    const int num_n_tiles = (p.Dk + BN - 1) / BN;
-    constexpr int KELEMS = ENC == HDC_ENC_BF16 ? BKB / 2 : BKB;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; s++) {
-            mbar_init(full(s), 1);
-            mbar_init(empty(s), 1);
-        }
-        for (int a = 0; a < 2; a++) {
-            mbar_init(tfull(a), 1);
-            mbar_init(tempty(a), BM);
-        }
-        mbar_init(done_bar, 1);
-        *abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-
-    if (warp == 4) {
-        if (lane == 0) {  // ---------------------------------- TMA producer
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-            int stage = 0;
-            uint32_t phase = 0;
-            bool issued[STAGES];
-            uint32_t ipar[STAGES];
-            for (int s = 0; s < STAGES; s++) { issued[s] = false; ipar[s] = 0; }
-            bool ab = false;
-            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
-                for (int nt = 0; nt < num_n_tiles && !ab; nt++)
-                    for (int kb = 0; kb < p.num_kb; kb++) {
-                        if (!mbar_wait(empty(stage), phase ^ 1, abort_flag)) { ab = true; break; }
-                        mbar_expect_tx(full(stage), STAGE_BYTES);
-                        tma_load_2d(su32(sA + stage * A_BYTES), &tmA, kb * KELEMS, (int)(mt * BM), full(stage));
-                        tma_load_2d(su32(sB + stage * B_BYTES), &tmB, kb * KELEMS, nt * BN, full(stage));
-                        issued[stage] = true;
-                        ipar[stage] = phase;
-                        if (++stage == STAGES) { stage = 0; phase ^= 1; }
-                    }
-            if (ab)  // let our own copies land before the CTA exits
-                for (int s = 0; s < STAGES; s++)
-                    if (issued[s]) {
-                        const unsigned long long t0 = gtimer();
-                        while (!mbar_try(full(s), ipar[s]) && gtimer() - t0 < 100000000ull) {}
-                    }
-        }
-    } else if (warp == 5) {
-        if (lane == 0) {  // ---------------------------------- MMA issuer
-            const uint32_t id = idesc<ENC>();
-            int stage = 0, acc = 0;
-            uint32_t phase = 0, aphase = 0;
-            bool ab = false;
-            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
-                for (int nt = 0; nt < num_n_tiles && !ab; nt++) {
-                    if (!mbar_wait(tempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
-                    tc_fence_after();
-                    const uint32_t d = tmem + (uint32_t)(acc * BN);
-                    for (int kb = 0; kb < p.num_kb; kb++) {
-                        if (!mbar_wait(full(stage), phase, abort_flag)) { ab = true; break; }
-                        tc_fence_after();
-                        const uint32_t a0 = su32(sA + stage * A_BYTES), b0 = su32(sB + stage * B_BYTES);
-#pragma unroll
-                        for (int k = 0; k < BKB / 32; k++)
-                            mma<ENC>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), id, (kb | k) != 0);
-                        mma_commit(empty(stage));
-                        if (++stage == STAGES) { stage = 0; phase ^= 1; }
-                    }
-                    if (ab) break;
-                    mma_commit(tfull(acc));
-                    if (++acc == 2) { acc = 0; aphase ^= 1; }
-                }
-            // all MMAs of this thread complete before TMEM is released
-            mma_commit(done_bar);
-            const unsigned long long t0 = gtimer();
-            while (!mbar_try(done_bar, 0) && gtimer() - t0 < 100000000ull) {}
-        }
-    } else {  // --------------------------------------------- epilogue warps 0-3
-        const int q = warp;  // TMEM lane quarter of this warp
-        int acc = 0;
-        uint32_t aphase = 0;
-        bool ab = false;
-        for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
-            const int64_t row = mt * BM + q * 32 + lane;
-            const bool valid = row < p.N;
-            int dist[CLASSIFY ? CMAX : 1];
-#pragma unroll
-            for (int c = 0; c < (CLASSIFY ? CMAX : 1); c++) dist[c] = 0;
-            for (int nt = 0; nt < num_n_tiles; nt++) {
-                // warp-uniform outcome: the TMEM loads below are .sync.aligned
-                const bool ok = mbar_wait(tfull(acc), aphase, abort_flag);
-                if (!__all_sync(0xffffffffu, ok)) { ab = true; break; }
-                tc_fence_after();
-                uint32_t words[BN / 32];
-#pragma unroll
-                for (int j = 0; j < BN / 32; j++) {
-                    uint32_t r[32];
-                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + j * 32), r);
-                    if (p.scores && valid) {
-                        const float rs = p.sx ? p.sx[row] : 1.f;
-#pragma unroll
-                        for (int i = 0; i < 32; i++) {
-                            const int col = nt * BN + j * 32 + i;
-                            if (col < p.Dk)
-                                p.scores[row * p.Dk + col] = __uint_as_float(r[i]) * rs * (p.sb ? p.sb[col] : 1.f);
-                        }
-                    }
-                    words[j] = pack_signs(r);
-                }
-                tc_fence_before();
-                mbar_arrive(tempty(acc));
-                if (++acc == 2) { acc = 0; aphase ^= 1; }
-                const int gw0 = nt * (BN / 32);
-                if (CLASSIFY) {
-#pragma unroll
-                    for (int j = 0; j < BN / 32; j++) {
-                        const int gw = gw0 + j;
-                        if (gw >= p.W) break;
-                        const uint32_t qw = words[j];
-                        if (p.nb == 1) {
-#pragma unroll
-                            for (int c = 0; c < CMAX; c++)
-                                if (c < p.C) dist[c] += __popc(qw ^ __ldg(p.planes + (int64_t)c * p.W + gw));
-                        } else {
-#pragma unroll
-                            for (int c = 0; c < CMAX; c++)
-                                if (c < p.C) {
-                                    int part = 0;
-                                    for (int pl = 0; pl < p.nb; pl++) {
-                                        const int cnt =
-                                            __popc(qw & __ldg(p.planes + ((int64_t)pl * p.C + c) * p.W + gw));
-                                        part += pl == p.nb - 1 ? -(cnt << pl) : (cnt << pl);
-                                    }
-                                    dist[c] += part;
-                                }
-                        }
-                    }
-                } else if (valid) {
-                    uint32_t *h = p.H + row * (int64_t)p.W + gw0;
-                    if (gw0 + 4 <= p.W) *reinterpret_cast<uint4 *>(h) = make_uint4(words[0], words[1], words[2], words[3]);
-                    if (gw0 + 8 <= p.W) *reinterpret_cast<uint4 *>(h + 4) = make_uint4(words[4], words[5], words[6], words[7]);
-                }
-            }
-            if (CLASSIFY && valid && !ab) {
-                int best = 0;
-                if (p.nb == 1) {
-                    int bv = dist[0];
-#pragma unroll
-                    for (int c = 0; c < CMAX; c++)
-                        if (c < p.C) {
-                            if (p.dists) p.dists[row * p.C + c] = dist[c];
-                            if (dist[c] < bv) { bv = dist[c]; best = c; }
-                        }
-                } else {
-                    double bs = 0.0;
-#pragma unroll
-                    for (int c = 0; c < CMAX; c++)
-                        if (c < p.C) {
-                            const double nrm = p.cnorm[c];
-                            const double s = nrm == 0.0 ? 0.0 : (double)(p.csum[c] - 2 * dist[c]) / nrm;
-                            if (p.sims) p.sims[row * p.C + c] = s;
-                            if (c == 0 || s > bs) { bs = s; best = c; }
-                        }
-                }
-                p.labels[row] = best;
-            }
-        }
-    }
-
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
-    }
-}
-
-// --------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -430,7 +24,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// 2-D map over a row-major [rows x ld] operand, box = 128 bytes of K x box_rows.
+// 2-D map over a row-major [rows x ld] operand; box = 128 bytes of K by
+// box_rows rows, 128-byte swizzle, zero fill outside the tensor.
 bool make_map(CUtensorMap *m, const void *base, int enc, int ld, int64_t rows, int box_rows)
 {
     auto fn = encode_fn();
@@ -438,7 +33,7 @@ bool make_map(CUtensorMap *m, const void *base, int enc, int ld, int64_t rows, i
     const int es = enc == HDC_ENC_BF16 ? 2 : 1;
     cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)ld * es};
-    cuuint32_t box[2] = {(cuuint32_t)(BKB / es), (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)(tc::BKB / es), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, enc == HDC_ENC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
                     const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -454,39 +49,16 @@ int sm_count()
     return n;
 }
 
-template <int ENC, int CMAX, bool CLASSIFY>
-cudaError_t launch_t(const CUtensorMap &ma, const CUtensorMap &mb, const Params &p, int64_t m_tiles, cudaStream_t st)
-{
-    auto k = tc_encode_kernel<ENC, CMAX, CLASSIFY>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    const int sms = sm_count();
-    if (sms <= 0) return cudaErrorNoDevice;
-    const int64_t grid = m_tiles < sms ? m_tiles : sms;
-    k<<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, st>>>(ma, mb, p);
-    return cudaGetLastError();
-}
-
-template <int ENC>
-cudaError_t launch_enc(const CUtensorMap &ma, const CUtensorMap &mb, const Params &p, int64_t m_tiles, bool classify,
-                       cudaStream_t st)
-{
-    if (!classify) return launch_t<ENC, 1, false>(ma, mb, p, m_tiles, st);
-    if (p.C <= 16) return launch_t<ENC, 16, true>(ma, mb, p, m_tiles, st);
-    if (p.C <= 32) return launch_t<ENC, 32, true>(ma, mb, p, m_tiles, st);
-    if (p.C <= 64) return launch_t<ENC, 64, true>(ma, mb, p, m_tiles, st);
-    return launch_t<ENC, 128, true>(ma, mb, p, m_tiles, st);
-}
-
 }  // namespace
 
 bool tc_supported(const TcArgs &a)
 {
     if (a.enc != HDC_ENC_BF16 && a.enc != HDC_ENC_FP8_E4M3) return false;
-    const int kel = a.enc == HDC_ENC_BF16 ? BKB / 2 : BKB;
+    const int kel = a.enc == HDC_ENC_BF16 ? tc::BKB / 2 : tc::BKB;
     if (a.ldx != a.ldb || a.ldx % kel != 0 || a.ldx <= 0) return false;
-    if (a.N <= 0 || a.N > 0x7fffffffLL - BM || a.Dk <= 0 || a.W != words_for(a.Dk)) return false;
-    if (a.planes && (a.C <= 0 || a.C > 128 || (a.nb != 1 && a.nb != 4 && a.nb != 8))) return false;
+    if (a.N <= 0 || a.N > 0x7fffffffLL - tc::BM || a.Dk <= 0 || a.W != words_for(a.Dk)) return false;
+    // fused classify: binary class hypervectors, up to 128 classes
+    if (a.planes && (a.C <= 0 || a.C > 128 || a.nb != 1)) return false;
     if (!a.planes && !a.H) return false;
     if (!encode_fn()) return false;
     return true;
@@ -495,12 +67,12 @@ bool tc_supported(const TcArgs &a)
 cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st)
 {
     CUtensorMap ma, mb;
-    if (!make_map(&ma, a.Xq, a.enc, a.ldx, a.N, BM) || !make_map(&mb, a.Bq, a.enc, a.ldb, a.Dk, BN))
+    if (!make_map(&ma, a.Xq, a.enc, a.ldx, a.N, tc::BM) || !make_map(&mb, a.Bq, a.enc, a.ldb, a.Dk, tc::BN))
         return cudaErrorInvalidValue;
-    Params p;
+    tc::Params p;
     p.N = a.N;
     p.Dk = a.Dk;
-    p.num_kb = a.ldx / (a.enc == HDC_ENC_BF16 ? BKB / 2 : BKB);
+    p.num_kb = a.ldx / (a.enc == HDC_ENC_BF16 ? tc::BKB / 2 : tc::BKB);
     p.W = a.W;
     p.sx = a.sx;
     p.sb = a.sb;
@@ -508,30 +80,23 @@ cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st)
     p.scores = a.scores;
     p.planes = a.planes;
     p.C = a.C;
-    p.nb = a.nb;
-    p.csum = a.csum;
-    p.cnorm = a.cnorm;
     p.labels = a.labels;
     p.dists = a.dists;
-    p.sims = a.sims;
-    const int64_t m_tiles = (a.N + BM - 1) / BM;
+    const int64_t m_tiles = (a.N + tc::BM - 1) / tc::BM;
+    const int sms = sm_count();
+    if (sms <= 0) return cudaErrorNoDevice;
+    const unsigned grid = (unsigned)(m_tiles < sms ? m_tiles : sms);
     const bool classify = a.planes != nullptr;
-    if (a.enc == HDC_ENC_BF16) return launch_enc<HDC_ENC_BF16>(ma, mb, p, m_tiles, classify, st);
-    return launch_enc<HDC_ENC_FP8_E4M3>(ma, mb, p, m_tiles, classify, st);
+    if (a.enc == HDC_ENC_BF16) return tc::launch_bf16(ma, mb, p, grid, classify, st);
+    return tc::launch_fp8(ma, mb, p, grid, classify, st);
 }
 
 cudaError_t tc_read_status(cudaStream_t st, int *status)
 {
-    int h = 0;
-    cudaError_t e = cudaMemcpyFromSymbolAsync(&h, g_tc_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return e;
-    *status = h;
-    if (h != 0) {
-        const int zero = 0;
-        e = cudaMemcpyToSymbolAsync(g_tc_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    }
+    int a = 0, b = 0;
+    cudaError_t e = tc::status_bf16(st, &a);
+    if (e == cudaSuccess) e = tc::status_fp8(st, &b);
+    *status = a ? a : b;
     return e;
 }
 

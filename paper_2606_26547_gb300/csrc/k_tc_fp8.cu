@@ -1,0 +1,16 @@
+// Tensor-core encoder instances for FP8 E4M3 operands (tcgen05.mma kind::f8f6f4).
+#include "tc_kernel.cuh"
+
+namespace hdc {
+namespace tc {
+
+cudaError_t launch_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const Params &p, unsigned grid, bool classify,
+                       cudaStream_t st)
+{
+    return launch_enc<HDC_ENC_FP8_E4M3>(ma, mb, p, grid, classify, st);
+}
+
+cudaError_t status_fp8(cudaStream_t st, int *status) { return read_status(st, status); }
+
+}  // namespace tc
+}  // namespace hdc
