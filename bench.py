@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Throughput of the HDC classification hot path on GB300.
+
+Workload: precision_F784_D10000_C10 (F = 784 FP32 features, 10-class
+Gaussian mixture, base hypermatrix 784 x 10,000 N(0,1), 60,000 training
+samples, bundling + 20 retraining epochs).  One step classifies one batch of
+queries drawn from the same mixture (default 1,048,576 queries = 3.3 GB of
+FP32 features, larger than L2) with the approximate configuration: FP8 E4M3
+encoding with per-row power-of-two scales on the tensor cores, dimension
+perforation of stride 2 (D' = 5,000), binary class hypervectors, Hamming
+arg-min -- quantise kernel + fused tcgen05 kernel per step.
+
+Also measured on the same GPU: the plain exact form (FP32 FFMA encode at the
+full D, packed Hamming), the accuracy of both on the 10,000-query set, an
+end-to-end figure through the same C-ABI call with pinned host buffers, and
+the CPU oracle on a bounded sample.  `--impl reference` times the CPU oracle
+alone on the host cores.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "precision_F784_D10000_C10"
+METRIC = "queries/sec at D=10,000 (approx vs exact, same GB300, <=1pt acc loss)"
+UNIT = "queries/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=1 << 20, help="queries per step (per GPU)")
+    ap.add_argument("--enc", default="fp8", choices=["bf16", "fp8"])
+    ap.add_argument("--stride", type=int, default=2)
+    ap.add_argument("--exact-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the oracle sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while running (read-only query)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+            except Exception:
+                continue
+        os.unlink(self.path)
+        inside = [r for r in rows if self.t0 and self.t1 and self.t0 - 1 <= r[0] <= self.t1 + 1] or rows
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in inside for n, v in zip(names, r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside)}
+
+
+# --------------------------------------------------------------- helpers
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def oracle_sample_qps(data, acc, enc_code, stride, target_s, threads):
+    """Time the CPU oracle (as it stands) on a bounded sample of queries."""
+    import numpy as np
+    import oracle
+    Xq, Bt = data["Xq"], data["Bt"]
+    n = threads
+    while True:  # grow the sample until one run takes about a third of the target
+        t = time.perf_counter()
+        labels, _ = oracle.classify(Xq[:n], Bt, acc, enc_code, 0.0, 1.0, stride, 1, threads=threads)
+        dt = time.perf_counter() - t
+        if dt >= target_s / 3 or n >= Xq.shape[0]:
+            return n / dt, n, dt, labels
+        n = min(Xq.shape[0], max(2 * n, int(n * target_s / 3 / max(dt, 1e-3))) // threads * threads)
+
+
+def train_model(hdc, torch, data, dev, epochs):
+    Bt = torch.from_numpy(data["Bt"]).to(dev)
+    base = hdc.Model(Bt, hdc.ApproxConfig(enc="fp32"))
+    Xtr = torch.from_numpy(data["Xtr"]).to(dev)
+    ytr = torch.from_numpy(data["ytr"]).to(dev)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    H = hdc.encode(Xtr, base)
+    acc, cls, ups = hdc.train(H, ytr, Bt.shape[0], int(data["ytr"].max()) + 1, epochs)
+    torch.cuda.synchronize()
+    return Bt, acc, ups, time.perf_counter() - t
+
+
+def timed_steps(torch, fn, steps, stream):
+    """Device time of `steps` calls of fn(i) between CUDA events."""
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for i in range(steps):
+        fn(i)
+    stop.record(stream)
+    stop.synchronize()
+    return start.elapsed_time(stop) / 1e3
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2606_26547_gb300 import build, hdc, synth
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    hdc.load()
+    w = synth.WORKLOADS[WORKLOAD]
+    data = synth.make(WORKLOAD)
+    Bt, acc, ups, train_s = train_model(hdc, torch, data, dev, w.epochs)
+
+    approx_cfg = hdc.ApproxConfig(enc=a.enc, perf_stride=a.stride)
+    exact_cfg = hdc.ApproxConfig(enc="fp32")
+    m_apx = hdc.Model(Bt, approx_cfg, acc=acc)
+    m_ex = hdc.Model(Bt, exact_cfg, acc=acc)
+
+    # accuracy on the 10,000-query set
+    Xq = torch.from_numpy(data["Xq"]).to(dev)
+    yq = data["yq"]
+    lab_ex = hdc.classify(Xq, m_ex).cpu().numpy()
+    lab_apx = hdc.classify(Xq, m_apx).cpu().numpy()
+    acc_ex = float((lab_ex == yq).mean())
+    acc_apx = float((lab_apx == yq).mean())
+
+    # throughput batch (this rank's shard of the job: weak scaling)
+    B = a.batch
+    X, _ = synth.device_gauss_queries(B, w, seed=777 + rank, device=dev)
+    labels = torch.empty(B, dtype=torch.int32, device=dev)
+    ws = m_apx.workspace(B)
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+
+    def step_apx(i):
+        hdc.classify(X, m_apx, ws=ws, labels=labels)
+
+    def step_apx_prof(i):
+        hdc.profile_events(*evs[i])
+        hdc.classify(X, m_apx, ws=ws, labels=labels)
+
+    for i in range(a.warmup):
+        step_apx(i)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.6)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.mark("t0")
+    el = timed_steps(torch, step_apx_prof, a.steps, stream)
+    clk.mark("t1")
+    hdc.profile_events(None, None)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    assert hdc.stream_status() == 0
+    kern_s = [s.elapsed_time(e) / 1e3 for s, e in evs]
+    if world > 1:
+        t = torch.tensor([el], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    value = world * B * a.steps / el
+
+    # exact form on the same GPU
+    ws_ex = m_ex.workspace(B)
+    hdc.classify(X, m_ex, ws=ws_ex, labels=labels)
+    torch.cuda.synchronize()
+    el_ex = timed_steps(torch, lambda i: hdc.classify(X, m_ex, ws=ws_ex, labels=labels), a.exact_steps, stream)
+    exact_qps = B * a.exact_steps / el_ex
+    del ws_ex
+
+    # end to end through the same call with pinned host buffers
+    Xh = X.cpu().pin_memory()
+    Lh = torch.empty(B, dtype=torch.int32).pin_memory()
+    Xd = torch.empty_like(X)
+    e2e_steps = max(3, min(a.steps, 20))
+
+    def step_e2e(i):
+        Xd.copy_(Xh, non_blocking=True)
+        hdc.classify(Xd, m_apx, ws=ws, labels=labels)
+        Lh.copy_(labels, non_blocking=True)
+
+    step_e2e(0)
+    torch.cuda.synchronize()
+    el_e2e = timed_steps(torch, step_e2e, e2e_steps, stream)
+    e2e_qps = world * B * e2e_steps / el_e2e
+
+    # roofline of the dominant kernel (fused tcgen05 encode + Hamming + arg-min)
+    F, Dk = w.F, m_apx.Dk
+    avg_k = sum(kern_s) / len(kern_s)
+    flops = 2.0 * B * F * Dk
+    pk = peaks()
+    ratio = 2.0 if a.enc == "fp8" else 1.0
+    if "bf16_tflops_sustained" in pk:
+        peak = pk["bf16_tflops_sustained"] * ratio
+        peak_src = "measured bf16 sustained x %.0f (nominal fp8/bf16 ratio)" % ratio if ratio != 1 else \
+            "measured bf16 sustained"
+    else:
+        peak = 1700.0 * ratio
+        peak_src = "fallback"
+    achieved = flops / avg_k / 1e12
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": el / a.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "%s operands, fp32 accumulate, binary hypervectors" % ("e4m3" if a.enc == "fp8" else "bf16"),
+        "data": "synthetic (seeded Gaussian mixture shaped like the workload; no dataset)",
+        "config": {"workload": WORKLOAD, "F": F, "D": w.D, "C": w.C, "enc": a.enc,
+                   "perforation": [0.0, 1.0, a.stride], "Dk": Dk, "class_bits": 1, "queries_per_step": B,
+                   "train": "bundling + %d retraining epochs on %d samples (FP32 encode)" % (w.epochs, w.n_train),
+                   "l2": "inputs larger than L2 (%.1f GB of FP32 queries per step)" % (B * F * 4 / 1e9),
+                   "parallelism": "dp%d (queries sharded, no collective)" % world},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "tc_encode_kernel (classify)",
+                     "peak_source": peak_src + " of measured", "kernel_ms": avg_k * 1e3,
+                     "algorithmic_flops_per_launch": flops},
+        "e2e": {"value": e2e_qps, "unit": UNIT, "h2d_bytes_per_step": B * F * 4, "d2h_bytes_per_step": B * 4},
+        "gpu_launches": 2 * a.steps,
+        "clocks": clocks,
+        "exact": {"value": exact_qps, "unit": UNIT, "enc": "fp32 (FFMA)", "Dk": w.D,
+                  "ms_per_step": el_ex / a.exact_steps * 1e3},
+        "speedup_vs_exact": value / exact_qps / world,
+        "accuracy": {"exact": acc_ex, "approx": acc_apx, "loss_pts": 100.0 * (acc_ex - acc_apx),
+                     "label_agreement": float((lab_ex == lab_apx).mean()), "queries": int(yq.size)},
+        "train_s": train_s, "train_updates": ups,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        import oracle
+        threads = os.cpu_count() or 1
+        acc_np = acc.cpu().numpy().astype(np.int64)
+        qps, n, dt, olab = oracle_sample_qps(data, acc_np, {"bf16": 1, "fp8": 2}[a.enc], a.stride, a.cpu_seconds,
+                                             threads)
+        out["cpu_baseline"] = {"value": qps, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": "%d of the 10,000 queries, same config, %.1f s" % (n, dt),
+                               "label_agreement_with_gpu": float((olab == lab_apx[:n]).mean())}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------- reference arm
+
+def run_reference(a):
+    """The CPU oracle, as it stands, on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2606_26547_gb300 import synth
+    oracle.build()
+    w = synth.WORKLOADS[WORKLOAD]
+    threads = os.cpu_count() or 1
+    n_train = 32 * threads
+    data = synth.make(WORKLOAD, n_train=n_train)
+    dims = oracle.kept_dims(w.D)
+    bits, _, _, _ = oracle.encode_bits(data["Xtr"], data["Bt"], oracle.ENC_FP32, dims, threads=threads)
+    acc, _ = oracle.train(bits, data["ytr"], w.C, 2)
+    enc = {"bf16": 1, "fp8": 2}[a.enc]
+    Xq = data["Xq"]
+    # size each step so warm-up + timed steps take about two minutes
+    t = time.perf_counter()
+    oracle.classify(Xq[:threads], data["Bt"], acc, enc, 0.0, 1.0, a.stride, 1, threads=threads)
+    probe = time.perf_counter() - t
+    per_step = threads * max(1, int(120.0 / max(1, a.steps + a.warmup) / max(probe, 1e-3)))
+    per_step = min(per_step, Xq.shape[0] // 2)
+    for i in range(a.warmup):
+        oracle.classify(Xq[:per_step], data["Bt"], acc, enc, 0.0, 1.0, a.stride, 1, threads=threads)
+    t = time.perf_counter()
+    for i in range(a.steps):
+        lo = (i * per_step) % (Xq.shape[0] - per_step)
+        oracle.classify(Xq[lo:lo + per_step], data["Bt"], acc, enc, 0.0, 1.0, a.stride, 1, threads=threads)
+    dt = time.perf_counter() - t
+    qps = per_step * a.steps / dt
+    out = {"impl": "reference", "metric": METRIC, "value": qps, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64 oracle of the %s path" % a.enc, "data": "synthetic",
+           "config": {"workload": WORKLOAD, "enc": a.enc, "perforation": [0.0, 1.0, a.stride],
+                      "queries_per_step": per_step,
+                      "train": "bundling + 2 retraining epochs on %d samples (oracle)" % n_train},
+           "cpu_baseline": {"value": qps, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": "%d queries per step x %d steps" % (per_step, a.steps)},
+           "e2e": {"value": qps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

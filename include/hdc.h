@@ -198,6 +198,14 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m,
  * stream itself reports an error).                                        */
 hdc_status hdc_stream_status(hdc_stream_t stream);
 
+/* Tracing hook (not part of the method): with start and stop set to
+ * cudaEvent_t handles, every later hdc_encode / hdc_classify call made by
+ * the calling host thread records `start` on its stream just before its
+ * encoding kernel and `stop` just after it, so that kernel can be timed on
+ * its own with cudaEventElapsedTime.  The handles stay owned by the caller;
+ * hdc_profile_events(NULL, NULL) turns the hook off.                        */
+void hdc_profile_events(void *start, void *stop);
+
 /* Static English text for a status code.                                   */
 const char *hdc_status_string(hdc_status s);
 

@@ -238,12 +238,19 @@ def cosine_scores(q: np.ndarray, chat: np.ndarray) -> np.ndarray:
 # ---------------------------------------------------------------- pipelines
 
 def encode_bits(X: np.ndarray, Bt: np.ndarray, enc: int, dims: np.ndarray,
-                integer: bool = False):
+                integer: bool = False, threads: int = 1):
     """Quantise -> encode over the kept dims -> binarise.
 
     Returns (bits N x Dk, scores in units of the row scales, scale_x, scale_b).
     ``integer=True`` encodes integer-valued inputs exactly in int64.
+    ``threads`` > 1 splits the rows over a thread pool (same result).
     """
+    if threads > 1 and X.shape[0] > 1:
+        chunks = np.array_split(np.arange(X.shape[0]), threads)
+        with ThreadPoolExecutor(threads) as ex:
+            parts = list(ex.map(lambda idx: encode_bits(X[idx], Bt, enc, dims, integer, 1), chunks))
+        return (np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]),
+                np.concatenate([p[2] for p in parts]), parts[0][3])
     if integer:
         s = encode_i64(np.rint(X).astype(np.int64), np.rint(Bt).astype(np.int64), dims)
         return binarise(s), s, np.ones(X.shape[0]), np.ones(Bt.shape[0])

@@ -104,6 +104,27 @@ hdc_status prepare_queries(const float *X, int64_t N, const hdc_model *m, char *
 // Tensor-core encoder for BF16/FP8 unless the configuration forces FFMA.
 bool use_tc(const hdc_model *m) { return m->enc != HDC_ENC_FP32 && !(m->flags & HDC_FLAG_SIMT_ENCODE); }
 
+// Tracing hook (hdc_profile_events): events recorded around the encoding
+// kernel of each call made by this host thread.
+thread_local cudaEvent_t t_prof_start = nullptr, t_prof_stop = nullptr;
+
+cudaError_t timed_tc(const TcArgs &a, cudaStream_t st)
+{
+    if (t_prof_start) cudaEventRecord(t_prof_start, st);
+    cudaError_t e = launch_tc_encode(a, st);
+    if (t_prof_stop) cudaEventRecord(t_prof_stop, st);
+    return e;
+}
+
+cudaError_t timed_simt(const void *X, int64_t ldx, int64_t N, int F, const void *Bq, int ldb, int Dk, int enc,
+                       const float *sx, const float *sb, uint32_t *H, int W, float *scores, cudaStream_t st)
+{
+    if (t_prof_start) cudaEventRecord(t_prof_start, st);
+    cudaError_t e = launch_encode_simt(X, ldx, N, F, Bq, ldb, Dk, enc, sx, sb, H, W, scores, st);
+    if (t_prof_stop) cudaEventRecord(t_prof_stop, st);
+    return e;
+}
+
 }  // namespace
 }  // namespace hdc
 
@@ -211,9 +232,9 @@ hdc_status hdc_encode(const float *X, int64_t N, const hdc_model *m, uint32_t *H
         TcArgs a = {};
         a.Xq = Xop; a.N = N; a.ldx = (int)ldx; a.Bq = m->Bq; a.ldb = m->ldb; a.Dk = m->Dk; a.enc = m->enc;
         a.sx = sx; a.sb = m->b_scale; a.H = H; a.scores = scores; a.W = m->W;
-        if (tc_supported(a)) return cu(launch_tc_encode(a, st));
+        if (tc_supported(a)) return cu(timed_tc(a, st));
     }
-    return cu(launch_encode_simt(Xop, ldx, N, m->F, m->Bq, m->ldb, m->Dk, m->enc, sx, m->b_scale, H, m->W, scores,
+    return cu(timed_simt(Xop, ldx, N, m->F, m->Bq, m->ldb, m->Dk, m->enc, sx, m->b_scale, H, m->W, scores,
                                  st));
 }
 
@@ -293,17 +314,17 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *
         a.planes = m->cls; a.C = m->C; a.nb = nb; a.csum = m->cls_sum; a.cnorm = m->cls_norm;
         a.labels = labels; a.dists = dists; a.sims = scores;
         // binary classes: fully fused; otherwise tensor-core encode + K4
-        if (tc_supported(a)) return cu(launch_tc_encode(a, st));
+        if (tc_supported(a)) return cu(timed_tc(a, st));
         TcArgs e = a;
         e.planes = nullptr; e.labels = nullptr; e.dists = nullptr; e.sims = nullptr; e.H = Hb;
         if (tc_supported(e)) {
-            s = cu(launch_tc_encode(e, st));
+            s = cu(timed_tc(e, st));
             if (s != HDC_OK) return s;
             encoded = true;
         }
     }
     if (!encoded) {
-        s = cu(launch_encode_simt(Xop, ldx, N, m->F, m->Bq, m->ldb, m->Dk, m->enc, sx, m->b_scale, Hb, m->W,
+        s = cu(timed_simt(Xop, ldx, N, m->F, m->Bq, m->ldb, m->Dk, m->enc, sx, m->b_scale, Hb, m->W,
                                   nullptr, st));
         if (s != HDC_OK) return s;
     }
@@ -320,6 +341,12 @@ hdc_status hdc_stream_status(hdc_stream_t stream)
     if (status == 1) return HDC_ERR_TIMEOUT;
     if (status != 0) return HDC_ERR_DEVICE;
     return HDC_OK;
+}
+
+void hdc_profile_events(void *start, void *stop)
+{
+    t_prof_start = (cudaEvent_t)start;
+    t_prof_stop = (cudaEvent_t)stop;
 }
 
 const char *hdc_status_string(hdc_status s)

@@ -57,6 +57,7 @@ _SIGS = {
     "hdc_train_epoch": (_I32, [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
     "hdc_classify": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _SZ, _P]),
     "hdc_stream_status": (_I32, [_P]),
+    "hdc_profile_events": (None, [_P, _P]),
     "hdc_status_string": (ctypes.c_char_p, [_I32]),
 }
 EXPORTED = tuple(_SIGS)
@@ -247,6 +248,13 @@ def classify(X: torch.Tensor, model: Model, sims: bool = False, ws: torch.Tensor
     if sims:
         return labels, (dd if dd is not None else sc)
     return labels
+
+
+def profile_events(start=None, stop=None) -> None:
+    """Record torch.cuda.Event pair around the encoding kernel of later calls
+    from this thread (None, None turns it off)."""
+    load().hdc_profile_events(ctypes.c_void_p(start.cuda_event) if start is not None else None,
+                              ctypes.c_void_p(stop.cuda_event) if stop is not None else None)
 
 
 def stream_status(stream=None) -> int:
