@@ -198,6 +198,10 @@ def run_ours(a):
     ws = m_apx.workspace(B)
     stream = torch.cuda.current_stream()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    for s, e in evs:  # torch creates the event handles on first record
+        s.record(stream)
+        e.record(stream)
+    torch.cuda.synchronize()
 
     def step_apx(i):
         hdc.classify(X, m_apx, ws=ws, labels=labels)
