@@ -230,7 +230,7 @@ hdc_status hdc_encode(const float *X, int64_t N, const hdc_model *m, uint32_t *H
     if (s != HDC_OK) return s;
     if (use_tc(m)) {
         TcArgs a = {};
-        a.Xq = Xop; a.N = N; a.ldx = (int)ldx; a.Bq = m->Bq; a.ldb = m->ldb; a.Dk = m->Dk; a.enc = m->enc;
+        a.Xq = Xop; a.N = N; a.F = m->F; a.ldx = (int)ldx; a.Bq = m->Bq; a.ldb = m->ldb; a.Dk = m->Dk; a.enc = m->enc;
         a.sx = sx; a.sb = m->b_scale; a.H = H; a.scores = scores; a.W = m->W;
         if (tc_supported(a)) return cu(timed_tc(a, st));
     }
@@ -309,7 +309,7 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *
     bool encoded = false;
     if (use_tc(m)) {
         TcArgs a = {};
-        a.Xq = Xop; a.N = N; a.ldx = (int)ldx; a.Bq = m->Bq; a.ldb = m->ldb; a.Dk = m->Dk; a.enc = m->enc;
+        a.Xq = Xop; a.N = N; a.F = m->F; a.ldx = (int)ldx; a.Bq = m->Bq; a.ldb = m->ldb; a.Dk = m->Dk; a.enc = m->enc;
         a.sx = sx; a.sb = m->b_scale; a.W = m->W;
         a.planes = m->cls; a.C = m->C; a.nb = nb; a.csum = m->cls_sum; a.cnorm = m->cls_norm;
         a.labels = labels; a.dists = dists; a.sims = scores;

@@ -24,10 +24,11 @@ struct Perf {
 };
 bool perf_of(int64_t D, const hdc_approx_config *cfg, Perf *p);
 
-// Row padding of the quantised operands, in elements: one 128-byte swizzle
-// row of the tensor-core tiles (64 BF16 or 128 FP8), 32 floats for FP32.
+// Row stride of the quantised operands, in elements: rows start on 16-byte
+// boundaries (the TMA stride rule; the tensor-core path zero-fills the K
+// tail past F itself), 32 floats for the FP32 copy of the base.
 inline int ld_for(int enc, int F) {
-    int q = enc == HDC_ENC_BF16 ? 64 : enc == HDC_ENC_FP8_E4M3 ? 128 : 32;
+    int q = enc == HDC_ENC_BF16 ? 8 : enc == HDC_ENC_FP8_E4M3 ? 16 : 32;
     return (F + q - 1) / q * q;
 }
 inline int esize_for(int enc) { return enc == HDC_ENC_BF16 ? 2 : enc == HDC_ENC_FP8_E4M3 ? 1 : 4; }
@@ -78,7 +79,8 @@ cudaError_t launch_binarise(const int32_t *acc, int C, int D, uint32_t *cls, int
 struct TcArgs {
     const void *Xq;   // N x ldx quantised queries (BF16 or FP8)
     int64_t N;
-    int ldx;          // elements per row (multiple of the K block)
+    int F;            // features (the contraction length)
+    int ldx;          // elements per row (16-byte multiple, >= F)
     const void *Bq;   // Dk x ldb quantised base rows
     int ldb;
     int Dk;

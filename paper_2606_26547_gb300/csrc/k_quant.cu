@@ -18,21 +18,69 @@
 namespace hdc {
 namespace {
 
-// Smallest k with amax <= 448 * 2^k (k = 0 for amax == 0).  Double
-// comparisons are exact: 448 * 2^k and the FP32 amax are both representable.
-__device__ int pow2_scale_exp(float amax)
+// Smallest k with amax <= 448 * 2^k (k = 0 for amax == 0), from the bits of
+// the FP32 amax = 2^e * (1 + frac/2^23): 448 = 2^8 * 1.75, so k = e - 8 when
+// 1 + frac/2^23 <= 1.75 and e - 7 otherwise.  Integer-only (no FP64).
+__device__ __forceinline__ int pow2_scale_exp(float amax)
 {
-    if (!(amax > 0.f)) return 0;
-    double a = (double)amax;
-    int k = ilogb(a) - 8;
-    while (a > ldexp(448.0, k)) k++;
-    while (a <= ldexp(448.0, k - 1)) k--;
-    return k;
+    const uint32_t b = __float_as_uint(amax) & 0x7fffffffu;
+    if (b == 0) return 0;
+    int e;
+    uint32_t frac;
+    if (b >= 0x00800000u) {
+        e = (int)(b >> 23) - 127;
+        frac = b & 0x7fffffu;
+    } else {  // subnormal: normalise the leading bit
+        const int p = 31 - __clz(b);
+        e = p - 149;
+        frac = (b << (23 - p)) & 0x7fffffu;
+    }
+    return e - 8 + (frac > 0x600000u ? 1 : 0);
 }
 
-__device__ __forceinline__ float ldg_or0(const float *p, int f, int F) { return f < F ? __ldg(p + f) : 0.f; }
+// x * 2^-k exactly (the result is at most 448 in magnitude, so scaling never
+// rounds a value that survives the E4M3 conversion).
+__device__ __forceinline__ float scale_pow2(float x, int k)
+{
+    if (k >= -126) return x * __int_as_float((127 - k) << 23);
+    return (x * __int_as_float((127 + 64) << 23)) * __int_as_float((127 - k - 64) << 23);
+}
 
-template <int ENC>
+__device__ __forceinline__ uint32_t to_e4m3x4(float a, float b, float c, float d)
+{
+    const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
+__device__ __forceinline__ uint2 to_bf16x4(float a, float b, float c, float d)
+{
+    __nv_bfloat162 x = __floats2bfloat162_rn(a, b), y = __floats2bfloat162_rn(c, d);
+    return make_uint2(*reinterpret_cast<uint32_t *>(&x), *reinterpret_cast<uint32_t *>(&y));
+}
+
+// Four consecutive elements [f, f+4) of a row (zero past F).
+template <bool VEC>
+__device__ __forceinline__ float4 load4(const float *row, int f, int F)
+{
+    if (VEC) {  // F % 4 == 0 and 16-byte aligned rows
+        if (f < F) return __ldg(reinterpret_cast<const float4 *>(row + f));
+        return make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float4 v;
+    v.x = f < F ? __ldg(row + f) : 0.f;
+    v.y = f + 1 < F ? __ldg(row + f + 1) : 0.f;
+    v.z = f + 2 < F ? __ldg(row + f + 2) : 0.f;
+    v.w = f + 3 < F ? __ldg(row + f + 3) : 0.f;
+    return v;
+}
+
+// One warp per row; each lane owns 4 consecutive elements of every 128.
+// Rows of up to 128*MAXIT elements stay in registers between the amax
+// reduction and the conversion.
+constexpr int MAXIT = 8;
+
+template <int ENC, bool VEC>
 __global__ void __launch_bounds__(256) quant_rows_kernel(const float *__restrict__ src, int64_t lds,
                                                          int64_t row_off, int64_t row_step, int64_t nrows,
                                                          int F, void *__restrict__ dst, int ldd,
@@ -41,50 +89,49 @@ __global__ void __launch_bounds__(256) quant_rows_kernel(const float *__restrict
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nit = (ldd + 127) / 128;
     for (int64_t r = warp; r < nrows; r += nwarps) {
         const float *row = src + (row_off + r * row_step) * lds;
-        float mul = 1.f;
+        float4 v[MAXIT];
+        const bool in_regs = nit <= MAXIT;
         int k = 0;
-        bool slow = false;
         if (ENC == HDC_ENC_FP8_E4M3) {
             float amax = 0.f;
-            for (int f = lane; f < F; f += 32) amax = fmaxf(amax, fabsf(__ldg(row + f)));
+            if (in_regs) {
+#pragma unroll
+                for (int it = 0; it < MAXIT; it++)
+                    if (it < nit) {
+                        v[it] = load4<VEC>(row, it * 128 + lane * 4, F);
+                        amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v[it].x), fabsf(v[it].y)),
+                                                 fmaxf(fabsf(v[it].z), fabsf(v[it].w))));
+                    }
+            } else {
+                for (int f = lane; f < F; f += 32) amax = fmaxf(amax, fabsf(__ldg(row + f)));
+            }
 #pragma unroll
             for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
             k = pow2_scale_exp(amax);
-            // 2^-k as an FP32 normal number when in range; else go through double
-            if (k >= -126 && k <= 126) mul = __int_as_float((127 - k) << 23);
-            else slow = true;
-            if (lane == 0) scale[r] = (float)ldexp(1.0, k);
+            if (lane == 0) scale[r] = k >= -126 ? __int_as_float((127 + k) << 23) : ldexpf(1.f, k);
         }
-        // each lane converts 4 consecutive elements per step
-        for (int f0 = lane * 4; f0 < ldd; f0 += 128) {
-            float v[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++) v[j] = ldg_or0(row, f0 + j, F);
+        auto emit = [&](int f0, float4 x) {
             if (ENC == HDC_ENC_FP32) {
                 float *o = (float *)dst + r * (int64_t)ldd + f0;
-#pragma unroll
-                for (int j = 0; j < 4; j++)
-                    if (f0 + j < ldd) o[j] = v[j];
+                o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
             } else if (ENC == HDC_ENC_BF16) {
-                __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
-                __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
-                uint2 pk;
-                pk.x = *reinterpret_cast<uint32_t *>(&a);
-                pk.y = *reinterpret_cast<uint32_t *>(&b);
-                *reinterpret_cast<uint2 *>((__nv_bfloat16 *)dst + r * (int64_t)ldd + f0) = pk;
+                *reinterpret_cast<uint2 *>((__nv_bfloat16 *)dst + r * (int64_t)ldd + f0) = to_bf16x4(x.x, x.y, x.z, x.w);
             } else {
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    if (slow) v[j] = (float)((double)v[j] * ldexp(1.0, -k));
-                    else v[j] *= mul;
-                }
-                __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[0], v[1]), __NV_SATFINITE, __NV_E4M3);
-                __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v[2], v[3]), __NV_SATFINITE, __NV_E4M3);
-                uint32_t pk = (uint32_t)lo | ((uint32_t)hi << 16);
-                *reinterpret_cast<uint32_t *>((uint8_t *)dst + r * (int64_t)ldd + f0) = pk;
+                *reinterpret_cast<uint32_t *>((uint8_t *)dst + r * (int64_t)ldd + f0) =
+                    to_e4m3x4(scale_pow2(x.x, k), scale_pow2(x.y, k), scale_pow2(x.z, k), scale_pow2(x.w, k));
             }
+        };
+        if (ENC == HDC_ENC_FP8_E4M3 && in_regs) {
+#pragma unroll
+            for (int it = 0; it < MAXIT; it++) {
+                const int f0 = it * 128 + lane * 4;
+                if (it < nit && f0 < ldd) emit(f0, v[it]);
+            }
+        } else {
+            for (int f0 = lane * 4; f0 < ldd; f0 += 128) emit(f0, load4<VEC>(row, f0, F));
         }
     }
 }
@@ -161,19 +208,23 @@ cudaError_t launch_quant_rows(const float *src, int64_t lds, int64_t row_off, in
                               int F, int enc, void *dst, int ldd, float *scale, cudaStream_t st)
 {
     if (nrows <= 0) return cudaSuccess;
+    // eight warps (rows) per block, about eight resident blocks per SM
     int64_t blocks = (nrows + 7) / 8;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > 152 * 8 * 4) blocks = 152 * 8 * 4;
     dim3 g((unsigned)blocks), b(256);
+    const bool vec = F % 4 == 0 && lds % 4 == 0 && ((uintptr_t)src % 16) == 0;
+#define HDC_QUANT(E, V) quant_rows_kernel<E, V><<<g, b, 0, st>>>(src, lds, row_off, row_step, nrows, F, dst, ldd, scale)
     switch (enc) {
     case HDC_ENC_FP32:
-        quant_rows_kernel<HDC_ENC_FP32><<<g, b, 0, st>>>(src, lds, row_off, row_step, nrows, F, dst, ldd, scale);
+        if (vec) HDC_QUANT(HDC_ENC_FP32, true); else HDC_QUANT(HDC_ENC_FP32, false);
         break;
     case HDC_ENC_BF16:
-        quant_rows_kernel<HDC_ENC_BF16><<<g, b, 0, st>>>(src, lds, row_off, row_step, nrows, F, dst, ldd, scale);
+        if (vec) HDC_QUANT(HDC_ENC_BF16, true); else HDC_QUANT(HDC_ENC_BF16, false);
         break;
     default:
-        quant_rows_kernel<HDC_ENC_FP8_E4M3><<<g, b, 0, st>>>(src, lds, row_off, row_step, nrows, F, dst, ldd, scale);
+        if (vec) HDC_QUANT(HDC_ENC_FP8_E4M3, true); else HDC_QUANT(HDC_ENC_FP8_E4M3, false);
     }
+#undef HDC_QUANT
     return cudaGetLastError();
 }
 

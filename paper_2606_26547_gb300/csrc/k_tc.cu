@@ -24,14 +24,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// 2-D map over a row-major [rows x ld] operand; box = 128 bytes of K by
+// 2-D map over a row-major [rows x F] operand with row stride ld; box = 128 bytes of K by
 // box_rows rows, 128-byte swizzle, zero fill outside the tensor.
-bool make_map(CUtensorMap *m, const void *base, int enc, int ld, int64_t rows, int box_rows)
+bool make_map(CUtensorMap *m, const void *base, int enc, int F, int ld, int64_t rows, int box_rows)
 {
     auto fn = encode_fn();
     if (!fn) return false;
     const int es = enc == HDC_ENC_BF16 ? 2 : 1;
-    cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+    cuuint64_t dims[2] = {(cuuint64_t)F, (cuuint64_t)rows};  // zero fill past F
     cuuint64_t strides[1] = {(cuuint64_t)ld * es};
     cuuint32_t box[2] = {(cuuint32_t)(tc::BKB / es), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
@@ -54,8 +54,8 @@ int sm_count()
 bool tc_supported(const TcArgs &a)
 {
     if (a.enc != HDC_ENC_BF16 && a.enc != HDC_ENC_FP8_E4M3) return false;
-    const int kel = a.enc == HDC_ENC_BF16 ? tc::BKB / 2 : tc::BKB;
-    if (a.ldx != a.ldb || a.ldx % kel != 0 || a.ldx <= 0) return false;
+    const int es = a.enc == HDC_ENC_BF16 ? 2 : 1;
+    if (a.F <= 0 || a.ldx != a.ldb || a.ldx < a.F || (a.ldx * es) % 16 != 0) return false;
     if (a.N <= 0 || a.N > 0x7fffffffLL - tc::BM || a.Dk <= 0 || a.W != words_for(a.Dk)) return false;
     // fused classify: binary class hypervectors, up to 128 classes
     if (a.planes && (a.C <= 0 || a.C > 128 || a.nb != 1)) return false;
@@ -67,12 +67,17 @@ bool tc_supported(const TcArgs &a)
 cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st)
 {
     CUtensorMap ma, mb;
-    if (!make_map(&ma, a.Xq, a.enc, a.ldx, a.N, tc::BM) || !make_map(&mb, a.Bq, a.enc, a.ldb, a.Dk, tc::BN))
+    if (!make_map(&ma, a.Xq, a.enc, a.F, a.ldx, a.N, tc::BM) || !make_map(&mb, a.Bq, a.enc, a.F, a.ldb, a.Dk, tc::BN))
         return cudaErrorInvalidValue;
     tc::Params p;
     p.N = a.N;
     p.Dk = a.Dk;
-    p.num_kb = a.ldx / (a.enc == HDC_ENC_BF16 ? tc::BKB / 2 : tc::BKB);
+    // K blocks of 128 bytes; the last one issues only the MMAs (32 bytes of
+    // K each) that reach into [0, F)
+    const int es = a.enc == HDC_ENC_BF16 ? 2 : 1;
+    const int kbytes = a.F * es;
+    p.num_kb = (kbytes + tc::BKB - 1) / tc::BKB;
+    p.kmma_last = (kbytes - (p.num_kb - 1) * tc::BKB + 31) / 32;
     p.W = a.W;
     p.sx = a.sx;
     p.sb = a.sb;
