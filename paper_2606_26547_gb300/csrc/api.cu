@@ -336,8 +336,10 @@ hdc_status hdc_stream_status(hdc_stream_t stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaStreamSynchronize(st) != cudaSuccess) return HDC_ERR_CUDA;
-    int status = 0;
+    int status = 0, qstatus = 0;
     if (tc_read_status(st, &status) != cudaSuccess) return HDC_ERR_CUDA;
+    if (quant_read_status(st, &qstatus) != cudaSuccess) return HDC_ERR_CUDA;
+    if (!status) status = qstatus;
     if (status == 1) return HDC_ERR_TIMEOUT;
     if (status != 0) return HDC_ERR_DEVICE;
     return HDC_OK;

@@ -102,6 +102,9 @@ struct TcArgs {
 cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st);
 bool tc_supported(const TcArgs &a);
 
+// Reads and clears the streaming quantiser's device status word.
+cudaError_t quant_read_status(cudaStream_t st, int *status);
+
 // Reads and clears the tensor-core kernels' device status word.
 cudaError_t tc_read_status(cudaStream_t st, int *status);
 

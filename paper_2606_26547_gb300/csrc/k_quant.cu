@@ -136,6 +136,121 @@ __global__ void __launch_bounds__(256) quant_rows_kernel(const float *__restrict
     }
 }
 
+// ---------------------------------------------------------------------------
+// Streaming variant for 16-byte aligned rows: every warp keeps a ring of
+// QSLOTS rows in shared memory, filled by bulk asynchronous copies
+// (cp.async.bulk, completion on one mbarrier per slot), so many rows are in
+// flight per SM without holding them in registers.  The warp reduces the
+// row maximum and converts straight from shared memory.  Waits are bounded
+// by the global timer; on expiry the kernel records status 1 and stops.
+constexpr int QSLOTS = 4, QWARPS = 4;
+constexpr unsigned long long QTIMEOUT_NS = 2000000000ull;
+
+static __device__ int g_quant_status;
+
+__device__ __forceinline__ unsigned long long qtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool qbar_try(uint32_t a, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+template <int ENC>
+__global__ void __launch_bounds__(QWARPS * 32) quant_rows_bulk_kernel(const float *__restrict__ src, int64_t lds,
+                                                                      int64_t row_off, int64_t row_step,
+                                                                      int64_t nrows, int F, void *__restrict__ dst,
+                                                                      int ldd, float *__restrict__ scale)
+{
+    extern __shared__ __align__(128) uint8_t qsm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t rowbytes = (uint32_t)F * 4u;  // multiple of 16 (F % 4 == 0)
+    float *ring = reinterpret_cast<float *>(qsm + (size_t)wib * QSLOTS * rowbytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(qsm + (size_t)QWARPS * QSLOTS * rowbytes) + wib * QSLOTS;
+    const int64_t gw = (int64_t)blockIdx.x * QWARPS + wib, nw = (int64_t)gridDim.x * QWARPS;
+    const int64_t my_rows = gw < nrows ? (nrows - 1 - gw) / nw + 1 : 0;
+    auto bar = [&](int s) { return (uint32_t)__cvta_generic_to_shared(bars + s); };
+    auto issue = [&](int64_t i) {  // lane 0: fetch this warp's i-th row into slot i % QSLOTS
+        const int s = (int)(i % QSLOTS);
+        const float *g = src + (row_off + (gw + i * nw) * row_step) * lds;
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(ring + (size_t)s * F);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(s)), "r"(rowbytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+                     "l"(g), "r"(rowbytes), "r"(bar(s))
+                     : "memory");
+    };
+    if (lane == 0) {
+        for (int s = 0; s < QSLOTS; s++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(s)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int64_t i = 0; i < my_rows && i < QSLOTS; i++) issue(i);
+    }
+    __syncwarp();
+    for (int64_t i = 0; i < my_rows; i++) {
+        const int s = (int)(i % QSLOTS);
+        const uint32_t parity = (uint32_t)((i / QSLOTS) & 1);
+        bool ok = qbar_try(bar(s), parity);
+        if (!ok) {
+            const unsigned long long t0 = qtimer();
+            while (!(ok = qbar_try(bar(s), parity)) && qtimer() - t0 < QTIMEOUT_NS) {}
+        }
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) {
+                atomicCAS(&g_quant_status, 0, 1);
+                // let this warp's copies in flight land before the block exits
+                const int64_t issued = i + QSLOTS < my_rows ? i + QSLOTS : my_rows;
+                for (int64_t j = i; j < issued; j++) {
+                    const unsigned long long t0 = qtimer();
+                    while (!qbar_try(bar((int)(j % QSLOTS)), (uint32_t)((j / QSLOTS) & 1)) &&
+                           qtimer() - t0 < 100000000ull) {}
+                }
+            }
+            break;
+        }
+        const float *row = ring + (size_t)s * F;
+        const int64_t r = gw + i * nw;
+        int k = 0;
+        if (ENC == HDC_ENC_FP8_E4M3) {
+            float amax = 0.f;
+            for (int f = lane * 4; f < F; f += 128) {
+                const float4 x = *reinterpret_cast<const float4 *>(row + f);
+                amax = fmaxf(amax, fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+            k = pow2_scale_exp(amax);
+            if (lane == 0) scale[r] = k >= -126 ? __int_as_float((127 + k) << 23) : ldexpf(1.f, k);
+        }
+        for (int f0 = lane * 4; f0 < ldd; f0 += 128) {
+            const float4 x = f0 < F ? *reinterpret_cast<const float4 *>(row + f0) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ENC == HDC_ENC_FP32) {
+                *reinterpret_cast<float4 *>((float *)dst + r * (int64_t)ldd + f0) = x;
+            } else if (ENC == HDC_ENC_BF16) {
+                *reinterpret_cast<uint2 *>((__nv_bfloat16 *)dst + r * (int64_t)ldd + f0) = to_bf16x4(x.x, x.y, x.z, x.w);
+            } else {
+                *reinterpret_cast<uint32_t *>((uint8_t *)dst + r * (int64_t)ldd + f0) =
+                    to_e4m3x4(scale_pow2(x.x, k), scale_pow2(x.y, k), scale_pow2(x.z, k), scale_pow2(x.w, k));
+            }
+        }
+        // every lane is done reading the slot before the copy engine refills it
+        __syncwarp();
+        if (lane == 0 && i + QSLOTS < my_rows) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(i + QSLOTS);
+        }
+    }
+}
+
 // One block per class.  b == 1: plane 0 = sign bits.  b > 1: symmetric
 // per-class quantisation, two's-complement planes, sums and norms over K.
 __global__ void __launch_bounds__(256) class_prepare_kernel(const int32_t *__restrict__ acc, int D, int64_t s0,
@@ -208,7 +323,33 @@ cudaError_t launch_quant_rows(const float *src, int64_t lds, int64_t row_off, in
                               int F, int enc, void *dst, int ldd, float *scale, cudaStream_t st)
 {
     if (nrows <= 0) return cudaSuccess;
-    // eight warps (rows) per block, about eight resident blocks per SM
+    const bool aligned_rows = F % 4 == 0 && lds % 4 == 0 && ((uintptr_t)src % 16) == 0;
+    const size_t qsmem = (size_t)QWARPS * QSLOTS * F * 4 + (size_t)QWARPS * QSLOTS * 8;
+    if (aligned_rows && qsmem <= 200 * 1024) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+        const int per_sm = (int)((220 * 1024) / qsmem) > 0 ? (int)((220 * 1024) / qsmem) : 1;
+        int64_t qblocks = (nrows + QWARPS - 1) / QWARPS;
+        if (qblocks > (int64_t)sms * per_sm) qblocks = (int64_t)sms * per_sm;
+#define HDC_QBULK(E)                                                                                              \
+    do {                                                                                                          \
+        cudaError_t e = cudaFuncSetAttribute(quant_rows_bulk_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)qsmem);                                                         \
+        if (e != cudaSuccess) return e;                                                                           \
+        quant_rows_bulk_kernel<E><<<(unsigned)qblocks, QWARPS * 32, qsmem, st>>>(src, lds, row_off, row_step,     \
+                                                                                 nrows, F, dst, ldd, scale);      \
+    } while (0)
+        switch (enc) {
+        case HDC_ENC_FP32: HDC_QBULK(HDC_ENC_FP32); break;
+        case HDC_ENC_BF16: HDC_QBULK(HDC_ENC_BF16); break;
+        default: HDC_QBULK(HDC_ENC_FP8_E4M3);
+        }
+#undef HDC_QBULK
+        return cudaGetLastError();
+    }
+    // unaligned rows: one warp per row straight from global memory
     int64_t blocks = (nrows + 7) / 8;
     if (blocks > 152 * 8 * 4) blocks = 152 * 8 * 4;
     dim3 g((unsigned)blocks), b(256);
@@ -234,6 +375,26 @@ cudaError_t launch_class_prepare(const int32_t *acc, int C, int D, const Perf &p
     if (C <= 0) return cudaSuccess;
     class_prepare_kernel<<<C, 256, 0, st>>>(acc, D, p.s0, p.stride, p.Dk, b, C, planes, W, csum, cnorm);
     return cudaGetLastError();
+}
+
+}  // namespace hdc
+
+namespace hdc {
+
+// Read and clear the streaming quantiser's device status word.
+cudaError_t quant_read_status(cudaStream_t st, int *status)
+{
+    int h = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(&h, g_quant_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    *status = h;
+    if (h != 0) {
+        const int zero = 0;
+        e = cudaMemcpyToSymbolAsync(g_quant_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    return e;
 }
 
 }  // namespace hdc

@@ -64,9 +64,10 @@ def decode_bq(model, enc):
 # ------------------------------------------------------------------ quantise
 
 @pytest.mark.parametrize("enc", ["bf16", "fp8", "fp32"])
-def test_base_quantisation_bit_exact(hdc, enc):
+@pytest.mark.parametrize("F", [617, 616])   # unaligned rows / 16-byte rows (streaming path)
+def test_base_quantisation_bit_exact(hdc, enc, F):
     rng = np.random.default_rng(1)
-    D, F = 700, 617
+    D = 700
     Bt = (rng.standard_normal((D, F)) * 10.0 ** rng.uniform(-3, 3, (D, 1))).astype(np.float32)
     Bt[5] = 0.0
     Bt[9] = (rng.standard_normal(F) * 1e-41).astype(np.float32)   # subnormal row: scale 2^k, k < -126
