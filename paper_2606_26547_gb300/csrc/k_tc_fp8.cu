@@ -7,9 +7,7 @@ namespace tc {
 cudaError_t launch_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const Params &p, unsigned grid, bool classify,
                        cudaStream_t st)
 {
-    // the query tile stays resident when its K blocks fit
-    if (p.num_kb <= MAXKB) return launch_enc<HDC_ENC_FP8_E4M3, true>(ma, mb, p, grid, classify, st);
-    return launch_enc<HDC_ENC_FP8_E4M3, false>(ma, mb, p, grid, classify, st);
+    return launch_enc<HDC_ENC_FP8_E4M3>(ma, mb, p, grid, classify, st);
 }
 
 cudaError_t status_fp8(cudaStream_t st, int *status) { return read_status(st, status); }

@@ -47,11 +47,13 @@ constexpr int B_BYTES = BN * BKB;            // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int NUM_THREADS = 192;
 constexpr int TMEM_COLS = 2 * BN;            // two accumulators
+constexpr int NUM_BARS = 2 * STAGES + 5;     // full, empty, tfull[2], tempty[2], done
+constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + NUM_BARS * 8 + 16;
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
 
 struct Params {
     int64_t N;
-    int Dk, num_kb, W;
+    int Dk, num_kb, kmma_last, W;
     const float *sx, *sb;
     uint32_t *H;
     float *scores;
@@ -194,38 +196,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
                  : "memory");
 }
 
-// 64 consecutive columns as two 32-column loads behind one wait.
-__device__ __forceinline__ void tmem_ld32x2(uint32_t taddr, uint32_t (&r0)[32], uint32_t (&r1)[32])
-{
-#define HDC_TLD(R, A)                                                                                              \
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "                                                       \
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"                                       \
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                      \
-                 : "=r"(R[0]), "=r"(R[1]), "=r"(R[2]), "=r"(R[3]), "=r"(R[4]), "=r"(R[5]), "=r"(R[6]), "=r"(R[7]), \
-                   "=r"(R[8]), "=r"(R[9]), "=r"(R[10]), "=r"(R[11]), "=r"(R[12]), "=r"(R[13]), "=r"(R[14]),       \
-                   "=r"(R[15]), "=r"(R[16]), "=r"(R[17]), "=r"(R[18]), "=r"(R[19]), "=r"(R[20]), "=r"(R[21]),     \
-                   "=r"(R[22]), "=r"(R[23]), "=r"(R[24]), "=r"(R[25]), "=r"(R[26]), "=r"(R[27]), "=r"(R[28]),     \
-                   "=r"(R[29]), "=r"(R[30]), "=r"(R[31])                                                          \
-                 : "r"(A))
-#define HDC_TDEP(R)                                                                                                \
-    asm volatile(""                                                                                                \
-                 : "+r"(R[0]), "+r"(R[1]), "+r"(R[2]), "+r"(R[3]), "+r"(R[4]), "+r"(R[5]), "+r"(R[6]), "+r"(R[7]), \
-                   "+r"(R[8]), "+r"(R[9]), "+r"(R[10]), "+r"(R[11]), "+r"(R[12]), "+r"(R[13]), "+r"(R[14]),       \
-                   "+r"(R[15]), "+r"(R[16]), "+r"(R[17]), "+r"(R[18]), "+r"(R[19]), "+r"(R[20]), "+r"(R[21]),     \
-                   "+r"(R[22]), "+r"(R[23]), "+r"(R[24]), "+r"(R[25]), "+r"(R[26]), "+r"(R[27]), "+r"(R[28]),     \
-                   "+r"(R[29]), "+r"(R[30]), "+r"(R[31])                                                          \
-                 :                                                                                                \
-                 : "memory")
-    HDC_TLD(r0, taddr);
-    HDC_TLD(r1, taddr + 32);
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    // the empty statements tie both register sets to a point after the wait
-    HDC_TDEP(r0);
-    HDC_TDEP(r1);
-#undef HDC_TLD
-#undef HDC_TDEP
-}
-
 // sign(0) = +1: -0.0 and +0.0 both give bit 0.
 __device__ __forceinline__ uint32_t pack_signs(const uint32_t (&r)[32])
 {
@@ -236,52 +206,30 @@ __device__ __forceinline__ uint32_t pack_signs(const uint32_t (&r)[32])
 }
 
 // ------------------------------------------------------------------ kernel
-// ARES = false: query (A) tiles stream through the stage ring with the base
-//               (B) tiles, one A tile per 256-dim tile.
-// ARES = true:  the whole 128 x K query tile stays resident in shared memory
-//               for all dim tiles of its query tile (K <= MAXKB blocks), and
-//               only base tiles stream; A block kb of the next query tile is
-//               reloaded as soon as the last MMA that reads it has completed.
-constexpr int MAXKB = 8;
-constexpr int ARES_RING = 3;
-
-__host__ __device__ constexpr int ring_of(bool ares) { return ares ? ARES_RING : STAGES; }
-__host__ __device__ constexpr int nbars_of(bool ares) { return 2 * ring_of(ares) + 5 + 2 * MAXKB; }
-inline size_t smem_bytes(bool ares, int num_kb)
-{
-    const int abufs = ares ? num_kb : STAGES;
-    return 1024 + (size_t)abufs * A_BYTES + (size_t)ring_of(ares) * B_BYTES + nbars_of(ares) * 8 + 16;
-}
-
-template <int ENC, int CMAX, bool CLASSIFY, bool ARES>
+template <int ENC, int CMAX, bool CLASSIFY>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_encode_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p)
 {
-    constexpr int RING = ring_of(ARES);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const int abufs = ARES ? p.num_kb : RING;
     uint8_t *sA = smem;
-    uint8_t *sB = smem + abufs * A_BYTES;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + RING * B_BYTES);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + nbars_of(ARES));
+    uint8_t *sB = smem + STAGES * A_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + NUM_BARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     auto full = [&](int s) { return su32(bars + s); };
-    auto empty = [&](int s) { return su32(bars + RING + s); };
-    auto tfull = [&](int a) { return su32(bars + 2 * RING + a); };
-    auto tempty = [&](int a) { return su32(bars + 2 * RING + 2 + a); };
-    const uint32_t done_bar = su32(bars + 2 * RING + 4);
-    auto afull = [&](int k) { return su32(bars + 2 * RING + 5 + k); };
-    auto afree = [&](int k) { return su32(bars + 2 * RING + 5 + MAXKB + k); };
+    auto empty = [&](int s) { return su32(bars + STAGES + s); };
+    auto tfull = [&](int a) { return su32(bars + 2 * STAGES + a); };
+    auto tempty = [&](int a) { return su32(bars + 2 * STAGES + 2 + a); };
+    const uint32_t done_bar = su32(bars + 2 * STAGES + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t num_m_tiles = (p.N + BM - 1) / BM;
     const int num_n_tiles = (p.Dk + BN - 1) / BN;
     constexpr int KELEMS = ENC == HDC_ENC_BF16 ? BKB / 2 : BKB;
-    constexpr uint32_t STAGE_TX = ARES ? B_BYTES : STAGE_BYTES;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < RING; s++) {
+        for (int s = 0; s < STAGES; s++) {
             mbar_init(full(s), 1);
             mbar_init(empty(s), 1);
         }
@@ -290,10 +238,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             mbar_init(tempty(a), BM);
         }
         mbar_init(done_bar, 1);
-        for (int k = 0; k < MAXKB; k++) {
-            mbar_init(afull(k), 1);
-            mbar_init(afree(k), 1);
-        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -314,45 +258,27 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
             int stage = 0;
             uint32_t phase = 0;
-            uint32_t issued = 0, ipar = 0;     // ring slots with a copy issued, their parity
-            uint32_t a_issued = 0, a_par = 0;  // resident A blocks likewise
+            bool issued[STAGES];
+            uint32_t ipar[STAGES];
+            for (int s = 0; s < STAGES; s++) { issued[s] = false; ipar[s] = 0; }
             bool ab = false;
-            int64_t it = 0;
-            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++) {
-                if (ARES) {
-                    const uint32_t apar = (uint32_t)(it & 1);
-                    for (int kb = 0; kb < p.num_kb; kb++) {
-                        if (!mbar_wait(afree(kb), apar ^ 1, abort_flag)) { ab = true; break; }
-                        mbar_expect_tx(afull(kb), A_BYTES);
-                        tma_load_2d(su32(sA + kb * A_BYTES), &tmA, kb * KELEMS, (int)(mt * BM), afull(kb));
-                        a_issued |= 1u << kb;
-                        a_par = (a_par & ~(1u << kb)) | (apar << kb);
-                    }
-                }
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
                 for (int nt = 0; nt < num_n_tiles && !ab; nt++)
                     for (int kb = 0; kb < p.num_kb; kb++) {
                         if (!mbar_wait(empty(stage), phase ^ 1, abort_flag)) { ab = true; break; }
-                        mbar_expect_tx(full(stage), STAGE_TX);
-                        if (!ARES)
-                            tma_load_2d(su32(sA + stage * A_BYTES), &tmA, kb * KELEMS, (int)(mt * BM), full(stage));
+                        mbar_expect_tx(full(stage), STAGE_BYTES);
+                        tma_load_2d(su32(sA + stage * A_BYTES), &tmA, kb * KELEMS, (int)(mt * BM), full(stage));
                         tma_load_2d(su32(sB + stage * B_BYTES), &tmB, kb * KELEMS, nt * BN, full(stage));
-                        issued |= 1u << stage;
-                        ipar = (ipar & ~(1u << stage)) | (phase << stage);
-                        if (++stage == RING) { stage = 0; phase ^= 1; }
+                        issued[stage] = true;
+                        ipar[stage] = phase;
+                        if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
-            }
-            if (ab) {  // let our own copies land before the CTA exits
-                for (int s = 0; s < RING; s++)
-                    if (issued >> s & 1) {
+            if (ab)  // let our own copies land before the CTA exits
+                for (int s = 0; s < STAGES; s++)
+                    if (issued[s]) {
                         const unsigned long long t0 = gtimer();
-                        while (!mbar_try(full(s), ipar >> s & 1) && gtimer() - t0 < 100000000ull) {}
+                        while (!mbar_try(full(s), ipar[s]) && gtimer() - t0 < 100000000ull) {}
                     }
-                for (int k = 0; k < MAXKB; k++)
-                    if (a_issued >> k & 1) {
-                        const unsigned long long t0 = gtimer();
-                        while (!mbar_try(afull(k), a_par >> k & 1) && gtimer() - t0 < 100000000ull) {}
-                    }
-            }
         }
     } else if (warp == 5) {
         if (lane == 0) {  // ---------------------------------- MMA issuer
@@ -360,26 +286,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             int stage = 0, acc = 0;
             uint32_t phase = 0, aphase = 0;
             bool ab = false;
-            int64_t it = 0;
-            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++)
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
                 for (int nt = 0; nt < num_n_tiles && !ab; nt++) {
                     if (!mbar_wait(tempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
                     tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)(acc * BN);
                     for (int kb = 0; kb < p.num_kb; kb++) {
-                        if (ARES && nt == 0 && !mbar_wait(afull(kb), (uint32_t)(it & 1), abort_flag)) {
-                            ab = true;
-                            break;
-                        }
                         if (!mbar_wait(full(stage), phase, abort_flag)) { ab = true; break; }
                         tc_fence_after();
-                        const uint32_t a0 = su32(sA + (ARES ? kb : stage) * A_BYTES), b0 = su32(sB + stage * B_BYTES);
+                        const uint32_t a0 = su32(sA + stage * A_BYTES), b0 = su32(sB + stage * B_BYTES);
+                        const int nk = kb == p.num_kb - 1 ? p.kmma_last : BKB / 32;
 #pragma unroll
                         for (int k = 0; k < BKB / 32; k++)
-                            mma<ENC>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), id, (kb | k) != 0);
+                            if (k < nk) mma<ENC>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), id, (kb | k) != 0);
                         mma_commit(empty(stage));
-                        if (ARES && nt == num_n_tiles - 1) mma_commit(afree(kb));
-                        if (++stage == RING) { stage = 0; phase ^= 1; }
+                        if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
                     if (ab) break;
                     mma_commit(tfull(acc));
@@ -408,21 +329,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 tc_fence_after();
                 uint32_t words[BN / 32];
 #pragma unroll
-                for (int j = 0; j < BN / 32; j += 2) {
-                    uint32_t r0[32], r1[32];
-                    const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + j * 32);
-                    tmem_ld32x2(ta, r0, r1);
+                for (int j = 0; j < BN / 32; j++) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + j * 32), r);
                     if (!CLASSIFY && p.scores && valid) {
                         const float rs = p.sx ? p.sx[row] : 1.f;
 #pragma unroll
-                        for (int i = 0; i < 64; i++) {
+                        for (int i = 0; i < 32; i++) {
                             const int col = nt * BN + j * 32 + i;
-                            const float v = __uint_as_float(i < 32 ? r0[i & 31] : r1[i & 31]);
-                            if (col < p.Dk) p.scores[row * p.Dk + col] = v * rs * (p.sb ? p.sb[col] : 1.f);
+                            if (col < p.Dk)
+                                p.scores[row * p.Dk + col] = __uint_as_float(r[i]) * rs * (p.sb ? p.sb[col] : 1.f);
                         }
                     }
-                    words[j] = pack_signs(r0);
-                    words[j + 1] = pack_signs(r1);
+                    words[j] = pack_signs(r);
                 }
                 tc_fence_before();
                 mbar_arrive(tempty(acc));
@@ -471,27 +390,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 }
 
 // Launch helpers, instantiated by each encoding's translation unit.
-template <int ENC, int CMAX, bool CLASSIFY, bool ARES>
+template <int ENC, int CMAX, bool CLASSIFY>
 static cudaError_t launch_one(const CUtensorMap &ma, const CUtensorMap &mb, const Params &p, unsigned grid,
                               cudaStream_t st)
 {
-    auto k = tc_encode_kernel<ENC, CMAX, CLASSIFY, ARES>;
-    const size_t smem = smem_bytes(ARES, p.num_kb);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto k = tc_encode_kernel<ENC, CMAX, CLASSIFY>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    k<<<grid, NUM_THREADS, smem, st>>>(ma, mb, p);
+    k<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(ma, mb, p);
     return cudaGetLastError();
 }
 
-template <int ENC, bool ARES>
+template <int ENC>
 static cudaError_t launch_enc(const CUtensorMap &ma, const CUtensorMap &mb, const Params &p, unsigned grid,
                               bool classify, cudaStream_t st)
 {
-    if (!classify) return launch_one<ENC, 1, false, ARES>(ma, mb, p, grid, st);
-    if (p.C <= 16) return launch_one<ENC, 16, true, ARES>(ma, mb, p, grid, st);
-    if (p.C <= 32) return launch_one<ENC, 32, true, ARES>(ma, mb, p, grid, st);
-    if (p.C <= 64) return launch_one<ENC, 64, true, ARES>(ma, mb, p, grid, st);
-    return launch_one<ENC, 128, true, ARES>(ma, mb, p, grid, st);
+    if (!classify) return launch_one<ENC, 1, false>(ma, mb, p, grid, st);
+    if (p.C <= 16) return launch_one<ENC, 16, true>(ma, mb, p, grid, st);
+    if (p.C <= 32) return launch_one<ENC, 32, true>(ma, mb, p, grid, st);
+    if (p.C <= 64) return launch_one<ENC, 64, true>(ma, mb, p, grid, st);
+    return launch_one<ENC, 128, true>(ma, mb, p, grid, st);
 }
 
 // Read and clear this translation unit's device status word.
