@@ -75,12 +75,10 @@ cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st)
     tc::Params p;
     p.N = a.N;
     p.Dk = a.Dk;
-    // K blocks of 128 bytes; the last one issues only the MMAs (32 bytes of
-    // K each) that reach into [0, F)
+    // K blocks of 128 bytes over the padded row (zeros past F); issuing only
+    // the MMAs that reach into [0, F) in the last block measured slower
     const int es = a.enc == HDC_ENC_BF16 ? 2 : 1;
-    const int kbytes = a.F * es;
-    p.num_kb = (kbytes + tc::BKB - 1) / tc::BKB;
-    p.kmma_last = (kbytes - (p.num_kb - 1) * tc::BKB + 31) / 32;
+    p.num_kb = (a.ldx * es + tc::BKB - 1) / tc::BKB;
     p.W = a.W;
     p.sx = a.sx;
     p.sb = a.sb;

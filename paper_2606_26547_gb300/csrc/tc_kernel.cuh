@@ -53,7 +53,7 @@ constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
 
 struct Params {
     int64_t N;
-    int Dk, num_kb, kmma_last, W;
+    int Dk, num_kb, W;
     const float *sx, *sb;
     uint32_t *H;
     float *scores;
@@ -295,10 +295,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         if (!mbar_wait(full(stage), phase, abort_flag)) { ab = true; break; }
                         tc_fence_after();
                         const uint32_t a0 = su32(sA + stage * A_BYTES), b0 = su32(sB + stage * B_BYTES);
-                        const int nk = kb == p.num_kb - 1 ? p.kmma_last : BKB / 32;
 #pragma unroll
                         for (int k = 0; k < BKB / 32; k++)
-                            if (k < nk) mma<ENC>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), id, (kb | k) != 0);
+                            mma<ENC>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), id, (kb | k) != 0);
                         mma_commit(empty(stage));
                         if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
