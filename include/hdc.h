@@ -193,6 +193,33 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m,
                         int32_t *labels, int32_t *dists, double *scores,
                         void *ws, size_t ws_bytes, hdc_stream_t stream);
 
+/* Size of the fixed scratch array behind hdc_classify_static.              */
+#define HDC_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* hdc_classify for callers that cannot allocate device memory.  The paper
+ * has no counterpart; this is a deployment convenience.  A plugin inside a
+ * serving process whose device memory belongs to another allocator, a
+ * process held to a device-memory budget fixed at start-up, or a loop that
+ * may not call cudaMalloc (it can synchronise the device) passes only its
+ * inputs and outputs; the scratch that hdc_classify takes as `ws` is a
+ * fixed device array compiled into the library instead.
+ *  - Limit: calls with hdc_workspace_bytes(N, m) > HDC_STATIC_SCRATCH_BYTES
+ *    (64 MiB: about 31,000 queries of 784 features at 10,000 dims) return
+ *    HDC_ERR_WORKSPACE and enqueue nothing; split larger batches.
+ *  - Every GPU that loads libhdc holds the array until the process exits.
+ *  - The first call on a device looks up the array's device address (set-up,
+ *    once per device, with that device current); make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array, which keeps the last call's contents
+ *    (nothing in it needs to start at zero).  Calls whose work overlaps on
+ *    the GPU -- e.g. on two streams without ordering -- race on it: order
+ *    them on one stream or with events.
+ * Arguments, outputs and errors are otherwise those of hdc_classify; the
+ * library allocates nothing.                                              */
+hdc_status hdc_classify_static(const float *X, int64_t N, const hdc_model *m,
+                               int32_t *labels, int32_t *dists, double *scores,
+                               hdc_stream_t stream);
+
 /* Waits for `stream`, then reads and clears the library's device status
  * words: HDC_OK, HDC_ERR_TIMEOUT or HDC_ERR_DEVICE (or HDC_ERR_CUDA if the
  * stream itself reports an error).                                        */

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libhdc.so")
 
 ENC = {"fp32": 0, "bf16": 1, "fp8": 2}
 FLAG_SIMT_ENCODE = 0x1
+STATIC_SCRATCH_BYTES = 64 << 20  # HDC_STATIC_SCRATCH_BYTES
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported configuration", 3: "buffer or workspace too small",
           4: "CUDA error", 5: "device wait timed out", 6: "device-side check failed"}
@@ -56,6 +57,7 @@ _SIGS = {
     "hdc_train_workspace_bytes": (_I32, [_I64, _I32, _I32, _P]),
     "hdc_train_epoch": (_I32, [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
     "hdc_classify": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _SZ, _P]),
+    "hdc_classify_static": (_I32, [_P, _I64, _P, _P, _P, _P, _P]),
     "hdc_stream_status": (_I32, [_P]),
     "hdc_profile_events": (None, [_P, _P]),
     "hdc_status_string": (ctypes.c_char_p, [_I32]),
@@ -255,6 +257,28 @@ def profile_events(start=None, stop=None) -> None:
     from this thread (None, None turns it off)."""
     load().hdc_profile_events(ctypes.c_void_p(start.cuda_event) if start is not None else None,
                               ctypes.c_void_p(stop.cuda_event) if stop is not None else None)
+
+
+def classify_static(X: torch.Tensor, model: Model, sims: bool = False, labels: torch.Tensor | None = None,
+                    stream=None):
+    """classify() through hdc_classify_static: no workspace argument; the
+    scratch is the library's fixed device array (one call at a time per
+    device, at most STATIC_SCRATCH_BYTES of workspace)."""
+    assert X.dtype == torch.float32 and X.dim() == 2 and X.shape[1] == model.m.F
+    N, C = X.shape[0], model.C
+    if labels is None:
+        labels = torch.empty(N, dtype=torch.int32, device=X.device)
+    dd = sc = None
+    if sims:
+        if model.m.class_bits == 1:
+            dd = torch.empty((N, C), dtype=torch.int32, device=X.device)
+        else:
+            sc = torch.empty((N, C), dtype=torch.float64, device=X.device)
+    _call("hdc_classify_static", _ptr(X), N, ctypes.byref(model.m), _ptr(labels), _ptr(dd), _ptr(sc),
+          _stream(stream))
+    if sims:
+        return labels, (dd if dd is not None else sc)
+    return labels
 
 
 def stream_status(stream=None) -> int:

@@ -82,3 +82,10 @@ def test_argument_checks_without_gpu(lib):
     assert lib.hdc_train_epoch(None, None, 5, 10, 2, 7, None, None, None, None, 0, None) == 1
     assert lib.hdc_classify(None, 5, ctypes.byref(m), None, None, None, None, 0, None) == 1
     assert lib.hdc_kept_dims(100, None) == 100
+
+
+def test_static_scratch_size_matches_header(lib):
+    from paper_2606_26547_gb300 import hdc
+    src = open(os.path.join(ROOT, "include", "hdc.h")).read()
+    m = re.search(r"#define HDC_STATIC_SCRATCH_BYTES \(\(size_t\)(\d+) << (\d+)\)", src)
+    assert m and int(m.group(1)) << int(m.group(2)) == hdc.STATIC_SCRATCH_BYTES
