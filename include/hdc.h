@@ -193,6 +193,48 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m,
                         int32_t *labels, int32_t *dists, double *scores,
                         void *ws, size_t ws_bytes, hdc_stream_t stream);
 
+/* Batched evaluation of approximation configurations.  The paper's tuner
+ * (Sec. 3, Fig. 1) compiles and runs the application once per candidate
+ * configuration and reads back its QoS (accuracy).  Here every combination
+ * of perforation stride x class-hypervector width of one trained model is
+ * scored in one launch from the same validation hypervectors encoded once
+ * at the full D: the strides' kept-dimension sets are nested (stride 8's
+ * dims are a subset of stride 4's, ...), so each configuration is a bit
+ * mask over the same words.
+ *   strides[i]  power of two <= 32: perforation (0, 1, stride) of D
+ *   bits[j]     1 (Hamming, arg-min), 4 or 8 (b-bit cosine, arg-max, as in
+ *               hdc_classify), or 0: cosine against the unquantised int32
+ *               accumulators themselves (requires sum over D of acc^2 < 2^63)
+ * block_threads / words_per_chunk are launch-shape knobs (0 = default;
+ * 64, 128 or 256 threads; a multiple of 4 words) chosen by an autotuner;
+ * results do not depend on them.                                           */
+#define HDC_SWEEP_MAX_STRIDES 6
+#define HDC_SWEEP_MAX_BITS 4
+typedef struct {
+    uint32_t struct_size;                 /* = sizeof(hdc_sweep_spec)       */
+    int32_t n_strides;                    /* 1 .. HDC_SWEEP_MAX_STRIDES     */
+    int32_t strides[HDC_SWEEP_MAX_STRIDES];
+    int32_t n_bits;                       /* 1 .. HDC_SWEEP_MAX_BITS        */
+    int32_t bits[HDC_SWEEP_MAX_BITS];
+    int32_t block_threads;                /* 0, 64, 128 or 256              */
+    int32_t words_per_chunk;              /* 0 or a multiple of 4           */
+} hdc_sweep_spec;
+
+/* Workspace bytes for hdc_sweep_eval.                                      */
+hdc_status hdc_sweep_workspace_bytes(int32_t D, int32_t C, const hdc_sweep_spec *spec,
+                                     size_t *bytes);
+
+/* Score every (bits[j], strides[i]) configuration: H (N x W(D) packed
+ * validation hypervectors encoded at the full D, any encoding type), y (N
+ * labels), acc (C x D class accumulators).  correct (n_bits x n_strides
+ * int32, overwritten) counts the queries whose predicted class equals y;
+ * labels (optional, n_bits x n_strides x N int32) receives the predictions,
+ * which equal hdc_classify's for the same model and configuration.        */
+hdc_status hdc_sweep_eval(const uint32_t *H, const int32_t *y, int64_t N, int32_t D,
+                          int32_t C, const int32_t *acc, const hdc_sweep_spec *spec,
+                          int32_t *correct, int32_t *labels, void *ws, size_t ws_bytes,
+                          hdc_stream_t stream);
+
 /* Size of the fixed scratch array behind hdc_classify_static.              */
 #define HDC_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
 

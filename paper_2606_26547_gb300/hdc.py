@@ -58,6 +58,8 @@ _SIGS = {
     "hdc_train_epoch": (_I32, [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
     "hdc_classify": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _SZ, _P]),
     "hdc_classify_static": (_I32, [_P, _I64, _P, _P, _P, _P, _P]),
+    "hdc_sweep_workspace_bytes": (_I32, [_I32, _I32, _P, _P]),
+    "hdc_sweep_eval": (_I32, [_P, _P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _SZ, _P]),
     "hdc_stream_status": (_I32, [_P]),
     "hdc_profile_events": (None, [_P, _P]),
     "hdc_status_string": (ctypes.c_char_p, [_I32]),
@@ -181,11 +183,12 @@ class Model:
 
 
 def encode(X: torch.Tensor, model: Model, scores: bool = False, ws: torch.Tensor | None = None,
-           stream=None):
+           stream=None, out: torch.Tensor | None = None):
     """Packed hypervectors (N x W int32 view of uint32 words), [projections]."""
     assert X.dtype == torch.float32 and X.dim() == 2 and X.shape[1] == model.m.F
     N = X.shape[0]
-    H = torch.empty((N, model.W), dtype=torch.int32, device=X.device)
+    H = torch.empty((N, model.W), dtype=torch.int32, device=X.device) if out is None else out
+    assert H.shape == (N, model.W) and H.dtype == torch.int32
     S = torch.empty((N, model.Dk), dtype=torch.float32, device=X.device) if scores else None
     ws = model.workspace(N) if ws is None else ws
     _call("hdc_encode", _ptr(X), N, ctypes.byref(model.m), _ptr(H), _ptr(S), _ptr(ws), ws.numel(),
@@ -279,6 +282,50 @@ def classify_static(X: torch.Tensor, model: Model, sims: bool = False, labels: t
     if sims:
         return labels, (dd if dd is not None else sc)
     return labels
+
+
+class SweepSpecC(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("n_strides", ctypes.c_int32), ("strides", ctypes.c_int32 * 6),
+                ("n_bits", ctypes.c_int32), ("bits", ctypes.c_int32 * 4), ("block_threads", ctypes.c_int32),
+                ("words_per_chunk", ctypes.c_int32)]
+
+
+def sweep_spec(strides, bits, block_threads: int = 0, words_per_chunk: int = 0) -> SweepSpecC:
+    s = SweepSpecC()
+    s.struct_size = ctypes.sizeof(SweepSpecC)
+    s.n_strides = len(strides)
+    for i, v in enumerate(strides):
+        s.strides[i] = v
+    s.n_bits = len(bits)
+    for i, v in enumerate(bits):
+        s.bits[i] = v
+    s.block_threads = block_threads
+    s.words_per_chunk = words_per_chunk
+    return s
+
+
+class Sweep:
+    """Batched scoring of (class width x perforation stride) configurations
+    of one trained model (hdc_sweep_eval); buffers are allocated once so the
+    call can be captured in a CUDA graph."""
+
+    def __init__(self, D: int, C: int, strides, bits, N: int, device, block_threads: int = 0,
+                 words_per_chunk: int = 0, keep_labels: bool = False):
+        self.D, self.C, self.N = D, C, N
+        self.strides, self.bits = list(strides), list(bits)
+        self.spec = sweep_spec(self.strides, self.bits, block_threads, words_per_chunk)
+        n = ctypes.c_size_t()
+        _call("hdc_sweep_workspace_bytes", D, C, ctypes.byref(self.spec), ctypes.byref(n))
+        self.ws = _empty_bytes(n.value, device)
+        self.correct = torch.zeros((len(self.bits), len(self.strides)), dtype=torch.int32, device=device)
+        self.labels = (torch.empty((len(self.bits), len(self.strides), N), dtype=torch.int32, device=device)
+                       if keep_labels else None)
+
+    def __call__(self, H: torch.Tensor, y: torch.Tensor, acc: torch.Tensor, stream=None) -> torch.Tensor:
+        assert H.shape[0] == self.N and y.shape[0] == self.N and acc.shape == (self.C, self.D)
+        _call("hdc_sweep_eval", _ptr(H), _ptr(y), self.N, self.D, self.C, _ptr(acc), ctypes.byref(self.spec),
+              _ptr(self.correct), _ptr(self.labels), _ptr(self.ws), self.ws.numel(), _stream(stream))
+        return self.correct
 
 
 def stream_status(stream=None) -> int:
