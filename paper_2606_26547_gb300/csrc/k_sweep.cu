@@ -115,7 +115,42 @@ __global__ void __launch_bounds__(256) sweep_prep_kernel(const int32_t *__restri
     }
 }
 
-// One query per thread.  Shared memory: the chunk's query words [WCH][TPB],
+// Per-stride sums over one chunk of words for a class with NP planes
+// (NP = 1: Hamming, popc(q ^ c); NP = 4, 8: b-bit cosine, popc(q & plane)
+// weighted 2^p, the top plane negative).  Counts stay int32 per (plane,
+// stride) and are weighted once per chunk.
+template <int NP>
+__device__ __forceinline__ void chunk_counts(const uint32_t *sq, int QLD, int tid, const uint32_t *spc,
+                                             int pstride, int nw, const SweepConf &cf, long long *out)
+{
+    int cnt[NP][MAXS];
+#pragma unroll
+    for (int p = 0; p < NP; p++)
+#pragma unroll
+        for (int i = 0; i < MAXS; i++) cnt[p][i] = 0;
+    for (int j = 0; j < nw; j++) {
+        const uint32_t qw = sq[(size_t)j * QLD + tid];
+#pragma unroll
+        for (int p = 0; p < NP; p++) {
+            const uint32_t cw = spc[(size_t)p * pstride + j];
+            const uint32_t x = NP == 1 ? qw ^ cw : qw & cw;
+#pragma unroll
+            for (int i = 0; i < MAXS; i++)
+                if (i < cf.ns) cnt[p][i] += __popc(x & cf.mask[i]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < MAXS; i++) {
+        long long s = 0;
+#pragma unroll
+        for (int p = 0; p < NP; p++)
+            s += NP == 1 ? (long long)cnt[p][i]
+                         : (p == NP - 1 ? -((long long)cnt[p][i] << p) : ((long long)cnt[p][i] << p));
+        out[i] = s;
+    }
+}
+
+// One query per thread.  Shared memory: the chunk's query words [WCH][TPB+1],
 // the chunk's class planes [planes][C][WCH], and the per-(config, class)
 // partial sums [nb*ns*C][TPB] (int64).
 __global__ void sweep_eval_kernel(const uint32_t *__restrict__ H, const int32_t *__restrict__ y, int64_t N, int C,
@@ -152,16 +187,19 @@ __global__ void sweep_eval_kernel(const uint32_t *__restrict__ H, const int32_t 
             const int b = cf.bits[jb], np = cf.planes[jb], p0 = cf.plane_off[jb];
             for (int c = 0; c < C; c++) {
                 long long part[MAXS];
+                const uint32_t *spc = sp + ((size_t)p0 * C + c) * WCH;
+                if (np == 1) {
+                    chunk_counts<1>(sq, QLD, tid, spc, C * WCH, nw, cf, part);
+                } else if (np == 4) {
+                    chunk_counts<4>(sq, QLD, tid, spc, C * WCH, nw, cf, part);
+                } else if (np == 8) {
+                    chunk_counts<8>(sq, QLD, tid, spc, C * WCH, nw, cf, part);
+                } else {  // unquantised accumulators: 32 planes, int64 weights
 #pragma unroll
                 for (int i = 0; i < MAXS; i++) part[i] = 0;
                 for (int j = 0; j < nw; j++) {
                     const uint32_t qw = sq[(size_t)j * QLD + tid];
-                    if (b == 1) {
-                        const uint32_t x = qw ^ sp[((size_t)p0 * C + c) * WCH + j];
-#pragma unroll
-                        for (int i = 0; i < MAXS; i++)
-                            if (i < cf.ns) part[i] += __popc(x & cf.mask[i]);
-                    } else {
+                    {
                         for (int p = 0; p < np; p++) {
                             const uint32_t x = qw & sp[((size_t)(p0 + p) * C + c) * WCH + j];
                             const long long wp = p == np - 1 ? -(1ll << p) : (1ll << p);
@@ -170,6 +208,7 @@ __global__ void sweep_eval_kernel(const uint32_t *__restrict__ H, const int32_t 
                                 if (i < cf.ns) part[i] += wp * __popc(x & cf.mask[i]);
                         }
                     }
+                }
                 }
 #pragma unroll
                 for (int i = 0; i < MAXS; i++)
