@@ -193,6 +193,19 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m,
                         int32_t *labels, int32_t *dists, double *scores,
                         void *ws, size_t ws_bytes, hdc_stream_t stream);
 
+/* hdc_classify for query rows in HOST memory: the n_parts row blocks
+ * parts_host[i] (part_rows[i] x m->F FP32 each, contiguous; page-locked for
+ * the copies to overlap other work) are copied in order into X_dev (device,
+ * sum(part_rows) x F FP32), classified with workspace ws as hdc_classify
+ * does, and the labels (device labels_dev, sum(part_rows) int32) are copied
+ * back to labels_host.  Everything is enqueued on `stream`; host buffers
+ * must stay valid and unmodified until the stream reaches this point.
+ * Used by the serving loop (one call per batch) and for end-to-end timing. */
+hdc_status hdc_classify_host(const float *const *parts_host, const int64_t *part_rows,
+                             int32_t n_parts, const hdc_model *m, float *X_dev,
+                             int32_t *labels_dev, int32_t *labels_host, void *ws,
+                             size_t ws_bytes, hdc_stream_t stream);
+
 /* Batched evaluation of approximation configurations.  The paper's tuner
  * (Sec. 3, Fig. 1) compiles and runs the application once per candidate
  * configuration and reads back its QoS (accuracy).  Here every combination

@@ -58,6 +58,7 @@ _SIGS = {
     "hdc_train_epoch": (_I32, [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
     "hdc_classify": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _SZ, _P]),
     "hdc_classify_static": (_I32, [_P, _I64, _P, _P, _P, _P, _P]),
+    "hdc_classify_host": (_I32, [_P, _P, _I32, _P, _P, _P, _P, _P, _SZ, _P]),
     "hdc_sweep_workspace_bytes": (_I32, [_I32, _I32, _P, _P]),
     "hdc_sweep_eval": (_I32, [_P, _P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _SZ, _P]),
     "hdc_stream_status": (_I32, [_P]),
@@ -282,6 +283,21 @@ def classify_static(X: torch.Tensor, model: Model, sims: bool = False, labels: t
     if sims:
         return labels, (dd if dd is not None else sc)
     return labels
+
+
+def classify_host(parts, model: Model, X_dev: torch.Tensor, labels_dev: torch.Tensor,
+                  labels_host: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
+    """hdc_classify_host: copy the host row blocks `parts` (CPU tensors,
+    pinned for overlap) into X_dev, classify, copy labels to labels_host
+    (CPU int32).  Asynchronous on the stream."""
+    n = len(parts)
+    ptrs = (ctypes.c_void_p * max(n, 1))(*[p.data_ptr() for p in parts])
+    rows = (ctypes.c_int64 * max(n, 1))(*[p.shape[0] for p in parts])
+    for p in parts:
+        assert not p.is_cuda and p.dtype == torch.float32 and p.is_contiguous() and p.shape[1] == model.m.F
+    assert not labels_host.is_cuda and labels_host.dtype == torch.int32
+    _call("hdc_classify_host", ptrs, rows, n, ctypes.byref(model.m), _ptr(X_dev), _ptr(labels_dev),
+          ctypes.c_void_p(labels_host.data_ptr()), _ptr(ws), ws.numel(), _stream(stream))
 
 
 class SweepSpecC(ctypes.Structure):

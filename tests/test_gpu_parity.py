@@ -291,3 +291,23 @@ def test_tc_persistent_many_tiles_matches_simt(hdc, enc):
     assert np.array_equal(words_np(h_tc)[sub], pack(bits, words_for(D)))
     torch.cuda.synchronize()
     assert hdc.stream_status() == 0
+
+
+@pytest.mark.parametrize("enc", ["fp32", "fp8"])
+def test_classify_host_blocks_equal_classify(hdc, enc):
+    """hdc_classify_host: host row blocks copied in order, classified, labels
+    copied back -- equal to hdc_classify on the concatenated rows."""
+    from paper_2606_26547_gb300 import synth
+    d = synth.make("precision_F784_D10000_C10", n_train=200, n_query=700, D=900)
+    acc = np.random.default_rng(2).integers(-50, 50, (10, 900)).astype(np.int32)
+    model = hdc.Model(T(d["Bt"]), hdc.ApproxConfig(enc=enc, perf_stride=3), acc=T(acc))
+    Xh = torch.from_numpy(d["Xq"]).pin_memory()
+    cuts = [0, 1, 1, 250, 699, 700]                      # includes an empty block
+    parts = [Xh[cuts[i]:cuts[i + 1]] for i in range(len(cuts) - 1)]
+    Xd = torch.empty((700, 784), device=dev())
+    Ld = torch.empty(700, dtype=torch.int32, device=dev())
+    Lh = torch.full((700,), -1, dtype=torch.int32).pin_memory()
+    hdc.classify_host(parts, model, Xd, Ld, Lh, model.workspace(700))
+    torch.cuda.synchronize()
+    ref = hdc.classify(T(d["Xq"]), model).cpu()
+    assert torch.equal(Lh, ref)
