@@ -180,6 +180,7 @@ def run_ours(a):
     import torch.distributed as dist
 
     from paper_2606_26547_gb300 import build, hdc, synth
+    from paper_2606_26547_gb300 import dist as hdist
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -245,11 +246,8 @@ def run_ours(a):
     clocks = clk.stop()
     assert hdc.stream_status() == 0
     kern_s = [s.elapsed_time(e) / 1e3 for s, e in evs]
-    if world > 1:
-        t = torch.tensor([el], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
-    value = world * B * a.steps / el
+    el = hdist.max_over_ranks(el, device=dev)
+    value = hdist.job_throughput(B, a.steps, world, el)
 
     # exact form on the same GPU
     ws_ex = m_ex.workspace(B)
