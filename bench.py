@@ -158,7 +158,40 @@ def train_model(hdc, torch, data, dev, epochs):
     H = hdc.encode(Xtr, base)
     acc, cls, ups = hdc.train(H, ytr, Bt.shape[0], int(data["ytr"].max()) + 1, epochs)
     torch.cuda.synchronize()
-    return Bt, acc, ups, time.perf_counter() - t
+    return Bt, acc, ups, time.perf_counter() - t, H, ytr
+
+
+def time_training(hdc, torch, H, y, D, C, reps=5):
+    """Device time of one bundling pass and one retraining epoch over the
+    packed training hypervectors H, with HBM throughput against algorithmic
+    bytes (bundling reads N*W*4; an epoch reads them for the prediction and
+    the misclassified rows twice more for the update)."""
+    N, W = H.shape
+    acc = torch.empty((C, D), dtype=torch.int32, device=H.device)
+    cls = torch.empty((C, W), dtype=torch.int32, device=H.device)
+    nu = torch.zeros(1, dtype=torch.int32, device=H.device)
+    n = __import__("ctypes").c_size_t()
+    hdc._call("hdc_train_workspace_bytes", N, D, C, __import__("ctypes").byref(n))
+    ws = hdc._empty_bytes(n.value, H.device)
+    out = {}
+    for name, mode in (("bundle", 0), ("retrain_epoch", 1)):
+        hdc.train_epoch(H, y, D, C, 0, acc, cls, ws=ws)      # start from the bundle
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(reps):
+            if mode == 1:
+                hdc.train_epoch(H, y, D, C, 0, acc, cls, ws=ws)
+            a.record()
+            hdc.train_epoch(H, y, D, C, mode, acc, cls, n_updates=nu, ws=ws)
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        t = sorted(ts)[len(ts) // 2]
+        upd = int(nu.item()) if mode == 1 else 0
+        nbytes = N * W * 4 + 2 * upd * W * 4
+        out[name] = {"ms": t * 1e3, "algorithmic_bytes": nbytes, "gbs": nbytes / t / 1e9,
+                     "updates": upd}
+    return out
 
 
 def timed_steps(torch, fn, steps, stream):
@@ -193,7 +226,9 @@ def run_ours(a):
     hdc.load()
     w = synth.WORKLOADS[WORKLOAD]
     data = synth.make(WORKLOAD)
-    Bt, acc, ups, train_s = train_model(hdc, torch, data, dev, w.epochs)
+    Bt, acc, ups, train_s, Htr, ytr = train_model(hdc, torch, data, dev, w.epochs)
+    train_passes = time_training(hdc, torch, Htr, ytr, w.D, w.C)
+    del Htr
 
     approx_cfg = hdc.ApproxConfig(enc=a.enc, perf_stride=a.stride)
     exact_cfg = hdc.ApproxConfig(enc="fp32")
@@ -325,6 +360,7 @@ def run_ours(a):
         "accuracy": {"exact": acc_ex, "approx": acc_apx, "loss_pts": 100.0 * (acc_ex - acc_apx),
                      "label_agreement": float((lab_ex == lab_apx).mean()), "queries": int(yq.size)},
         "train_s": train_s, "train_updates": ups,
+        "train_passes": dict(train_passes, hbm_peak_gbs=pk.get("hbm_gbs")),
     }
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         import oracle

@@ -251,10 +251,30 @@ hdc_status hdc_hamming_argmin(const uint32_t *Q, const uint32_t *Cls, int64_t N,
                                 labels, dists, nullptr, (cudaStream_t)stream));
 }
 
+namespace {
+// Training workspace: predictions, the class-grouped sample order, and the
+// counting-sort histogram / offsets / cursors.
+struct TrainLayout {
+    size_t pred, perm, hist, offsets, cursor, total;
+};
+TrainLayout train_layout(int64_t N, int C)
+{
+    TrainLayout L;
+    size_t off = 0;
+    L.pred = off;    off = align_up(off + (size_t)N * 4, kAlign);
+    L.perm = off;    off = align_up(off + (size_t)N * 4, kAlign);
+    L.hist = off;    off = align_up(off + (size_t)C * 4, kAlign);
+    L.offsets = off; off = align_up(off + (size_t)(C + 1) * 4, kAlign);
+    L.cursor = off;  off = align_up(off + (size_t)C * 4, kAlign);
+    L.total = off;
+    return L;
+}
+}  // namespace
+
 hdc_status hdc_train_workspace_bytes(int64_t N, int32_t D, int32_t C, size_t *bytes)
 {
     if (!bytes || N < 0 || D <= 0 || C <= 0) return HDC_ERR_INVALID_ARG;
-    *bytes = align_up((size_t)N * 4, kAlign);
+    *bytes = train_layout(N, C).total;
     return HDC_OK;
 }
 
@@ -267,9 +287,11 @@ hdc_status hdc_train_epoch(const uint32_t *H, const int32_t *y, int64_t N, int32
     if (N > 0 && (!H || !y || !aligned(H, 16))) return HDC_ERR_INVALID_ARG;
     const int W = words_for(D);
     cudaStream_t st = (cudaStream_t)stream;
-    if (mode == 1 && N > 0) {
-        if (!ws || ws_bytes < (size_t)N * 4) return HDC_ERR_WORKSPACE;
-    }
+    const TrainLayout L = train_layout(N, C);
+    if (N > 0 && (!ws || ws_bytes < L.total || !aligned(ws, kAlign))) return HDC_ERR_WORKSPACE;
+    char *w = (char *)ws;
+    TrainScratch sc = {(int32_t *)(w + L.perm), (int32_t *)(w + L.hist), (int32_t *)(w + L.offsets),
+                       (int32_t *)(w + L.cursor)};
     if (n_updates) {
         hdc_status s = cu(cudaMemsetAsync(n_updates, 0, sizeof(int32_t), st));
         if (s != HDC_OK) return s;
@@ -277,14 +299,14 @@ hdc_status hdc_train_epoch(const uint32_t *H, const int32_t *y, int64_t N, int32
     if (mode == 0) {
         hdc_status s = cu(cudaMemsetAsync(acc, 0, (size_t)C * D * sizeof(int32_t), st));
         if (s != HDC_OK) return s;
-        s = cu(launch_train_count(H, W, y, nullptr, N, D, C, 0, acc, nullptr, st));
+        s = cu(launch_train_count(H, W, y, nullptr, N, D, C, 0, acc, nullptr, sc, st));
         if (s != HDC_OK) return s;
     } else if (N > 0) {
-        int32_t *pred = (int32_t *)ws;
+        int32_t *pred = (int32_t *)(w + L.pred);
         hdc_status s = cu(launch_similarity(H, N, cls, C, W, 1, D, nullptr, nullptr, nullptr, pred, nullptr, nullptr,
                                             st));
         if (s != HDC_OK) return s;
-        s = cu(launch_train_count(H, W, y, pred, N, D, C, 1, acc, n_updates, st));
+        s = cu(launch_train_count(H, W, y, pred, N, D, C, 1, acc, n_updates, sc, st));
         if (s != HDC_OK) return s;
     }
     return cu(launch_binarise(acc, C, D, cls, W, st));

@@ -68,10 +68,14 @@ cudaError_t launch_similarity(const uint32_t *Q, int64_t N, const uint32_t *plan
 // K5: signed bit counts of the training rows into acc (C x D int32).
 //  mode 0: row n adds (1-2 bit) to class y_n.
 //  mode 1: rows with pred_n != y_n add to y_n and subtract from pred_n,
-//          and n_updates (if not NULL) counts them.
+//          and n_updates (if not NULL, zeroed by the caller) counts them.
+// Scratch: perm (N int32), hist / cursor (C int32), offsets (C+1 int32).
+struct TrainScratch {
+    int32_t *perm, *hist, *offsets, *cursor;
+};
 cudaError_t launch_train_count(const uint32_t *H, int W, const int32_t *y, const int32_t *pred,
                                int64_t N, int D, int C, int mode, int32_t *acc, int32_t *n_updates,
-                               cudaStream_t st);
+                               const TrainScratch &s, cudaStream_t st);
 
 // K6 (binary): cls[c] = pack(acc[c] < 0) over D dims, W words per row.
 cudaError_t launch_binarise(const int32_t *acc, int C, int D, uint32_t *cls, int W, cudaStream_t st);

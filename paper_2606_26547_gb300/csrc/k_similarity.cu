@@ -110,6 +110,83 @@ __global__ void __launch_bounds__(TPB) similarity_kernel(const uint32_t *__restr
     }
 }
 
+// Hamming arg-min for C <= CMAX with the distances in registers.  A block
+// stages 128 queries x RWCH words coalesced into shared memory, transposed
+// ([word][query], padded), with the chunk's class words and masks; every
+// class word is then a broadcast read.
+constexpr int RWCH = 32;
+
+template <int CMAX>
+__global__ void __launch_bounds__(TPB) hamming_reg_kernel(const uint32_t *__restrict__ Q, int64_t N,
+                                                          const uint32_t *__restrict__ cls, int C, int W,
+                                                          int use_mask, int64_t s0, int64_t e0, int64_t stride,
+                                                          int32_t *__restrict__ labels, int32_t *__restrict__ dists)
+{
+    __shared__ uint32_t sq[RWCH][TPB + 1];
+    __shared__ uint32_t sc[CMAX][RWCH];
+    __shared__ uint32_t mk[RWCH];
+    const int tid = threadIdx.x;
+    const int64_t row0 = (int64_t)blockIdx.x * TPB;
+    int dist[CMAX];
+#pragma unroll
+    for (int c = 0; c < CMAX; c++) dist[c] = 0;
+    for (int w0 = 0; w0 < W; w0 += RWCH) {
+        const int nw = min(RWCH, W - w0);
+        __syncthreads();
+        for (int i = tid; i < TPB * RWCH; i += TPB) {  // consecutive threads: consecutive words of a row
+            const int r = i / RWCH, j = i % RWCH;
+            sq[j][r] = (row0 + r < N && j < nw) ? __ldg(Q + (row0 + r) * W + w0 + j) : 0u;
+        }
+        for (int i = tid; i < CMAX * RWCH; i += TPB) {
+            const int c = i / RWCH, j = i % RWCH;
+            sc[c][j] = (c < C && j < nw) ? __ldg(cls + (int64_t)c * W + w0 + j) : 0u;
+        }
+        if (tid < RWCH) {
+            uint32_t m = tid < nw ? 0xffffffffu : 0u;
+            if (use_mask && tid < nw) {  // kept dims s0, s0+stride, ... < e0 inside this word
+                m = 0;
+                const int64_t base = (int64_t)(w0 + tid) * 32;
+                const int64_t lo = max(s0, base), hi = min(e0, base + 32);
+                if (lo < hi) {
+                    const int64_t r = (lo - s0) % stride;
+                    for (int64_t d = r ? lo + (stride - r) : lo; d < hi; d += stride) m |= 1u << (d - base);
+                }
+            }
+            mk[tid] = m;
+        }
+        __syncthreads();
+        for (int j = 0; j < nw; j++) {
+            const uint32_t m = mk[j];
+            const uint32_t q = sq[j][tid] & m;
+#pragma unroll
+            for (int c = 0; c < CMAX; c++)
+                if (c < C) dist[c] += __popc(q ^ (sc[c][j] & m));
+        }
+    }
+    const int64_t row = row0 + tid;
+    if (row >= N) return;
+    int best = 0, bv = dist[0];
+#pragma unroll
+    for (int c = 0; c < CMAX; c++)
+        if (c < C) {
+            if (dists) dists[row * C + c] = dist[c];
+            if (dist[c] < bv) { bv = dist[c]; best = c; }
+        }
+    labels[row] = best;
+}
+
+template <int CMAX>
+cudaError_t launch_reg(const uint32_t *Q, int64_t N, const uint32_t *cls, int C, int W, int64_t D, const Perf *p,
+                       int32_t *labels, int32_t *dists, cudaStream_t st)
+{
+    const int use_mask = p != nullptr;
+    const int64_t s0 = p ? p->s0 : 0, e0 = p ? p->e0 : D, stride = p ? p->stride : 1;
+    const int64_t blocks = (N + TPB - 1) / TPB;
+    hamming_reg_kernel<CMAX><<<(unsigned)blocks, TPB, 0, st>>>(Q, N, cls, C, W, use_mask, s0, e0, stride, labels,
+                                                               dists);
+    return cudaGetLastError();
+}
+
 template <int NB>
 cudaError_t launch_nb(const uint32_t *Q, int64_t N, const uint32_t *planes, int C, int W, int64_t D, const Perf *p,
                       const int32_t *csum, const double *cnorm, int32_t *labels, int32_t *dists, double *scores,
@@ -139,6 +216,9 @@ cudaError_t launch_similarity(const uint32_t *Q, int64_t N, const uint32_t *plan
                               int32_t *dists, double *scores, cudaStream_t st)
 {
     if (N <= 0) return cudaSuccess;
+    if (nb == 1 && C <= 16) return launch_reg<16>(Q, N, planes, C, W, D, p, labels, dists, st);
+    if (nb == 1 && C <= 32) return launch_reg<32>(Q, N, planes, C, W, D, p, labels, dists, st);
+    if (nb == 1 && C <= 64) return launch_reg<64>(Q, N, planes, C, W, D, p, labels, dists, st);
     switch (nb) {
     case 1: return launch_nb<1>(Q, N, planes, C, W, D, p, csum, cnorm, labels, dists, scores, st);
     case 4: return launch_nb<4>(Q, N, planes, C, W, D, nullptr, csum, cnorm, labels, dists, scores, st);
