@@ -20,7 +20,7 @@
 namespace hdc {
 namespace {
 
-constexpr int CH = 2048;  // samples per counting work item
+constexpr int CH = 252;  // samples per counting work item (byte-lane counters hold <= 255)
 
 // key of sample n: bundling -> y_n; retraining -> y_n (which == 0) or
 // pred_n (which == 1) for misclassified samples only; -1 = not counted.
@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(128) segment_count_kernel(const uint32_t *__re
                                                             int32_t *__restrict__ acc)
 {
     __shared__ int32_t s_off[257];
+    __shared__ int32_t s_rows[CH];
     const bool small = C <= 256;
     if (small)
         for (int c = threadIdx.x; c <= C; c += blockDim.x) s_off[c] = offsets[c];
@@ -93,31 +94,37 @@ __global__ void __launch_bounds__(128) segment_count_kernel(const uint32_t *__re
     for (int c = 0; c < C; c++) {
         const int lo = off(c), hi = off(c + 1);
         for (int r0 = lo; r0 < hi; r0 += CH, item++) {
-            if (item % gridDim.y != blockIdx.y) continue;
-            if (word >= W) continue;
+            if (item % gridDim.y != blockIdx.y) continue;  // uniform across the block
             const int r1 = min(hi, r0 + CH);
+            __syncthreads();
+            for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) s_rows[r - r0] = __ldg(perm + r);
+            __syncthreads();
+            if (word >= W) continue;
+            // CH <= 255: the byte lanes cannot overflow within one item
             uint32_t lanes[8];
-            int cnt[32];
 #pragma unroll
             for (int j = 0; j < 8; j++) lanes[j] = 0;
-#pragma unroll
-            for (int j = 0; j < 32; j++) cnt[j] = 0;
-            int pending = 0;
-            for (int r = r0; r < r1; r++) {
-                const uint32_t w = __ldg(H + (int64_t)__ldg(perm + r) * W + word);
-#pragma unroll
-                for (int j = 0; j < 8; j++) lanes[j] += (w >> j) & 0x01010101u;  // dims j, j+8, j+16, j+24
-                if (++pending == 255 || r + 1 == r1) {
-#pragma unroll
-                    for (int j = 0; j < 8; j++) {
-#pragma unroll
-                        for (int k = 0; k < 4; k++) cnt[j + 8 * k] += (lanes[j] >> (8 * k)) & 0xffu;
-                        lanes[j] = 0;
-                    }
-                    pending = 0;
-                }
-            }
             const int n = r1 - r0;
+            int r = 0;
+            for (; r + 4 <= n; r += 4) {  // four independent row loads in flight
+                uint32_t w[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) w[u] = __ldg(H + (int64_t)s_rows[r + u] * W + word);
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+#pragma unroll
+                    for (int j = 0; j < 8; j++) lanes[j] += (w[u] >> j) & 0x01010101u;  // dims j, j+8, j+16, j+24
+            }
+            for (; r < n; r++) {
+                const uint32_t w = __ldg(H + (int64_t)s_rows[r] * W + word);
+#pragma unroll
+                for (int j = 0; j < 8; j++) lanes[j] += (w >> j) & 0x01010101u;
+            }
+            int cnt[32];
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+#pragma unroll
+                for (int k = 0; k < 4; k++) cnt[j + 8 * k] = (lanes[j] >> (8 * k)) & 0xffu;
 #pragma unroll
             for (int b = 0; b < 32; b++) {
                 const int d = word * 32 + b;
