@@ -45,10 +45,11 @@ constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BKB;            // 16 KB
 constexpr int B_BYTES = BN * BKB;            // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int NUM_THREADS = 192;
+// threads: 4*EWG epilogue warps (EWG = 1 or 2 warpgroups), a TMA warp, an MMA warp
+__host__ __device__ constexpr int num_threads(int ewg) { return (4 * ewg + 2) * 32; }
 constexpr int TMEM_COLS = 2 * BN;            // two accumulators
-constexpr int NUM_BARS = 2 * STAGES + 5;     // full, empty, tfull[2], tempty[2], done
-constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + NUM_BARS * 8 + 16;
+constexpr int NUM_BARS = 2 * STAGES + 7;     // full, empty, tfull[2], tempty[2], done, merge_full, merge_empty
+constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + NUM_BARS * 8 + 16 + 2 * BM * 4;
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
 
 struct Params {
@@ -206,8 +207,13 @@ __device__ __forceinline__ uint32_t pack_signs(const uint32_t (&r)[32])
 }
 
 // ------------------------------------------------------------------ kernel
-template <int ENC, int CMAX, bool CLASSIFY>
-__global__ void __launch_bounds__(NUM_THREADS, 1)
+// EWG = 2 (classify only): two epilogue warpgroups read the same TMEM lanes
+// and pack the same words; warpgroup g counts classes [g*CMAX, (g+1)*CMAX),
+// and warpgroup 1 hands its per-row minimum to warpgroup 0 through shared
+// memory (an mbarrier pair with bounded waits), which keeps the lower class
+// index on ties.
+template <int ENC, int CMAX, bool CLASSIFY, int EWG>
+__global__ void __launch_bounds__(num_threads(EWG), 1)
     tc_encode_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -222,6 +228,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     auto tfull = [&](int a) { return su32(bars + 2 * STAGES + a); };
     auto tempty = [&](int a) { return su32(bars + 2 * STAGES + 2 + a); };
     const uint32_t done_bar = su32(bars + 2 * STAGES + 4);
+    const uint32_t merge_full = su32(bars + 2 * STAGES + 5), merge_empty = su32(bars + 2 * STAGES + 6);
+    int32_t *s_val = reinterpret_cast<int32_t *>(tmem_slot + 4);  // warpgroup 1's per-row minimum
+    int32_t *s_idx = s_val + BM;                                    // and its class
+    constexpr int PRODUCER = 4 * EWG, ISSUER = 4 * EWG + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t num_m_tiles = (p.N + BM - 1) / BM;
@@ -235,9 +245,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         for (int a = 0; a < 2; a++) {
             mbar_init(tfull(a), 1);
-            mbar_init(tempty(a), BM);
+            mbar_init(tempty(a), BM * EWG);
         }
         mbar_init(done_bar, 1);
+        mbar_init(merge_full, BM);
+        mbar_init(merge_empty, BM);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -252,7 +264,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 4) {
+    if (warp == PRODUCER) {
         if (lane == 0) {  // ---------------------------------- TMA producer
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
@@ -280,7 +292,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         while (!mbar_try(full(s), ipar[s]) && gtimer() - t0 < 100000000ull) {}
                     }
         }
-    } else if (warp == 5) {
+    } else if (warp == ISSUER) {
         if (lane == 0) {  // ---------------------------------- MMA issuer
             const uint32_t id = idesc<ENC>();
             int stage = 0, acc = 0;
@@ -310,12 +322,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const unsigned long long t0 = gtimer();
             while (!mbar_try(done_bar, 0) && gtimer() - t0 < 100000000ull) {}
         }
-    } else {  // --------------------------------------------- epilogue warps 0-3
-        const int q = warp;  // TMEM lane quarter of this warp
+    } else {  // ------------------------------------ epilogue warps 0 .. 4*EWG-1
+        const int q = warp & 3;             // TMEM lane quarter of this warp
+        const int g = warp >> 2;            // epilogue warpgroup
+        const int c0 = g * CMAX;            // first class this warpgroup counts
         int acc = 0;
         uint32_t aphase = 0;
         bool ab = false;
-        for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
+        int64_t it = 0;
+        for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++) {
             const int64_t row = mt * BM + q * 32 + lane;
             const bool valid = row < p.N;
             int dist[CLASSIFY ? CMAX : 1];
@@ -353,8 +368,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     const bool hi = gw0 + 8 <= p.W;
 #pragma unroll
                     for (int c = 0; c < CMAX; c++)
-                        if (c < p.C) {
-                            const uint4 *cw = reinterpret_cast<const uint4 *>(p.planes + (int64_t)c * p.W + gw0);
+                        if (c0 + c < p.C) {
+                            const uint4 *cw = reinterpret_cast<const uint4 *>(p.planes + (int64_t)(c0 + c) * p.W + gw0);
                             const uint4 c0 = __ldg(cw);
                             const uint4 c1 = hi ? __ldg(cw + 1) : make_uint4(0u, 0u, 0u, 0u);
                             dist[c] += __popc(words[0] ^ c0.x) + __popc(words[1] ^ c0.y) + __popc(words[2] ^ c0.z) +
@@ -367,15 +382,30 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     if (gw0 + 8 <= p.W) *reinterpret_cast<uint4 *>(h + 4) = make_uint4(words[4], words[5], words[6], words[7]);
                 }
             }
-            if (CLASSIFY && valid && !ab) {  // arg-min, lowest index on ties
-                int best = 0, bv = dist[0];
+            if (CLASSIFY && !ab) {  // arg-min over this warpgroup's classes, lowest index on ties
+                int best = c0, bv = 0x7fffffff;
 #pragma unroll
                 for (int c = 0; c < CMAX; c++)
-                    if (c < p.C) {
-                        if (p.dists) p.dists[row * p.C + c] = dist[c];
-                        if (dist[c] < bv) { bv = dist[c]; best = c; }
+                    if (c0 + c < p.C) {
+                        if (p.dists && valid) p.dists[row * p.C + c0 + c] = dist[c];
+                        if (dist[c] < bv) { bv = dist[c]; best = c0 + c; }
                     }
-                p.labels[row] = best;
+                const int r = q * 32 + lane;
+                if (EWG == 2) {
+                    const uint32_t par = (uint32_t)(it & 1);
+                    if (g == 1) {
+                        if (!mbar_wait(merge_empty, par ^ 1, abort_flag)) { ab = true; break; }
+                        s_val[r] = bv;
+                        s_idx[r] = best;
+                        mbar_arrive(merge_full);
+                    } else {
+                        if (!mbar_wait(merge_full, par, abort_flag)) { ab = true; break; }
+                        const int v1 = s_val[r], i1 = s_idx[r];
+                        mbar_arrive(merge_empty);
+                        if (v1 < bv) { bv = v1; best = i1; }  // ties keep the lower class range
+                    }
+                }
+                if (g == 0 && valid) p.labels[row] = best;
             }
         }
     }
@@ -389,14 +419,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 }
 
 // Launch helpers, instantiated by each encoding's translation unit.
-template <int ENC, int CMAX, bool CLASSIFY>
+template <int ENC, int CMAX, bool CLASSIFY, int EWG>
 static cudaError_t launch_one(const CUtensorMap &ma, const CUtensorMap &mb, const Params &p, unsigned grid,
                               cudaStream_t st)
 {
-    auto k = tc_encode_kernel<ENC, CMAX, CLASSIFY>;
+    auto k = tc_encode_kernel<ENC, CMAX, CLASSIFY, EWG>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    k<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(ma, mb, p);
+    k<<<grid, num_threads(EWG), SMEM_BYTES, st>>>(ma, mb, p);
     return cudaGetLastError();
 }
 
@@ -404,11 +434,12 @@ template <int ENC>
 static cudaError_t launch_enc(const CUtensorMap &ma, const CUtensorMap &mb, const Params &p, unsigned grid,
                               bool classify, cudaStream_t st)
 {
-    if (!classify) return launch_one<ENC, 1, false>(ma, mb, p, grid, st);
-    if (p.C <= 16) return launch_one<ENC, 16, true>(ma, mb, p, grid, st);
-    if (p.C <= 32) return launch_one<ENC, 32, true>(ma, mb, p, grid, st);
-    if (p.C <= 64) return launch_one<ENC, 64, true>(ma, mb, p, grid, st);
-    return launch_one<ENC, 128, true>(ma, mb, p, grid, st);
+    if (!classify) return launch_one<ENC, 1, false, 1>(ma, mb, p, grid, st);
+    // up to 16 classes: one epilogue warpgroup; more: two, each counting half
+    if (p.C <= 16) return launch_one<ENC, 16, true, 1>(ma, mb, p, grid, st);
+    if (p.C <= 32) return launch_one<ENC, 16, true, 2>(ma, mb, p, grid, st);
+    if (p.C <= 64) return launch_one<ENC, 32, true, 2>(ma, mb, p, grid, st);
+    return launch_one<ENC, 64, true, 2>(ma, mb, p, grid, st);
 }
 
 // Read and clear this translation unit's device status word.
