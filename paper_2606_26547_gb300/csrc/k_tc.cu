@@ -44,6 +44,22 @@ bool make_map(CUtensorMap *m, const void *base, int enc, int F, int ld, int64_t 
     return r == CUDA_SUCCESS;
 }
 
+// Map over the binary class words (C rows x W uint32): box = 8 words (one
+// 256-dim tile) x C rows, no swizzle, zeros past W.
+bool make_cls_map(CUtensorMap *m, const uint32_t *planes, int W, int C)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)C};
+    cuuint64_t strides[1] = {(cuuint64_t)W * 4};
+    cuuint32_t box[2] = {8, (cuuint32_t)C};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t *>(planes), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 int sm_count()
 {
     int dev = 0, n = 0;
@@ -93,8 +109,10 @@ cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st)
     if (sms <= 0) return cudaErrorNoDevice;
     const unsigned grid = (unsigned)(m_tiles < sms ? m_tiles : sms);
     const bool classify = a.planes != nullptr;
-    if (a.enc == HDC_ENC_BF16) return tc::launch_bf16(ma, mb, p, grid, classify, st);
-    return tc::launch_fp8(ma, mb, p, grid, classify, st);
+    CUtensorMap mc = mb;  // unused by encode-only launches
+    if (classify && !make_cls_map(&mc, a.planes, a.W, a.C)) return cudaErrorInvalidValue;
+    if (a.enc == HDC_ENC_BF16) return tc::launch_bf16(ma, mb, mc, p, grid, classify, st);
+    return tc::launch_fp8(ma, mb, mc, p, grid, classify, st);
 }
 
 cudaError_t tc_read_status(cudaStream_t st, int *status)

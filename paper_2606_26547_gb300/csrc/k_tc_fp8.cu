@@ -4,10 +4,11 @@
 namespace hdc {
 namespace tc {
 
-cudaError_t launch_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const Params &p, unsigned grid, bool classify,
+cudaError_t launch_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const Params &p,
+                        unsigned grid, bool classify,
                        cudaStream_t st)
 {
-    return launch_enc<HDC_ENC_FP8_E4M3>(ma, mb, p, grid, classify, st);
+    return launch_enc<HDC_ENC_FP8_E4M3>(ma, mb, mc, p, grid, classify, st);
 }
 
 cudaError_t status_fp8(cudaStream_t st, int *status) { return read_status(st, status); }

@@ -48,8 +48,11 @@ constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 // threads: 4*EWG epilogue warps (EWG = 1 or 2 warpgroups), a TMA warp, an MMA warp
 __host__ __device__ constexpr int num_threads(int ewg) { return (4 * ewg + 2) * 32; }
 constexpr int TMEM_COLS = 2 * BN;            // two accumulators
-constexpr int NUM_BARS = 2 * STAGES + 7;     // full, empty, tfull[2], tempty[2], done, merge_full, merge_empty
-constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + NUM_BARS * 8 + 16 + 2 * BM * 4;
+// class-word ring (classify): the 8 words of every class for one 256-dim tile
+constexpr int CBUF = 4, CLS_BYTES = 128 * 32;
+// full, empty, tfull[2], tempty[2], done, merge_full, merge_empty, cfull[CBUF], cempty[CBUF]
+constexpr int NUM_BARS = 2 * STAGES + 7 + 2 * CBUF;
+constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + CBUF * CLS_BYTES + NUM_BARS * 8 + 16 + 2 * BM * 4;
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
 
 struct Params {
@@ -214,13 +217,15 @@ __device__ __forceinline__ uint32_t pack_signs(const uint32_t (&r)[32])
 // index on ties.
 template <int ENC, int CMAX, bool CLASSIFY, int EWG>
 __global__ void __launch_bounds__(num_threads(EWG), 1)
-    tc_encode_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Params p)
+    tc_encode_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ CUtensorMap tmC, const Params p)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;
     uint8_t *sB = smem + STAGES * A_BYTES;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint8_t *sCls = smem + STAGES * STAGE_BYTES;  // CBUF x [128 classes][8 words]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sCls + CBUF * CLS_BYTES);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + NUM_BARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     auto full = [&](int s) { return su32(bars + s); };
@@ -229,6 +234,8 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
     auto tempty = [&](int a) { return su32(bars + 2 * STAGES + 2 + a); };
     const uint32_t done_bar = su32(bars + 2 * STAGES + 4);
     const uint32_t merge_full = su32(bars + 2 * STAGES + 5), merge_empty = su32(bars + 2 * STAGES + 6);
+    auto cfull = [&](int b) { return su32(bars + 2 * STAGES + 7 + b); };
+    auto cempty = [&](int b) { return su32(bars + 2 * STAGES + 7 + CBUF + b); };
     int32_t *s_val = reinterpret_cast<int32_t *>(tmem_slot + 4);  // warpgroup 1's per-row minimum
     int32_t *s_idx = s_val + BM;                                    // and its class
     constexpr int PRODUCER = 4 * EWG, ISSUER = 4 * EWG + 1;
@@ -250,6 +257,10 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
         mbar_init(done_bar, 1);
         mbar_init(merge_full, BM);
         mbar_init(merge_empty, BM);
+        for (int b = 0; b < CBUF; b++) {
+            mbar_init(cfull(b), 1);
+            mbar_init(cempty(b), BM * EWG);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -268,14 +279,24 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
         if (lane == 0) {  // ---------------------------------- TMA producer
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-            int stage = 0;
-            uint32_t phase = 0;
+            if (CLASSIFY) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmC)) : "memory");
+            int stage = 0, cb = 0;
+            uint32_t phase = 0, cph = 0;
             bool issued[STAGES];
             uint32_t ipar[STAGES];
             for (int s = 0; s < STAGES; s++) { issued[s] = false; ipar[s] = 0; }
+            uint32_t c_issued = 0, c_par = 0;
             bool ab = false;
             for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
-                for (int nt = 0; nt < num_n_tiles && !ab; nt++)
+                for (int nt = 0; nt < num_n_tiles && !ab; nt++) {
+                    if (CLASSIFY) {  // this dim tile's class words: C rows x 8 words (zeros past W)
+                        if (!mbar_wait(cempty(cb), cph ^ 1, abort_flag)) { ab = true; break; }
+                        mbar_expect_tx(cfull(cb), (uint32_t)p.C * 32u);
+                        tma_load_2d(su32(sCls + cb * CLS_BYTES), &tmC, nt * 8, 0, cfull(cb));
+                        c_issued |= 1u << cb;
+                        c_par = (c_par & ~(1u << cb)) | (cph << cb);
+                        if (++cb == CBUF) { cb = 0; cph ^= 1; }
+                    }
                     for (int kb = 0; kb < p.num_kb; kb++) {
                         if (!mbar_wait(empty(stage), phase ^ 1, abort_flag)) { ab = true; break; }
                         mbar_expect_tx(full(stage), STAGE_BYTES);
@@ -285,12 +306,19 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
                         ipar[stage] = phase;
                         if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
-            if (ab)  // let our own copies land before the CTA exits
+                }
+            if (ab) {  // let our own copies land before the CTA exits
                 for (int s = 0; s < STAGES; s++)
                     if (issued[s]) {
                         const unsigned long long t0 = gtimer();
                         while (!mbar_try(full(s), ipar[s]) && gtimer() - t0 < 100000000ull) {}
                     }
+                for (int b = 0; b < CBUF; b++)
+                    if (c_issued >> b & 1) {
+                        const unsigned long long t0 = gtimer();
+                        while (!mbar_try(cfull(b), c_par >> b & 1) && gtimer() - t0 < 100000000ull) {}
+                    }
+            }
         }
     } else if (warp == ISSUER) {
         if (lane == 0) {  // ---------------------------------- MMA issuer
@@ -326,8 +354,8 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
         const int q = warp & 3;             // TMEM lane quarter of this warp
         const int g = warp >> 2;            // epilogue warpgroup
         const int c0 = g * CMAX;            // first class this warpgroup counts
-        int acc = 0;
-        uint32_t aphase = 0;
+        int acc = 0, cb = 0;
+        uint32_t aphase = 0, cph = 0;
         bool ab = false;
         int64_t it = 0;
         for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++) {
@@ -362,20 +390,22 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
                 if (++acc == 2) { acc = 0; aphase ^= 1; }
                 const int gw0 = nt * (BN / 32);
                 if (CLASSIFY) {
-                    // this tile's 8 words of every class (the last tile may
-                    // have only 4: W is a multiple of 4; missing words are 0
-                    // in the query too).  Same address across the warp.
-                    const bool hi = gw0 + 8 <= p.W;
+                    // this tile's 8 words of every class, staged by the TMA
+                    // producer (words past W are zero, as in the query);
+                    // every lane reads the same address: broadcast
+                    const bool okc = mbar_wait(cfull(cb), cph, abort_flag);
+                    if (!__all_sync(0xffffffffu, okc)) { ab = true; break; }
+                    const uint4 *sc = reinterpret_cast<const uint4 *>(sCls + cb * CLS_BYTES);
 #pragma unroll
                     for (int c = 0; c < CMAX; c++)
                         if (c0 + c < p.C) {
-                            const uint4 *cw = reinterpret_cast<const uint4 *>(p.planes + (int64_t)(c0 + c) * p.W + gw0);
-                            const uint4 c0 = __ldg(cw);
-                            const uint4 c1 = hi ? __ldg(cw + 1) : make_uint4(0u, 0u, 0u, 0u);
-                            dist[c] += __popc(words[0] ^ c0.x) + __popc(words[1] ^ c0.y) + __popc(words[2] ^ c0.z) +
-                                       __popc(words[3] ^ c0.w) + __popc(words[4] ^ c1.x) + __popc(words[5] ^ c1.y) +
-                                       __popc(words[6] ^ c1.z) + __popc(words[7] ^ c1.w);
+                            const uint4 ca = sc[2 * (c0 + c)], cc = sc[2 * (c0 + c) + 1];
+                            dist[c] += __popc(words[0] ^ ca.x) + __popc(words[1] ^ ca.y) + __popc(words[2] ^ ca.z) +
+                                       __popc(words[3] ^ ca.w) + __popc(words[4] ^ cc.x) + __popc(words[5] ^ cc.y) +
+                                       __popc(words[6] ^ cc.z) + __popc(words[7] ^ cc.w);
                         }
+                    mbar_arrive(cempty(cb));
+                    if (++cb == CBUF) { cb = 0; cph ^= 1; }
                 } else if (valid) {
                     uint32_t *h = p.H + row * (int64_t)p.W + gw0;
                     if (gw0 + 4 <= p.W) *reinterpret_cast<uint4 *>(h) = make_uint4(words[0], words[1], words[2], words[3]);
@@ -420,26 +450,26 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
 
 // Launch helpers, instantiated by each encoding's translation unit.
 template <int ENC, int CMAX, bool CLASSIFY, int EWG>
-static cudaError_t launch_one(const CUtensorMap &ma, const CUtensorMap &mb, const Params &p, unsigned grid,
-                              cudaStream_t st)
+static cudaError_t launch_one(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const Params &p,
+                              unsigned grid, cudaStream_t st)
 {
     auto k = tc_encode_kernel<ENC, CMAX, CLASSIFY, EWG>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    k<<<grid, num_threads(EWG), SMEM_BYTES, st>>>(ma, mb, p);
+    k<<<grid, num_threads(EWG), SMEM_BYTES, st>>>(ma, mb, mc, p);
     return cudaGetLastError();
 }
 
 template <int ENC>
-static cudaError_t launch_enc(const CUtensorMap &ma, const CUtensorMap &mb, const Params &p, unsigned grid,
-                              bool classify, cudaStream_t st)
+static cudaError_t launch_enc(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const Params &p,
+                              unsigned grid, bool classify, cudaStream_t st)
 {
-    if (!classify) return launch_one<ENC, 1, false, 1>(ma, mb, p, grid, st);
+    if (!classify) return launch_one<ENC, 1, false, 1>(ma, mb, mc, p, grid, st);
     // up to 16 classes: one epilogue warpgroup; more: two, each counting half
-    if (p.C <= 16) return launch_one<ENC, 16, true, 1>(ma, mb, p, grid, st);
-    if (p.C <= 32) return launch_one<ENC, 16, true, 2>(ma, mb, p, grid, st);
-    if (p.C <= 64) return launch_one<ENC, 32, true, 2>(ma, mb, p, grid, st);
-    return launch_one<ENC, 64, true, 2>(ma, mb, p, grid, st);
+    if (p.C <= 16) return launch_one<ENC, 16, true, 1>(ma, mb, mc, p, grid, st);
+    if (p.C <= 32) return launch_one<ENC, 16, true, 2>(ma, mb, mc, p, grid, st);
+    if (p.C <= 64) return launch_one<ENC, 32, true, 2>(ma, mb, mc, p, grid, st);
+    return launch_one<ENC, 64, true, 2>(ma, mb, mc, p, grid, st);
 }
 
 // Read and clear this translation unit's device status word.
@@ -459,10 +489,10 @@ static cudaError_t read_status(cudaStream_t st, int *status)
 }
 
 // Entry points of the two encoding translation units.
-cudaError_t launch_bf16(const CUtensorMap &ma, const CUtensorMap &mb, const Params &p, unsigned grid, bool classify,
-                        cudaStream_t st);
-cudaError_t launch_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const Params &p, unsigned grid, bool classify,
-                       cudaStream_t st);
+cudaError_t launch_bf16(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const Params &p,
+                        unsigned grid, bool classify, cudaStream_t st);
+cudaError_t launch_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const Params &p,
+                       unsigned grid, bool classify, cudaStream_t st);
 cudaError_t status_bf16(cudaStream_t st, int *status);
 cudaError_t status_fp8(cudaStream_t st, int *status);
 
