@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, help="synth.WORKLOADS key")
     ap.add_argument("--batch", type=int, default=1 << 20, help="queries per step (per GPU)")
     ap.add_argument("--enc", default="fp8", choices=["bf16", "fp8"])
     ap.add_argument("--stride", type=int, default=2)
@@ -224,8 +225,8 @@ def run_ours(a):
     dev = torch.device("cuda", local)
     build.build()
     hdc.load()
-    w = synth.WORKLOADS[WORKLOAD]
-    data = synth.make(WORKLOAD)
+    w = synth.WORKLOADS[a.workload]
+    data = synth.make(w, n_query=min(w.n_query, 20000))
     Bt, acc, ups, train_s, Htr, ytr = train_model(hdc, torch, data, dev, w.epochs)
     train_passes = time_training(hdc, torch, Htr, ytr, w.D, w.C)
     del Htr
@@ -335,14 +336,14 @@ def run_ours(a):
     achieved = flops / avg_k / 1e12
     pt = PROFILED_TRAFFIC
     traffic = (pt["dram_bytes_per_query"] * B if tc_sources_sha() == pt["sources_sha1_16"] and a.enc == pt["enc"]
-               and a.stride == pt["stride"] else None)
+               and a.stride == pt["stride"] and a.workload == WORKLOAD else None)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": el / a.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "%s operands, fp32 accumulate, binary hypervectors" % ("e4m3" if a.enc == "fp8" else "bf16"),
         "data": "synthetic (seeded Gaussian mixture shaped like the workload; no dataset)",
-        "config": {"workload": WORKLOAD, "F": F, "D": w.D, "C": w.C, "enc": a.enc,
+        "config": {"workload": a.workload, "F": F, "D": w.D, "C": w.C, "enc": a.enc,
                    "perforation": [0.0, 1.0, a.stride], "Dk": Dk, "class_bits": 1, "queries_per_step": B,
                    "train": "bundling + %d retraining epochs on %d samples (FP32 encode)" % (w.epochs, w.n_train),
                    "l2": "inputs larger than L2 (%.1f GB of FP32 queries per step)" % (B * F * 4 / 1e9),
@@ -388,10 +389,10 @@ def run_reference(a):
     import oracle
     from paper_2606_26547_gb300 import synth
     oracle.build()
-    w = synth.WORKLOADS[WORKLOAD]
+    w = synth.WORKLOADS[a.workload]
     threads = os.cpu_count() or 1
     n_train = 32 * threads
-    data = synth.make(WORKLOAD, n_train=n_train)
+    data = synth.make(w, n_train=n_train, n_query=min(w.n_query, 20000))
     dims = oracle.kept_dims(w.D)
     bits, _, _, _ = oracle.encode_bits(data["Xtr"], data["Bt"], oracle.ENC_FP32, dims, threads=threads)
     acc, _ = oracle.train(bits, data["ytr"], w.C, 2)
@@ -414,7 +415,7 @@ def run_reference(a):
     out = {"impl": "reference", "metric": METRIC, "value": qps, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64 oracle of the %s path" % a.enc, "data": "synthetic",
-           "config": {"workload": WORKLOAD, "enc": a.enc, "perforation": [0.0, 1.0, a.stride],
+           "config": {"workload": a.workload, "enc": a.enc, "perforation": [0.0, 1.0, a.stride],
                       "queries_per_step": per_step,
                       "train": "bundling + 2 retraining epochs on %d samples (oracle)" % n_train},
            "cpu_baseline": {"value": qps, "unit": UNIT, "cores": threads, "kind": "oracle",

@@ -125,16 +125,20 @@ def make(workload: str | Workload, n_train: int | None = None, n_query: int | No
 def device_gauss_queries(n: int, w: Workload, seed: int, device="cuda"):
     """Large query batches drawn on the device (throughput runs only).
 
-    Same mixture as ``gauss_mixture`` (same centroids) but the noise comes
-    from a seeded torch generator on ``device``; returns (X float32, y int32).
+    Same mixture as ``gauss_mixture`` / ``int_mixture`` (same centroids) but
+    the noise comes from a seeded torch generator on ``device``; integer
+    workloads are rounded half to even and clipped to [-8, 7] like
+    ``int_mixture``.  Returns (X float32, y int32).
     """
     import torch
 
-    mu = torch.from_numpy(gauss_centroids(w.F, w.C, w.seed + _S_CENTROIDS)).to(
-        device=device, dtype=torch.float32)
+    cents = int_centroids if w.kind == "int" else gauss_centroids
+    mu = torch.from_numpy(cents(w.F, w.C, w.seed + _S_CENTROIDS)).to(device=device, dtype=torch.float32)
     g = torch.Generator(device=device)
     g.manual_seed(seed)
     y = (torch.arange(n, device=device, dtype=torch.int64) % w.C)
     X = torch.randn(n, w.F, generator=g, device=device, dtype=torch.float32)
     X.mul_(w.sigma).add_(mu[y])
+    if w.kind == "int":
+        X.round_().clamp_(-8, 7)       # torch.round: half to even
     return X, y.to(torch.int32)
