@@ -152,22 +152,26 @@ __device__ __forceinline__ void chunk_counts(const uint32_t *sq, int QLD, int ti
 
 // One query per thread.  Shared memory: the chunk's query words [WCH][TPB+1],
 // the chunk's class planes [planes][C][WCH], and the per-(config, class)
-// partial sums [nb*ns*C][TPB] (int64).
+// partial sums [ns*C][TPB] (int64) of the block's class width.
 __global__ void sweep_eval_kernel(const uint32_t *__restrict__ H, const int32_t *__restrict__ y, int64_t N, int C,
                                   int W, int WCH, SweepConf cf, const uint32_t *__restrict__ planes,
                                   const long long *__restrict__ sums, const double *__restrict__ norms,
                                   int32_t *__restrict__ correct, int32_t *__restrict__ labels)
 {
+    // blockIdx.y = class-width entry jb: blocks of different widths share
+    // the query words through L2 and run side by side
     extern __shared__ __align__(16) uint8_t sm[];
     const int TPB = blockDim.x, tid = threadIdx.x;
-    const int ncfg = cf.nb * cf.ns;
-    long long *accs = reinterpret_cast<long long *>(sm);                    // ncfg*C x TPB
+    const int jb = blockIdx.y;
+    const int np = cf.planes[jb], p0 = cf.plane_off[jb];
+    const int ns = cf.ns;
+    long long *accs = reinterpret_cast<long long *>(sm);                         // ns*C x TPB
     const int QLD = TPB + 1;  // padded: conflict-free stores and loads
-    uint32_t *sq = reinterpret_cast<uint32_t *>(accs + (size_t)ncfg * C * TPB);  // WCH x QLD
-    uint32_t *sp = sq + (size_t)WCH * QLD;                                  // planes x C x WCH
+    uint32_t *sq = reinterpret_cast<uint32_t *>(accs + (size_t)ns * C * TPB);      // WCH x QLD
+    uint32_t *sp = sq + (size_t)WCH * QLD;                                       // np x C x WCH
     const int64_t row = (int64_t)blockIdx.x * TPB + tid;
     const bool valid = row < N;
-    for (int k = 0; k < ncfg * C; k++) accs[(size_t)k * TPB + tid] = 0;
+    for (int k = 0; k < ns * C; k++) accs[(size_t)k * TPB + tid] = 0;
 
     for (int w0 = 0; w0 < W; w0 += WCH) {
         const int nw = min(WCH, W - w0);
@@ -178,71 +182,65 @@ __global__ void sweep_eval_kernel(const uint32_t *__restrict__ H, const int32_t 
             const int64_t gr = (int64_t)blockIdx.x * TPB + r;
             sq[(size_t)j * QLD + r] = (gr < N && j < nw) ? H[gr * W + w0 + j] : 0u;
         }
-        for (int i = tid; i < cf.total_planes * C * WCH; i += TPB) {
+        for (int i = tid; i < np * C * WCH; i += TPB) {
             const int pc = i / WCH, j = i % WCH;
-            sp[i] = j < nw ? planes[(int64_t)pc * W + w0 + j] : 0u;
+            sp[i] = j < nw ? planes[((int64_t)p0 * C + pc) * W + w0 + j] : 0u;
         }
         __syncthreads();
-        for (int jb = 0; jb < cf.nb; jb++) {
-            const int b = cf.bits[jb], np = cf.planes[jb], p0 = cf.plane_off[jb];
-            for (int c = 0; c < C; c++) {
-                long long part[MAXS];
-                const uint32_t *spc = sp + ((size_t)p0 * C + c) * WCH;
-                if (np == 1) {
-                    chunk_counts<1>(sq, QLD, tid, spc, C * WCH, nw, cf, part);
-                } else if (np == 4) {
-                    chunk_counts<4>(sq, QLD, tid, spc, C * WCH, nw, cf, part);
-                } else if (np == 8) {
-                    chunk_counts<8>(sq, QLD, tid, spc, C * WCH, nw, cf, part);
-                } else {  // unquantised accumulators: 32 planes, int64 weights
+        for (int c = 0; c < C; c++) {
+            long long part[MAXS];
+            const uint32_t *spc = sp + (size_t)c * WCH;
+            if (np == 1) {
+                chunk_counts<1>(sq, QLD, tid, spc, C * WCH, nw, cf, part);
+            } else if (np == 4) {
+                chunk_counts<4>(sq, QLD, tid, spc, C * WCH, nw, cf, part);
+            } else if (np == 8) {
+                chunk_counts<8>(sq, QLD, tid, spc, C * WCH, nw, cf, part);
+            } else {  // unquantised accumulators: 32 planes, int64 weights
 #pragma unroll
                 for (int i = 0; i < MAXS; i++) part[i] = 0;
                 for (int j = 0; j < nw; j++) {
                     const uint32_t qw = sq[(size_t)j * QLD + tid];
-                    {
-                        for (int p = 0; p < np; p++) {
-                            const uint32_t x = qw & sp[((size_t)(p0 + p) * C + c) * WCH + j];
-                            const long long wp = p == np - 1 ? -(1ll << p) : (1ll << p);
+                    for (int p = 0; p < np; p++) {
+                        const uint32_t x = qw & sp[((size_t)p * C + c) * WCH + j];
+                        const long long wp = p == np - 1 ? -(1ll << p) : (1ll << p);
 #pragma unroll
-                            for (int i = 0; i < MAXS; i++)
-                                if (i < cf.ns) part[i] += wp * __popc(x & cf.mask[i]);
-                        }
+                        for (int i = 0; i < MAXS; i++)
+                            if (i < ns) part[i] += wp * __popc(x & cf.mask[i]);
                     }
                 }
-                }
-#pragma unroll
-                for (int i = 0; i < MAXS; i++)
-                    if (i < cf.ns) accs[((size_t)(jb * cf.ns + i) * C + c) * TPB + tid] += part[i];
             }
+#pragma unroll
+            for (int i = 0; i < MAXS; i++)
+                if (i < ns) accs[((size_t)i * C + c) * TPB + tid] += part[i];
         }
     }
-    // arg-min / arg-max per configuration, counts of correct predictions
+    // arg-min / arg-max per stride, counts of correct predictions
     const int lane = tid & 31;
     const int yv = valid ? y[row] : -1;
-    for (int jb = 0; jb < cf.nb; jb++)
-        for (int i = 0; i < cf.ns; i++) {
-            const int k = jb * cf.ns + i;
-            int best = 0;
-            if (cf.bits[jb] == 1) {
-                long long bv = accs[((size_t)k * C) * TPB + tid];
-                for (int c = 1; c < C; c++) {
-                    const long long v = accs[((size_t)k * C + c) * TPB + tid];
-                    if (v < bv) { bv = v; best = c; }
-                }
-            } else {
-                double bs = 0.0;
-                for (int c = 0; c < C; c++) {
-                    const double nrm = norms[(int64_t)k * C + c];
-                    const double s = nrm == 0.0 ? 0.0
-                                                : (double)(sums[(int64_t)k * C + c] -
-                                                           2 * accs[((size_t)k * C + c) * TPB + tid]) / nrm;
-                    if (c == 0 || s > bs) { bs = s; best = c; }
-                }
+    for (int i = 0; i < ns; i++) {
+        const int k = jb * ns + i;
+        int best = 0;
+        if (cf.bits[jb] == 1) {
+            long long bv = accs[((size_t)i * C) * TPB + tid];
+            for (int c = 1; c < C; c++) {
+                const long long v = accs[((size_t)i * C + c) * TPB + tid];
+                if (v < bv) { bv = v; best = c; }
             }
-            if (valid && labels) labels[(int64_t)k * N + row] = best;
-            const unsigned hit = __ballot_sync(0xffffffffu, valid && best == yv);
-            if (lane == 0 && hit) atomicAdd(correct + k, __popc(hit));
+        } else {
+            double bs = 0.0;
+            for (int c = 0; c < C; c++) {
+                const double nrm = norms[(int64_t)k * C + c];
+                const double sc = nrm == 0.0 ? 0.0
+                                             : (double)(sums[(int64_t)k * C + c] -
+                                                        2 * accs[((size_t)i * C + c) * TPB + tid]) / nrm;
+                if (c == 0 || sc > bs) { bs = sc; best = c; }
+            }
         }
+        if (valid && labels) labels[(int64_t)k * N + row] = best;
+        const unsigned hit = __ballot_sync(0xffffffffu, valid && best == yv);
+        if (lane == 0 && hit) atomicAdd(correct + k, __popc(hit));
+    }
 }
 
 bool is_pow2_le32(int s) { return s >= 1 && s <= 32 && (s & (s - 1)) == 0; }
@@ -322,7 +320,9 @@ extern "C" hdc_status hdc_sweep_eval(const uint32_t *H, const int32_t *y, int64_
     const SweepLayout L = sweep_layout(D, C, cf);
     if (!ws || ws_bytes < L.total || ((uintptr_t)ws % kAlign) != 0) return HDC_ERR_WORKSPACE;
     const size_t ncfg = (size_t)cf.nb * cf.ns;
-    const size_t smem = ncfg * C * tpb * 8 + (size_t)wch * (tpb + 1) * 4 + (size_t)cf.total_planes * C * wch * 4;
+    int maxp = 0;
+    for (int j = 0; j < cf.nb; j++) maxp = cf.planes[j] > maxp ? cf.planes[j] : maxp;
+    const size_t smem = (size_t)cf.ns * C * tpb * 8 + (size_t)wch * (tpb + 1) * 4 + (size_t)maxp * C * wch * 4;
     if (smem > 220 * 1024) return HDC_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     char *w = (char *)ws;
@@ -335,7 +335,7 @@ extern "C" hdc_status hdc_sweep_eval(const uint32_t *H, const int32_t *y, int64_
         cudaSuccess)
         return HDC_ERR_CUDA;
     const int64_t blocks = (N + tpb - 1) / tpb;
-    sweep_eval_kernel<<<(unsigned)blocks, tpb, smem, st>>>(H, y, N, C, W, wch, cf, (const uint32_t *)(w + L.planes),
+    sweep_eval_kernel<<<dim3((unsigned)blocks, (unsigned)cf.nb), tpb, smem, st>>>(H, y, N, C, W, wch, cf, (const uint32_t *)(w + L.planes),
                                                           (const long long *)(w + L.sums),
                                                           (const double *)(w + L.norms), correct, labels);
     return cudaGetLastError() == cudaSuccess ? HDC_OK : HDC_ERR_CUDA;
