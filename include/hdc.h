@@ -209,12 +209,18 @@ hdc_status hdc_classify_host(const float *const *parts_host, const int64_t *part
 /* Batched evaluation of approximation configurations.  The paper's tuner
  * (Sec. 3, Fig. 1) compiles and runs the application once per candidate
  * configuration and reads back its QoS (accuracy).  Here every combination
- * of perforation stride x class-hypervector width of one trained model is
+ * of perforation entry x class-hypervector width of one trained model is
  * scored in one launch from the same validation hypervectors encoded once
- * at the full D: the strides' kept-dimension sets are nested (stride 8's
- * dims are a subset of stride 4's, ...), so each configuration is a bit
- * mask over the same words.
- *   strides[i]  power of two <= 32: perforation (0, 1, stride) of D
+ * at the full D: every entry's kept dimensions are one 32-bit mask pattern
+ * per word (stride a power of two <= 32), cut at the entry's first and last
+ * word, so all configurations share the same loads.
+ *   entry i     the perforation (starts[i], ends[i], strides[i]) of
+ *               hdc_classify: with s0 = floor(starts[i]*D) and
+ *               e0 = floor(ends[i]*D) (both formed in double), the kept
+ *               dims are d = s0 + k*strides[i] < e0
+ *   strides[i]  power of two <= 32
+ *   starts[i]   start fraction in [0, 1)
+ *   ends[i]     end fraction in (0, 1] (0 means 1.0); e0 > s0 is required
  *   bits[j]     1 (Hamming, arg-min), 4 or 8 (b-bit cosine, arg-max, as in
  *               hdc_classify), or 0: cosine against the unquantised int32
  *               accumulators themselves (requires sum over D of acc^2 < 2^63)
@@ -227,6 +233,8 @@ typedef struct {
     uint32_t struct_size;                 /* = sizeof(hdc_sweep_spec)       */
     int32_t n_strides;                    /* 1 .. HDC_SWEEP_MAX_STRIDES     */
     int32_t strides[HDC_SWEEP_MAX_STRIDES];
+    float starts[HDC_SWEEP_MAX_STRIDES];
+    float ends[HDC_SWEEP_MAX_STRIDES];
     int32_t n_bits;                       /* 1 .. HDC_SWEEP_MAX_BITS        */
     int32_t bits[HDC_SWEEP_MAX_BITS];
     int32_t block_threads;                /* 0, 64, 128 or 256              */

@@ -3,16 +3,19 @@
 //
 // For one trained model: validation hypervectors H (N x W words, encoded
 // once at the full D) are scored under every (class width b, perforation
-// stride s) pair.  Strides are powers of two <= 32 with start 0, so the kept
-// dims of stride s inside any word are the bits at positions = 0 (mod s):
-// one constant mask per stride (0xFFFFFFFF, 0x55555555, 0x11111111, ...),
-// and the configurations share every load.
+// entry (s0, e0, s)) pair.  Strides are powers of two <= 32, so the kept
+// dims of an entry inside any word are the bits at positions = s0 (mod s):
+// one constant mask per entry (0x55555555 << (s0 mod 2) for s = 2, ...),
+// cleared below s0 in the first word and from e0 on in the last, and the
+// configurations share every load.
 //   b = 1       Hamming over the stride's dims          -> arg-min
 //   b = 4, 8    cosine with b-bit class values (planes) -> arg-max
 //   b = 0       cosine with the int32 accumulators themselves (32 planes)
 // The b-bit quantisation, the sums and the norms are those of hdc_classify
 // (per class over the full D; sums and norms over each stride's dims), so
 // every configuration's predictions equal hdc_classify's.
+#include <math.h>
+
 #include "hdc_internal.cuh"
 
 namespace hdc {
@@ -24,7 +27,13 @@ constexpr int MAXB = HDC_SWEEP_MAX_BITS;
 struct SweepConf {
     int ns, nb;
     int stride[MAXS];
-    uint32_t mask[MAXS];
+    uint32_t mask[MAXS];    // kept bit positions inside a word
+    int64_t s0[MAXS];       // first kept dim of each entry
+    int sw[MAXS];           // word holding s0
+    uint32_t shead[MAXS];   // bits of word sw at or above s0
+    int64_t e0[MAXS];       // end dim (exclusive) of each entry
+    int ew[MAXS];           // words fully below e0
+    uint32_t etail[MAXS];   // kept bits of word ew (below e0)
     int bits[MAXB];
     int planes[MAXB];       // planes of each width
     int plane_off[MAXB];    // first plane of each width in the plane array
@@ -86,7 +95,7 @@ __global__ void __launch_bounds__(256) sweep_prep_kernel(const int32_t *__restri
             }
 #pragma unroll
             for (int i = 0; i < MAXS; i++)
-                if (i < cf.ns && valid && d % cf.stride[i] == 0) {
+                if (i < cf.ns && valid && d >= cf.s0[i] && (d - cf.s0[i]) % cf.stride[i] == 0 && d < cf.e0[i]) {
                     lsum[j * MAXS + i] += v;
                     lsq[j * MAXS + i] += v * v;
                 }
@@ -119,9 +128,19 @@ __global__ void __launch_bounds__(256) sweep_prep_kernel(const int32_t *__restri
 // (NP = 1: Hamming, popc(q ^ c); NP = 4, 8: b-bit cosine, popc(q & plane)
 // weighted 2^p, the top plane negative).  Counts stay int32 per (plane,
 // stride) and are weighted once per chunk.
+// Mask of entry i for global word w: the entry's bit pattern, cut below s0
+// and from e0 on.
+__device__ __forceinline__ uint32_t entry_mask(const SweepConf &cf, int i, int w)
+{
+    uint32_t m = (w < cf.sw[i] || w > cf.ew[i]) ? 0u : cf.mask[i];
+    if (w == cf.sw[i]) m &= cf.shead[i];
+    if (w == cf.ew[i]) m &= cf.etail[i];
+    return m;
+}
+
 template <int NP>
 __device__ __forceinline__ void chunk_counts(const uint32_t *sq, int QLD, int tid, const uint32_t *spc,
-                                             int pstride, int nw, const SweepConf &cf, long long *out)
+                                             int pstride, int nw, int w0, const SweepConf &cf, long long *out)
 {
     int cnt[NP][MAXS];
 #pragma unroll
@@ -130,13 +149,16 @@ __device__ __forceinline__ void chunk_counts(const uint32_t *sq, int QLD, int ti
         for (int i = 0; i < MAXS; i++) cnt[p][i] = 0;
     for (int j = 0; j < nw; j++) {
         const uint32_t qw = sq[(size_t)j * QLD + tid];
+        uint32_t m[MAXS];
+#pragma unroll
+        for (int i = 0; i < MAXS; i++) m[i] = i < cf.ns ? entry_mask(cf, i, w0 + j) : 0u;
 #pragma unroll
         for (int p = 0; p < NP; p++) {
             const uint32_t cw = spc[(size_t)p * pstride + j];
             const uint32_t x = NP == 1 ? qw ^ cw : qw & cw;
 #pragma unroll
             for (int i = 0; i < MAXS; i++)
-                if (i < cf.ns) cnt[p][i] += __popc(x & cf.mask[i]);
+                if (i < cf.ns) cnt[p][i] += __popc(x & m[i]);
         }
     }
 #pragma unroll
@@ -191,11 +213,11 @@ __global__ void sweep_eval_kernel(const uint32_t *__restrict__ H, const int32_t 
             long long part[MAXS];
             const uint32_t *spc = sp + (size_t)c * WCH;
             if (np == 1) {
-                chunk_counts<1>(sq, QLD, tid, spc, C * WCH, nw, cf, part);
+                chunk_counts<1>(sq, QLD, tid, spc, C * WCH, nw, w0, cf, part);
             } else if (np == 4) {
-                chunk_counts<4>(sq, QLD, tid, spc, C * WCH, nw, cf, part);
+                chunk_counts<4>(sq, QLD, tid, spc, C * WCH, nw, w0, cf, part);
             } else if (np == 8) {
-                chunk_counts<8>(sq, QLD, tid, spc, C * WCH, nw, cf, part);
+                chunk_counts<8>(sq, QLD, tid, spc, C * WCH, nw, w0, cf, part);
             } else {  // unquantised accumulators: 32 planes, int64 weights
 #pragma unroll
                 for (int i = 0; i < MAXS; i++) part[i] = 0;
@@ -206,7 +228,7 @@ __global__ void sweep_eval_kernel(const uint32_t *__restrict__ H, const int32_t 
                         const long long wp = p == np - 1 ? -(1ll << p) : (1ll << p);
 #pragma unroll
                         for (int i = 0; i < MAXS; i++)
-                            if (i < ns) part[i] += wp * __popc(x & cf.mask[i]);
+                            if (i < ns) part[i] += wp * __popc(x & entry_mask(cf, i, w0 + j));
                     }
                 }
             }
@@ -245,20 +267,42 @@ __global__ void sweep_eval_kernel(const uint32_t *__restrict__ H, const int32_t 
 
 bool is_pow2_le32(int s) { return s >= 1 && s <= 32 && (s & (s - 1)) == 0; }
 
-bool make_conf(const hdc_sweep_spec *sp, SweepConf *cf)
+bool make_conf(const hdc_sweep_spec *sp, int64_t D, SweepConf *cf)
 {
     if (!sp || sp->struct_size < sizeof(hdc_sweep_spec)) return false;
     if (sp->n_strides < 1 || sp->n_strides > MAXS || sp->n_bits < 1 || sp->n_bits > MAXB) return false;
     cf->ns = sp->n_strides;
     cf->nb = sp->n_bits;
-    for (int i = 0; i < MAXS; i++) { cf->stride[i] = 1; cf->mask[i] = 0; }
+    for (int i = 0; i < MAXS; i++) {
+        cf->stride[i] = 1;
+        cf->mask[i] = 0;
+        cf->s0[i] = 0;
+        cf->sw[i] = 0;
+        cf->shead[i] = 0;
+        cf->e0[i] = D;
+        cf->ew[i] = 0;
+        cf->etail[i] = 0;
+    }
     for (int i = 0; i < cf->ns; i++) {
         const int s = sp->strides[i];
         if (!is_pow2_le32(s)) return false;
+        // start and end of entry i: floor(fraction * D) formed in double, as
+        // for hdc_classify
+        const float start = sp->starts[i], end = sp->ends[i];
+        if (!(start >= 0.f) || !(start < 1.f) || !(end >= 0.f) || end > 1.f) return false;
+        const int64_t s0 = (int64_t)floor((double)start * (double)D);
+        const int64_t e0 = end == 0.f ? D : (int64_t)floor((double)end * (double)D);
+        if (e0 <= s0) return false;  // keeps at least dim s0
         uint32_t m = 0;
-        for (int b = 0; b < 32; b += s) m |= 1u << b;
+        for (int b = (int)(s0 % s); b < 32; b += s) m |= 1u << b;
         cf->stride[i] = s;
         cf->mask[i] = m;
+        cf->s0[i] = s0;
+        cf->sw[i] = (int)(s0 >> 5);
+        cf->shead[i] = ~0u << (s0 & 31);
+        cf->e0[i] = e0;
+        cf->ew[i] = (int)(e0 >> 5);
+        cf->etail[i] = (1u << (e0 & 31)) - 1u;
     }
     int off = 0;
     for (int j = 0; j < MAXB; j++) { cf->bits[j] = 1; cf->planes[j] = 0; cf->plane_off[j] = 0; }
@@ -299,7 +343,7 @@ using namespace hdc;
 extern "C" hdc_status hdc_sweep_workspace_bytes(int32_t D, int32_t C, const hdc_sweep_spec *spec, size_t *bytes)
 {
     SweepConf cf;
-    if (!bytes || D <= 0 || C <= 0 || !make_conf(spec, &cf)) return HDC_ERR_INVALID_ARG;
+    if (!bytes || D <= 0 || C <= 0 || !make_conf(spec, D, &cf)) return HDC_ERR_INVALID_ARG;
     *bytes = sweep_layout(D, C, cf).total;
     return HDC_OK;
 }
@@ -309,7 +353,7 @@ extern "C" hdc_status hdc_sweep_eval(const uint32_t *H, const int32_t *y, int64_
                                      int32_t *labels, void *ws, size_t ws_bytes, hdc_stream_t stream)
 {
     SweepConf cf;
-    if (N < 0 || D <= 0 || C <= 0 || !make_conf(spec, &cf) || !correct || !acc) return HDC_ERR_INVALID_ARG;
+    if (N < 0 || D <= 0 || C <= 0 || !make_conf(spec, D, &cf) || !correct || !acc) return HDC_ERR_INVALID_ARG;
     if (N > 0 && (!H || !y || ((uintptr_t)H % 16) != 0)) return HDC_ERR_INVALID_ARG;
     const int tpb = spec->block_threads ? spec->block_threads : 128;
     if (tpb != 64 && tpb != 128 && tpb != 256) return HDC_ERR_INVALID_ARG;

@@ -302,16 +302,22 @@ def classify_host(parts, model: Model, X_dev: torch.Tensor, labels_dev: torch.Te
 
 class SweepSpecC(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("n_strides", ctypes.c_int32), ("strides", ctypes.c_int32 * 6),
-                ("n_bits", ctypes.c_int32), ("bits", ctypes.c_int32 * 4), ("block_threads", ctypes.c_int32),
-                ("words_per_chunk", ctypes.c_int32)]
+                ("starts", ctypes.c_float * 6), ("ends", ctypes.c_float * 6), ("n_bits", ctypes.c_int32), ("bits", ctypes.c_int32 * 4),
+                ("block_threads", ctypes.c_int32), ("words_per_chunk", ctypes.c_int32)]
 
 
-def sweep_spec(strides, bits, block_threads: int = 0, words_per_chunk: int = 0) -> SweepSpecC:
+def sweep_spec(strides, bits, block_threads: int = 0, words_per_chunk: int = 0, ends=None,
+               starts=None) -> SweepSpecC:
+    """strides[i] with optional starts[i] (fraction of D, default 0.0) and
+    ends[i] (default 1.0) form the perforation (starts[i], ends[i],
+    strides[i]) of entry i."""
     s = SweepSpecC()
     s.struct_size = ctypes.sizeof(SweepSpecC)
     s.n_strides = len(strides)
     for i, v in enumerate(strides):
         s.strides[i] = v
+        s.starts[i] = 0.0 if starts is None else starts[i]
+        s.ends[i] = 1.0 if ends is None else ends[i]
     s.n_bits = len(bits)
     for i, v in enumerate(bits):
         s.bits[i] = v
@@ -326,10 +332,12 @@ class Sweep:
     call can be captured in a CUDA graph."""
 
     def __init__(self, D: int, C: int, strides, bits, N: int, device, block_threads: int = 0,
-                 words_per_chunk: int = 0, keep_labels: bool = False):
+                 words_per_chunk: int = 0, keep_labels: bool = False, ends=None, starts=None):
         self.D, self.C, self.N = D, C, N
         self.strides, self.bits = list(strides), list(bits)
-        self.spec = sweep_spec(self.strides, self.bits, block_threads, words_per_chunk)
+        self.ends = [1.0] * len(self.strides) if ends is None else list(ends)
+        self.starts = [0.0] * len(self.strides) if starts is None else list(starts)
+        self.spec = sweep_spec(self.strides, self.bits, block_threads, words_per_chunk, self.ends, self.starts)
         n = ctypes.c_size_t()
         _call("hdc_sweep_workspace_bytes", D, C, ctypes.byref(self.spec), ctypes.byref(n))
         self.ws = _empty_bytes(n.value, device)

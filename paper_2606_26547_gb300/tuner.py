@@ -1,0 +1,498 @@
+"""Approximation tuner over the batched evaluator (the paper's tuning loop,
+Sec. 3 and Sec. 5.2), with every candidate scored on the GPU.
+
+Knobs (Sec. 4.2, 4.3) as this library implements them:
+  enc      element type of the encoding: fp32, bf16 or fp8 (global)
+  dim      encoding dimensionality D' in {D, D/2, D/4, ...} (global)
+  epochs   TRAIN_ITERATIONS: retraining epochs after bundling (custom knob)
+  start, end, stride
+           red_perf of the inference similarity reduction
+  bits     class hypervector width: 1 (Hamming) or 4 / 8 (cosine), the
+           algorithmic choice and element type of the similarity
+The encoding's feature reduction is never perforated here: every space
+carries the no-approx hint on the encoding.  The pruning modes of Sec. 5.2
+therefore become: ``full`` (start, stride and end tunable; Full RedPerf
+with the hint), ``end_only`` (start 0 and stride 1 fixed) and ``none``
+(no perforation).
+
+Search: an ensemble of techniques (uniform random, greedy uniform mutation,
+normal mutation, differential evolution) chosen per proposal by an
+area-under-curve bandit, the scheme OpenTuner's default meta-technique
+follows; each run starts from the baseline configuration.  QoS is a
+constraint: a configuration is feasible when its validation accuracy is
+at least the baseline's minus ``qos_drop`` (0.05 in the paper's runs).
+The objective is the application's time: training (encode the training
+set, bundle, retrain) plus classifying the validation set, each part
+measured with CUDA events.  Proposals are scored in batches: one
+hdc_sweep_eval launch per trained snapshot (enc, dim, epochs) scores all
+of the batch's perforation entries (up to six per launch) under every
+class width at once.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import json
+import math
+import time
+
+import numpy as np
+
+ENCS = ("fp32", "bf16", "fp8")
+STRIDES = (1, 2, 4, 8, 16, 32)
+BITS = (1, 4, 8)
+GRID = 100          # start / end fractions on a 1/GRID grid
+MIN_SPAN = 5        # end - start >= MIN_SPAN / GRID
+MODES = ("none", "end_only", "full")
+
+
+@dataclasses.dataclass(frozen=True, order=True)
+class Config:
+    enc: str
+    dim: int
+    epochs: int
+    start: float
+    end: float
+    stride: int
+    bits: int
+
+
+class Space:
+    """The knobs of one pruning mode as index ranges; a point is a tuple of
+    value indices in KNOBS order."""
+    KNOBS = ("enc", "dim", "epochs", "start", "end", "stride", "bits")
+
+    def __init__(self, mode: str, D: int, max_epochs: int, dim_levels: int = 5, min_dim: int = 128):
+        if mode not in MODES:
+            raise ValueError(mode)
+        self.mode = mode
+        dims = tuple(D >> k for k in range(dim_levels) if (D >> k) >= min_dim)
+        starts = tuple(i / GRID for i in range(GRID - MIN_SPAN + 1)) if mode == "full" else (0.0,)
+        ends = tuple(i / GRID for i in range(MIN_SPAN, GRID + 1)) if mode != "none" else (1.0,)
+        strides = STRIDES if mode == "full" else (1,)
+        self.values = dict(enc=ENCS, dim=dims, epochs=tuple(range(max_epochs + 1)), start=starts, end=ends,
+                           stride=strides, bits=BITS)
+        self.sizes = tuple(len(self.values[k]) for k in self.KNOBS)
+
+    def log10_size(self) -> float:
+        return float(sum(math.log10(n) for n in self.sizes))
+
+    def config(self, point) -> Config:
+        return Config(*(self.values[k][i] for k, i in zip(self.KNOBS, point)))
+
+    def point(self, c: Config):
+        return tuple(self.values[k].index(getattr(c, k)) for k in self.KNOBS)
+
+    def contains(self, c: Config) -> bool:
+        try:
+            self.point(c)
+        except ValueError:
+            return False
+        return self.valid(c)
+
+    @staticmethod
+    def valid(c: Config) -> bool:
+        return round((c.end - c.start) * GRID) >= MIN_SPAN
+
+    def repair(self, point):
+        """Nearest valid point: move end up (else start down) to the span."""
+        p = list(point)
+        ks, ke = self.KNOBS.index("start"), self.KNOBS.index("end")
+        while not self.valid(self.config(p)):
+            if p[ke] + 1 < self.sizes[ke]:
+                p[ke] += 1
+            else:
+                p[ks] -= 1
+        return tuple(p)
+
+    def random(self, rng):
+        return self.repair(tuple(int(rng.integers(n)) for n in self.sizes))
+
+    def all_points(self):
+        for p in np.ndindex(*self.sizes):
+            if self.valid(self.config(p)):
+                yield tuple(int(i) for i in p)
+
+
+# ------------------------------------------------------------ techniques
+class Technique:
+    name = "technique"
+
+    def propose(self, space: Space, search: "Search", rng):
+        raise NotImplementedError
+
+
+class UniformRandom(Technique):
+    name = "uniform_random"
+
+    def propose(self, space, search, rng):
+        return space.random(rng)
+
+
+class GreedyMutation(Technique):
+    """Copy the best point; each knob independently (at least one) takes a
+    uniformly random value."""
+    name = "greedy_mutation"
+
+    def __init__(self, rate: float = 0.2):
+        self.rate = rate
+
+    def propose(self, space, search, rng):
+        p = list(search.best_point)
+        live = [k for k, n in enumerate(space.sizes) if n > 1]
+        hit = [k for k in live if rng.random() < self.rate] or [live[int(rng.integers(len(live)))]]
+        for k in hit:
+            p[k] = int(rng.integers(space.sizes[k]))
+        return space.repair(tuple(p))
+
+
+class NormalMutation(Technique):
+    """Copy the best point; each knob independently (at least one) moves by
+    a normal step of sigma x its range, rounded and clipped."""
+    name = "normal_mutation"
+
+    def __init__(self, rate: float = 0.3, sigma: float = 0.1):
+        self.rate, self.sigma = rate, sigma
+
+    def propose(self, space, search, rng):
+        p = list(search.best_point)
+        live = [k for k, n in enumerate(space.sizes) if n > 1]
+        hit = [k for k in live if rng.random() < self.rate] or [live[int(rng.integers(len(live)))]]
+        for k in hit:
+            n = space.sizes[k]
+            step = int(round(rng.normal(0.0, max(self.sigma * n, 0.6))))
+            p[k] = min(max(p[k] + (step or (1 if rng.random() < 0.5 else -1)), 0), n - 1)
+        return space.repair(tuple(p))
+
+
+class DifferentialEvolution(Technique):
+    """x = a + F (b - c) over index vectors of three ranked points, crossed
+    over with a fourth at rate CR (the population is the best ``pop``
+    points seen)."""
+    name = "differential_evolution"
+
+    def __init__(self, pop: int = 30, F: float = 0.7, CR: float = 0.5):
+        self.pop, self.F, self.CR = pop, F, CR
+
+    def propose(self, space, search, rng):
+        ranked = search.ranked_points(self.pop)
+        if len(ranked) < 4:
+            return space.random(rng)
+        i = rng.choice(len(ranked), 4, replace=False)
+        x, a, b, c = (ranked[j] for j in i)
+        out = []
+        kf = int(rng.integers(len(space.sizes)))
+        for k, n in enumerate(space.sizes):
+            if k == kf or rng.random() < self.CR:
+                v = int(round(a[k] + self.F * (b[k] - c[k])))
+                out.append(min(max(v, 0), n - 1))
+            else:
+                out.append(x[k])
+        return space.repair(tuple(out))
+
+
+class AUCBandit:
+    """Technique choice by area under the curve of recent successes (a use
+    scores 1 when its proposal became the new best) plus an exploration
+    bonus C sqrt(2 ln T / n), over a sliding window of uses."""
+
+    def __init__(self, techniques, C: float = 0.05, window: int = 500):
+        self.techniques = list(techniques)
+        self.C, self.window = C, window
+        self.history = []   # (technique index, success)
+
+    def _auc(self, k):
+        uses = [s for t, s in self.history if t == k]
+        if not uses:
+            return 0.0
+        # later successes weigh more: sum_i i * s_i normalised
+        n = len(uses)
+        return sum((i + 1) * s for i, s in enumerate(uses)) * 2.0 / (n * (n + 1))
+
+    def choose(self, rng) -> int:
+        T = len(self.history)
+        best, bv = 0, -1.0
+        for k in range(len(self.techniques)):
+            n = sum(1 for t, _ in self.history if t == k)
+            if n == 0:
+                return k
+            v = self._auc(k) + self.C * math.sqrt(2.0 * math.log(T) / n)
+            if v > bv:
+                best, bv = k, v
+        return best
+
+    def credit(self, k: int, success: bool) -> None:
+        self.history.append((k, 1 if success else 0))
+        if len(self.history) > self.window:
+            self.history.pop(0)
+
+
+# ---------------------------------------------------------------- search
+@dataclasses.dataclass
+class Result:
+    accuracy: float
+    ms: float
+
+
+class Search:
+    """Constrained minimisation of ms subject to accuracy >= target."""
+
+    def __init__(self, space: Space, evaluate, baseline: Config, qos_drop: float = 0.05, seed: int = 0,
+                 batch: int = 36, techniques=None):
+        self.space, self.evaluate = space, evaluate
+        self.rng = np.random.default_rng(seed)
+        self.batch = batch
+        self.bandit = AUCBandit(techniques or [UniformRandom(), GreedyMutation(), NormalMutation(),
+                                               DifferentialEvolution()])
+        self.results = {}   # Config -> Result
+        got = evaluate([baseline])
+        self.results.update(got)
+        base = got[baseline]
+        self.baseline, self.base_result = baseline, base
+        self.target = base.accuracy - qos_drop
+        self.best = baseline
+        self.best_point = space.point(baseline) if space.contains(baseline) else space.random(self.rng)
+        self.trace = [(1, 0.0, 1.0)]   # (evaluations, seconds, running-best speedup)
+        self.t0 = time.perf_counter()
+
+    def feasible(self, c: Config) -> bool:
+        return self.results[c].accuracy >= self.target
+
+    def fitness(self, c: Config):
+        r = self.results[c]
+        return (0, r.ms) if r.accuracy >= self.target else (1, self.target - r.accuracy)
+
+    def ranked_points(self, n: int):
+        cs = [c for c in self.results if self.space.contains(c)]
+        cs.sort(key=self.fitness)
+        return [self.space.point(c) for c in cs[:n]]
+
+    def speedup(self, c: Config) -> float:
+        return self.base_result.ms / self.results[c].ms
+
+    def step(self) -> int:
+        """One batch of proposals; returns the number of new evaluations."""
+        props, used = [], []
+        seen = set()
+        for _ in range(self.batch * 4):
+            if len(props) == self.batch:
+                break
+            k = self.bandit.choose(self.rng)
+            c = self.space.config(self.bandit.techniques[k].propose(self.space, self, self.rng))
+            if c in self.results or c in seen:
+                self.bandit.credit(k, False)
+                continue
+            seen.add(c)
+            props.append(c)
+            used.append(k)
+        if len(props) < self.batch and math.prod(self.space.sizes) <= 20000:
+            # a small space whose proposals keep repeating: fill the batch
+            # with points not yet evaluated
+            rest = [c for c in map(self.space.config, self.space.all_points())
+                    if c not in self.results and c not in seen]
+            for i in self.rng.permutation(len(rest))[:self.batch - len(props)]:
+                seen.add(rest[i])
+                props.append(rest[i])
+                used.append(0)   # credited to uniform random
+        if not props:
+            return 0
+        got = self.evaluate(props)
+        for c, r in got.items():
+            self.results[c] = r
+        for c, k in zip(props, used):
+            better = self.feasible(c) and self.results[c].ms < self.results[self.best].ms
+            if better:
+                self.best = c
+                self.best_point = self.space.point(c)
+            self.bandit.credit(k, better)
+        for c in got:   # extra configurations the batched evaluator scored
+            if c not in seen and self.space.contains(c) and self.feasible(c) and \
+                    self.results[c].ms < self.results[self.best].ms:
+                self.best, self.best_point = c, self.space.point(c)
+        self.trace.append((len(self.results), time.perf_counter() - self.t0, self.speedup(self.best)))
+        return len(got)
+
+    def run(self, evaluations: int | None = None, seconds: float | None = None):
+        idle = 0
+        while idle < 8:   # eight batches without a new point: the space is exhausted
+            if evaluations is not None and len(self.results) >= evaluations:
+                break
+            if seconds is not None and time.perf_counter() - self.t0 >= seconds:
+                break
+            idle = idle + 1 if self.step() == 0 else 0
+        return self
+
+    def report(self) -> dict:
+        b = self.best
+        return {"mode": self.space.mode, "log10_space": round(self.space.log10_size(), 2),
+                "evaluations": len(self.results), "seconds": round(time.perf_counter() - self.t0, 3),
+                "baseline": dataclasses.asdict(self.baseline), "baseline_accuracy": self.base_result.accuracy,
+                "baseline_ms": self.base_result.ms, "qos_target": self.target,
+                "best": dataclasses.asdict(b), "best_accuracy": self.results[b].accuracy,
+                "best_ms": self.results[b].ms, "speedup": self.speedup(b),
+                "techniques": {t.name: sum(1 for k, _ in self.bandit.history if k == i)
+                               for i, t in enumerate(self.bandit.techniques)},
+                "running_best": [list(map(lambda v: round(v, 4), t)) for t in _thin(self.trace, 24)]}
+
+
+def _thin(trace, n):
+    if len(trace) <= n:
+        return trace
+    idx = sorted(set(np.linspace(0, len(trace) - 1, n).round().astype(int).tolist()))
+    return [trace[i] for i in idx]
+
+
+# ---------------------------------------------------------- GPU evaluator
+class GpuEvaluator:
+    """Trained snapshots per (enc, dim, epochs), validation hypervectors per
+    (enc, dim), and measured cost tables; scores configurations through
+    hdc_sweep_eval and prices them from the tables."""
+
+    def __init__(self, workload: str, max_epochs: int, dims, n_train=None, n_val=None, device="cuda",
+                 reps: int = 5):
+        import torch
+        from . import hdc, synth
+        self.torch, self.hdc = torch, hdc
+        self.w = w = synth.WORKLOADS[workload] if isinstance(workload, str) else workload
+        d = synth.make(w, n_train=n_train, n_query=n_val)
+        dev = torch.device(device)
+        self.dev, self.reps = dev, reps
+        self.Bt = torch.from_numpy(d["Bt"]).to(dev)
+        self.Xtr = torch.from_numpy(d["Xtr"]).to(dev)
+        self.ytr = torch.from_numpy(d["ytr"]).to(dev)
+        self.Xv = torch.from_numpy(d["Xq"]).to(dev)
+        self.yv = torch.from_numpy(d["yq"]).to(dev)
+        self.max_epochs, self.dims = max_epochs, tuple(dims)
+        self.snap, self.Hv = {}, {}
+        self.t_encode_train, self.t_train = {}, {}
+        self.t_classify = {}
+        self.sweep_launches = 0
+        self._prepare()
+
+    def _ms(self, fn) -> float:
+        torch = self.torch
+        fn()
+        ts = []
+        for _ in range(self.reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    def _prepare(self):
+        torch, hdc, w = self.torch, self.hdc, self.w
+        N = self.Xtr.shape[0]
+        for enc in ENCS:
+            for dim in self.dims:
+                base = hdc.Model(self.Bt[:dim], hdc.ApproxConfig(enc=enc))
+                ws = base.workspace(N)
+                Htr = torch.empty((N, base.W), dtype=torch.int32, device=self.dev)
+                self.t_encode_train[(enc, dim)] = self._ms(lambda: hdc.encode(self.Xtr, base, ws=ws, out=Htr))
+                n = ctypes.c_size_t()
+                hdc._call("hdc_train_workspace_bytes", N, dim, w.C, ctypes.byref(n))
+                tws = hdc._empty_bytes(n.value, self.dev)
+                acc = torch.empty((w.C, dim), dtype=torch.int32, device=self.dev)
+                cls = torch.empty((w.C, hdc.words(dim)), dtype=torch.int32, device=self.dev)
+                # training as the application runs it: bundling, then epochs;
+                # each pass timed, the accumulators kept after each
+                for rep in range(2):   # the first run warms up
+                    times = []
+                    for ep in range(self.max_epochs + 1):
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record()
+                        hdc.train_epoch(Htr, self.ytr, dim, w.C, 0 if ep == 0 else 1, acc, cls, ws=tws)
+                        b.record()
+                        if rep:
+                            self.snap[(enc, dim, ep)] = acc.clone()
+                        times.append((a, b))
+                    torch.cuda.synchronize()
+                cum = np.cumsum([a.elapsed_time(b) for a, b in times])
+                for ep in range(self.max_epochs + 1):
+                    self.t_train[(enc, dim, ep)] = float(cum[ep])
+                self.Hv[(enc, dim)] = hdc.encode(self.Xv, base)
+        torch.cuda.synchronize()
+
+    def classify_ms(self, c: Config) -> float:
+        hdc, torch = self.hdc, self.torch
+        cfg = hdc.ApproxConfig(enc=c.enc, class_bits=c.bits, perf_start=c.start, perf_end=c.end,
+                               perf_stride=c.stride)
+        Dk = hdc.kept_dims(c.dim, cfg)
+        key = (c.enc, Dk, c.bits)
+        if key not in self.t_classify:
+            model = hdc.Model(self.Bt[:c.dim], cfg, acc=self.snap[(c.enc, c.dim, 0)])
+            ws = model.workspace(self.Xv.shape[0])
+            lab = torch.empty(self.Xv.shape[0], dtype=torch.int32, device=self.dev)
+            self.t_classify[key] = self._ms(lambda: hdc.classify(self.Xv, model, ws=ws, labels=lab))
+        return self.t_classify[key]
+
+    def ms(self, c: Config) -> float:
+        return self.t_encode_train[(c.enc, c.dim)] + self.t_train[(c.enc, c.dim, c.epochs)] + self.classify_ms(c)
+
+    def accuracy(self, configs) -> dict:
+        """Accuracy of every (entry, width) the batch's sweeps score: the
+        proposals and, for free, their entries under the other widths."""
+        hdc = self.hdc
+        N = self.Xv.shape[0]
+        groups = {}
+        for c in configs:
+            groups.setdefault((c.enc, c.dim, c.epochs), set()).add((c.start, c.end, c.stride))
+        pending = []
+        for (enc, dim, ep), entries in groups.items():
+            entries = sorted(entries)
+            for i in range(0, len(entries), 6):
+                chunk = entries[i:i + 6]
+                sw = hdc.Sweep(dim, self.w.C, [e[2] for e in chunk], BITS, N, self.dev,
+                               starts=[e[0] for e in chunk], ends=[e[1] for e in chunk])
+                sw(self.Hv[(enc, dim)], self.yv, self.snap[(enc, dim, ep)])
+                self.sweep_launches += 1
+                pending.append((enc, dim, ep, chunk, sw.correct))
+        out = {}
+        for enc, dim, ep, chunk, corr in pending:
+            corr = corr.cpu().numpy()
+            for jb, b in enumerate(BITS):
+                for j, (s, e, st) in enumerate(chunk):
+                    out[Config(enc, dim, ep, s, e, st, b)] = float(corr[jb, j]) / N
+        return out
+
+    def __call__(self, configs) -> dict:
+        acc = self.accuracy(configs)
+        return {c: Result(a, self.ms(c)) for c, a in acc.items()}
+
+
+def baseline_config(D: int, max_epochs: int) -> Config:
+    """The unapproximated application: fp32 encoding at the full D, every
+    retraining epoch, no perforation, the widest class width (8-bit cosine)."""
+    return Config("fp32", D, max_epochs, 0.0, 1.0, 1, 8)
+
+
+def main(argv=None):
+    import argparse
+    ap = argparse.ArgumentParser(description="approximation tuner over the batched evaluator")
+    ap.add_argument("--workload", default="sweep_F561_D10000_C6")
+    ap.add_argument("--epochs", type=int, default=10, help="TRAIN_ITERATIONS of the baseline (the knob's max)")
+    ap.add_argument("--qos-drop", type=float, default=0.05)
+    ap.add_argument("--evaluations", type=int, default=3000, help="budget per pruning mode")
+    ap.add_argument("--seconds", type=float, default=None, help="time budget per pruning mode")
+    ap.add_argument("--modes", default=",".join(MODES))
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args(argv)
+    from . import hdc, synth
+    hdc.load()
+    w = synth.WORKLOADS[a.workload]
+    t = time.perf_counter()
+    dims = Space("none", w.D, a.epochs).values["dim"]
+    ev = GpuEvaluator(a.workload, a.epochs, dims)
+    prep = time.perf_counter() - t
+    reports = []
+    for mode in a.modes.split(","):
+        s = Search(Space(mode, w.D, a.epochs), ev, baseline_config(w.D, a.epochs), a.qos_drop, a.seed)
+        reports.append(s.run(a.evaluations, a.seconds).report())
+    print(json.dumps({"workload": a.workload, "prepare_s": round(prep, 3), "sweep_launches": ev.sweep_launches,
+                      "classify_cost_entries": len(ev.t_classify), "modes": reports}))
+
+
+if __name__ == "__main__":
+    main()

@@ -89,3 +89,39 @@ def test_static_scratch_size_matches_header(lib):
     src = open(os.path.join(ROOT, "include", "hdc.h")).read()
     m = re.search(r"#define HDC_STATIC_SCRATCH_BYTES \(\(size_t\)(\d+) << (\d+)\)", src)
     assert m and int(m.group(1)) << int(m.group(2)) == hdc.STATIC_SCRATCH_BYTES
+
+
+def test_sweep_spec_layout_matches_header(lib):
+    """The binding's hdc_sweep_spec fields are the header's, in order."""
+    from paper_2606_26547_gb300 import hdc
+    src = open(os.path.join(ROOT, "include", "hdc.h")).read()
+    body = re.search(r"typedef struct \{([^}]*)\} hdc_sweep_spec;", src).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"\b([a-z_]+)\s*(?:\[[A-Z_]+\])?\s*;", body)
+    assert names == [f[0] for f in hdc.SweepSpecC._fields_]
+
+
+def test_sweep_spec_checks_without_gpu(lib):
+    """Entry extents: start in [0, 1), end in (0, 1] (0 = 1.0), and at least
+    one kept dim (floor(end*D) > floor(start*D)); strides powers of two <= 32."""
+    from paper_2606_26547_gb300 import hdc
+    n = ctypes.c_size_t()
+
+    def ok(D, strides, bits=(1,), **kw):
+        spec = hdc.sweep_spec(strides, bits, **kw)
+        return lib.hdc_sweep_workspace_bytes(D, 10, ctypes.byref(spec), ctypes.byref(n)) == 0
+
+    assert ok(10000, (1, 2, 4, 8, 16, 32))
+    assert ok(10000, (1, 2), ends=(0.5, 0.0), starts=(0.25, 0.9))
+    assert ok(100, (1,), starts=(0.0,), ends=(0.015,))          # e0 = 1: dim 0 only
+    assert not ok(100, (1,), starts=(0.0,), ends=(0.001,))      # e0 = 0: nothing kept
+    assert not ok(100, (1,), starts=(0.5,), ends=(0.505,))      # e0 == s0
+    assert not ok(100, (1,), starts=(1.0,))
+    assert not ok(100, (1,), starts=(-0.1,))
+    assert not ok(100, (1,), ends=(1.5,))
+    assert not ok(100, (3,))
+    assert not ok(100, (64,))
+    assert not ok(100, (1,), bits=(2,))
+    spec = hdc.sweep_spec((1,) * 6, (1,))
+    spec.n_strides = 7
+    assert lib.hdc_sweep_workspace_bytes(100, 10, ctypes.byref(spec), ctypes.byref(n)) == 1

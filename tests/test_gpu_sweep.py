@@ -116,3 +116,44 @@ def test_batched_sweep_graph_equals_eager(hdc):
     assert bs.results() == eager
     assert len(eager) == 2 * 3 * 12 + 4
     assert hdc.stream_status() == 0
+
+
+@pytest.mark.parametrize("enc", ["fp8", "fp32"])
+def test_sweep_entries_with_extents_equal_classify(hdc, trained, enc):
+    """Entries (start, end, stride): kept dims d = s0 + k*stride < e0, as
+    hdc_classify's perforation (start, end, stride); odd starts shift the
+    stride's bit pattern inside each word."""
+    w, d, Bt, out = trained
+    m = out[enc]
+    yv = torch.from_numpy(d["yq"]).to(Bt.device)
+    cases = [((1, 2, 4, 1, 8, 2), (0.0, 0.0, 0.0, 0.0, 0.0, 0.0), (0.5, 0.75, 1.0, 0.33, 0.9, 0.031)),
+             ((8, 32, 2, 1, 16, 4), (0.013, 0.1, 0.25, 0.5, 0.0071, 0.9), (1.0, 0.95, 0.6, 0.52, 0.4, 1.0))]
+    for strides, starts, ends in cases:
+        sw = hdc.Sweep(w.D, w.C, strides, (1, 8), d["Xq"].shape[0], Bt.device, keep_labels=True, ends=ends,
+                       starts=starts)
+        correct = sw(m["H"], yv, m["acc"]).cpu().numpy()
+        for jb, b in enumerate((1, 8)):
+            for i, (s, a, e) in enumerate(zip(strides, starts, ends)):
+                model = hdc.Model(Bt, hdc.ApproxConfig(enc=enc, class_bits=b, perf_start=a, perf_end=e,
+                                                       perf_stride=s), acc=m["acc"])
+                ref = hdc.classify(m["Xv"], model).cpu().numpy()
+                assert np.array_equal(sw.labels[jb, i].cpu().numpy(), ref), (enc, b, s, a, e)
+                assert correct[jb, i] == int((ref == d["yq"]).sum())
+
+
+def test_sweep_extent_control_vs_oracle(hdc, trained):
+    """Unquantised-accumulator cosine over (start, end, stride) entries
+    against the oracle's kept dims and cosine arg-max."""
+    w, d, Bt, out = trained
+    m = out["bf16"]
+    yv = torch.from_numpy(d["yq"]).to(Bt.device)
+    strides, starts, ends = (1, 4, 32, 2), (0.2, 0.031, 0.0, 0.5), (0.7, 1.0, 1.0, 0.51)
+    sw = hdc.Sweep(w.D, w.C, strides, (0,), d["Xq"].shape[0], Bt.device, keep_labels=True, ends=ends,
+                   starts=starts)
+    sw(m["H"], yv, m["acc"])
+    qbits = unpack(m["H"].cpu().numpy().view(np.uint32), w.D)
+    acc = m["acc"].cpu().numpy().astype(np.int64)
+    for i, (s, a, e) in enumerate(zip(strides, starts, ends)):
+        dims = orc.kept_dims(w.D, float(np.float32(a)), float(np.float32(e)), s)
+        ref = orc.argmax(orc.cosine_scores(orc.gather_cols(qbits, dims), orc.gather_cols(acc, dims)))
+        assert np.array_equal(sw.labels[0, i].cpu().numpy(), ref), (s, a, e)
