@@ -471,7 +471,7 @@ def baseline_config(D: int, max_epochs: int) -> Config:
 def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description="approximation tuner over the batched evaluator")
-    ap.add_argument("--workload", default="sweep_F561_D10000_C6")
+    ap.add_argument("--workload", default="classify_F617_D2048_C26")
     ap.add_argument("--epochs", type=int, default=10, help="TRAIN_ITERATIONS of the baseline (the knob's max)")
     ap.add_argument("--qos-drop", type=float, default=0.05)
     ap.add_argument("--evaluations", type=int, default=3000, help="budget per pruning mode")
