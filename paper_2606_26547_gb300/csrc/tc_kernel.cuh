@@ -22,7 +22,11 @@
 //   warps 0-3      epilogue: tcgen05.ld of the thread's row (TMEM lane),
 //                  32 columns at a time -> one packed word, releases the
 //                  accumulator, then popcounts against the class words
-//                  (CMAX register counters per query).
+//                  (CMAX register counters per query).  With EWG = 2 or 4
+//                  epilogue warpgroups (classify, C > 16) each warpgroup
+//                  packs 8/EWG of the tile's 8 words, the words are
+//                  exchanged through shared memory, and warpgroup g counts
+//                  the g-th of EWG equal class ranges.
 // Every wait is bounded by the global timer; on expiry the kernel records
 // status 1 in g_tc_status, stops its loops, drains its own copies and MMAs
 // (again with a bound), frees TMEM and returns.
@@ -45,14 +49,24 @@ constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BKB;            // 16 KB
 constexpr int B_BYTES = BN * BKB;            // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-// threads: 4*EWG epilogue warps (EWG = 1 or 2 warpgroups), a TMA warp, an MMA warp
+// threads: 4*EWG epilogue warps (EWG = 1, 2 or 4 warpgroups), a TMA warp, an MMA warp
 __host__ __device__ constexpr int num_threads(int ewg) { return (4 * ewg + 2) * 32; }
 constexpr int TMEM_COLS = 2 * BN;            // two accumulators
 // class-word ring (classify): the 8 words of every class for one 256-dim tile
 constexpr int CBUF = 4, CLS_BYTES = 128 * 32;
-// full, empty, tfull[2], tempty[2], done, merge_full, merge_empty, cfull[CBUF], cempty[CBUF]
-constexpr int NUM_BARS = 2 * STAGES + 7 + 2 * CBUF;
-constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + CBUF * CLS_BYTES + NUM_BARS * 8 + 16 + 2 * BM * 4;
+// sign words exchanged between epilogue warpgroups: WXB buffers of [8 words][BM rows]
+constexpr int WXB = 2;
+// full, empty, tfull[2], tempty[2], done, merge_full, merge_empty, cfull[CBUF], cempty[CBUF], wfull[WXB]
+constexpr int NUM_BARS = 2 * STAGES + 7 + 2 * CBUF + WXB;
+// dynamic shared memory: 1 KB alignment slack, stages, class ring, barriers,
+// TMEM slot + abort flag, per-row minimum and class of warpgroups 1..EWG-1,
+// exchanged words
+__host__ __device__ constexpr size_t smem_bytes(int ewg)
+{
+    return 1024 + (size_t)STAGES * STAGE_BYTES + CBUF * CLS_BYTES + NUM_BARS * 8 + 16 +
+           (size_t)2 * BM * 4 * (ewg > 1 ? ewg - 1 : 1) + (ewg > 1 ? (size_t)WXB * 8 * BM * 4 : 0);
+}
+static_assert(smem_bytes(4) <= 232448, "shared memory of the four-warpgroup kernel");
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
 
 struct Params {
@@ -210,10 +224,13 @@ __device__ __forceinline__ uint32_t pack_signs(const uint32_t (&r)[32])
 }
 
 // ------------------------------------------------------------------ kernel
-// EWG = 2 (classify only): two epilogue warpgroups read the same TMEM lanes
-// and pack the same words; warpgroup g counts classes [g*CMAX, (g+1)*CMAX),
-// and warpgroup 1 hands its per-row minimum to warpgroup 0 through shared
-// memory (an mbarrier pair with bounded waits), which keeps the lower class
+// EWG = 2 or 4 (classify only): the epilogue warpgroups read the same TMEM
+// lanes, warpgroup g the columns of words [g*8/EWG, (g+1)*8/EWG); every
+// thread publishes its words to shared memory and, after an mbarrier that
+// all epilogue threads arrive on (bounded wait), reads the row's 8 words.
+// Warpgroup g counts classes [g*CP, (g+1)*CP), CP = ceil(C/EWG) <= CMAX,
+// and warpgroups 1..EWG-1 hand their per-row minimum to warpgroup 0 through
+// shared memory (an mbarrier pair with bounded waits), which keeps the lower class
 // index on ties.
 template <int ENC, int CMAX, bool CLASSIFY, int EWG>
 __global__ void __launch_bounds__(num_threads(EWG), 1)
@@ -236,9 +253,14 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
     const uint32_t merge_full = su32(bars + 2 * STAGES + 5), merge_empty = su32(bars + 2 * STAGES + 6);
     auto cfull = [&](int b) { return su32(bars + 2 * STAGES + 7 + b); };
     auto cempty = [&](int b) { return su32(bars + 2 * STAGES + 7 + CBUF + b); };
-    int32_t *s_val = reinterpret_cast<int32_t *>(tmem_slot + 4);  // warpgroup 1's per-row minimum
-    int32_t *s_idx = s_val + BM;                                    // and its class
+    auto wfull = [&](int b) { return su32(bars + 2 * STAGES + 7 + 2 * CBUF + b); };
+    constexpr int NMRG = EWG > 1 ? EWG - 1 : 1;
+    int32_t *s_val = reinterpret_cast<int32_t *>(tmem_slot + 4);  // per-row minimum of warpgroups 1..EWG-1
+    int32_t *s_idx = s_val + NMRG * BM;                             // and its class
+    uint32_t *s_words = reinterpret_cast<uint32_t *>(s_idx + NMRG * BM);  // WXB x [8][BM]
     constexpr int PRODUCER = 4 * EWG, ISSUER = 4 * EWG + 1;
+    constexpr int WPG = (BN / 32) / EWG;  // words packed by each epilogue warpgroup
+    static_assert(EWG == 1 || (CLASSIFY && (EWG == 2 || EWG == 4)), "several epilogue warpgroups: classify only");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t num_m_tiles = (p.N + BM - 1) / BM;
@@ -255,12 +277,13 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
             mbar_init(tempty(a), BM * EWG);
         }
         mbar_init(done_bar, 1);
-        mbar_init(merge_full, BM);
+        mbar_init(merge_full, BM * NMRG);
         mbar_init(merge_empty, BM);
         for (int b = 0; b < CBUF; b++) {
             mbar_init(cfull(b), 1);
             mbar_init(cempty(b), BM * EWG);
         }
+        for (int b = 0; b < WXB; b++) mbar_init(wfull(b), BM * EWG);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -353,13 +376,16 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
     } else {  // ------------------------------------ epilogue warps 0 .. 4*EWG-1
         const int q = warp & 3;             // TMEM lane quarter of this warp
         const int g = warp >> 2;            // epilogue warpgroup
-        const int c0 = g * CMAX;            // first class this warpgroup counts
-        int acc = 0, cb = 0;
-        uint32_t aphase = 0, cph = 0;
+        const int r = q * 32 + lane;        // row of the tile (TMEM lane)
+        const int cper = (p.C + EWG - 1) / EWG;
+        const int c0 = g * cper;            // classes [c0, c1) counted by this warpgroup
+        const int c1 = min(c0 + cper, p.C);
+        int acc = 0, cb = 0, wb = 0;
+        uint32_t aphase = 0, cph = 0, wph = 0;
         bool ab = false;
         int64_t it = 0;
         for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++) {
-            const int64_t row = mt * BM + q * 32 + lane;
+            const int64_t row = mt * BM + r;
             const bool valid = row < p.N;
             int dist[CLASSIFY ? CMAX : 1];
 #pragma unroll
@@ -371,23 +397,36 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
                 tc_fence_after();
                 uint32_t words[BN / 32];
 #pragma unroll
-                for (int j = 0; j < BN / 32; j++) {
-                    uint32_t r[32];
-                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + j * 32), r);
+                for (int j = 0; j < WPG; j++) {
+                    uint32_t v[32];
+                    const int jw = g * WPG + j;   // word of the tile
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + jw * 32), v);
                     if (!CLASSIFY && p.scores && valid) {
                         const float rs = p.sx ? p.sx[row] : 1.f;
 #pragma unroll
                         for (int i = 0; i < 32; i++) {
-                            const int col = nt * BN + j * 32 + i;
+                            const int col = nt * BN + jw * 32 + i;
                             if (col < p.Dk)
-                                p.scores[row * p.Dk + col] = __uint_as_float(r[i]) * rs * (p.sb ? p.sb[col] : 1.f);
+                                p.scores[row * p.Dk + col] = __uint_as_float(v[i]) * rs * (p.sb ? p.sb[col] : 1.f);
                         }
                     }
-                    words[j] = pack_signs(r);
+                    words[j] = pack_signs(v);
                 }
                 tc_fence_before();
                 mbar_arrive(tempty(acc));
                 if (++acc == 2) { acc = 0; aphase ^= 1; }
+                if (EWG > 1) {
+                    // publish this warpgroup's words, then read the row's 8
+                    uint32_t *sw = s_words + (size_t)wb * 8 * BM;
+#pragma unroll
+                    for (int j = 0; j < WPG; j++) sw[(g * WPG + j) * BM + r] = words[j];
+                    mbar_arrive(wfull(wb));
+                    const bool okw = mbar_wait(wfull(wb), wph, abort_flag);
+                    if (!__all_sync(0xffffffffu, okw)) { ab = true; break; }
+#pragma unroll
+                    for (int j = 0; j < BN / 32; j++) words[j] = sw[j * BM + r];
+                    if (++wb == WXB) { wb = 0; wph ^= 1; }
+                }
                 const int gw0 = nt * (BN / 32);
                 if (CLASSIFY) {
                     // this tile's 8 words of every class, staged by the TMA
@@ -398,7 +437,7 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
                     const uint4 *sc = reinterpret_cast<const uint4 *>(sCls + cb * CLS_BYTES);
 #pragma unroll
                     for (int c = 0; c < CMAX; c++)
-                        if (c0 + c < p.C) {
+                        if (c0 + c < c1) {
                             const uint4 ca = sc[2 * (c0 + c)], cc = sc[2 * (c0 + c) + 1];
                             dist[c] += __popc(words[0] ^ ca.x) + __popc(words[1] ^ ca.y) + __popc(words[2] ^ ca.z) +
                                        __popc(words[3] ^ ca.w) + __popc(words[4] ^ cc.x) + __popc(words[5] ^ cc.y) +
@@ -416,23 +455,25 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
                 int best = c0, bv = 0x7fffffff;
 #pragma unroll
                 for (int c = 0; c < CMAX; c++)
-                    if (c0 + c < p.C) {
+                    if (c0 + c < c1) {
                         if (p.dists && valid) p.dists[row * p.C + c0 + c] = dist[c];
                         if (dist[c] < bv) { bv = dist[c]; best = c0 + c; }
                     }
-                const int r = q * 32 + lane;
-                if (EWG == 2) {
+                if (EWG > 1) {
                     const uint32_t par = (uint32_t)(it & 1);
-                    if (g == 1) {
+                    if (g > 0) {
                         if (!mbar_wait(merge_empty, par ^ 1, abort_flag)) { ab = true; break; }
-                        s_val[r] = bv;
-                        s_idx[r] = best;
+                        s_val[(g - 1) * BM + r] = bv;
+                        s_idx[(g - 1) * BM + r] = best;
                         mbar_arrive(merge_full);
                     } else {
                         if (!mbar_wait(merge_full, par, abort_flag)) { ab = true; break; }
-                        const int v1 = s_val[r], i1 = s_idx[r];
+#pragma unroll
+                        for (int h = 0; h < EWG - 1; h++) {  // ascending class ranges: ties keep the lower
+                            const int v1 = s_val[h * BM + r], i1 = s_idx[h * BM + r];
+                            if (v1 < bv) { bv = v1; best = i1; }
+                        }
                         mbar_arrive(merge_empty);
-                        if (v1 < bv) { bv = v1; best = i1; }  // ties keep the lower class range
                     }
                 }
                 if (g == 0 && valid) p.labels[row] = best;
@@ -454,9 +495,10 @@ static cudaError_t launch_one(const CUtensorMap &ma, const CUtensorMap &mb, cons
                               unsigned grid, cudaStream_t st)
 {
     auto k = tc_encode_kernel<ENC, CMAX, CLASSIFY, EWG>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    constexpr size_t smem = smem_bytes(EWG);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, num_threads(EWG), SMEM_BYTES, st>>>(ma, mb, mc, p);
+    k<<<grid, num_threads(EWG), smem, st>>>(ma, mb, mc, p);
     return cudaGetLastError();
 }
 
@@ -465,11 +507,12 @@ static cudaError_t launch_enc(const CUtensorMap &ma, const CUtensorMap &mb, cons
                               unsigned grid, bool classify, cudaStream_t st)
 {
     if (!classify) return launch_one<ENC, 1, false, 1>(ma, mb, mc, p, grid, st);
-    // up to 16 classes: one epilogue warpgroup; more: two, each counting half
+    // up to 16 classes: one epilogue warpgroup; up to 32: two; more: four,
+    // each counting ceil(C / EWG) <= CMAX classes
     if (p.C <= 16) return launch_one<ENC, 16, true, 1>(ma, mb, mc, p, grid, st);
     if (p.C <= 32) return launch_one<ENC, 16, true, 2>(ma, mb, mc, p, grid, st);
-    if (p.C <= 64) return launch_one<ENC, 32, true, 2>(ma, mb, mc, p, grid, st);
-    return launch_one<ENC, 64, true, 2>(ma, mb, mc, p, grid, st);
+    if (p.C <= 64) return launch_one<ENC, 16, true, 4>(ma, mb, mc, p, grid, st);
+    return launch_one<ENC, 32, true, 4>(ma, mb, mc, p, grid, st);
 }
 
 // Read and clear this translation unit's device status word.

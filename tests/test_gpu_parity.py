@@ -254,7 +254,8 @@ def test_classify_edge_cases(hdc):
 # ------------------------------------------- tensor-core path specifics
 
 @pytest.mark.parametrize("enc", ["bf16", "fp8"])
-@pytest.mark.parametrize("C,bits_", [(1, 1), (17, 1), (65, 4), (100, 1), (128, 8), (33, 8)])
+@pytest.mark.parametrize("C,bits_", [(1, 1), (16, 1), (17, 1), (32, 1), (33, 1), (64, 1), (65, 1), (100, 1),
+                                      (128, 1), (65, 4), (128, 8), (33, 8)])
 def test_tc_classify_matches_oracle_many_classes(hdc, enc, C, bits_):
     """Class counts across every register block of the fused epilogue."""
     rng = np.random.default_rng(C * 10 + bits_)
@@ -271,6 +272,43 @@ def test_tc_classify_matches_oracle_many_classes(hdc, enc, C, bits_):
         assert np.array_equal(sims.cpu().numpy().astype(np.int64), osim)
     else:
         assert np.array_equal(sims.cpu().numpy(), osim)
+
+
+@pytest.mark.parametrize("C", [20, 50, 100])
+def test_tc_classify_ties_across_warpgroups(hdc, C):
+    """Equal class hypervectors in every warpgroup's class range: each query
+    takes the lowest class index among its nearest."""
+    rng = np.random.default_rng(C)
+    F, D, N = 128, 777, 300
+    X = rng.integers(-8, 8, (N, F)).astype(np.float32)
+    Bt = (1 - 2 * rng.integers(0, 2, (D, F))).astype(np.float32)
+    base = rng.integers(-50, 51, (3, D))
+    acc = base[rng.integers(0, 3, C)]          # only three distinct classes
+    acc[-1] = base[0]
+    model = hdc.Model(T(Bt), hdc.ApproxConfig(enc="fp8"), acc=T(acc.astype(np.int32)))
+    labels, dists = hdc.classify(T(X), model, sims=True)
+    ol, od = orc.classify(X, Bt, acc.astype(np.int64), orc.ENC_FP32, 0.0, 1.0, 1, 1, integer=True)
+    assert np.array_equal(labels.cpu().numpy(), ol)
+    assert np.array_equal(dists.cpu().numpy().astype(np.int64), od)
+
+
+@pytest.mark.parametrize("C", [10, 30, 60, 100])
+def test_tc_classify_many_tiles_matches_simt(hdc, C):
+    """Persistent fused classify over more query tiles than SMs, every
+    epilogue width, against the FFMA encoder + similarity kernel."""
+    rng = np.random.default_rng(C + 5)
+    F, D, N = 96, 1000, 152 * 128 * 2 + 77
+    X = rng.integers(-8, 8, (N, F)).astype(np.float32)
+    Bt = (1 - 2 * rng.integers(0, 2, (D, F))).astype(np.float32)
+    acc = rng.integers(-200, 201, (C, D)).astype(np.int32)
+    m_tc = hdc.Model(T(Bt), hdc.ApproxConfig(enc="fp8"), acc=T(acc))
+    m_si = hdc.Model(T(Bt), hdc.ApproxConfig(enc="fp8", simt=True), acc=T(acc))
+    Xd = T(X)
+    l_tc, d_tc = hdc.classify(Xd, m_tc, sims=True)
+    l_si, d_si = hdc.classify(Xd, m_si, sims=True)
+    assert torch.equal(l_tc, l_si) and torch.equal(d_tc, d_si)
+    torch.cuda.synchronize()
+    assert hdc.stream_status() == 0
 
 
 @pytest.mark.parametrize("enc", ["bf16", "fp8"])
