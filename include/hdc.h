@@ -256,6 +256,37 @@ hdc_status hdc_sweep_eval(const uint32_t *H, const int32_t *y, int64_t N, int32_
                           int32_t *correct, int32_t *labels, void *ws, size_t ws_bytes,
                           hdc_stream_t stream);
 
+/* HD-Clustering (Sec. 5.1): K-means over binary hypervectors.  The paper's
+ * benchmark clusters encoded points with K cluster hypervectors, refining
+ * them for TRAIN_ITERATIONS iterations, and scores the result by NMI; its
+ * two similarity ops (training and inference) are tuned independently.
+ * One iteration:
+ *   assign  label[n] = arg-min_k Hamming(H[n], cls[k]) over the kept dims of
+ *           train_sim's perforation (lowest k on ties);
+ *   update  acc[k] = sum over the members n of (1 - 2*bit_n) over all D,
+ *           cls[k] = (acc[k] < 0) -- a cluster without members becomes all
+ *           +1 (bit 0), as sign(0) = +1.
+ * After `iters` iterations, labels = the assignment under infer_sim.
+ *   H        N x W(D) packed point hypervectors (device, 16-byte aligned)
+ *   cls      K x W(D) packed cluster hypervectors: the initial ones on
+ *            entry (e.g. K distinct points), the final ones on return
+ *   acc      K x D int32 (out): the accumulators of the last update
+ *            (untouched when iters = 0)
+ *   labels   N int32 (out)
+ *   changes  optional int32[iters] (out): points whose cluster differs
+ *            from the previous iteration's (iteration 0: N)
+ *   train_sim, infer_sim  perforation (perf_start, perf_end, perf_stride)
+ *            of the two similarity ops; NULL = all D; class_bits must be 1
+ *            (enc is not used)
+ *   ws       hdc_cluster_workspace_bytes(N, D, K) bytes, 256-byte aligned
+ * Errors: HDC_ERR_INVALID_ARG (sizes, pointers, a perforation that keeps
+ * nothing), HDC_ERR_WORKSPACE, HDC_ERR_CUDA.                               */
+hdc_status hdc_cluster_workspace_bytes(int64_t N, int32_t D, int32_t K, size_t *bytes);
+hdc_status hdc_cluster(const uint32_t *H, int64_t N, int32_t D, int32_t K, int32_t iters,
+                       const hdc_approx_config *train_sim, const hdc_approx_config *infer_sim,
+                       uint32_t *cls, int32_t *acc, int32_t *labels, int32_t *changes, void *ws,
+                       size_t ws_bytes, hdc_stream_t stream);
+
 /* Size of the fixed scratch array behind hdc_classify_static.              */
 #define HDC_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
 

@@ -269,6 +269,34 @@ def train(bits: np.ndarray, y: np.ndarray, C: int, epochs: int):
     return acc, ups
 
 
+def kmeans(bits: np.ndarray, init: np.ndarray, iters: int, train_perf=(0.0, 1.0, 1),
+           infer_perf=(0.0, 1.0, 1)):
+    """HD-Clustering (Sec. 5.1): K-means over binary hypervectors.
+
+    bits: N x D unpacked point bits; init: K x D initial cluster bits.  Each
+    of ``iters`` iterations assigns every point to the nearest cluster
+    (Hamming over the kept dims of ``train_perf`` = (start, end, stride),
+    arg-min, lowest index on ties), then re-forms each cluster as the bundle
+    of its members over all D (sign of the sum; no members -> zero sum -> all
+    +1, bit 0).  The final labels use the kept dims of ``infer_perf``.
+    Returns (labels, cluster bits, acc of the last update or None, changes).
+    """
+    bits = _c(bits, np.uint8)
+    cb = _c(init, np.uint8).copy()
+    K, D = cb.shape
+    tdims = kept_dims(D, *train_perf)
+    idims = kept_dims(D, *infer_perf)
+    prev, acc, changes = None, None, []
+    for _ in range(iters):
+        lab = argmin(hamming(gather_cols(bits, tdims), gather_cols(cb, tdims)))
+        changes.append(bits.shape[0] if prev is None else int((lab != prev).sum()))
+        prev = lab
+        acc = bundle(bits, lab, K)
+        cb = class_bits(acc)
+    labels = argmin(hamming(gather_cols(bits, idims), gather_cols(cb, idims)))
+    return labels, cb, acc, changes
+
+
 def classify(X: np.ndarray, Bt: np.ndarray, acc: np.ndarray, enc: int = ENC_FP32,
              start: float = 0.0, end: float = 1.0, stride: int = 1, class_bits_: int = 1,
              integer: bool = False, threads: int = 1):

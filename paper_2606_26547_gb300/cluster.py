@@ -1,0 +1,100 @@
+"""HD-Clustering driver (Sec. 5.1 / 5.2): encode every point, run K-means
+over the binary hypervectors (hdc_cluster), score the clusters by NMI.
+
+Knobs: element type of the encoding, dimensionality D' (first D' rows of
+the base hypermatrix), TRAIN_ITERATIONS (K-means iterations), and the two
+independently perforated similarity ops (assignment during training,
+final assignment at inference)."""
+from __future__ import annotations
+
+import dataclasses
+import json
+
+import numpy as np
+import torch
+
+from . import hdc, metrics, synth
+
+
+@dataclasses.dataclass(frozen=True)
+class ClusterConfig:
+    enc: str = "fp32"
+    dim: int = 1024
+    iters: int = 20
+    train_perf: tuple = (0.0, 1.0, 1)
+    infer_perf: tuple = (0.0, 1.0, 1)
+
+
+def _sim(p):
+    return hdc.ApproxConfig(perf_start=p[0], perf_end=p[1], perf_stride=p[2])
+
+
+class ClusterRun:
+    """Device-resident points of one workload; run(cfg) encodes and clusters."""
+
+    def __init__(self, workload: str = "cluster_F617_D1024_K26", device="cuda"):
+        self.w = w = synth.WORKLOADS[workload] if isinstance(workload, str) else workload
+        d = synth.make(w)
+        self.dev = torch.device(device)
+        self.Bt = torch.from_numpy(d["Bt"]).to(self.dev)
+        self.X = torch.from_numpy(d["Xq"]).to(self.dev)
+        self.y = d["yq"]
+        self.init_idx = torch.from_numpy(synth.cluster_init(self.X.shape[0], w.C, w.seed)).to(self.dev)
+        self._models = {}
+
+    def model(self, enc: str, dim: int):
+        key = (enc, dim)
+        if key not in self._models:
+            m = hdc.Model(self.Bt[:dim], hdc.ApproxConfig(enc=enc))
+            self._models[key] = (m, m.workspace(self.X.shape[0]))
+        return self._models[key]
+
+    def run(self, c: ClusterConfig, timed: bool = False):
+        m, ws = self.model(c.enc, c.dim)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)] if timed else None
+        if timed:
+            ev[0].record()
+        H = hdc.encode(self.X, m, ws=ws)
+        if timed:
+            ev[1].record()
+        init = H[self.init_idx].contiguous()
+        lab, cls, acc, changes = hdc.cluster(H, c.dim, init, c.iters, _sim(c.train_perf), _sim(c.infer_perf))
+        if timed:
+            ev[2].record()
+        lab = lab.cpu().numpy()
+        out = {"nmi": metrics.nmi(self.y, lab), "changes": changes.cpu().numpy().tolist()}
+        if timed:
+            out["encode_ms"] = ev[0].elapsed_time(ev[1])
+            out["cluster_ms"] = ev[1].elapsed_time(ev[2])
+        return out
+
+    def time_ms(self, c: ClusterConfig, reps: int = 5) -> float:
+        self.run(c)
+        ts = []
+        for _ in range(reps):
+            r = self.run(c, timed=True)
+            ts.append(r["encode_ms"] + r["cluster_ms"])
+        return float(np.median(ts))
+
+
+def main(argv=None):
+    import argparse
+    ap = argparse.ArgumentParser(description="HD-Clustering on the GPU")
+    ap.add_argument("--workload", default="cluster_F617_D1024_K26")
+    a = ap.parse_args(argv)
+    hdc.load()
+    cr = ClusterRun(a.workload)
+    w = cr.w
+    rows = []
+    for c in (ClusterConfig("fp32", w.D, w.epochs), ClusterConfig("fp8", w.D, w.epochs),
+              ClusterConfig("fp8", w.D, 3), ClusterConfig("fp8", w.D, 3, infer_perf=(0.0, 0.9, 1)),
+              ClusterConfig("fp8", w.D, 3, train_perf=(0.0, 0.5, 1), infer_perf=(0.0, 0.9, 1)),
+              ClusterConfig("fp8", w.D // 2, 3)):
+        r = cr.run(c)
+        rows.append({**dataclasses.asdict(c), "nmi": round(r["nmi"], 4), "ms": round(cr.time_ms(c), 4),
+                     "changes_last": r["changes"][-1:] })
+    print(json.dumps({"workload": w.name, "points": int(cr.X.shape[0]), "K": w.C, "configs": rows}))
+
+
+if __name__ == "__main__":
+    main()

@@ -61,6 +61,8 @@ _SIGS = {
     "hdc_classify_host": (_I32, [_P, _P, _I32, _P, _P, _P, _P, _P, _SZ, _P]),
     "hdc_sweep_workspace_bytes": (_I32, [_I32, _I32, _P, _P]),
     "hdc_sweep_eval": (_I32, [_P, _P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _SZ, _P]),
+    "hdc_cluster_workspace_bytes": (_I32, [_I64, _I32, _I32, _P]),
+    "hdc_cluster": (_I32, [_P, _I64, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "hdc_stream_status": (_I32, [_P]),
     "hdc_profile_events": (None, [_P, _P]),
     "hdc_status_string": (ctypes.c_char_p, [_I32]),
@@ -350,6 +352,28 @@ class Sweep:
         _call("hdc_sweep_eval", _ptr(H), _ptr(y), self.N, self.D, self.C, _ptr(acc), ctypes.byref(self.spec),
               _ptr(self.correct), _ptr(self.labels), _ptr(self.ws), self.ws.numel(), _stream(stream))
         return self.correct
+
+
+def cluster(H: torch.Tensor, D: int, init: torch.Tensor, iters: int, train_sim: ApproxConfig | None = None,
+            infer_sim: ApproxConfig | None = None, stream=None):
+    """HD-Clustering (hdc_cluster): K-means over the packed hypervectors H
+    (N x W) from the packed initial cluster hypervectors ``init`` (K x W).
+    Returns (labels N, cluster hypervectors K x W, acc K x D, changes[iters])."""
+    N, K = H.shape[0], init.shape[0]
+    assert H.dtype == torch.int32 and init.dtype == torch.int32 and init.shape[1] == H.shape[1]
+    cls = init.clone()
+    acc = torch.zeros((K, D), dtype=torch.int32, device=H.device)
+    labels = torch.empty(N, dtype=torch.int32, device=H.device)
+    changes = torch.zeros(max(iters, 1), dtype=torch.int32, device=H.device)
+    n = ctypes.c_size_t()
+    _call("hdc_cluster_workspace_bytes", N, D, K, ctypes.byref(n))
+    ws = _empty_bytes(n.value, H.device)
+    ts = train_sim.c() if train_sim else None
+    isim = infer_sim.c() if infer_sim else None
+    _call("hdc_cluster", _ptr(H), N, D, K, iters, ctypes.byref(ts) if ts else None,
+          ctypes.byref(isim) if isim else None, _ptr(cls), _ptr(acc), _ptr(labels), _ptr(changes), _ptr(ws),
+          ws.numel(), _stream(stream))
+    return labels, cls, acc, changes[:iters]
 
 
 def stream_status(stream=None) -> int:

@@ -22,6 +22,10 @@ class-clustered mixtures stand in for them):
   baseline near 0.87 accuracy): 26-class mixture with 6238 training and
   1559 validation rows, sigma set so the unapproximated form lands near
   that accuracy.
+* ``cluster_F617_D1024_K26``     -- the HD-Clustering case (Sec. 5.2: D =
+  1024, 20 training iterations, NMI near 0.72): 7797 points of a 26-class
+  mixture clustered into K = 26, sigma set so the binary 20-iteration form
+  lands near that NMI.
 """
 from __future__ import annotations
 
@@ -59,6 +63,9 @@ WORKLOADS = {
         "large_F1024_D16384_C100", 1024, 16384, 100, 100000, 1000000, "gauss", 0.6, 3, 5000),
     "classify_F617_D2048_C26": Workload(
         "classify_F617_D2048_C26", 617, 2048, 26, 6238, 1559, "gauss", 5.2, 10, 6100),
+    # clustering: every point is a "query"; epochs = K-means iterations
+    "cluster_F617_D1024_K26": Workload(
+        "cluster_F617_D1024_K26", 617, 1024, 26, 0, 7797, "gauss", 4.05, 20, 8000),
 }
 
 # stream offsets added to a workload's base seed
@@ -129,6 +136,12 @@ def make(workload: str | Workload, n_train: int | None = None, n_query: int | No
         Xq, yq = gauss_mixture(nq, w.F, w.C, w.sigma, w.seed + _S_QUERY, cs)
         Bt = base_gauss(Dd, w.F, w.seed + _S_BASE)
     return dict(Bt=Bt, Xtr=Xtr, ytr=ytr, Xq=Xq, yq=yq)
+
+
+def cluster_init(n: int, K: int, seed: int) -> np.ndarray:
+    """K distinct point indices (the initial cluster hypervectors), drawn
+    with the workload's init stream (base seed + 7)."""
+    return np.sort(_rng(seed + 7).choice(n, K, replace=False)).astype(np.int64)
 
 
 def device_gauss_queries(n: int, w: Workload, seed: int, device="cuda"):

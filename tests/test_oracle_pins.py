@@ -413,3 +413,94 @@ def test_classify_threads_invariant(orc):
     l1, s1 = orc.classify(d["Xq"], d["Bt"], acc, orc.ENC_BF16, 0.0, 1.0, 2, 1)
     l4, s4 = orc.classify(d["Xq"], d["Bt"], acc, orc.ENC_BF16, 0.0, 1.0, 2, 1, threads=4)
     assert np.array_equal(l1, l4) and np.array_equal(s1, s4)
+
+
+# ------------------------------------------------- HD-Clustering (K-means)
+
+def _planted(rng, K=5, D=400, per=40, flip=0.12):
+    """K random centres; each point flips each bit of its centre w.p. flip."""
+    centres = rng.integers(0, 2, (K, D)).astype(np.uint8)
+    y = np.repeat(np.arange(K), per)
+    bits = centres[y] ^ (rng.random((K * per, D)) < flip).astype(np.uint8)
+    return bits, y, centres
+
+
+def _brute_assign(bits, cb, dims):
+    d = (bits[:, None, dims] != cb[None, :, dims]).sum(-1)
+    return d.argmin(1)      # numpy: first index on ties
+
+
+def test_kmeans_steps_are_assignment_and_majority(orc):
+    """Every iteration: labels = brute-force nearest (perforated dims), and
+    each cluster = per-dim majority of its members over all D (a tie, or no
+    member, gives bit 0)."""
+    rng = np.random.default_rng(21)
+    bits, _, _ = _planted(rng, K=4, D=300, per=30, flip=0.3)
+    init = bits[[0, 31, 62, 93]]
+    D = bits.shape[1]
+    tdims = orc.kept_dims(D, 0.1, 0.8, 3)
+    cb = init.copy()
+    for it in range(1, 5):
+        lab, cb_o, acc, _ = orc.kmeans(bits, init, it, train_perf=(0.1, 0.8, 3))
+        want_lab = _brute_assign(bits, cb, tdims)
+        ones = np.stack([bits[want_lab == k].sum(0) for k in range(4)])
+        cnt = np.bincount(want_lab, minlength=4)[:, None]
+        want_cb = (2 * ones > cnt).astype(np.uint8)           # more -1s than +1s
+        assert np.array_equal(cb_o, want_cb), it
+        assert np.array_equal(acc, cnt - 2 * ones)             # sum of (1 - 2 bit)
+        cb = want_cb
+
+
+def test_kmeans_objective_never_increases(orc):
+    """Unperforated K-means: sum over points of the Hamming distance to the
+    assigned cluster cannot increase (nearest assignment, then the majority
+    that minimises each cluster's sum)."""
+    rng = np.random.default_rng(5)
+    bits, _, _ = _planted(rng, K=6, D=256, per=50, flip=0.35)
+    init = bits[rng.choice(bits.shape[0], 6, replace=False)]
+    J = []
+    for it in range(0, 8):
+        _, cb, _, _ = orc.kmeans(bits, init, it)
+        J.append(int((bits[:, None, :] != cb[None]).sum(-1).min(1).sum()))
+    assert all(b <= a for a, b in zip(J, J[1:])), J
+    assert J[-1] < J[0]
+
+
+def test_kmeans_recovers_planted_clusters(orc):
+    from paper_2606_26547_gb300 import metrics
+    rng = np.random.default_rng(9)
+    bits, y, centres = _planted(rng, K=5, D=512, per=60, flip=0.1)
+    init = bits[[0, 60, 120, 180, 240]]
+    lab, cb, _, changes = orc.kmeans(bits, init, 3, infer_perf=(0.0, 0.5, 2))
+    assert metrics.nmi(y, lab) == pytest.approx(1.0)
+    assert np.array_equal(cb, centres)        # the majority of 60 noisy copies is the centre
+    assert changes[0] == bits.shape[0] and changes[-1] == 0
+
+
+def test_kmeans_zero_iterations_and_empty_cluster(orc):
+    rng = np.random.default_rng(3)
+    bits, _, _ = _planted(rng, K=3, D=128, per=10)
+    init = bits[[0, 0, 15]]                   # clusters 0 and 1 equal: ties go to 0
+    lab0, cb0, acc0, ch0 = orc.kmeans(bits, init, 0)
+    assert acc0 is None and ch0 == [] and np.array_equal(cb0, init)
+    assert np.array_equal(lab0, _brute_assign(bits, init, np.arange(128)))
+    lab, cb, acc, _ = orc.kmeans(bits, init, 1)
+    assert not (lab == 1).any() and not acc[1].any() and not cb[1].any()
+
+
+def test_nmi_definition():
+    from paper_2606_26547_gb300 import metrics
+    assert metrics.nmi([0, 0, 1, 1], [1, 1, 0, 0]) == pytest.approx(1.0)
+    assert metrics.nmi([0, 0, 1, 1], [0, 1, 0, 1]) == pytest.approx(0.0)
+    assert metrics.nmi([0, 0, 0], [0, 0, 0]) == 1.0
+    # hand computation: U = [0,0,1,1], V = [0,0,0,1]
+    h_u = math.log(2)
+    h_v = -(0.75 * math.log(0.75) + 0.25 * math.log(0.25))
+    mi = 0.5 * math.log(0.5 / (0.5 * 0.75)) + 0.25 * math.log(0.25 / (0.5 * 0.75)) + \
+        0.25 * math.log(0.25 / (0.5 * 0.25))
+    assert metrics.nmi([0, 0, 1, 1], [0, 0, 0, 1]) == pytest.approx(mi / ((h_u + h_v) / 2))
+    sk = pytest.importorskip("sklearn.metrics")
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        a, b = rng.integers(0, 7, 300), rng.integers(0, 5, 300)
+        assert metrics.nmi(a, b) == pytest.approx(sk.normalized_mutual_info_score(a, b), abs=1e-12)
