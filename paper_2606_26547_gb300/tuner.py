@@ -57,28 +57,40 @@ class Config:
     bits: int
 
 
+def perf_values(mode: str):
+    """(starts, ends, strides) of one red_perf op under a pruning mode."""
+    starts = tuple(i / GRID for i in range(GRID - MIN_SPAN + 1)) if mode == "full" else (0.0,)
+    ends = tuple(i / GRID for i in range(MIN_SPAN, GRID + 1)) if mode != "none" else (1.0,)
+    strides = STRIDES if mode == "full" else (1,)
+    return starts, ends, strides
+
+
 class Space:
     """The knobs of one pruning mode as index ranges; a point is a tuple of
-    value indices in KNOBS order."""
+    value indices in KNOBS order.  SPANS lists the (start, end) knob pairs of
+    the red_perf ops, each of which must keep end - start >= MIN_SPAN/GRID."""
     KNOBS = ("enc", "dim", "epochs", "start", "end", "stride", "bits")
+    SPANS = (("start", "end"),)
+    CONFIG = Config
 
     def __init__(self, mode: str, D: int, max_epochs: int, dim_levels: int = 5, min_dim: int = 128):
         if mode not in MODES:
             raise ValueError(mode)
         self.mode = mode
-        dims = tuple(D >> k for k in range(dim_levels) if (D >> k) >= min_dim)
-        starts = tuple(i / GRID for i in range(GRID - MIN_SPAN + 1)) if mode == "full" else (0.0,)
-        ends = tuple(i / GRID for i in range(MIN_SPAN, GRID + 1)) if mode != "none" else (1.0,)
-        strides = STRIDES if mode == "full" else (1,)
-        self.values = dict(enc=ENCS, dim=dims, epochs=tuple(range(max_epochs + 1)), start=starts, end=ends,
-                           stride=strides, bits=BITS)
+        self.values = self._values(mode, tuple(D >> k for k in range(dim_levels) if (D >> k) >= min_dim),
+                                   max_epochs)
         self.sizes = tuple(len(self.values[k]) for k in self.KNOBS)
+
+    def _values(self, mode, dims, max_epochs):
+        starts, ends, strides = perf_values(mode)
+        return dict(enc=ENCS, dim=dims, epochs=tuple(range(max_epochs + 1)), start=starts, end=ends,
+                    stride=strides, bits=BITS)
 
     def log10_size(self) -> float:
         return float(sum(math.log10(n) for n in self.sizes))
 
-    def config(self, point) -> Config:
-        return Config(*(self.values[k][i] for k, i in zip(self.KNOBS, point)))
+    def config(self, point):
+        return self.CONFIG(*(self.values[k][i] for k, i in zip(self.KNOBS, point)))
 
     def point(self, c: Config):
         return tuple(self.values[k].index(getattr(c, k)) for k in self.KNOBS)
@@ -90,19 +102,19 @@ class Space:
             return False
         return self.valid(c)
 
-    @staticmethod
-    def valid(c: Config) -> bool:
-        return round((c.end - c.start) * GRID) >= MIN_SPAN
+    def valid(self, c) -> bool:
+        return all(round((getattr(c, e) - getattr(c, a)) * GRID) >= MIN_SPAN for a, e in self.SPANS)
 
     def repair(self, point):
-        """Nearest valid point: move end up (else start down) to the span."""
+        """Nearest valid point: per span, move end up (else start down)."""
         p = list(point)
-        ks, ke = self.KNOBS.index("start"), self.KNOBS.index("end")
-        while not self.valid(self.config(p)):
-            if p[ke] + 1 < self.sizes[ke]:
-                p[ke] += 1
-            else:
-                p[ks] -= 1
+        for a, e in self.SPANS:
+            ks, ke = self.KNOBS.index(a), self.KNOBS.index(e)
+            while round((self.values[e][p[ke]] - self.values[a][p[ks]]) * GRID) < MIN_SPAN:
+                if p[ke] + 1 < self.sizes[ke]:
+                    p[ke] += 1
+                else:
+                    p[ks] -= 1
         return tuple(p)
 
     def random(self, rng):
@@ -112,6 +124,33 @@ class Space:
         for p in np.ndindex(*self.sizes):
             if self.valid(self.config(p)):
                 yield tuple(int(i) for i in p)
+
+
+@dataclasses.dataclass(frozen=True, order=True)
+class ClusterCfg:
+    enc: str
+    dim: int
+    iters: int
+    t_start: float
+    t_end: float
+    t_stride: int
+    i_start: float
+    i_end: float
+    i_stride: int
+
+
+class ClusterSpace(Space):
+    """HD-Clustering knobs: element type, D', TRAIN_ITERATIONS (K-means
+    iterations, 1..max) and the red_perf of its two similarity ops, the
+    assignment during training (t_*) and the final one (i_*)."""
+    KNOBS = ("enc", "dim", "iters", "t_start", "t_end", "t_stride", "i_start", "i_end", "i_stride")
+    SPANS = (("t_start", "t_end"), ("i_start", "i_end"))
+    CONFIG = ClusterCfg
+
+    def _values(self, mode, dims, max_epochs):
+        starts, ends, strides = perf_values(mode)
+        return dict(enc=ENCS, dim=dims, iters=tuple(range(1, max_epochs + 1)), t_start=starts, t_end=ends,
+                    t_stride=strides, i_start=starts, i_end=ends, i_stride=strides)
 
 
 # ------------------------------------------------------------ techniques
@@ -462,6 +501,47 @@ class GpuEvaluator:
         return {c: Result(a, self.ms(c)) for c, a in acc.items()}
 
 
+class ClusterEvaluator:
+    """HD-Clustering candidates: each is encoded and clustered through
+    hdc_cluster (K-means iterations cannot share one launch the way the
+    classification sweep does); QoS = NMI; time = one CUDA-graph replay of
+    encode + clustering, measured once per (enc, D', iterations, kept dims
+    of both similarity ops)."""
+
+    def __init__(self, workload: str = "cluster_F617_D1024_K26", device="cuda"):
+        from . import cluster
+        self.cl = cluster
+        self.run = cluster.ClusterRun(workload, device)
+        self.t = {}
+        self.runs = 0
+
+    def _cc(self, c: ClusterCfg):
+        return self.cl.ClusterConfig(c.enc, c.dim, c.iters, (c.t_start, c.t_end, c.t_stride),
+                                     (c.i_start, c.i_end, c.i_stride))
+
+    def ms(self, c: ClusterCfg) -> float:
+        from . import hdc
+        kt = hdc.kept_dims(c.dim, hdc.ApproxConfig(perf_start=c.t_start, perf_end=c.t_end, perf_stride=c.t_stride))
+        ki = hdc.kept_dims(c.dim, hdc.ApproxConfig(perf_start=c.i_start, perf_end=c.i_end, perf_stride=c.i_stride))
+        key = (c.enc, c.dim, c.iters, kt, ki)
+        if key not in self.t:
+            self.t[key] = self.run.graph_ms(self._cc(c), reps=3)[0]
+        return self.t[key]
+
+    def __call__(self, configs) -> dict:
+        out = {}
+        for c in configs:
+            out[c] = Result(self.run.run(self._cc(c))["nmi"], self.ms(c))
+            self.runs += 1
+        return out
+
+
+def cluster_baseline(D: int, max_iters: int) -> ClusterCfg:
+    """The unapproximated clustering: FP32 encoding at the full D, every
+    iteration, no perforation of either similarity op."""
+    return ClusterCfg("fp32", D, max_iters, 0.0, 1.0, 1, 0.0, 1.0, 1)
+
+
 def baseline_config(D: int, max_epochs: int) -> Config:
     """The unapproximated application: fp32 encoding at the full D, every
     retraining epoch, no perforation, the widest class width (8-bit cosine)."""
@@ -471,8 +551,10 @@ def baseline_config(D: int, max_epochs: int) -> Config:
 def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description="approximation tuner over the batched evaluator")
-    ap.add_argument("--workload", default="classify_F617_D2048_C26")
-    ap.add_argument("--epochs", type=int, default=10, help="TRAIN_ITERATIONS of the baseline (the knob's max)")
+    ap.add_argument("--app", default="classify", choices=["classify", "cluster"])
+    ap.add_argument("--workload", default=None, help="default: classify_F617_D2048_C26 / cluster_F617_D1024_K26")
+    ap.add_argument("--epochs", type=int, default=None,
+                    help="TRAIN_ITERATIONS of the baseline (the knob's max; default: the workload's)")
     ap.add_argument("--qos-drop", type=float, default=0.05)
     ap.add_argument("--evaluations", type=int, default=3000, help="budget per pruning mode")
     ap.add_argument("--seconds", type=float, default=None, help="time budget per pruning mode")
@@ -481,17 +563,25 @@ def main(argv=None):
     a = ap.parse_args(argv)
     from . import hdc, synth
     hdc.load()
-    w = synth.WORKLOADS[a.workload]
+    wl = a.workload or ("classify_F617_D2048_C26" if a.app == "classify" else "cluster_F617_D1024_K26")
+    w = synth.WORKLOADS[wl]
+    epochs = a.epochs if a.epochs is not None else w.epochs
     t = time.perf_counter()
-    dims = Space("none", w.D, a.epochs).values["dim"]
-    ev = GpuEvaluator(a.workload, a.epochs, dims)
+    if a.app == "classify":
+        dims = Space("none", w.D, epochs).values["dim"]
+        ev = GpuEvaluator(wl, epochs, dims)
+        space_cls, base = Space, baseline_config(w.D, epochs)
+    else:
+        ev = ClusterEvaluator(wl)
+        space_cls, base = ClusterSpace, cluster_baseline(w.D, epochs)
     prep = time.perf_counter() - t
     reports = []
     for mode in a.modes.split(","):
-        s = Search(Space(mode, w.D, a.epochs), ev, baseline_config(w.D, a.epochs), a.qos_drop, a.seed)
+        s = Search(space_cls(mode, w.D, epochs), ev, base, a.qos_drop, a.seed)
         reports.append(s.run(a.evaluations, a.seconds).report())
-    print(json.dumps({"workload": a.workload, "prepare_s": round(prep, 3), "sweep_launches": ev.sweep_launches,
-                      "classify_cost_entries": len(ev.t_classify), "modes": reports}))
+    extra = ({"sweep_launches": ev.sweep_launches, "classify_cost_entries": len(ev.t_classify)}
+             if a.app == "classify" else {"cluster_runs": ev.runs, "graph_cost_entries": len(ev.t)})
+    print(json.dumps({"app": a.app, "workload": wl, "prepare_s": round(prep, 3), **extra, "modes": reports}))
 
 
 if __name__ == "__main__":

@@ -55,3 +55,25 @@ def test_tuner_modes_respect_pruning(ev):
         s.run(evaluations=80)
         b = s.best
         assert b.start == 0.0 and b.stride == 1 and (mode != "none" or b.end == 1.0)
+
+
+def test_cluster_tuner_nmi_equals_direct_run(ev):
+    """Clustering candidates: the evaluator's NMI equals encoding and
+    clustering the configuration directly through the ABI, and its graph
+    replay gives the same labels as the eager run."""
+    from paper_2606_26547_gb300 import cluster, hdc, metrics, synth, tuner as T
+    w = synth.Workload("ctest", 300, 512, 8, 0, 1200, "gauss", 2.5, 6, 8100)
+    cev = T.ClusterEvaluator(w)
+    s = T.Search(T.ClusterSpace("full", 512, 6, dim_levels=3), cev, T.cluster_baseline(512, 6), seed=2, batch=12)
+    s.run(evaluations=40)
+    assert s.feasible(s.best) and s.report()["speedup"] >= 1.0
+    run = cluster.ClusterRun(w)
+    for c in list(s.results)[:6] + [s.best]:
+        Bt = run.Bt[:c.dim]
+        H = hdc.encode(run.X, hdc.Model(Bt, hdc.ApproxConfig(enc=c.enc)))
+        sim = lambda a, e, st: hdc.ApproxConfig(perf_start=a, perf_end=e, perf_stride=st)
+        lab, _, _, _ = hdc.cluster(H, c.dim, H[run.init_idx].contiguous(), c.iters,
+                                   sim(c.t_start, c.t_end, c.t_stride), sim(c.i_start, c.i_end, c.i_stride))
+        assert s.results[c].accuracy == metrics.nmi(run.y, lab.cpu().numpy()), c
+    ms, nmi = run.graph_ms(cev._cc(s.best), reps=2)
+    assert ms > 0 and nmi == s.results[s.best].accuracy

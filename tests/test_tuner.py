@@ -52,7 +52,7 @@ def test_space_sizes_and_round_trip():
         p = full.random(rng)
         c = full.config(p)
         assert full.valid(c) and full.point(c) == p and full.contains(c)
-    assert not T.Space.valid(T.Config("fp8", 10000, 0, 0.5, 0.52, 1, 1))
+    assert not full.valid(T.Config("fp8", 10000, 0, 0.5, 0.52, 1, 1))
     assert full.valid(full.config(full.repair(full.point(T.Config("fp8", 10000, 0, 0.95, 0.96, 1, 1)))))
 
 
@@ -112,3 +112,34 @@ def test_end_only_never_moves_start_or_stride():
     for c in s.results:
         if space.contains(c):
             assert c.start == 0.0 and c.stride == 1
+
+
+def test_cluster_space_spans_and_modes():
+    for mode, n_perf in (("none", 1), ("end_only", 96), ("full", None)):
+        sp = T.ClusterSpace(mode, 1024, 20)
+        assert sp.values["iters"] == tuple(range(1, 21))
+        assert sp.values["dim"] == (1024, 512, 256, 128)
+        if n_perf:
+            assert len(sp.values["t_end"]) == len(sp.values["i_end"]) == n_perf
+    sp = T.ClusterSpace("full", 1024, 20)
+    rng = np.random.default_rng(4)
+    for _ in range(300):
+        c = sp.config(sp.random(rng))
+        assert sp.valid(c) and c.t_end - c.t_start >= 0.049 and c.i_end - c.i_start >= 0.049
+    base = T.cluster_baseline(1024, 20)
+    assert sp.contains(base) and T.ClusterSpace("none", 1024, 20).contains(base)
+
+
+def test_cluster_search_with_fake_evaluator():
+    def ev(configs):
+        out = {}
+        for c in configs:
+            kt = (c.t_end - c.t_start) / c.t_stride
+            nmi = 0.8 - 0.03 * (20 - c.iters) / 20 - 0.1 * (1 - kt) ** 2 - 0.05 * (1 - c.i_end) \
+                - 0.04 * math.log2(1024 / c.dim)
+            ms = 0.1 * c.iters * kt * c.dim / 1024 + {"fp32": 0.3, "bf16": 0.1, "fp8": 0.08}[c.enc]
+            out[c] = T.Result(nmi, ms)
+        return out
+    s = T.Search(T.ClusterSpace("end_only", 1024, 20), ev, T.cluster_baseline(1024, 20), seed=1)
+    s.run(evaluations=800)
+    assert s.feasible(s.best) and s.report()["speedup"] > 3
