@@ -87,6 +87,18 @@ typedef struct {
 /* Force the CUDA-core (FFMA) encoder even for BF16/FP8 inputs.             */
 #define HDC_FLAG_SIMT_ENCODE 0x1u
 
+/* Float query hypervectors (Sec. 4.2 Algorithmic Choice: cosine similarity
+ * on non-binarised hypervectors, the paper's float + cosine baselines of
+ * Sec. 5.2).  The encoded query is not binarised: for each kept dim k,
+ *   q_k = bf16( s_k * sb_k ),  s_k = sum_f x^_f b^_{k,f}
+ * (sb_k the FP8 scale of base row k, 1 otherwise; the query row's scale is
+ * a common positive factor and is dropped, since the cosine ignores it), and
+ *   score_c = sum_k q_k c_k / ( ||q|| ||c|| )   (0 when a norm is 0)
+ * against the b-bit class values c of class_bits 4 or 8 (the quantisation of
+ * the binary path), FP32 tensor-core dot products, FP64 score, arg-max with
+ * the lowest index on ties.  Requires class_bits 4 or 8 and C <= 256.       */
+#define HDC_FLAG_FLOAT_QUERY 0x2u
+
 /* Fill *cfg with the unapproximated configuration: perforation (0, 1, 1),
  * FP32 encoding, binary class hypervectors.                                */
 void hdc_default_config(hdc_approx_config *cfg);

@@ -71,6 +71,9 @@ def _L():
                 "orc_retrain_epoch": (i64, [P, P, i64, i64, i64, P]),
                 "orc_class_quantise": (None, [P, i64, i64, i32, P]),
                 "orc_cosine_scores": (None, [P, i64, P, i64, i64, P]),
+                "orc_round_bf16_f64": (f64, [f64]),
+                "orc_round_bf16_f64_array": (None, [P, i64, P]),
+                "orc_cosine_float": (None, [P, i64, P, i64, i64, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -295,6 +298,44 @@ def kmeans(bits: np.ndarray, init: np.ndarray, iters: int, train_perf=(0.0, 1.0,
         cb = class_bits(acc)
     labels = argmin(hamming(gather_cols(bits, idims), gather_cols(cb, idims)))
     return labels, cb, acc, changes
+
+
+def round_bf16_f64(x: np.ndarray) -> np.ndarray:
+    """BF16 rounding (nearest, ties to even) of FP64 values."""
+    x = _c(x, np.float64)
+    out = np.empty_like(x)
+    _L().orc_round_bf16_f64_array(_p(x), x.size, _p(out))
+    return out
+
+
+def cosine_float(q: np.ndarray, chat: np.ndarray) -> np.ndarray:
+    q = _c(q, np.float64); chat = _c(chat, np.int64)
+    assert q.shape[1] == chat.shape[1]
+    out = np.empty((q.shape[0], chat.shape[0]), dtype=np.float64)
+    _L().orc_cosine_float(_p(q), q.shape[0], _p(chat), chat.shape[0], q.shape[1], _p(out))
+    return out
+
+
+def float_queries(X: np.ndarray, Bt: np.ndarray, enc: int, dims: np.ndarray, integer: bool = False):
+    """Float query hypervectors (the flag HDC_FLAG_FLOAT_QUERY of the C ABI):
+    q[i][k] = bf16(s[i][k] * sb[k]) with s the projection of the quantised
+    inputs over the kept dims and sb the base row's scale (1 unless FP8)."""
+    _, s, _, sb = encode_bits(X, Bt, enc, dims, integer)
+    scale = np.ones(len(dims)) if integer else np.asarray(sb, np.float64)[dims]
+    return round_bf16_f64(s.astype(np.float64) * scale[None, :])
+
+
+def classify_float(X: np.ndarray, Bt: np.ndarray, acc: np.ndarray, enc: int = ENC_FP32,
+                   start: float = 0.0, end: float = 1.0, stride: int = 1, class_bits_: int = 8,
+                   integer: bool = False):
+    """Cosine of float query hypervectors against the b-bit class values over
+    the kept dims, arg-max.  Returns (labels, scores, q)."""
+    D = Bt.shape[0]
+    dims = kept_dims(D, start, end, stride)
+    q = float_queries(X, Bt, enc, dims, integer)
+    chat = gather_cols(class_quantise(acc, class_bits_), dims)
+    sc = cosine_float(q, chat)
+    return argmax(sc), sc, q
 
 
 def classify(X: np.ndarray, Bt: np.ndarray, acc: np.ndarray, enc: int = ENC_FP32,

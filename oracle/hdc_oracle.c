@@ -95,6 +95,26 @@ double orc_round_bf16(float v)
     return copysign(q, (double)v);
 }
 
+/* The same rounding of a double (no intermediate FP32 step): used for the
+ * float query hypervectors, whose projections are formed in FP64 here.    */
+double orc_round_bf16_f64(double v)
+{
+    double a = fabs(v);
+    if (a == 0.0 || isinf(a) || isnan(a)) return v;
+    int ex;
+    frexp(a, &ex);
+    int e = ex - 1;
+    if (e < -126) e = -126;
+    double ulp = ldexp(1.0, e - 7);
+    double q = rint(a / ulp) * ulp;
+    return copysign(q, v);
+}
+
+void orc_round_bf16_f64_array(const double *v, int64_t n, double *out)
+{
+    for (int64_t i = 0; i < n; i++) out[i] = orc_round_bf16_f64(v[i]);
+}
+
 /* FP8 E4M3 ("fn" variant: no infinities): 1 sign, 4 exponent bits with bias
  * 7, 3 fraction bits.  Normal values 2^e * (1 + m/8) for e in [-6, 8]; the
  * largest finite value is 448 = 2^8 * 1.75; subnormals are multiples of
@@ -353,6 +373,27 @@ void orc_cosine_scores(const uint8_t *q, int64_t N, const int64_t *chat, int64_t
             for (int64_t k = 0; k < Dk; k++)
                 dot += (1 - 2 * (int64_t)q[i * Dk + k]) * chat[j * Dk + k];
             score[i * C + j] = (nn == 0) ? 0.0 : (double)dot / norm;
+        }
+    }
+}
+
+/* Cosine similarity of float query hypervectors (Sec. 4.2 Algorithmic
+ * Choice: cosine on non-binarised hypervectors):
+ *   score[i][j] = sum_k q[i][k] chat[j][k] / (||q_i|| ||chat_j||)
+ * in FP64, 0 when either norm is 0.  q is N x Dk, chat is C x Dk.         */
+void orc_cosine_float(const double *q, int64_t N, const int64_t *chat, int64_t C, int64_t Dk,
+                      double *score)
+{
+    for (int64_t i = 0; i < N; i++) {
+        double qq = 0.0;
+        for (int64_t k = 0; k < Dk; k++) qq += q[i * Dk + k] * q[i * Dk + k];
+        for (int64_t j = 0; j < C; j++) {
+            double dot = 0.0, cc = 0.0;
+            for (int64_t k = 0; k < Dk; k++) {
+                dot += q[i * Dk + k] * (double)chat[j * Dk + k];
+                cc += (double)chat[j * Dk + k] * (double)chat[j * Dk + k];
+            }
+            score[i * C + j] = (qq == 0.0 || cc == 0.0) ? 0.0 : dot / (sqrt(qq) * sqrt(cc));
         }
     }
 }

@@ -38,25 +38,41 @@ bool cfg_ok(const hdc_approx_config *cfg)
 
 bool bits_ok(uint32_t b) { return b == 1 || b == 4 || b == 8; }
 
+bool float_query(uint32_t flags) { return (flags & HDC_FLAG_FLOAT_QUERY) != 0; }
+
+// The float-query path: cosine on b-bit classes, at most 256 of them.
+bool flags_ok(uint32_t flags, uint32_t bits, int C)
+{
+    if (flags & ~(HDC_FLAG_SIMT_ENCODE | HDC_FLAG_FLOAT_QUERY)) return false;
+    return !float_query(flags) || (bits > 1 && C <= 256);
+}
+
+// Row length (BF16 elements) of the float projections and class values.
+inline int lds_for(int Dk) { return ld_for(HDC_ENC_BF16, Dk); }
+inline int cpad_for(int C) { return (C + 15) / 16 * 16; }
+
 bool model_ok(const hdc_model *m)
 {
     return m && m->struct_size >= sizeof(hdc_model) && m->F > 0 && m->D > 0 && m->Dk > 0 && m->Dk <= m->D &&
            m->C >= 0 && m->Bq && m->ldb >= m->F && m->W == words_for(m->Dk) && bits_ok((uint32_t)m->class_bits) &&
-           m->enc >= HDC_ENC_FP32 && m->enc <= HDC_ENC_FP8_E4M3 && (m->enc != HDC_ENC_FP8_E4M3 || m->b_scale);
+           m->enc >= HDC_ENC_FP32 && m->enc <= HDC_ENC_FP8_E4M3 && (m->enc != HDC_ENC_FP8_E4M3 || m->b_scale) &&
+           flags_ok(m->flags, (uint32_t)m->class_bits, m->C);
 }
 
 struct ModelLayout {
     size_t bq, bscale, planes, csum, cnorm, total;
 };
 
-ModelLayout model_layout(int F, int Dk, int C, int enc, int bits)
+ModelLayout model_layout(int F, int Dk, int C, int enc, int bits, uint32_t flags)
 {
     ModelLayout L;
     size_t off = 0;
     const int ldb = ld_for(enc, F), W = words_for(Dk);
+    // binary queries: b planes [b][C][W]; float queries: Cp x ldS BF16 values
+    const size_t cls_bytes = float_query(flags) ? (size_t)cpad_for(C) * lds_for(Dk) * 2 : (size_t)bits * C * W * 4;
     L.bq = off;     off = align_up(off + (size_t)Dk * ldb * esize_for(enc), kAlign);
     L.bscale = off; off = align_up(off + (enc == HDC_ENC_FP8_E4M3 ? (size_t)Dk * 4 : 0), kAlign);
-    L.planes = off; off = align_up(off + (size_t)bits * C * W * 4, kAlign);
+    L.planes = off; off = align_up(off + cls_bytes, kAlign);
     L.csum = off;   off = align_up(off + (size_t)C * 4, kAlign);
     L.cnorm = off;  off = align_up(off + (size_t)C * 8, kAlign);
     L.total = off;
@@ -64,8 +80,10 @@ ModelLayout model_layout(int F, int Dk, int C, int enc, int bits)
 }
 
 struct WsLayout {
-    size_t xq, sx, h, total;
+    size_t xq, sx, h, sp, qn, sf, total;
 };
+
+bool use_tc(const hdc_model *m);
 
 WsLayout ws_layout(int64_t N, const hdc_model *m)
 {
@@ -73,9 +91,15 @@ WsLayout ws_layout(int64_t N, const hdc_model *m)
     size_t off = 0;
     const bool quant = m->enc != HDC_ENC_FP32;
     const int ldx = ld_for(m->enc, m->F);
+    const bool fq = float_query(m->flags);
     L.xq = off; off = align_up(off + (quant ? (size_t)N * ldx * esize_for(m->enc) : 0), kAlign);
     L.sx = off; off = align_up(off + (m->enc == HDC_ENC_FP8_E4M3 ? (size_t)N * 4 : 0), kAlign);
     L.h = off;  off = align_up(off + (size_t)N * m->W * 4, kAlign);
+    // float queries: BF16 projections and their norms; FP32 projections
+    // first when the CUDA-core encoder computes them
+    L.sp = off; off = align_up(off + (fq ? (size_t)N * lds_for(m->Dk) * 2 : 0), kAlign);
+    L.qn = off; off = align_up(off + (fq ? (size_t)N * 4 : 0), kAlign);
+    L.sf = off; off = align_up(off + (fq ? (size_t)N * m->Dk * 4 : 0), kAlign);
     L.total = off;
     return L;
 }
@@ -158,8 +182,8 @@ hdc_status hdc_model_bytes(int32_t F, int32_t D, int32_t C, const hdc_approx_con
 {
     Perf p;
     if (!bytes || F <= 0 || D <= 0 || C < 0 || !cfg_ok(cfg) || !perf_of(D, cfg, &p)) return HDC_ERR_INVALID_ARG;
-    if (!bits_ok(cfg->class_bits)) return HDC_ERR_UNSUPPORTED;
-    *bytes = model_layout(F, (int)p.Dk, C, cfg->enc, (int)cfg->class_bits).total;
+    if (!bits_ok(cfg->class_bits) || !flags_ok(cfg->flags, cfg->class_bits, C)) return HDC_ERR_UNSUPPORTED;
+    *bytes = model_layout(F, (int)p.Dk, C, cfg->enc, (int)cfg->class_bits, cfg->flags).total;
     return HDC_OK;
 }
 
@@ -171,9 +195,9 @@ hdc_status hdc_model_prepare(const float *Bt, int32_t F, int32_t D, const int32_
     if (!Bt || !buf || !out || F <= 0 || D <= 0 || C < 0 || (C > 0 && !acc) || !cfg_ok(cfg) ||
         !perf_of(D, cfg, &p) || !aligned(buf, kAlign))
         return HDC_ERR_INVALID_ARG;
-    if (!bits_ok(cfg->class_bits)) return HDC_ERR_UNSUPPORTED;
+    if (!bits_ok(cfg->class_bits) || !flags_ok(cfg->flags, cfg->class_bits, C)) return HDC_ERR_UNSUPPORTED;
     const int Dk = (int)p.Dk, enc = cfg->enc, bits = (int)cfg->class_bits;
-    const ModelLayout L = model_layout(F, Dk, C, enc, bits);
+    const ModelLayout L = model_layout(F, Dk, C, enc, bits, cfg->flags);
     if (buf_bytes < L.total) return HDC_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     char *b = (char *)buf;
@@ -199,8 +223,15 @@ hdc_status hdc_model_prepare(const float *Bt, int32_t F, int32_t D, const int32_
         m.cls = (const uint32_t *)(b + L.planes);
         m.cls_sum = (const int32_t *)(b + L.csum);
         m.cls_norm = (const double *)(b + L.cnorm);
+        if (float_query(cfg->flags)) {
+            // rows past C stay zero (the cosine kernel reads Cp rows)
+            s = cu(cudaMemsetAsync(b + L.planes, 0, L.csum - L.planes, st));
+            if (s != HDC_OK) return s;
+        }
         s = cu(launch_class_prepare(acc, C, D, p, bits, (uint32_t *)(b + L.planes), m.W, (int32_t *)(b + L.csum),
-                                    (double *)(b + L.cnorm), st));
+                                    (double *)(b + L.cnorm),
+                                    float_query(cfg->flags) ? (uint16_t *)(b + L.planes) : nullptr, lds_for(Dk),
+                                    st));
         if (s != HDC_OK) return s;
     }
     *out = m;
@@ -328,6 +359,38 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *
     hdc_status s = prepare_queries(X, N, m, (char *)ws, L, &Xop, &ldx, &sx, st);
     if (s != HDC_OK) return s;
     uint32_t *Hb = (uint32_t *)((char *)ws + L.h);
+    if (float_query(m->flags)) {
+        // float queries: BF16 projections (tensor-core encoder's projection
+        // epilogue, or FFMA projections converted), then the cosine GEMM
+        uint16_t *sp = (uint16_t *)((char *)ws + L.sp);
+        float *qn = (float *)((char *)ws + L.qn);
+        const int ldS = lds_for(m->Dk);
+        bool done = false;
+        if (use_tc(m)) {
+            TcArgs e = {};
+            e.Xq = Xop; e.N = N; e.F = m->F; e.ldx = (int)ldx; e.Bq = m->Bq; e.ldb = m->ldb; e.Dk = m->Dk;
+            e.enc = m->enc; e.sx = sx; e.sb = m->b_scale; e.W = m->W; e.sproj = sp; e.ldS = ldS; e.qn = qn;
+            if (tc_supported(e)) {
+                s = cu(timed_tc(e, st));
+                if (s != HDC_OK) return s;
+                done = true;
+            }
+        }
+        if (!done) {
+            // FFMA projections carry the query row's scale too (a power of
+            // two, common to the row: neither BF16 rounding nor the cosine
+            // changes relative to the dropped-scale definition)
+            float *sf = (float *)((char *)ws + L.sf);
+            s = cu(timed_simt(Xop, ldx, N, m->F, m->Bq, m->ldb, m->Dk, m->enc, sx, m->b_scale, Hb, m->W, sf, st));
+            if (s != HDC_OK) return s;
+            s = cu(launch_proj_bf16(sf, N, m->Dk, sp, ldS, qn, st));
+            if (s != HDC_OK) return s;
+        }
+        CosArgs c = {};
+        c.q = sp; c.qn = qn; c.N = N; c.ldS = ldS; c.cv = (const uint16_t *)m->cls; c.cnorm = m->cls_norm;
+        c.C = m->C; c.Cp = cpad_for(m->C); c.labels = labels; c.scores = scores;
+        return cu(launch_tc_cosine(c, st));
+    }
     bool encoded = false;
     if (use_tc(m)) {
         TcArgs a = {};

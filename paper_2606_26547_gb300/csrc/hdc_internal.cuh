@@ -44,10 +44,16 @@ cudaError_t launch_quant_rows(const float *src, int64_t lds, int64_t row_off, in
                               int64_t nrows, int F, int enc, void *dst, int ldd, float *scale,
                               cudaStream_t st);
 
-// Class preparation: planes [b][C][W], sums and norms over the kept dims.
+// Class preparation: planes [b][C][W] (or, with vals, the b-bit values as
+// BF16 rows of ldv elements, zero past Dk), sums and norms over the kept dims.
 cudaError_t launch_class_prepare(const int32_t *acc, int C, int D, const Perf &p, int b,
                                  uint32_t *planes, int W, int32_t *csum, double *cnorm,
-                                 cudaStream_t st);
+                                 uint16_t *vals, int ldv, cudaStream_t st);
+
+// FP32 projections (N x Dk, from the CUDA-core encoder) -> BF16 rows of ldS
+// elements (zero past Dk) and the squared norms of the BF16 rows.
+cudaError_t launch_proj_bf16(const float *s, int64_t N, int Dk, uint16_t *q, int ldS, float *qn,
+                             cudaStream_t st);
 
 // K0: CUDA-core encode + sign + pack: H (N x W), optional scores (N x Dk).
 // X: N x ldx elements of type enc (FP32 rows may be unpadded: ldx = F),
@@ -94,6 +100,9 @@ struct TcArgs {
     const float *sx, *sb;       // row scales (FP8) or NULL
     uint32_t *H;                // encode-only output (N x W) or NULL
     float *scores;              // optional N x Dk projections
+    uint16_t *sproj;            // encode-only: BF16 projections (N x ldS) or NULL
+    int ldS;
+    float *qn;                  // with sproj: squared norms of the BF16 rows
     int W;
     // fused similarity (classify); planes == NULL for encode-only
     const uint32_t *planes;
@@ -111,5 +120,22 @@ cudaError_t quant_read_status(cudaStream_t st, int *status);
 
 // Reads and clears the tensor-core kernels' device status word.
 cudaError_t tc_read_status(cudaStream_t st, int *status);
+
+// Cosine of float query hypervectors on the tensor cores (k_tc_cos.cu):
+// q (N x ldS BF16), qn (N squared norms), cv (Cp x ldS BF16 class values,
+// Cp = C rounded up to 16, C <= 256), cnorm (C) -> labels, optional scores.
+struct CosArgs {
+    const uint16_t *q;
+    const float *qn;
+    int64_t N;
+    int ldS;
+    const uint16_t *cv;
+    const double *cnorm;
+    int C, Cp;
+    int32_t *labels;
+    double *scores;
+};
+cudaError_t launch_tc_cosine(const CosArgs &a, cudaStream_t st);
+cudaError_t tc_cosine_read_status(cudaStream_t st, int *status);
 
 }  // namespace hdc

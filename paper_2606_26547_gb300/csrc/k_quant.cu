@@ -256,7 +256,8 @@ __global__ void __launch_bounds__(QWARPS * 32) quant_rows_bulk_kernel(const floa
 __global__ void __launch_bounds__(256) class_prepare_kernel(const int32_t *__restrict__ acc, int D, int64_t s0,
                                                             int64_t stride, int64_t Dk, int b, int C,
                                                             uint32_t *__restrict__ planes, int W,
-                                                            int32_t *__restrict__ csum, double *__restrict__ cnorm)
+                                                            int32_t *__restrict__ csum, double *__restrict__ cnorm,
+                                                            uint16_t *__restrict__ vals, int ldv)
 {
     __shared__ long long s_max;
     __shared__ long long s_sum, s_sq;
@@ -278,7 +279,9 @@ __global__ void __launch_bounds__(256) class_prepare_kernel(const int32_t *__res
     }
     const long long Q = (1ll << (b - 1)) - 1;
     long long lsum = 0, lsq = 0;
-    for (int w = warp; w < W; w += nw) {
+    // with vals: the row of ldv BF16 values (integers |v| <= 127: exact)
+    const int nwords = vals ? (ldv + 31) / 32 : W;
+    for (int w = warp; w < nwords; w += nw) {
         int64_t k = (int64_t)w * 32 + lane;
         long long val = 0;
         bool kept = k < Dk;
@@ -294,6 +297,10 @@ __global__ void __launch_bounds__(256) class_prepare_kernel(const int32_t *__res
         }
         lsum += val;
         lsq += val * val;
+        if (vals) {
+            if (k < ldv) vals[(int64_t)c * ldv + k] = __bfloat16_as_ushort(__float2bfloat16_rn((float)val));
+            continue;
+        }
         for (int j = 0; j < b; j++) {
             // b == 1: the single plane is the sign (set bit = element -1)
             bool bit = b == 1 ? val < 0 : ((val >> j) & 1) != 0;
@@ -370,10 +377,41 @@ cudaError_t launch_quant_rows(const float *src, int64_t lds, int64_t row_off, in
 }
 
 cudaError_t launch_class_prepare(const int32_t *acc, int C, int D, const Perf &p, int b, uint32_t *planes, int W,
-                                 int32_t *csum, double *cnorm, cudaStream_t st)
+                                 int32_t *csum, double *cnorm, uint16_t *vals, int ldv, cudaStream_t st)
 {
     if (C <= 0) return cudaSuccess;
-    class_prepare_kernel<<<C, 256, 0, st>>>(acc, D, p.s0, p.stride, p.Dk, b, C, planes, W, csum, cnorm);
+    class_prepare_kernel<<<C, 256, 0, st>>>(acc, D, p.s0, p.stride, p.Dk, b, C, planes, W, csum, cnorm, vals, ldv);
+    return cudaGetLastError();
+}
+
+namespace {
+// One warp per row: BF16 of each projection (zero past Dk) and the FP32
+// sum of the squared BF16 values, in column order per lane, lanes combined
+// by a butterfly.
+__global__ void proj_bf16_kernel(const float *__restrict__ s, int64_t N, int Dk, uint16_t *__restrict__ q, int ldS,
+                                 float *__restrict__ qn)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= N) return;
+    float acc = 0.f;
+    for (int k = lane; k < ldS; k += 32) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(k < Dk ? s[row * Dk + k] : 0.f);
+        const float g = __bfloat162float(b);
+        acc = fmaf(g, g, acc);
+        q[row * ldS + k] = __bfloat16_as_ushort(b);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) qn[row] = acc;
+}
+}  // namespace
+
+cudaError_t launch_proj_bf16(const float *s, int64_t N, int Dk, uint16_t *q, int ldS, float *qn, cudaStream_t st)
+{
+    if (N <= 0) return cudaSuccess;
+    const int64_t blocks = (N * 32 + 255) / 256;
+    proj_bf16_kernel<<<(unsigned)blocks, 256, 0, st>>>(s, N, Dk, q, ldS, qn);
     return cudaGetLastError();
 }
 

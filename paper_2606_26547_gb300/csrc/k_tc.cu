@@ -78,7 +78,8 @@ bool tc_supported(const TcArgs &a)
     if (a.N <= 0 || a.N > 0x7fffffffLL - tc::BM || a.Dk <= 0 || a.W != words_for(a.Dk)) return false;
     // fused classify: binary class hypervectors, up to 128 classes
     if (a.planes && (a.C <= 0 || a.C > 128 || a.nb != 1)) return false;
-    if (!a.planes && !a.H) return false;
+    if (!a.planes && !a.H && !a.sproj) return false;
+    if (a.sproj && (a.planes || !a.qn || a.ldS % 64 != 0 || a.ldS < a.Dk)) return false;
     if (!encode_fn()) return false;
     return true;
 }
@@ -104,6 +105,9 @@ cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st)
     p.C = a.C;
     p.labels = a.labels;
     p.dists = a.dists;
+    p.sproj = a.sproj;
+    p.ldS = a.ldS;
+    p.qn = a.qn;
     const int64_t m_tiles = (a.N + tc::BM - 1) / tc::BM;
     const int sms = sm_count();
     if (sms <= 0) return cudaErrorNoDevice;
@@ -117,10 +121,11 @@ cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st)
 
 cudaError_t tc_read_status(cudaStream_t st, int *status)
 {
-    int a = 0, b = 0;
+    int a = 0, b = 0, c = 0;
     cudaError_t e = tc::status_bf16(st, &a);
     if (e == cudaSuccess) e = tc::status_fp8(st, &b);
-    *status = a ? a : b;
+    if (e == cudaSuccess) e = tc_cosine_read_status(st, &c);
+    *status = a ? a : b ? b : c;
     return e;
 }
 

@@ -32,6 +32,7 @@
 // (again with a bound), frees TMEM and returns.
 #pragma once
 #include <cuda.h>
+#include <cuda_bf16.h>
 
 #include "hdc_internal.cuh"
 
@@ -78,6 +79,9 @@ struct Params {
     const uint32_t *planes;  // binary class hypervectors, C x W
     int C;
     int32_t *labels, *dists;
+    uint16_t *sproj;         // encode-only: BF16 projections s_k * sb_k (N x ldS) or NULL
+    int ldS;
+    float *qn;               // and the squared norm of each BF16 row
 };
 
 // ------------------------------------------------------------ PTX wrappers
@@ -387,6 +391,7 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
         for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++) {
             const int64_t row = mt * BM + r;
             const bool valid = row < p.N;
+            float qsum = 0.f;   // squared norm of the BF16 projections of this row
             int dist[CLASSIFY ? CMAX : 1];
 #pragma unroll
             for (int c = 0; c < (CLASSIFY ? CMAX : 1); c++) dist[c] = 0;
@@ -409,6 +414,26 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
                             if (col < p.Dk)
                                 p.scores[row * p.Dk + col] = __uint_as_float(v[i]) * rs * (p.sb ? p.sb[col] : 1.f);
                         }
+                    }
+                    const int col0 = nt * BN + jw * 32;
+                    if (!CLASSIFY && p.sproj && valid && col0 < p.ldS) {
+                        // 32 BF16 projections (zeros past Dk: the base rows
+                        // there are TMA zero fill), 4 x 16-byte stores
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int i = 0; i < 32; i += 2) {
+                            const int c = col0 + i;
+                            const float f0 = c < p.Dk ? __uint_as_float(v[i]) * (p.sb ? p.sb[c] : 1.f) : 0.f;
+                            const float f1 = c + 1 < p.Dk ? __uint_as_float(v[i + 1]) * (p.sb ? p.sb[c + 1] : 1.f) : 0.f;
+                            const __nv_bfloat16 b0 = __float2bfloat16_rn(f0), b1 = __float2bfloat16_rn(f1);
+                            const float g0 = __bfloat162float(b0), g1 = __bfloat162float(b1);
+                            qsum = fmaf(g0, g0, qsum);
+                            qsum = fmaf(g1, g1, qsum);
+                            pk[i / 2] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+                        }
+                        uint4 *dst = reinterpret_cast<uint4 *>(p.sproj + row * (int64_t)p.ldS + col0);
+#pragma unroll
+                        for (int i = 0; i < 4; i++) dst[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
                     }
                     words[j] = pack_signs(v);
                 }
@@ -445,12 +470,13 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
                         }
                     mbar_arrive(cempty(cb));
                     if (++cb == CBUF) { cb = 0; cph ^= 1; }
-                } else if (valid) {
+                } else if (valid && p.H) {
                     uint32_t *h = p.H + row * (int64_t)p.W + gw0;
                     if (gw0 + 4 <= p.W) *reinterpret_cast<uint4 *>(h) = make_uint4(words[0], words[1], words[2], words[3]);
                     if (gw0 + 8 <= p.W) *reinterpret_cast<uint4 *>(h + 4) = make_uint4(words[4], words[5], words[6], words[7]);
                 }
             }
+            if (!CLASSIFY && !ab && p.qn && valid) p.qn[row] = qsum;
             if (CLASSIFY && !ab) {  // arg-min over this warpgroup's classes, lowest index on ties
                 int best = c0, bv = 0x7fffffff;
 #pragma unroll

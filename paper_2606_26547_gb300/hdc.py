@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libhdc.so")
 
 ENC = {"fp32": 0, "bf16": 1, "fp8": 2}
 FLAG_SIMT_ENCODE = 0x1
+FLAG_FLOAT_QUERY = 0x2
 STATIC_SCRATCH_BYTES = 64 << 20  # HDC_STATIC_SCRATCH_BYTES
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported configuration", 3: "buffer or workspace too small",
@@ -117,6 +118,7 @@ class ApproxConfig:
     enc: str = "fp32"
     class_bits: int = 1
     simt: bool = False  # force the CUDA-core encoder
+    float_query: bool = False  # cosine on non-binarised query hypervectors (class_bits 4 / 8)
 
     def c(self) -> ApproxConfigC:
         cfg = ApproxConfigC()
@@ -126,7 +128,7 @@ class ApproxConfig:
         cfg.perf_stride = self.perf_stride
         cfg.enc = ENC[self.enc]
         cfg.class_bits = self.class_bits
-        cfg.flags = FLAG_SIMT_ENCODE if self.simt else 0
+        cfg.flags = (FLAG_SIMT_ENCODE if self.simt else 0) | (FLAG_FLOAT_QUERY if self.float_query else 0)
         return cfg
 
 

@@ -504,3 +504,78 @@ def test_nmi_definition():
     for _ in range(20):
         a, b = rng.integers(0, 7, 300), rng.integers(0, 5, 300)
         assert metrics.nmi(a, b) == pytest.approx(sk.normalized_mutual_info_score(a, b), abs=1e-12)
+
+
+# --------------------------------------------- float query hypervectors
+
+def _bf16_table():
+    """Every finite BF16 value, ascending, with its bit pattern's parity."""
+    bits = np.arange(0, 1 << 16, dtype=np.uint32)
+    vals = (bits << 16).view(np.float32).astype(np.float64)
+    ok = np.isfinite(vals)
+    v, b = vals[ok], bits[ok]
+    order = np.argsort(v, kind="stable")
+    v, b = v[order], b[order]
+    keep = np.concatenate([[True], v[1:] != v[:-1]])      # +0 / -0 once
+    return v[keep], b[keep]
+
+
+def test_round_bf16_f64_nearest_even_brute_force(orc):
+    table, tbits = _bf16_table()
+    rng = np.random.default_rng(17)
+    x = np.concatenate([rng.standard_normal(3000) * 10.0 ** rng.integers(-40, 38, 3000),
+                        table[rng.integers(0, table.size - 1, 500)]])
+    # exact ties between neighbours, and ties nudged by less than an FP32 ulp
+    i = rng.integers(20000, 30000, 200)
+    mids = (table[i] + table[i + 1]) / 2
+    x = np.concatenate([x, mids, mids + np.abs(mids) * 2.0 ** -40, mids - np.abs(mids) * 2.0 ** -40])
+    x = x[np.abs(x) < table[-1]]
+    got = orc.round_bf16_f64(x)
+    for v, g in zip(x, got):
+        j = np.searchsorted(table, v)
+        lo, hi = table[max(j - 1, 0)], table[min(j, table.size - 1)]
+        if v - lo < hi - v:
+            want = lo
+        elif hi - v < v - lo:
+            want = hi
+        else:   # tie: even bit pattern
+            want = lo if tbits[max(j - 1, 0)] % 2 == 0 else hi
+        assert g == want, (v, g, want)
+    # an FP32 intermediate would round twice here: 1 + 2^-8 + 2^-40 -> 1 + 2^-7
+    assert orc.round_bf16_f64(np.array([1 + 2.0 ** -8 + 2.0 ** -40]))[0] == 1 + 2.0 ** -7
+
+
+def test_cosine_float_definition(orc):
+    rng = np.random.default_rng(8)
+    q = rng.standard_normal((40, 300))
+    chat = rng.integers(-127, 128, (7, 300))
+    sc = orc.cosine_float(q, chat)
+    want = 1.0 - sdist.cdist(q, chat.astype(np.float64), "cosine")
+    assert np.allclose(sc, want, rtol=0, atol=1e-12)
+    assert np.allclose(orc.cosine_float(q * 2.5e7, chat), sc, rtol=0, atol=1e-12)    # scale invariance
+    # +-1 queries: the binary-query cosine (which leaves out ||q|| = sqrt(Dk))
+    bits = rng.integers(0, 2, (40, 300)).astype(np.uint8)
+    pm = 1.0 - 2.0 * bits
+    assert np.allclose(orc.cosine_float(pm, chat) * math.sqrt(300), orc.cosine_scores(bits, chat),
+                       rtol=1e-13, atol=1e-12)
+    z = orc.cosine_float(np.zeros((2, 300)), chat)
+    assert not z.any()
+    chat[3] = 0
+    assert not orc.cosine_float(q, chat)[:, 3].any()
+
+
+def test_float_queries_integer_data(orc):
+    """Integer features, +-1 base: the projections are exact integers and
+    their BF16 rounding is the cast of those integers."""
+    from paper_2606_26547_gb300 import synth
+    d = synth.make("int_exact_F617_D2048_C26", n_train=10, n_query=30)
+    dims = orc.kept_dims(2048, 0.0, 1.0, 3)
+    q = orc.float_queries(d["Xq"], d["Bt"], orc.ENC_FP32, dims, integer=True)
+    s = d["Xq"].astype(np.int64) @ d["Bt"].astype(np.int64)[dims].T
+    want = torch.from_numpy(s.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(q, want)
+    # E4M3 is exact on this data; sb undoes the base-row scale, and the query
+    # row's power-of-two scale (dropped by the definition) scales BF16 exactly
+    q8 = orc.float_queries(d["Xq"], d["Bt"], orc.ENC_FP8, dims)
+    _, sx = orc.quantise_rows(d["Xq"], orc.ENC_FP8)
+    assert np.array_equal(q8 * sx[:, None], want)
