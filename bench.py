@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=1 << 20, help="queries per step (per GPU)")
     ap.add_argument("--enc", default="fp8", choices=["bf16", "fp8"])
     ap.add_argument("--stride", type=int, default=2)
+    ap.add_argument("--class-bits", type=int, default=None, help="1 (default), 4 or 8 (8 with --float-query)")
+    ap.add_argument("--float-query", action="store_true",
+                    help="cosine on non-binarised (BF16) query hypervectors against b-bit classes")
     ap.add_argument("--exact-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the oracle sample")
@@ -231,7 +234,8 @@ def run_ours(a):
     train_passes = time_training(hdc, torch, Htr, ytr, w.D, w.C)
     del Htr
 
-    approx_cfg = hdc.ApproxConfig(enc=a.enc, perf_stride=a.stride)
+    cbits = a.class_bits or (8 if a.float_query else 1)
+    approx_cfg = hdc.ApproxConfig(enc=a.enc, perf_stride=a.stride, class_bits=cbits, float_query=a.float_query)
     exact_cfg = hdc.ApproxConfig(enc="fp32")
     m_apx = hdc.Model(Bt, approx_cfg, acc=acc)
     m_ex = hdc.Model(Bt, exact_cfg, acc=acc)
@@ -336,24 +340,30 @@ def run_ours(a):
     achieved = flops / avg_k / 1e12
     pt = PROFILED_TRAFFIC
     traffic = (pt["dram_bytes_per_query"] * B if tc_sources_sha() == pt["sources_sha1_16"] and a.enc == pt["enc"]
-               and a.stride == pt["stride"] and a.workload == WORKLOAD else None)
+               and a.stride == pt["stride"] and a.workload == WORKLOAD and cbits == 1 and not a.float_query
+               else None)
+    fused = cbits == 1 and not a.float_query
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": el / a.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "%s operands, fp32 accumulate, binary hypervectors" % ("e4m3" if a.enc == "fp8" else "bf16"),
+        "dtype": "%s operands, fp32 accumulate, %s" % ("e4m3" if a.enc == "fp8" else "bf16",
+                                                         "bf16 query hypervectors" if a.float_query
+                                                         else "binary hypervectors"),
         "data": "synthetic (seeded Gaussian mixture shaped like the workload; no dataset)",
         "config": {"workload": a.workload, "F": F, "D": w.D, "C": w.C, "enc": a.enc,
-                   "perforation": [0.0, 1.0, a.stride], "Dk": Dk, "class_bits": 1, "queries_per_step": B,
+                   "perforation": [0.0, 1.0, a.stride], "Dk": Dk, "class_bits": cbits,
+                   "query": "float (BF16 projections, cosine)" if a.float_query else "binary", "queries_per_step": B,
                    "train": "bundling + %d retraining epochs on %d samples (FP32 encode)" % (w.epochs, w.n_train),
                    "l2": "inputs larger than L2 (%.1f GB of FP32 queries per step)" % (B * F * 4 / 1e9),
                    "parallelism": "dp%d (queries sharded, no collective)" % world},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "tc_encode_kernel (classify)",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "tc_encode_kernel (%s)" % ("classify" if fused else "encode"),
                      "peak_source": peak_src + " of measured", "kernel_ms": avg_k * 1e3,
                      "algorithmic_flops_per_launch": flops},
         "e2e": {"value": e2e_qps, "unit": UNIT, "h2d_bytes_per_step": B * F * 4, "d2h_bytes_per_step": B * 4},
-        "gpu_launches": 2 * a.steps,
+        "gpu_launches": (2 if fused else 3) * a.steps,   # quantise + fused, or + similarity / cosine
         "clocks": clocks,
         "exact": {"value": exact_qps, "unit": UNIT, "enc": "fp32 (FFMA)", "Dk": w.D,
                   "ms_per_step": el_ex / a.exact_steps * 1e3},
@@ -363,7 +373,7 @@ def run_ours(a):
         "train_s": train_s, "train_updates": ups,
         "train_passes": dict(train_passes, hbm_peak_gbs=pk.get("hbm_gbs")),
     }
-    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+    if rank == 0 and world == 1 and not a.no_cpu_baseline and fused:   # the oracle sample times the binary path
         import oracle
         threads = os.cpu_count() or 1
         acc_np = acc.cpu().numpy().astype(np.int64)
