@@ -9,6 +9,9 @@ Knobs (Sec. 4.2, 4.3) as this library implements them:
            red_perf of the inference similarity reduction
   bits     class hypervector width: 1 (Hamming) or 4 / 8 (cosine), the
            algorithmic choice and element type of the similarity
+  query    binary (packed signs) or float (BF16 projections; cosine, so
+           4 / 8-bit classes only): the algorithmic choice of Sec. 4.2
+           between the float + cosine form and automatic binarization
 The encoding's feature reduction is never perforated here: every space
 carries the no-approx hint on the encoding.  The pruning modes of Sec. 5.2
 therefore become: ``full`` (start, stride and end tunable; Full RedPerf
@@ -55,6 +58,10 @@ class Config:
     end: float
     stride: int
     bits: int
+    query: str = "binary"
+
+
+QUERIES = ("binary", "float")
 
 
 def perf_values(mode: str):
@@ -69,7 +76,7 @@ class Space:
     """The knobs of one pruning mode as index ranges; a point is a tuple of
     value indices in KNOBS order.  SPANS lists the (start, end) knob pairs of
     the red_perf ops, each of which must keep end - start >= MIN_SPAN/GRID."""
-    KNOBS = ("enc", "dim", "epochs", "start", "end", "stride", "bits")
+    KNOBS = ("enc", "dim", "epochs", "start", "end", "stride", "bits", "query")
     SPANS = (("start", "end"),)
     CONFIG = Config
 
@@ -84,7 +91,7 @@ class Space:
     def _values(self, mode, dims, max_epochs):
         starts, ends, strides = perf_values(mode)
         return dict(enc=ENCS, dim=dims, epochs=tuple(range(max_epochs + 1)), start=starts, end=ends,
-                    stride=strides, bits=BITS)
+                    stride=strides, bits=BITS, query=QUERIES)
 
     def log10_size(self) -> float:
         return float(sum(math.log10(n) for n in self.sizes))
@@ -103,6 +110,8 @@ class Space:
         return self.valid(c)
 
     def valid(self, c) -> bool:
+        if getattr(c, "query", "binary") == "float" and c.bits == 1:
+            return False     # a float query is compared by cosine only
         return all(round((getattr(c, e) - getattr(c, a)) * GRID) >= MIN_SPAN for a, e in self.SPANS)
 
     def repair(self, point):
@@ -115,6 +124,10 @@ class Space:
                     p[ke] += 1
                 else:
                     p[ks] -= 1
+        if "query" in self.KNOBS:
+            kq, kb = self.KNOBS.index("query"), self.KNOBS.index("bits")
+            if self.values["query"][p[kq]] == "float" and self.values["bits"][p[kb]] == 1:
+                p[kb] = self.values["bits"].index(8)
         return tuple(p)
 
     def random(self, rng):
@@ -457,9 +470,9 @@ class GpuEvaluator:
     def classify_ms(self, c: Config) -> float:
         hdc, torch = self.hdc, self.torch
         cfg = hdc.ApproxConfig(enc=c.enc, class_bits=c.bits, perf_start=c.start, perf_end=c.end,
-                               perf_stride=c.stride)
+                               perf_stride=c.stride, float_query=c.query == "float")
         Dk = hdc.kept_dims(c.dim, cfg)
-        key = (c.enc, Dk, c.bits)
+        key = (c.enc, Dk, c.bits, c.query)
         if key not in self.t_classify:
             model = hdc.Model(self.Bt[:c.dim], cfg, acc=self.snap[(c.enc, c.dim, 0)])
             ws = model.workspace(self.Xv.shape[0])
@@ -470,13 +483,27 @@ class GpuEvaluator:
     def ms(self, c: Config) -> float:
         return self.t_encode_train[(c.enc, c.dim)] + self.t_train[(c.enc, c.dim, c.epochs)] + self.classify_ms(c)
 
+    def float_accuracy(self, c: Config) -> float:
+        """A float-query candidate: classify the validation set with a model
+        prepared for it (the sweep scores binary queries only)."""
+        hdc = self.hdc
+        cfg = hdc.ApproxConfig(enc=c.enc, class_bits=c.bits, perf_start=c.start, perf_end=c.end,
+                               perf_stride=c.stride, float_query=True)
+        model = hdc.Model(self.Bt[:c.dim], cfg, acc=self.snap[(c.enc, c.dim, c.epochs)])
+        lab = hdc.classify(self.Xv, model)
+        return float((lab == self.yv).sum().item()) / self.Xv.shape[0]
+
     def accuracy(self, configs) -> dict:
         """Accuracy of every (entry, width) the batch's sweeps score: the
-        proposals and, for free, their entries under the other widths."""
+        proposals and, for free, their entries under the other widths;
+        float-query proposals one by one."""
         hdc = self.hdc
         N = self.Xv.shape[0]
+        out = {c: self.float_accuracy(c) for c in configs if c.query == "float"}
         groups = {}
         for c in configs:
+            if c.query == "float":
+                continue
             groups.setdefault((c.enc, c.dim, c.epochs), set()).add((c.start, c.end, c.stride))
         pending = []
         for (enc, dim, ep), entries in groups.items():
@@ -488,7 +515,6 @@ class GpuEvaluator:
                 sw(self.Hv[(enc, dim)], self.yv, self.snap[(enc, dim, ep)])
                 self.sweep_launches += 1
                 pending.append((enc, dim, ep, chunk, sw.correct))
-        out = {}
         for enc, dim, ep, chunk, corr in pending:
             corr = corr.cpu().numpy()
             for jb, b in enumerate(BITS):
@@ -543,9 +569,10 @@ def cluster_baseline(D: int, max_iters: int) -> ClusterCfg:
 
 
 def baseline_config(D: int, max_epochs: int) -> Config:
-    """The unapproximated application: fp32 encoding at the full D, every
-    retraining epoch, no perforation, the widest class width (8-bit cosine)."""
-    return Config("fp32", D, max_epochs, 0.0, 1.0, 1, 8)
+    """The unapproximated application, the paper's float + cosine form: fp32
+    encoding at the full D, every retraining epoch, no perforation, float
+    query hypervectors, cosine against the widest class width (8 bits)."""
+    return Config("fp32", D, max_epochs, 0.0, 1.0, 1, 8, "float")
 
 
 def main(argv=None):

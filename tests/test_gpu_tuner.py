@@ -27,7 +27,7 @@ def one_by_one(ev, c):
     H = hdc.encode(ev.Xtr, hdc.Model(Bt, hdc.ApproxConfig(enc=c.enc)))
     acc, _, _ = hdc.train(H, ev.ytr, c.dim, ev.w.C, c.epochs)
     m = hdc.Model(Bt, hdc.ApproxConfig(enc=c.enc, class_bits=c.bits, perf_start=c.start, perf_end=c.end,
-                                       perf_stride=c.stride), acc=acc)
+                                       perf_stride=c.stride, float_query=c.query == "float"), acc=acc)
     lab = hdc.classify(ev.Xv, m)
     return float((lab == ev.yv).sum().item()) / ev.Xv.shape[0]
 
@@ -41,7 +41,8 @@ def test_tuner_accuracies_equal_one_by_one(ev):
     assert s.feasible(s.best) and rep["speedup"] >= 1.0
     rng = np.random.default_rng(0)
     cs = list(s.results)
-    picks = [s.best, s.baseline] + [cs[i] for i in rng.choice(len(cs), 6, replace=False)]
+    fl = [c for c in cs if c.query == "float"]
+    picks = [s.best, s.baseline] + [cs[i] for i in rng.choice(len(cs), 6, replace=False)] + fl[:3]
     for c in picks:
         assert s.results[c].accuracy == one_by_one(ev, c), c
         assert s.results[c].ms > 0

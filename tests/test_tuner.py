@@ -14,9 +14,10 @@ def fake_eval(c: T.Config):
     fewer kept dims; time grows with the kept dims and the epochs."""
     kept = (c.end - c.start) / c.stride
     acc = 0.9 - 0.02 * math.log2(10000 / c.dim) - 0.01 * (10 - c.epochs) - 0.015 * (c.bits == 1) \
-        - 0.08 * (1 - kept) ** 2 - 0.005 * {"fp32": 0, "bf16": 1, "fp8": 2}[c.enc]
+        - 0.08 * (1 - kept) ** 2 - 0.005 * {"fp32": 0, "bf16": 1, "fp8": 2}[c.enc] \
+        + 0.01 * (c.query == "float")
     ms = 5.0 * {"fp32": 3, "bf16": 1.5, "fp8": 1}[c.enc] * c.dim / 10000 + 0.3 * c.epochs \
-        + 2.0 * kept * c.dim / 10000 * (0.5 if c.bits == 1 else 1.0)
+        + 2.0 * kept * c.dim / 10000 * (0.5 if c.bits == 1 else 1.0) + 1.5 * (c.query == "float")
     return T.Result(acc, ms)
 
 
@@ -44,7 +45,7 @@ def brute_best(space, target):
 def test_space_sizes_and_round_trip():
     full, end, none = (T.Space(m, 10000, 10) for m in ("full", "end_only", "none"))
     assert none.values["dim"] == (10000, 5000, 2500, 1250, 625)
-    assert none.sizes == (3, 5, 11, 1, 1, 1, 3)
+    assert none.sizes == (3, 5, 11, 1, 1, 1, 3, 2)
     assert end.sizes[T.Space.KNOBS.index("end")] == 96 and end.sizes[T.Space.KNOBS.index("stride")] == 1
     assert full.log10_size() > end.log10_size() > none.log10_size()
     rng = np.random.default_rng(1)
@@ -53,6 +54,8 @@ def test_space_sizes_and_round_trip():
         c = full.config(p)
         assert full.valid(c) and full.point(c) == p and full.contains(c)
     assert not full.valid(T.Config("fp8", 10000, 0, 0.5, 0.52, 1, 1))
+    assert not full.valid(T.Config("fp8", 10000, 0, 0.0, 1.0, 1, 1, "float"))   # float queries: cosine only
+    assert full.config(full.repair(full.point(T.Config("fp8", 10000, 0, 0.0, 1.0, 1, 8, "float")))).bits == 8
     assert full.valid(full.config(full.repair(full.point(T.Config("fp8", 10000, 0, 0.95, 0.96, 1, 1)))))
 
 
