@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
     uint32_t *s_words = reinterpret_cast<uint32_t *>(s_idx + NMRG * BM);  // WXB x [8][BM]
     constexpr int PRODUCER = 4 * EWG, ISSUER = 4 * EWG + 1;
     constexpr int WPG = (BN / 32) / EWG;  // words packed by each epilogue warpgroup
-    static_assert(EWG == 1 || (CLASSIFY && (EWG == 2 || EWG == 4)), "several epilogue warpgroups: classify only");
+    static_assert(EWG == 1 || EWG == 2 || EWG == 4, "one, two or four epilogue warpgroups");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t num_m_tiles = (p.N + BM - 1) / BM;
@@ -419,12 +419,23 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
                     if (!CLASSIFY && p.sproj && valid && col0 < p.ldS) {
                         // 32 BF16 projections (zeros past Dk: the base rows
                         // there are TMA zero fill), 4 x 16-byte stores
+                        float sbv[32];
+                        if (p.sb && col0 + 32 <= p.Dk) {
+                            const float4 *s4 = reinterpret_cast<const float4 *>(p.sb + col0);
+#pragma unroll
+                            for (int i = 0; i < 8; i++) {
+                                const float4 t = s4[i];
+                                sbv[4 * i] = t.x; sbv[4 * i + 1] = t.y; sbv[4 * i + 2] = t.z; sbv[4 * i + 3] = t.w;
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 32; i++) sbv[i] = col0 + i < p.Dk ? (p.sb ? p.sb[col0 + i] : 1.f) : 0.f;
+                        }
                         uint32_t pk[16];
 #pragma unroll
                         for (int i = 0; i < 32; i += 2) {
-                            const int c = col0 + i;
-                            const float f0 = c < p.Dk ? __uint_as_float(v[i]) * (p.sb ? p.sb[c] : 1.f) : 0.f;
-                            const float f1 = c + 1 < p.Dk ? __uint_as_float(v[i + 1]) * (p.sb ? p.sb[c + 1] : 1.f) : 0.f;
+                            const float f0 = __uint_as_float(v[i]) * sbv[i];
+                            const float f1 = __uint_as_float(v[i + 1]) * sbv[i + 1];
                             const __nv_bfloat16 b0 = __float2bfloat16_rn(f0), b1 = __float2bfloat16_rn(f1);
                             const float g0 = __bfloat162float(b0), g1 = __bfloat162float(b1);
                             qsum = fmaf(g0, g0, qsum);
@@ -440,7 +451,7 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
                 tc_fence_before();
                 mbar_arrive(tempty(acc));
                 if (++acc == 2) { acc = 0; aphase ^= 1; }
-                if (EWG > 1) {
+                if (CLASSIFY && EWG > 1) {
                     // publish this warpgroup's words, then read the row's 8
                     uint32_t *sw = s_words + (size_t)wb * 8 * BM;
 #pragma unroll
@@ -472,11 +483,37 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
                     if (++cb == CBUF) { cb = 0; cph ^= 1; }
                 } else if (valid && p.H) {
                     uint32_t *h = p.H + row * (int64_t)p.W + gw0;
-                    if (gw0 + 4 <= p.W) *reinterpret_cast<uint4 *>(h) = make_uint4(words[0], words[1], words[2], words[3]);
-                    if (gw0 + 8 <= p.W) *reinterpret_cast<uint4 *>(h + 4) = make_uint4(words[4], words[5], words[6], words[7]);
+                    if (EWG == 1) {
+                        if (gw0 + 4 <= p.W) *reinterpret_cast<uint4 *>(h) = make_uint4(words[0], words[1], words[2], words[3]);
+                        if (gw0 + 8 <= p.W) *reinterpret_cast<uint4 *>(h + 4) = make_uint4(words[4], words[5], words[6], words[7]);
+                    } else {  // this warpgroup's words only (W is a multiple of 4)
+                        const int w0 = gw0 + g * WPG;
+                        if (w0 + WPG <= p.W) {
+#pragma unroll
+                            for (int j = 0; j < WPG; j++) h[g * WPG + j] = words[j];
+                        }
+                    }
                 }
             }
-            if (!CLASSIFY && !ab && p.qn && valid) p.qn[row] = qsum;
+            if (!CLASSIFY && !ab && p.qn) {
+                if (EWG == 1) {
+                    if (valid) p.qn[row] = qsum;
+                } else {  // partial norms of the warpgroups' columns, summed in order g = 0, 1, ...
+                    const uint32_t par = (uint32_t)(it & 1);
+                    if (g > 0) {
+                        if (!mbar_wait(merge_empty, par ^ 1, abort_flag)) { ab = true; break; }
+                        s_val[(g - 1) * BM + r] = __float_as_int(qsum);
+                        mbar_arrive(merge_full);
+                    } else {
+                        if (!mbar_wait(merge_full, par, abort_flag)) { ab = true; break; }
+                        float t = qsum;
+#pragma unroll
+                        for (int h = 0; h < EWG - 1; h++) t += __int_as_float(s_val[h * BM + r]);
+                        mbar_arrive(merge_empty);
+                        if (valid) p.qn[row] = t;
+                    }
+                }
+            }
             if (CLASSIFY && !ab) {  // arg-min over this warpgroup's classes, lowest index on ties
                 int best = c0, bv = 0x7fffffff;
 #pragma unroll
@@ -532,7 +569,11 @@ template <int ENC>
 static cudaError_t launch_enc(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const Params &p,
                               unsigned grid, bool classify, cudaStream_t st)
 {
-    if (!classify) return launch_one<ENC, 1, false, 1>(ma, mb, mc, p, grid, st);
+    // encode-only: packed words with one warpgroup; BF16 projections (heavier
+    // epilogue) with four, each converting and storing its 64 columns
+    if (!classify)
+        return p.sproj ? launch_one<ENC, 1, false, 4>(ma, mb, mc, p, grid, st)
+                       : launch_one<ENC, 1, false, 1>(ma, mb, mc, p, grid, st);
     // up to 16 classes: one epilogue warpgroup; up to 32: two; more: four,
     // each counting ceil(C / EWG) <= CMAX classes
     if (p.C <= 16) return launch_one<ENC, 16, true, 1>(ma, mb, mc, p, grid, st);
