@@ -268,6 +268,48 @@ hdc_status hdc_sweep_eval(const uint32_t *H, const int32_t *y, int64_t N, int32_
                           int32_t *correct, int32_t *labels, void *ws, size_t ws_bytes,
                           hdc_stream_t stream);
 
+/* Level-ID encoding (Sec. 4.2 Algorithmic Choice: ID-based encoding as the
+ * alternative to random projection; Sec. 5.3: Micro-HD-Classification's
+ * encoder, with its N_LEVELS knob L).  Packed bits use the convention of the
+ * rest of the ABI: bit 1 = element -1.
+ *   level(x_f) = clamp(floor((x_f - lo) * scale), 0, L-1), the difference
+ *                and the product each rounded to FP32 (no fused multiply-
+ *                add), NaN -> level 0; scale = (float)(L / (x_hi - x_lo))
+ *                formed in double
+ *   LEVEL_l[d] = hi_hv[d] if l >= flip[d] else lo_hv[d]   (flip[d] in
+ *                1..L-1: level 0 is lo_hv, level L-1 is hi_hv)
+ *   s_d        = sum_f ID_f[d] * LEVEL_{level(x_f)}[d],  bit_d = s_d < 0
+ * over the kept dims of cfg's perforation (compacted at preparation, as
+ * for the random projection; enc, class_bits and flags are not used).
+ * The encoded rows feed hdc_train_epoch / hdc_hamming_argmin / hdc_cluster
+ * with D = Dk.  Limits: F < 8192 and (F + L) * 128 bytes <= 200 KB.       */
+typedef struct {
+    uint32_t struct_size;        /* = sizeof(hdc_levelid_model)             */
+    int32_t F, D, Dk, L, W;      /* W = hdc_words(Dk)                       */
+    float lo, scale;
+    const uint32_t *id;          /* F x W packed ID hypervectors (kept dims) */
+    const uint32_t *level;       /* L x W packed level hypervectors         */
+} hdc_levelid_model;
+
+/* Bytes of the model buffer (256-byte aligned, caller-owned).             */
+hdc_status hdc_levelid_model_bytes(int32_t F, int32_t D, int32_t L, const hdc_approx_config *cfg,
+                                   size_t *bytes);
+
+/* Build a Level-ID model in buf.  Device inputs: id_bits (F x W(D) packed ID
+ * hypervectors), lo_hv and hi_hv (W(D) words each), flip (D int32).  The
+ * random hypervectors and flip levels are the caller's draws.  flip_error
+ * (optional device int32) is set to 1 if some flip[d] is outside 1..L-1.
+ * Errors: HDC_ERR_INVALID_ARG (sizes, pointers, x_hi <= x_lo, non-finite
+ * bounds), HDC_ERR_UNSUPPORTED (limits), HDC_ERR_WORKSPACE, HDC_ERR_CUDA. */
+hdc_status hdc_levelid_prepare(const uint32_t *id_bits, const uint32_t *lo_hv, const uint32_t *hi_hv,
+                               const int32_t *flip, int32_t F, int32_t D, int32_t L, float x_lo,
+                               float x_hi, const hdc_approx_config *cfg, void *buf, size_t buf_bytes,
+                               int32_t *flip_error, hdc_levelid_model *out, hdc_stream_t stream);
+
+/* Encode N rows of X (N x F FP32, device) into H (N x W packed, device).   */
+hdc_status hdc_levelid_encode(const float *X, int64_t N, const hdc_levelid_model *m, uint32_t *H,
+                              hdc_stream_t stream);
+
 /* HD-Clustering (Sec. 5.1): K-means over binary hypervectors.  The paper's
  * benchmark clusters encoded points with K cluster hypervectors, refining
  * them for TRAIN_ITERATIONS iterations, and scores the result by NMI; its

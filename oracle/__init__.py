@@ -74,6 +74,10 @@ def _L():
                 "orc_round_bf16_f64": (f64, [f64]),
                 "orc_round_bf16_f64_array": (None, [P, i64, P]),
                 "orc_cosine_float": (None, [P, i64, P, i64, i64, P]),
+                "orc_levelid_scale": (f32, [i32, f32, f32]),
+                "orc_levelid_quantise": (None, [P, i64, f32, f32, i32, P]),
+                "orc_levelid_levels": (None, [P, P, P, i64, i32, P]),
+                "orc_levelid_encode": (None, [P, i64, i64, P, P, i64, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -336,6 +340,38 @@ def classify_float(X: np.ndarray, Bt: np.ndarray, acc: np.ndarray, enc: int = EN
     chat = gather_cols(class_quantise(acc, class_bits_), dims)
     sc = cosine_float(q, chat)
     return argmax(sc), sc, q
+
+
+def levelid_scale(L: int, x_lo: float, x_hi: float) -> float:
+    return float(_L().orc_levelid_scale(L, x_lo, x_hi))
+
+
+def levelid_quantise(X: np.ndarray, x_lo: float, scale: float, L: int) -> np.ndarray:
+    X = _c(X, np.float32)
+    out = np.empty(X.shape, dtype=np.int32)
+    _L().orc_levelid_quantise(_p(X), X.size, x_lo, scale, L, _p(out))
+    return out
+
+
+def levelid_levels(lo_bits: np.ndarray, hi_bits: np.ndarray, flip: np.ndarray, L: int) -> np.ndarray:
+    lo_bits = _c(lo_bits, np.uint8); hi_bits = _c(hi_bits, np.uint8); flip = _c(flip, np.int32)
+    out = np.empty((L, lo_bits.size), dtype=np.uint8)
+    _L().orc_levelid_levels(_p(lo_bits), _p(hi_bits), _p(flip), lo_bits.size, L, _p(out))
+    return out
+
+
+def levelid_encode(X: np.ndarray, id_bits: np.ndarray, lo_bits: np.ndarray, hi_bits: np.ndarray,
+                   flip: np.ndarray, L: int, x_lo: float, x_hi: float, dims: np.ndarray):
+    """Level-ID encoding over the kept dims (Sec. 4.2 ID-based encoding):
+    quantise each feature to a level, bind its ID hypervector with that
+    level's hypervector, bundle over features, binarise.  Returns (bits, s)."""
+    lev = levelid_quantise(X, x_lo, levelid_scale(L, x_lo, x_hi), L)
+    levels = levelid_levels(lo_bits, hi_bits, flip, L)
+    idk = gather_cols(_c(id_bits, np.uint8), dims)
+    lvk = gather_cols(levels, dims)
+    s = np.empty((X.shape[0], len(dims)), dtype=np.int64)
+    _L().orc_levelid_encode(_p(lev), X.shape[0], X.shape[1], _p(idk), _p(lvk), len(dims), _p(s))
+    return binarise(s), s
 
 
 def classify(X: np.ndarray, Bt: np.ndarray, acc: np.ndarray, enc: int = ENC_FP32,

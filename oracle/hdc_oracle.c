@@ -397,3 +397,55 @@ void orc_cosine_float(const double *q, int64_t N, const int64_t *chat, int64_t C
         }
     }
 }
+
+/* Level-ID encoding (Sec. 4.2 Algorithmic Choice: ID-based encoding; the
+ * Level-ID encoder of Micro-HD-Classification, Sec. 5.3).
+ *
+ * Quantisation of a feature to one of L levels over [x_lo, x_hi]:
+ *   scale = (float)(L / (x_hi - x_lo))          (the quotient in double)
+ *   t     = (x - lo) * scale                    (each operation in float)
+ *   level = L-1 if t >= L, floor(t) if t > 0, else 0 (also for NaN).       */
+float orc_levelid_scale(int32_t L, float x_lo, float x_hi)
+{
+    return (float)((double)L / ((double)x_hi - (double)x_lo));
+}
+
+void orc_levelid_quantise(const float *x, int64_t n, float lo, float scale, int32_t L, int32_t *level)
+{
+    for (int64_t i = 0; i < n; i++) {
+        float d = x[i] - lo;
+        float t = d * scale;
+        if (t >= (float)L)
+            level[i] = L - 1;
+        else if (t > 0.0f)
+            level[i] = (int32_t)floorf(t);
+        else
+            level[i] = 0;
+    }
+}
+
+/* Level hypervectors: level l takes hi[d] where l >= flip[d], else lo[d]
+ * (unpacked bits, 1 = element -1).                                        */
+void orc_levelid_levels(const uint8_t *lo, const uint8_t *hi, const int32_t *flip, int64_t D, int32_t L,
+                        uint8_t *levels)
+{
+    for (int32_t l = 0; l < L; l++)
+        for (int64_t d = 0; d < D; d++) levels[(int64_t)l * D + d] = l >= flip[d] ? hi[d] : lo[d];
+}
+
+/* s[i][d] = sum_f id[f][d] * lev[level[i][f]][d] with bits mapped to +-1
+ * (bit 1 = -1), exact in int64.                                            */
+void orc_levelid_encode(const int32_t *level, int64_t N, int64_t F, const uint8_t *id, const uint8_t *lev,
+                        int64_t D, int64_t *s)
+{
+    for (int64_t i = 0; i < N; i++)
+        for (int64_t d = 0; d < D; d++) {
+            int64_t acc = 0;
+            for (int64_t f = 0; f < F; f++) {
+                int64_t a = 1 - 2 * (int64_t)id[f * D + d];
+                int64_t b = 1 - 2 * (int64_t)lev[(int64_t)level[i * F + f] * D + d];
+                acc += a * b;
+            }
+            s[i * D + d] = acc;
+        }
+}

@@ -63,6 +63,10 @@ _SIGS = {
     "hdc_sweep_workspace_bytes": (_I32, [_I32, _I32, _P, _P]),
     "hdc_sweep_eval": (_I32, [_P, _P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _SZ, _P]),
     "hdc_cluster_workspace_bytes": (_I32, [_I64, _I32, _I32, _P]),
+    "hdc_levelid_model_bytes": (_I32, [_I32, _I32, _I32, _P, _P]),
+    "hdc_levelid_prepare": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, ctypes.c_float, ctypes.c_float, _P, _P, _SZ,
+                                   _P, _P, _P]),
+    "hdc_levelid_encode": (_I32, [_P, _I64, _P, _P, _P]),
     "hdc_cluster": (_I32, [_P, _I64, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "hdc_stream_status": (_I32, [_P]),
     "hdc_profile_events": (None, [_P, _P]),
@@ -376,6 +380,65 @@ def cluster(H: torch.Tensor, D: int, init: torch.Tensor, iters: int, train_sim: 
           ctypes.byref(isim) if isim else None, _ptr(cls), _ptr(acc), _ptr(labels), _ptr(changes), _ptr(ws),
           ws.numel(), _stream(stream))
     return labels, cls, acc, changes[:iters]
+
+
+class LevelIdModelC(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("F", ctypes.c_int32), ("D", ctypes.c_int32),
+                ("Dk", ctypes.c_int32), ("L", ctypes.c_int32), ("W", ctypes.c_int32), ("lo", ctypes.c_float),
+                ("scale", ctypes.c_float), ("id", ctypes.c_void_p), ("level", ctypes.c_void_p)]
+
+
+def pack_bits(bits) -> torch.Tensor:
+    """Unpacked 0/1 rows (n x L, uint8 or bool tensor) -> packed int32 words
+    (n x hdc_words(L)), bit d of a row in word d // 32, bit d % 32."""
+    bits = torch.as_tensor(bits)
+    n, L = bits.shape
+    W = words(L)
+    padded = torch.zeros((n, W * 32), dtype=torch.int64, device=bits.device)
+    padded[:, :L] = bits.to(torch.int64)
+    weights = (torch.ones(32, dtype=torch.int64, device=bits.device) << torch.arange(32, device=bits.device))
+    w = (padded.view(n, W, 32) * weights).sum(-1)
+    return (w - ((w >> 31) << 32)).to(torch.int32)    # two's-complement view of the uint32 word
+
+
+class LevelIdModel:
+    """Level-ID encoder (hdc_levelid_prepare): ID hypervectors (F x D bits),
+    level end points lo / hi (D bits each) and flip levels (D, in 1..L-1),
+    all device tensors of the caller's draws."""
+
+    def __init__(self, id_bits: torch.Tensor, lo_bits: torch.Tensor, hi_bits: torch.Tensor, flip: torch.Tensor,
+                 L: int, x_lo: float, x_hi: float, cfg: ApproxConfig | None = None, stream=None):
+        F, D = id_bits.shape
+        self.idp = pack_bits(id_bits)
+        self.lop = pack_bits(lo_bits.view(1, -1))
+        self.hip = pack_bits(hi_bits.view(1, -1))
+        self.flip = flip.to(torch.int32).contiguous()
+        c = cfg.c() if cfg else None
+        n = ctypes.c_size_t()
+        _call("hdc_levelid_model_bytes", F, D, L, ctypes.byref(c) if c else None, ctypes.byref(n))
+        self.buf = _empty_bytes(n.value, id_bits.device)
+        self.flip_error = torch.zeros(1, dtype=torch.int32, device=id_bits.device)
+        self.m = LevelIdModelC()
+        _call("hdc_levelid_prepare", _ptr(self.idp), _ptr(self.lop), _ptr(self.hip), _ptr(self.flip), F, D, L,
+              x_lo, x_hi, ctypes.byref(c) if c else None, _ptr(self.buf), n.value, _ptr(self.flip_error),
+              ctypes.byref(self.m), _stream(stream))
+
+    @property
+    def W(self) -> int:
+        return self.m.W
+
+    @property
+    def Dk(self) -> int:
+        return self.m.Dk
+
+
+def levelid_encode(X: torch.Tensor, model: LevelIdModel, out: torch.Tensor | None = None, stream=None):
+    """Packed Level-ID hypervectors (N x W int32 view of uint32 words)."""
+    assert X.dtype == torch.float32 and X.dim() == 2 and X.shape[1] == model.m.F
+    N = X.shape[0]
+    H = torch.empty((N, model.W), dtype=torch.int32, device=X.device) if out is None else out
+    _call("hdc_levelid_encode", _ptr(X), N, ctypes.byref(model.m), _ptr(H), _stream(stream))
+    return H
 
 
 def stream_status(stream=None) -> int:

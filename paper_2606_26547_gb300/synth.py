@@ -138,6 +138,18 @@ def make(workload: str | Workload, n_train: int | None = None, n_query: int | No
     return dict(Bt=Bt, Xtr=Xtr, ytr=ytr, Xq=Xq, yq=yq)
 
 
+def levelid_hvs(F: int, D: int, L: int, seed: int):
+    """Random draws of a Level-ID encoder: ID hypervector bits (F x D), the
+    two level end points (D bits each), Bernoulli(0.5), and the level at
+    which each dim switches between them, uniform in 1..L-1."""
+    r = _rng(seed + 11)
+    ids = r.integers(0, 2, size=(F, D)).astype(np.uint8)
+    lo = r.integers(0, 2, size=D).astype(np.uint8)
+    hi = r.integers(0, 2, size=D).astype(np.uint8)
+    flip = r.integers(1, L, size=D).astype(np.int32)
+    return ids, lo, hi, flip
+
+
 def cluster_init(n: int, K: int, seed: int) -> np.ndarray:
     """K distinct point indices (the initial cluster hypervectors), drawn
     with the workload's init stream (base seed + 7)."""

@@ -579,3 +579,71 @@ def test_float_queries_integer_data(orc):
     q8 = orc.float_queries(d["Xq"], d["Bt"], orc.ENC_FP8, dims)
     _, sx = orc.quantise_rows(d["Xq"], orc.ENC_FP8)
     assert np.array_equal(q8 * sx[:, None], want)
+
+
+# ------------------------------------------------------ Level-ID encoding
+
+def test_levelid_quantise_bins(orc):
+    """lo = -8, hi = 8, L = 16: scale 1, so the level of an exactly
+    representable x is floor(x + 8), clamped; out-of-range values clamp,
+    NaN gives 0; levels never decrease with x; uniform x fills the bins
+    evenly."""
+    sc = orc.levelid_scale(16, -8.0, 8.0)
+    assert sc == 1.0
+    x = np.array([-100, -8, -7.5, -0.25, 0, 3.999, 7.75, 8, 1e30, np.nan, -np.inf, np.inf], np.float32)
+    want = [0, 0, 0, 7, 8, 11, 15, 15, 15, 0, 0, 15]
+    assert orc.levelid_quantise(x, -8.0, sc, 16).tolist() == want
+    rng = np.random.default_rng(2)
+    for L, lo, hi in ((128, -1.3, 2.9), (2, 0.0, 1.0), (1000, -5.0, 5.0)):
+        s = orc.levelid_scale(L, lo, hi)
+        xs = np.sort(rng.uniform(lo - 0.5, hi + 0.5, 20000).astype(np.float32))
+        lv = orc.levelid_quantise(xs, lo, s, L)
+        assert lv.min() >= 0 and lv.max() <= L - 1 and np.all(np.diff(lv) >= 0)
+        inside = (xs > lo + 1e-3) & (xs < hi - 1e-3)
+        # each level covers (hi - lo) / L of the range, up to FP32 rounding at the edges
+        assert np.all(np.abs(lv[inside] - (xs[inside] - lo) * L / (hi - lo)) <= 1.0 + 1e-3)
+        if L <= 128:
+            cnt = np.bincount(lv[inside], minlength=L)
+            assert cnt.min() > 0.6 * cnt.mean() and cnt.max() < 1.4 * cnt.mean()
+
+
+def test_levelid_levels_interpolate(orc):
+    rng = np.random.default_rng(3)
+    D, L = 500, 9
+    lo, hi = rng.integers(0, 2, D).astype(np.uint8), rng.integers(0, 2, D).astype(np.uint8)
+    flip = rng.integers(1, L, D).astype(np.int32)
+    lv = orc.levelid_levels(lo, hi, flip, L)
+    assert np.array_equal(lv[0], lo) and np.array_equal(lv[L - 1], hi)
+    for i in range(L):
+        for j in range(i, L):
+            want = int(((lo != hi) & (flip > i) & (flip <= j)).sum())
+            assert int((lv[i] != lv[j]).sum()) == want
+    d = [int((lv[0] != lv[j]).sum()) for j in range(L)]
+    assert d == sorted(d)
+
+
+def test_levelid_encode_bind_bundle(orc):
+    """s = sum_f (+-1 id_f) * (+-1 level row of x_f), checked with a dense
+    +-1 einsum; F = 1 is the XOR of the ID and level bits; the sign bit is the
+    majority of the XORs (more than floor(F/2) differ)."""
+    rng = np.random.default_rng(4)
+    for F, D, L in ((1, 64, 4), (7, 100, 16), (8, 33, 2), (61, 257, 128)):
+        ids = rng.integers(0, 2, (F, D)).astype(np.uint8)
+        lo, hi = rng.integers(0, 2, D).astype(np.uint8), rng.integers(0, 2, D).astype(np.uint8)
+        flip = rng.integers(1, L, D).astype(np.int32)
+        X = rng.uniform(-1.2, 1.2, (25, F)).astype(np.float32)
+        dims = orc.kept_dims(D, 0.0, 1.0, 1)
+        bits, s = orc.levelid_encode(X, ids, lo, hi, flip, L, -1.0, 1.0, dims)
+        lev = orc.levelid_quantise(X, -1.0, orc.levelid_scale(L, -1.0, 1.0), L)
+        LV = 1 - 2 * orc.levelid_levels(lo, hi, flip, L).astype(np.int64)
+        ID = 1 - 2 * ids.astype(np.int64)
+        want = np.einsum("fd,nfd->nd", ID, LV[lev])
+        assert np.array_equal(s, want)
+        xor_cnt = (ids[None, :, :] ^ orc.levelid_levels(lo, hi, flip, L)[lev]).sum(1)
+        assert np.array_equal(bits, (xor_cnt > F // 2).astype(np.uint8))
+        if F == 1:
+            assert np.array_equal(bits, ids[0][None, :] ^ orc.levelid_levels(lo, hi, flip, L)[lev[:, 0]])
+    # perforation keeps the same dims of s
+    dims = orc.kept_dims(257, 0.1, 0.9, 3)
+    b2, s2 = orc.levelid_encode(X, ids, lo, hi, flip, L, -1.0, 1.0, dims)
+    assert np.array_equal(s2, s[:, dims]) and np.array_equal(b2, bits[:, dims])
