@@ -2,7 +2,9 @@
 Sec. 3 and Sec. 5.2), with every candidate scored on the GPU.
 
 Knobs (Sec. 4.2, 4.3) as this library implements them:
-  enc      element type of the encoding: fp32, bf16 or fp8 (global)
+  enc      the encoder: random projection with element type fp32, bf16 or
+           fp8, or Level-ID with N_LEVELS levels ("lid<L>"; the encoder
+           algorithmic choice and the N_LEVELS knob of Sec. 5.3)
   dim      encoding dimensionality D' in {D, D/2, D/4, ...} (global)
   epochs   TRAIN_ITERATIONS: retraining epochs after bundling (custom knob)
   start, end, stride
@@ -42,6 +44,13 @@ import time
 import numpy as np
 
 ENCS = ("fp32", "bf16", "fp8")
+LEVELS = (16, 32, 64, 128, 256, 512, 814)
+LID_ENCS = tuple("lid%d" % L for L in LEVELS)
+
+
+def lid_levels(enc: str) -> int:
+    """N_LEVELS of a Level-ID encoder name, 0 for a random projection."""
+    return int(enc[3:]) if enc.startswith("lid") else 0
 STRIDES = (1, 2, 4, 8, 16, 32)
 BITS = (1, 4, 8)
 GRID = 100          # start / end fractions on a 1/GRID grid
@@ -80,17 +89,19 @@ class Space:
     SPANS = (("start", "end"),)
     CONFIG = Config
 
-    def __init__(self, mode: str, D: int, max_epochs: int, dim_levels: int = 5, min_dim: int = 128):
+    def __init__(self, mode: str, D: int, max_epochs: int, dim_levels: int = 5, min_dim: int = 128,
+                 levelid: bool = False):
         if mode not in MODES:
             raise ValueError(mode)
         self.mode = mode
+        self.encs = ENCS + (LID_ENCS if levelid else ())
         self.values = self._values(mode, tuple(D >> k for k in range(dim_levels) if (D >> k) >= min_dim),
                                    max_epochs)
         self.sizes = tuple(len(self.values[k]) for k in self.KNOBS)
 
     def _values(self, mode, dims, max_epochs):
         starts, ends, strides = perf_values(mode)
-        return dict(enc=ENCS, dim=dims, epochs=tuple(range(max_epochs + 1)), start=starts, end=ends,
+        return dict(enc=self.encs, dim=dims, epochs=tuple(range(max_epochs + 1)), start=starts, end=ends,
                     stride=strides, bits=BITS, query=QUERIES)
 
     def log10_size(self) -> float:
@@ -112,6 +123,8 @@ class Space:
     def valid(self, c) -> bool:
         if getattr(c, "query", "binary") == "float" and c.bits == 1:
             return False     # a float query is compared by cosine only
+        if lid_levels(c.enc) and (c.bits != 1 or getattr(c, "query", "binary") != "binary"):
+            return False     # Level-ID rows are binary, compared by Hamming
         return all(round((getattr(c, e) - getattr(c, a)) * GRID) >= MIN_SPAN for a, e in self.SPANS)
 
     def repair(self, point):
@@ -125,8 +138,10 @@ class Space:
                 else:
                     p[ks] -= 1
         if "query" in self.KNOBS:
-            kq, kb = self.KNOBS.index("query"), self.KNOBS.index("bits")
-            if self.values["query"][p[kq]] == "float" and self.values["bits"][p[kb]] == 1:
+            kq, kb, ke = self.KNOBS.index("query"), self.KNOBS.index("bits"), self.KNOBS.index("enc")
+            if lid_levels(self.values["enc"][p[ke]]):
+                p[kq], p[kb] = self.values["query"].index("binary"), self.values["bits"].index(1)
+            elif self.values["query"][p[kq]] == "float" and self.values["bits"][p[kb]] == 1:
                 p[kb] = self.values["bits"].index(8)
         return tuple(p)
 
@@ -401,10 +416,10 @@ class GpuEvaluator:
     hdc_sweep_eval and prices them from the tables."""
 
     def __init__(self, workload: str, max_epochs: int, dims, n_train=None, n_val=None, device="cuda",
-                 reps: int = 5):
+                 reps: int = 5, encs=ENCS):
         import torch
         from . import hdc, synth
-        self.torch, self.hdc = torch, hdc
+        self.torch, self.hdc, self.encs = torch, hdc, tuple(encs)
         self.w = w = synth.WORKLOADS[workload] if isinstance(workload, str) else workload
         d = synth.make(w, n_train=n_train, n_query=n_val)
         dev = torch.device(device)
@@ -414,6 +429,14 @@ class GpuEvaluator:
         self.ytr = torch.from_numpy(d["ytr"]).to(dev)
         self.Xv = torch.from_numpy(d["Xq"]).to(dev)
         self.yv = torch.from_numpy(d["yq"]).to(dev)
+        # Level-ID: the caller's draws (ID rows, level end points, flip levels
+        # per N_LEVELS) and the feature range of the training set
+        self.lid = {}
+        self.x_lo, self.x_hi = float(d["Xtr"].min()), float(d["Xtr"].max())
+        for enc in self.encs:
+            if lid_levels(enc):
+                self.lid[enc] = tuple(torch.from_numpy(a).to(dev)
+                                      for a in synth.levelid_hvs(w.F, w.D, lid_levels(enc), w.seed))
         self.max_epochs, self.dims = max_epochs, tuple(dims)
         self.snap, self.Hv = {}, {}
         self.t_encode_train, self.t_train = {}, {}
@@ -434,15 +457,29 @@ class GpuEvaluator:
             ts.append(a.elapsed_time(b))
         return float(np.median(ts))
 
+    def _lid_model(self, enc: str, dim: int, cfg=None):
+        ids, lo, hi, flip = self.lid[enc]
+        return self.hdc.LevelIdModel(ids[:, :dim].contiguous(), lo[:dim].contiguous(), hi[:dim].contiguous(),
+                                     flip[:dim].contiguous(), lid_levels(enc), self.x_lo, self.x_hi, cfg)
+
+    def _encoder(self, enc: str, dim: int, N: int):
+        """(encode(X, out) for N rows at D' = dim, words per row)."""
+        hdc = self.hdc
+        if lid_levels(enc):
+            m = self._lid_model(enc, dim)
+            return (lambda X, out: hdc.levelid_encode(X, m, out=out)), m.W
+        base = hdc.Model(self.Bt[:dim], hdc.ApproxConfig(enc=enc))
+        ws = base.workspace(N)
+        return (lambda X, out: hdc.encode(X, base, ws=ws, out=out)), base.W
+
     def _prepare(self):
         torch, hdc, w = self.torch, self.hdc, self.w
         N = self.Xtr.shape[0]
-        for enc in ENCS:
+        for enc in self.encs:
             for dim in self.dims:
-                base = hdc.Model(self.Bt[:dim], hdc.ApproxConfig(enc=enc))
-                ws = base.workspace(N)
-                Htr = torch.empty((N, base.W), dtype=torch.int32, device=self.dev)
-                self.t_encode_train[(enc, dim)] = self._ms(lambda: hdc.encode(self.Xtr, base, ws=ws, out=Htr))
+                encf, W = self._encoder(enc, dim, N)
+                Htr = torch.empty((N, W), dtype=torch.int32, device=self.dev)
+                self.t_encode_train[(enc, dim)] = self._ms(lambda: encf(self.Xtr, Htr))
                 n = ctypes.c_size_t()
                 hdc._call("hdc_train_workspace_bytes", N, dim, w.C, ctypes.byref(n))
                 tws = hdc._empty_bytes(n.value, self.dev)
@@ -464,11 +501,25 @@ class GpuEvaluator:
                 cum = np.cumsum([a.elapsed_time(b) for a, b in times])
                 for ep in range(self.max_epochs + 1):
                     self.t_train[(enc, dim, ep)] = float(cum[ep])
-                self.Hv[(enc, dim)] = hdc.encode(self.Xv, base)
+                encv, _ = self._encoder(enc, dim, self.Xv.shape[0])
+                self.Hv[(enc, dim)] = torch.empty((self.Xv.shape[0], W), dtype=torch.int32, device=self.dev)
+                encv(self.Xv, self.Hv[(enc, dim)])
         torch.cuda.synchronize()
 
     def classify_ms(self, c: Config) -> float:
         hdc, torch = self.hdc, self.torch
+        if lid_levels(c.enc):
+            # Level-ID encode of the kept dims + Hamming arg-min over them
+            cfg = hdc.ApproxConfig(perf_start=c.start, perf_end=c.end, perf_stride=c.stride)
+            Dk = hdc.kept_dims(c.dim, cfg)
+            key = (c.enc, Dk, 1, "binary")
+            if key not in self.t_classify:
+                m = self._lid_model(c.enc, c.dim, cfg)
+                H = torch.empty((self.Xv.shape[0], m.W), dtype=torch.int32, device=self.dev)
+                cls = torch.zeros((self.w.C, m.W), dtype=torch.int32, device=self.dev)
+                self.t_classify[key] = self._ms(lambda: (hdc.levelid_encode(self.Xv, m, out=H),
+                                                         hdc.hamming_argmin(H, cls, Dk)))
+            return self.t_classify[key]
         cfg = hdc.ApproxConfig(enc=c.enc, class_bits=c.bits, perf_start=c.start, perf_end=c.end,
                                perf_stride=c.stride, float_query=c.query == "float")
         Dk = hdc.kept_dims(c.dim, cfg)
@@ -587,6 +638,7 @@ def main(argv=None):
     ap.add_argument("--seconds", type=float, default=None, help="time budget per pruning mode")
     ap.add_argument("--modes", default=",".join(MODES))
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--levelid", action="store_true", help="add the Level-ID encoder (N_LEVELS knob)")
     a = ap.parse_args(argv)
     from . import hdc, synth
     hdc.load()
@@ -596,8 +648,8 @@ def main(argv=None):
     t = time.perf_counter()
     if a.app == "classify":
         dims = Space("none", w.D, epochs).values["dim"]
-        ev = GpuEvaluator(wl, epochs, dims)
-        space_cls, base = Space, baseline_config(w.D, epochs)
+        ev = GpuEvaluator(wl, epochs, dims, encs=ENCS + (LID_ENCS if a.levelid else ()))
+        space_cls, base = (lambda m, D, e: Space(m, D, e, levelid=a.levelid)), baseline_config(w.D, epochs)
     else:
         ev = ClusterEvaluator(wl)
         space_cls, base = ClusterSpace, cluster_baseline(w.D, epochs)

@@ -22,7 +22,13 @@ def ev():
 
 def one_by_one(ev, c):
     """Train at c.dim for c.epochs and classify under c through the ABI."""
-    from paper_2606_26547_gb300 import hdc
+    from paper_2606_26547_gb300 import hdc, tuner as T
+    if T.lid_levels(c.enc):
+        m = ev._lid_model(c.enc, c.dim)
+        acc, cls, _ = hdc.train(hdc.levelid_encode(ev.Xtr, m), ev.ytr, c.dim, ev.w.C, c.epochs)
+        cfg = hdc.ApproxConfig(perf_start=c.start, perf_end=c.end, perf_stride=c.stride)
+        lab = hdc.hamming_argmin(hdc.levelid_encode(ev.Xv, m), cls, c.dim, cfg)
+        return float((lab == ev.yv).sum().item()) / ev.Xv.shape[0]
     Bt = ev.Bt[:c.dim]
     H = hdc.encode(ev.Xtr, hdc.Model(Bt, hdc.ApproxConfig(enc=c.enc)))
     acc, _, _ = hdc.train(H, ev.ytr, c.dim, ev.w.C, c.epochs)
@@ -78,3 +84,21 @@ def test_cluster_tuner_nmi_equals_direct_run(ev):
         assert s.results[c].accuracy == metrics.nmi(run.y, lab.cpu().numpy()), c
     ms, nmi = run.graph_ms(cev._cc(s.best), reps=2)
     assert ms > 0 and nmi == s.results[s.best].accuracy
+
+
+def test_tuner_levelid_candidates_equal_one_by_one():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_26547_gb300 import synth, tuner as T
+    w = synth.Workload("tune_lid", 200, 1024, 6, 1500, 800, "gauss", 2.0, 3, 7300)
+    ev = T.GpuEvaluator(w, 3, (1024, 512), reps=2, encs=("fp8", "lid16", "lid128"))
+    space = T.Space("full", 1024, 3, dim_levels=2, levelid=True)
+    space.values["enc"] = ("fp8", "lid16", "lid128")
+    space.sizes = tuple(len(space.values[k]) for k in space.KNOBS)
+    s = T.Search(space, ev, T.Config("fp8", 1024, 3, 0.0, 1.0, 1, 8, "float"), seed=3, batch=24)
+    s.run(evaluations=120)
+    lid = [c for c in s.results if T.lid_levels(c.enc)]
+    assert len(lid) >= 5
+    for c in lid[:6]:
+        assert s.results[c].accuracy == one_by_one(ev, c), c
+        assert s.results[c].ms > 0

@@ -146,3 +146,20 @@ def test_cluster_search_with_fake_evaluator():
     s = T.Search(T.ClusterSpace("end_only", 1024, 20), ev, T.cluster_baseline(1024, 20), seed=1)
     s.run(evaluations=800)
     assert s.feasible(s.best) and s.report()["speedup"] > 3
+
+
+def test_levelid_encoders_are_binary_hamming_only():
+    sp = T.Space("full", 2048, 10, levelid=True)
+    assert set(T.LID_ENCS) <= set(sp.values["enc"]) and T.lid_levels("lid128") == 128 and T.lid_levels("fp8") == 0
+    assert not sp.valid(T.Config("lid64", 2048, 3, 0.0, 1.0, 1, 8, "binary"))
+    assert not sp.valid(T.Config("lid64", 2048, 3, 0.0, 1.0, 1, 1, "float"))
+    rng = np.random.default_rng(6)
+    seen = 0
+    for _ in range(2000):
+        c = sp.config(sp.random(rng))
+        assert sp.valid(c)
+        if T.lid_levels(c.enc):
+            seen += 1
+            assert c.bits == 1 and c.query == "binary"
+    assert seen > 500
+    assert "lid16" not in T.Space("full", 2048, 10).values["enc"]
