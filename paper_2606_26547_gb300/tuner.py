@@ -569,6 +569,8 @@ class GpuEvaluator:
         for enc, dim, ep, chunk, corr in pending:
             corr = corr.cpu().numpy()
             for jb, b in enumerate(BITS):
+                if lid_levels(enc) and b != 1:
+                    continue   # Level-ID candidates are Hamming only
                 for j, (s, e, st) in enumerate(chunk):
                     out[Config(enc, dim, ep, s, e, st, b)] = float(corr[jb, j]) / N
         return out

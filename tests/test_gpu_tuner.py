@@ -98,6 +98,7 @@ def test_tuner_levelid_candidates_equal_one_by_one():
     s = T.Search(space, ev, T.Config("fp8", 1024, 3, 0.0, 1.0, 1, 8, "float"), seed=3, batch=24)
     s.run(evaluations=120)
     lid = [c for c in s.results if T.lid_levels(c.enc)]
+    assert all(space.contains(c) for c in lid)
     assert len(lid) >= 5
     for c in lid[:6]:
         assert s.results[c].accuracy == one_by_one(ev, c), c
