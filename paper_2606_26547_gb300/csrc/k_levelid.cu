@@ -17,11 +17,13 @@
 //
 // Encode kernel: one block per (32 queries, 32 words); the block stages its
 // word slice of every ID row and every level row in shared memory.  A warp
-// takes one query at a time, a lane one word (32 dims): lane j quantises
-// feature f0 + j of the query, the warp broadcasts the levels by shuffle, and
-// each lane adds id ^ level rows into a bit-sliced counter (carry-save adders
-// over groups of 8 rows, then a ripple-carry add of the weight-8 plane), then
-// compares the counter against floor(F/2) bit-sliced.
+// takes four queries at a time (four independent counter chains, each ID
+// word loaded once for the four), a lane one word (32 dims): lane j
+// quantises feature f0 + j of each query, the warp broadcasts the levels by
+// shuffle, and each lane adds id ^ level rows into a bit-sliced counter per
+// query (carry-save adders over groups of 8 rows, then a ripple-carry add of
+// the weight-8 plane), then compares the counter against floor(F/2)
+// bit-sliced.
 #include <cmath>
 #include <cstring>
 
@@ -52,6 +54,68 @@ __device__ __forceinline__ int quant_level(float x, float lo, float scale, int L
     return 0;                    // t <= 0, or NaN
 }
 
+// Add 8 rows of weight 1 into the counter (ones, twos, fours, hp): a
+// carry-save tree to one row of weight 8, then a ripple-carry add of it.
+__device__ __forceinline__ void add8(uint32_t &ones, uint32_t &twos, uint32_t &fours, uint32_t (&hp)[HPLANES],
+                                     const uint32_t (&r)[8])
+{
+    uint32_t t2a, t2b, t4a, t4b, e8;
+    csa(t2a, ones, ones, r[0], r[1]);
+    csa(t2b, ones, ones, r[2], r[3]);
+    csa(t4a, twos, twos, t2a, t2b);
+    csa(t2a, ones, ones, r[4], r[5]);
+    csa(t2b, ones, ones, r[6], r[7]);
+    csa(t4b, twos, twos, t2a, t2b);
+    csa(e8, fours, fours, t4a, t4b);
+    uint32_t c = e8;
+#pragma unroll
+    for (int k = 0; k < HPLANES; k++) {
+        const uint32_t t = hp[k] & c;
+        hp[k] ^= c;
+        c = t;
+    }
+}
+
+// Add one row of weight 1 (ripple carry through every plane).
+__device__ __forceinline__ void add1(uint32_t &ones, uint32_t &twos, uint32_t &fours, uint32_t (&hp)[HPLANES],
+                                     uint32_t c)
+{
+    uint32_t t = ones & c; ones ^= c; c = t;
+    t = twos & c; twos ^= c; c = t;
+    t = fours & c; fours ^= c; c = t;
+#pragma unroll
+    for (int k = 0; k < HPLANES; k++) {
+        const uint32_t u = hp[k] & c;
+        hp[k] ^= c;
+        c = u;
+    }
+}
+
+// cnt > T per bit position, from the most significant plane down.
+__device__ __forceinline__ uint32_t greater(uint32_t ones, uint32_t twos, uint32_t fours,
+                                            const uint32_t (&hp)[HPLANES], uint32_t T)
+{
+    uint32_t gt = 0, eq = 0xffffffffu;
+#pragma unroll
+    for (int k = HPLANES - 1; k >= 0; k--) {
+        const uint32_t cp = hp[k];
+        if ((T >> (k + 3)) & 1u) eq &= cp;
+        else { gt |= eq & cp; eq &= ~cp; }
+    }
+    const uint32_t pl[3] = {fours, twos, ones};
+#pragma unroll
+    for (int k = 2; k >= 0; k--) {
+        const uint32_t cp = pl[2 - k];
+        if ((T >> k) & 1u) eq &= cp;
+        else { gt |= eq & cp; eq &= ~cp; }
+    }
+    return gt;
+}
+
+// A warp encodes QW queries at once (independent counter chains; each ID
+// word loaded once for all of them).
+constexpr int QW = 4;
+
 __global__ void __launch_bounds__(LWARPS * 32) levelid_encode_kernel(const float *__restrict__ X, int64_t N, int F,
                                                                    int L, int W, float lo, float scale,
                                                                    const uint32_t *__restrict__ id,
@@ -74,74 +138,52 @@ __global__ void __launch_bounds__(LWARPS * 32) levelid_encode_kernel(const float
     }
     __syncthreads();
     const uint32_t T = (uint32_t)F >> 1;
-    for (int qi = warp; qi < LQ; qi += LWARPS) {
-        const int64_t q = (int64_t)blockIdx.x * LQ + qi;
-        if (q >= N) break;                        // warp-uniform
-        const float *xr = X + q * (int64_t)F;
-        uint32_t ones = 0, twos = 0, fours = 0;
-        uint32_t hp[HPLANES];
+    for (int qb = warp * QW; qb < LQ; qb += LWARPS * QW) {
+        const int64_t q0 = (int64_t)blockIdx.x * LQ + qb;
+        if (q0 >= N) break;                       // warp-uniform
+        uint32_t ones[QW], twos[QW], fours[QW], hp[QW][HPLANES];
 #pragma unroll
-        for (int k = 0; k < HPLANES; k++) hp[k] = 0;
-        uint32_t pend[8];
-        int np = 0;
+        for (int a = 0; a < QW; a++) {
+            ones[a] = twos[a] = fours[a] = 0;
+#pragma unroll
+            for (int k = 0; k < HPLANES; k++) hp[a][k] = 0;
+        }
         for (int f0 = 0; f0 < F; f0 += 32) {
             const int f = f0 + lane;
-            const int my = f < F ? quant_level(xr[f], lo, scale, L) : 0;
-            const int nf = min(32, F - f0);
-            for (int j = 0; j < nf; j++) {
-                const int l = __shfl_sync(0xffffffffu, my, j);
-                pend[np & 7] = sid[(f0 + j) * LWC + lane] ^ slv[l * LWC + lane];
-                if (++np == 8) {
-                    uint32_t t2a, t2b, t4a, t4b, e8;
-                    csa(t2a, ones, ones, pend[0], pend[1]);
-                    csa(t2b, ones, ones, pend[2], pend[3]);
-                    csa(t4a, twos, twos, t2a, t2b);
-                    csa(t2a, ones, ones, pend[4], pend[5]);
-                    csa(t2b, ones, ones, pend[6], pend[7]);
-                    csa(t4b, twos, twos, t2a, t2b);
-                    csa(e8, fours, fours, t4a, t4b);
-                    uint32_t c = e8;
+            int my[QW];   // level of feature f of each query (rows past N: level 0, not stored)
 #pragma unroll
-                    for (int k = 0; k < HPLANES; k++) {
-                        const uint32_t t = hp[k] & c;
-                        hp[k] ^= c;
-                        c = t;
+            for (int a = 0; a < QW; a++)
+                my[a] = (f < F && q0 + a < N) ? quant_level(X[(q0 + a) * (int64_t)F + f], lo, scale, L) : 0;
+            const int nf = min(32, F - f0);
+            int j = 0;
+            for (; j + 8 <= nf; j += 8) {
+                uint32_t idw[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) idw[u] = sid[(f0 + j + u) * LWC + lane];
+#pragma unroll
+                for (int a = 0; a < QW; a++) {
+                    uint32_t r[8];
+#pragma unroll
+                    for (int u = 0; u < 8; u++) {
+                        const int l = __shfl_sync(0xffffffffu, my[a], j + u);
+                        r[u] = idw[u] ^ slv[l * LWC + lane];
                     }
-                    np = 0;
+                    add8(ones[a], twos[a], fours[a], hp[a], r);
+                }
+            }
+            for (; j < nf; j++) {
+                const uint32_t idw = sid[(f0 + j) * LWC + lane];
+#pragma unroll
+                for (int a = 0; a < QW; a++) {
+                    const int l = __shfl_sync(0xffffffffu, my[a], j);
+                    add1(ones[a], twos[a], fours[a], hp[a], idw ^ slv[l * LWC + lane]);
                 }
             }
         }
-        // the last < 8 rows: ripple-carry adds of weight 1
-        for (int j = 0; j < np; j++) {
-            uint32_t c = pend[j];
-            uint32_t t = ones & c; ones ^= c; c = t;
-            t = twos & c; twos ^= c; c = t;
-            t = fours & c; fours ^= c; c = t;
 #pragma unroll
-            for (int k = 0; k < HPLANES; k++) {
-                const uint32_t u = hp[k] & c;
-                hp[k] ^= c;
-                c = u;
-            }
-        }
-        // cnt > T, bit-sliced, from the most significant plane down
-        uint32_t gt = 0, eq = 0xffffffffu;
-#pragma unroll
-        for (int k = HPLANES - 1; k >= 0; k--) {
-            const uint32_t cp = hp[k];
-            if ((T >> (k + 3)) & 1u) eq &= cp;
-            else { gt |= eq & cp; eq &= ~cp; }
-        }
-        {
-            const uint32_t pl[3] = {fours, twos, ones};
-#pragma unroll
-            for (int k = 2; k >= 0; k--) {
-                const uint32_t cp = pl[2 - k];
-                if ((T >> k) & 1u) eq &= cp;
-                else { gt |= eq & cp; eq &= ~cp; }
-            }
-        }
-        if (lane < nw) H[q * (int64_t)W + w0 + lane] = gt;
+        for (int a = 0; a < QW; a++)
+            if (q0 + a < N && lane < nw)
+                H[(q0 + a) * (int64_t)W + w0 + lane] = greater(ones[a], twos[a], fours[a], hp[a], T);
     }
 }
 
