@@ -60,8 +60,18 @@ bool model_ok(const hdc_model *m)
 }
 
 struct ModelLayout {
-    size_t bq, bscale, planes, csum, cnorm, total;
+    size_t bq, bscale, planes, csum, cnorm, csign, total;
 };
+
+// Binary classes with 17 <= C <= 112 also keep E4M3 +-1 class bytes for the
+// tensor-core Hamming distances: Cp rows (C rounded to 16) of one byte per
+// kept dim, padded to whole 192-dim tiles plus the 64 bytes the last tile's
+// second 128-byte box reaches past them.
+inline bool tc_hamming_classes(int bits, int C, uint32_t flags)
+{
+    return bits == 1 && C > 16 && C <= 112 && !(flags & HDC_FLAG_FLOAT_QUERY);
+}
+inline int ldcs_for(int Dk) { return (Dk + 191) / 192 * 192 + 64; }
 
 ModelLayout model_layout(int F, int Dk, int C, int enc, int bits, uint32_t flags)
 {
@@ -75,6 +85,8 @@ ModelLayout model_layout(int F, int Dk, int C, int enc, int bits, uint32_t flags
     L.planes = off; off = align_up(off + cls_bytes, kAlign);
     L.csum = off;   off = align_up(off + (size_t)C * 4, kAlign);
     L.cnorm = off;  off = align_up(off + (size_t)C * 8, kAlign);
+    L.csign = off;
+    off = align_up(off + (tc_hamming_classes(bits, C, flags) ? (size_t)cpad_for(C) * ldcs_for(Dk) : 0), kAlign);
     L.total = off;
     return L;
 }
@@ -233,6 +245,13 @@ hdc_status hdc_model_prepare(const float *Bt, int32_t F, int32_t D, const int32_
                                     float_query(cfg->flags) ? (uint16_t *)(b + L.planes) : nullptr, lds_for(Dk),
                                     st));
         if (s != HDC_OK) return s;
+        if (tc_hamming_classes(bits, C, cfg->flags)) {
+            m.cls_sign = (const uint8_t *)(b + L.csign);
+            m.ldcs = ldcs_for(Dk);
+            s = cu(launch_class_sign((const uint32_t *)(b + L.planes), C, m.W, Dk, cpad_for(C), m.ldcs,
+                                     (uint8_t *)(b + L.csign), st));
+            if (s != HDC_OK) return s;
+        }
     }
     *out = m;
     return HDC_OK;
@@ -398,6 +417,7 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *
         a.sx = sx; a.sb = m->b_scale; a.W = m->W;
         a.planes = m->cls; a.C = m->C; a.nb = nb; a.csum = m->cls_sum; a.cnorm = m->cls_norm;
         a.labels = labels; a.dists = dists; a.sims = scores;
+        a.cls_sign = m->cls_sign; a.ldcs = m->ldcs;
         // binary classes: fully fused; otherwise tensor-core encode + K4
         if (tc_supported(a)) return cu(timed_tc(a, st));
         TcArgs e = a;

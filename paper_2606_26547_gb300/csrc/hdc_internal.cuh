@@ -50,6 +50,11 @@ cudaError_t launch_class_prepare(const int32_t *acc, int C, int D, const Perf &p
                                  uint32_t *planes, int W, int32_t *csum, double *cnorm,
                                  uint16_t *vals, int ldv, cudaStream_t st);
 
+// Binary class planes (C x W words) -> E4M3 +-1 bytes (Cp x ldcs; 0 past Dk
+// and for rows C..Cp-1) for the tensor-core Hamming distances.
+cudaError_t launch_class_sign(const uint32_t *planes, int C, int W, int Dk, int Cp, int ldcs, uint8_t *out,
+                              cudaStream_t st);
+
 // FP32 projections (N x Dk, from the CUDA-core encoder) -> BF16 rows of ldS
 // elements (zero past Dk) and the squared norms of the BF16 rows.
 cudaError_t launch_proj_bf16(const float *s, int64_t N, int Dk, uint16_t *q, int ldS, float *qn,
@@ -103,6 +108,8 @@ struct TcArgs {
     uint16_t *sproj;            // encode-only: BF16 projections (N x ldS) or NULL
     int ldS;
     float *qn;                  // with sproj: squared norms of the BF16 rows
+    const uint8_t *cls_sign;    // classify, binary classes: E4M3 +-1 class bytes (Cp x ldcs) or NULL
+    int ldcs;
     int W;
     // fused similarity (classify); planes == NULL for encode-only
     const uint32_t *planes;

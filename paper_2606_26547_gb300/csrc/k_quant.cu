@@ -385,6 +385,28 @@ cudaError_t launch_class_prepare(const int32_t *acc, int C, int D, const Perf &p
 }
 
 namespace {
+__global__ void class_sign_kernel(const uint32_t *__restrict__ planes, int C, int W, int Dk, int Cp, int ldcs,
+                                  uint8_t *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)Cp * ldcs) return;
+    const int c = (int)(i / ldcs), k = (int)(i % ldcs);
+    uint8_t v = 0;
+    if (c < C && k < Dk) v = ((planes[(int64_t)c * W + (k >> 5)] >> (k & 31)) & 1u) ? 0xB8 : 0x38;  // -1.0 : +1.0
+    out[i] = v;
+}
+}  // namespace
+
+cudaError_t launch_class_sign(const uint32_t *planes, int C, int W, int Dk, int Cp, int ldcs, uint8_t *out,
+                              cudaStream_t st)
+{
+    const int64_t n = (int64_t)Cp * ldcs;
+    if (n <= 0) return cudaSuccess;
+    class_sign_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(planes, C, W, Dk, Cp, ldcs, out);
+    return cudaGetLastError();
+}
+
+namespace {
 // One warp per row: BF16 of each projection (zero past Dk) and the FP32
 // sum of the squared BF16 values, in column order per lane, lanes combined
 // by a butterfly.

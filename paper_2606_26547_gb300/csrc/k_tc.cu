@@ -4,7 +4,7 @@
 
 #include <mutex>
 
-#include "tc_kernel.cuh"
+#include "tc_hamming.cuh"
 
 namespace hdc {
 namespace {
@@ -60,6 +60,21 @@ bool make_cls_map(CUtensorMap *m, const uint32_t *planes, int W, int C)
     return r == CUDA_SUCCESS;
 }
 
+// Map over the E4M3 +-1 class bytes (Cp rows x ldcs bytes): box = one
+// 128-byte K atom x Cp rows, 128-byte swizzle (the MMA operand layout).
+bool make_sign_map(CUtensorMap *m, const uint8_t *signs, int ldcs, int Cp)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)ldcs, (cuuint64_t)Cp};
+    cuuint64_t strides[1] = {(cuuint64_t)ldcs};
+    cuuint32_t box[2] = {128, (cuuint32_t)Cp};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(signs), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int sm_count()
 {
     int dev = 0, n = 0;
@@ -113,6 +128,26 @@ cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st)
     if (sms <= 0) return cudaErrorNoDevice;
     const unsigned grid = (unsigned)(m_tiles < sms ? m_tiles : sms);
     const bool classify = a.planes != nullptr;
+    if (classify && a.cls_sign && a.nb == 1 && a.C > 16 && a.C <= tc::H_CMAX) {
+        // binary classes, 17..112 of them: Hamming distances on the tensor
+        // cores (a second MMA of the sign tile against the class signs)
+        CUtensorMap mb2, ms;
+        const int Cp = (a.C + 15) / 16 * 16;
+        if (!make_map(&mb2, a.Bq, a.enc, a.F, a.ldb, a.Dk, tc::HBN) || !make_sign_map(&ms, a.cls_sign, a.ldcs, Cp))
+            return cudaErrorInvalidValue;
+        tc::HParams h;
+        h.N = a.N;
+        h.Dk = a.Dk;
+        h.num_kb = p.num_kb;
+        h.nt = (a.Dk + tc::HBN - 1) / tc::HBN;
+        h.C = a.C;
+        h.Cp = Cp;
+        h.labels = a.labels;
+        h.dists = a.dists;
+        if (a.ldcs < h.nt * tc::HBN + 64) return cudaErrorInvalidValue;
+        if (a.enc == HDC_ENC_BF16) return tc::launch_hamming_bf16(ma, mb2, ms, h, grid, st);
+        return tc::launch_hamming_fp8(ma, mb2, ms, h, grid, st);
+    }
     CUtensorMap mc = mb;  // unused by encode-only launches
     if (classify && !make_cls_map(&mc, a.planes, a.W, a.C)) return cudaErrorInvalidValue;
     if (a.enc == HDC_ENC_BF16) return tc::launch_bf16(ma, mb, mc, p, grid, classify, st);

@@ -1,5 +1,5 @@
 // Tensor-core encoder instances for BF16 operands (tcgen05.mma kind::f16).
-#include "tc_kernel.cuh"
+#include "tc_hamming.cuh"
 
 namespace hdc {
 namespace tc {
@@ -12,6 +12,12 @@ cudaError_t launch_bf16(const CUtensorMap &ma, const CUtensorMap &mb, const CUte
 }
 
 cudaError_t status_bf16(cudaStream_t st, int *status) { return read_status(st, status); }
+
+cudaError_t launch_hamming_bf16(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &ms,
+                                const HParams &p, unsigned grid, cudaStream_t st)
+{
+    return launch_hamming_enc<HDC_ENC_BF16>(ma, mb, ms, p, grid, st);
+}
 
 }  // namespace tc
 }  // namespace hdc

@@ -1,5 +1,5 @@
 // Tensor-core encoder instances for FP8 E4M3 operands (tcgen05.mma kind::f8f6f4).
-#include "tc_kernel.cuh"
+#include "tc_hamming.cuh"
 
 namespace hdc {
 namespace tc {
@@ -12,6 +12,12 @@ cudaError_t launch_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const CUten
 }
 
 cudaError_t status_fp8(cudaStream_t st, int *status) { return read_status(st, status); }
+
+cudaError_t launch_hamming_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &ms,
+                               const HParams &p, unsigned grid, cudaStream_t st)
+{
+    return launch_hamming_enc<HDC_ENC_FP8_E4M3>(ma, mb, ms, p, grid, st);
+}
 
 }  // namespace tc
 }  // namespace hdc

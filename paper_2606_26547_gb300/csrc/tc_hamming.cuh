@@ -1,0 +1,354 @@
+// Fused classify with the Hamming distances on the tensor cores (binary
+// classes, 17 <= C <= 112).
+//
+// For +-1 vectors over the kept dims, Hamming(q, c) = (Dk - q.c) / 2, and
+// q.c is a sum of Dk products +-1 (0 for padding): an exact integer in FP32
+// for Dk < 2^24.  So after the encode GEMM of a 192-dim tile
+//   S = Xq . Bq^T          (MMA1: M 128, N 192, K = F, BF16 or E4M3)
+// the epilogue writes sign(S) as E4M3 +-1 bytes into a 128 x 192 shared
+// operand, and a second GEMM accumulates
+//   D2 += sign(S) . Csign^T  (MMA2: M 128, N = Cp, K = 192, E4M3)
+// over all tiles of the query block, Csign being the class hypervectors as
+// E4M3 +-1 bytes (zero past Dk and for the pad classes up to Cp = C rounded
+// to 16).  The final epilogue reads D2 and takes the arg-min of
+// (Dk - dot) / 2 (lowest class on ties).
+//
+// Tensor memory (512 columns): two 192-column encode accumulators (the
+// encode stays double buffered) and the Cp <= 128 columns of D2.
+//
+// Roles (15 warps): warps 0-11 epilogue (three warpgroups, 64 columns of a
+// tile each), warp 12 TMA producer of the A / B stages (4 x 40 KB), warp 13
+// MMA issuer (MMA1 of tile t, then MMA2 of tile t - 1), warp 14 TMA producer
+// of the class-sign tiles.  Every wait is bounded as in the encoder.
+#pragma once
+#include "tc_kernel.cuh"
+
+namespace hdc {
+namespace tc {
+
+constexpr int HBN = 192;                      // dims per tile
+constexpr int H_STAGES = 4;
+constexpr int HA_BYTES = BM * BKB;            // 16 KB
+constexpr int HB_BYTES = HBN * BKB;           // 24 KB
+constexpr int H_STAGE_BYTES = HA_BYTES + HB_BYTES;
+constexpr int HEWG = 3;                       // epilogue warpgroups
+constexpr int H_THREADS = (4 * HEWG + 3) * 32;
+constexpr int A2_ATOM = BM * 128;             // one 128-byte K atom of the sign tile
+constexpr int A2_BYTES = 2 * A2_ATOM;         // K = 192 bytes in two atoms
+constexpr int H_CMAX = 112;
+// full[S], empty[S], sfull[2], sempty[2], a2full, a2empty, b2full, b2empty,
+// d2full, d2empty, done, merge_full, merge_empty
+constexpr int H_NUM_BARS = 2 * H_STAGES + 4 + 6 + 3;
+
+__host__ __device__ constexpr size_t h_smem_bytes(int Cp)
+{
+    return 1024 + (size_t)H_STAGES * H_STAGE_BYTES + A2_BYTES + (size_t)2 * Cp * 128 + H_NUM_BARS * 8 + 16 +
+           (size_t)2 * BM * 4 * (HEWG - 1);
+}
+static_assert(h_smem_bytes(H_CMAX) <= 232448, "shared memory of the tensor-core Hamming kernel");
+
+struct HParams {
+    int64_t N;
+    int Dk, num_kb, nt;     // nt: 192-dim tiles
+    int C, Cp;
+    int32_t *labels, *dists;
+};
+
+template <int ENC>
+__device__ __forceinline__ uint32_t idesc_n(int n)
+{
+    const uint32_t fmt = ENC == HDC_ENC_BF16 ? 1u : 0u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+template <int ENC>
+__global__ void __launch_bounds__(H_THREADS, 1)
+    tc_hamming_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const __grid_constant__ CUtensorMap tmS, const HParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + H_STAGES * HA_BYTES;
+    uint8_t *sA2 = smem + H_STAGES * H_STAGE_BYTES;
+    uint8_t *sB2 = sA2 + A2_BYTES;                                  // 2 atoms x Cp rows x 128 B
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB2 + 2 * p.Cp * 128);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + H_NUM_BARS);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    int32_t *s_val = reinterpret_cast<int32_t *>(tmem_slot + 4);    // warpgroups 1.. : per-row minimum
+    int32_t *s_idx = s_val + (HEWG - 1) * BM;                        // and its class
+    auto full = [&](int s) { return su32(bars + s); };
+    auto empty = [&](int s) { return su32(bars + H_STAGES + s); };
+    auto sfull = [&](int a) { return su32(bars + 2 * H_STAGES + a); };
+    auto sempty = [&](int a) { return su32(bars + 2 * H_STAGES + 2 + a); };
+    const uint32_t a2full = su32(bars + 2 * H_STAGES + 4), a2empty = su32(bars + 2 * H_STAGES + 5);
+    const uint32_t b2full = su32(bars + 2 * H_STAGES + 6), b2empty = su32(bars + 2 * H_STAGES + 7);
+    const uint32_t d2full = su32(bars + 2 * H_STAGES + 8), d2empty = su32(bars + 2 * H_STAGES + 9);
+    const uint32_t done_bar = su32(bars + 2 * H_STAGES + 10);
+    const uint32_t merge_full = su32(bars + 2 * H_STAGES + 11), merge_empty = su32(bars + 2 * H_STAGES + 12);
+    constexpr int PRODUCER = 4 * HEWG, ISSUER = 4 * HEWG + 1, CPRODUCER = 4 * HEWG + 2;
+    constexpr int KELEMS = ENC == HDC_ENC_BF16 ? BKB / 2 : BKB;
+    constexpr uint32_t D2_COL = 2 * HBN;     // D2 after the two encode accumulators
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t num_m_tiles = (p.N + BM - 1) / BM;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < H_STAGES; s++) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        for (int a = 0; a < 2; a++) {
+            mbar_init(sfull(a), 1);
+            mbar_init(sempty(a), BM * HEWG);
+        }
+        mbar_init(a2full, BM * HEWG);
+        mbar_init(a2empty, 1);
+        mbar_init(b2full, 1);
+        mbar_init(b2empty, 1);
+        mbar_init(d2full, 1);
+        mbar_init(d2empty, BM * HEWG);
+        mbar_init(done_bar, 1);
+        mbar_init(merge_full, BM * (HEWG - 1));
+        mbar_init(merge_empty, BM);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == PRODUCER) {
+        if (lane == 0) {  // ------------------------------ A / B stage producer
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+            int stage = 0;
+            uint32_t phase = 0;
+            bool issued[H_STAGES];
+            uint32_t ipar[H_STAGES];
+            for (int s = 0; s < H_STAGES; s++) { issued[s] = false; ipar[s] = 0; }
+            bool ab = false;
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
+                for (int t = 0; t < p.nt && !ab; t++)
+                    for (int kb = 0; kb < p.num_kb; kb++) {
+                        if (!mbar_wait(empty(stage), phase ^ 1, abort_flag)) { ab = true; break; }
+                        mbar_expect_tx(full(stage), H_STAGE_BYTES);
+                        tma_load_2d(su32(sA + stage * HA_BYTES), &tmA, kb * KELEMS, (int)(mt * BM), full(stage));
+                        tma_load_2d(su32(sB + stage * HB_BYTES), &tmB, kb * KELEMS, t * HBN, full(stage));
+                        issued[stage] = true;
+                        ipar[stage] = phase;
+                        if (++stage == H_STAGES) { stage = 0; phase ^= 1; }
+                    }
+            if (ab) {
+                for (int s = 0; s < H_STAGES; s++)
+                    if (issued[s]) {
+                        const unsigned long long t0 = gtimer();
+                        while (!mbar_try(full(s), ipar[s]) && gtimer() - t0 < 100000000ull) {}
+                    }
+            }
+        }
+    } else if (warp == CPRODUCER) {
+        if (lane == 0) {  // ------------------------------ class-sign producer
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmS)) : "memory");
+            uint32_t ph = 0, last = 0;
+            bool any = false, ab = false;
+            const uint32_t bytes = 2u * (uint32_t)p.Cp * 128u;
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
+                for (int t = 0; t < p.nt; t++) {
+                    if (!mbar_wait(b2empty, ph ^ 1, abort_flag)) { ab = true; break; }
+                    mbar_expect_tx(b2full, bytes);
+                    tma_load_2d(su32(sB2), &tmS, t * HBN, 0, b2full);
+                    tma_load_2d(su32(sB2 + p.Cp * 128), &tmS, t * HBN + 128, 0, b2full);
+                    any = true;
+                    last = ph;
+                    ph ^= 1;
+                }
+            if (ab && any) {
+                const unsigned long long t0 = gtimer();
+                while (!mbar_try(b2full, last) && gtimer() - t0 < 100000000ull) {}
+            }
+        }
+    } else if (warp == ISSUER) {
+        if (lane == 0) {  // ------------------------------ MMA issuer
+            const uint32_t id1 = idesc_n<ENC>(HBN);
+            const uint32_t id2 = idesc_n<HDC_ENC_FP8_E4M3>(p.Cp);
+            int stage = 0, acc = 0;
+            uint32_t phase = 0, aphase = 0, a2ph = 0, b2ph = 0, d2ph = 0;
+            bool ab = false;
+            // MMA2 of tile t: D2 (+)= signs . class signs over K = 192
+            auto mma2 = [&](bool first) -> bool {
+                if (first && !mbar_wait(d2empty, d2ph ^ 1, abort_flag)) return false;
+                if (!mbar_wait(a2full, a2ph, abort_flag)) return false;
+                if (!mbar_wait(b2full, b2ph, abort_flag)) return false;
+                tc_fence_after();
+                const uint32_t a0 = su32(sA2), b0 = su32(sB2);
+#pragma unroll
+                for (int k = 0; k < 6; k++) {   // atom 0: K bytes 0..127, atom 1: 128..191
+                    const uint32_t off_a = (k < 4 ? 0u : (uint32_t)A2_ATOM) + 32u * (k & 3);
+                    const uint32_t off_b = (k < 4 ? 0u : (uint32_t)(p.Cp * 128)) + 32u * (k & 3);
+                    mma<HDC_ENC_FP8_E4M3>(tmem + D2_COL, sdesc(a0 + off_a), sdesc(b0 + off_b), id2,
+                                          (first && k == 0) ? 0u : 1u);
+                }
+                mma_commit(a2empty);
+                mma_commit(b2empty);
+                a2ph ^= 1;
+                b2ph ^= 1;
+                return true;
+            };
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
+                for (int t = 0; t < p.nt && !ab; t++) {
+                    if (!mbar_wait(sempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
+                    tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)(acc * HBN);
+                    for (int kb = 0; kb < p.num_kb; kb++) {
+                        if (!mbar_wait(full(stage), phase, abort_flag)) { ab = true; break; }
+                        tc_fence_after();
+                        const uint32_t a0 = su32(sA + stage * HA_BYTES), b0 = su32(sB + stage * HB_BYTES);
+#pragma unroll
+                        for (int k = 0; k < BKB / 32; k++)
+                            mma<ENC>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), id1, (kb | k) != 0);
+                        mma_commit(empty(stage));
+                        if (++stage == H_STAGES) { stage = 0; phase ^= 1; }
+                    }
+                    if (ab) break;
+                    mma_commit(sfull(acc));
+                    if (++acc == 2) { acc = 0; aphase ^= 1; }
+                    if (t > 0 && !mma2(t == 1)) { ab = true; break; }
+                }
+                if (ab) break;
+                if (!mma2(p.nt == 1)) { ab = true; break; }
+                mma_commit(d2full);
+                d2ph ^= 1;
+            }
+            mma_commit(done_bar);
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try(done_bar, 0) && gtimer() - t0 < 100000000ull) {}
+        }
+    } else {  // ------------------------------------------ epilogue warps 0 .. 11
+        const int q = warp & 3, g = warp >> 2;
+        const int r = q * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        // this warpgroup's 64 columns of a tile: atom g / 2, 16-byte chunks from (g & 1) * 4
+        uint8_t *a2row = sA2 + (g >> 1) * A2_ATOM + (r >> 3) * 1024 + (r & 7) * 128;
+        const int ch0 = (g & 1) * 4;
+        int acc = 0;
+        uint32_t aphase = 0, a2ph = 0, d2ph = 0;
+        bool ab = false;
+        int64_t it = 0;
+        for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++) {
+            const int64_t row = mt * BM + r;
+            const bool valid = row < p.N;
+            for (int t = 0; t < p.nt; t++) {
+                const bool ok = mbar_wait(sfull(acc), aphase, abort_flag);
+                if (!__all_sync(0xffffffffu, ok)) { ab = true; break; }
+                tc_fence_after();
+                uint32_t v0[32], v1[32];
+                tmem_ld32(tmem + lane_base + (uint32_t)(acc * HBN + g * 64), v0);
+                tmem_ld32(tmem + lane_base + (uint32_t)(acc * HBN + g * 64 + 32), v1);
+                tc_fence_before();
+                mbar_arrive(sempty(acc));
+                if (++acc == 2) { acc = 0; aphase ^= 1; }
+                // E4M3 +1.0 = 0x38, -1.0 = 0xB8 (sign(0) = +1); byte i of a word is column 4w + i
+                uint32_t w[16];
+#pragma unroll
+                for (int i = 0; i < 8; i++) {
+                    uint32_t x = 0;
+#pragma unroll
+                    for (int b = 0; b < 4; b++)
+                        x |= (__uint_as_float(v0[4 * i + b]) < 0.f ? 0xB8u : 0x38u) << (8 * b);
+                    w[i] = x;
+                    uint32_t y = 0;
+#pragma unroll
+                    for (int b = 0; b < 4; b++)
+                        y |= (__uint_as_float(v1[4 * i + b]) < 0.f ? 0xB8u : 0x38u) << (8 * b);
+                    w[8 + i] = y;
+                }
+                const bool oka = mbar_wait(a2empty, a2ph ^ 1, abort_flag);   // MMA2 of the previous tile done
+                if (!__all_sync(0xffffffffu, oka)) { ab = true; break; }
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const int ch = (ch0 + i) ^ (r & 7);   // 128-byte swizzle
+                    *reinterpret_cast<uint4 *>(a2row + ch * 16) = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2],
+                                                                            w[4 * i + 3]);
+                }
+                fence_async_smem();
+                mbar_arrive(a2full);
+                a2ph ^= 1;
+            }
+            if (ab) break;
+            // distances of this warpgroup's 32-class chunks (chunk j to warpgroup j % 3)
+            const bool okd = mbar_wait(d2full, d2ph, abort_flag);
+            if (!__all_sync(0xffffffffu, okd)) { ab = true; break; }
+            tc_fence_after();
+            int best = 0x7fffffff, bv = 0x7fffffff;
+            for (int j = g; j * 32 < p.Cp; j += HEWG) {
+                uint32_t v[32];
+                tmem_ld32(tmem + lane_base + D2_COL + (uint32_t)(j * 32), v);
+#pragma unroll
+                for (int i = 0; i < 32; i++) {
+                    const int c = j * 32 + i;
+                    if (c < p.C) {
+                        const int dist = (p.Dk - (int)__uint_as_float(v[i])) / 2;
+                        if (p.dists && valid) p.dists[row * p.C + c] = dist;
+                        if (dist < bv) { bv = dist; best = c; }   // ascending c: lowest on ties
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(d2empty);
+            d2ph ^= 1;
+            const uint32_t par = (uint32_t)(it & 1);
+            if (g > 0) {
+                if (!mbar_wait(merge_empty, par ^ 1, abort_flag)) { ab = true; break; }
+                s_val[(g - 1) * BM + r] = bv;
+                s_idx[(g - 1) * BM + r] = best;
+                mbar_arrive(merge_full);
+            } else {
+                if (!mbar_wait(merge_full, par, abort_flag)) { ab = true; break; }
+#pragma unroll
+                for (int h = 0; h < HEWG - 1; h++) {   // (distance, class) order: lowest class on ties
+                    const int v1 = s_val[h * BM + r], i1 = s_idx[h * BM + r];
+                    if (v1 < bv || (v1 == bv && i1 < best)) { bv = v1; best = i1; }
+                }
+                mbar_arrive(merge_empty);
+                if (valid) p.labels[row] = best;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+template <int ENC>
+static cudaError_t launch_hamming_enc(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &ms,
+                                      const HParams &p, unsigned grid, cudaStream_t st)
+{
+    auto k = tc_hamming_kernel<ENC>;
+    const size_t smem = h_smem_bytes(p.Cp);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, H_THREADS, smem, st>>>(ma, mb, ms, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hamming_bf16(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &ms,
+                                const HParams &p, unsigned grid, cudaStream_t st);
+cudaError_t launch_hamming_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &ms,
+                               const HParams &p, unsigned grid, cudaStream_t st);
+
+}  // namespace tc
+}  // namespace hdc

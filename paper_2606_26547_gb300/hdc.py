@@ -42,7 +42,8 @@ class ModelC(ctypes.Structure):
                 ("Dk", ctypes.c_int32), ("C", ctypes.c_int32), ("enc", ctypes.c_int32), ("ldb", ctypes.c_int32),
                 ("class_bits", ctypes.c_int32), ("W", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("Bq", ctypes.c_void_p), ("b_scale", ctypes.c_void_p), ("cls", ctypes.c_void_p),
-                ("cls_sum", ctypes.c_void_p), ("cls_norm", ctypes.c_void_p)]
+                ("cls_sum", ctypes.c_void_p), ("cls_norm", ctypes.c_void_p), ("cls_sign", ctypes.c_void_p),
+                ("ldcs", ctypes.c_int32)]
 
 
 _P, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
