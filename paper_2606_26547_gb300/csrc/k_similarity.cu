@@ -127,52 +127,58 @@ __global__ void __launch_bounds__(TPB) hamming_reg_kernel(const uint32_t *__rest
     __shared__ uint32_t mk[RWCH];
     const int tid = threadIdx.x;
     const int64_t row0 = (int64_t)blockIdx.x * TPB;
-    int dist[CMAX];
+    const int64_t row = row0 + tid;
+    int best = 0, bv = 0x7fffffff;
+    // classes in chunks of CMAX (one chunk when C <= CMAX); chunks ascend, so
+    // a strict comparison keeps the lowest class on ties
+    for (int cb = 0; cb < C; cb += CMAX) {
+        const int cn = min(CMAX, C - cb);
+        int dist[CMAX];
 #pragma unroll
-    for (int c = 0; c < CMAX; c++) dist[c] = 0;
-    for (int w0 = 0; w0 < W; w0 += RWCH) {
-        const int nw = min(RWCH, W - w0);
-        __syncthreads();
-        for (int i = tid; i < TPB * RWCH; i += TPB) {  // consecutive threads: consecutive words of a row
-            const int r = i / RWCH, j = i % RWCH;
-            sq[j][r] = (row0 + r < N && j < nw) ? __ldg(Q + (row0 + r) * W + w0 + j) : 0u;
-        }
-        for (int i = tid; i < CMAX * RWCH; i += TPB) {
-            const int c = i / RWCH, j = i % RWCH;
-            sc[c][j] = (c < C && j < nw) ? __ldg(cls + (int64_t)c * W + w0 + j) : 0u;
-        }
-        if (tid < RWCH) {
-            uint32_t m = tid < nw ? 0xffffffffu : 0u;
-            if (use_mask && tid < nw) {  // kept dims s0, s0+stride, ... < e0 inside this word
-                m = 0;
-                const int64_t base = (int64_t)(w0 + tid) * 32;
-                const int64_t lo = max(s0, base), hi = min(e0, base + 32);
-                if (lo < hi) {
-                    const int64_t r = (lo - s0) % stride;
-                    for (int64_t d = r ? lo + (stride - r) : lo; d < hi; d += stride) m |= 1u << (d - base);
-                }
+        for (int c = 0; c < CMAX; c++) dist[c] = 0;
+        for (int w0 = 0; w0 < W; w0 += RWCH) {
+            const int nw = min(RWCH, W - w0);
+            __syncthreads();
+            for (int i = tid; i < TPB * RWCH; i += TPB) {  // consecutive threads: consecutive words of a row
+                const int r = i / RWCH, j = i % RWCH;
+                sq[j][r] = (row0 + r < N && j < nw) ? __ldg(Q + (row0 + r) * W + w0 + j) : 0u;
             }
-            mk[tid] = m;
+            for (int i = tid; i < CMAX * RWCH; i += TPB) {
+                const int c = i / RWCH, j = i % RWCH;
+                sc[c][j] = (c < cn && j < nw) ? __ldg(cls + (int64_t)(cb + c) * W + w0 + j) : 0u;
+            }
+            if (tid < RWCH) {
+                uint32_t m = tid < nw ? 0xffffffffu : 0u;
+                if (use_mask && tid < nw) {  // kept dims s0, s0+stride, ... < e0 inside this word
+                    m = 0;
+                    const int64_t base = (int64_t)(w0 + tid) * 32;
+                    const int64_t lo = max(s0, base), hi = min(e0, base + 32);
+                    if (lo < hi) {
+                        const int64_t r = (lo - s0) % stride;
+                        for (int64_t d = r ? lo + (stride - r) : lo; d < hi; d += stride) m |= 1u << (d - base);
+                    }
+                }
+                mk[tid] = m;
+            }
+            __syncthreads();
+            for (int j = 0; j < nw; j++) {
+                const uint32_t m = mk[j];
+                const uint32_t q = sq[j][tid] & m;
+#pragma unroll
+                for (int c = 0; c < CMAX; c++)
+                    if (c < cn) dist[c] += __popc(q ^ (sc[c][j] & m));
+            }
         }
-        __syncthreads();
-        for (int j = 0; j < nw; j++) {
-            const uint32_t m = mk[j];
-            const uint32_t q = sq[j][tid] & m;
+        if (row < N) {
 #pragma unroll
             for (int c = 0; c < CMAX; c++)
-                if (c < C) dist[c] += __popc(q ^ (sc[c][j] & m));
+                if (c < cn) {
+                    if (dists) dists[row * C + cb + c] = dist[c];
+                    if (dist[c] < bv) { bv = dist[c]; best = cb + c; }
+                }
         }
     }
-    const int64_t row = row0 + tid;
-    if (row >= N) return;
-    int best = 0, bv = dist[0];
-#pragma unroll
-    for (int c = 0; c < CMAX; c++)
-        if (c < C) {
-            if (dists) dists[row * C + c] = dist[c];
-            if (dist[c] < bv) { bv = dist[c]; best = c; }
-        }
-    labels[row] = best;
+    if (row < N) labels[row] = best;
 }
 
 template <int CMAX>
@@ -218,7 +224,7 @@ cudaError_t launch_similarity(const uint32_t *Q, int64_t N, const uint32_t *plan
     if (N <= 0) return cudaSuccess;
     if (nb == 1 && C <= 16) return launch_reg<16>(Q, N, planes, C, W, D, p, labels, dists, st);
     if (nb == 1 && C <= 32) return launch_reg<32>(Q, N, planes, C, W, D, p, labels, dists, st);
-    if (nb == 1 && C <= 64) return launch_reg<64>(Q, N, planes, C, W, D, p, labels, dists, st);
+    if (nb == 1) return launch_reg<64>(Q, N, planes, C, W, D, p, labels, dists, st);   // chunks of 64 classes
     switch (nb) {
     case 1: return launch_nb<1>(Q, N, planes, C, W, D, p, csum, cnorm, labels, dists, scores, st);
     case 4: return launch_nb<4>(Q, N, planes, C, W, D, nullptr, csum, cnorm, labels, dists, scores, st);
