@@ -218,6 +218,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
                  : "memory");
 }
 
+// One 32-byte store (a whole sector); p must be 32-byte aligned.
+__device__ __forceinline__ void st_global_v8(void *p, const uint32_t *w)
+{
+    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]),
+                 "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+
 // sign(0) = +1: -0.0 and +0.0 both give bit 0.
 __device__ __forceinline__ uint32_t pack_signs(const uint32_t (&r)[32])
 {
@@ -418,7 +426,7 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
                     const int col0 = nt * BN + jw * 32;
                     if (!CLASSIFY && p.sproj && valid && col0 < p.ldS) {
                         // 32 BF16 projections (zeros past Dk: the base rows
-                        // there are TMA zero fill), 4 x 16-byte stores
+                        // there are TMA zero fill), two whole 32-byte sectors
                         float sbv[32];
                         if (p.sb && col0 + 32 <= p.Dk) {
                             const float4 *s4 = reinterpret_cast<const float4 *>(p.sb + col0);
@@ -442,9 +450,9 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
                             qsum = fmaf(g1, g1, qsum);
                             pk[i / 2] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
                         }
-                        uint4 *dst = reinterpret_cast<uint4 *>(p.sproj + row * (int64_t)p.ldS + col0);
-#pragma unroll
-                        for (int i = 0; i < 4; i++) dst[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+                        uint16_t *dst = p.sproj + row * (int64_t)p.ldS + col0;   // 64-byte aligned
+                        st_global_v8(dst, pk);
+                        st_global_v8(dst + 16, pk + 8);
                     }
                     words[j] = pack_signs(v);
                 }
