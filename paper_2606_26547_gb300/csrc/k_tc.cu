@@ -150,16 +150,8 @@ cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st)
     }
     CUtensorMap mc = mb;  // unused by encode-only launches
     if (classify && !make_cls_map(&mc, a.planes, a.W, a.C)) return cudaErrorInvalidValue;
-    // up to 16 classes: a two-CTA cluster launch sharing the base stages,
-    // each CTA loading 128 of a stage's 256 base rows
-    CUtensorMap mbh;
-    const CUtensorMap *half = nullptr;
-    if (classify && a.C <= 16) {
-        if (!make_map(&mbh, a.Bq, a.enc, a.F, a.ldb, a.Dk, tc::BN / 2)) return cudaErrorInvalidValue;
-        half = &mbh;
-    }
-    if (a.enc == HDC_ENC_BF16) return tc::launch_bf16(ma, mb, mc, p, grid, classify, st, half);
-    return tc::launch_fp8(ma, mb, mc, p, grid, classify, st, half);
+    if (a.enc == HDC_ENC_BF16) return tc::launch_bf16(ma, mb, mc, p, grid, classify, st);
+    return tc::launch_fp8(ma, mb, mc, p, grid, classify, st);
 }
 
 cudaError_t tc_read_status(cudaStream_t st, int *status)

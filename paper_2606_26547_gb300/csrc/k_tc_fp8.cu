@@ -5,9 +5,10 @@ namespace hdc {
 namespace tc {
 
 cudaError_t launch_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const Params &p,
-                       unsigned grid, bool classify, cudaStream_t st, const CUtensorMap *mb_half)
+                        unsigned grid, bool classify,
+                       cudaStream_t st)
 {
-    return launch_enc<HDC_ENC_FP8_E4M3>(ma, mb, mc, p, grid, classify, st, mb_half);
+    return launch_enc<HDC_ENC_FP8_E4M3>(ma, mb, mc, p, grid, classify, st);
 }
 
 cudaError_t status_fp8(cudaStream_t st, int *status) { return read_status(st, status); }

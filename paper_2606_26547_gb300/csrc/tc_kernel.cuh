@@ -151,33 +151,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-// Cluster of two CTAs (base-tile multicast): this CTA's rank, a full
-// cluster barrier (every thread of both CTAs), a TMA load whose box lands at
-// the same shared offset in every CTA of `mask` and completes bytes on the
-// mbarrier at the same offset in each, and an MMA commit that arrives on the
-// mbarrier at the same offset in every CTA of `mask`.
-__device__ __forceinline__ uint32_t cluster_ctarank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ void cluster_sync_all()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar,
-                                               uint16_t mask)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
-        : "memory");
-}
-
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -220,13 +193,6 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
 __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-                 ::"r"(bar), "h"(mask)
-                 : "memory");
 }
 
 // 32 consecutive FP32 columns of this thread's TMEM lane; the wait names the
@@ -278,11 +244,7 @@ __device__ __forceinline__ uint32_t pack_signs(const uint32_t (&r)[32])
 // and warpgroups 1..EWG-1 hand their per-row minimum to warpgroup 0 through
 // shared memory (an mbarrier pair with bounded waits), which keeps the lower class
 // index on ties.
-// MC: launched in clusters of two CTAs that walk the same dim tiles for two
-// query tiles (2u and 2u+1); each loads half of every base stage (128 rows)
-// and multicasts it to both, so a CTA pulls 32 KB instead of 48 KB per stage
-// from L2.  A stage's empty barrier then counts the MMA commits of both CTAs.
-template <int ENC, int CMAX, bool CLASSIFY, int EWG, bool MC = false>
+template <int ENC, int CMAX, bool CLASSIFY, int EWG>
 __global__ void __launch_bounds__(num_threads(EWG), 1)
     tc_encode_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmC, const Params p)
@@ -316,18 +278,11 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
     const int64_t num_m_tiles = (p.N + BM - 1) / BM;
     const int num_n_tiles = (p.Dk + BN - 1) / BN;
     constexpr int KELEMS = ENC == HDC_ENC_BF16 ? BKB / 2 : BKB;
-    // work units: query tiles, or (MC) pairs of query tiles, one per CTA of
-    // the cluster; both CTAs of a pair take the same number of units (a tile
-    // past N is zero fill and writes nothing)
-    const int rank = MC ? (int)cluster_ctarank() : 0;
-    const int64_t num_units = MC ? (num_m_tiles + 1) / 2 : num_m_tiles;
-    const int64_t unit0 = MC ? blockIdx.x / 2 : blockIdx.x;
-    const int64_t unit_step = MC ? gridDim.x / 2 : gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
             mbar_init(full(s), 1);
-            mbar_init(empty(s), MC ? 2 : 1);
+            mbar_init(empty(s), 1);
         }
         for (int a = 0; a < 2; a++) {
             mbar_init(tfull(a), 1);
@@ -352,7 +307,6 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (MC) cluster_sync_all();   // the peer's barriers exist before anything multicasts into them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -368,9 +322,8 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
             for (int s = 0; s < STAGES; s++) { issued[s] = false; ipar[s] = 0; }
             uint32_t c_issued = 0, c_par = 0;
             bool ab = false;
-            for (int64_t u = unit0; u < num_units && !ab; u += unit_step)
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
                 for (int nt = 0; nt < num_n_tiles && !ab; nt++) {
-                    const int64_t mt = MC ? 2 * u + rank : u;
                     if (CLASSIFY) {  // this dim tile's class words: C rows x 8 words (zeros past W)
                         if (!mbar_wait(cempty(cb), cph ^ 1, abort_flag)) { ab = true; break; }
                         mbar_expect_tx(cfull(cb), (uint32_t)p.C * 32u);
@@ -383,11 +336,7 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
                         if (!mbar_wait(empty(stage), phase ^ 1, abort_flag)) { ab = true; break; }
                         mbar_expect_tx(full(stage), STAGE_BYTES);
                         tma_load_2d(su32(sA + stage * A_BYTES), &tmA, kb * KELEMS, (int)(mt * BM), full(stage));
-                        if (MC)  // this CTA's 128 base rows, to both CTAs of the cluster
-                            tma_load_2d_mc(su32(sB + stage * B_BYTES + rank * (B_BYTES / 2)), &tmB, kb * KELEMS,
-                                           nt * BN + rank * (BN / 2), full(stage), (uint16_t)0x3);
-                        else
-                            tma_load_2d(su32(sB + stage * B_BYTES), &tmB, kb * KELEMS, nt * BN, full(stage));
+                        tma_load_2d(su32(sB + stage * B_BYTES), &tmB, kb * KELEMS, nt * BN, full(stage));
                         issued[stage] = true;
                         ipar[stage] = phase;
                         if (++stage == STAGES) { stage = 0; phase ^= 1; }
@@ -412,7 +361,7 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
             int stage = 0, acc = 0;
             uint32_t phase = 0, aphase = 0;
             bool ab = false;
-            for (int64_t u = unit0; u < num_units && !ab; u += unit_step)
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
                 for (int nt = 0; nt < num_n_tiles && !ab; nt++) {
                     if (!mbar_wait(tempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
                     tc_fence_after();
@@ -424,10 +373,7 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
 #pragma unroll
                         for (int k = 0; k < BKB / 32; k++)
                             mma<ENC>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), id, (kb | k) != 0);
-                        if (MC)  // the stage is free once both CTAs have read it
-                            mma_commit_mc(empty(stage), (uint16_t)0x3);
-                        else
-                            mma_commit(empty(stage));
+                        mma_commit(empty(stage));
                         if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
                     if (ab) break;
@@ -450,8 +396,7 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
         uint32_t aphase = 0, cph = 0, wph = 0;
         bool ab = false;
         int64_t it = 0;
-        for (int64_t u = unit0; u < num_units && !ab; u += unit_step, it++) {
-            const int64_t mt = MC ? 2 * u + rank : u;
+        for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++) {
             const int64_t row = mt * BM + r;
             const bool valid = row < p.N;
             float qsum = 0.f;   // squared norm of the BF16 projections of this row
@@ -609,8 +554,6 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
 
     tc_fence_before();
     __syncthreads();
-    // no CTA leaves while its peer may still multicast into it or arrive on its barriers
-    if (MC) cluster_sync_all();
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
@@ -630,46 +573,10 @@ static cudaError_t launch_one(const CUtensorMap &ma, const CUtensorMap &mb, cons
     return cudaGetLastError();
 }
 
-// Clusters of two CTAs sharing the base stages (mb: a map whose box is 128
-// base rows).  The grid is two CTAs per cluster, as many clusters as the
-// device holds at once (a persistent kernel must not wait for a second wave),
-// at most one per pair of query tiles.
-template <int ENC, int CMAX, bool CLASSIFY, int EWG>
-static cudaError_t launch_one_mc(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc,
-                                 const Params &p, cudaStream_t st)
-{
-    auto k = tc_encode_kernel<ENC, CMAX, CLASSIFY, EWG, true>;
-    constexpr size_t smem = smem_bytes(EWG);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(num_threads(EWG));
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cfg.gridDim = dim3(2);
-    int clusters = 0;
-    e = cudaOccupancyMaxActiveClusters(&clusters, k, &cfg);
-    if (e != cudaSuccess) return e;
-    if (clusters < 1) return cudaErrorNotSupported;
-    const int64_t pairs = ((p.N + BM - 1) / BM + 1) / 2;
-    cfg.gridDim = dim3((unsigned)(2 * (pairs < clusters ? pairs : clusters)));
-    return cudaLaunchKernelEx(&cfg, k, ma, mb, mc, p);
-}
-
 template <int ENC>
 static cudaError_t launch_enc(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const Params &p,
-                              unsigned grid, bool classify, cudaStream_t st, const CUtensorMap *mb_half = nullptr)
+                              unsigned grid, bool classify, cudaStream_t st)
 {
-    // up to 16 classes with at least two query tiles: clusters of two CTAs
-    // sharing the base stages
-    if (classify && p.C <= 16 && mb_half && p.N > BM) return launch_one_mc<ENC, 16, true, 1>(ma, *mb_half, mc, p, st);
     // encode-only: packed words with one warpgroup; BF16 projections (heavier
     // epilogue) with four, each converting and storing its 64 columns
     if (!classify)
@@ -700,12 +607,10 @@ static cudaError_t read_status(cudaStream_t st, int *status)
 }
 
 // Entry points of the two encoding translation units.
-// mb_half (optional): the base map with a 128-row box, for the two-CTA
-// cluster launch of the fused classify with up to 16 classes.
 cudaError_t launch_bf16(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const Params &p,
-                        unsigned grid, bool classify, cudaStream_t st, const CUtensorMap *mb_half);
+                        unsigned grid, bool classify, cudaStream_t st);
 cudaError_t launch_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const Params &p,
-                       unsigned grid, bool classify, cudaStream_t st, const CUtensorMap *mb_half);
+                       unsigned grid, bool classify, cudaStream_t st);
 cudaError_t status_bf16(cudaStream_t st, int *status);
 cudaError_t status_fp8(cudaStream_t st, int *status);
 
