@@ -138,6 +138,15 @@ def make(workload: str | Workload, n_train: int | None = None, n_query: int | No
     return dict(Bt=Bt, Xtr=Xtr, ytr=ytr, Xq=Xq, yq=yq)
 
 
+def more_queries(w: Workload, n: int, stream: int = 97):
+    """n further query rows of a workload's mixture (same centroids), drawn
+    with the seed stream base seed + `stream`; returns (X, y)."""
+    cs = w.seed + _S_CENTROIDS
+    if w.kind == "int":
+        return int_mixture(n, w.F, w.C, w.sigma, w.seed + stream, cs)
+    return gauss_mixture(n, w.F, w.C, w.sigma, w.seed + stream, cs)
+
+
 def levelid_hvs(F: int, D: int, L: int, seed: int):
     """Random draws of a Level-ID encoder: ID hypervector bits (F x D), the
     two level end points (D bits each), Bernoulli(0.5), and the level at
