@@ -82,6 +82,17 @@ typedef struct {
     int32_t enc;          /* hdc_enc                                        */
     uint32_t class_bits;  /* 1, 4 or 8                                      */
     uint32_t flags;       /* HDC_FLAG_* below                               */
+    /* Reduction perforation of the encoding itself (the matmul over the F
+     * features; Sec. 4.2, and what the paper's no-approx hint of Sec. 4.3
+     * forbids): kept features s0 + k*stride < e0 with s0 = floor(start*F),
+     * e0 = floor(end*F) as for the dims.  (0, 1, 1) keeps every feature.
+     * Signs, class decisions and cosines do not depend on the rescaling
+     * by F / F' that a perforated mat-vec estimate would take, so none is
+     * applied; hdc_encode's optional projections are sums over the kept
+     * features.                                                            */
+    float enc_perf_start;
+    float enc_perf_end;
+    uint32_t enc_perf_stride;
 } hdc_approx_config;
 
 /* Force the CUDA-core (FFMA) encoder even for BF16/FP8 inputs.             */
@@ -136,6 +147,9 @@ typedef struct {
                                /* Cp = C rounded to 16) for the tensor-core */
                                /* Hamming distances; NULL otherwise         */
     int32_t ldcs;              /* bytes per row of cls_sign                 */
+    int32_t Fk;                /* kept features F' (= F without encoding    */
+                               /* perforation); Bq rows hold these          */
+    int32_t fs0, fstride;      /* kept feature k is column fs0 + k*fstride  */
 } hdc_model;
 
 /* Bytes of device buffer hdc_model_prepare needs for this configuration.  */

@@ -244,6 +244,15 @@ def cosine_scores(q: np.ndarray, chat: np.ndarray) -> np.ndarray:
 
 # ---------------------------------------------------------------- pipelines
 
+def perforate_features(X: np.ndarray, Bt: np.ndarray, start: float = 0.0, end: float = 1.0,
+                       stride: int = 1):
+    """Reduction perforation of the encoding itself (Sec. 4.2 red_perf on the
+    matmul over features): keep features s0 + k*stride < e0 of both the
+    query rows and the base rows (the rule of kept_dims over F)."""
+    f = kept_dims(X.shape[1], start, end, stride)
+    return X[:, f], Bt[:, f]
+
+
 def encode_bits(X: np.ndarray, Bt: np.ndarray, enc: int, dims: np.ndarray,
                 integer: bool = False, threads: int = 1):
     """Quantise -> encode over the kept dims -> binarise.

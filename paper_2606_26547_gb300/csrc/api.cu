@@ -25,6 +25,19 @@ bool perf_of(int64_t D, const hdc_approx_config *cfg, Perf *p)
     return p->Dk > 0;
 }
 
+// Kept features of the encoding's perforation (the same rule over F).
+bool feat_perf_of(int64_t F, const hdc_approx_config *cfg, Perf *p)
+{
+    hdc_approx_config c;
+    hdc_default_config(&c);
+    if (cfg) {
+        c.perf_start = cfg->enc_perf_start;
+        c.perf_end = cfg->enc_perf_end;
+        c.perf_stride = cfg->enc_perf_stride;
+    }
+    return perf_of(F, &c, p);
+}
+
 namespace {
 
 inline bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
@@ -54,7 +67,9 @@ inline int cpad_for(int C) { return (C + 15) / 16 * 16; }
 bool model_ok(const hdc_model *m)
 {
     return m && m->struct_size >= sizeof(hdc_model) && m->F > 0 && m->D > 0 && m->Dk > 0 && m->Dk <= m->D &&
-           m->C >= 0 && m->Bq && m->ldb >= m->F && m->W == words_for(m->Dk) && bits_ok((uint32_t)m->class_bits) &&
+           m->Fk > 0 && m->Fk <= m->F && m->fs0 >= 0 && m->fstride >= 1 &&
+           m->fs0 + (int64_t)(m->Fk - 1) * m->fstride < m->F &&
+           m->C >= 0 && m->Bq && m->ldb >= m->Fk && m->W == words_for(m->Dk) && bits_ok((uint32_t)m->class_bits) &&
            m->enc >= HDC_ENC_FP32 && m->enc <= HDC_ENC_FP8_E4M3 && (m->enc != HDC_ENC_FP8_E4M3 || m->b_scale) &&
            flags_ok(m->flags, (uint32_t)m->class_bits, m->C);
 }
@@ -102,9 +117,10 @@ WsLayout ws_layout(int64_t N, const hdc_model *m)
     WsLayout L;
     size_t off = 0;
     const bool quant = m->enc != HDC_ENC_FP32;
-    const int ldx = ld_for(m->enc, m->F);
+    const bool gather = m->Fk != m->F;   // perforated encoding: the kept features are gathered first
+    const int ldx = ld_for(m->enc, m->Fk);
     const bool fq = float_query(m->flags);
-    L.xq = off; off = align_up(off + (quant ? (size_t)N * ldx * esize_for(m->enc) : 0), kAlign);
+    L.xq = off; off = align_up(off + (quant || gather ? (size_t)N * ldx * esize_for(m->enc) : 0), kAlign);
     L.sx = off; off = align_up(off + (m->enc == HDC_ENC_FP8_E4M3 ? (size_t)N * 4 : 0), kAlign);
     L.h = off;  off = align_up(off + (size_t)N * m->W * 4, kAlign);
     // float queries: BF16 projections and their norms; FP32 projections
@@ -122,15 +138,17 @@ hdc_status cu(cudaError_t e) { return e == cudaSuccess ? HDC_OK : HDC_ERR_CUDA; 
 hdc_status prepare_queries(const float *X, int64_t N, const hdc_model *m, char *ws, const WsLayout &L,
                            const void **Xop, int64_t *ldx, const float **sx, cudaStream_t st)
 {
-    if (m->enc == HDC_ENC_FP32) {
+    if (m->enc == HDC_ENC_FP32 && m->Fk == m->F) {
         *Xop = X;
         *ldx = m->F;
         *sx = nullptr;
         return HDC_OK;
     }
-    const int ld = ld_for(m->enc, m->F);
+    // quantise (and, for a perforated encoding, gather the kept features)
+    const int ld = ld_for(m->enc, m->Fk);
     float *scale = m->enc == HDC_ENC_FP8_E4M3 ? (float *)(ws + L.sx) : nullptr;
-    hdc_status s = cu(launch_quant_rows(X, m->F, 0, 1, N, m->F, m->enc, ws + L.xq, ld, scale, st));
+    hdc_status s = cu(launch_quant_rows(X, m->F, 0, 1, N, m->Fk, m->enc, ws + L.xq, ld, scale, st, m->fs0,
+                                        m->fstride));
     *Xop = ws + L.xq;
     *ldx = ld;
     *sx = scale;
@@ -179,6 +197,9 @@ void hdc_default_config(hdc_approx_config *cfg)
     cfg->enc = HDC_ENC_FP32;
     cfg->class_bits = 1;
     cfg->flags = 0;
+    cfg->enc_perf_start = 0.f;
+    cfg->enc_perf_end = 1.f;
+    cfg->enc_perf_stride = 1;
 }
 
 int64_t hdc_kept_dims(int32_t D, const hdc_approx_config *cfg)
@@ -195,7 +216,9 @@ hdc_status hdc_model_bytes(int32_t F, int32_t D, int32_t C, const hdc_approx_con
     Perf p;
     if (!bytes || F <= 0 || D <= 0 || C < 0 || !cfg_ok(cfg) || !perf_of(D, cfg, &p)) return HDC_ERR_INVALID_ARG;
     if (!bits_ok(cfg->class_bits) || !flags_ok(cfg->flags, cfg->class_bits, C)) return HDC_ERR_UNSUPPORTED;
-    *bytes = model_layout(F, (int)p.Dk, C, cfg->enc, (int)cfg->class_bits, cfg->flags).total;
+    Perf pf;
+    if (!feat_perf_of(F, cfg, &pf)) return HDC_ERR_INVALID_ARG;
+    *bytes = model_layout((int)pf.Dk, (int)p.Dk, C, cfg->enc, (int)cfg->class_bits, cfg->flags).total;
     return HDC_OK;
 }
 
@@ -208,8 +231,10 @@ hdc_status hdc_model_prepare(const float *Bt, int32_t F, int32_t D, const int32_
         !perf_of(D, cfg, &p) || !aligned(buf, kAlign))
         return HDC_ERR_INVALID_ARG;
     if (!bits_ok(cfg->class_bits) || !flags_ok(cfg->flags, cfg->class_bits, C)) return HDC_ERR_UNSUPPORTED;
-    const int Dk = (int)p.Dk, enc = cfg->enc, bits = (int)cfg->class_bits;
-    const ModelLayout L = model_layout(F, Dk, C, enc, bits, cfg->flags);
+    Perf pf;
+    if (!feat_perf_of(F, cfg, &pf)) return HDC_ERR_INVALID_ARG;
+    const int Dk = (int)p.Dk, enc = cfg->enc, bits = (int)cfg->class_bits, Fk = (int)pf.Dk;
+    const ModelLayout L = model_layout(Fk, Dk, C, enc, bits, cfg->flags);
     if (buf_bytes < L.total) return HDC_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     char *b = (char *)buf;
@@ -221,15 +246,19 @@ hdc_status hdc_model_prepare(const float *Bt, int32_t F, int32_t D, const int32_
     m.Dk = Dk;
     m.C = C;
     m.enc = enc;
-    m.ldb = ld_for(enc, F);
+    m.ldb = ld_for(enc, Fk);
+    m.Fk = Fk;
+    m.fs0 = (int32_t)pf.s0;
+    m.fstride = (int32_t)pf.stride;
     m.class_bits = bits;
     m.flags = cfg->flags;
     m.W = words_for(Dk);
     m.Bq = b + L.bq;
     m.b_scale = enc == HDC_ENC_FP8_E4M3 ? (const float *)(b + L.bscale) : nullptr;
     // rows K of B^T: row k of Bq = quantise(Bt[s0 + k*stride])
-    hdc_status s = cu(launch_quant_rows(Bt, F, p.s0, p.stride, Dk, F, enc, b + L.bq, m.ldb,
-                                        (float *)(b + L.bscale), st));
+    // rows K of B^T (and, for a perforated encoding, their kept features)
+    hdc_status s = cu(launch_quant_rows(Bt, F, p.s0, p.stride, Dk, Fk, enc, b + L.bq, m.ldb,
+                                        (float *)(b + L.bscale), st, pf.s0, pf.stride));
     if (s != HDC_OK) return s;
     if (C > 0) {
         m.cls = (const uint32_t *)(b + L.planes);
@@ -280,11 +309,11 @@ hdc_status hdc_encode(const float *X, int64_t N, const hdc_model *m, uint32_t *H
     if (s != HDC_OK) return s;
     if (use_tc(m)) {
         TcArgs a = {};
-        a.Xq = Xop; a.N = N; a.F = m->F; a.ldx = (int)ldx; a.Bq = m->Bq; a.ldb = m->ldb; a.Dk = m->Dk; a.enc = m->enc;
+        a.Xq = Xop; a.N = N; a.F = m->Fk; a.ldx = (int)ldx; a.Bq = m->Bq; a.ldb = m->ldb; a.Dk = m->Dk; a.enc = m->enc;
         a.sx = sx; a.sb = m->b_scale; a.H = H; a.scores = scores; a.W = m->W;
         if (tc_supported(a)) return cu(timed_tc(a, st));
     }
-    return cu(timed_simt(Xop, ldx, N, m->F, m->Bq, m->ldb, m->Dk, m->enc, sx, m->b_scale, H, m->W, scores,
+    return cu(timed_simt(Xop, ldx, N, m->Fk, m->Bq, m->ldb, m->Dk, m->enc, sx, m->b_scale, H, m->W, scores,
                                  st));
 }
 
@@ -387,7 +416,7 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *
         bool done = false;
         if (use_tc(m)) {
             TcArgs e = {};
-            e.Xq = Xop; e.N = N; e.F = m->F; e.ldx = (int)ldx; e.Bq = m->Bq; e.ldb = m->ldb; e.Dk = m->Dk;
+            e.Xq = Xop; e.N = N; e.F = m->Fk; e.ldx = (int)ldx; e.Bq = m->Bq; e.ldb = m->ldb; e.Dk = m->Dk;
             e.enc = m->enc; e.sx = sx; e.sb = m->b_scale; e.W = m->W; e.sproj = sp; e.ldS = ldS; e.qn = qn;
             if (tc_supported(e)) {
                 s = cu(timed_tc(e, st));
@@ -400,7 +429,7 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *
             // two, common to the row: neither BF16 rounding nor the cosine
             // changes relative to the dropped-scale definition)
             float *sf = (float *)((char *)ws + L.sf);
-            s = cu(timed_simt(Xop, ldx, N, m->F, m->Bq, m->ldb, m->Dk, m->enc, sx, m->b_scale, Hb, m->W, sf, st));
+            s = cu(timed_simt(Xop, ldx, N, m->Fk, m->Bq, m->ldb, m->Dk, m->enc, sx, m->b_scale, Hb, m->W, sf, st));
             if (s != HDC_OK) return s;
             s = cu(launch_proj_bf16(sf, N, m->Dk, sp, ldS, qn, st));
             if (s != HDC_OK) return s;
@@ -413,7 +442,7 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *
     bool encoded = false;
     if (use_tc(m)) {
         TcArgs a = {};
-        a.Xq = Xop; a.N = N; a.F = m->F; a.ldx = (int)ldx; a.Bq = m->Bq; a.ldb = m->ldb; a.Dk = m->Dk; a.enc = m->enc;
+        a.Xq = Xop; a.N = N; a.F = m->Fk; a.ldx = (int)ldx; a.Bq = m->Bq; a.ldb = m->ldb; a.Dk = m->Dk; a.enc = m->enc;
         a.sx = sx; a.sb = m->b_scale; a.W = m->W;
         a.planes = m->cls; a.C = m->C; a.nb = nb; a.csum = m->cls_sum; a.cnorm = m->cls_norm;
         a.labels = labels; a.dists = dists; a.sims = scores;
@@ -429,7 +458,7 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *
         }
     }
     if (!encoded) {
-        s = cu(timed_simt(Xop, ldx, N, m->F, m->Bq, m->ldb, m->Dk, m->enc, sx, m->b_scale, Hb, m->W,
+        s = cu(timed_simt(Xop, ldx, N, m->Fk, m->Bq, m->ldb, m->Dk, m->enc, sx, m->b_scale, Hb, m->W,
                                   nullptr, st));
         if (s != HDC_OK) return s;
     }

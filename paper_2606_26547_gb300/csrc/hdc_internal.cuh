@@ -39,10 +39,12 @@ inline int esize_for(int enc) { return enc == HDC_ENC_BF16 ? 2 : enc == HDC_ENC_
 
 // K1: quantise rows src[row_off + k*row_step] (F floats each, row stride lds)
 // into dst row k (ldd elements, zero padded); FP8 writes the row's power-of-
-// two scale to scale[k].  enc: HDC_ENC_FP32 (copy), BF16, FP8_E4M3.
+// two scale to scale[k].  enc: HDC_ENC_FP32 (copy), BF16, FP8_E4M3.  With
+// (c0, cstep) != (0, 1), element f of a row is source column c0 + f*cstep
+// (the kept features of a perforated encoding reduction).
 cudaError_t launch_quant_rows(const float *src, int64_t lds, int64_t row_off, int64_t row_step,
                               int64_t nrows, int F, int enc, void *dst, int ldd, float *scale,
-                              cudaStream_t st);
+                              cudaStream_t st, int64_t c0 = 0, int64_t cstep = 1);
 
 // Class preparation: planes [b][C][W] (or, with vals, the b-bit values as
 // BF16 rows of ldv elements, zero past Dk), sums and norms over the kept dims.

@@ -59,10 +59,19 @@ __device__ __forceinline__ uint2 to_bf16x4(float a, float b, float c, float d)
     return make_uint2(*reinterpret_cast<uint32_t *>(&x), *reinterpret_cast<uint32_t *>(&y));
 }
 
-// Four consecutive elements [f, f+4) of a row (zero past F).
-template <bool VEC>
-__device__ __forceinline__ float4 load4(const float *row, int f, int F)
+// Four consecutive elements [f, f+4) of a row (zero past F); with GATHER,
+// element f of the row is column c0 + f * cstep of the source.
+template <bool VEC, bool GATHER = false>
+__device__ __forceinline__ float4 load4(const float *row, int f, int F, int64_t c0 = 0, int64_t cstep = 1)
 {
+    if (GATHER) {
+        float4 v;
+        v.x = f < F ? __ldg(row + c0 + (int64_t)f * cstep) : 0.f;
+        v.y = f + 1 < F ? __ldg(row + c0 + (int64_t)(f + 1) * cstep) : 0.f;
+        v.z = f + 2 < F ? __ldg(row + c0 + (int64_t)(f + 2) * cstep) : 0.f;
+        v.w = f + 3 < F ? __ldg(row + c0 + (int64_t)(f + 3) * cstep) : 0.f;
+        return v;
+    }
     if (VEC) {  // F % 4 == 0 and 16-byte aligned rows
         if (f < F) return __ldg(reinterpret_cast<const float4 *>(row + f));
         return make_float4(0.f, 0.f, 0.f, 0.f);
@@ -80,11 +89,14 @@ __device__ __forceinline__ float4 load4(const float *row, int f, int F)
 // reduction and the conversion.
 constexpr int MAXIT = 8;
 
-template <int ENC, bool VEC>
+// GATHER: the F elements of a row are the source columns c0 + f * cstep
+// (the kept features of a perforated encoding reduction).
+template <int ENC, bool VEC, bool GATHER = false>
 __global__ void __launch_bounds__(256) quant_rows_kernel(const float *__restrict__ src, int64_t lds,
                                                          int64_t row_off, int64_t row_step, int64_t nrows,
                                                          int F, void *__restrict__ dst, int ldd,
-                                                         float *__restrict__ scale)
+                                                         float *__restrict__ scale, int64_t c0 = 0,
+                                                         int64_t cstep = 1)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -101,12 +113,12 @@ __global__ void __launch_bounds__(256) quant_rows_kernel(const float *__restrict
 #pragma unroll
                 for (int it = 0; it < MAXIT; it++)
                     if (it < nit) {
-                        v[it] = load4<VEC>(row, it * 128 + lane * 4, F);
+                        v[it] = load4<VEC, GATHER>(row, it * 128 + lane * 4, F, c0, cstep);
                         amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v[it].x), fabsf(v[it].y)),
                                                  fmaxf(fabsf(v[it].z), fabsf(v[it].w))));
                     }
             } else {
-                for (int f = lane; f < F; f += 32) amax = fmaxf(amax, fabsf(__ldg(row + f)));
+                for (int f = lane; f < F; f += 32) amax = fmaxf(amax, fabsf(__ldg(row + c0 + (int64_t)f * cstep)));
             }
 #pragma unroll
             for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
@@ -131,7 +143,7 @@ __global__ void __launch_bounds__(256) quant_rows_kernel(const float *__restrict
                 if (it < nit && f0 < ldd) emit(f0, v[it]);
             }
         } else {
-            for (int f0 = lane * 4; f0 < ldd; f0 += 128) emit(f0, load4<VEC>(row, f0, F));
+            for (int f0 = lane * 4; f0 < ldd; f0 += 128) emit(f0, load4<VEC, GATHER>(row, f0, F, c0, cstep));
         }
     }
 }
@@ -327,9 +339,20 @@ __global__ void __launch_bounds__(256) class_prepare_kernel(const int32_t *__res
 }  // namespace
 
 cudaError_t launch_quant_rows(const float *src, int64_t lds, int64_t row_off, int64_t row_step, int64_t nrows,
-                              int F, int enc, void *dst, int ldd, float *scale, cudaStream_t st)
+                              int F, int enc, void *dst, int ldd, float *scale, cudaStream_t st, int64_t c0,
+                              int64_t cstep)
 {
     if (nrows <= 0) return cudaSuccess;
+    if (c0 != 0 || cstep != 1) {  // kept features of a perforated encoding: gathering row kernel
+        const int64_t blocks = (nrows + 7) / 8 < 65535 * 8 ? (nrows + 7) / 8 : 65535 * 8;
+#define HDC_QUANT_G(E) quant_rows_kernel<E, false, true><<<(unsigned)blocks, 256, 0, st>>>( \
+        src, lds, row_off, row_step, nrows, F, dst, ldd, scale, c0, cstep)
+        if (enc == HDC_ENC_FP32) HDC_QUANT_G(HDC_ENC_FP32);
+        else if (enc == HDC_ENC_BF16) HDC_QUANT_G(HDC_ENC_BF16);
+        else HDC_QUANT_G(HDC_ENC_FP8_E4M3);
+#undef HDC_QUANT_G
+        return cudaGetLastError();
+    }
     const bool aligned_rows = F % 4 == 0 && lds % 4 == 0 && ((uintptr_t)src % 16) == 0;
     const size_t qsmem = (size_t)QWARPS * QSLOTS * F * 4 + (size_t)QWARPS * QSLOTS * 8;
     if (aligned_rows && qsmem <= 200 * 1024) {

@@ -34,7 +34,8 @@ class HdcError(RuntimeError):
 class ApproxConfigC(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("perf_start", ctypes.c_float), ("perf_end", ctypes.c_float),
                 ("perf_stride", ctypes.c_uint32), ("enc", ctypes.c_int32), ("class_bits", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("enc_perf_start", ctypes.c_float), ("enc_perf_end", ctypes.c_float),
+                ("enc_perf_stride", ctypes.c_uint32)]
 
 
 class ModelC(ctypes.Structure):
@@ -43,7 +44,7 @@ class ModelC(ctypes.Structure):
                 ("class_bits", ctypes.c_int32), ("W", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("Bq", ctypes.c_void_p), ("b_scale", ctypes.c_void_p), ("cls", ctypes.c_void_p),
                 ("cls_sum", ctypes.c_void_p), ("cls_norm", ctypes.c_void_p), ("cls_sign", ctypes.c_void_p),
-                ("ldcs", ctypes.c_int32)]
+                ("ldcs", ctypes.c_int32), ("Fk", ctypes.c_int32), ("fs0", ctypes.c_int32), ("fstride", ctypes.c_int32)]
 
 
 _P, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
@@ -124,6 +125,10 @@ class ApproxConfig:
     class_bits: int = 1
     simt: bool = False  # force the CUDA-core encoder
     float_query: bool = False  # cosine on non-binarised query hypervectors (class_bits 4 / 8)
+    # perforation of the encoding's own reduction over the F features
+    enc_perf_start: float = 0.0
+    enc_perf_end: float = 1.0
+    enc_perf_stride: int = 1
 
     def c(self) -> ApproxConfigC:
         cfg = ApproxConfigC()
@@ -134,6 +139,9 @@ class ApproxConfig:
         cfg.enc = ENC[self.enc]
         cfg.class_bits = self.class_bits
         cfg.flags = (FLAG_SIMT_ENCODE if self.simt else 0) | (FLAG_FLOAT_QUERY if self.float_query else 0)
+        cfg.enc_perf_start = self.enc_perf_start
+        cfg.enc_perf_end = self.enc_perf_end
+        cfg.enc_perf_stride = self.enc_perf_stride
         return cfg
 
 

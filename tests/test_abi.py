@@ -125,3 +125,38 @@ def test_sweep_spec_checks_without_gpu(lib):
     spec = hdc.sweep_spec((1,) * 6, (1,))
     spec.n_strides = 7
     assert lib.hdc_sweep_workspace_bytes(100, 10, ctypes.byref(spec), ctypes.byref(n)) == 1
+
+
+def _struct_fields(name):
+    src = open(os.path.join(ROOT, "include", "hdc.h")).read()
+    body = re.search(r"typedef struct \{([^}]*)\} " + name + ";", src).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            names += [n.strip().lstrip("*") for n in re.sub(r"^(const\s+)?\w+\s*\**", "", decl).split(",")]
+    return [n.strip("* ") for n in names]
+
+
+@pytest.mark.parametrize("cname,pyname", [("hdc_approx_config", "ApproxConfigC"), ("hdc_model", "ModelC"),
+                                          ("hdc_levelid_model", "LevelIdModelC")])
+def test_struct_layouts_match_header(lib, cname, pyname):
+    from paper_2606_26547_gb300 import hdc
+    assert _struct_fields(cname) == [f[0] for f in getattr(hdc, pyname)._fields_]
+
+
+def test_encoding_perforation_checks_without_gpu(lib):
+    """Encoding perforation (start, end, stride over F) is validated like the
+    dimension perforation; the model is sized for the kept features."""
+    from paper_2606_26547_gb300 import hdc
+    n0, n1 = ctypes.c_size_t(), ctypes.c_size_t()
+    full = hdc.ApproxConfig(enc="fp8").c()
+    half = hdc.ApproxConfig(enc="fp8", enc_perf_end=0.5).c()
+    assert lib.hdc_model_bytes(784, 10000, 10, ctypes.byref(full), ctypes.byref(n0)) == 0
+    assert lib.hdc_model_bytes(784, 10000, 10, ctypes.byref(half), ctypes.byref(n1)) == 0
+    assert n1.value < n0.value
+    for bad in (hdc.ApproxConfig(enc_perf_start=0.6, enc_perf_end=0.5), hdc.ApproxConfig(enc_perf_stride=0),
+                hdc.ApproxConfig(enc_perf_end=0.001)):
+        c = bad.c()
+        assert lib.hdc_model_bytes(784, 10000, 10, ctypes.byref(c), ctypes.byref(n0)) == 1
