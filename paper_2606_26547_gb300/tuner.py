@@ -35,6 +35,7 @@ class width at once.
 """
 from __future__ import annotations
 
+import collections
 import ctypes
 import dataclasses
 import json
@@ -55,7 +56,10 @@ STRIDES = (1, 2, 4, 8, 16, 32)
 BITS = (1, 4, 8)
 GRID = 100          # start / end fractions on a 1/GRID grid
 MIN_SPAN = 5        # end - start >= MIN_SPAN / GRID
-MODES = ("none", "end_only", "full")
+# Sec. 5.2's pruning modes: none = (3) No RedPerf, end_only = (2) End-only
+# + hint, full = (4) Full RedPerf + hint, full_nohint = (1) Full RedPerf
+# (the encoding's own reduction perforated too)
+MODES = ("none", "end_only", "full", "full_nohint")
 
 
 @dataclasses.dataclass(frozen=True, order=True)
@@ -68,16 +72,24 @@ class Config:
     stride: int
     bits: int
     query: str = "binary"
+    e_start: float = 0.0     # red_perf of the encoding's reduction over features
+    e_end: float = 1.0
+    e_stride: int = 1
+
+    def fperf(self):
+        return (self.e_start, self.e_end, self.e_stride)
 
 
+NO_FPERF = (0.0, 1.0, 1)
 QUERIES = ("binary", "float")
 
 
 def perf_values(mode: str):
     """(starts, ends, strides) of one red_perf op under a pruning mode."""
-    starts = tuple(i / GRID for i in range(GRID - MIN_SPAN + 1)) if mode == "full" else (0.0,)
+    full = mode in ("full", "full_nohint")
+    starts = tuple(i / GRID for i in range(GRID - MIN_SPAN + 1)) if full else (0.0,)
     ends = tuple(i / GRID for i in range(MIN_SPAN, GRID + 1)) if mode != "none" else (1.0,)
-    strides = STRIDES if mode == "full" else (1,)
+    strides = STRIDES if full else (1,)
     return starts, ends, strides
 
 
@@ -85,8 +97,8 @@ class Space:
     """The knobs of one pruning mode as index ranges; a point is a tuple of
     value indices in KNOBS order.  SPANS lists the (start, end) knob pairs of
     the red_perf ops, each of which must keep end - start >= MIN_SPAN/GRID."""
-    KNOBS = ("enc", "dim", "epochs", "start", "end", "stride", "bits", "query")
-    SPANS = (("start", "end"),)
+    KNOBS = ("enc", "dim", "epochs", "start", "end", "stride", "bits", "query", "e_start", "e_end", "e_stride")
+    SPANS = (("start", "end"), ("e_start", "e_end"))
     CONFIG = Config
 
     def __init__(self, mode: str, D: int, max_epochs: int, dim_levels: int = 5, min_dim: int = 128,
@@ -101,8 +113,10 @@ class Space:
 
     def _values(self, mode, dims, max_epochs):
         starts, ends, strides = perf_values(mode)
+        # the encoding's reduction is perforated only without the no-approx hint
+        es, ee, est = perf_values("full") if mode == "full_nohint" else ((0.0,), (1.0,), (1,))
         return dict(enc=self.encs, dim=dims, epochs=tuple(range(max_epochs + 1)), start=starts, end=ends,
-                    stride=strides, bits=BITS, query=QUERIES)
+                    stride=strides, bits=BITS, query=QUERIES, e_start=es, e_end=ee, e_stride=est)
 
     def log10_size(self) -> float:
         return float(sum(math.log10(n) for n in self.sizes))
@@ -123,8 +137,10 @@ class Space:
     def valid(self, c) -> bool:
         if getattr(c, "query", "binary") == "float" and c.bits == 1:
             return False     # a float query is compared by cosine only
-        if lid_levels(c.enc) and (c.bits != 1 or getattr(c, "query", "binary") != "binary"):
-            return False     # Level-ID rows are binary, compared by Hamming
+        if lid_levels(c.enc) and (c.bits != 1 or getattr(c, "query", "binary") != "binary" or
+                                  getattr(c, "e_start", 0.0) != 0.0 or getattr(c, "e_end", 1.0) != 1.0 or
+                                  getattr(c, "e_stride", 1) != 1):
+            return False     # Level-ID rows are binary, compared by Hamming, all features
         return all(round((getattr(c, e) - getattr(c, a)) * GRID) >= MIN_SPAN for a, e in self.SPANS)
 
     def repair(self, point):
@@ -141,6 +157,8 @@ class Space:
             kq, kb, ke = self.KNOBS.index("query"), self.KNOBS.index("bits"), self.KNOBS.index("enc")
             if lid_levels(self.values["enc"][p[ke]]):
                 p[kq], p[kb] = self.values["query"].index("binary"), self.values["bits"].index(1)
+                for k, v in (("e_start", 0.0), ("e_end", 1.0), ("e_stride", 1)):
+                    p[self.KNOBS.index(k)] = self.values[k].index(v)
             elif self.values["query"][p[kq]] == "float" and self.values["bits"][p[kb]] == 1:
                 p[kb] = self.values["bits"].index(8)
         return tuple(p)
@@ -438,11 +456,20 @@ class GpuEvaluator:
                 self.lid[enc] = tuple(torch.from_numpy(a).to(dev)
                                       for a in synth.levelid_hvs(w.F, w.D, lid_levels(enc), w.seed))
         self.max_epochs, self.dims = max_epochs, tuple(dims)
-        self.snap, self.Hv = {}, {}
-        self.t_encode_train, self.t_train = {}, {}
+        # per family (enc, dim, feature perforation): the accumulators after
+        # each epoch, the validation hypervectors and the measured training
+        # times; families with a perforated encoding are built on first use
+        # and the least recently used of them dropped past `max_families`
+        self.fam = collections.OrderedDict()
+        self.max_families = 96
         self.t_classify = {}
         self.sweep_launches = 0
-        self._prepare()
+        self.families_built = 0
+        for enc in self.encs:
+            for dim in self.dims:
+                self._family((enc, dim, NO_FPERF), pin=True)
+        torch = self.torch
+        torch.cuda.synchronize()
 
     def _ms(self, fn) -> float:
         torch = self.torch
@@ -462,49 +489,65 @@ class GpuEvaluator:
         return self.hdc.LevelIdModel(ids[:, :dim].contiguous(), lo[:dim].contiguous(), hi[:dim].contiguous(),
                                      flip[:dim].contiguous(), lid_levels(enc), self.x_lo, self.x_hi, cfg)
 
-    def _encoder(self, enc: str, dim: int, N: int):
+    def _rp_cfg(self, enc: str, fperf, **kw):
+        return self.hdc.ApproxConfig(enc=enc, enc_perf_start=fperf[0], enc_perf_end=fperf[1],
+                                     enc_perf_stride=fperf[2], **kw)
+
+    def _encoder(self, enc: str, dim: int, N: int, fperf=NO_FPERF):
         """(encode(X, out) for N rows at D' = dim, words per row)."""
         hdc = self.hdc
         if lid_levels(enc):
             m = self._lid_model(enc, dim)
             return (lambda X, out: hdc.levelid_encode(X, m, out=out)), m.W
-        base = hdc.Model(self.Bt[:dim], hdc.ApproxConfig(enc=enc))
+        base = hdc.Model(self.Bt[:dim], self._rp_cfg(enc, fperf))
         ws = base.workspace(N)
         return (lambda X, out: hdc.encode(X, base, ws=ws, out=out)), base.W
 
-    def _prepare(self):
+    def _family(self, key, pin: bool = False) -> dict:
+        """Train the family (enc, dim, fperf) as the application runs it --
+        bundling, then every epoch, each pass timed and the accumulators kept
+        after each -- and encode the validation set."""
+        if key in self.fam:
+            self.fam.move_to_end(key)
+            return self.fam[key]
         torch, hdc, w = self.torch, self.hdc, self.w
+        enc, dim, fperf = key
         N = self.Xtr.shape[0]
-        for enc in self.encs:
-            for dim in self.dims:
-                encf, W = self._encoder(enc, dim, N)
-                Htr = torch.empty((N, W), dtype=torch.int32, device=self.dev)
-                self.t_encode_train[(enc, dim)] = self._ms(lambda: encf(self.Xtr, Htr))
-                n = ctypes.c_size_t()
-                hdc._call("hdc_train_workspace_bytes", N, dim, w.C, ctypes.byref(n))
-                tws = hdc._empty_bytes(n.value, self.dev)
-                acc = torch.empty((w.C, dim), dtype=torch.int32, device=self.dev)
-                cls = torch.empty((w.C, hdc.words(dim)), dtype=torch.int32, device=self.dev)
-                # training as the application runs it: bundling, then epochs;
-                # each pass timed, the accumulators kept after each
-                for rep in range(2):   # the first run warms up
-                    times = []
-                    for ep in range(self.max_epochs + 1):
-                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                        a.record()
-                        hdc.train_epoch(Htr, self.ytr, dim, w.C, 0 if ep == 0 else 1, acc, cls, ws=tws)
-                        b.record()
-                        if rep:
-                            self.snap[(enc, dim, ep)] = acc.clone()
-                        times.append((a, b))
-                    torch.cuda.synchronize()
-                cum = np.cumsum([a.elapsed_time(b) for a, b in times])
-                for ep in range(self.max_epochs + 1):
-                    self.t_train[(enc, dim, ep)] = float(cum[ep])
-                encv, _ = self._encoder(enc, dim, self.Xv.shape[0])
-                self.Hv[(enc, dim)] = torch.empty((self.Xv.shape[0], W), dtype=torch.int32, device=self.dev)
-                encv(self.Xv, self.Hv[(enc, dim)])
-        torch.cuda.synchronize()
+        encf, W = self._encoder(enc, dim, N, fperf)
+        Htr = torch.empty((N, W), dtype=torch.int32, device=self.dev)
+        f = {"pin": pin, "t_encode": self._ms(lambda: encf(self.Xtr, Htr)), "snap": [], "t_train": []}
+        n = ctypes.c_size_t()
+        hdc._call("hdc_train_workspace_bytes", N, dim, w.C, ctypes.byref(n))
+        tws = hdc._empty_bytes(n.value, self.dev)
+        acc = torch.empty((w.C, dim), dtype=torch.int32, device=self.dev)
+        cls = torch.empty((w.C, hdc.words(dim)), dtype=torch.int32, device=self.dev)
+        for rep in range(2):   # the first run warms up
+            times = []
+            for ep in range(self.max_epochs + 1):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                hdc.train_epoch(Htr, self.ytr, dim, w.C, 0 if ep == 0 else 1, acc, cls, ws=tws)
+                b.record()
+                if rep:
+                    f["snap"].append(acc.clone())
+                times.append((a, b))
+            torch.cuda.synchronize()
+        f["t_train"] = [float(v) for v in np.cumsum([a.elapsed_time(b) for a, b in times])]
+        encv, _ = self._encoder(enc, dim, self.Xv.shape[0], fperf)
+        f["Hv"] = torch.empty((self.Xv.shape[0], W), dtype=torch.int32, device=self.dev)
+        encv(self.Xv, f["Hv"])
+        self.fam[key] = f
+        self.families_built += 1
+        while len(self.fam) > self.max_families:   # drop the least recently used unpinned family
+            victim = next((k for k, v in self.fam.items() if not v["pin"]), None)
+            if victim is None:
+                break
+            del self.fam[victim]
+        return f
+
+    @staticmethod
+    def _key(c: Config):
+        return (c.enc, c.dim, c.fperf())
 
     def classify_ms(self, c: Config) -> float:
         hdc, torch = self.hdc, self.torch
@@ -512,7 +555,7 @@ class GpuEvaluator:
             # Level-ID encode of the kept dims + Hamming arg-min over them
             cfg = hdc.ApproxConfig(perf_start=c.start, perf_end=c.end, perf_stride=c.stride)
             Dk = hdc.kept_dims(c.dim, cfg)
-            key = (c.enc, Dk, 1, "binary")
+            key = (c.enc, Dk, 1, "binary", self.w.F)
             if key not in self.t_classify:
                 m = self._lid_model(c.enc, c.dim, cfg)
                 H = torch.empty((self.Xv.shape[0], m.W), dtype=torch.int32, device=self.dev)
@@ -520,27 +563,32 @@ class GpuEvaluator:
                 self.t_classify[key] = self._ms(lambda: (hdc.levelid_encode(self.Xv, m, out=H),
                                                          hdc.hamming_argmin(H, cls, Dk)))
             return self.t_classify[key]
-        cfg = hdc.ApproxConfig(enc=c.enc, class_bits=c.bits, perf_start=c.start, perf_end=c.end,
-                               perf_stride=c.stride, float_query=c.query == "float")
+        cfg = self._rp_cfg(c.enc, c.fperf(), class_bits=c.bits, perf_start=c.start, perf_end=c.end,
+                           perf_stride=c.stride, float_query=c.query == "float")
+        fam = self._family(self._key(c))
+        model = None
         Dk = hdc.kept_dims(c.dim, cfg)
-        key = (c.enc, Dk, c.bits, c.query)
+        Fk = len(range(int(np.floor(np.float64(np.float32(c.e_start)) * self.w.F)),
+                       int(np.floor(np.float64(np.float32(c.e_end)) * self.w.F)), c.e_stride))
+        key = (c.enc, Dk, c.bits, c.query, Fk)
         if key not in self.t_classify:
-            model = hdc.Model(self.Bt[:c.dim], cfg, acc=self.snap[(c.enc, c.dim, 0)])
+            model = hdc.Model(self.Bt[:c.dim], cfg, acc=fam["snap"][0])
             ws = model.workspace(self.Xv.shape[0])
             lab = torch.empty(self.Xv.shape[0], dtype=torch.int32, device=self.dev)
             self.t_classify[key] = self._ms(lambda: hdc.classify(self.Xv, model, ws=ws, labels=lab))
         return self.t_classify[key]
 
     def ms(self, c: Config) -> float:
-        return self.t_encode_train[(c.enc, c.dim)] + self.t_train[(c.enc, c.dim, c.epochs)] + self.classify_ms(c)
+        fam = self._family(self._key(c))
+        return fam["t_encode"] + fam["t_train"][c.epochs] + self.classify_ms(c)
 
     def float_accuracy(self, c: Config) -> float:
         """A float-query candidate: classify the validation set with a model
         prepared for it (the sweep scores binary queries only)."""
         hdc = self.hdc
-        cfg = hdc.ApproxConfig(enc=c.enc, class_bits=c.bits, perf_start=c.start, perf_end=c.end,
-                               perf_stride=c.stride, float_query=True)
-        model = hdc.Model(self.Bt[:c.dim], cfg, acc=self.snap[(c.enc, c.dim, c.epochs)])
+        cfg = self._rp_cfg(c.enc, c.fperf(), class_bits=c.bits, perf_start=c.start, perf_end=c.end,
+                           perf_stride=c.stride, float_query=True)
+        model = hdc.Model(self.Bt[:c.dim], cfg, acc=self._family(self._key(c))["snap"][c.epochs])
         lab = hdc.classify(self.Xv, model)
         return float((lab == self.yv).sum().item()) / self.Xv.shape[0]
 
@@ -555,24 +603,25 @@ class GpuEvaluator:
         for c in configs:
             if c.query == "float":
                 continue
-            groups.setdefault((c.enc, c.dim, c.epochs), set()).add((c.start, c.end, c.stride))
+            groups.setdefault((self._key(c), c.epochs), set()).add((c.start, c.end, c.stride))
         pending = []
-        for (enc, dim, ep), entries in groups.items():
+        for (key, ep), entries in groups.items():
+            fam = self._family(key)
             entries = sorted(entries)
             for i in range(0, len(entries), 6):
                 chunk = entries[i:i + 6]
-                sw = hdc.Sweep(dim, self.w.C, [e[2] for e in chunk], BITS, N, self.dev,
+                sw = hdc.Sweep(key[1], self.w.C, [e[2] for e in chunk], BITS, N, self.dev,
                                starts=[e[0] for e in chunk], ends=[e[1] for e in chunk])
-                sw(self.Hv[(enc, dim)], self.yv, self.snap[(enc, dim, ep)])
+                sw(fam["Hv"], self.yv, fam["snap"][ep])
                 self.sweep_launches += 1
-                pending.append((enc, dim, ep, chunk, sw.correct))
-        for enc, dim, ep, chunk, corr in pending:
+                pending.append((key, ep, chunk, sw.correct))
+        for (enc, dim, fperf), ep, chunk, corr in pending:
             corr = corr.cpu().numpy()
             for jb, b in enumerate(BITS):
                 if lid_levels(enc) and b != 1:
                     continue   # Level-ID candidates are Hamming only
                 for j, (s, e, st) in enumerate(chunk):
-                    out[Config(enc, dim, ep, s, e, st, b)] = float(corr[jb, j]) / N
+                    out[Config(enc, dim, ep, s, e, st, b, "binary", *fperf)] = float(corr[jb, j]) / N
         return out
 
     def __call__(self, configs) -> dict:
@@ -660,7 +709,8 @@ def main(argv=None):
     for mode in a.modes.split(","):
         s = Search(space_cls(mode, w.D, epochs), ev, base, a.qos_drop, a.seed)
         reports.append(s.run(a.evaluations, a.seconds).report())
-    extra = ({"sweep_launches": ev.sweep_launches, "classify_cost_entries": len(ev.t_classify)}
+    extra = ({"sweep_launches": ev.sweep_launches, "classify_cost_entries": len(ev.t_classify),
+              "trained_families": ev.families_built}
              if a.app == "classify" else {"cluster_runs": ev.runs, "graph_cost_entries": len(ev.t)})
     print(json.dumps({"app": a.app, "workload": wl, "prepare_s": round(prep, 3), **extra, "modes": reports}))
 

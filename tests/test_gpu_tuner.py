@@ -30,10 +30,11 @@ def one_by_one(ev, c):
         lab = hdc.hamming_argmin(hdc.levelid_encode(ev.Xv, m), cls, c.dim, cfg)
         return float((lab == ev.yv).sum().item()) / ev.Xv.shape[0]
     Bt = ev.Bt[:c.dim]
-    H = hdc.encode(ev.Xtr, hdc.Model(Bt, hdc.ApproxConfig(enc=c.enc)))
+    fp = dict(enc_perf_start=c.e_start, enc_perf_end=c.e_end, enc_perf_stride=c.e_stride)
+    H = hdc.encode(ev.Xtr, hdc.Model(Bt, hdc.ApproxConfig(enc=c.enc, **fp)))
     acc, _, _ = hdc.train(H, ev.ytr, c.dim, ev.w.C, c.epochs)
     m = hdc.Model(Bt, hdc.ApproxConfig(enc=c.enc, class_bits=c.bits, perf_start=c.start, perf_end=c.end,
-                                       perf_stride=c.stride, float_query=c.query == "float"), acc=acc)
+                                       perf_stride=c.stride, float_query=c.query == "float", **fp), acc=acc)
     lab = hdc.classify(ev.Xv, m)
     return float((lab == ev.yv).sum().item()) / ev.Xv.shape[0]
 
@@ -103,3 +104,16 @@ def test_tuner_levelid_candidates_equal_one_by_one():
     for c in lid[:6]:
         assert s.results[c].accuracy == one_by_one(ev, c), c
         assert s.results[c].ms > 0
+
+
+def test_tuner_full_nohint_perforates_the_encoding(ev):
+    """Mode (1): candidates with a perforated encoding are trained on
+    demand; their accuracies equal the same configurations run one by one."""
+    from paper_2606_26547_gb300 import tuner as T
+    space = T.Space("full_nohint", 1024, 4, dim_levels=3)
+    s = T.Search(space, ev, T.baseline_config(1024, 4), seed=11, batch=24)
+    s.run(evaluations=100)
+    perf = [c for c in s.results if c.fperf() != T.NO_FPERF]
+    assert len(perf) >= 10 and ev.families_built > 9
+    for c in perf[:5]:
+        assert s.results[c].accuracy == one_by_one(ev, c), c

@@ -45,7 +45,7 @@ def brute_best(space, target):
 def test_space_sizes_and_round_trip():
     full, end, none = (T.Space(m, 10000, 10) for m in ("full", "end_only", "none"))
     assert none.values["dim"] == (10000, 5000, 2500, 1250, 625)
-    assert none.sizes == (3, 5, 11, 1, 1, 1, 3, 2)
+    assert none.sizes == (3, 5, 11, 1, 1, 1, 3, 2, 1, 1, 1)
     assert end.sizes[T.Space.KNOBS.index("end")] == 96 and end.sizes[T.Space.KNOBS.index("stride")] == 1
     assert full.log10_size() > end.log10_size() > none.log10_size()
     rng = np.random.default_rng(1)
@@ -163,3 +163,18 @@ def test_levelid_encoders_are_binary_hamming_only():
             assert c.bits == 1 and c.query == "binary"
     assert seen > 500
     assert "lid16" not in T.Space("full", 2048, 10).values["enc"]
+
+
+def test_full_nohint_adds_encoding_perforation_knobs():
+    full, nohint = T.Space("full", 2048, 10), T.Space("full_nohint", 2048, 10)
+    assert full.values["e_start"] == (0.0,) and full.values["e_end"] == (1.0,) and full.values["e_stride"] == (1,)
+    assert len(nohint.values["e_end"]) == 96 and nohint.log10_size() > full.log10_size()
+    rng = np.random.default_rng(1)
+    for _ in range(500):
+        c = nohint.config(nohint.random(rng))
+        assert nohint.valid(c) and c.e_end - c.e_start >= 0.049
+    lid = T.Space("full_nohint", 2048, 10, levelid=True)
+    for _ in range(500):
+        c = lid.config(lid.random(rng))
+        if T.lid_levels(c.enc):
+            assert c.fperf() == T.NO_FPERF
