@@ -414,6 +414,16 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *
         float *qn = (float *)((char *)ws + L.qn);
         const int ldS = lds_for(m->Dk);
         bool done = false;
+        if (use_tc(m) && m->C <= 112) {
+            // encode and cosine fused: the BF16 projections stay on chip
+            TcArgs f = {};
+            f.Xq = Xop; f.N = N; f.F = m->Fk; f.ldx = (int)ldx; f.Bq = m->Bq; f.ldb = m->ldb; f.Dk = m->Dk;
+            f.enc = m->enc; f.sx = sx; f.sb = m->b_scale; f.W = m->W; f.C = m->C; f.labels = labels;
+            if (t_prof_start) cudaEventRecord(t_prof_start, st);
+            const cudaError_t e = launch_tc_fcos(f, (const uint16_t *)m->cls, ldS, m->cls_norm, scores, st);
+            if (t_prof_stop) cudaEventRecord(t_prof_stop, st);
+            if (e != cudaErrorNotSupported) return cu(e);
+        }
         if (use_tc(m)) {
             TcArgs e = {};
             e.Xq = Xop; e.N = N; e.F = m->Fk; e.ldx = (int)ldx; e.Bq = m->Bq; e.ldb = m->ldb; e.Dk = m->Dk;

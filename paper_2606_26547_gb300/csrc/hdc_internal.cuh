@@ -145,6 +145,12 @@ struct CosArgs {
     double *scores;
 };
 cudaError_t launch_tc_cosine(const CosArgs &a, cudaStream_t st);
+
+// Float queries with C <= 112 classes, encode and cosine fused (tc_fcos.cuh):
+// the encoder operands of `a` (Xq, Bq, scales, Dk, C, labels), the BF16 class
+// values cv (Cp x ldS) and their norms; cudaErrorNotSupported outside it.
+cudaError_t launch_tc_fcos(const TcArgs &a, const uint16_t *cv, int ldS, const double *cnorm, double *scores,
+                          cudaStream_t st);
 cudaError_t tc_cosine_read_status(cudaStream_t st, int *status);
 
 }  // namespace hdc

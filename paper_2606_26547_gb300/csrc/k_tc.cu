@@ -4,7 +4,7 @@
 
 #include <mutex>
 
-#include "tc_hamming.cuh"
+#include "tc_fcos.cuh"
 
 namespace hdc {
 namespace {
@@ -152,6 +152,53 @@ cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st)
     if (classify && !make_cls_map(&mc, a.planes, a.W, a.C)) return cudaErrorInvalidValue;
     if (a.enc == HDC_ENC_BF16) return tc::launch_bf16(ma, mb, mc, p, grid, classify, st);
     return tc::launch_fp8(ma, mb, mc, p, grid, classify, st);
+}
+
+cudaError_t launch_tc_fcos(const TcArgs &a, const uint16_t *cv, int ldS, const double *cnorm, double *scores,
+                          cudaStream_t st)
+{
+    if (a.C <= 0 || a.C > tc::FC_CMAX || a.N <= 0 || a.N > 0x7fffffffLL - tc::BM || !cv || !cnorm || !a.labels ||
+        ldS % 64 != 0 || ldS < a.Dk)
+        return cudaErrorNotSupported;
+    // the encoder's operand rules (as tc_supported)
+    if (a.enc != HDC_ENC_BF16 && a.enc != HDC_ENC_FP8_E4M3) return cudaErrorNotSupported;
+    if (a.F <= 0 || a.ldx != a.ldb || a.ldx < a.F || (a.ldx * (a.enc == HDC_ENC_BF16 ? 2 : 1)) % 16 != 0 ||
+        a.Dk <= 0)
+        return cudaErrorNotSupported;
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const int Cp = (a.C + 15) / 16 * 16;
+    CUtensorMap ma, mb, mv;
+    if (!make_map(&ma, a.Xq, a.enc, a.F, a.ldx, a.N, tc::BM) || !make_map(&mb, a.Bq, a.enc, a.F, a.ldb, a.Dk, tc::HBN))
+        return cudaErrorInvalidValue;
+    {
+        cuuint64_t dims[2] = {(cuuint64_t)ldS, (cuuint64_t)Cp};
+        cuuint64_t strides[1] = {(cuuint64_t)ldS * 2};
+        cuuint32_t box[2] = {64, (cuuint32_t)Cp};
+        cuuint32_t estr[2] = {1, 1};
+        if (fn(&mv, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(cv), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    tc::FCParams p;
+    p.N = a.N;
+    p.Dk = a.Dk;
+    const int es = a.enc == HDC_ENC_BF16 ? 2 : 1;
+    p.num_kb = (a.ldx * es + tc::BKB - 1) / tc::BKB;
+    p.nt = (a.Dk + tc::HBN - 1) / tc::HBN;
+    p.C = a.C;
+    p.Cp = Cp;
+    p.sb = a.sb;
+    p.cnorm = cnorm;
+    p.labels = a.labels;
+    p.scores = scores;
+    const int sms = sm_count();
+    if (sms <= 0) return cudaErrorNoDevice;
+    const int64_t m_tiles = (a.N + tc::BM - 1) / tc::BM;
+    const unsigned grid = (unsigned)(m_tiles < sms ? m_tiles : sms);
+    if (a.enc == HDC_ENC_BF16) return tc::launch_fcos_bf16(ma, mb, mv, p, grid, st);
+    return tc::launch_fcos_fp8(ma, mb, mv, p, grid, st);
 }
 
 cudaError_t tc_read_status(cudaStream_t st, int *status)

@@ -1,5 +1,5 @@
 // Tensor-core encoder instances for BF16 operands (tcgen05.mma kind::f16).
-#include "tc_hamming.cuh"
+#include "tc_fcos.cuh"
 
 namespace hdc {
 namespace tc {
@@ -17,6 +17,12 @@ cudaError_t launch_hamming_bf16(const CUtensorMap &ma, const CUtensorMap &mb, co
                                 const HParams &p, unsigned grid, cudaStream_t st)
 {
     return launch_hamming_enc<HDC_ENC_BF16>(ma, mb, ms, p, grid, st);
+}
+
+cudaError_t launch_fcos_bf16(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
+                         const FCParams &p, unsigned grid, cudaStream_t st)
+{
+    return launch_fcos_enc<HDC_ENC_BF16>(ma, mb, mv, p, grid, st);
 }
 
 }  // namespace tc

@@ -1,0 +1,354 @@
+// Fused classify of float (non-binarised) query hypervectors: encode and
+// cosine in one kernel (Sec. 4.2 Algorithmic Choice; the float + cosine form
+// of Sec. 5.2), C <= 112 classes.
+//
+// For each 192-dim tile t of a 128-query block:
+//   S = Xq . Bq^T                (MMA1: M 128, N 192, K = F, BF16 or E4M3)
+//   q = bf16(S * sb_k)           (the epilogue: one 64-column K atom per
+//                                 warpgroup into a 128 x 192 BF16 operand;
+//                                 sum of q^2 kept per row)
+//   D2 += q . Cv^T               (MMA2: M 128, N = Cp, K = 192, BF16)
+// with Cv the model's BF16 class values (Cp x ldS; TMA zero fill past ldS).
+// After the last tile: score_c = D2_c / (||q|| ||c||) in FP64 (0 for a zero
+// norm), arg-max with the lowest class on ties.  The projections never
+// reach device memory.
+//
+// Tensor memory: two 192-column encode accumulators and D2 (Cp <= 128).
+// Shared memory: three A/B stages (40 KB each), the 48 KB value tile and the
+// Cp x 384-byte class tile.  Roles as the tensor-core Hamming kernel:
+// warps 0-11 epilogue (three warpgroups), 12 stage producer, 13 MMA issuer,
+// 14 class-tile producer; every wait bounded.
+#pragma once
+#include "tc_hamming.cuh"
+
+namespace hdc {
+namespace tc {
+
+constexpr int FC_STAGES = 3;
+constexpr int FC_A2_BYTES = 3 * A2_ATOM;            // 128 rows x 192 BF16 in three 128-byte K atoms
+constexpr int FC_CMAX = 112;
+// full[S], empty[S], sfull[2], sempty[2], a2full, a2empty, b2full, b2empty,
+// d2full, d2empty, done, merge_full, merge_empty, qfull[2]
+constexpr int FC_NUM_BARS = 2 * FC_STAGES + 4 + 6 + 3 + 2;
+
+__host__ __device__ constexpr size_t fc_smem_bytes(int Cp)
+{
+    return 1024 + (size_t)FC_STAGES * H_STAGE_BYTES + FC_A2_BYTES + (size_t)3 * Cp * 128 + FC_NUM_BARS * 8 + 16 +
+           (size_t)2 * BM * 8 * (HEWG - 1) + (size_t)2 * HEWG * BM * 4;
+}
+static_assert(fc_smem_bytes(FC_CMAX) <= 232448, "shared memory of the fused float-query kernel");
+
+struct FCParams {
+    int64_t N;
+    int Dk, num_kb, nt;
+    int C, Cp;
+    const float *sb;         // base-row scales (FP8) or NULL
+    const double *cnorm;     // C norms of the class values over the kept dims
+    int32_t *labels;
+    double *scores;          // optional N x C
+};
+
+template <int ENC>
+__global__ void __launch_bounds__(H_THREADS, 1)
+    tc_fcos_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmV, const FCParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + FC_STAGES * HA_BYTES;
+    uint8_t *sA2 = smem + FC_STAGES * H_STAGE_BYTES;
+    uint8_t *sB2 = sA2 + FC_A2_BYTES;                               // 3 atoms x Cp rows x 128 B
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB2 + 3 * p.Cp * 128);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + FC_NUM_BARS);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    double *s_val = reinterpret_cast<double *>(tmem_slot + 4);       // warpgroups 1.. : per-row best score
+    int32_t *s_idx = reinterpret_cast<int32_t *>(s_val + (HEWG - 1) * BM);   // and its class
+    float *s_q = reinterpret_cast<float *>(s_idx + (HEWG - 1) * BM);  // 2 x [HEWG][BM] partial squared norms
+    auto full = [&](int s) { return su32(bars + s); };
+    auto empty = [&](int s) { return su32(bars + FC_STAGES + s); };
+    auto sfull = [&](int a) { return su32(bars + 2 * FC_STAGES + a); };
+    auto sempty = [&](int a) { return su32(bars + 2 * FC_STAGES + 2 + a); };
+    const uint32_t a2full = su32(bars + 2 * FC_STAGES + 4), a2empty = su32(bars + 2 * FC_STAGES + 5);
+    const uint32_t b2full = su32(bars + 2 * FC_STAGES + 6), b2empty = su32(bars + 2 * FC_STAGES + 7);
+    const uint32_t d2full = su32(bars + 2 * FC_STAGES + 8), d2empty = su32(bars + 2 * FC_STAGES + 9);
+    const uint32_t done_bar = su32(bars + 2 * FC_STAGES + 10);
+    const uint32_t merge_full = su32(bars + 2 * FC_STAGES + 11), merge_empty = su32(bars + 2 * FC_STAGES + 12);
+    auto qfull = [&](int b) { return su32(bars + 2 * FC_STAGES + 13 + b); };
+    constexpr int PRODUCER = 4 * HEWG, ISSUER = 4 * HEWG + 1, CPRODUCER = 4 * HEWG + 2;
+    constexpr int KELEMS = ENC == HDC_ENC_BF16 ? BKB / 2 : BKB;
+    constexpr uint32_t D2_COL = 2 * HBN;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t num_m_tiles = (p.N + BM - 1) / BM;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < FC_STAGES; s++) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        for (int a = 0; a < 2; a++) {
+            mbar_init(sfull(a), 1);
+            mbar_init(sempty(a), BM * HEWG);
+            mbar_init(qfull(a), BM * HEWG);
+        }
+        mbar_init(a2full, BM * HEWG);
+        mbar_init(a2empty, 1);
+        mbar_init(b2full, 1);
+        mbar_init(b2empty, 1);
+        mbar_init(d2full, 1);
+        mbar_init(d2empty, BM * HEWG);
+        mbar_init(done_bar, 1);
+        mbar_init(merge_full, BM * (HEWG - 1));
+        mbar_init(merge_empty, BM);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == PRODUCER) {
+        if (lane == 0) {  // ------------------------------ A / B stage producer
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+            int stage = 0;
+            uint32_t phase = 0;
+            bool issued[FC_STAGES];
+            uint32_t ipar[FC_STAGES];
+            for (int s = 0; s < FC_STAGES; s++) { issued[s] = false; ipar[s] = 0; }
+            bool ab = false;
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
+                for (int t = 0; t < p.nt && !ab; t++)
+                    for (int kb = 0; kb < p.num_kb; kb++) {
+                        if (!mbar_wait(empty(stage), phase ^ 1, abort_flag)) { ab = true; break; }
+                        mbar_expect_tx(full(stage), H_STAGE_BYTES);
+                        tma_load_2d(su32(sA + stage * HA_BYTES), &tmA, kb * KELEMS, (int)(mt * BM), full(stage));
+                        tma_load_2d(su32(sB + stage * HB_BYTES), &tmB, kb * KELEMS, t * HBN, full(stage));
+                        issued[stage] = true;
+                        ipar[stage] = phase;
+                        if (++stage == FC_STAGES) { stage = 0; phase ^= 1; }
+                    }
+            if (ab) {
+                for (int s = 0; s < FC_STAGES; s++)
+                    if (issued[s]) {
+                        const unsigned long long t0 = gtimer();
+                        while (!mbar_try(full(s), ipar[s]) && gtimer() - t0 < 100000000ull) {}
+                    }
+            }
+        }
+    } else if (warp == CPRODUCER) {
+        if (lane == 0) {  // ------------------------------ class-value tile producer
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmV)) : "memory");
+            uint32_t ph = 0, last = 0;
+            bool any = false, ab = false;
+            const uint32_t bytes = 3u * (uint32_t)p.Cp * 128u;
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
+                for (int t = 0; t < p.nt; t++) {
+                    if (!mbar_wait(b2empty, ph ^ 1, abort_flag)) { ab = true; break; }
+                    mbar_expect_tx(b2full, bytes);
+#pragma unroll
+                    for (int a = 0; a < 3; a++)   // 64 BF16 of K per atom
+                        tma_load_2d(su32(sB2 + a * p.Cp * 128), &tmV, t * HBN + a * 64, 0, b2full);
+                    any = true;
+                    last = ph;
+                    ph ^= 1;
+                }
+            if (ab && any) {
+                const unsigned long long t0 = gtimer();
+                while (!mbar_try(b2full, last) && gtimer() - t0 < 100000000ull) {}
+            }
+        }
+    } else if (warp == ISSUER) {
+        if (lane == 0) {  // ------------------------------ MMA issuer
+            const uint32_t id1 = idesc_n<ENC>(HBN);
+            const uint32_t id2 = idesc_n<HDC_ENC_BF16>(p.Cp);
+            int stage = 0, acc = 0;
+            uint32_t phase = 0, aphase = 0, a2ph = 0, b2ph = 0, d2ph = 0;
+            bool ab = false;
+            auto mma2 = [&](bool first) -> bool {
+                if (first && !mbar_wait(d2empty, d2ph ^ 1, abort_flag)) return false;
+                if (!mbar_wait(a2full, a2ph, abort_flag)) return false;
+                if (!mbar_wait(b2full, b2ph, abort_flag)) return false;
+                tc_fence_after();
+                const uint32_t a0 = su32(sA2), b0 = su32(sB2);
+#pragma unroll
+                for (int k = 0; k < 12; k++) {   // three atoms of four 16-element K steps
+                    const uint32_t off_a = (uint32_t)((k >> 2) * A2_ATOM) + 32u * (k & 3);
+                    const uint32_t off_b = (uint32_t)((k >> 2) * p.Cp * 128) + 32u * (k & 3);
+                    mma<HDC_ENC_BF16>(tmem + D2_COL, sdesc(a0 + off_a), sdesc(b0 + off_b), id2,
+                                      (first && k == 0) ? 0u : 1u);
+                }
+                mma_commit(a2empty);
+                mma_commit(b2empty);
+                a2ph ^= 1;
+                b2ph ^= 1;
+                return true;
+            };
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
+                for (int t = 0; t < p.nt && !ab; t++) {
+                    if (!mbar_wait(sempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
+                    tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)(acc * HBN);
+                    for (int kb = 0; kb < p.num_kb; kb++) {
+                        if (!mbar_wait(full(stage), phase, abort_flag)) { ab = true; break; }
+                        tc_fence_after();
+                        const uint32_t a0 = su32(sA + stage * HA_BYTES), b0 = su32(sB + stage * HB_BYTES);
+#pragma unroll
+                        for (int k = 0; k < BKB / 32; k++)
+                            mma<ENC>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), id1, (kb | k) != 0);
+                        mma_commit(empty(stage));
+                        if (++stage == FC_STAGES) { stage = 0; phase ^= 1; }
+                    }
+                    if (ab) break;
+                    mma_commit(sfull(acc));
+                    if (++acc == 2) { acc = 0; aphase ^= 1; }
+                    if (t > 0 && !mma2(t == 1)) { ab = true; break; }
+                }
+                if (ab) break;
+                if (!mma2(p.nt == 1)) { ab = true; break; }
+                mma_commit(d2full);
+                d2ph ^= 1;
+            }
+            mma_commit(done_bar);
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try(done_bar, 0) && gtimer() - t0 < 100000000ull) {}
+        }
+    } else {  // ------------------------------------------ epilogue warps 0 .. 11
+        const int q = warp & 3, g = warp >> 2;
+        const int r = q * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        uint8_t *a2row = sA2 + g * A2_ATOM + (r >> 3) * 1024 + (r & 7) * 128;   // atom g: this warpgroup's 64 dims
+        int acc = 0, qb = 0;
+        uint32_t aphase = 0, a2ph = 0, d2ph = 0, qph = 0;
+        bool ab = false;
+        int64_t it = 0;
+        for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++) {
+            const int64_t row = mt * BM + r;
+            const bool valid = row < p.N;
+            float qsum = 0.f;
+            for (int t = 0; t < p.nt; t++) {
+                const bool ok = mbar_wait(sfull(acc), aphase, abort_flag);
+                if (!__all_sync(0xffffffffu, ok)) { ab = true; break; }
+                tc_fence_after();
+                uint32_t v0[32], v1[32];
+                tmem_ld32(tmem + lane_base + (uint32_t)(acc * HBN + g * 64), v0);
+                tmem_ld32(tmem + lane_base + (uint32_t)(acc * HBN + g * 64 + 32), v1);
+                tc_fence_before();
+                mbar_arrive(sempty(acc));
+                if (++acc == 2) { acc = 0; aphase ^= 1; }
+                // BF16 of s * sb (zero past Dk), packed in pairs; squared norm of the BF16 values
+                const int col0 = t * HBN + g * 64;
+                uint32_t w[32];
+#pragma unroll
+                for (int i = 0; i < 32; i++) {
+                    const uint32_t *src = i < 16 ? v0 : v1;
+                    const int j = (i & 15) * 2;
+                    const int c = col0 + (i < 16 ? 0 : 32) + j;
+                    const float s0 = c < p.Dk ? __uint_as_float(src[j]) * (p.sb ? p.sb[c] : 1.f) : 0.f;
+                    const float s1 = c + 1 < p.Dk ? __uint_as_float(src[j + 1]) * (p.sb ? p.sb[c + 1] : 1.f) : 0.f;
+                    const __nv_bfloat16 b0 = __float2bfloat16_rn(s0), b1 = __float2bfloat16_rn(s1);
+                    const float g0 = __bfloat162float(b0), g1 = __bfloat162float(b1);
+                    qsum = fmaf(g0, g0, qsum);
+                    qsum = fmaf(g1, g1, qsum);
+                    w[i] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+                }
+                const bool oka = mbar_wait(a2empty, a2ph ^ 1, abort_flag);   // MMA2 of the previous tile done
+                if (!__all_sync(0xffffffffu, oka)) { ab = true; break; }
+#pragma unroll
+                for (int ch = 0; ch < 8; ch++) {   // 8 BF16 per 16-byte chunk, 128-byte swizzle
+                    *reinterpret_cast<uint4 *>(a2row + ((ch ^ (r & 7)) * 16)) =
+                        make_uint4(w[4 * ch], w[4 * ch + 1], w[4 * ch + 2], w[4 * ch + 3]);
+                }
+                fence_async_smem();
+                mbar_arrive(a2full);
+                a2ph ^= 1;
+            }
+            if (ab) break;
+            // the row's squared norm: the warpgroups' partial sums in order g = 0, 1, 2
+            float *sq = s_q + (size_t)qb * HEWG * BM;
+            sq[g * BM + r] = qsum;
+            mbar_arrive(qfull(qb));
+            const bool okq = mbar_wait(qfull(qb), qph, abort_flag);
+            if (!__all_sync(0xffffffffu, okq)) { ab = true; break; }
+            float qn = 0.f;
+#pragma unroll
+            for (int h = 0; h < HEWG; h++) qn += sq[h * BM + r];
+            if (++qb == 2) { qb = 0; qph ^= 1; }
+            const double qnorm = sqrt((double)qn);
+            const bool okd = mbar_wait(d2full, d2ph, abort_flag);
+            if (!__all_sync(0xffffffffu, okd)) { ab = true; break; }
+            tc_fence_after();
+            int best = -1;
+            double bs = 0.0;
+            for (int j = g; j * 32 < p.Cp; j += HEWG) {
+                uint32_t v[32];
+                tmem_ld32(tmem + lane_base + D2_COL + (uint32_t)(j * 32), v);
+#pragma unroll
+                for (int i = 0; i < 32; i++) {
+                    const int c = j * 32 + i;
+                    if (c < p.C) {
+                        const double den = qnorm * p.cnorm[c];
+                        const double sc = den == 0.0 ? 0.0 : (double)__uint_as_float(v[i]) / den;
+                        if (p.scores && valid) p.scores[row * p.C + c] = sc;
+                        if (best < 0 || sc > bs) { bs = sc; best = c; }   // ascending c: lowest on ties
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(d2empty);
+            d2ph ^= 1;
+            const uint32_t par = (uint32_t)(it & 1);
+            if (g > 0) {
+                if (!mbar_wait(merge_empty, par ^ 1, abort_flag)) { ab = true; break; }
+                s_val[(g - 1) * BM + r] = bs;
+                s_idx[(g - 1) * BM + r] = best;
+                mbar_arrive(merge_full);
+            } else {
+                if (!mbar_wait(merge_full, par, abort_flag)) { ab = true; break; }
+#pragma unroll
+                for (int h = 0; h < HEWG - 1; h++) {   // (score desc, class asc)
+                    const double v1 = s_val[h * BM + r];
+                    const int i1 = s_idx[h * BM + r];
+                    if (i1 >= 0 && (best < 0 || v1 > bs || (v1 == bs && i1 < best))) { bs = v1; best = i1; }
+                }
+                mbar_arrive(merge_empty);
+                if (valid) p.labels[row] = best < 0 ? 0 : best;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+template <int ENC>
+static cudaError_t launch_fcos_enc(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
+                                   const FCParams &p, unsigned grid, cudaStream_t st)
+{
+    auto k = tc_fcos_kernel<ENC>;
+    const size_t smem = fc_smem_bytes(p.Cp);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, H_THREADS, smem, st>>>(ma, mb, mv, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fcos_bf16(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
+                             const FCParams &p, unsigned grid, cudaStream_t st);
+cudaError_t launch_fcos_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
+                            const FCParams &p, unsigned grid, cudaStream_t st);
+
+}  // namespace tc
+}  // namespace hdc
