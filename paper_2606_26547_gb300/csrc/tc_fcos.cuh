@@ -238,35 +238,61 @@ __global__ void __launch_bounds__(H_THREADS, 1)
                 const bool ok = mbar_wait(sfull(acc), aphase, abort_flag);
                 if (!__all_sync(0xffffffffu, ok)) { ab = true; break; }
                 tc_fence_after();
-                uint32_t v0[32], v1[32];
-                tmem_ld32(tmem + lane_base + (uint32_t)(acc * HBN + g * 64), v0);
-                tmem_ld32(tmem + lane_base + (uint32_t)(acc * HBN + g * 64 + 32), v1);
-                tc_fence_before();
-                mbar_arrive(sempty(acc));
-                if (++acc == 2) { acc = 0; aphase ^= 1; }
-                // BF16 of s * sb (zero past Dk), packed in pairs; squared norm of the BF16 values
+                // two halves of the warpgroup's 64 columns: BF16 of s * sb (zero
+                // past Dk) into chunks 4h..4h+3 of atom g; squared norm of the BF16 values
                 const int col0 = t * HBN + g * 64;
-                uint32_t w[32];
+                bool okh = true;
+#pragma unroll 1
+                for (int h = 0; h < 2; h++) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + lane_base + (uint32_t)(acc * HBN + g * 64 + 32 * h), v);
+                    const int c0 = col0 + 32 * h;
+                    float sbv[32];
+                    if (c0 + 32 <= p.Dk) {
+                        if (p.sb) {
+                            const float4 *s4 = reinterpret_cast<const float4 *>(p.sb + c0);
 #pragma unroll
-                for (int i = 0; i < 32; i++) {
-                    const uint32_t *src = i < 16 ? v0 : v1;
-                    const int j = (i & 15) * 2;
-                    const int c = col0 + (i < 16 ? 0 : 32) + j;
-                    const float s0 = c < p.Dk ? __uint_as_float(src[j]) * (p.sb ? p.sb[c] : 1.f) : 0.f;
-                    const float s1 = c + 1 < p.Dk ? __uint_as_float(src[j + 1]) * (p.sb ? p.sb[c + 1] : 1.f) : 0.f;
-                    const __nv_bfloat16 b0 = __float2bfloat16_rn(s0), b1 = __float2bfloat16_rn(s1);
-                    const float g0 = __bfloat162float(b0), g1 = __bfloat162float(b1);
-                    qsum = fmaf(g0, g0, qsum);
-                    qsum = fmaf(g1, g1, qsum);
-                    w[i] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
-                }
-                const bool oka = mbar_wait(a2empty, a2ph ^ 1, abort_flag);   // MMA2 of the previous tile done
-                if (!__all_sync(0xffffffffu, oka)) { ab = true; break; }
+                            for (int i = 0; i < 8; i++) {
+                                const float4 x = s4[i];
+                                sbv[4 * i] = x.x; sbv[4 * i + 1] = x.y; sbv[4 * i + 2] = x.z; sbv[4 * i + 3] = x.w;
+                            }
+                        } else {
 #pragma unroll
-                for (int ch = 0; ch < 8; ch++) {   // 8 BF16 per 16-byte chunk, 128-byte swizzle
-                    *reinterpret_cast<uint4 *>(a2row + ((ch ^ (r & 7)) * 16)) =
-                        make_uint4(w[4 * ch], w[4 * ch + 1], w[4 * ch + 2], w[4 * ch + 3]);
+                            for (int i = 0; i < 32; i++) sbv[i] = 1.f;
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; i++) sbv[i] = c0 + i < p.Dk ? (p.sb ? p.sb[c0 + i] : 1.f) : 0.f;
+                    }
+                    uint32_t w[16];
+                    float qa = 0.f, qb2 = 0.f;   // two chains
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        const __nv_bfloat16 b0 = __float2bfloat16_rn(__uint_as_float(v[2 * i]) * sbv[2 * i]);
+                        const __nv_bfloat16 b1 = __float2bfloat16_rn(__uint_as_float(v[2 * i + 1]) * sbv[2 * i + 1]);
+                        const float g0 = __bfloat162float(b0), g1 = __bfloat162float(b1);
+                        qa = fmaf(g0, g0, qa);
+                        qb2 = fmaf(g1, g1, qb2);
+                        w[i] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+                    }
+                    qsum += qa + qb2;
+                    if (h == 1) {   // both halves are in registers: release the accumulator
+                        tc_fence_before();
+                        mbar_arrive(sempty(acc));
+                        if (++acc == 2) { acc = 0; aphase ^= 1; }
+                    } else {        // the MMA2 of the previous tile has read the value tile
+                        const bool oka = mbar_wait(a2empty, a2ph ^ 1, abort_flag);
+                        if (!__all_sync(0xffffffffu, oka)) { okh = false; }
+                    }
+                    if (!okh) break;
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {   // 8 BF16 per 16-byte chunk, 128-byte swizzle
+                        const int ch = 4 * h + i;
+                        *reinterpret_cast<uint4 *>(a2row + ((ch ^ (r & 7)) * 16)) =
+                            make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+                    }
                 }
+                if (!okh) { ab = true; break; }
                 fence_async_smem();
                 mbar_arrive(a2full);
                 a2ph ^= 1;
