@@ -24,19 +24,23 @@
 namespace hdc {
 namespace tc {
 
-constexpr int FC_STAGES = 3;
+// A/B stages: four when the class tile leaves room (C <= 16), else three.
+// At N = 192 a stage feeds about 0.2 us of MMA work, so the stages in
+// flight are what covers the L2 latency (36 % tensor activity measured with
+// three stages at C = 10).
 constexpr int FC_A2_BYTES = 3 * A2_ATOM;            // 128 rows x 192 BF16 in three 128-byte K atoms
 constexpr int FC_CMAX = 112;
 // full[S], empty[S], sfull[2], sempty[2], a2full, a2empty, b2full, b2empty,
 // d2full, d2empty, done, merge_full, merge_empty, qfull[2]
-constexpr int FC_NUM_BARS = 2 * FC_STAGES + 4 + 6 + 3 + 2;
+__host__ __device__ constexpr int fc_num_bars(int stages) { return 2 * stages + 4 + 6 + 3 + 2; }
 
-__host__ __device__ constexpr size_t fc_smem_bytes(int Cp)
+__host__ __device__ constexpr size_t fc_smem_bytes(int stages, int Cp)
 {
-    return 1024 + (size_t)FC_STAGES * H_STAGE_BYTES + FC_A2_BYTES + (size_t)3 * Cp * 128 + FC_NUM_BARS * 8 + 16 +
-           (size_t)2 * BM * 8 * (HEWG - 1) + (size_t)2 * HEWG * BM * 4;
+    return 1024 + (size_t)stages * H_STAGE_BYTES + FC_A2_BYTES + (size_t)3 * Cp * 128 + fc_num_bars(stages) * 8 +
+           16 + (size_t)2 * BM * 8 * (HEWG - 1) + (size_t)2 * HEWG * BM * 4;
 }
-static_assert(fc_smem_bytes(FC_CMAX) <= 232448, "shared memory of the fused float-query kernel");
+static_assert(fc_smem_bytes(3, FC_CMAX) <= 232448, "shared memory of the fused float-query kernel");
+static_assert(fc_smem_bytes(4, 16) <= 232448, "shared memory of the four-stage fused float-query kernel");
 
 struct FCParams {
     int64_t N;
@@ -48,7 +52,7 @@ struct FCParams {
     double *scores;          // optional N x C
 };
 
-template <int ENC>
+template <int ENC, int FC_STAGES>
 __global__ void __launch_bounds__(H_THREADS, 1)
     tc_fcos_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmV, const FCParams p)
@@ -60,6 +64,7 @@ __global__ void __launch_bounds__(H_THREADS, 1)
     uint8_t *sA2 = smem + FC_STAGES * H_STAGE_BYTES;
     uint8_t *sB2 = sA2 + FC_A2_BYTES;                               // 3 atoms x Cp rows x 128 B
     uint64_t *bars = reinterpret_cast<uint64_t *>(sB2 + 3 * p.Cp * 128);
+    constexpr int FC_NUM_BARS = fc_num_bars(FC_STAGES);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + FC_NUM_BARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     double *s_val = reinterpret_cast<double *>(tmem_slot + 4);       // warpgroups 1.. : per-row best score
@@ -359,16 +364,24 @@ __global__ void __launch_bounds__(H_THREADS, 1)
     }
 }
 
-template <int ENC>
-static cudaError_t launch_fcos_enc(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
-                                   const FCParams &p, unsigned grid, cudaStream_t st)
+template <int ENC, int STAGES>
+static cudaError_t launch_fcos_stages(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
+                                      const FCParams &p, unsigned grid, cudaStream_t st)
 {
-    auto k = tc_fcos_kernel<ENC>;
-    const size_t smem = fc_smem_bytes(p.Cp);
+    auto k = tc_fcos_kernel<ENC, STAGES>;
+    const size_t smem = fc_smem_bytes(STAGES, p.Cp);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, H_THREADS, smem, st>>>(ma, mb, mv, p);
     return cudaGetLastError();
+}
+
+template <int ENC>
+static cudaError_t launch_fcos_enc(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
+                                   const FCParams &p, unsigned grid, cudaStream_t st)
+{
+    if (fc_smem_bytes(4, p.Cp) <= 232448) return launch_fcos_stages<ENC, 4>(ma, mb, mv, p, grid, st);
+    return launch_fcos_stages<ENC, 3>(ma, mb, mv, p, grid, st);
 }
 
 cudaError_t launch_fcos_bf16(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
