@@ -317,15 +317,19 @@ __global__ void __launch_bounds__(H_THREADS, 1)
             const bool okd = mbar_wait(d2full, d2ph, abort_flag);
             if (!__all_sync(0xffffffffu, okd)) { ab = true; break; }
             tc_fence_after();
+            // warpgroup g scores classes [c0, c1), a third of them (FP64
+            // arithmetic is slow on this part: spread it over all warpgroups)
+            const int cper = (p.C + HEWG - 1) / HEWG;
+            const int c0 = g * cper, c1 = min(c0 + cper, p.C);
             int best = -1;
             double bs = 0.0;
-            for (int j = g; j * 32 < p.Cp; j += HEWG) {
+            for (int j = c0 / 32; j * 32 < c1; j++) {   // the 32-class chunks that hold [c0, c1)
                 uint32_t v[32];
                 tmem_ld32(tmem + lane_base + D2_COL + (uint32_t)(j * 32), v);
 #pragma unroll
                 for (int i = 0; i < 32; i++) {
                     const int c = j * 32 + i;
-                    if (c < p.C) {
+                    if (c >= c0 && c < c1) {
                         const double den = qnorm * p.cnorm[c];
                         const double sc = den == 0.0 ? 0.0 : (double)__uint_as_float(v[i]) / den;
                         if (p.scores && valid) p.scores[row * p.C + c] = sc;
