@@ -21,9 +21,11 @@
 // word loaded once for the four), a lane one word (32 dims): lane j
 // quantises feature f0 + j of each query, the warp broadcasts the levels by
 // shuffle, and each lane adds id ^ level rows into a bit-sliced counter per
-// query (carry-save adders over groups of 8 rows, then a ripple-carry add of
-// the weight-8 plane), then compares the counter against floor(F/2)
-// bit-sliced.
+// query (carry-save adders over groups of 16 rows with the planes of weight
+// 1, 2, 4 and 8 as carry-save state, then a ripple-carry add of the
+// weight-16 row into planes sized for F), then compares the counter against
+// floor(F/2) bit-sliced.  The next 32 features of each query are loaded
+// while the current ones are counted.
 #include <cmath>
 #include <cstring>
 
@@ -35,14 +37,15 @@ namespace {
 constexpr int LQ = 32;       // queries per block
 constexpr int LWC = 32;      // words per block (one per lane)
 constexpr int LWARPS = 8;
-constexpr int HPLANES = 10;  // counter planes of weight 8, 16, ...: F < 8 * 2^10
+// counter planes of weight 16, 32, ...: HP of them hold floor(F / 16) < 2^HP
+__host__ __device__ constexpr int hp_for(int F) { return F < 1024 ? 6 : 9; }
 
 __device__ __forceinline__ void csa(uint32_t &h, uint32_t &l, uint32_t a, uint32_t b, uint32_t c)
 {
-    // full adder per bit position: l = a ^ b ^ c (weight 1), h = majority (weight 2)
-    const uint32_t u = a ^ b;
-    h = (a & b) | (u & c);
-    l = u ^ c;
+    // full adder per bit position: l = a ^ b ^ c (weight 1), h = majority
+    // (weight 2); each a single three-input logic operation
+    h = (a & b) | (a & c) | (b & c);
+    l = a ^ b ^ c;
 }
 
 __device__ __forceinline__ int quant_level(float x, float lo, float scale, int L)
@@ -54,59 +57,76 @@ __device__ __forceinline__ int quant_level(float x, float lo, float scale, int L
     return 0;                    // t <= 0, or NaN
 }
 
-// Add 8 rows of weight 1 into the counter (ones, twos, fours, hp): a
-// carry-save tree to one row of weight 8, then a ripple-carry add of it.
-__device__ __forceinline__ void add8(uint32_t &ones, uint32_t &twos, uint32_t &fours, uint32_t (&hp)[HPLANES],
-                                     const uint32_t (&r)[8])
+// The counter of one query and lane: planes c1, c2, c4, c8 (weights 1, 2,
+// 4, 8) and hp[k] (weight 16 * 2^k); bit position i of the planes spells
+// the count of dim i in binary.
+template <int HP>
+struct Counter {
+    uint32_t c1, c2, c4, c8, hp[HP];
+};
+
+// Add 16 rows of weight 1: a carry-save tree (15 full adders) to one row of
+// weight 16, then a ripple-carry add of it into hp.
+template <int HP>
+__device__ __forceinline__ void add16(Counter<HP> &k, const uint32_t (&r)[16])
 {
-    uint32_t t2a, t2b, t4a, t4b, e8;
-    csa(t2a, ones, ones, r[0], r[1]);
-    csa(t2b, ones, ones, r[2], r[3]);
-    csa(t4a, twos, twos, t2a, t2b);
-    csa(t2a, ones, ones, r[4], r[5]);
-    csa(t2b, ones, ones, r[6], r[7]);
-    csa(t4b, twos, twos, t2a, t2b);
-    csa(e8, fours, fours, t4a, t4b);
-    uint32_t c = e8;
+    uint32_t a2, b2, a4, b4, a8, b8, e16;
+    csa(a2, k.c1, k.c1, r[0], r[1]);
+    csa(b2, k.c1, k.c1, r[2], r[3]);
+    csa(a4, k.c2, k.c2, a2, b2);
+    csa(a2, k.c1, k.c1, r[4], r[5]);
+    csa(b2, k.c1, k.c1, r[6], r[7]);
+    csa(b4, k.c2, k.c2, a2, b2);
+    csa(a8, k.c4, k.c4, a4, b4);
+    csa(a2, k.c1, k.c1, r[8], r[9]);
+    csa(b2, k.c1, k.c1, r[10], r[11]);
+    csa(a4, k.c2, k.c2, a2, b2);
+    csa(a2, k.c1, k.c1, r[12], r[13]);
+    csa(b2, k.c1, k.c1, r[14], r[15]);
+    csa(b4, k.c2, k.c2, a2, b2);
+    csa(b8, k.c4, k.c4, a4, b4);
+    csa(e16, k.c8, k.c8, a8, b8);
+    uint32_t c = e16;
 #pragma unroll
-    for (int k = 0; k < HPLANES; k++) {
-        const uint32_t t = hp[k] & c;
-        hp[k] ^= c;
+    for (int i = 0; i < HP; i++) {
+        const uint32_t t = k.hp[i] & c;
+        k.hp[i] ^= c;
         c = t;
     }
 }
 
 // Add one row of weight 1 (ripple carry through every plane).
-__device__ __forceinline__ void add1(uint32_t &ones, uint32_t &twos, uint32_t &fours, uint32_t (&hp)[HPLANES],
-                                     uint32_t c)
+template <int HP>
+__device__ __forceinline__ void add1(Counter<HP> &k, uint32_t c)
 {
-    uint32_t t = ones & c; ones ^= c; c = t;
-    t = twos & c; twos ^= c; c = t;
-    t = fours & c; fours ^= c; c = t;
+    uint32_t t = k.c1 & c; k.c1 ^= c; c = t;
+    t = k.c2 & c; k.c2 ^= c; c = t;
+    t = k.c4 & c; k.c4 ^= c; c = t;
+    t = k.c8 & c; k.c8 ^= c; c = t;
 #pragma unroll
-    for (int k = 0; k < HPLANES; k++) {
-        const uint32_t u = hp[k] & c;
-        hp[k] ^= c;
+    for (int i = 0; i < HP; i++) {
+        const uint32_t u = k.hp[i] & c;
+        k.hp[i] ^= c;
         c = u;
     }
 }
 
-// cnt > T per bit position, from the most significant plane down.
-__device__ __forceinline__ uint32_t greater(uint32_t ones, uint32_t twos, uint32_t fours,
-                                            const uint32_t (&hp)[HPLANES], uint32_t T)
+// count > T per bit position, from the most significant plane down.
+template <int HP>
+__device__ __forceinline__ uint32_t greater(const Counter<HP> &k, uint32_t T)
 {
     uint32_t gt = 0, eq = 0xffffffffu;
 #pragma unroll
-    for (int k = HPLANES - 1; k >= 0; k--) {
-        const uint32_t cp = hp[k];
-        if ((T >> (k + 3)) & 1u) eq &= cp;
+    for (int i = HP - 1; i >= 0; i--) {
+        const uint32_t cp = k.hp[i];
+        if ((T >> (i + 4)) & 1u) eq &= cp;
         else { gt |= eq & cp; eq &= ~cp; }
     }
-    const uint32_t pl[3] = {fours, twos, ones};
+    const uint32_t pl[4] = {k.c8, k.c4, k.c2, k.c1};
 #pragma unroll
-    for (int k = 2; k >= 0; k--) {
-        const uint32_t cp = pl[2 - k];
-        if ((T >> k) & 1u) eq &= cp;
+    for (int i = 0; i < 4; i++) {
+        const uint32_t cp = pl[i];
+        if ((T >> (3 - i)) & 1u) eq &= cp;
         else { gt |= eq & cp; eq &= ~cp; }
     }
     return gt;
@@ -116,6 +136,7 @@ __device__ __forceinline__ uint32_t greater(uint32_t ones, uint32_t twos, uint32
 // word loaded once for all of them).
 constexpr int QW = 4;
 
+template <int HP>
 __global__ void __launch_bounds__(LWARPS * 32) levelid_encode_kernel(const float *__restrict__ X, int64_t N, int F,
                                                                    int L, int W, float lo, float scale,
                                                                    const uint32_t *__restrict__ id,
@@ -141,34 +162,42 @@ __global__ void __launch_bounds__(LWARPS * 32) levelid_encode_kernel(const float
     for (int qb = warp * QW; qb < LQ; qb += LWARPS * QW) {
         const int64_t q0 = (int64_t)blockIdx.x * LQ + qb;
         if (q0 >= N) break;                       // warp-uniform
-        uint32_t ones[QW], twos[QW], fours[QW], hp[QW][HPLANES];
+        Counter<HP> cnt[QW];
 #pragma unroll
         for (int a = 0; a < QW; a++) {
-            ones[a] = twos[a] = fours[a] = 0;
+            cnt[a].c1 = cnt[a].c2 = cnt[a].c4 = cnt[a].c8 = 0;
 #pragma unroll
-            for (int k = 0; k < HPLANES; k++) hp[a][k] = 0;
+            for (int k = 0; k < HP; k++) cnt[a].hp[k] = 0;
         }
+        // feature f0 + lane of each query, loaded one 32-feature batch ahead
+        // so the quantisation does not wait on device memory
+        float xn[QW];
+#pragma unroll
+        for (int a = 0; a < QW; a++) xn[a] = (lane < F && q0 + a < N) ? X[(q0 + a) * (int64_t)F + lane] : 0.f;
         for (int f0 = 0; f0 < F; f0 += 32) {
             const int f = f0 + lane;
             int my[QW];   // level of feature f of each query (rows past N: level 0, not stored)
 #pragma unroll
-            for (int a = 0; a < QW; a++)
-                my[a] = (f < F && q0 + a < N) ? quant_level(X[(q0 + a) * (int64_t)F + f], lo, scale, L) : 0;
+            for (int a = 0; a < QW; a++) {
+                my[a] = (f < F && q0 + a < N) ? quant_level(xn[a], lo, scale, L) : 0;
+                const int fn = f + 32;
+                xn[a] = (fn < F && q0 + a < N) ? X[(q0 + a) * (int64_t)F + fn] : 0.f;
+            }
             const int nf = min(32, F - f0);
             int j = 0;
-            for (; j + 8 <= nf; j += 8) {
-                uint32_t idw[8];
+            for (; j + 16 <= nf; j += 16) {
+                uint32_t idw[16];
 #pragma unroll
-                for (int u = 0; u < 8; u++) idw[u] = sid[(f0 + j + u) * LWC + lane];
+                for (int u = 0; u < 16; u++) idw[u] = sid[(f0 + j + u) * LWC + lane];
 #pragma unroll
                 for (int a = 0; a < QW; a++) {
-                    uint32_t r[8];
+                    uint32_t r[16];
 #pragma unroll
-                    for (int u = 0; u < 8; u++) {
+                    for (int u = 0; u < 16; u++) {
                         const int l = __shfl_sync(0xffffffffu, my[a], j + u);
                         r[u] = idw[u] ^ slv[l * LWC + lane];
                     }
-                    add8(ones[a], twos[a], fours[a], hp[a], r);
+                    add16(cnt[a], r);
                 }
             }
             for (; j < nf; j++) {
@@ -176,14 +205,14 @@ __global__ void __launch_bounds__(LWARPS * 32) levelid_encode_kernel(const float
 #pragma unroll
                 for (int a = 0; a < QW; a++) {
                     const int l = __shfl_sync(0xffffffffu, my[a], j);
-                    add1(ones[a], twos[a], fours[a], hp[a], idw ^ slv[l * LWC + lane]);
+                    add1(cnt[a], idw ^ slv[l * LWC + lane]);
                 }
             }
         }
 #pragma unroll
         for (int a = 0; a < QW; a++)
             if (q0 + a < N && lane < nw)
-                H[(q0 + a) * (int64_t)W + w0 + lane] = greater(ones[a], twos[a], fours[a], hp[a], T);
+                H[(q0 + a) * (int64_t)W + w0 + lane] = greater(cnt[a], T);
     }
 }
 
@@ -309,12 +338,12 @@ extern "C" hdc_status hdc_levelid_encode(const float *X, int64_t N, const hdc_le
     if (N == 0) return HDC_OK;
     if (!X || !H) return HDC_ERR_INVALID_ARG;
     const size_t smem = encode_smem(m->F, m->L);
-    if (cudaFuncSetAttribute(levelid_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    // counter planes for floor(F / 16) (F < 8192: at most 9)
+    auto k = hp_for(m->F) == 6 ? levelid_encode_kernel<6> : levelid_encode_kernel<9>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return HDC_ERR_CUDA;
     const dim3 grid((unsigned)((N + LQ - 1) / LQ), (unsigned)((m->W + LWC - 1) / LWC));
     if (grid.y > 65535) return HDC_ERR_UNSUPPORTED;
-    levelid_encode_kernel<<<grid, LWARPS * 32, smem, (cudaStream_t)stream>>>(X, N, m->F, m->L, m->W, m->lo, m->scale,
-                                                                            m->id, m->level, H);
+    k<<<grid, LWARPS * 32, smem, (cudaStream_t)stream>>>(X, N, m->F, m->L, m->W, m->lo, m->scale, m->id, m->level, H);
     return cudaGetLastError() == cudaSuccess ? HDC_OK : HDC_ERR_CUDA;
 }
