@@ -135,6 +135,9 @@ __device__ __forceinline__ uint32_t greater(const Counter<HP> &k, uint32_t T)
 // A warp encodes QW queries at once (independent counter chains; each ID
 // word loaded once for all of them).
 constexpr int QW = 4;
+// per warp: the level-row offsets (level x LWC words) of its QW queries'
+// current 32 features, read back 16 at a time as broadcasts
+constexpr size_t LOFF_BYTES = (size_t)LWARPS * QW * 32 * 4;
 
 template <int HP>
 __global__ void __launch_bounds__(LWARPS * 32) levelid_encode_kernel(const float *__restrict__ X, int64_t N, int F,
@@ -147,6 +150,7 @@ __global__ void __launch_bounds__(LWARPS * 32) levelid_encode_kernel(const float
     uint32_t *sid = lsm;                          // F x LWC
     uint32_t *slv = lsm + (size_t)F * LWC;        // L x LWC
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int *soff = reinterpret_cast<int *>(lsm + (size_t)(F + L) * LWC) + warp * (QW * 32);   // [QW][32]
     const int w0 = blockIdx.y * LWC;
     const int nw = min(LWC, W - w0);
     for (int i = threadIdx.x; i < F * LWC; i += blockDim.x) {
@@ -176,13 +180,14 @@ __global__ void __launch_bounds__(LWARPS * 32) levelid_encode_kernel(const float
         for (int a = 0; a < QW; a++) xn[a] = (lane < F && q0 + a < N) ? X[(q0 + a) * (int64_t)F + lane] : 0.f;
         for (int f0 = 0; f0 < F; f0 += 32) {
             const int f = f0 + lane;
-            int my[QW];   // level of feature f of each query (rows past N: level 0, not stored)
+            // level-row offset of feature f of each query (rows past N: level 0, not stored)
 #pragma unroll
             for (int a = 0; a < QW; a++) {
-                my[a] = (f < F && q0 + a < N) ? quant_level(xn[a], lo, scale, L) : 0;
+                soff[a * 32 + lane] = (f < F && q0 + a < N) ? quant_level(xn[a], lo, scale, L) * LWC : 0;
                 const int fn = f + 32;
                 xn[a] = (fn < F && q0 + a < N) ? X[(q0 + a) * (int64_t)F + fn] : 0.f;
             }
+            __syncwarp();
             const int nf = min(32, F - f0);
             int j = 0;
             for (; j + 16 <= nf; j += 16) {
@@ -191,23 +196,25 @@ __global__ void __launch_bounds__(LWARPS * 32) levelid_encode_kernel(const float
                 for (int u = 0; u < 16; u++) idw[u] = sid[(f0 + j + u) * LWC + lane];
 #pragma unroll
                 for (int a = 0; a < QW; a++) {
+                    int o[16];   // four 16-byte broadcasts (j is a multiple of 16)
+                    const int4 *o4 = reinterpret_cast<const int4 *>(soff + a * 32 + j);
+#pragma unroll
+                    for (int v = 0; v < 4; v++) {
+                        const int4 t = o4[v];
+                        o[4 * v] = t.x; o[4 * v + 1] = t.y; o[4 * v + 2] = t.z; o[4 * v + 3] = t.w;
+                    }
                     uint32_t r[16];
 #pragma unroll
-                    for (int u = 0; u < 16; u++) {
-                        const int l = __shfl_sync(0xffffffffu, my[a], j + u);
-                        r[u] = idw[u] ^ slv[l * LWC + lane];
-                    }
+                    for (int u = 0; u < 16; u++) r[u] = idw[u] ^ slv[o[u] + lane];
                     add16(cnt[a], r);
                 }
             }
             for (; j < nf; j++) {
                 const uint32_t idw = sid[(f0 + j) * LWC + lane];
 #pragma unroll
-                for (int a = 0; a < QW; a++) {
-                    const int l = __shfl_sync(0xffffffffu, my[a], j);
-                    add1(cnt[a], idw ^ slv[l * LWC + lane]);
-                }
+                for (int a = 0; a < QW; a++) add1(cnt[a], idw ^ slv[soff[a * 32 + j] + lane]);
             }
+            __syncwarp();   // the batch's offsets are read before the next batch writes them
         }
 #pragma unroll
         for (int a = 0; a < QW; a++)
@@ -337,7 +344,7 @@ extern "C" hdc_status hdc_levelid_encode(const float *X, int64_t N, const hdc_le
         return HDC_ERR_INVALID_ARG;
     if (N == 0) return HDC_OK;
     if (!X || !H) return HDC_ERR_INVALID_ARG;
-    const size_t smem = encode_smem(m->F, m->L);
+    const size_t smem = encode_smem(m->F, m->L) + LOFF_BYTES;
     // counter planes for floor(F / 16) (F < 8192: at most 9)
     auto k = hp_for(m->F) == 6 ? levelid_encode_kernel<6> : levelid_encode_kernel<9>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
