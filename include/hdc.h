@@ -393,6 +393,17 @@ hdc_status hdc_classify_static(const float *X, int64_t N, const hdc_model *m,
  * stream itself reports an error).                                        */
 hdc_status hdc_stream_status(hdc_stream_t stream);
 
+/* Failure-detection self-test (not part of the method).  Enqueues one
+ * 32-thread block that waits on a shared-memory barrier nothing arrives
+ * on, through the same bounded-wait routine the tensor-core kernels use,
+ * with a limit of `limit_us` microseconds (1 .. 2,000,000).  The wait runs
+ * out, the block records a timeout in the device status word and returns:
+ * the next hdc_stream_status on `stream` returns HDC_ERR_TIMEOUT, and the
+ * context stays usable.  Nothing faults, traps or hangs.  Returns
+ * HDC_ERR_INVALID_ARG for a limit out of range (nothing enqueued),
+ * HDC_ERR_CUDA if the launch fails, else HDC_OK.                          */
+hdc_status hdc_selftest_wait(uint32_t limit_us, hdc_stream_t stream);
+
 /* Tracing hook (not part of the method): with start and stop set to
  * cudaEvent_t handles, every later hdc_encode / hdc_classify call made by
  * the calling host thread records `start` on its stream just before its

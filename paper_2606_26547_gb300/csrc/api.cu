@@ -489,6 +489,12 @@ hdc_status hdc_stream_status(hdc_stream_t stream)
     return HDC_OK;
 }
 
+hdc_status hdc_selftest_wait(uint32_t limit_us, hdc_stream_t stream)
+{
+    if (limit_us < 1 || limit_us > 2000000) return HDC_ERR_INVALID_ARG;
+    return cu(launch_wait_selftest((unsigned long long)limit_us * 1000ull, (cudaStream_t)stream));
+}
+
 void hdc_profile_events(void *start, void *stop)
 {
     t_prof_start = (cudaEvent_t)start;

@@ -129,6 +129,9 @@ cudaError_t quant_read_status(cudaStream_t st, int *status);
 
 // Reads and clears the tensor-core kernels' device status word.
 cudaError_t tc_read_status(cudaStream_t st, int *status);
+// One block waiting, bounded by limit_ns, on a barrier nothing arrives on
+// (the expiry is reported through tc_read_status).
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, cudaStream_t st);
 
 // Cosine of float query hypervectors on the tensor cores (k_tc_cos.cu):
 // q (N x ldS BF16), qn (N squared norms), cv (Cp x ldS BF16 class values,

@@ -71,6 +71,7 @@ _SIGS = {
     "hdc_levelid_encode": (_I32, [_P, _I64, _P, _P, _P]),
     "hdc_cluster": (_I32, [_P, _I64, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "hdc_stream_status": (_I32, [_P]),
+    "hdc_selftest_wait": (_I32, [ctypes.c_uint32, _P]),
     "hdc_profile_events": (None, [_P, _P]),
     "hdc_status_string": (ctypes.c_char_p, [_I32]),
 }
@@ -453,3 +454,10 @@ def levelid_encode(X: torch.Tensor, model: LevelIdModel, out: torch.Tensor | Non
 def stream_status(stream=None) -> int:
     """Synchronise the stream and return (and clear) the device status."""
     return int(load().hdc_stream_status(_stream(stream)))
+
+
+def selftest_wait(limit_us: int = 1000, stream=None) -> int:
+    """Enqueue the failure-detection self-test (a bounded wait that runs out
+    after limit_us microseconds); returns the launch status.  The expiry shows
+    up in the next stream_status()."""
+    return int(load().hdc_selftest_wait(int(limit_us), _stream(stream)))

@@ -82,6 +82,8 @@ def test_argument_checks_without_gpu(lib):
     assert lib.hdc_train_epoch(None, None, 5, 10, 2, 7, None, None, None, None, 0, None) == 1
     assert lib.hdc_classify(None, 5, ctypes.byref(m), None, None, None, None, 0, None) == 1
     assert lib.hdc_kept_dims(100, None) == 100
+    assert lib.hdc_selftest_wait(0, None) == 1           # wait limit out of range: nothing enqueued
+    assert lib.hdc_selftest_wait(2000001, None) == 1
 
 
 def test_static_scratch_size_matches_header(lib):
