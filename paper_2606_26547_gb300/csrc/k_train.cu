@@ -106,14 +106,25 @@ __global__ void __launch_bounds__(128) segment_count_kernel(const uint32_t *__re
             for (int j = 0; j < 8; j++) lanes[j] = 0;
             const int n = r1 - r0;
             int r = 0;
-            for (; r + 4 <= n; r += 4) {  // four independent row loads in flight
+            // sixteen independent gathered row loads in flight per thread: the
+            // pass is bound by how many bytes each SM has outstanding
+            for (; r + 16 <= n; r += 16) {
+                uint32_t w[16];
+#pragma unroll
+                for (int u = 0; u < 16; u++) w[u] = __ldg(H + (int64_t)s_rows[r + u] * W + word);
+#pragma unroll
+                for (int u = 0; u < 16; u++)
+#pragma unroll
+                    for (int j = 0; j < 8; j++) lanes[j] += (w[u] >> j) & 0x01010101u;  // dims j, j+8, j+16, j+24
+            }
+            for (; r + 4 <= n; r += 4) {
                 uint32_t w[4];
 #pragma unroll
                 for (int u = 0; u < 4; u++) w[u] = __ldg(H + (int64_t)s_rows[r + u] * W + word);
 #pragma unroll
                 for (int u = 0; u < 4; u++)
 #pragma unroll
-                    for (int j = 0; j < 8; j++) lanes[j] += (w[u] >> j) & 0x01010101u;  // dims j, j+8, j+16, j+24
+                    for (int j = 0; j < 8; j++) lanes[j] += (w[u] >> j) & 0x01010101u;
             }
             for (; r < n; r++) {
                 const uint32_t w = __ldg(H + (int64_t)s_rows[r] * W + word);
