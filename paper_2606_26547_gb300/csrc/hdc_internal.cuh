@@ -129,6 +129,12 @@ cudaError_t quant_read_status(cudaStream_t st, int *status);
 
 // Reads and clears the tensor-core kernels' device status word.
 cudaError_t tc_read_status(cudaStream_t st, int *status);
+// Hamming arg-min of packed rows on the tensor cores (17 <= C <= 256 binary
+// classes, W a multiple of 4 up to 4096): kept dims s0 + k*stride < min(e0, D).
+bool hamming_packed_ok(int C, int W);
+cudaError_t launch_hamming_packed(const uint32_t *Q, int64_t N, const uint32_t *cls, int C, int W, int64_t D,
+                                  int64_t s0, int64_t e0, int64_t stride, int32_t *labels, int32_t *dists,
+                                  cudaStream_t st);
 // One block waiting, bounded by limit_ns, on a barrier nothing arrives on
 // (the expiry is reported through tc_read_status).
 cudaError_t launch_wait_selftest(unsigned long long limit_ns, cudaStream_t st);

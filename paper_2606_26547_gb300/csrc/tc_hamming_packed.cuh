@@ -1,0 +1,265 @@
+// Hamming arg-min of packed binary hypervectors on the tensor cores
+// (Sec. 4.1 Hamming distance and arg-min primitives; 17 <= C <= 256 binary
+// classes).
+//
+// For +-1 vectors over the kept dims K, Hamming(q, c) = (|K| - q.c) / 2 and
+// q.c is an exact integer in FP32.  The packed words of a 256-dim tile are
+// expanded in shared memory into E4M3 bytes: +1.0 (0x38) for bit 0, -1.0
+// (0xB8) for bit 1, 0 for a dim outside K (perforated away, or past D).  A
+// nibble of four dims becomes four bytes through one multiply that spreads
+// its bits to the byte boundaries:
+//   ((nib * 0x00204081) & 0x01010101) * 0x80 + 0x38383838
+// (the four shifted copies of the nibble occupy disjoint bits, so there are
+// no carries).  Then
+//   D2 += Qtile . Ctile^T     (M 128 queries, N = Cp, K = 256 bytes)
+// accumulates over all tiles in tensor memory, and the epilogue takes the
+// arg-min of (|K| - dot) / 2 with the lowest class on ties.
+//
+// Roles (9 warps): warps 0-7 expand the query tile (thread = row x 128-dim
+// half) and the class tile, double buffered, and afterwards read D2 (two
+// warpgroups, alternate 32-class chunks, merged by (distance, class));
+// warp 8 issues the MMAs.  Every wait is bounded as in the encoder.
+#pragma once
+#include "tc_hamming.cuh"
+
+namespace hdc {
+namespace tc {
+
+constexpr int HP_TD = 256;                     // dims per tile (two 128-byte K atoms)
+constexpr int HP_EXP = 256;                    // expanding threads (warps 0-7)
+constexpr int HP_THREADS = HP_EXP + 32;
+constexpr int HP_CMAX = 256;
+constexpr int HP_A_BYTES = 2 * BM * 128;       // query tile: two atoms of 128 rows x 128 bytes
+constexpr int HP_MAX_W = 4096;                 // words of a packed row (D <= 131072)
+// full[2], empty[2], d2full, d2empty, merge_full, merge_empty, done
+constexpr int HP_NUM_BARS = 9;
+
+__host__ __device__ constexpr size_t hp_smem_bytes(int Cp, int W)
+{
+    return 1024 + (size_t)2 * HP_A_BYTES + (size_t)2 * 2 * Cp * 128 + (size_t)(W + 2) * 4 + HP_NUM_BARS * 8 + 16 +
+           (size_t)2 * BM * 4;
+}
+static_assert(hp_smem_bytes(HP_CMAX, HP_MAX_W) <= 232448, "shared memory of the packed tensor-core Hamming kernel");
+
+struct HPParams {
+    const uint32_t *Q;       // N x W packed rows
+    const uint32_t *cls;     // C x W packed class hypervectors
+    int64_t N;
+    int W, C, Cp, nt;        // nt: 256-dim tiles = ceil(W / 8)
+    int64_t D, s0, e0, stride;   // dims of the rows; kept dims s0 + k*stride < e0 (stride 1, [0, D) if none)
+    int32_t *labels, *dists;
+};
+
+// Four dims of a word (bits 4k..4k+3) as four E4M3 bytes, zero where the
+// mask nibble is 0.
+__device__ __forceinline__ uint32_t expand_nibble(uint32_t nib, uint32_t mnib)
+{
+    const uint32_t v = ((nib * 0x00204081u) & 0x01010101u) * 0x80u + 0x38383838u;
+    const uint32_t m = ((mnib * 0x00204081u) & 0x01010101u) * 0xFFu;
+    return v & m;
+}
+
+// 128 dims (four words) of one row into its 128-byte row of a K atom
+// (128-byte swizzle: 16-byte chunk ch of row r at ((ch ^ (r & 7)) * 16)).
+__device__ __forceinline__ void expand_row(uint8_t *atom, int r, const uint4 w, const uint4 m)
+{
+    uint8_t *row = atom + (r >> 3) * 1024 + (r & 7) * 128;
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w}, ms[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        uint32_t b[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) b[k] = expand_nibble((ws[i] >> (4 * k)) & 0xFu, (ms[i] >> (4 * k)) & 0xFu);
+        *reinterpret_cast<uint4 *>(row + (((2 * i) ^ (r & 7)) * 16)) = make_uint4(b[0], b[1], b[2], b[3]);
+        *reinterpret_cast<uint4 *>(row + (((2 * i + 1) ^ (r & 7)) * 16)) = make_uint4(b[4], b[5], b[6], b[7]);
+    }
+}
+
+__global__ void __launch_bounds__(HP_THREADS, 1) tc_hamming_packed_kernel(const HPParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;                                          // 2 buffers x HP_A_BYTES
+    uint8_t *sB = sA + 2 * HP_A_BYTES;                           // 2 buffers x two atoms of Cp x 128 bytes
+    const int b_bytes = 2 * p.Cp * 128;
+    uint32_t *smask = reinterpret_cast<uint32_t *>(sB + 2 * b_bytes);   // W mask words
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smask + ((p.W + 1) & ~1));
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + HP_NUM_BARS);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    int *s_kept = reinterpret_cast<int *>(tmem_slot + 2);
+    int32_t *s_val = reinterpret_cast<int32_t *>(tmem_slot + 4);   // warpgroup 1: per-row minimum
+    int32_t *s_idx = s_val + BM;                                   // and its class
+    auto full = [&](int b) { return su32(bars + b); };
+    auto empty = [&](int b) { return su32(bars + 2 + b); };
+    const uint32_t d2full = su32(bars + 4), d2empty = su32(bars + 5);
+    const uint32_t merge_full = su32(bars + 6), merge_empty = su32(bars + 7), done_bar = su32(bars + 8);
+    constexpr int ISSUER = HP_EXP / 32;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t num_m_tiles = (p.N + BM - 1) / BM;
+
+    if (tid == 0) {
+        for (int b = 0; b < 2; b++) {
+            mbar_init(full(b), HP_EXP);
+            mbar_init(empty(b), 1);
+        }
+        mbar_init(d2full, 1);
+        mbar_init(d2empty, HP_EXP);
+        mbar_init(merge_full, BM);
+        mbar_init(merge_empty, BM);
+        mbar_init(done_bar, 1);
+        *abort_flag = 0;
+        *s_kept = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // kept-dim mask of every word (dims past D are never kept), and |K|
+    for (int w = tid; w < p.W; w += blockDim.x) {
+        uint32_t m = 0;
+        const int64_t base = (int64_t)w * 32;
+        const int64_t lo = max(p.s0, base), hi = min(min(p.e0, p.D), base + 32);
+        if (lo < hi) {
+            if (p.stride == 1) {
+                const int a = (int)(lo - base), b = (int)(hi - base);
+                m = (b == 32 ? 0xffffffffu : ((1u << b) - 1u)) & ~((1u << a) - 1u);
+            } else {
+                const int64_t r0 = (lo - p.s0) % p.stride;
+                for (int64_t d = r0 ? lo + (p.stride - r0) : lo; d < hi; d += p.stride) m |= 1u << (d - base);
+            }
+        }
+        smask[w] = m;
+        if (m) atomicAdd(s_kept, __popc(m));
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int kept = *s_kept;
+
+    if (warp == ISSUER) {
+        if (lane == 0) {  // ------------------------------ MMA issuer
+            const uint32_t id = idesc_n<HDC_ENC_FP8_E4M3>(p.Cp);
+            int buf = 0;
+            uint32_t ph = 0, d2ph = 0;
+            bool ab = false;
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
+                if (!mbar_wait(d2empty, d2ph ^ 1, abort_flag)) { ab = true; break; }
+                for (int t = 0; t < p.nt; t++) {
+                    if (!mbar_wait(full(buf), ph, abort_flag)) { ab = true; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = su32(sA + buf * HP_A_BYTES), b0 = su32(sB + buf * b_bytes);
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {   // two atoms of four 32-byte K steps
+                        const uint32_t oa = (uint32_t)((k >> 2) * (BM * 128)) + 32u * (k & 3);
+                        const uint32_t ob = (uint32_t)((k >> 2) * (p.Cp * 128)) + 32u * (k & 3);
+                        mma<HDC_ENC_FP8_E4M3>(tmem, sdesc(a0 + oa), sdesc(b0 + ob), id, (t | k) != 0);
+                    }
+                    mma_commit(empty(buf));
+                    if (++buf == 2) { buf = 0; ph ^= 1; }
+                }
+                if (ab) break;
+                mma_commit(d2full);
+                d2ph ^= 1;
+            }
+            mma_commit(done_bar);
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try(done_bar, 0) && gtimer() - t0 < 100000000ull) {}
+        }
+    } else if (warp < ISSUER) {  // ------------------------ expansion and epilogue warps 0 .. 7
+        const int r = tid & (BM - 1), half = tid >> 7;   // query row of the tile, 128-dim half (atom)
+        const int g = half;                               // epilogue warpgroup
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        int buf = 0;
+        uint32_t ph = 0, d2ph = 0;
+        bool ab = false;
+        int64_t it = 0;
+        for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++) {
+            const int64_t row = mt * BM + r;
+            const bool valid = row < p.N;
+            const uint32_t *qrow = p.Q + (valid ? row : 0) * (int64_t)p.W;
+            // words of the next tile, loaded one tile ahead
+            uint4 qn = make_uint4(0, 0, 0, 0);
+            {
+                const int w0 = half * 4;
+                if (valid && w0 < p.W) qn = *reinterpret_cast<const uint4 *>(qrow + w0);
+            }
+            for (int t = 0; t < p.nt; t++) {
+                const uint4 qw = qn;
+                const int w0 = t * 8 + half * 4;                  // this thread's four words
+                const int wn = w0 + 8;
+                if (t + 1 < p.nt) qn = (valid && wn < p.W) ? *reinterpret_cast<const uint4 *>(qrow + wn)
+                                                          : make_uint4(0, 0, 0, 0);
+                const bool oke = mbar_wait(empty(buf), ph ^ 1, abort_flag);   // the MMAs of this buffer's last use
+                if (!__all_sync(0xffffffffu, oke)) { ab = true; break; }
+                const uint4 mq = w0 < p.W ? *reinterpret_cast<const uint4 *>(smask + w0) : make_uint4(0, 0, 0, 0);
+                expand_row(sA + buf * HP_A_BYTES + half * (BM * 128), r, qw, mq);
+                // class rows: items (class c, half h) spread over the 256 threads
+                uint8_t *bt = sB + buf * b_bytes;
+                for (int i = tid; i < 2 * p.Cp; i += HP_EXP) {
+                    const int c = i >> 1, h = i & 1;
+                    const int wc = t * 8 + h * 4;
+                    uint4 cw = make_uint4(0, 0, 0, 0), mc = make_uint4(0, 0, 0, 0);
+                    if (c < p.C && wc < p.W) {
+                        cw = *reinterpret_cast<const uint4 *>(p.cls + (int64_t)c * p.W + wc);
+                        mc = *reinterpret_cast<const uint4 *>(smask + wc);
+                    }
+                    expand_row(bt + h * (p.Cp * 128), c, cw, mc);
+                }
+                fence_async_smem();
+                mbar_arrive(full(buf));
+                if (++buf == 2) { buf = 0; ph ^= 1; }
+            }
+            if (ab) break;
+            // distances: warpgroup g reads the 32-class chunks j = g, g + 2, ...
+            const bool okd = mbar_wait(d2full, d2ph, abort_flag);
+            if (!__all_sync(0xffffffffu, okd)) { ab = true; break; }
+            tc_fence_after();
+            int best = 0x7fffffff, bv = 0x7fffffff;
+            for (int j = g; j * 32 < p.Cp; j += 2) {
+                uint32_t v[32];
+                tmem_ld32(tmem + lane_base + (uint32_t)(j * 32), v);
+#pragma unroll
+                for (int i = 0; i < 32; i++) {
+                    const int c = j * 32 + i;
+                    if (c < p.C) {
+                        const int dist = (kept - (int)__uint_as_float(v[i])) / 2;
+                        if (p.dists && valid) p.dists[row * p.C + c] = dist;
+                        if (dist < bv) { bv = dist; best = c; }   // ascending c: lowest on ties
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(d2empty);
+            d2ph ^= 1;
+            const uint32_t par = (uint32_t)(it & 1);
+            if (g > 0) {
+                if (!mbar_wait(merge_empty, par ^ 1, abort_flag)) { ab = true; break; }
+                s_val[r] = bv;
+                s_idx[r] = best;
+                mbar_arrive(merge_full);
+            } else {
+                if (!mbar_wait(merge_full, par, abort_flag)) { ab = true; break; }
+                const int v1 = s_val[r], i1 = s_idx[r];
+                if (v1 < bv || (v1 == bv && i1 < best)) { bv = v1; best = i1; }   // (distance, class)
+                mbar_arrive(merge_empty);
+                if (valid) p.labels[row] = best;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+    }
+}
+
+}  // namespace tc
+}  // namespace hdc

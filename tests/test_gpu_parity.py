@@ -150,6 +150,54 @@ def test_hamming_argmin_bit_exact(hdc, N, C, D, perf):
     assert np.array_equal(labels.cpu().numpy(), orc.argmin(od))
 
 
+@pytest.mark.parametrize("C", [17, 33, 64, 100, 128, 200, 256, 257])
+@pytest.mark.parametrize("D,perf", [(1000, None), (4096, (0.1, 0.9, 3)), (96, None), (2050, (0.0, 1.0, 2))])
+def test_hamming_argmin_tensor_core_range(hdc, C, D, perf):
+    """33..256 binary classes run as a tensor-core product of the rows
+    expanded to +-1 (17..32 and 257 on the popcount paths): distances and
+    labels equal the oracle's per-dim definition, with ties across the two
+    epilogue warpgroups' class chunks and exact matches."""
+    rng = np.random.default_rng(C * 31 + D)
+    N = 300
+    q = rng.integers(0, 2, (N, D)).astype(np.uint8)
+    c = rng.integers(0, 2, (C, D)).astype(np.uint8)
+    c[C - 1] = c[0]                      # ties: classes in different 32-class chunks
+    c[C // 2] = c[1]
+    q[:5] = c[:5]                        # distance 0
+    cfg = hdc.ApproxConfig(perf_start=perf[0], perf_end=perf[1], perf_stride=perf[2]) if perf else None
+    labels, dd = hdc.hamming_argmin(T(pack(q).view(np.int32)), T(pack(c).view(np.int32)), D, cfg, dists=True)
+    dims = orc.kept_dims(D, *perf) if perf else orc.kept_dims(D)
+    od = orc.hamming(orc.gather_cols(q, dims), orc.gather_cols(c, dims))
+    assert np.array_equal(dd.cpu().numpy().astype(np.int64), od)
+    assert np.array_equal(labels.cpu().numpy(), orc.argmin(od))
+
+
+def test_hamming_argmin_tensor_core_many_tiles(hdc):
+    """More 128-row tiles than SMs (the persistent loop), labels only."""
+    rng = np.random.default_rng(11)
+    N, C, D = 20000, 40, 512
+    c = rng.integers(0, 2, (C, D)).astype(np.uint8)
+    y = rng.integers(0, C, N)
+    q = c[y] ^ (rng.random((N, D)) < 0.3).astype(np.uint8)
+    labels = hdc.hamming_argmin(T(pack(q).view(np.int32)), T(pack(c).view(np.int32)), D)
+    od = orc.hamming(q, c)
+    assert np.array_equal(labels.cpu().numpy(), orc.argmin(od))
+
+
+def test_train_many_classes_bit_exact(hdc):
+    """Retraining with 100 classes: its predictions run on the tensor-core
+    Hamming kernel; accumulators and update counts equal the oracle's."""
+    rng = np.random.default_rng(100)
+    N, D, C = 1500, 2048, 100
+    protos = rng.integers(0, 2, (C, D)).astype(np.uint8)
+    y = rng.integers(0, C, N).astype(np.int32)
+    bits = protos[y] ^ (rng.random((N, D)) < 0.45).astype(np.uint8)
+    acc, cls, ups = hdc.train(T(pack(bits).view(np.int32)), T(y), D, C, epochs=3)
+    oacc, oups = orc.train(bits, y, C, 3)
+    assert np.array_equal(acc.cpu().numpy().astype(np.int64), oacc)
+    assert ups == oups
+
+
 def test_hamming_all_ties(hdc):
     q = np.zeros((40, 64), np.uint8)
     c = np.ones((5, 64), np.uint8)
