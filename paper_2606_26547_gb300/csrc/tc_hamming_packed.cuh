@@ -59,17 +59,30 @@ __device__ __forceinline__ uint32_t expand_nibble(uint32_t nib, uint32_t mnib)
     return v & m;
 }
 
+// Without a mask (every dim kept).
+__device__ __forceinline__ uint32_t expand_nibble_all(uint32_t nib)
+{
+    return ((nib * 0x00204081u) & 0x01010101u) * 0x80u + 0x38383838u;
+}
+
 // 128 dims (four words) of one row into its 128-byte row of a K atom
 // (128-byte swizzle: 16-byte chunk ch of row r at ((ch ^ (r & 7)) * 16)).
+// Four all-ones mask words (no perforation, not the tail) skip the mask.
 __device__ __forceinline__ void expand_row(uint8_t *atom, int r, const uint4 w, const uint4 m)
 {
     uint8_t *row = atom + (r >> 3) * 1024 + (r & 7) * 128;
     const uint32_t ws[4] = {w.x, w.y, w.z, w.w}, ms[4] = {m.x, m.y, m.z, m.w};
+    const bool all = (m.x & m.y & m.z & m.w) == 0xffffffffu;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         uint32_t b[8];
+        if (all) {
 #pragma unroll
-        for (int k = 0; k < 8; k++) b[k] = expand_nibble((ws[i] >> (4 * k)) & 0xFu, (ms[i] >> (4 * k)) & 0xFu);
+            for (int k = 0; k < 8; k++) b[k] = expand_nibble_all((ws[i] >> (4 * k)) & 0xFu);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; k++) b[k] = expand_nibble((ws[i] >> (4 * k)) & 0xFu, (ms[i] >> (4 * k)) & 0xFu);
+        }
         *reinterpret_cast<uint4 *>(row + (((2 * i) ^ (r & 7)) * 16)) = make_uint4(b[0], b[1], b[2], b[3]);
         *reinterpret_cast<uint4 *>(row + (((2 * i + 1) ^ (r & 7)) * 16)) = make_uint4(b[4], b[5], b[6], b[7]);
     }
