@@ -161,5 +161,7 @@ cudaError_t launch_tc_cosine(const CosArgs &a, cudaStream_t st);
 cudaError_t launch_tc_fcos(const TcArgs &a, const uint16_t *cv, int ldS, const double *cnorm, double *scores,
                           cudaStream_t st);
 cudaError_t tc_cosine_read_status(cudaStream_t st, int *status);
+// Status word of the auxiliary tensor-core kernels (packed Hamming, wait self-test).
+cudaError_t tc_aux_read_status(cudaStream_t st, int *status);
 
 }  // namespace hdc

@@ -203,11 +203,12 @@ cudaError_t launch_tc_fcos(const TcArgs &a, const uint16_t *cv, int ldS, const d
 
 cudaError_t tc_read_status(cudaStream_t st, int *status)
 {
-    int a = 0, b = 0, c = 0;
+    int a = 0, b = 0, c = 0, x = 0;
     cudaError_t e = tc::status_bf16(st, &a);
     if (e == cudaSuccess) e = tc::status_fp8(st, &b);
     if (e == cudaSuccess) e = tc_cosine_read_status(st, &c);
-    *status = a ? a : b ? b : c;
+    if (e == cudaSuccess) e = tc_aux_read_status(st, &x);
+    *status = a ? a : b ? b : c ? c : x;
     return e;
 }
 

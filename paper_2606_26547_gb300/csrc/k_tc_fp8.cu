@@ -1,6 +1,5 @@
 // Tensor-core encoder instances for FP8 E4M3 operands (tcgen05.mma kind::f8f6f4).
 #include "tc_fcos.cuh"
-#include "tc_hamming_packed.cuh"
 
 namespace hdc {
 namespace tc {
@@ -26,67 +25,5 @@ cudaError_t launch_fcos_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const 
     return launch_fcos_enc<HDC_ENC_FP8_E4M3>(ma, mb, mv, p, grid, st);
 }
 
-// Failure-detection self-test: thread 0 waits, through the bounded-wait
-// routine of the tensor-core kernels, on an mbarrier that nothing arrives
-// on; the expiry records status 1 (timeout) in this unit's status word.
-__global__ void __launch_bounds__(32, 1) wait_selftest_kernel(unsigned long long limit_ns)
-{
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ int abort_flag;
-    if (threadIdx.x == 0) {
-        mbar_init(su32(&bar), 1);
-        abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-    if (threadIdx.x == 0) (void)mbar_wait(su32(&bar), 0, &abort_flag, limit_ns);
-}
-
 }  // namespace tc
-
-bool hamming_packed_ok(int C, int W)
-{
-    return C > 16 && C <= tc::HP_CMAX && W > 0 && W <= tc::HP_MAX_W && W % 4 == 0;
-}
-
-cudaError_t launch_hamming_packed(const uint32_t *Q, int64_t N, const uint32_t *cls, int C, int W, int64_t D,
-                                  int64_t s0, int64_t e0, int64_t stride, int32_t *labels, int32_t *dists,
-                                  cudaStream_t st)
-{
-    if (N <= 0) return cudaSuccess;
-    if (!hamming_packed_ok(C, W) || stride < 1) return cudaErrorNotSupported;
-    tc::HPParams p;
-    p.Q = Q;
-    p.cls = cls;
-    p.N = N;
-    p.W = W;
-    p.C = C;
-    p.Cp = (C + 15) / 16 * 16;
-    p.nt = (W + 7) / 8;
-    p.D = D;
-    p.s0 = s0;
-    p.e0 = e0;
-    p.stride = stride;
-    p.labels = labels;
-    p.dists = dists;
-    const size_t smem = tc::hp_smem_bytes(p.Cp, W);
-    cudaError_t e = cudaFuncSetAttribute(tc::tc_hamming_packed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                     cudaSuccess || sms <= 0)
-        sms = 152;
-    const int64_t tiles = (N + tc::BM - 1) / tc::BM;
-    const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
-    tc::tc_hamming_packed_kernel<<<grid, tc::HP_THREADS, smem, st>>>(p);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_wait_selftest(unsigned long long limit_ns, cudaStream_t st)
-{
-    tc::wait_selftest_kernel<<<1, 32, 0, st>>>(limit_ns);
-    return cudaGetLastError();
-}
-
 }  // namespace hdc
