@@ -78,13 +78,13 @@ struct ModelLayout {
     size_t bq, bscale, planes, csum, cnorm, csign, total;
 };
 
-// Binary classes with 17 <= C <= 112 also keep E4M3 +-1 class bytes for the
+// Binary classes with 33 <= C <= 112 also keep E4M3 +-1 class bytes for the
 // tensor-core Hamming distances: Cp rows (C rounded to 16) of one byte per
 // kept dim, padded to whole 192-dim tiles plus the 64 bytes the last tile's
 // second 128-byte box reaches past them.
 inline bool tc_hamming_classes(int bits, int C, uint32_t flags)
 {
-    return bits == 1 && C > 16 && C <= 112 && !(flags & HDC_FLAG_FLOAT_QUERY);
+    return bits == 1 && C > 32 && C <= 112 && !(flags & HDC_FLAG_FLOAT_QUERY);
 }
 inline int ldcs_for(int Dk) { return (Dk + 191) / 192 * 192 + 64; }
 

@@ -263,6 +263,115 @@ __global__ void __launch_bounds__(QWARPS * 32) quant_rows_bulk_kernel(const floa
     }
 }
 
+// Streaming variant for rows that are not 16-byte aligned (F % 4 != 0, an
+// odd row stride or base): the 16-byte aligned span around each row (at
+// most 12 bytes before and after it, inside the same tensor) is copied by
+// cp.async.bulk into the slot, and the row is read from its offset there.
+// A row whose span would reach outside [first row, end of the last row) of
+// this launch -- at most the first and the last -- is read from device
+// memory directly (its slot's barrier gets a plain arrival).  The
+// arithmetic per element is that of quant_rows_kernel.
+__host__ __device__ inline uint32_t span_slot_bytes(int F) { return (((uint32_t)F * 4u + 15u) & ~15u) + 16u; }
+
+template <int ENC>
+__global__ void __launch_bounds__(QWARPS * 32) quant_rows_span_kernel(const float *__restrict__ src, int64_t lds,
+                                                                      int64_t row_off, int64_t row_step,
+                                                                      int64_t nrows, int F, void *__restrict__ dst,
+                                                                      int ldd, float *__restrict__ scale)
+{
+    extern __shared__ __align__(128) uint8_t qsm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t slot_bytes = span_slot_bytes(F);
+    uint8_t *ring = qsm + (size_t)wib * QSLOTS * slot_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(qsm + (size_t)QWARPS * QSLOTS * slot_bytes) + wib * QSLOTS;
+    const int64_t gw = (int64_t)blockIdx.x * QWARPS + wib, nw = (int64_t)gridDim.x * QWARPS;
+    const int64_t my_rows = gw < nrows ? (nrows - 1 - gw) / nw + 1 : 0;
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(src + row_off * lds);
+    const uintptr_t hi = reinterpret_cast<uintptr_t>(src + (row_off + (nrows - 1) * row_step) * lds + F);
+    auto bar = [&](int s) { return (uint32_t)__cvta_generic_to_shared(bars + s); };
+    auto rowptr = [&](int64_t i) { return src + (row_off + (gw + i * nw) * row_step) * lds; };
+    auto span_start = [&](const float *g) { return reinterpret_cast<uintptr_t>(g) & ~(uintptr_t)15; };
+    auto span_bytes = [&](const float *g) {
+        return (uint32_t)(((reinterpret_cast<uintptr_t>(g) & 15u) + (uint32_t)F * 4u + 15u) & ~15u);
+    };
+    auto direct = [&](const float *g) { return span_start(g) < lo || span_start(g) + span_bytes(g) > hi; };
+    auto issue = [&](int64_t i) {  // lane 0: this warp's i-th row into slot i % QSLOTS
+        const int s = (int)(i % QSLOTS);
+        const float *g = rowptr(i);
+        if (direct(g)) {
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(s)) : "memory");
+            return;
+        }
+        const uint32_t nb = span_bytes(g);
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(ring + (size_t)s * slot_bytes);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(s)), "r"(nb) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+                     "l"(span_start(g)), "r"(nb), "r"(bar(s))
+                     : "memory");
+    };
+    if (lane == 0) {
+        for (int s = 0; s < QSLOTS; s++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(s)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int64_t i = 0; i < my_rows && i < QSLOTS; i++) issue(i);
+    }
+    __syncwarp();
+    for (int64_t i = 0; i < my_rows; i++) {
+        const int s = (int)(i % QSLOTS);
+        const uint32_t parity = (uint32_t)((i / QSLOTS) & 1);
+        bool ok = qbar_try(bar(s), parity);
+        if (!ok) {
+            const unsigned long long t0 = qtimer();
+            while (!(ok = qbar_try(bar(s), parity)) && qtimer() - t0 < QTIMEOUT_NS) {}
+        }
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) {
+                atomicCAS(&g_quant_status, 0, 1);
+                // let this warp's copies in flight land before the block exits
+                const int64_t issued = i + QSLOTS < my_rows ? i + QSLOTS : my_rows;
+                for (int64_t j = i; j < issued; j++) {
+                    const unsigned long long t0 = qtimer();
+                    while (!qbar_try(bar((int)(j % QSLOTS)), (uint32_t)((j / QSLOTS) & 1)) &&
+                           qtimer() - t0 < 100000000ull) {}
+                }
+            }
+            break;
+        }
+        const float *g = rowptr(i);
+        const float *row = direct(g) ? g
+                                     : reinterpret_cast<const float *>(ring + (size_t)s * slot_bytes +
+                                                                       (reinterpret_cast<uintptr_t>(g) & 15u));
+        const int64_t r = gw + i * nw;
+        int k = 0;
+        if (ENC == HDC_ENC_FP8_E4M3) {
+            float amax = 0.f;
+            for (int f = lane; f < F; f += 32) amax = fmaxf(amax, fabsf(row[f]));
+#pragma unroll
+            for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+            k = pow2_scale_exp(amax);
+            if (lane == 0) scale[r] = k >= -126 ? __int_as_float((127 + k) << 23) : ldexpf(1.f, k);
+        }
+        for (int f0 = lane * 4; f0 < ldd; f0 += 128) {
+            const float4 x = make_float4(f0 < F ? row[f0] : 0.f, f0 + 1 < F ? row[f0 + 1] : 0.f,
+                                         f0 + 2 < F ? row[f0 + 2] : 0.f, f0 + 3 < F ? row[f0 + 3] : 0.f);
+            if (ENC == HDC_ENC_FP32) {
+                *reinterpret_cast<float4 *>((float *)dst + r * (int64_t)ldd + f0) = x;
+            } else if (ENC == HDC_ENC_BF16) {
+                *reinterpret_cast<uint2 *>((__nv_bfloat16 *)dst + r * (int64_t)ldd + f0) = to_bf16x4(x.x, x.y, x.z, x.w);
+            } else {
+                *reinterpret_cast<uint32_t *>((uint8_t *)dst + r * (int64_t)ldd + f0) =
+                    to_e4m3x4(scale_pow2(x.x, k), scale_pow2(x.y, k), scale_pow2(x.z, k), scale_pow2(x.w, k));
+            }
+        }
+        // every lane is done reading the slot before the copy engine refills it
+        __syncwarp();
+        if (lane == 0 && i + QSLOTS < my_rows) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(i + QSLOTS);
+        }
+    }
+}
+
 // One block per class.  b == 1: plane 0 = sign bits.  b > 1: symmetric
 // per-class quantisation, two's-complement planes, sums and norms over K.
 __global__ void __launch_bounds__(256) class_prepare_kernel(const int32_t *__restrict__ acc, int D, int64_t s0,
@@ -379,7 +488,33 @@ cudaError_t launch_quant_rows(const float *src, int64_t lds, int64_t row_off, in
 #undef HDC_QBULK
         return cudaGetLastError();
     }
-    // unaligned rows: one warp per row straight from global memory
+    // rows not 16-byte aligned: their aligned spans streamed the same way
+    const size_t ssmem = (size_t)QWARPS * QSLOTS * span_slot_bytes(F) + (size_t)QWARPS * QSLOTS * 8;
+    if (ssmem <= 200 * 1024 && ldd % 4 == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+        const int per_sm = (int)((220 * 1024) / ssmem) > 0 ? (int)((220 * 1024) / ssmem) : 1;
+        int64_t qblocks = (nrows + QWARPS - 1) / QWARPS;
+        if (qblocks > (int64_t)sms * per_sm) qblocks = (int64_t)sms * per_sm;
+#define HDC_QSPAN(E)                                                                                              \
+    do {                                                                                                          \
+        cudaError_t e = cudaFuncSetAttribute(quant_rows_span_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)ssmem);                                                         \
+        if (e != cudaSuccess) return e;                                                                           \
+        quant_rows_span_kernel<E><<<(unsigned)qblocks, QWARPS * 32, ssmem, st>>>(src, lds, row_off, row_step,     \
+                                                                                 nrows, F, dst, ldd, scale);      \
+    } while (0)
+        switch (enc) {
+        case HDC_ENC_FP32: HDC_QSPAN(HDC_ENC_FP32); break;
+        case HDC_ENC_BF16: HDC_QSPAN(HDC_ENC_BF16); break;
+        default: HDC_QSPAN(HDC_ENC_FP8_E4M3);
+        }
+#undef HDC_QSPAN
+        return cudaGetLastError();
+    }
+    // very long rows: one warp per row straight from global memory
     int64_t blocks = (nrows + 7) / 8;
     if (blocks > 152 * 8 * 4) blocks = 152 * 8 * 4;
     dim3 g((unsigned)blocks), b(256);

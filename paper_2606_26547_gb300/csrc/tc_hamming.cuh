@@ -1,5 +1,5 @@
 // Fused classify with the Hamming distances on the tensor cores (binary
-// classes, 17 <= C <= 112).
+// classes, up to 112; the library routes 33 <= C <= 112 here).
 //
 // For +-1 vectors over the kept dims, Hamming(q, c) = (Dk - q.c) / 2, and
 // q.c is a sum of Dk products +-1 (0 for padding): an exact integer in FP32
