@@ -196,33 +196,45 @@ __global__ void __launch_bounds__(HP_THREADS, 1) tc_hamming_packed_kernel(const 
             const int64_t row = mt * BM + r;
             const bool valid = row < p.N;
             const uint32_t *qrow = p.Q + (valid ? row : 0) * (int64_t)p.W;
-            // words of the next tile, loaded one tile ahead
+            // query and class words of the next tile, loaded one tile ahead;
+            // class items (class c, half h) i = tid and tid + HP_EXP
+            auto class_words = [&](int i, int t) {
+                const int c = i >> 1, wc = t * 8 + (i & 1) * 4;
+                return (i < 2 * p.Cp && c < p.C && wc < p.W)
+                           ? *reinterpret_cast<const uint4 *>(p.cls + (int64_t)c * p.W + wc)
+                           : make_uint4(0, 0, 0, 0);
+            };
             uint4 qn = make_uint4(0, 0, 0, 0);
             {
                 const int w0 = half * 4;
                 if (valid && w0 < p.W) qn = *reinterpret_cast<const uint4 *>(qrow + w0);
             }
+            uint4 cn0 = class_words(tid, 0), cn1 = class_words(tid + HP_EXP, 0);
             for (int t = 0; t < p.nt; t++) {
-                const uint4 qw = qn;
+                const uint4 qw = qn, cw0 = cn0, cw1 = cn1;
                 const int w0 = t * 8 + half * 4;                  // this thread's four words
                 const int wn = w0 + 8;
-                if (t + 1 < p.nt) qn = (valid && wn < p.W) ? *reinterpret_cast<const uint4 *>(qrow + wn)
-                                                          : make_uint4(0, 0, 0, 0);
+                if (t + 1 < p.nt) {
+                    qn = (valid && wn < p.W) ? *reinterpret_cast<const uint4 *>(qrow + wn) : make_uint4(0, 0, 0, 0);
+                    cn0 = class_words(tid, t + 1);
+                    cn1 = class_words(tid + HP_EXP, t + 1);
+                }
                 const bool oke = mbar_wait(empty(buf), ph ^ 1, abort_flag);   // the MMAs of this buffer's last use
                 if (!__all_sync(0xffffffffu, oke)) { ab = true; break; }
                 const uint4 mq = w0 < p.W ? *reinterpret_cast<const uint4 *>(smask + w0) : make_uint4(0, 0, 0, 0);
                 expand_row(sA + buf * HP_A_BYTES + half * (BM * 128), r, qw, mq);
-                // class rows: items (class c, half h) spread over the 256 threads
+                // class rows: items (class c, half h) i = tid, tid + HP_EXP (2 * Cp <= 512)
                 uint8_t *bt = sB + buf * b_bytes;
-                for (int i = tid; i < 2 * p.Cp; i += HP_EXP) {
-                    const int c = i >> 1, h = i & 1;
-                    const int wc = t * 8 + h * 4;
-                    uint4 cw = make_uint4(0, 0, 0, 0), mc = make_uint4(0, 0, 0, 0);
-                    if (c < p.C && wc < p.W) {
-                        cw = *reinterpret_cast<const uint4 *>(p.cls + (int64_t)c * p.W + wc);
-                        mc = *reinterpret_cast<const uint4 *>(smask + wc);
+#pragma unroll
+                for (int ii = 0; ii < 2; ii++) {
+                    const int i = tid + ii * HP_EXP;
+                    if (i < 2 * p.Cp) {
+                        const int c = i >> 1, h = i & 1;
+                        const int wc = t * 8 + h * 4;
+                        const uint4 mc = (c < p.C && wc < p.W) ? *reinterpret_cast<const uint4 *>(smask + wc)
+                                                               : make_uint4(0, 0, 0, 0);
+                        expand_row(bt + h * (p.Cp * 128), c, ii ? cw1 : cw0, mc);
                     }
-                    expand_row(bt + h * (p.Cp * 128), c, cw, mc);
                 }
                 fence_async_smem();
                 mbar_arrive(full(buf));
