@@ -172,6 +172,22 @@ def test_hamming_argmin_tensor_core_range(hdc, C, D, perf):
     assert np.array_equal(labels.cpu().numpy(), orc.argmin(od))
 
 
+@pytest.mark.parametrize("N", [1, 127, 129])
+@pytest.mark.parametrize("C", [32, 33, 48, 112, 113])
+def test_hamming_argmin_class_count_edges(hdc, N, C):
+    """Partial and single-row tiles at the class counts where the routes and
+    the 16-class padding change (32 / 33, 112 / 113)."""
+    rng = np.random.default_rng(N * 1000 + C)
+    D = 700
+    q = rng.integers(0, 2, (N, D)).astype(np.uint8)
+    c = rng.integers(0, 2, (C, D)).astype(np.uint8)
+    c[C - 1] = c[0]
+    labels, dd = hdc.hamming_argmin(T(pack(q).view(np.int32)), T(pack(c).view(np.int32)), D, dists=True)
+    od = orc.hamming(q, c)
+    assert np.array_equal(dd.cpu().numpy().astype(np.int64), od)
+    assert np.array_equal(labels.cpu().numpy(), orc.argmin(od))
+
+
 def test_hamming_argmin_tensor_core_many_tiles(hdc):
     """More 128-row tiles than SMs (the persistent loop), labels only."""
     rng = np.random.default_rng(11)
