@@ -16,8 +16,9 @@
 // Tensor memory: two 192-column encode accumulators and D2 (Cp <= 128).
 // Shared memory: three A/B stages (40 KB each), the 48 KB value tile and the
 // Cp x 384-byte class tile.  Roles as the tensor-core Hamming kernel:
-// warps 0-11 epilogue (three warpgroups), 12 stage producer, 13 MMA issuer,
-// 14 class-tile producer; every wait bounded.
+// warps 0-11 epilogue (three warpgroups), 12 stage producer, 13 MMA1 issuer,
+// 14 class-tile producer, 15 MMA2 issuer (its own commit chain: 4.65 vs
+// 5.47 ms per 2^20 queries at C = 10 with one issuer); every wait bounded.
 #pragma once
 #include "tc_hamming.cuh"
 
@@ -29,10 +30,11 @@ namespace tc {
 // flight are what covers the L2 latency (36 % tensor activity measured with
 // three stages at C = 10).
 constexpr int FC_A2_BYTES = 3 * A2_ATOM;            // 128 rows x 192 BF16 in three 128-byte K atoms
+constexpr int FC_THREADS = (4 * HEWG + 4) * 32;     // + the cosine MMA issuer
 constexpr int FC_CMAX = 112;
 // full[S], empty[S], sfull[2], sempty[2], a2full, a2empty, b2full, b2empty,
-// d2full, d2empty, done, merge_full, merge_empty, qfull[2]
-__host__ __device__ constexpr int fc_num_bars(int stages) { return 2 * stages + 4 + 6 + 3 + 2; }
+// d2full, d2empty, done, merge_full, merge_empty, qfull[2], done2
+__host__ __device__ constexpr int fc_num_bars(int stages) { return 2 * stages + 4 + 6 + 3 + 2 + 1; }
 
 __host__ __device__ constexpr size_t fc_smem_bytes(int stages, int Cp)
 {
@@ -53,7 +55,7 @@ struct FCParams {
 };
 
 template <int ENC, int FC_STAGES>
-__global__ void __launch_bounds__(H_THREADS, 1)
+__global__ void __launch_bounds__(FC_THREADS, 1)
     tc_fcos_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmV, const FCParams p)
 {
@@ -80,7 +82,8 @@ __global__ void __launch_bounds__(H_THREADS, 1)
     const uint32_t done_bar = su32(bars + 2 * FC_STAGES + 10);
     const uint32_t merge_full = su32(bars + 2 * FC_STAGES + 11), merge_empty = su32(bars + 2 * FC_STAGES + 12);
     auto qfull = [&](int b) { return su32(bars + 2 * FC_STAGES + 13 + b); };
-    constexpr int PRODUCER = 4 * HEWG, ISSUER = 4 * HEWG + 1, CPRODUCER = 4 * HEWG + 2;
+    const uint32_t done2_bar = su32(bars + 2 * FC_STAGES + 15);
+    constexpr int PRODUCER = 4 * HEWG, ISSUER = 4 * HEWG + 1, CPRODUCER = 4 * HEWG + 2, ISSUER2 = 4 * HEWG + 3;
     constexpr int KELEMS = ENC == HDC_ENC_BF16 ? BKB / 2 : BKB;
     constexpr uint32_t D2_COL = 2 * HBN;
 
@@ -104,6 +107,7 @@ __global__ void __launch_bounds__(H_THREADS, 1)
         mbar_init(d2full, 1);
         mbar_init(d2empty, BM * HEWG);
         mbar_init(done_bar, 1);
+        mbar_init(done2_bar, 1);
         mbar_init(merge_full, BM * (HEWG - 1));
         mbar_init(merge_empty, BM);
         *abort_flag = 0;
@@ -172,31 +176,11 @@ __global__ void __launch_bounds__(H_THREADS, 1)
             }
         }
     } else if (warp == ISSUER) {
-        if (lane == 0) {  // ------------------------------ MMA issuer
+        if (lane == 0) {  // ------------------------------ MMA1 issuer (encode)
             const uint32_t id1 = idesc_n<ENC>(HBN);
-            const uint32_t id2 = idesc_n<HDC_ENC_BF16>(p.Cp);
             int stage = 0, acc = 0;
-            uint32_t phase = 0, aphase = 0, a2ph = 0, b2ph = 0, d2ph = 0;
+            uint32_t phase = 0, aphase = 0;
             bool ab = false;
-            auto mma2 = [&](bool first) -> bool {
-                if (first && !mbar_wait(d2empty, d2ph ^ 1, abort_flag)) return false;
-                if (!mbar_wait(a2full, a2ph, abort_flag)) return false;
-                if (!mbar_wait(b2full, b2ph, abort_flag)) return false;
-                tc_fence_after();
-                const uint32_t a0 = su32(sA2), b0 = su32(sB2);
-#pragma unroll
-                for (int k = 0; k < 12; k++) {   // three atoms of four 16-element K steps
-                    const uint32_t off_a = (uint32_t)((k >> 2) * A2_ATOM) + 32u * (k & 3);
-                    const uint32_t off_b = (uint32_t)((k >> 2) * p.Cp * 128) + 32u * (k & 3);
-                    mma<HDC_ENC_BF16>(tmem + D2_COL, sdesc(a0 + off_a), sdesc(b0 + off_b), id2,
-                                      (first && k == 0) ? 0u : 1u);
-                }
-                mma_commit(a2empty);
-                mma_commit(b2empty);
-                a2ph ^= 1;
-                b2ph ^= 1;
-                return true;
-            };
             for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
                 for (int t = 0; t < p.nt && !ab; t++) {
                     if (!mbar_wait(sempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
@@ -215,16 +199,44 @@ __global__ void __launch_bounds__(H_THREADS, 1)
                     if (ab) break;
                     mma_commit(sfull(acc));
                     if (++acc == 2) { acc = 0; aphase ^= 1; }
-                    if (t > 0 && !mma2(t == 1)) { ab = true; break; }
                 }
-                if (ab) break;
-                if (!mma2(p.nt == 1)) { ab = true; break; }
-                mma_commit(d2full);
-                d2ph ^= 1;
             }
             mma_commit(done_bar);
             const unsigned long long t0 = gtimer();
             while (!mbar_try(done_bar, 0) && gtimer() - t0 < 100000000ull) {}
+        }
+    } else if (warp == ISSUER2) {
+        if (lane == 0) {  // ------------------------------ MMA2 issuer (cosine), its own commit chain
+            const uint32_t id2 = idesc_n<HDC_ENC_BF16>(p.Cp);
+            uint32_t a2ph = 0, b2ph = 0, d2ph = 0;
+            bool ab = false;
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
+                for (int t = 0; t < p.nt; t++) {
+                    const bool first = t == 0;
+                    if (first && !mbar_wait(d2empty, d2ph ^ 1, abort_flag)) { ab = true; break; }
+                    if (!mbar_wait(a2full, a2ph, abort_flag)) { ab = true; break; }
+                    if (!mbar_wait(b2full, b2ph, abort_flag)) { ab = true; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = su32(sA2), b0 = su32(sB2);
+#pragma unroll
+                    for (int k = 0; k < 12; k++) {   // three atoms of four 16-element K steps
+                        const uint32_t off_a = (uint32_t)((k >> 2) * A2_ATOM) + 32u * (k & 3);
+                        const uint32_t off_b = (uint32_t)((k >> 2) * p.Cp * 128) + 32u * (k & 3);
+                        mma<HDC_ENC_BF16>(tmem + D2_COL, sdesc(a0 + off_a), sdesc(b0 + off_b), id2,
+                                          (first && k == 0) ? 0u : 1u);
+                    }
+                    mma_commit(a2empty);
+                    mma_commit(b2empty);
+                    a2ph ^= 1;
+                    b2ph ^= 1;
+                }
+                if (ab) break;
+                mma_commit(d2full);
+                d2ph ^= 1;
+            }
+            mma_commit(done2_bar);
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try(done2_bar, 0) && gtimer() - t0 < 100000000ull) {}
         }
     } else {  // ------------------------------------------ epilogue warps 0 .. 11
         const int q = warp & 3, g = warp >> 2;
@@ -376,7 +388,7 @@ static cudaError_t launch_fcos_stages(const CUtensorMap &ma, const CUtensorMap &
     const size_t smem = fc_smem_bytes(STAGES, p.Cp);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, H_THREADS, smem, st>>>(ma, mb, mv, p);
+    k<<<grid, FC_THREADS, smem, st>>>(ma, mb, mv, p);
     return cudaGetLastError();
 }
 
