@@ -197,9 +197,11 @@ __global__ void __launch_bounds__(HP_THREADS, 1) tc_hamming_packed_kernel(const 
             const bool valid = row < p.N;
             const uint32_t *qrow = p.Q + (valid ? row : 0) * (int64_t)p.W;
             // query and class words of the next tile, loaded one tile ahead;
-            // class items (class c, half h) i = tid and tid + HP_EXP
+            // class items i = tid and tid + HP_EXP: half h = i / Cp, class
+            // c = i % Cp (consecutive lanes on consecutive rows of one atom:
+            // no shared-memory bank conflicts on the expanded stores)
             auto class_words = [&](int i, int t) {
-                const int c = i >> 1, wc = t * 8 + (i & 1) * 4;
+                const int c = i % p.Cp, wc = t * 8 + (i / p.Cp) * 4;
                 return (i < 2 * p.Cp && c < p.C && wc < p.W)
                            ? *reinterpret_cast<const uint4 *>(p.cls + (int64_t)c * p.W + wc)
                            : make_uint4(0, 0, 0, 0);
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(HP_THREADS, 1) tc_hamming_packed_kernel(const 
                 for (int ii = 0; ii < 2; ii++) {
                     const int i = tid + ii * HP_EXP;
                     if (i < 2 * p.Cp) {
-                        const int c = i >> 1, h = i & 1;
+                        const int c = i % p.Cp, h = i / p.Cp;
                         const int wc = t * 8 + h * 4;
                         const uint4 mc = (c < p.C && wc < p.W) ? *reinterpret_cast<const uint4 *>(smask + wc)
                                                                : make_uint4(0, 0, 0, 0);
