@@ -25,7 +25,7 @@
 namespace hdc {
 namespace tc {
 
-constexpr int HP_TD = 256;                     // dims per tile (two 128-byte K atoms)
+// 256-dim tiles: eight packed words per row, two 128-byte K atoms
 constexpr int HP_EXP = 256;                    // expanding threads (warps 0-7)
 constexpr int HP_THREADS = HP_EXP + 32;
 constexpr int HP_CMAX = 256;
