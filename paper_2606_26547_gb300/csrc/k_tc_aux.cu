@@ -50,16 +50,19 @@ cudaError_t launch_hamming_packed(const uint32_t *Q, int64_t N, const uint32_t *
     p.labels = labels;
     p.dists = dists;
     const size_t smem = tc::hp_smem_bytes(p.Cp, W);
-    cudaError_t e = cudaFuncSetAttribute(tc::tc_hamming_packed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                      cudaSuccess || sms <= 0)
         sms = 152;
     const int64_t tiles = (N + tc::BM - 1) / tc::BM;
-    const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
-    tc::tc_hamming_packed_kernel<<<grid, tc::HP_THREADS, smem, st>>>(p);
+    // two CTAs per SM when both fit in shared memory (TMEM: 2 x 256 columns)
+    const bool two = 2 * (smem + 1024) <= 228 * 1024;
+    auto k = two ? tc::tc_hamming_packed_kernel<2> : tc::tc_hamming_packed_kernel<1>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t slots = (int64_t)sms * (two ? 2 : 1);
+    const unsigned grid = (unsigned)(tiles < slots ? tiles : slots);
+    k<<<grid, tc::HP_THREADS, smem, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -88,7 +88,9 @@ __device__ __forceinline__ void expand_row(uint8_t *atom, int r, const uint4 w, 
     }
 }
 
-__global__ void __launch_bounds__(HP_THREADS, 1) tc_hamming_packed_kernel(const HPParams p)
+// MINB = 2: two CTAs per SM (small class tiles), registers capped to fit.
+template <int MINB>
+__global__ void __launch_bounds__(HP_THREADS, MINB) tc_hamming_packed_kernel(const HPParams p)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
