@@ -49,15 +49,19 @@ cudaError_t launch_hamming_packed(const uint32_t *Q, int64_t N, const uint32_t *
     p.stride = stride;
     p.labels = labels;
     p.dists = dists;
-    const size_t smem = tc::hp_smem_bytes(p.Cp, W);
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                      cudaSuccess || sms <= 0)
         sms = 152;
     const int64_t tiles = (N + tc::BM - 1) / tc::BM;
-    // two CTAs per SM when both fit in shared memory (TMEM: 2 x 256 columns)
-    const bool two = 2 * (smem + 1024) <= 228 * 1024;
-    auto k = two ? tc::tc_hamming_packed_kernel<2> : tc::tc_hamming_packed_kernel<1>;
+    // two CTAs per SM when both fit in shared memory (TMEM: 2 x 256 columns),
+    // with two class-tile buffers if they fit, else one
+    auto fits2 = [](size_t bytes) { return 2 * (bytes + 1024) <= 228 * 1024; };
+    const size_t smem2 = tc::hp_smem_bytes(p.Cp, W, 2), smem1 = tc::hp_smem_bytes(p.Cp, W, 1);
+    const bool two = fits2(smem2) || fits2(smem1);
+    const size_t smem = fits2(smem2) ? smem2 : fits2(smem1) ? smem1 : smem2;
+    auto k = fits2(smem2) ? tc::tc_hamming_packed_kernel<2, 2>
+                          : fits2(smem1) ? tc::tc_hamming_packed_kernel<2, 1> : tc::tc_hamming_packed_kernel<1, 2>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t slots = (int64_t)sms * (two ? 2 : 1);

@@ -34,9 +34,10 @@ constexpr int HP_MAX_W = 4096;                 // words of a packed row (D <= 13
 // full[2], empty[2], d2full, d2empty, merge_full, merge_empty, done
 constexpr int HP_NUM_BARS = 9;
 
-__host__ __device__ constexpr size_t hp_smem_bytes(int Cp, int W)
+// bbuf: class-tile buffers (2, or 1 so that two CTAs fit per SM)
+__host__ __device__ constexpr size_t hp_smem_bytes(int Cp, int W, int bbuf = 2)
 {
-    return 1024 + (size_t)2 * HP_A_BYTES + (size_t)2 * 2 * Cp * 128 + (size_t)(W + 2) * 4 + HP_NUM_BARS * 8 + 16 +
+    return 1024 + (size_t)2 * HP_A_BYTES + (size_t)bbuf * 2 * Cp * 128 + (size_t)(W + 2) * 4 + HP_NUM_BARS * 8 + 16 +
            (size_t)2 * BM * 4;
 }
 static_assert(hp_smem_bytes(HP_CMAX, HP_MAX_W) <= 232448, "shared memory of the packed tensor-core Hamming kernel");
@@ -88,8 +89,10 @@ __device__ __forceinline__ void expand_row(uint8_t *atom, int r, const uint4 w, 
     }
 }
 
-// MINB = 2: two CTAs per SM (small class tiles), registers capped to fit.
-template <int MINB>
+// MINB = 2: two CTAs per SM, registers capped to fit.  BBUF = 1: one
+// class-tile buffer (so two CTAs fit with larger class tiles): the class rows
+// of tile t are written once the MMAs of tile t - 1 have read them.
+template <int MINB, int BBUF>
 __global__ void __launch_bounds__(HP_THREADS, MINB) tc_hamming_packed_kernel(const HPParams p)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -97,7 +100,7 @@ __global__ void __launch_bounds__(HP_THREADS, MINB) tc_hamming_packed_kernel(con
     uint8_t *sA = smem;                                          // 2 buffers x HP_A_BYTES
     uint8_t *sB = sA + 2 * HP_A_BYTES;                           // 2 buffers x two atoms of Cp x 128 bytes
     const int b_bytes = 2 * p.Cp * 128;
-    uint32_t *smask = reinterpret_cast<uint32_t *>(sB + 2 * b_bytes);   // W mask words
+    uint32_t *smask = reinterpret_cast<uint32_t *>(sB + BBUF * b_bytes);   // W mask words
     uint64_t *bars = reinterpret_cast<uint64_t *>(smask + ((p.W + 1) & ~1));
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + HP_NUM_BARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(HP_THREADS, MINB) tc_hamming_packed_kernel(con
                 for (int t = 0; t < p.nt; t++) {
                     if (!mbar_wait(full(buf), ph, abort_flag)) { ab = true; break; }
                     tc_fence_after();
-                    const uint32_t a0 = su32(sA + buf * HP_A_BYTES), b0 = su32(sB + buf * b_bytes);
+                    const uint32_t a0 = su32(sA + buf * HP_A_BYTES), b0 = su32(sB + (BBUF == 2 ? buf : 0) * b_bytes);
 #pragma unroll
                     for (int k = 0; k < 8; k++) {   // two atoms of four 32-byte K steps
                         const uint32_t oa = (uint32_t)((k >> 2) * (BM * 128)) + 32u * (k & 3);
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(HP_THREADS, MINB) tc_hamming_packed_kernel(con
         int buf = 0;
         uint32_t ph = 0, d2ph = 0;
         bool ab = false;
-        int64_t it = 0;
+        int64_t it = 0, gt = 0;   // gt: tiles expanded by this CTA
         for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++) {
             const int64_t row = mt * BM + r;
             const bool valid = row < p.N;
@@ -225,10 +228,15 @@ __global__ void __launch_bounds__(HP_THREADS, MINB) tc_hamming_packed_kernel(con
                 }
                 const bool oke = mbar_wait(empty(buf), ph ^ 1, abort_flag);   // the MMAs of this buffer's last use
                 if (!__all_sync(0xffffffffu, oke)) { ab = true; break; }
+                if (BBUF == 1 && gt > 0) {   // the single class tile: the previous tile's MMAs have read it
+                    const bool okp = mbar_wait(empty(buf ^ 1), buf ? ph : ph ^ 1, abort_flag);
+                    if (!__all_sync(0xffffffffu, okp)) { ab = true; break; }
+                }
+                gt++;
                 const uint4 mq = w0 < p.W ? *reinterpret_cast<const uint4 *>(smask + w0) : make_uint4(0, 0, 0, 0);
                 expand_row(sA + buf * HP_A_BYTES + half * (BM * 128), r, qw, mq);
                 // class rows: items (class c, half h) i = tid, tid + HP_EXP (2 * Cp <= 512)
-                uint8_t *bt = sB + buf * b_bytes;
+                uint8_t *bt = sB + (BBUF == 2 ? buf : 0) * b_bytes;
 #pragma unroll
                 for (int ii = 0; ii < 2; ii++) {
                     const int i = tid + ii * HP_EXP;
