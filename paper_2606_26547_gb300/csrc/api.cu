@@ -414,7 +414,7 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *
         float *qn = (float *)((char *)ws + L.qn);
         const int ldS = lds_for(m->Dk);
         bool done = false;
-        if (use_tc(m) && m->C <= 112) {
+        if (use_tc(m) && m->C <= 128) {
             // encode and cosine fused: the BF16 projections stay on chip
             TcArgs f = {};
             f.Xq = Xop; f.N = N; f.F = m->Fk; f.ldx = (int)ldx; f.Bq = m->Bq; f.ldb = m->ldb; f.Dk = m->Dk;

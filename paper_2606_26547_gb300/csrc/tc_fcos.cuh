@@ -1,6 +1,6 @@
 // Fused classify of float (non-binarised) query hypervectors: encode and
 // cosine in one kernel (Sec. 4.2 Algorithmic Choice; the float + cosine form
-// of Sec. 5.2), C <= 112 classes.
+// of Sec. 5.2), C <= 128 classes.
 //
 // For each 192-dim tile t of a 128-query block:
 //   S = Xq . Bq^T                (MMA1: M 128, N 192, K = F, BF16 or E4M3)
@@ -31,7 +31,7 @@ namespace tc {
 // three stages at C = 10).
 constexpr int FC_A2_BYTES = 3 * A2_ATOM;            // 128 rows x 192 BF16 in three 128-byte K atoms
 constexpr int FC_THREADS = (4 * HEWG + 4) * 32;     // + the cosine MMA issuer
-constexpr int FC_CMAX = 112;
+constexpr int FC_CMAX = 128;   // TMEM: 2 x 192 + 128 columns
 // full[S], empty[S], sfull[2], sempty[2], a2full, a2empty, b2full, b2empty,
 // d2full, d2empty, done, merge_full, merge_empty, qfull[2], done2
 __host__ __device__ constexpr int fc_num_bars(int stages) { return 2 * stages + 4 + 6 + 3 + 2 + 1; }

@@ -59,7 +59,8 @@ def check(labels, scores, o_lab, o_sc, b):
 
 @pytest.mark.parametrize("enc,simt", [("bf16", False), ("fp8", False), ("fp32", False), ("fp8", True)])
 @pytest.mark.parametrize("C,bits_,perf", [(10, 8, (0.0, 1.0, 1)), (26, 4, (0.0, 0.5, 1)), (100, 8, (0.1, 0.97, 3)),
-                                          (1, 8, (0.0, 1.0, 2)), (256, 4, (0.0, 1.0, 1)), (17, 8, (0.3, 1.0, 2))])
+                                          (1, 8, (0.0, 1.0, 2)), (256, 4, (0.0, 1.0, 1)), (17, 8, (0.3, 1.0, 2)),
+                                          (113, 8, (0.0, 1.0, 2)), (128, 4, (0.05, 0.95, 1))])
 def test_float_query_integer_data(hdc, enc, simt, C, bits_, perf):
     rng = np.random.default_rng(C * 31 + bits_)
     F, D, N = 300, 1000, 333
