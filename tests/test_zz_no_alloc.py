@@ -15,7 +15,6 @@ fresh process.
 """
 import ctypes
 
-import numpy as np
 import pytest
 import torch
 
