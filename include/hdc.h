@@ -141,7 +141,7 @@ typedef struct {
                                /* complement class value (1 plane = sign)   */
     const int32_t *cls_sum;    /* C: sum over K of the class values (b > 1) */
     const double *cls_norm;    /* C: sqrt(sum over K of class value^2)       */
-    const uint8_t *cls_sign;   /* binary classes, 17 <= C <= 112: Cp x ldcs  */
+    const uint8_t *cls_sign;   /* binary classes, 33 <= C <= 112: Cp x ldcs  */
                                /* E4M3 +-1 bytes of the class hypervectors  */
                                /* (0 past Dk and for the pad classes up to  */
                                /* Cp = C rounded to 16) for the tensor-core */

@@ -332,19 +332,22 @@ hdc_status hdc_hamming_argmin(const uint32_t *Q, const uint32_t *Cls, int64_t N,
 
 namespace {
 // Training workspace: predictions, the class-grouped sample order, and the
-// counting-sort histogram / offsets / cursors.
+// counting-sort histogram / offsets / first work item per group / cursors.
 struct TrainLayout {
-    size_t pred, perm, hist, offsets, cursor, total;
+    size_t pred, perm, hist, offsets, items, cursor, total;
 };
 TrainLayout train_layout(int64_t N, int C)
 {
     TrainLayout L;
     size_t off = 0;
     L.pred = off;    off = align_up(off + (size_t)N * 4, kAlign);
-    L.perm = off;    off = align_up(off + (size_t)N * 4, kAlign);
-    L.hist = off;    off = align_up(off + (size_t)C * 4, kAlign);
-    L.offsets = off; off = align_up(off + (size_t)(C + 1) * 4, kAlign);
-    L.cursor = off;  off = align_up(off + (size_t)C * 4, kAlign);
+    // retraining groups a misclassified sample twice (true and predicted
+    // class): 2N permutation entries over 2C groups
+    L.perm = off;    off = align_up(off + (size_t)2 * N * 4, kAlign);
+    L.hist = off;    off = align_up(off + (size_t)2 * C * 4, kAlign);
+    L.offsets = off; off = align_up(off + (size_t)(2 * C + 1) * 4, kAlign);
+    L.items = off;   off = align_up(off + (size_t)(2 * C + 1) * 4, kAlign);
+    L.cursor = off;  off = align_up(off + (size_t)2 * C * 4, kAlign);
     L.total = off;
     return L;
 }
@@ -370,7 +373,7 @@ hdc_status hdc_train_epoch(const uint32_t *H, const int32_t *y, int64_t N, int32
     if (N > 0 && (!ws || ws_bytes < L.total || !aligned(ws, kAlign))) return HDC_ERR_WORKSPACE;
     char *w = (char *)ws;
     TrainScratch sc = {(int32_t *)(w + L.perm), (int32_t *)(w + L.hist), (int32_t *)(w + L.offsets),
-                       (int32_t *)(w + L.cursor)};
+                       (int32_t *)(w + L.items), (int32_t *)(w + L.cursor)};
     if (n_updates) {
         hdc_status s = cu(cudaMemsetAsync(n_updates, 0, sizeof(int32_t), st));
         if (s != HDC_OK) return s;

@@ -84,7 +84,7 @@ cudaError_t launch_similarity(const uint32_t *Q, int64_t N, const uint32_t *plan
 //          and n_updates (if not NULL, zeroed by the caller) counts them.
 // Scratch: perm (N int32), hist / cursor (C int32), offsets (C+1 int32).
 struct TrainScratch {
-    int32_t *perm, *hist, *offsets, *cursor;
+    int32_t *perm, *hist, *offsets, *items, *cursor;
 };
 cudaError_t launch_train_count(const uint32_t *H, int W, const int32_t *y, const int32_t *pred,
                                int64_t N, int D, int C, int mode, int32_t *acc, int32_t *n_updates,
