@@ -111,23 +111,31 @@ __global__ void __launch_bounds__(TPB) similarity_kernel(const uint32_t *__restr
 }
 
 // Hamming arg-min for C <= CMAX with the distances in registers.  A block
-// stages 128 queries x RWCH words coalesced into shared memory, transposed
-// ([word][query], padded), with the chunk's class words and masks; every
-// class word is then a broadcast read.
+// stages RB = 128 / S queries x RWCH words coalesced into shared memory,
+// transposed ([word][query], padded), with the chunk's class words and
+// masks; every class word is then a broadcast read.  S threads share a
+// query when the batch gives fewer than twelve 128-query blocks per SM
+// (S = 4; 10^5 queries of 512 words ran ~15 % faster so, 3 * 10^5 of 32
+// words ~5 % slower): thread (r, s) counts the words s, s + S, ... of each
+// chunk for query r, and the partial distances are summed through shared
+// memory before the arg-min.
 constexpr int RWCH = 32;
 
-template <int CMAX>
+template <int CMAX, int S>
 __global__ void __launch_bounds__(TPB) hamming_reg_kernel(const uint32_t *__restrict__ Q, int64_t N,
                                                           const uint32_t *__restrict__ cls, int C, int W,
                                                           int use_mask, int64_t s0, int64_t e0, int64_t stride,
                                                           int32_t *__restrict__ labels, int32_t *__restrict__ dists)
 {
-    __shared__ uint32_t sq[RWCH][TPB + 1];
+    constexpr int RB = TPB / S;
+    __shared__ uint32_t sq[RWCH][RB + 1];
     __shared__ uint32_t sc[CMAX][RWCH];
     __shared__ uint32_t mk[RWCH];
+    __shared__ int32_t sd[S > 1 ? S - 1 : 1][CMAX][RB];
     const int tid = threadIdx.x;
-    const int64_t row0 = (int64_t)blockIdx.x * TPB;
-    const int64_t row = row0 + tid;
+    const int r = tid % RB, s = tid / RB;  // a warp holds 32 consecutive queries of one s
+    const int64_t row0 = (int64_t)blockIdx.x * RB;
+    const int64_t row = row0 + r;
     int best = 0, bv = 0x7fffffff;
     // classes in chunks of CMAX (one chunk when C <= CMAX); chunks ascend, so
     // a strict comparison keeps the lowest class on ties
@@ -139,9 +147,9 @@ __global__ void __launch_bounds__(TPB) hamming_reg_kernel(const uint32_t *__rest
         for (int w0 = 0; w0 < W; w0 += RWCH) {
             const int nw = min(RWCH, W - w0);
             __syncthreads();
-            for (int i = tid; i < TPB * RWCH; i += TPB) {  // consecutive threads: consecutive words of a row
-                const int r = i / RWCH, j = i % RWCH;
-                sq[j][r] = (row0 + r < N && j < nw) ? __ldg(Q + (row0 + r) * W + w0 + j) : 0u;
+            for (int i = tid; i < RB * RWCH; i += TPB) {  // consecutive threads: consecutive words of a row
+                const int rr = i / RWCH, j = i % RWCH;
+                sq[j][rr] = (row0 + rr < N && j < nw) ? __ldg(Q + (row0 + rr) * W + w0 + j) : 0u;
             }
             for (int i = tid; i < CMAX * RWCH; i += TPB) {
                 const int c = i / RWCH, j = i % RWCH;
@@ -161,15 +169,26 @@ __global__ void __launch_bounds__(TPB) hamming_reg_kernel(const uint32_t *__rest
                 mk[tid] = m;
             }
             __syncthreads();
-            for (int j = 0; j < nw; j++) {
+            for (int j = s; j < nw; j += S) {
                 const uint32_t m = mk[j];
-                const uint32_t q = sq[j][tid] & m;
+                const uint32_t q = sq[j][r] & m;
 #pragma unroll
                 for (int c = 0; c < CMAX; c++)
                     if (c < cn) dist[c] += __popc(q ^ (sc[c][j] & m));
             }
         }
-        if (row < N) {
+        if (S > 1) {  // the next write of sd follows the next chunk loop's barriers
+            if (s > 0)
+#pragma unroll
+                for (int c = 0; c < CMAX; c++) sd[s - 1][c][r] = dist[c];
+            __syncthreads();
+            if (s == 0)
+#pragma unroll
+                for (int c = 0; c < CMAX; c++)
+#pragma unroll
+                    for (int t = 0; t < S - 1; t++) dist[c] += sd[t][c][r];
+        }
+        if (s == 0 && row < N) {
 #pragma unroll
             for (int c = 0; c < CMAX; c++)
                 if (c < cn) {
@@ -178,7 +197,19 @@ __global__ void __launch_bounds__(TPB) hamming_reg_kernel(const uint32_t *__rest
                 }
         }
     }
-    if (row < N) labels[row] = best;
+    if (s == 0 && row < N) labels[row] = best;
+}
+
+int device_sms()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                     cudaSuccess)
+            n = 0;
+    }
+    return n > 0 ? n : 152;
 }
 
 template <int CMAX>
@@ -187,9 +218,15 @@ cudaError_t launch_reg(const uint32_t *Q, int64_t N, const uint32_t *cls, int C,
 {
     const int use_mask = p != nullptr;
     const int64_t s0 = p ? p->s0 : 0, e0 = p ? p->e0 : D, stride = p ? p->stride : 1;
-    const int64_t blocks = (N + TPB - 1) / TPB;
-    hamming_reg_kernel<CMAX><<<(unsigned)blocks, TPB, 0, st>>>(Q, N, cls, C, W, use_mask, s0, e0, stride, labels,
-                                                               dists);
+    if ((N + TPB - 1) / TPB < 12 * (int64_t)device_sms()) {  // short batch: four threads per query
+        const int64_t blocks = (N + TPB / 4 - 1) / (TPB / 4);
+        hamming_reg_kernel<CMAX, 4><<<(unsigned)blocks, TPB, 0, st>>>(Q, N, cls, C, W, use_mask, s0, e0, stride,
+                                                                      labels, dists);
+    } else {
+        const int64_t blocks = (N + TPB - 1) / TPB;
+        hamming_reg_kernel<CMAX, 1><<<(unsigned)blocks, TPB, 0, st>>>(Q, N, cls, C, W, use_mask, s0, e0, stride,
+                                                                      labels, dists);
+    }
     return cudaGetLastError();
 }
 

@@ -226,15 +226,20 @@ def hamming_argmin(Q: torch.Tensor, Cls: torch.Tensor, D: int, cfg: ApproxConfig
     return (labels, dd) if dists else labels
 
 
+def train_workspace(N: int, D: int, C: int, device) -> torch.Tensor:
+    """Device workspace for hdc_train_epoch over N samples, D dims, C classes."""
+    n = ctypes.c_size_t()
+    _call("hdc_train_workspace_bytes", N, D, C, ctypes.byref(n))
+    return _empty_bytes(n.value, device)
+
+
 def train_epoch(H: torch.Tensor, y: torch.Tensor, D: int, C: int, mode: int, acc: torch.Tensor,
                 cls: torch.Tensor, n_updates: torch.Tensor | None = None, ws: torch.Tensor | None = None,
                 stream=None) -> None:
     """One bundling (mode 0) or retraining (mode 1) pass; updates acc and cls."""
     N = H.shape[0]
     if ws is None:
-        n = ctypes.c_size_t()
-        _call("hdc_train_workspace_bytes", N, D, C, ctypes.byref(n))
-        ws = _empty_bytes(n.value, H.device)
+        ws = train_workspace(N, D, C, H.device)
     _call("hdc_train_epoch", _ptr(H), _ptr(y), N, D, C, mode, _ptr(acc), _ptr(cls), _ptr(n_updates),
           _ptr(ws), ws.numel(), _stream(stream))
 

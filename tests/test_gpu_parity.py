@@ -188,6 +188,24 @@ def test_hamming_argmin_class_count_edges(hdc, N, C):
     assert np.array_equal(labels.cpu().numpy(), orc.argmin(od))
 
 
+@pytest.mark.parametrize("N", [233471, 240037])   # either side of twelve 128-row blocks per SM on 152 SMs
+@pytest.mark.parametrize("C", [10, 32, 257])
+def test_hamming_argmin_popcount_batch_sizes(hdc, N, C):
+    """The popcount kernel with one and with four threads per query (short
+    batches split each row's words): distances and labels, the 257-class
+    case on a sample of rows."""
+    rng = np.random.default_rng(N + C)
+    D = 96
+    q = rng.integers(0, 2, (N, D)).astype(np.uint8)
+    c = rng.integers(0, 2, (C, D)).astype(np.uint8)
+    c[2] = c[1]
+    labels, dd = hdc.hamming_argmin(T(pack(q).view(np.int32)), T(pack(c).view(np.int32)), D, dists=True)
+    rows = np.arange(N) if C <= 32 else np.unique(np.r_[rng.integers(0, N, 3000), 0, N - 1])
+    od = orc.hamming(q[rows], c)
+    assert np.array_equal(dd.cpu().numpy()[rows].astype(np.int64), od)
+    assert np.array_equal(labels.cpu().numpy()[rows], orc.argmin(od))
+
+
 def test_hamming_argmin_tensor_core_many_tiles(hdc):
     """More 128-row tiles than SMs (the persistent loop), labels only."""
     rng = np.random.default_rng(11)
@@ -212,6 +230,24 @@ def test_train_many_classes_bit_exact(hdc):
     oacc, oups = orc.train(bits, y, C, 3)
     assert np.array_equal(acc.cpu().numpy().astype(np.int64), oacc)
     assert ups == oups
+
+
+@pytest.mark.parametrize("N,D,C", [(3000, 256, 3),      # ~1,000 samples a class: several counting items per group
+                                   (2400, 128, 600),    # retraining: 1,200 groups, offsets read from device memory
+                                   (2000, 64, 7000)])   # retraining: 14,000 groups, histogram in device memory
+def test_train_group_layouts_bit_exact(hdc, N, D, C):
+    """Bundling and retraining epochs across the grouping layouts: multi-chunk
+    groups, more groups than the counting kernel stages, more than the
+    histogram kernel counts in shared memory."""
+    rng = np.random.default_rng(N + C)
+    protos = rng.integers(0, 2, (C, D)).astype(np.uint8)
+    y = rng.integers(0, C, N).astype(np.int32)
+    bits = protos[y] ^ (rng.random((N, D)) < 0.45).astype(np.uint8)
+    acc, cls, ups = hdc.train(T(pack(bits).view(np.int32)), T(y), D, C, epochs=2)
+    oacc, oups = orc.train(bits, y, C, 2)
+    assert np.array_equal(acc.cpu().numpy().astype(np.int64), oacc)
+    assert ups == oups
+    assert min(oups) > 0
 
 
 def test_hamming_all_ties(hdc):
