@@ -329,6 +329,10 @@ def run_ours(a):
     torch.cuda.synchronize()
     el_e2e = timed_steps(torch, step_e2e, e2e_steps, stream)
     e2e_qps = world * B * e2e_steps / el_e2e
+    # the host link on this machine: one plain pinned copy of the same rows, so
+    # the e2e figure can be read against the copy bound it meets
+    el_copy = timed_steps(torch, lambda i: Xd.copy_(Xh, non_blocking=True), 3, stream)
+    h2d_gbs = 3 * B * w.F * 4 / el_copy / 1e9
 
     # roofline of the dominant kernel (fused tcgen05 encode + Hamming + arg-min)
     F, Dk = w.F, m_apx.Dk
@@ -368,7 +372,8 @@ def run_ours(a):
                      "kernel": "tc_encode_kernel (%s)" % ("classify" if fused else "encode"),
                      "peak_source": peak_src + " of measured", "kernel_ms": avg_k * 1e3,
                      "algorithmic_flops_per_launch": flops},
-        "e2e": {"value": e2e_qps, "unit": UNIT, "h2d_bytes_per_step": B * F * 4, "d2h_bytes_per_step": B * 4},
+        "e2e": {"value": e2e_qps, "unit": UNIT, "h2d_bytes_per_step": B * F * 4, "d2h_bytes_per_step": B * 4,
+                "h2d_copy_gbs": h2d_gbs, "frac_of_copy_bound": e2e_qps / world / (h2d_gbs * 1e9 / (F * 4))},
         "gpu_launches": (2 if fused else 3) * a.steps,   # quantise + fused, or + similarity / cosine
         "clocks": clocks,
         "exact": {"value": exact_qps, "unit": UNIT, "enc": "fp32 (FFMA)", "Dk": w.D,
