@@ -86,6 +86,21 @@ def test_argument_checks_without_gpu(lib):
     assert lib.hdc_selftest_wait(2000001, None) == 1
 
 
+@pytest.mark.parametrize("N,C", [(1, 1), (60000, 10), (100000, 100), (2000, 7000)])
+def test_train_workspace_covers_retraining_groups(lib, N, C):
+    """A retraining epoch groups each misclassified sample twice (true and
+    predicted class, 2C groups): the workspace holds N predictions, 2N
+    permutation entries and per-group histogram, offsets, first items and
+    cursors; one byte less is refused before anything is enqueued."""
+    n = ctypes.c_size_t()
+    assert lib.hdc_train_workspace_bytes(N, 1024, C, ctypes.byref(n)) == 0
+    G = 2 * C
+    assert n.value >= 4 * N + 4 * 2 * N + 4 * G + 4 * (G + 1) + 4 * (G + 1) + 4 * G
+    fake = ctypes.c_void_p(1 << 20)                      # aligned, never dereferenced: the size check comes first
+    assert lib.hdc_train_epoch(fake, fake, N, 1024, C, 1, fake, fake, None, fake, n.value - 1, None) == 3
+    assert lib.hdc_train_workspace_bytes(N, 0, C, ctypes.byref(n)) == 1
+
+
 def test_static_scratch_size_matches_header(lib):
     from paper_2606_26547_gb300 import hdc
     src = open(os.path.join(ROOT, "include", "hdc.h")).read()
