@@ -29,6 +29,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "bitslice.cuh"
 #include "hdc_internal.cuh"
 
 namespace hdc {
@@ -39,14 +40,6 @@ constexpr int LWC = 32;      // words per block (one per lane)
 constexpr int LWARPS = 8;
 // counter planes of weight 16, 32, ...: HP of them hold floor(F / 16) < 2^HP
 __host__ __device__ constexpr int hp_for(int F) { return F < 1024 ? 6 : 9; }
-
-__device__ __forceinline__ void csa(uint32_t &h, uint32_t &l, uint32_t a, uint32_t b, uint32_t c)
-{
-    // full adder per bit position: l = a ^ b ^ c (weight 1), h = majority
-    // (weight 2); each a single three-input logic operation
-    h = (a & b) | (a & c) | (b & c);
-    l = a ^ b ^ c;
-}
 
 __device__ __forceinline__ int quant_level(float x, float lo, float scale, int L)
 {
@@ -70,23 +63,7 @@ struct Counter {
 template <int HP>
 __device__ __forceinline__ void add16(Counter<HP> &k, const uint32_t (&r)[16])
 {
-    uint32_t a2, b2, a4, b4, a8, b8, e16;
-    csa(a2, k.c1, k.c1, r[0], r[1]);
-    csa(b2, k.c1, k.c1, r[2], r[3]);
-    csa(a4, k.c2, k.c2, a2, b2);
-    csa(a2, k.c1, k.c1, r[4], r[5]);
-    csa(b2, k.c1, k.c1, r[6], r[7]);
-    csa(b4, k.c2, k.c2, a2, b2);
-    csa(a8, k.c4, k.c4, a4, b4);
-    csa(a2, k.c1, k.c1, r[8], r[9]);
-    csa(b2, k.c1, k.c1, r[10], r[11]);
-    csa(a4, k.c2, k.c2, a2, b2);
-    csa(a2, k.c1, k.c1, r[12], r[13]);
-    csa(b2, k.c1, k.c1, r[14], r[15]);
-    csa(b4, k.c2, k.c2, a2, b2);
-    csa(b8, k.c4, k.c4, a4, b4);
-    csa(e16, k.c8, k.c8, a8, b8);
-    uint32_t c = e16;
+    uint32_t c = csa16(k.c1, k.c2, k.c4, k.c8, r);
 #pragma unroll
     for (int i = 0; i < HP; i++) {
         const uint32_t t = k.hp[i] & c;

@@ -12,9 +12,14 @@
 // class, sum_{n in S} (1 - 2 bit[n][d]) = |S| - 2 * count_{n in S} bit[n][d].
 // The samples are grouped by class with a counting sort (histogram, scan,
 // scatter of indices), then each thread counts the set bits of one 32-dim
-// word over a chunk of one class's samples, four dims per 32-bit add (byte
-// lanes, flushed every 255 rows), and adds |S| - 2*count to acc with one
-// atomic per (chunk, dim).  Integer sums: exact and independent of order.
+// word over a chunk of at most 252 of one class's samples: sixteen rows at a
+// time through a carry-save tree of 15 full adders (bit-sliced planes of
+// weight 1, 2, 4, 8, 32 dims per logic operation), whose weight-16 carry is
+// added four dims per 32-bit add into byte lanes; at the end of the chunk
+// count = 16 * carries + planes <= 255 per byte.  It then adds
+// |S| - 2*count to acc with one atomic per (chunk, dim).  Integer sums:
+// exact and independent of order.
+#include "bitslice.cuh"
 #include "hdc_internal.cuh"
 
 namespace hdc {
@@ -150,10 +155,11 @@ __global__ void __launch_bounds__(128, 8) segment_count_kernel(const uint32_t *_
             for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) s_rows[r - r0] = __ldg(perm + r);
             __syncthreads();
             if (word >= W) continue;
-            // CH <= 255: the byte lanes cannot overflow within one item
+            // CH <= 252: 16 * (carries <= 15) + (planes <= 15) fits a byte lane
             uint32_t lanes[8];
 #pragma unroll
             for (int j = 0; j < 8; j++) lanes[j] = 0;
+            uint32_t c1 = 0, c2 = 0, c4 = 0, c8 = 0;
             const int n = r1 - r0;
             // sixteen gathered row loads in flight per thread, and the next
             // sixteen issued before the current ones are counted: the pass is
@@ -171,11 +177,14 @@ __global__ void __launch_bounds__(128, 8) segment_count_kernel(const uint32_t *_
                     for (int u = 0; u < 16; u++)
                         nxt[u] = r + 16 + u < n ? __ldg(H + (int64_t)s_rows[r + 16 + u] * W + word) : 0u;
                 }
+                const uint32_t e16 = csa16(c1, c2, c4, c8, w);
 #pragma unroll
-                for (int u = 0; u < 16; u++)
-#pragma unroll
-                    for (int j = 0; j < 8; j++) lanes[j] += (w[u] >> j) & 0x01010101u;  // dims j, j+8, j+16, j+24
+                for (int j = 0; j < 8; j++) lanes[j] += (e16 >> j) & 0x01010101u;  // dims j, j+8, j+16, j+24
             }
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                lanes[j] = (lanes[j] << 4) + ((c1 >> j) & 0x01010101u) + (((c2 >> j) & 0x01010101u) << 1) +
+                           (((c4 >> j) & 0x01010101u) << 2) + (((c8 >> j) & 0x01010101u) << 3);
             int cnt[32];
 #pragma unroll
             for (int j = 0; j < 8; j++)
