@@ -250,6 +250,24 @@ def test_train_group_layouts_bit_exact(hdc, N, D, C):
     assert min(oups) > 0
 
 
+@pytest.mark.parametrize("fill", [1, 0])
+def test_train_saturated_chunks_bit_exact(hdc, fill):
+    """Every row of a class identical (all bits set, or none): a 252-sample
+    counting chunk reaches the largest per-dim count (16 carries of the
+    carry-save tree less one, plus a full residue: 252), and a class of 520
+    samples spans two full chunks and a partial one."""
+    rng = np.random.default_rng(520 + fill)
+    N, D, C = 600, 64, 2
+    y = np.r_[np.zeros(520, np.int32), np.ones(80, np.int32)]
+    rng.shuffle(y)
+    bits = rng.integers(0, 2, (N, D)).astype(np.uint8)
+    bits[y == 0] = fill
+    acc, cls, ups = hdc.train(T(pack(bits).view(np.int32)), T(y), D, C, epochs=2)
+    oacc, oups = orc.train(bits, y, C, 2)
+    assert np.array_equal(acc.cpu().numpy().astype(np.int64), oacc)
+    assert ups == oups
+
+
 def test_hamming_all_ties(hdc):
     q = np.zeros((40, 64), np.uint8)
     c = np.ones((5, 64), np.uint8)
