@@ -195,7 +195,12 @@ hdc_status hdc_hamming_argmin(const uint32_t *Q, const uint32_t *Cls,
                               const hdc_approx_config *cfg, int32_t *labels,
                               int32_t *dists, hdc_stream_t stream);
 
-/* Workspace bytes for hdc_train_epoch.                                     */
+/* Workspace bytes for hdc_train_epoch (about 12 N + 32 C bytes): the N
+ * predictions of a retraining epoch, a 2N-entry permutation grouping the
+ * samples (a misclassified sample sits in its true class's group and in its
+ * predicted class's), and per-group (2C) counts, offsets, first counting
+ * items and cursors.  HDC_ERR_INVALID_ARG for N < 0, D <= 0, C <= 0 or a
+ * NULL bytes.                                                              */
 hdc_status hdc_train_workspace_bytes(int64_t N, int32_t D, int32_t C,
                                      size_t *bytes);
 
@@ -209,7 +214,12 @@ hdc_status hdc_train_workspace_bytes(int64_t N, int32_t D, int32_t C,
  *         h = 1 - 2*bit (perceptron, applied once per epoch).
  * In both modes cls (C x W(D)) is then rewritten as the sign of acc.
  * n_updates (one int32, device, optional) receives the number of updates.
- * acc (C x D int32) must not overflow: |acc| < 2^31.                      */
+ * acc (C x D int32) must not overflow: |acc| < 2^31.  All pointers are
+ * caller-owned device memory: H and cls 16-byte aligned, ws (>=
+ * hdc_train_workspace_bytes(N, D, C), 256-byte aligned) scratch for this
+ * call only.  Errors: HDC_ERR_INVALID_ARG (sizes, mode, NULL or misaligned
+ * pointers), HDC_ERR_WORKSPACE (ws too small or misaligned), HDC_ERR_CUDA;
+ * nothing is enqueued on an argument error.                               */
 hdc_status hdc_train_epoch(const uint32_t *H, const int32_t *y, int64_t N,
                            int32_t D, int32_t C, int32_t mode, int32_t *acc,
                            uint32_t *cls, int32_t *n_updates, void *ws,
