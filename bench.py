@@ -12,8 +12,10 @@ arg-min -- quantise kernel + fused tcgen05 kernel per step.
 
 Also measured on the same GPU: the plain exact form (FP32 FFMA encode at the
 full D, packed Hamming), the accuracy of both on the 10,000-query set, an
-end-to-end figure through the same C-ABI call with pinned host buffers, and
-the CPU oracle on a bounded sample.  `--impl reference` times the CPU oracle
+end-to-end figure through the same C-ABI call with pinned host buffers (with
+the rate of one plain pinned copy of the same rows in the same run, the bound
+that figure meets), the bundling and retraining-epoch passes, and the CPU
+oracle on a bounded sample.  `--impl reference` times the CPU oracle
 alone on the host cores.
 
 Prints one JSON line (rank 0).
