@@ -200,7 +200,8 @@ hdc_status hdc_hamming_argmin(const uint32_t *Q, const uint32_t *Cls,
  * samples (a misclassified sample sits in its true class's group and in its
  * predicted class's), and per-group (2C) counts, offsets, first counting
  * items and cursors.  HDC_ERR_INVALID_ARG for N < 0, D <= 0, C <= 0 or a
- * NULL bytes.                                                              */
+ * NULL bytes; HDC_ERR_UNSUPPORTED for N > 2^30 - 1 or C > 2^28 (the
+ * grouping's int32 offsets cover 2N entries).                              */
 hdc_status hdc_train_workspace_bytes(int64_t N, int32_t D, int32_t C,
                                      size_t *bytes);
 
@@ -218,8 +219,9 @@ hdc_status hdc_train_workspace_bytes(int64_t N, int32_t D, int32_t C,
  * caller-owned device memory: H and cls 16-byte aligned, ws (>=
  * hdc_train_workspace_bytes(N, D, C), 256-byte aligned) scratch for this
  * call only.  Errors: HDC_ERR_INVALID_ARG (sizes, mode, NULL or misaligned
- * pointers), HDC_ERR_WORKSPACE (ws too small or misaligned), HDC_ERR_CUDA;
- * nothing is enqueued on an argument error.                               */
+ * pointers), HDC_ERR_UNSUPPORTED (N > 2^30 - 1 or C > 2^28),
+ * HDC_ERR_WORKSPACE (ws too small or misaligned), HDC_ERR_CUDA; nothing is
+ * enqueued on an argument error.                                          */
 hdc_status hdc_train_epoch(const uint32_t *H, const int32_t *y, int64_t N,
                            int32_t D, int32_t C, int32_t mode, int32_t *acc,
                            uint32_t *cls, int32_t *n_updates, void *ws,
@@ -364,7 +366,8 @@ hdc_status hdc_levelid_encode(const float *X, int64_t N, const hdc_levelid_model
  *            (enc is not used)
  *   ws       hdc_cluster_workspace_bytes(N, D, K) bytes, 256-byte aligned
  * Errors: HDC_ERR_INVALID_ARG (sizes, pointers, a perforation that keeps
- * nothing), HDC_ERR_WORKSPACE, HDC_ERR_CUDA.                               */
+ * nothing), HDC_ERR_UNSUPPORTED (N > 2^30 - 1 or K > 2^28, as training),
+ * HDC_ERR_WORKSPACE, HDC_ERR_CUDA.                                         */
 hdc_status hdc_cluster_workspace_bytes(int64_t N, int32_t D, int32_t K, size_t *bytes);
 hdc_status hdc_cluster(const uint32_t *H, int64_t N, int32_t D, int32_t K, int32_t iters,
                        const hdc_approx_config *train_sim, const hdc_approx_config *infer_sim,

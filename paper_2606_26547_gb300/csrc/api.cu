@@ -356,6 +356,7 @@ TrainLayout train_layout(int64_t N, int C)
 hdc_status hdc_train_workspace_bytes(int64_t N, int32_t D, int32_t C, size_t *bytes)
 {
     if (!bytes || N < 0 || D <= 0 || C <= 0) return HDC_ERR_INVALID_ARG;
+    if (N > kMaxTrainRows || C > kMaxTrainClasses) return HDC_ERR_UNSUPPORTED;
     *bytes = train_layout(N, C).total;
     return HDC_OK;
 }
@@ -367,6 +368,7 @@ hdc_status hdc_train_epoch(const uint32_t *H, const int32_t *y, int64_t N, int32
     if (N < 0 || D <= 0 || C <= 0 || (mode != 0 && mode != 1) || !acc || !cls || !aligned(cls, 16))
         return HDC_ERR_INVALID_ARG;
     if (N > 0 && (!H || !y || !aligned(H, 16))) return HDC_ERR_INVALID_ARG;
+    if (N > kMaxTrainRows || C > kMaxTrainClasses) return HDC_ERR_UNSUPPORTED;
     const int W = words_for(D);
     cudaStream_t st = (cudaStream_t)stream;
     const TrainLayout L = train_layout(N, C);

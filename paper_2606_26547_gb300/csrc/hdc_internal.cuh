@@ -11,6 +11,11 @@ namespace hdc {
 
 constexpr int kAlign = 256;  // alignment of every sub-buffer we carve
 
+// Training groups samples with int32 offsets over up to 2N entries (a
+// retraining epoch places a misclassified sample in two groups) and 2C groups.
+constexpr int64_t kMaxTrainRows = (int64_t(1) << 30) - 1;
+constexpr int kMaxTrainClasses = 1 << 28;
+
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Words per packed row of L dims: ceil(L/32) rounded up to a multiple of 4.

@@ -57,7 +57,9 @@ using namespace hdc;
 extern "C" hdc_status hdc_cluster_workspace_bytes(int64_t N, int32_t D, int32_t K, size_t *bytes)
 {
     ClusterLayout L;
-    if (!bytes || N < 0 || D <= 0 || K <= 0 || !cluster_layout(N, D, K, &L)) return HDC_ERR_INVALID_ARG;
+    if (!bytes || N < 0 || D <= 0 || K <= 0) return HDC_ERR_INVALID_ARG;
+    if (N > kMaxTrainRows || K > kMaxTrainClasses) return HDC_ERR_UNSUPPORTED;
+    if (!cluster_layout(N, D, K, &L)) return HDC_ERR_INVALID_ARG;
     *bytes = L.total;
     return HDC_OK;
 }
@@ -74,6 +76,7 @@ extern "C" hdc_status hdc_cluster(const uint32_t *H, int64_t N, int32_t D, int32
     if (hdc_kept_dims(D, train_sim) <= 0 || hdc_kept_dims(D, infer_sim) <= 0) return HDC_ERR_INVALID_ARG;
     if (N > 0 && (!H || ((uintptr_t)H % 16) != 0)) return HDC_ERR_INVALID_ARG;
     if (((uintptr_t)cls % 16) != 0) return HDC_ERR_INVALID_ARG;
+    if (N > kMaxTrainRows || K > kMaxTrainClasses) return HDC_ERR_UNSUPPORTED;
     ClusterLayout L;
     if (!cluster_layout(N, D, K, &L)) return HDC_ERR_INVALID_ARG;
     if (N > 0 && (!ws || ws_bytes < L.total || ((uintptr_t)ws % kAlign) != 0)) return HDC_ERR_WORKSPACE;

@@ -101,6 +101,21 @@ def test_train_workspace_covers_retraining_groups(lib, N, C):
     assert lib.hdc_train_workspace_bytes(N, 0, C, ctypes.byref(n)) == 1
 
 
+def test_training_size_limits_without_gpu(lib):
+    """Training and clustering group samples with int32 offsets over up to
+    2N entries: N > 2^30 - 1 or more than 2^28 classes is refused as
+    unsupported before anything is enqueued."""
+    n = ctypes.c_size_t()
+    big = 1 << 30
+    assert lib.hdc_train_workspace_bytes(big - 1, 64, 10, ctypes.byref(n)) == 0
+    assert lib.hdc_train_workspace_bytes(big, 64, 10, ctypes.byref(n)) == 2
+    assert lib.hdc_train_workspace_bytes(10, 64, (1 << 28) + 1, ctypes.byref(n)) == 2
+    fake = ctypes.c_void_p(1 << 20)                      # aligned, never dereferenced
+    assert lib.hdc_train_epoch(fake, fake, big, 64, 10, 1, fake, fake, None, fake, 1 << 40, None) == 2
+    assert lib.hdc_cluster_workspace_bytes(big, 64, 10, ctypes.byref(n)) == 2
+    assert lib.hdc_cluster(fake, big, 64, 10, 5, None, None, fake, fake, fake, None, fake, 1 << 40, None) == 2
+
+
 def test_static_scratch_size_matches_header(lib):
     from paper_2606_26547_gb300 import hdc
     src = open(os.path.join(ROOT, "include", "hdc.h")).read()
