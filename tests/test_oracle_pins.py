@@ -511,7 +511,8 @@ def test_nmi_definition():
 def _bf16_table():
     """Every finite BF16 value, ascending, with its bit pattern's parity."""
     bits = np.arange(0, 1 << 16, dtype=np.uint32)
-    vals = (bits << 16).view(np.float32).astype(np.float64)
+    with np.errstate(invalid="ignore"):                  # the NaN patterns, dropped just below
+        vals = (bits << 16).view(np.float32).astype(np.float64)
     ok = np.isfinite(vals)
     v, b = vals[ok], bits[ok]
     order = np.argsort(v, kind="stable")
