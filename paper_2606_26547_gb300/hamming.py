@@ -4,7 +4,9 @@ hypervectors at the shapes of the retraining and clustering passes.
 Up to 32 classes (and above 256) the distances are popcounts, bound by the
 popcount unit (about 16 results per clock per SM); 33..256 classes run as a
 tensor-core product of the rows expanded to +-1.  Reported per shape: time,
-queries/s and 32-dim word comparisons per second (N * C * W)."""
+queries/s, 32-dim word comparisons per second (N * C * W) and, on the
+popcount route, their fraction of 16 popcounts per clock per SM x the SMs x
+the maximum SM clock (a lower bound when the clock ran lower)."""
 from __future__ import annotations
 
 import json
@@ -12,6 +14,16 @@ import json
 import torch
 
 from . import hdc
+from .levelid import sm_clock_mhz
+
+POPC_PER_CLK_SM = 16
+
+
+def popcount_roofline(word_compares_per_s: float, sms: int, mhz: float) -> dict:
+    """Word comparisons per second against the popcount unit's peak."""
+    peak = POPC_PER_CLK_SM * sms * mhz * 1e6
+    return {"bound": "alu (popcount)", "achieved_per_s": word_compares_per_s, "peak_per_s": peak,
+            "frac": word_compares_per_s / peak, "sms": sms, "sm_max_mhz": mhz}
 
 
 def measure(N: int, D: int, C: int, reps: int = 10, seed: int = 0) -> dict:
@@ -39,9 +51,14 @@ def measure(N: int, D: int, C: int, reps: int = 10, seed: int = 0) -> dict:
     b.synchronize()
     ms = a.elapsed_time(b) / reps
     assert hdc.stream_status() == 0
-    return {"N": N, "D": D, "C": C, "W": W, "ms": round(ms, 4), "queries_per_s": N / (ms / 1e3),
-            "word_compares_per_s": N * C * W / (ms / 1e3),
-            "route": "tensor cores (rows expanded to +-1)" if 32 < C <= 256 else "popcount"}
+    tc = 32 < C <= 256
+    out = {"N": N, "D": D, "C": C, "W": W, "ms": round(ms, 4), "queries_per_s": N / (ms / 1e3),
+           "word_compares_per_s": N * C * W / (ms / 1e3),
+           "route": "tensor cores (rows expanded to +-1)" if tc else "popcount"}
+    if not tc:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        out["roofline"] = popcount_roofline(out["word_compares_per_s"], sms, sm_clock_mhz())
+    return out
 
 
 def main(argv=None):

@@ -1,6 +1,7 @@
-"""Host-side checks of the training throughput module's sample generator
-(no GPU): packed Bernoulli rows use the library's packed layout, keep pad
-bits zero and flip bits at the requested rate."""
+"""Host-side checks of the throughput modules (no GPU): the training
+module's packed Bernoulli rows use the library's packed layout, keep pad
+bits zero and flip bits at the requested rate; the Hamming module's popcount
+roofline arithmetic."""
 import numpy as np
 import pytest
 import torch
@@ -31,3 +32,11 @@ def test_packed_bernoulli_is_seeded():
         g.manual_seed(11)
         out.append(packed_bernoulli(100, 300, words_for(300), 0.3, g, torch.device("cpu")))
     assert torch.equal(out[0], out[1])
+
+
+def test_popcount_roofline_arithmetic():
+    """The Hamming module's popcount peak: 16 per clock per SM x SMs x clock."""
+    from paper_2606_26547_gb300.hamming import popcount_roofline
+    r = popcount_roofline(16 * 152 * 1e9, 152, 1000.0)
+    assert r["peak_per_s"] == 16 * 152 * 1000.0 * 1e6
+    assert abs(r["frac"] - 1.0) < 1e-12
