@@ -10,13 +10,22 @@ encoding with per-row power-of-two scales on the tensor cores, dimension
 perforation of stride 2 (D' = 5,000), binary class hypervectors, Hamming
 arg-min -- quantise kernel + fused tcgen05 kernel per step.
 
-Also measured on the same GPU: the plain exact form (FP32 FFMA encode at the
-full D, packed Hamming), the accuracy of both on the 10,000-query set, an
-end-to-end figure through the same C-ABI call with pinned host buffers (with
-the rate of one plain pinned copy of the same rows in the same run, the bound
-that figure meets), the bundling and retraining-epoch passes, and the CPU
-oracle on a bounded sample.  `--impl reference` times the CPU oracle
-alone on the host cores.
+Also measured on the same GPU, outside the timed region:
+  * the plain exact form (FP32 FFMA encode at the full D, packed Hamming);
+  * accuracy of both forms on the 10,000-query set, and on the calibrated
+    6-class mixture (F = 561, sigma 8.3, exact form near 0.87) where the
+    1-point loss budget is informative;
+  * the per-element score error of the BF16 and FP8 projections against
+    FP64 projections of the original FP32 inputs (FP64 GEMMs on the device);
+  * an end-to-end figure through the same C-ABI call with pinned host
+    buffers, beside a plain copy of the same rows in the same chunks and
+    streams (the bound it meets);
+  * the bundling and retraining-epoch passes, on the separable workload and
+    on 60,000 samples of the calibrated mixture (an epoch that updates);
+  * serving: continuous batching over three resident models under a Poisson
+    stream of 20,000 requests/s, p50/p99 latency;
+  * the CPU oracle on a bounded sample (all host cores, and one core).
+`--impl reference` times the CPU oracle alone on the host cores.
 
 Prints one JSON line (rank 0).
 """
@@ -56,62 +65,126 @@ def parse():
     ap.add_argument("--exact-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work of the oracle sample")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="measured window of the serving leg")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    """nvidia-smi samples every 200 ms while running (read-only query)."""
+    """Read-only samples of the SM clock, its maximum and the clock-event
+    (throttle) reasons of the GPU under test, taken every
+    `period` seconds on a background thread through NVML (the counters
+    nvidia-smi reports), so a timed region of tens of milliseconds still gets
+    many samples.  Falls back to `nvidia-smi -lms 200` when NVML cannot be
+    loaded.  Nothing is ever set."""
+    REASONS = ((0x4, "sw_power_cap"), (0x8, "hw_slowdown"), (0x20, "sw_thermal_slowdown"),
+               (0x40, "hw_thermal_slowdown"), (0x80, "hw_power_brake_slowdown"))
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.path = tempfile.mktemp(suffix=".csv")
-        self.proc = None
-        self.gpu = gpu_index
+    def __init__(self, device_index: int, period: float = 0.005):
+        self.dev, self.period = device_index, period
+        self.samples = []           # (time, sm MHz, max sm MHz, set of reasons)
         self.t0 = self.t1 = None
+        self.source = None
+        self._stop = False
+        self._thread = self._proc = None
+
+    def _uuid(self):
+        import torch
+        u = str(torch.cuda.get_device_properties(self.dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+
+    def _nvml(self):
+        import ctypes
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        if nv.nvmlDeviceGetHandleByUUID(self._uuid().encode(), ctypes.byref(h)) != 0:
+            raise OSError("no NVML handle for the device")
+        reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+
+        def sample():
+            nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk))       # NVML_CLOCK_SM
+            nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+            reasons(h, ctypes.byref(rs))
+            return (time.time(), float(clk.value), float(mx.value),
+                    {n for bit, n in self.REASONS if rs.value & bit})
+        sample()
+        return sample
 
     def start(self):
+        import threading
+        try:
+            sample = self._nvml()
+            self.source = "nvml every %.0f ms" % (self.period * 1e3)
+
+            def loop():
+                while not self._stop:
+                    self.samples.append(sample())
+                    time.sleep(self.period)
+            self._thread = threading.Thread(target=loop, daemon=True)
+            self._thread.start()
+        except Exception:
+            self._start_smi()
+
+    def _start_smi(self):
+        self.source = "nvidia-smi every 200 ms"
+        self.path = tempfile.mktemp(suffix=".csv")
         try:
             self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
-                                         stderr=subprocess.DEVNULL)
+            self._proc = subprocess.Popen(["nvidia-smi", "-i", self._uuid(), "--query-gpu=" + self.FIELDS,
+                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                          stderr=subprocess.DEVNULL)
         except Exception:
-            self.proc = None
+            self._proc = None
 
     def mark(self, which):
         setattr(self, which, time.time())
 
-    def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
+    def _read_smi(self):
+        self._proc.terminate()
         try:
-            self.proc.wait(5)
+            self._proc.wait(5)
         except Exception:
-            self.proc.kill()
+            self._proc.kill()
         self.f.close()
-        rows = []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 10:
                 continue
             try:
                 ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
-                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+                self.samples.append((ts, float(parts[2]), float(parts[3]),
+                                     {n for n, v in zip(names, parts[6:10]) if v.lower() == "active"}))
             except Exception:
                 continue
         os.unlink(self.path)
-        inside = [r for r in rows if self.t0 and self.t1 and self.t0 - 1 <= r[0] <= self.t1 + 1] or rows
+
+    def stop(self):
+        self._stop = True
+        if self._thread is not None:
+            self._thread.join(2)
+        elif self._proc is not None:
+            self._read_smi()
+        else:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock source"], "samples": 0}
+        slack = 0.0 if self._thread is not None else 1.0
+        inside = [r for r in self.samples if self.t0 and self.t1 and self.t0 - slack <= r[0] <= self.t1 + slack]
         if not inside:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({n for r in inside for n, v in zip(names, r[3]) if v.lower() == "active"})
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0,
+                    "source": self.source}
         return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
-                "reasons": reasons, "samples": len(inside)}
+                "sm_mhz_min": min(r[1] for r in inside),
+                "reasons": sorted(set().union(*(r[3] for r in inside))), "samples": len(inside),
+                "source": self.source}
 
 
 # --------------------------------------------------------------- helpers
@@ -206,6 +279,100 @@ def time_training(hdc, torch, H, y, D, C, reps=5):
     return out
 
 
+SCORE_TOL = {"bf16": 1e-2, "fp8": 6e-2}
+
+
+def score_error(hdc, torch, X, Bt, stride):
+    """Per-element error of the BF16 and FP8 projections (hdc_encode's
+    de-scaled scores) against FP64 projections of the original FP32 inputs,
+    relative to sum_f |x_f b_f| (the gate: <= 1e-2 for BF16, <= 6e-2 for
+    FP8).  The FP64 side is two FP64 GEMMs on the device (exact products,
+    sums rounded in FP64: far below the errors measured)."""
+    D = Bt.shape[0]
+    dims = torch.arange(0, D, stride, device=X.device)       # perforation (0, 1, stride)
+    Bk = Bt[dims].double()
+    Xd = X.double()
+    s = Xd @ Bk.T
+    A = Xd.abs() @ Bk.abs().T
+    out = {"rows": int(X.shape[0]), "dims": int(dims.numel()), "perforation": [0.0, 1.0, stride]}
+    for enc in ("bf16", "fp8"):
+        m = hdc.Model(Bt, hdc.ApproxConfig(enc=enc, perf_stride=stride))
+        _, S = hdc.encode(X, m, scores=True)
+        diff = S.double() - s
+        r = (diff.abs() / A).flatten()
+        k = max(1, r.numel() // 100)
+        out[enc] = {"max": float(r.max()), "p99": float(torch.topk(r, k).values.min()),
+                    "frob_rel": float(diff.norm() / s.norm()),
+                    "sign_flip_rate": float(((S < 0) != (s < 0)).double().mean()),
+                    "tol": SCORE_TOL[enc], "pass": bool(float(r.max()) <= SCORE_TOL[enc])}
+        del S, diff, r
+    return out
+
+
+def calibrated_accuracy(hdc, torch, dev, a):
+    """Exact vs approximate accuracy on the calibrated 6-class mixture
+    (F = 561, D = 10,000, sigma 8.3: the exact form lands near 0.87, so the
+    1-point budget is informative), trained with its 10 epochs."""
+    from paper_2606_26547_gb300 import synth
+    w = synth.WORKLOADS["sweep_F561_D10000_C6"]
+    data = synth.make(w)
+    Bt, acc, ups, _, H, _ = train_model(hdc, torch, data, dev, w.epochs)
+    del H
+    Xq = torch.from_numpy(data["Xq"]).to(dev)
+    yq = data["yq"]
+    m_ex = hdc.Model(Bt, hdc.ApproxConfig(enc="fp32"), acc=acc)
+    m_apx = hdc.Model(Bt, hdc.ApproxConfig(enc=a.enc, perf_stride=a.stride), acc=acc)
+    l_ex, l_apx = hdc.classify(Xq, m_ex).cpu().numpy(), hdc.classify(Xq, m_apx).cpu().numpy()
+    ae, aa = float((l_ex == yq).mean()), float((l_apx == yq).mean())
+    return {"workload": w.name, "sigma": w.sigma, "exact": ae, "approx": aa, "loss_pts": 100.0 * (ae - aa),
+            "label_agreement": float((l_ex == l_apx).mean()), "queries": int(yq.size),
+            "train": "bundling + %d retraining epochs on %d samples (FP32 encode)" % (w.epochs, w.n_train),
+            "train_updates": ups}
+
+
+def updating_epoch_passes(hdc, torch, dev, n=60000):
+    """Bundling and one retraining epoch over n packed samples of the
+    calibrated mixture, where an epoch from the bundle updates a sizeable
+    fraction of the samples."""
+    from paper_2606_26547_gb300 import synth
+    w = synth.WORKLOADS["sweep_F561_D10000_C6"]
+    data = synth.make(w, n_train=n, n_query=1)
+    Bt = torch.from_numpy(data["Bt"]).to(dev)
+    H = hdc.encode(torch.from_numpy(data["Xtr"]).to(dev), hdc.Model(Bt, hdc.ApproxConfig(enc="fp32")))
+    y = torch.from_numpy(data["ytr"]).to(dev)
+    out = time_training(hdc, torch, H, y, w.D, w.C)
+    out["shape"] = "%d x %d x %d (%s)" % (n, w.D, w.C, w.name)
+    return out
+
+
+def serving_leg(hdc, torch, dev, seconds, warmup=0.5, rate=20000.0):
+    """Continuous batching over the three resident serving models (BF16
+    encode, binary classes) under a seeded Poisson stream: p50/p99 latency
+    (arrival to completion), achieved against offered queries/s, and the
+    unbatched exact form (one request at a time, FP32 FFMA)."""
+    from paper_2606_26547_gb300 import serve
+    trained = serve.build_models(dev)
+    models = [hdc.Model(Bt, hdc.ApproxConfig(enc="bf16"), acc=acc) for (w, Bt, acc) in trained]
+    pools = serve.query_pools(trained, 1 << 16)
+    ex = serve.GpuExecutor(models, 4 << 30, 16384, 3)
+    sched = serve.Scheduler(ex, len(models), 16384, chunk=4096, slots=3)
+    t_arr, model, rows = serve.poisson_requests(rate, warmup + seconds, len(models), 4096, 1234)
+    for m in range(len(models)):
+        hdc.classify(pools[m][:256].to(dev), models[m])
+    torch.cuda.synchronize()
+    reqs, window, qrows = serve.run_open_loop(sched, pools, t_arr, model, rows, warmup)
+    st = serve.latency_stats(reqs)
+    offered = float(rows[t_arr >= warmup].sum()) / seconds
+    achieved = qrows / window
+    exact = serve.exact_unbatched_qps(trained, pools, t_arr, model, rows, n_req=200)
+    del ex
+    return {"rate_req_s": rate, "window_s": window, "models": [list(x) for x in serve.SERVING_MODELS],
+            "enc": "bf16", "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "requests": st["requests"], "offered_qps": offered, "achieved_qps": achieved,
+            "stable": bool(achieved >= 0.95 * offered), "batches": sched.n_batches,
+            "unbatched_exact_qps": exact, "unbatched_exact_stable": bool(exact >= offered)}
+
+
 def timed_steps(torch, fn, steps, stream):
     """Device time of `steps` calls of fn(i) between CUDA events."""
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -275,12 +442,11 @@ def run_ours(a):
         hdc.profile_events(*evs[i])
         hdc.classify(X, m_apx, ws=ws, labels=labels)
 
+    clk = ClockSampler(local)
+    clk.start()
     for i in range(a.warmup):
         step_apx(i)
     torch.cuda.synchronize()
-    clk = ClockSampler(local)
-    clk.start()
-    time.sleep(0.6)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -331,10 +497,25 @@ def run_ours(a):
     torch.cuda.synchronize()
     el_e2e = timed_steps(torch, step_e2e, e2e_steps, stream)
     e2e_qps = world * B * e2e_steps / el_e2e
-    # the host link on this machine: one plain pinned copy of the same rows, so
-    # the e2e figure can be read against the copy bound it meets
-    el_copy = timed_steps(torch, lambda i: Xd.copy_(Xh, non_blocking=True), 3, stream)
-    h2d_gbs = 3 * B * w.F * 4 / el_copy / 1e9
+
+    # the bound that figure meets: the same rows and labels copied in the
+    # same chunks on the same two streams, with no kernel between them
+    def step_copy(i):
+        for s in e2e_streams:
+            s.wait_stream(stream)
+        for c in range(nch):
+            lo, hi = bounds[c], bounds[c + 1]
+            with torch.cuda.stream(e2e_streams[c % 2]):
+                Xd[lo:hi].copy_(Xh[lo:hi], non_blocking=True)
+                Lh[lo:hi].copy_(labels[lo:hi], non_blocking=True)
+        for s in e2e_streams:
+            stream.wait_stream(s)
+
+    step_copy(0)
+    torch.cuda.synchronize()
+    el_copy = timed_steps(torch, step_copy, e2e_steps, stream)
+    copy_qps = B * e2e_steps / el_copy
+    h2d_gbs = B * w.F * 4 * e2e_steps / el_copy / 1e9
 
     # roofline of the dominant kernel (fused tcgen05 encode + Hamming + arg-min)
     F, Dk = w.F, m_apx.Dk
@@ -342,13 +523,18 @@ def run_ours(a):
     flops = 2.0 * B * F * Dk
     pk = peaks()
     ratio = 2.0 if a.enc == "fp8" else 1.0
-    if "bf16_tflops_sustained" in pk:
-        peak = pk["bf16_tflops_sustained"] * ratio
-        peak_src = "measured bf16 sustained x %.0f (nominal fp8/bf16 ratio)" % ratio if ratio != 1 else \
-            "measured bf16 sustained"
+    rtxt = " x %.0f (nominal fp8/bf16 ratio)" % ratio if ratio != 1 else ""
+    region_s = el
+    # the timed region is a burst (tens to hundreds of milliseconds): the
+    # burst matmul figure is its peak; the sustained one (seconds under the
+    # power cap, lower clocks) is reported beside it
+    if "bf16_tflops" in pk:
+        peak = pk["bf16_tflops"] * ratio
+        peak_src = "measured bf16 burst (cuBLAS 8192^3, best of 10)%s, of measured" % rtxt
     else:
-        peak = 1700.0 * ratio
-        peak_src = "fallback"
+        peak = 1900.0 * ratio
+        peak_src = "fallback bf16 burst 1.9 PFLOP/s%s, of fallback" % rtxt
+    peak_sus = pk.get("bf16_tflops_sustained", 1700.0) * ratio
     achieved = flops / avg_k / 1e12
     pt = PROFILED_TRAFFIC
     traffic = (pt["dram_bytes_per_query"] * B if tc_sources_sha() == pt["sources_sha1_16"] and a.enc == pt["enc"]
@@ -372,10 +558,18 @@ def run_ours(a):
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "tc_encode_kernel (%s)" % ("classify" if fused else "encode"),
-                     "peak_source": peak_src + " of measured", "kernel_ms": avg_k * 1e3,
-                     "algorithmic_flops_per_launch": flops},
+                     "peak_source": peak_src, "kernel_ms": avg_k * 1e3,
+                     "algorithmic_flops_per_launch": flops,
+                     "timed_region_ms": region_s * 1e3,
+                     "frac_vs_sustained": achieved / peak_sus,
+                     "clock_note": "burst peak measured with SM clocks up to %s MHz; sustained peak at a median "
+                                   "%s MHz under the power cap; this region's median %s MHz"
+                                   % (pk.get("sm_max_mhz"), pk.get("clocks_under_load", {}).get("sm_mhz_median"),
+                                      clocks.get("sm_mhz"))},
         "e2e": {"value": e2e_qps, "unit": UNIT, "h2d_bytes_per_step": B * F * 4, "d2h_bytes_per_step": B * 4,
-                "h2d_copy_gbs": h2d_gbs, "frac_of_copy_bound": e2e_qps / world / (h2d_gbs * 1e9 / (F * 4))},
+                "copy_only_qps": copy_qps * world, "h2d_copy_gbs": h2d_gbs,
+                "frac_of_copy_bound": e2e_qps / world / copy_qps,
+                "copy_bound": "the same rows and labels, %d chunks on 2 streams, copies only" % nch},
         "gpu_launches": (2 if fused else 3) * a.steps,   # quantise + fused, or + similarity / cosine
         "clocks": clocks,
         "exact": {"value": exact_qps, "unit": UNIT, "enc": "fp32 (FFMA)", "Dk": w.D,
@@ -386,17 +580,28 @@ def run_ours(a):
         "train_s": train_s, "train_updates": ups,
         "train_passes": dict(train_passes, hbm_peak_gbs=pk.get("hbm_gbs")),
     }
+    if rank == 0:
+        out["score_error"] = score_error(hdc, torch, Xq, Bt, a.stride)
+        out["accuracy_calibrated"] = calibrated_accuracy(hdc, torch, dev, a)
+        out["train_passes_updating"] = dict(updating_epoch_passes(hdc, torch, dev), hbm_peak_gbs=pk.get("hbm_gbs"))
+        if not a.no_serving:
+            out["serving"] = serving_leg(hdc, torch, dev, a.serve_seconds)
+        torch.cuda.synchronize()
+        assert hdc.stream_status() == 0
     if rank == 0 and world == 1 and not a.no_cpu_baseline and fused:   # the oracle sample times the binary path
         import oracle
         threads = os.cpu_count() or 1
         acc_np = acc.cpu().numpy().astype(np.int64)
-        qps, n, dt, olab = oracle_sample_qps(data, w, acc_np, {"bf16": 1, "fp8": 2}[a.enc], a.stride,
-                                             a.cpu_seconds, threads)
+        enc_code = {"bf16": 1, "fp8": 2}[a.enc]
+        qps, n, dt, olab = oracle_sample_qps(data, w, acc_np, enc_code, a.stride, a.cpu_seconds, threads)
+        qps1, n1, dt1, _ = oracle_sample_qps(data, w, acc_np, enc_code, a.stride, a.cpu_seconds / 3, 1)
         m = min(n, lab_apx.shape[0])
         out["cpu_baseline"] = {"value": qps, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "sample": "%d queries of the same mixture (the first %d are the accuracy set), "
                                          "same config, %.1f s" % (n, m, dt),
-                               "label_agreement_with_gpu": float((olab[:m] == lab_apx[:m]).mean())}
+                               "label_agreement_with_gpu": float((olab[:m] == lab_apx[:m]).mean()),
+                               "single_thread": {"value": qps1, "unit": UNIT, "cores": 1,
+                                                 "sample": "%d queries, %.1f s" % (n1, dt1)}}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -66,7 +66,8 @@ def _L():
                 "orc_hamming": (None, [P, i64, P, i64, i64, P]),
                 "orc_argmin_i64": (None, [P, i64, i64, P]),
                 "orc_argmax_f64": (None, [P, i64, i64, P]),
-                "orc_bundle": (None, [P, P, i64, i64, i64, P]),
+                "orc_bundle": (i64, [P, P, i64, i64, i64, P]),
+                "orc_acc_in_int32": (i32, [P, i64]),
                 "orc_class_bits": (None, [P, i64, i64, P]),
                 "orc_retrain_epoch": (i64, [P, P, i64, i64, i64, P]),
                 "orc_class_quantise": (None, [P, i64, i64, i32, P]),
@@ -147,9 +148,21 @@ def quantise_rows(X: np.ndarray, enc: int):
     return out, sc
 
 
-def encode_f64(X: np.ndarray, Bt: np.ndarray, dims: np.ndarray) -> np.ndarray:
+def _row_blocks(fn, X: np.ndarray, threads: int, *args) -> np.ndarray:
+    """fn(X[rows], *args) over a thread pool of row blocks, concatenated
+    (the C steps run without the GIL; the result does not depend on it)."""
+    if threads <= 1 or X.shape[0] <= 1:
+        return fn(X, *args)
+    idx = np.array_split(np.arange(X.shape[0]), min(threads, X.shape[0]))
+    with ThreadPoolExecutor(len(idx)) as ex:
+        return np.concatenate(list(ex.map(lambda r: fn(X[r], *args), idx)))
+
+
+def encode_f64(X: np.ndarray, Bt: np.ndarray, dims: np.ndarray, threads: int = 1) -> np.ndarray:
     X = _c(X, np.float64); Bt = _c(Bt, np.float64); dims = _c(dims, np.int64)
     assert X.shape[1] == Bt.shape[1]
+    if threads > 1:
+        return _row_blocks(encode_f64, X, threads, Bt, dims)
     s = np.empty((X.shape[0], dims.size), dtype=np.float64)
     _L().orc_encode_f64(_p(X), X.shape[0], X.shape[1], _p(Bt), _p(dims), dims.size, _p(s))
     return s
@@ -163,8 +176,10 @@ def encode_i64(X: np.ndarray, Bt: np.ndarray, dims: np.ndarray) -> np.ndarray:
     return s
 
 
-def encode_absdot(X: np.ndarray, Bt: np.ndarray, dims: np.ndarray) -> np.ndarray:
+def encode_absdot(X: np.ndarray, Bt: np.ndarray, dims: np.ndarray, threads: int = 1) -> np.ndarray:
     X = _c(X, np.float64); Bt = _c(Bt, np.float64); dims = _c(dims, np.int64)
+    if threads > 1:
+        return _row_blocks(encode_absdot, X, threads, Bt, dims)
     s = np.empty((X.shape[0], dims.size), dtype=np.float64)
     _L().orc_encode_absdot_f64(_p(X), X.shape[0], X.shape[1], _p(Bt), _p(dims), dims.size, _p(s))
     return s
@@ -203,10 +218,15 @@ def argmax(v: np.ndarray) -> np.ndarray:
     return out
 
 
+class AccumulatorOverflow(OverflowError):
+    """A class accumulator left the int32 range the library stores it in."""
+
+
 def bundle(bits: np.ndarray, y: np.ndarray, C: int) -> np.ndarray:
     bits = _c(bits, np.uint8); y = _c(y, np.int32)
     acc = np.empty((C, bits.shape[1]), dtype=np.int64)
-    _L().orc_bundle(_p(bits), _p(y), bits.shape[0], bits.shape[1], C, _p(acc))
+    if _L().orc_bundle(_p(bits), _p(y), bits.shape[0], bits.shape[1], C, _p(acc)) == -2:
+        raise AccumulatorOverflow("oracle bundling: an accumulator leaves the int32 range")
     return acc
 
 
@@ -222,6 +242,8 @@ def retrain_epoch(bits: np.ndarray, y: np.ndarray, acc: np.ndarray) -> int:
     bits = _c(bits, np.uint8); y = _c(y, np.int32)
     assert acc.dtype == np.int64 and acc.flags["C_CONTIGUOUS"]
     n = _L().orc_retrain_epoch(_p(bits), _p(y), bits.shape[0], bits.shape[1], acc.shape[0], _p(acc))
+    if n == -2:
+        raise AccumulatorOverflow("oracle retrain epoch: an accumulator leaves the int32 range")
     if n < 0:
         raise MemoryError("oracle retrain epoch: out of memory")
     return int(n)

@@ -269,11 +269,22 @@ void orc_argmax_f64(const double *v, int64_t N, int64_t C, int32_t *label)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Class accumulators are int32 in the library; the oracle sums in int64 and
+ * reports a result that int32 cannot hold.  Returns 1 when every entry lies
+ * in [-2^31, 2^31 - 1], else 0.                                           */
+int orc_acc_in_int32(const int64_t *acc, int64_t n)
+{
+    for (int64_t i = 0; i < n; i++)
+        if (acc[i] < -2147483648LL || acc[i] > 2147483647LL) return 0;
+    return 1;
+}
+
 /* Training by bundling (Sec. 2.1 training stage: same-class hypervectors are
  * added, then normalised).  acc[c][d] = sum over n with y_n = c of the +-1
- * element h[n][d] = 1 - 2*bit[n][d].  acc is overwritten.                  */
-void orc_bundle(const uint8_t *bits, const int32_t *y, int64_t N, int64_t D,
-                int64_t C, int64_t *acc)
+ * element h[n][d] = 1 - 2*bit[n][d].  acc is overwritten.  Returns 0, or
+ * -2 when an accumulator leaves the int32 range.                          */
+int64_t orc_bundle(const uint8_t *bits, const int32_t *y, int64_t N, int64_t D,
+                   int64_t C, int64_t *acc)
 {
     for (int64_t i = 0; i < C * D; i++) acc[i] = 0;
     for (int64_t n = 0; n < N; n++) {
@@ -282,6 +293,7 @@ void orc_bundle(const uint8_t *bits, const int32_t *y, int64_t N, int64_t D,
         for (int64_t d = 0; d < D; d++)
             acc[c * D + d] += 1 - 2 * (int64_t)bits[n * D + d];
     }
+    return orc_acc_in_int32(acc, C * D) ? 0 : -2;
 }
 
 /* Normalisation of a bundled class hypervector = its sign (our reading of
@@ -295,7 +307,9 @@ void orc_class_bits(const int64_t *acc, int64_t C, int64_t D, uint8_t *cbits)
  * reading, the paper names only the epoch count).  Every sample is first
  * classified with the class bits taken from acc at the start of the epoch
  * (Hamming arg-min over all D dimensions); then, for each misclassified n,
- * acc[y_n] += h_n and acc[pred_n] -= h_n.  Returns the number of updates.  */
+ * acc[y_n] += h_n and acc[pred_n] -= h_n.  Returns the number of updates,
+ * -1 when out of memory, or -2 when an accumulator leaves the int32 range
+ * (acc then holds the int64 result).                                       */
 int64_t orc_retrain_epoch(const uint8_t *bits, const int32_t *y, int64_t N,
                           int64_t D, int64_t C, int64_t *acc)
 {
@@ -320,7 +334,7 @@ int64_t orc_retrain_epoch(const uint8_t *bits, const int32_t *y, int64_t N,
         updates++;
     }
     free(cb); free(dist); free(pred);
-    return updates;
+    return orc_acc_in_int32(acc, C * D) ? updates : -2;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -245,6 +245,17 @@ class GpuExecutor:
         _, m, s = handle
         return self.stage_l[m][s][:rows].numpy().copy()
 
+    def status(self) -> int:
+        """Synchronise every slot stream and return the library's device
+        status (0, or the first error code: a bounded device wait that ran
+        out makes the labels of that run untrustworthy)."""
+        for row in self.streams:
+            for st in row:
+                rc = self.hdc.stream_status(st)
+                if rc != 0:
+                    return rc
+        return 0
+
 
 # ------------------------------------------------------------------ load
 
@@ -262,9 +273,15 @@ def poisson_requests(rate: float, duration: float, n_models: int, max_rows: int,
     return t, model, rows
 
 
+class DeviceStatusError(RuntimeError):
+    """The executor reported a device-side failure during a serving run."""
+
+
 def run_open_loop(sched: Scheduler, pools, t_arr, model, rows, warmup: float, clock=time.perf_counter):
     """Feed requests at their arrival times; returns (finished requests in
-    the measured window, window seconds, rows classified in it)."""
+    the measured window, window seconds, rows classified in it).  Once the
+    scheduler is idle the executor's device status is read (if it has one):
+    a failure raises DeviceStatusError instead of returning the run."""
     import gc
     gc.collect()
     gc.disable()          # a collection over ~10^5 live requests would stall the loop
@@ -285,6 +302,10 @@ def run_open_loop(sched: Scheduler, pools, t_arr, model, rows, warmup: float, cl
         end = clock() - t0
     finally:
         gc.enable()
+    status = getattr(sched.ex, "status", None)
+    rc = status() if status is not None else 0
+    if rc != 0:
+        raise DeviceStatusError("device status %d after the serving run: its results are not valid" % rc)
     meas = [r for r in sched.completed if r.t_arrive - t0 >= warmup]
     window = max(1e-9, end - warmup)
     return meas, window, sum(r.n for r in meas)

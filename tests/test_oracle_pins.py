@@ -156,6 +156,29 @@ def test_quantise_rows_fp8_in_table(orc):
     assert np.all(np.abs(rec - X)[big] <= np.abs(X)[big] * 2.0 ** -4 + 1e-30)
 
 
+def test_quantise_rows_dispatch_matches_torch_casts(orc):
+    """Each element type of quantise_rows on FP32 rows that are not
+    representable in BF16 or E4M3: BF16 = torch's CPU cast with scale 1, FP8 =
+    torch's cast of x / s with s the row's power-of-two scale, FP32 = the
+    input.  A swapped type code or a skipped rounding fails here."""
+    rng = np.random.default_rng(55)
+    X = (rng.standard_normal((24, 97)) * 10.0 ** rng.uniform(-6, 6, (24, 1))).astype(np.float32)
+    X[:, 0] = np.float32(1 + 2 ** -9)                 # between BF16 neighbours, and E4M3 ones
+    X[5] = 0.0
+    t = torch.from_numpy(X)
+    # most values are not representable in either format
+    assert (t.to(torch.bfloat16).to(torch.float32) != t).float().mean() > 0.9
+    q, sc = orc.quantise_rows(X, orc.ENC_BF16)
+    assert np.array_equal(q, t.to(torch.bfloat16).to(torch.float64).numpy()) and np.all(sc == 1.0)
+    q, sc = orc.quantise_rows(X, orc.ENC_FP8)
+    amax = np.abs(X.astype(np.float64)).max(1)
+    assert all(sc[i] == orc.pow2_scale(amax[i]) for i in range(24))
+    scaled = torch.from_numpy((X.astype(np.float64) / sc[:, None]).astype(np.float32))   # exact: s = 2^k
+    assert np.array_equal(q, scaled.to(torch.float8_e4m3fn).to(torch.float64).numpy())
+    q, sc = orc.quantise_rows(X, orc.ENC_FP32)
+    assert np.array_equal(q, X.astype(np.float64)) and np.all(sc == 1.0)
+
+
 # --------------------------------------------------------------- encoding
 
 def test_encode_int_matches_numpy(orc):
@@ -324,6 +347,27 @@ def test_retrain_converges_on_separable(orc):
     assert ups[-1] == 0
     frozen = acc.copy()
     assert orc.retrain_epoch(bits, y, acc) == 0 and np.array_equal(acc, frozen)
+
+
+def test_accumulators_checked_against_int32(orc):
+    """The library keeps class accumulators in int32: the oracle (int64)
+    refuses an epoch whose result int32 cannot hold, and accepts one that
+    ends exactly at the int32 limits."""
+    # class bits: class 0 = 0,1,0,0,0 and class 1 = 0,0,1,1,1.  Sample 0
+    # (class 0, bits 0,1,1,1,1) is 3 from class 0 and 1 from class 1, so it
+    # is misclassified and adds h = +1,-1,-1,-1,-1 to class 0; sample 1 equals
+    # class 1 and is right
+    bits = np.array([[0, 1, 1, 1, 1], [0, 0, 1, 1, 1]], np.uint8)
+    y = np.array([0, 1], np.int32)
+    over = np.array([[2 ** 31 - 1, -(2 ** 31), 5, 5, 5], [0, 0, -1, -1, -1]], np.int64)
+    with pytest.raises(orc.AccumulatorOverflow):
+        orc.retrain_epoch(bits, y, over)
+    ok = np.array([[2 ** 31 - 2, -(2 ** 31) + 1, 5, 5, 5], [0, 0, -1, -1, -1]], np.int64)
+    assert orc.retrain_epoch(bits, y, ok) == 1
+    assert ok[0].tolist() == [2 ** 31 - 1, -(2 ** 31), 4, 4, 4] and ok[1].tolist() == [-1, 1, 0, 0, 0]
+    assert orc._L().orc_acc_in_int32(orc._p(np.array([2 ** 31], np.int64)), 1) == 0
+    assert orc._L().orc_acc_in_int32(orc._p(np.array([-(2 ** 31) - 1], np.int64)), 1) == 0
+    assert orc._L().orc_acc_in_int32(orc._p(np.array([-(2 ** 31), 2 ** 31 - 1], np.int64)), 2) == 1
 
 
 # --------------------------------------------------------- class quantise

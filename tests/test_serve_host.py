@@ -101,3 +101,25 @@ def test_latency_stats():
         rs.append(r)
     st = serve.latency_stats(rs)
     assert abs(st["p50_ms"] - 50.5) < 1e-6 and st["requests"] == 100
+
+
+def test_open_loop_fails_on_device_status():
+    """A device-side failure reported by the executor after the run (e.g. a
+    bounded wait that ran out) fails the serving run instead of returning
+    its latencies."""
+    import pytest
+
+    class BadExec(FakeExec):
+        def status(self):
+            return 5
+
+    pools = [np.zeros((64, 3), np.float32)]
+    for ex, raises in ((FakeExec(10 ** 9), False), (BadExec(10 ** 9), True)):
+        s = serve.Scheduler(ex, 1, max_batch=64, chunk=64, slots=1)
+        t, m, r = np.array([0.0, 0.0]), np.array([0, 0]), np.array([3, 5])
+        if raises:
+            with pytest.raises(serve.DeviceStatusError):
+                serve.run_open_loop(s, pools, t, m, r, 0.0)
+        else:
+            reqs, _, rows = serve.run_open_loop(s, pools, t, m, r, 0.0)
+            assert rows == 8 and len(reqs) == 2
