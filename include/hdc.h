@@ -212,8 +212,14 @@ hdc_status hdc_train_workspace_bytes(int64_t N, int32_t D, int32_t C,
  *  mode 1 (retraining epoch, TRAIN_ITERATIONS): every sample is classified
  *         by Hamming arg-min against cls as it is on entry; then, for each
  *         misclassified n, acc[y_n] += h_n and acc[pred_n] -= h_n with
- *         h = 1 - 2*bit (perceptron, applied once per epoch).
- * In both modes cls (C x W(D)) is then rewritten as the sign of acc.
+ *         h = 1 - 2*bit (perceptron, applied once per epoch);
+ *  mode 2 (the retraining delta of one shard of the samples): as mode 1,
+ *         but acc is overwritten with the updates alone (acc = 0 plus the
+ *         +h_n / -h_n of this call's misclassified samples) and cls is left
+ *         as it is.  Shards that share the start-of-epoch cls and sum their
+ *         deltas (an integer all-reduce) reproduce mode 1 over all samples
+ *         exactly; hdc_train_apply then adds the sum and re-binarises.
+ * In modes 0 and 1 cls (C x W(D)) is then rewritten as the sign of acc.
  * n_updates (one int32, device, optional) receives the number of updates.
  * acc (C x D int32) must not overflow: |acc| < 2^31.  All pointers are
  * caller-owned device memory: H and cls 16-byte aligned, ws (>=
@@ -226,6 +232,19 @@ hdc_status hdc_train_epoch(const uint32_t *H, const int32_t *y, int64_t N,
                            int32_t D, int32_t C, int32_t mode, int32_t *acc,
                            uint32_t *cls, int32_t *n_updates, void *ws,
                            size_t ws_bytes, hdc_stream_t stream);
+
+/* The exchange step of training over sharded samples (Sec. 2.1 training;
+ * TRAIN_ITERATIONS epochs, each epoch's updates applied at once):
+ * acc[c][d] += delta[c][d] (skipped when delta is NULL), then cls (C x W(D))
+ * = pack(acc < 0), the sign of the bundle.  After per-shard bundles (mode 0)
+ * are summed into acc, delta = NULL binarises the sum; after per-shard
+ * deltas (mode 2) are summed into delta, this applies the epoch.  acc and
+ * delta are C x D int32 device arrays (|acc + delta| < 2^31), cls is device
+ * memory, 16-byte aligned.  Errors: HDC_ERR_INVALID_ARG (C <= 0, D <= 0,
+ * NULL acc or cls, misaligned cls), HDC_ERR_CUDA; nothing is enqueued on an
+ * argument error.                                                         */
+hdc_status hdc_train_apply(const int32_t *delta, int32_t C, int32_t D,
+                           int32_t *acc, uint32_t *cls, hdc_stream_t stream);
 
 /* Classify (Listing 1 end to end under the model's knobs):
  * labels[i] for X (N x F FP32).  class_bits 1: Hamming arg-min over K,
@@ -327,13 +346,15 @@ typedef struct {
 hdc_status hdc_levelid_model_bytes(int32_t F, int32_t D, int32_t L, const hdc_approx_config *cfg,
                                    size_t *bytes);
 
-/* Build a Level-ID model in buf.  Device inputs: id_bits (F x W(D) packed ID
- * hypervectors), lo_hv and hi_hv (W(D) words each), flip (D int32).  The
- * random hypervectors and flip levels are the caller's draws.  flip_error
+/* Build a Level-ID model in buf: the kept dims of the ID and level
+ * hypervectors, packed.  Device inputs, one byte per element (nonzero = the
+ * element -1, zero = +1): id_bits (F x D, row-major), lo_bits and hi_bits
+ * (D each, the two level end points); flip (D int32).  The random
+ * hypervectors and flip levels are the caller's draws.  flip_error
  * (optional device int32) is set to 1 if some flip[d] is outside 1..L-1.
  * Errors: HDC_ERR_INVALID_ARG (sizes, pointers, x_hi <= x_lo, non-finite
  * bounds), HDC_ERR_UNSUPPORTED (limits), HDC_ERR_WORKSPACE, HDC_ERR_CUDA. */
-hdc_status hdc_levelid_prepare(const uint32_t *id_bits, const uint32_t *lo_hv, const uint32_t *hi_hv,
+hdc_status hdc_levelid_prepare(const uint8_t *id_bits, const uint8_t *lo_bits, const uint8_t *hi_bits,
                                const int32_t *flip, int32_t F, int32_t D, int32_t L, float x_lo,
                                float x_hi, const hdc_approx_config *cfg, void *buf, size_t buf_bytes,
                                int32_t *flip_error, hdc_levelid_model *out, hdc_stream_t stream);

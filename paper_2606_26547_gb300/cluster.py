@@ -4,7 +4,9 @@ over the binary hypervectors (hdc_cluster), score the clusters by NMI.
 Knobs: element type of the encoding, dimensionality D' (first D' rows of
 the base hypermatrix), TRAIN_ITERATIONS (K-means iterations), and the two
 independently perforated similarity ops (assignment during training,
-final assignment at inference)."""
+final assignment at inference).  graph_ms times a configuration as one CUDA
+graph (the tuner's application time); bench_kernels.py's `cluster`
+subcommand reports a set of configurations."""
 from __future__ import annotations
 
 import dataclasses
@@ -25,7 +27,8 @@ class ClusterConfig:
     infer_perf: tuple = (0.0, 1.0, 1)
 
 
-def _sim(p):
+def sim_config(p):
+    """The perforation (start, end, stride) of a similarity op as a config."""
     return hdc.ApproxConfig(perf_start=p[0], perf_end=p[1], perf_stride=p[2])
 
 
@@ -58,7 +61,7 @@ class ClusterRun:
         if timed:
             ev[1].record()
         init = H[self.init_idx].contiguous()
-        lab, cls, acc, changes = hdc.cluster(H, c.dim, init, c.iters, _sim(c.train_perf), _sim(c.infer_perf))
+        lab, cls, acc, changes = hdc.cluster(H, c.dim, init, c.iters, sim_config(c.train_perf), sim_config(c.infer_perf))
         if timed:
             ev[2].record()
         lab = lab.cpu().numpy()
@@ -68,18 +71,10 @@ class ClusterRun:
             out["cluster_ms"] = ev[1].elapsed_time(ev[2])
         return out
 
-    def time_ms(self, c: ClusterConfig, reps: int = 5) -> float:
-        """Eager encode + cluster (one launch sequence per call)."""
-        self.run(c)
-        ts = []
-        for _ in range(reps):
-            r = self.run(c, timed=True)
-            ts.append(r["encode_ms"] + r["cluster_ms"])
-        return float(np.median(ts))
-
     def graph_ms(self, c: ClusterConfig, reps: int = 20):
         """Encode + cluster captured in one CUDA graph (the per-iteration
-        launches then cost no host time); returns (ms per replay, NMI)."""
+        launches then cost no host time): the tuner's application time for
+        a clustering configuration.  Returns (ms per replay, NMI)."""
         m, ws = self.model(c.enc, c.dim)
         self.run(c)   # warm-up: lazy module loads and kernel attributes
         torch.cuda.synchronize()
@@ -90,7 +85,8 @@ class ClusterRun:
             with torch.cuda.graph(g, stream=s):
                 H = hdc.encode(self.X, m, ws=ws)
                 init = H[self.init_idx].contiguous()
-                lab, _, _, _ = hdc.cluster(H, c.dim, init, c.iters, _sim(c.train_perf), _sim(c.infer_perf))
+                lab, _, _, _ = hdc.cluster(H, c.dim, init, c.iters, sim_config(c.train_perf),
+                                           sim_config(c.infer_perf))
         torch.cuda.current_stream().wait_stream(s)
         g.replay()
         torch.cuda.synchronize()
@@ -101,28 +97,3 @@ class ClusterRun:
         b.record()
         b.synchronize()
         return a.elapsed_time(b) / reps, metrics.nmi(self.y, lab.cpu().numpy())
-
-
-def main(argv=None):
-    import argparse
-    ap = argparse.ArgumentParser(description="HD-Clustering on the GPU")
-    ap.add_argument("--workload", default="cluster_F617_D1024_K26")
-    a = ap.parse_args(argv)
-    hdc.load()
-    cr = ClusterRun(a.workload)
-    w = cr.w
-    rows = []
-    for c in (ClusterConfig("fp32", w.D, w.epochs), ClusterConfig("fp8", w.D, w.epochs),
-              ClusterConfig("fp8", w.D, 3), ClusterConfig("fp8", w.D, 3, infer_perf=(0.0, 0.9, 1)),
-              ClusterConfig("fp8", w.D, 3, train_perf=(0.0, 0.5, 1), infer_perf=(0.0, 0.9, 1)),
-              ClusterConfig("fp8", w.D // 2, 3)):
-        r = cr.run(c)
-        gms, gnmi = cr.graph_ms(c)
-        assert gnmi == r["nmi"]
-        rows.append({**dataclasses.asdict(c), "nmi": round(r["nmi"], 4), "ms": round(cr.time_ms(c), 4),
-                     "graph_ms": round(gms, 4), "changes_last": r["changes"][-1:]})
-    print(json.dumps({"workload": w.name, "points": int(cr.X.shape[0]), "K": w.C, "configs": rows}))
-
-
-if __name__ == "__main__":
-    main()

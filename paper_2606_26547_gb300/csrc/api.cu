@@ -365,7 +365,7 @@ hdc_status hdc_train_epoch(const uint32_t *H, const int32_t *y, int64_t N, int32
                            int32_t *acc, uint32_t *cls, int32_t *n_updates, void *ws, size_t ws_bytes,
                            hdc_stream_t stream)
 {
-    if (N < 0 || D <= 0 || C <= 0 || (mode != 0 && mode != 1) || !acc || !cls || !aligned(cls, 16))
+    if (N < 0 || D <= 0 || C <= 0 || mode < 0 || mode > 2 || !acc || !cls || !aligned(cls, 16))
         return HDC_ERR_INVALID_ARG;
     if (N > 0 && (!H || !y || !aligned(H, 16))) return HDC_ERR_INVALID_ARG;
     if (N > kMaxTrainRows || C > kMaxTrainClasses) return HDC_ERR_UNSUPPORTED;
@@ -380,10 +380,13 @@ hdc_status hdc_train_epoch(const uint32_t *H, const int32_t *y, int64_t N, int32
         hdc_status s = cu(cudaMemsetAsync(n_updates, 0, sizeof(int32_t), st));
         if (s != HDC_OK) return s;
     }
-    if (mode == 0) {
+    if (mode == 0 || mode == 2) {
+        // bundling, or a shard's retraining delta: acc starts from zero
         hdc_status s = cu(cudaMemsetAsync(acc, 0, (size_t)C * D * sizeof(int32_t), st));
         if (s != HDC_OK) return s;
-        s = cu(launch_train_count(H, W, y, nullptr, N, D, C, 0, acc, nullptr, sc, st));
+    }
+    if (mode == 0) {
+        hdc_status s = cu(launch_train_count(H, W, y, nullptr, N, D, C, 0, acc, nullptr, sc, st));
         if (s != HDC_OK) return s;
     } else if (N > 0) {
         int32_t *pred = (int32_t *)(w + L.pred);
@@ -393,7 +396,15 @@ hdc_status hdc_train_epoch(const uint32_t *H, const int32_t *y, int64_t N, int32
         s = cu(launch_train_count(H, W, y, pred, N, D, C, 1, acc, n_updates, sc, st));
         if (s != HDC_OK) return s;
     }
+    if (mode == 2) return HDC_OK;   // the delta alone: cls stays the start-of-epoch classes
     return cu(launch_binarise(acc, C, D, cls, W, st));
+}
+
+hdc_status hdc_train_apply(const int32_t *delta, int32_t C, int32_t D, int32_t *acc, uint32_t *cls,
+                           hdc_stream_t stream)
+{
+    if (C <= 0 || D <= 0 || !acc || !cls || !aligned(cls, 16)) return HDC_ERR_INVALID_ARG;
+    return cu(launch_apply_binarise(delta, acc, C, D, cls, words_for(D), (cudaStream_t)stream));
 }
 
 hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *labels, int32_t *dists,

@@ -97,6 +97,10 @@ cudaError_t launch_train_count(const uint32_t *H, int W, const int32_t *y, const
 
 // K6 (binary): cls[c] = pack(acc[c] < 0) over D dims, W words per row.
 cudaError_t launch_binarise(const int32_t *acc, int C, int D, uint32_t *cls, int W, cudaStream_t st);
+// K6 with the exchange step of sharded training: acc += delta (delta may be
+// NULL), then cls = pack(acc < 0).
+cudaError_t launch_apply_binarise(const int32_t *delta, int32_t *acc, int C, int D, uint32_t *cls, int W,
+                                  cudaStream_t st);
 
 // Tensor-core (tcgen05) encode, fused with Hamming / cosine and arg-min.
 // Returns cudaErrorNotSupported when the shape is outside what it handles.

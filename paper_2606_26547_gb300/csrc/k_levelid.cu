@@ -200,12 +200,14 @@ __global__ void __launch_bounds__(LWARPS * 32) levelid_encode_kernel(const float
     }
 }
 
-// Model preparation: one thread per output word of the compacted rows.
-//   rows [0, F):      ID row f, kept dims gathered from id_bits (W(D) words per row)
+// Model preparation: one thread per output word of the compacted rows,
+// packing the caller's unpacked bytes (nonzero = the element -1) of the
+// kept dims d = s0 + k*stride.
+//   rows [0, F):      ID row f (id_bits: F x D bytes)
 //   rows [F, F + L):  level l, bit d = l >= flip[d] ? hi[d] : lo[d]
-__global__ void levelid_prepare_kernel(const uint32_t *__restrict__ id_bits, const uint32_t *__restrict__ lo_hv,
-                                       const uint32_t *__restrict__ hi_hv, const int32_t *__restrict__ flip, int F,
-                                       int L, int WD, int64_t s0, int64_t stride, int64_t Dk, int Wk,
+__global__ void levelid_prepare_kernel(const uint8_t *__restrict__ id_bits, const uint8_t *__restrict__ lo_bits,
+                                       const uint8_t *__restrict__ hi_bits, const int32_t *__restrict__ flip, int F,
+                                       int L, int64_t D, int64_t s0, int64_t stride, int64_t Dk, int Wk,
                                        uint32_t *__restrict__ id, uint32_t *__restrict__ lv)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -216,15 +218,14 @@ __global__ void levelid_prepare_kernel(const uint32_t *__restrict__ id_bits, con
         const int64_t k = (int64_t)kw * 32 + j;
         if (k >= Dk) break;
         const int64_t d = s0 + k * stride;
-        uint32_t bit;
+        uint8_t b;
         if (r < F) {
-            bit = (id_bits[(int64_t)r * WD + (d >> 5)] >> (d & 31)) & 1u;
+            b = id_bits[(int64_t)r * D + d];
         } else {
             const int l = r - F;
-            const uint32_t *src = l >= flip[d] ? hi_hv : lo_hv;
-            bit = (src[d >> 5] >> (d & 31)) & 1u;
+            b = l >= flip[d] ? hi_bits[d] : lo_bits[d];
         }
-        word |= bit << j;
+        word |= (uint32_t)(b != 0) << j;
     }
     if (r < F) id[(int64_t)r * Wk + kw] = word;
     else lv[(int64_t)(r - F) * Wk + kw] = word;
@@ -269,7 +270,7 @@ extern "C" hdc_status hdc_levelid_model_bytes(int32_t F, int32_t D, int32_t L, c
     return HDC_OK;
 }
 
-extern "C" hdc_status hdc_levelid_prepare(const uint32_t *id_bits, const uint32_t *lo_hv, const uint32_t *hi_hv,
+extern "C" hdc_status hdc_levelid_prepare(const uint8_t *id_bits, const uint8_t *lo_bits, const uint8_t *hi_bits,
                                           const int32_t *flip, int32_t F, int32_t D, int32_t L, float x_lo,
                                           float x_hi, const hdc_approx_config *cfg, void *buf, size_t buf_bytes,
                                           int32_t *flip_error, hdc_levelid_model *out, hdc_stream_t stream)
@@ -277,7 +278,7 @@ extern "C" hdc_status hdc_levelid_prepare(const uint32_t *id_bits, const uint32_
     size_t need = 0;
     hdc_status s = hdc_levelid_model_bytes(F, D, L, cfg, &need);
     if (s != HDC_OK) return s;
-    if (!id_bits || !lo_hv || !hi_hv || !flip || !out || !buf || ((uintptr_t)buf % kAlign) != 0 ||
+    if (!id_bits || !lo_bits || !hi_bits || !flip || !out || !buf || ((uintptr_t)buf % kAlign) != 0 ||
         !(x_hi > x_lo) || !std::isfinite(x_lo) || !std::isfinite(x_hi))
         return HDC_ERR_INVALID_ARG;
     if (buf_bytes < need) return HDC_ERR_WORKSPACE;
@@ -294,7 +295,7 @@ extern "C" hdc_status hdc_levelid_prepare(const uint32_t *id_bits, const uint32_
     }
     const int64_t n = (int64_t)(F + L) * Wk;
     levelid_prepare_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-        id_bits, lo_hv, hi_hv, flip, F, L, words_for(D), p.s0, p.stride, p.Dk, Wk, (uint32_t *)(b + Ly.id),
+        id_bits, lo_bits, hi_bits, flip, F, L, (int64_t)D, p.s0, p.stride, p.Dk, Wk, (uint32_t *)(b + Ly.id),
         (uint32_t *)(b + Ly.lv));
     if (cudaGetLastError() != cudaSuccess) return HDC_ERR_CUDA;
     hdc_levelid_model m;

@@ -199,15 +199,26 @@ __global__ void __launch_bounds__(128, 8) segment_count_kernel(const uint32_t *_
     }
 }
 
-// One warp per (class, word): ballot of acc < 0 over the word's 32 dims.
-__global__ void binarise_kernel(const int32_t *__restrict__ acc, int C, int D, uint32_t *__restrict__ cls, int W)
+// One warp per (class, word): ballot of acc < 0 over the word's 32 dims,
+// after adding delta (the summed shard updates of an epoch) when given.
+__global__ void binarise_kernel(int32_t *__restrict__ acc, const int32_t *__restrict__ delta, int C, int D,
+                                uint32_t *__restrict__ cls, int W)
 {
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (gw >= (int64_t)C * W) return;
     const int c = (int)(gw / W), w = (int)(gw % W);
     const int d = w * 32 + lane;
-    const bool neg = d < D && acc[(int64_t)c * D + d] < 0;
+    bool neg = false;
+    if (d < D) {
+        const int64_t i = (int64_t)c * D + d;
+        int32_t v = acc[i];
+        if (delta) {
+            v += delta[i];
+            acc[i] = v;
+        }
+        neg = v < 0;
+    }
     const unsigned b = __ballot_sync(0xffffffffu, neg);
     if (lane == 0) cls[gw] = b;
 }
@@ -262,13 +273,20 @@ cudaError_t launch_train_count(const uint32_t *H, int W, const int32_t *y, const
     return group_and_count(H, W, y, pred, N, D, C, mode, acc, mode == 0 ? nullptr : n_updates, s, st);
 }
 
-cudaError_t launch_binarise(const int32_t *acc, int C, int D, uint32_t *cls, int W, cudaStream_t st)
+cudaError_t launch_apply_binarise(const int32_t *delta, int32_t *acc, int C, int D, uint32_t *cls, int W,
+                                  cudaStream_t st)
 {
     const int64_t warps = (int64_t)C * W;
     if (warps <= 0) return cudaSuccess;
     const int64_t blocks = (warps * 32 + 255) / 256;
-    binarise_kernel<<<(unsigned)blocks, 256, 0, st>>>(acc, C, D, cls, W);
+    binarise_kernel<<<(unsigned)blocks, 256, 0, st>>>(acc, delta, C, D, cls, W);
     return cudaGetLastError();
+}
+
+cudaError_t launch_binarise(const int32_t *acc, int C, int D, uint32_t *cls, int W, cudaStream_t st)
+{
+    // without a delta the kernel only reads acc
+    return launch_apply_binarise(nullptr, const_cast<int32_t *>(acc), C, D, cls, W, st);
 }
 
 }  // namespace hdc

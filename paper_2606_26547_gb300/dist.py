@@ -10,8 +10,11 @@ one all-reduce per epoch.  Retraining is epoch-synchronous (predictions use
 the class hypervectors from the start of the epoch), so the sharded result
 equals the single-process one exactly: integer sums do not depend on order.
 
-The local compute is passed in (the GPU kernels in production, the CPU
-oracle in the host-side tests), so this module holds only the exchange.
+`sharded_train` takes the local compute as callables (the CPU oracle in the
+host-side tests); `gpu_sharded_train` is the same schedule on the library's
+kernels: hdc_train_epoch mode 0 (a shard's bundle) and mode 2 (a shard's
+retraining delta against the shared start-of-epoch classes), an int32
+all-reduce of each, and hdc_train_apply (add the summed delta, re-binarise).
 """
 from __future__ import annotations
 
@@ -68,3 +71,31 @@ def sharded_train(bits_local, y_local, C: int, epochs: int, bundle, retrain_delt
         acc += delta
         updates.append(int(n.item()))
     return acc, updates
+
+
+def gpu_sharded_train(H_local: torch.Tensor, y_local: torch.Tensor, D: int, C: int, epochs: int,
+                      stream=None, exchange=allreduce_sum_):
+    """Bundling + `epochs` retraining epochs of this rank's packed samples
+    (H_local: n x W(D) int32 words, y_local: n int32) on the GPU kernels,
+    with one integer all-reduce (`exchange`, in place, over device tensors)
+    of the bundle and of every epoch's delta.  Every rank ends with the same
+    acc (C x D int32) and class words (C x W(D)), equal to single-process
+    training on all samples; returns (acc, cls, per-epoch update counts)."""
+    from . import hdc
+    dev = H_local.device
+    acc = torch.empty((C, D), dtype=torch.int32, device=dev)
+    cls = torch.empty((C, hdc.words(D)), dtype=torch.int32, device=dev)
+    ws = hdc.train_workspace(max(H_local.shape[0], 1), D, C, dev)
+    hdc.train_epoch(H_local, y_local, D, C, 0, acc, cls, ws=ws, stream=stream)
+    exchange(acc)
+    hdc.train_apply(acc, cls, stream=stream)
+    delta = torch.empty_like(acc)
+    nu = torch.zeros(1, dtype=torch.int32, device=dev)
+    ups = []
+    for _ in range(epochs):
+        hdc.train_epoch(H_local, y_local, D, C, 2, delta, cls, n_updates=nu, ws=ws, stream=stream)
+        exchange(delta)
+        exchange(nu)
+        hdc.train_apply(acc, cls, delta=delta, stream=stream)
+        ups.append(int(nu.item()))
+    return acc, cls, ups

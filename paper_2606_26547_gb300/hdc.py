@@ -59,6 +59,7 @@ _SIGS = {
     "hdc_hamming_argmin": (_I32, [_P, _P, _I64, _I32, _I32, _P, _P, _P, _P]),
     "hdc_train_workspace_bytes": (_I32, [_I64, _I32, _I32, _P]),
     "hdc_train_epoch": (_I32, [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
+    "hdc_train_apply": (_I32, [_P, _I32, _I32, _P, _P, _P]),
     "hdc_classify": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _SZ, _P]),
     "hdc_classify_static": (_I32, [_P, _I64, _P, _P, _P, _P, _P]),
     "hdc_classify_host": (_I32, [_P, _P, _I32, _P, _P, _P, _P, _P, _SZ, _P]),
@@ -236,12 +237,21 @@ def train_workspace(N: int, D: int, C: int, device) -> torch.Tensor:
 def train_epoch(H: torch.Tensor, y: torch.Tensor, D: int, C: int, mode: int, acc: torch.Tensor,
                 cls: torch.Tensor, n_updates: torch.Tensor | None = None, ws: torch.Tensor | None = None,
                 stream=None) -> None:
-    """One bundling (mode 0) or retraining (mode 1) pass; updates acc and cls."""
+    """One bundling (mode 0) or retraining (mode 1) pass, updating acc and
+    cls; mode 2 writes this shard's retraining delta to acc and leaves cls."""
     N = H.shape[0]
     if ws is None:
         ws = train_workspace(N, D, C, H.device)
     _call("hdc_train_epoch", _ptr(H), _ptr(y), N, D, C, mode, _ptr(acc), _ptr(cls), _ptr(n_updates),
           _ptr(ws), ws.numel(), _stream(stream))
+
+
+def train_apply(acc: torch.Tensor, cls: torch.Tensor, delta: torch.Tensor | None = None, stream=None) -> None:
+    """hdc_train_apply: acc += delta (if given), then cls = sign of acc."""
+    C, D = acc.shape
+    assert acc.dtype == torch.int32 and cls.shape == (C, words(D))
+    assert delta is None or (delta.shape == acc.shape and delta.dtype == torch.int32)
+    _call("hdc_train_apply", _ptr(delta), C, D, _ptr(acc), _ptr(cls), _stream(stream))
 
 
 def train(H: torch.Tensor, y: torch.Tensor, D: int, C: int, epochs: int, stream=None):
@@ -403,30 +413,19 @@ class LevelIdModelC(ctypes.Structure):
                 ("scale", ctypes.c_float), ("id", ctypes.c_void_p), ("level", ctypes.c_void_p)]
 
 
-def pack_bits(bits) -> torch.Tensor:
-    """Unpacked 0/1 rows (n x L, uint8 or bool tensor) -> packed int32 words
-    (n x hdc_words(L)), bit d of a row in word d // 32, bit d % 32."""
-    bits = torch.as_tensor(bits)
-    n, L = bits.shape
-    W = words(L)
-    padded = torch.zeros((n, W * 32), dtype=torch.int64, device=bits.device)
-    padded[:, :L] = bits.to(torch.int64)
-    weights = (torch.ones(32, dtype=torch.int64, device=bits.device) << torch.arange(32, device=bits.device))
-    w = (padded.view(n, W, 32) * weights).sum(-1)
-    return (w - ((w >> 31) << 32)).to(torch.int32)    # two's-complement view of the uint32 word
-
-
 class LevelIdModel:
     """Level-ID encoder (hdc_levelid_prepare): ID hypervectors (F x D bits),
-    level end points lo / hi (D bits each) and flip levels (D, in 1..L-1),
-    all device tensors of the caller's draws."""
+    level end points lo / hi (D bits each), one uint8 or bool element per
+    dim (1 = the element -1), and flip levels (D, in 1..L-1), all device
+    tensors of the caller's draws."""
 
     def __init__(self, id_bits: torch.Tensor, lo_bits: torch.Tensor, hi_bits: torch.Tensor, flip: torch.Tensor,
                  L: int, x_lo: float, x_hi: float, cfg: ApproxConfig | None = None, stream=None):
         F, D = id_bits.shape
-        self.idp = pack_bits(id_bits)
-        self.lop = pack_bits(lo_bits.view(1, -1))
-        self.hip = pack_bits(hi_bits.view(1, -1))
+        assert lo_bits.numel() == D and hi_bits.numel() == D and flip.numel() == D
+        self.idb = id_bits.to(torch.uint8).contiguous()
+        self.lob = lo_bits.to(torch.uint8).contiguous()
+        self.hib = hi_bits.to(torch.uint8).contiguous()
         self.flip = flip.to(torch.int32).contiguous()
         c = cfg.c() if cfg else None
         n = ctypes.c_size_t()
@@ -434,7 +433,7 @@ class LevelIdModel:
         self.buf = _empty_bytes(n.value, id_bits.device)
         self.flip_error = torch.zeros(1, dtype=torch.int32, device=id_bits.device)
         self.m = LevelIdModelC()
-        _call("hdc_levelid_prepare", _ptr(self.idp), _ptr(self.lop), _ptr(self.hip), _ptr(self.flip), F, D, L,
+        _call("hdc_levelid_prepare", _ptr(self.idb), _ptr(self.lob), _ptr(self.hib), _ptr(self.flip), F, D, L,
               x_lo, x_hi, ctypes.byref(c) if c else None, _ptr(self.buf), n.value, _ptr(self.flip_error),
               ctypes.byref(self.m), _stream(stream))
 

@@ -80,6 +80,11 @@ def test_argument_checks_without_gpu(lib):
     assert lib.hdc_encode(None, 5, ctypes.byref(m), None, None, None, 0, None) == 1
     assert lib.hdc_hamming_argmin(None, None, 5, 0, 10, None, None, None, None) == 1
     assert lib.hdc_train_epoch(None, None, 5, 10, 2, 7, None, None, None, None, 0, None) == 1
+    fake = ctypes.c_void_p(1 << 20)                      # aligned, never dereferenced: argument checks come first
+    assert lib.hdc_train_epoch(fake, fake, 5, 10, 2, 3, fake, fake, None, fake, 1 << 20, None) == 1
+    assert lib.hdc_train_apply(None, 0, 10, fake, fake, None) == 1         # C = 0
+    assert lib.hdc_train_apply(None, 2, 10, None, fake, None) == 1         # no accumulators
+    assert lib.hdc_train_apply(fake, 2, 10, fake, ctypes.c_void_p((1 << 20) + 4), None) == 1   # cls misaligned
     assert lib.hdc_classify(None, 5, ctypes.byref(m), None, None, None, None, 0, None) == 1
     assert lib.hdc_kept_dims(100, None) == 100
     assert lib.hdc_selftest_wait(0, None) == 1           # wait limit out of range: nothing enqueued

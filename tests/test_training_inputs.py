@@ -1,7 +1,6 @@
-"""Host-side checks of the throughput modules (no GPU): the training
-module's packed Bernoulli rows use the library's packed layout, keep pad
-bits zero and flip bits at the requested rate; the Hamming module's popcount
-roofline arithmetic."""
+"""Host-side checks of bench_kernels.py (no GPU): the training samples'
+packed Bernoulli rows use the library's packed layout, keep pad bits zero and
+flip bits at the requested rate; the popcount and LOP3 roofline arithmetic."""
 import numpy as np
 import pytest
 import torch
@@ -11,7 +10,7 @@ from tests._helpers import unpack, words_for
 
 @pytest.mark.parametrize("n,D,p", [(5, 40, 0.5), (300, 1000, 0.48), (64, 64, 0.0), (64, 96, 1.0)])
 def test_packed_bernoulli_layout_and_rate(n, D, p):
-    from paper_2606_26547_gb300.training import packed_bernoulli
+    from bench_kernels import packed_bernoulli
     W = words_for(D)
     g = torch.Generator()
     g.manual_seed(3)
@@ -25,7 +24,7 @@ def test_packed_bernoulli_layout_and_rate(n, D, p):
 
 
 def test_packed_bernoulli_is_seeded():
-    from paper_2606_26547_gb300.training import packed_bernoulli
+    from bench_kernels import packed_bernoulli
     out = []
     for _ in range(2):
         g = torch.Generator()
@@ -35,8 +34,10 @@ def test_packed_bernoulli_is_seeded():
 
 
 def test_popcount_roofline_arithmetic():
-    """The Hamming module's popcount peak: 16 per clock per SM x SMs x clock."""
-    from paper_2606_26547_gb300.hamming import popcount_roofline
+    """The popcount peak: 16 per clock per SM x SMs x clock; LOP3: 64."""
+    from bench_kernels import lop3_roofline, popcount_roofline
     r = popcount_roofline(16 * 152 * 1e9, 152, 1000.0)
     assert r["peak_per_s"] == 16 * 152 * 1000.0 * 1e6
     assert abs(r["frac"] - 1.0) < 1e-12
+    r = lop3_roofline(64 * 148 * 1.5e9 / 2, 148, 1500.0)
+    assert r["peak_tlops"] == 64 * 148 * 1500.0 * 1e6 / 1e12 and abs(r["frac"] - 0.5) < 1e-12
