@@ -331,12 +331,14 @@ hdc_status hdc_hamming_argmin(const uint32_t *Q, const uint32_t *Cls, int64_t N,
 }
 
 namespace {
-// Training workspace: predictions, the class-grouped sample order, and the
-// counting-sort histogram / offsets / first work item per group / cursors.
+// Training workspace: predictions, the class-grouped sample order, the
+// counting-sort histogram / offsets / first work item per group / cursors,
+// and the byte-lane bit counts of every counting item (32 bytes per item and
+// word).
 struct TrainLayout {
-    size_t pred, perm, hist, offsets, items, cursor, total;
+    size_t pred, perm, hist, offsets, items, cursor, partial, total;
 };
-TrainLayout train_layout(int64_t N, int C)
+TrainLayout train_layout(int64_t N, int D, int C)
 {
     TrainLayout L;
     size_t off = 0;
@@ -348,6 +350,7 @@ TrainLayout train_layout(int64_t N, int C)
     L.offsets = off; off = align_up(off + (size_t)(2 * C + 1) * 4, kAlign);
     L.items = off;   off = align_up(off + (size_t)(2 * C + 1) * 4, kAlign);
     L.cursor = off;  off = align_up(off + (size_t)2 * C * 4, kAlign);
+    L.partial = off; off = align_up(off + (size_t)train_max_items(N, C) * words_for(D) * 32, kAlign);
     L.total = off;
     return L;
 }
@@ -357,7 +360,7 @@ hdc_status hdc_train_workspace_bytes(int64_t N, int32_t D, int32_t C, size_t *by
 {
     if (!bytes || N < 0 || D <= 0 || C <= 0) return HDC_ERR_INVALID_ARG;
     if (N > kMaxTrainRows || C > kMaxTrainClasses) return HDC_ERR_UNSUPPORTED;
-    *bytes = train_layout(N, C).total;
+    *bytes = train_layout(N, D, C).total;
     return HDC_OK;
 }
 
@@ -371,33 +374,26 @@ hdc_status hdc_train_epoch(const uint32_t *H, const int32_t *y, int64_t N, int32
     if (N > kMaxTrainRows || C > kMaxTrainClasses) return HDC_ERR_UNSUPPORTED;
     const int W = words_for(D);
     cudaStream_t st = (cudaStream_t)stream;
-    const TrainLayout L = train_layout(N, C);
+    const TrainLayout L = train_layout(N, D, C);
     if (N > 0 && (!ws || ws_bytes < L.total || !aligned(ws, kAlign))) return HDC_ERR_WORKSPACE;
     char *w = (char *)ws;
-    TrainScratch sc = {(int32_t *)(w + L.perm), (int32_t *)(w + L.hist), (int32_t *)(w + L.offsets),
-                       (int32_t *)(w + L.items), (int32_t *)(w + L.cursor)};
     if (n_updates) {
         hdc_status s = cu(cudaMemsetAsync(n_updates, 0, sizeof(int32_t), st));
         if (s != HDC_OK) return s;
     }
-    if (mode == 0 || mode == 2) {
-        // bundling, or a shard's retraining delta: acc starts from zero
-        hdc_status s = cu(cudaMemsetAsync(acc, 0, (size_t)C * D * sizeof(int32_t), st));
-        if (s != HDC_OK) return s;
+    if (N == 0) {
+        // no samples: a bundle or a delta of zero; an epoch leaves acc as it is
+        if (mode != 1) {
+            hdc_status s = cu(cudaMemsetAsync(acc, 0, (size_t)C * D * sizeof(int32_t), st));
+            if (s != HDC_OK) return s;
+        }
+        return mode == 2 ? HDC_OK : cu(launch_binarise(acc, C, D, cls, W, st));
     }
-    if (mode == 0) {
-        hdc_status s = cu(launch_train_count(H, W, y, nullptr, N, D, C, 0, acc, nullptr, sc, st));
-        if (s != HDC_OK) return s;
-    } else if (N > 0) {
-        int32_t *pred = (int32_t *)(w + L.pred);
-        hdc_status s = cu(launch_similarity(H, N, cls, C, W, 1, D, nullptr, nullptr, nullptr, pred, nullptr, nullptr,
-                                            st));
-        if (s != HDC_OK) return s;
-        s = cu(launch_train_count(H, W, y, pred, N, D, C, 1, acc, n_updates, sc, st));
-        if (s != HDC_OK) return s;
-    }
-    if (mode == 2) return HDC_OK;   // the delta alone: cls stays the start-of-epoch classes
-    return cu(launch_binarise(acc, C, D, cls, W, st));
+    TrainScratch sc = {(int32_t *)(w + L.perm), (int32_t *)(w + L.hist), (int32_t *)(w + L.offsets),
+                       (int32_t *)(w + L.items), (int32_t *)(w + L.cursor), (uint32_t *)(w + L.partial)};
+    // mode 2 (a shard's delta) leaves cls as the start-of-epoch classes
+    return cu(launch_train_pass(H, W, y, N, D, C, mode, cls, (int32_t *)(w + L.pred), acc,
+                                mode == 2 ? nullptr : cls, n_updates, sc, st));
 }
 
 hdc_status hdc_train_apply(const int32_t *delta, int32_t C, int32_t D, int32_t *acc, uint32_t *cls,

@@ -83,17 +83,30 @@ cudaError_t launch_similarity(const uint32_t *Q, int64_t N, const uint32_t *plan
                               const double *cnorm, int32_t *labels, int32_t *dists, double *scores,
                               cudaStream_t st);
 
-// K5: signed bit counts of the training rows into acc (C x D int32).
-//  mode 0: row n adds (1-2 bit) to class y_n.
-//  mode 1: rows with pred_n != y_n add to y_n and subtract from pred_n,
-//          and n_updates (if not NULL, zeroed by the caller) counts them.
-// Scratch: perm (N int32), hist / cursor (C int32), offsets (C+1 int32).
+// Hamming arg-min of N packed rows H against C <= 16 binary classes over all
+// W words (pred), counting the retraining groups of each misclassified row
+// into hist (2C int32, zeroed by the caller): hist[y]++ and hist[C + pred]++.
+// cudaErrorNotSupported for C > 16.
+cudaError_t launch_argmin_groups(const uint32_t *H, int64_t N, const uint32_t *cls, int C, int W, const int32_t *y,
+                                 int32_t *pred, int32_t *hist, cudaStream_t st);
+
+// K5: one training pass over N packed rows H (W words, D dims, C classes):
+//  mode 0: acc = per-class sums of (1 - 2 bit) (bundling), cls_out = sign;
+//  mode 1: pred = Hamming arg-min against cls_in; rows with pred != y add to
+//          y and subtract from pred: acc += that, cls_out = sign(acc);
+//  mode 2: as mode 1, but acc = the updates alone and cls_out is NULL.
+// n_updates (if not NULL, zeroed by the caller) counts the updated rows.
+// Scratch (train_max_items(N, C) counting items): perm (2N int32), hist and
+// cursor (2C int32), offsets and items (2C + 1 int32), partial (max items x
+// W x 8 uint32 byte lanes).
 struct TrainScratch {
     int32_t *perm, *hist, *offsets, *items, *cursor;
+    uint32_t *partial;
 };
-cudaError_t launch_train_count(const uint32_t *H, int W, const int32_t *y, const int32_t *pred,
-                               int64_t N, int D, int C, int mode, int32_t *acc, int32_t *n_updates,
-                               const TrainScratch &s, cudaStream_t st);
+int64_t train_max_items(int64_t N, int C);
+cudaError_t launch_train_pass(const uint32_t *H, int W, const int32_t *y, int64_t N, int D, int C, int mode,
+                              const uint32_t *cls_in, int32_t *pred, int32_t *acc, uint32_t *cls_out,
+                              int32_t *n_updates, const TrainScratch &s, cudaStream_t st);
 
 // K6 (binary): cls[c] = pack(acc[c] < 0) over D dims, W words per row.
 cudaError_t launch_binarise(const int32_t *acc, int C, int D, uint32_t *cls, int W, cudaStream_t st);

@@ -15,6 +15,7 @@
 // One query per thread, 128 per block; class words are staged through shared
 // memory in chunks of WCH words, partial sums live in shared memory
 // (acc[c][thread]) so C is a runtime value.
+#include "bitslice.cuh"
 #include "hdc_internal.cuh"
 
 namespace hdc {
@@ -200,6 +201,174 @@ __global__ void __launch_bounds__(TPB) hamming_reg_kernel(const uint32_t *__rest
     if (s == 0 && row < N) labels[row] = best;
 }
 
+// Kept dims of a perforation (s0, s0 + stride, ... < e0) inside 32-dim word w.
+__device__ __forceinline__ uint32_t perf_word_mask(int64_t w, int64_t s0, int64_t e0, int64_t stride)
+{
+    uint32_t m = 0;
+    const int64_t base = w * 32;
+    const int64_t lo = max(s0, base), hi = min(e0, base + 32);
+    if (lo < hi) {
+        const int64_t r = (lo - s0) % stride;
+        for (int64_t d = r ? lo + (stride - r) : lo; d < hi; d += stride) m |= 1u << (d - base);
+    }
+    return m;
+}
+
+// Hamming arg-min for at most 16 binary classes (CM = C rounded up to even).
+// Four threads per query: thread s takes the 16-byte groups of four words
+// 4s, 4s + 16, 4s + 32, ... of its query (a warp reads eight 64-byte runs).
+// The class words of a chunk of WC words sit in shared memory (zero past C;
+// both the class words and the query words are ANDed with the kept-dim mask,
+// so (q ^ c) counts only kept dims).  Per class, the four mismatch words
+// x = q ^ c enter a bit-sliced carry-save counter of planes of weight 1 and
+// 2 (three full adders); only the carry of weight 4 is popcounted, one
+// popcount per four words instead of four, the remaining work being 3-input
+// logic operations.  dist = 4 * sum popc(e4) + 2 popc(c2) + popc(c1), summed
+// over the four threads by shuffles.  With HIST, the kernel also counts the
+// groups of a retraining epoch: a sample whose prediction differs from its
+// label y goes to group y (added) and group C + prediction (subtracted).
+template <int CM, bool MASKED, bool HIST>
+__global__ void __launch_bounds__(TPB) hamming_csa_kernel(const uint32_t *__restrict__ Q, int64_t N,
+                                                          const uint32_t *__restrict__ cls, int C, int W, int WC,
+                                                          int64_t s0, int64_t e0, int64_t stride,
+                                                          int32_t *__restrict__ labels, int32_t *__restrict__ dists,
+                                                          const int32_t *__restrict__ y, int32_t *__restrict__ hist)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t *sc = smem;              // CM x WC
+    uint32_t *mk = smem + CM * WC;    // WC (MASKED)
+    __shared__ int32_t sh[2 * CM];
+    const int tid = threadIdx.x, s = tid & 3;
+    const int64_t row = (int64_t)blockIdx.x * (TPB / 4) + (tid >> 2);
+    const bool valid = row < N;
+    const uint32_t *q = Q + (valid ? row : 0) * (int64_t)W;
+    uint32_t c1[CM], c2[CM];
+    int d4[CM];
+#pragma unroll
+    for (int c = 0; c < CM; c++) {
+        c1[c] = 0;
+        c2[c] = 0;
+        d4[c] = 0;
+    }
+    if (HIST && tid < 2 * CM) sh[tid] = 0;
+    const uint4 zero = make_uint4(0, 0, 0, 0);
+    for (int w0 = 0; w0 < W; w0 += WC) {
+        const int nw = min(WC, W - w0);   // a multiple of 4
+        const int n16 = (nw + 15) & ~15;
+        __syncthreads();
+        if (MASKED)
+            for (int j = tid; j < n16; j += TPB) mk[j] = j < nw ? perf_word_mask(w0 + j, s0, e0, stride) : 0u;
+        if (MASKED) __syncthreads();
+        for (int i = tid; i < CM * (n16 >> 2); i += TPB) {
+            const int c = i / (n16 >> 2), j = (i % (n16 >> 2)) * 4;
+            uint4 v = zero;
+            if (c < C && j < nw) {
+                v = __ldg(reinterpret_cast<const uint4 *>(cls + (int64_t)c * W + w0 + j));
+                if (MASKED) {
+                    v.x &= mk[j];
+                    v.y &= mk[j + 1];
+                    v.z &= mk[j + 2];
+                    v.w &= mk[j + 3];
+                }
+            }
+            *reinterpret_cast<uint4 *>(sc + c * WC + j) = v;
+        }
+        __syncthreads();
+        // query words three groups ahead of the one counted
+        auto qload = [&](int j) {
+            return (valid && j < nw) ? __ldg(reinterpret_cast<const uint4 *>(q + w0 + j)) : zero;
+        };
+        uint4 qa = qload(4 * s), qb = qload(4 * s + 16), qc = qload(4 * s + 32);
+        for (int k = 0; k < n16; k += 16) {
+            const int j = k + 4 * s;
+            uint4 qv = qa;
+            qa = qb;
+            qb = qc;
+            qc = qload(j + 48);
+            if (MASKED) {
+                const uint4 m = *reinterpret_cast<const uint4 *>(mk + j);
+                qv.x &= m.x;
+                qv.y &= m.y;
+                qv.z &= m.z;
+                qv.w &= m.w;
+            }
+#pragma unroll
+            for (int c = 0; c < CM; c++) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(sc + c * WC + j);
+                uint32_t a2, b2, e4;
+                csa(a2, c1[c], c1[c], qv.x ^ v.x, qv.y ^ v.y);
+                csa(b2, c1[c], c1[c], qv.z ^ v.z, qv.w ^ v.w);
+                csa(e4, c2[c], c2[c], a2, b2);
+                d4[c] += __popc(e4);
+            }
+        }
+    }
+    int best = 0, bv = 0x7fffffff;
+#pragma unroll
+    for (int c = 0; c < CM; c++) {
+        int v = 4 * d4[c] + 2 * __popc(c2[c]) + __popc(c1[c]);
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        if (c < C) {
+            if (dists && valid && s == 0) dists[row * C + c] = v;
+            if (v < bv) {
+                bv = v;
+                best = c;
+            }
+        }
+    }
+    if (valid && s == 0) {
+        labels[row] = best;
+        if (HIST) {
+            const int yc = y[row];
+            if (yc >= 0 && yc < C && yc != best) {
+                atomicAdd(&sh[yc], 1);
+                atomicAdd(&sh[C + best], 1);
+            }
+        }
+    }
+    if (HIST) {
+        __syncthreads();
+        if (tid < 2 * C && sh[tid]) atomicAdd(hist + tid, sh[tid]);
+    }
+}
+
+template <int CM, bool MASKED, bool HIST>
+cudaError_t launch_csa_cm(const uint32_t *Q, int64_t N, const uint32_t *cls, int C, int W, int64_t s0, int64_t e0,
+                          int64_t stride, int32_t *labels, int32_t *dists, const int32_t *y, int32_t *hist,
+                          cudaStream_t st)
+{
+    const int w16 = (W + 15) & ~15;
+    const int WC = w16 < 512 ? w16 : 512;
+    const size_t smem = ((size_t)CM * WC + (MASKED ? WC : 0)) * sizeof(uint32_t);
+    auto k = hamming_csa_kernel<CM, MASKED, HIST>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t blocks = (N + TPB / 4 - 1) / (TPB / 4);
+    k<<<(unsigned)blocks, TPB, smem, st>>>(Q, N, cls, C, W, WC, s0, e0, stride, labels, dists, y, hist);
+    return cudaGetLastError();
+}
+
+template <bool MASKED, bool HIST>
+cudaError_t launch_csa(const uint32_t *Q, int64_t N, const uint32_t *cls, int C, int W, int64_t s0, int64_t e0,
+                       int64_t stride, int32_t *labels, int32_t *dists, const int32_t *y, int32_t *hist,
+                       cudaStream_t st)
+{
+    switch ((C + 1) / 2) {
+    case 1: return launch_csa_cm<2, MASKED, HIST>(Q, N, cls, C, W, s0, e0, stride, labels, dists, y, hist, st);
+    case 2: return launch_csa_cm<4, MASKED, HIST>(Q, N, cls, C, W, s0, e0, stride, labels, dists, y, hist, st);
+    case 3: return launch_csa_cm<6, MASKED, HIST>(Q, N, cls, C, W, s0, e0, stride, labels, dists, y, hist, st);
+    case 4: return launch_csa_cm<8, MASKED, HIST>(Q, N, cls, C, W, s0, e0, stride, labels, dists, y, hist, st);
+    case 5: return launch_csa_cm<10, MASKED, HIST>(Q, N, cls, C, W, s0, e0, stride, labels, dists, y, hist, st);
+    case 6: return launch_csa_cm<12, MASKED, HIST>(Q, N, cls, C, W, s0, e0, stride, labels, dists, y, hist, st);
+    case 7: return launch_csa_cm<14, MASKED, HIST>(Q, N, cls, C, W, s0, e0, stride, labels, dists, y, hist, st);
+    case 8: return launch_csa_cm<16, MASKED, HIST>(Q, N, cls, C, W, s0, e0, stride, labels, dists, y, hist, st);
+    default: return cudaErrorNotSupported;
+    }
+}
+
 int device_sms()
 {
     static int n = 0;
@@ -259,7 +428,11 @@ cudaError_t launch_similarity(const uint32_t *Q, int64_t N, const uint32_t *plan
                               int32_t *dists, double *scores, cudaStream_t st)
 {
     if (N <= 0) return cudaSuccess;
-    if (nb == 1 && C <= 16) return launch_reg<16>(Q, N, planes, C, W, D, p, labels, dists, st);
+    if (nb == 1 && C <= 16) {
+        if (p) return launch_csa<true, false>(Q, N, planes, C, W, p->s0, p->e0, p->stride, labels, dists, nullptr,
+                                              nullptr, st);
+        return launch_csa<false, false>(Q, N, planes, C, W, 0, D, 1, labels, dists, nullptr, nullptr, st);
+    }
     if (nb == 1 && C <= 32) return launch_reg<32>(Q, N, planes, C, W, D, p, labels, dists, st);
     // 33..256 binary classes: the distances as a tensor-core product of the
     // rows expanded to +-1 (the popcount loop is bound by the popcount unit,
@@ -275,6 +448,14 @@ cudaError_t launch_similarity(const uint32_t *Q, int64_t N, const uint32_t *plan
     case 8: return launch_nb<8>(Q, N, planes, C, W, D, nullptr, csum, cnorm, labels, dists, scores, st);
     default: return cudaErrorNotSupported;
     }
+}
+
+cudaError_t launch_argmin_groups(const uint32_t *H, int64_t N, const uint32_t *cls, int C, int W, const int32_t *y,
+                                int32_t *pred, int32_t *hist, cudaStream_t st)
+{
+    if (N <= 0) return cudaSuccess;
+    if (C > 16) return cudaErrorNotSupported;
+    return launch_csa<false, true>(H, N, cls, C, W, 0, (int64_t)W * 32, 1, pred, nullptr, y, hist, st);
 }
 
 }  // namespace hdc

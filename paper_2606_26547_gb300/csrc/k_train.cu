@@ -10,15 +10,22 @@
 //
 // Both are class-grouped signed bit counts: for a set S of samples of one
 // class, sum_{n in S} (1 - 2 bit[n][d]) = |S| - 2 * count_{n in S} bit[n][d].
-// The samples are grouped by class with a counting sort (histogram, scan,
-// scatter of indices), then each thread counts the set bits of one 32-dim
-// word over a chunk of at most 252 of one class's samples: sixteen rows at a
-// time through a carry-save tree of 15 full adders (bit-sliced planes of
-// weight 1, 2, 4, 8, 32 dims per logic operation), whose weight-16 carry is
-// added four dims per 32-bit add into byte lanes; at the end of the chunk
-// count = 16 * carries + planes <= 255 per byte.  It then adds
-// |S| - 2*count to acc with one atomic per (chunk, dim).  Integer sums:
-// exact and independent of order.
+// The samples are grouped by class with a counting sort (histogram -- folded
+// into the arg-min of a retraining epoch for up to 16 classes --, scan,
+// scatter of indices).  A counting work item is a chunk of at most 252 of
+// one group's samples; a block streams the item's rows, 16 at a time, for a
+// range of words through a ring of shared-memory stages filled by cp.async
+// (several stages in flight per block, so the gathered rows stream at HBM
+// rate instead of one load latency per 16 rows), and each thread counts the
+// set bits of one 32-dim word: a carry-save tree of 15 full adders per 16
+// rows (bit-sliced planes of weight 1, 2, 4, 8, 32 dims per logic operation)
+// whose weight-16 carry is added four dims per 32-bit add into byte lanes;
+// at the end of the item count = 16 * carries + planes <= 255 per byte.
+// The item's byte lanes go to a partial buffer; a reduce kernel then sums,
+// per (class, word), |S| - 2*count over the class's items (signed by group),
+// writes or adds acc and packs the sign bits: no global atomics, and the
+// re-binarisation is part of the same pass.  Integer sums: exact and
+// independent of order.
 #include "bitslice.cuh"
 #include "hdc_internal.cuh"
 
@@ -111,92 +118,165 @@ __global__ void scatter_kernel(const int32_t *__restrict__ y, const int32_t *__r
     }
 }
 
-// Work item = (group g, chunk of at most CH of its samples); thread = word.
-// Group g adds to class g mod C, with sign -1 for the groups C..2C-1 of
-// retraining.  Grid row y counts the items y, y + gridDim.y, ...; the group
-// of an item is found by binary search over items[] (first item per group).
-constexpr int SEG_SMEM_G = 1024;  // groups whose offsets are staged in shared memory
-__global__ void __launch_bounds__(128, 8) segment_count_kernel(const uint32_t *__restrict__ H, int W, int D,
-                                                            const int32_t *__restrict__ perm,
-                                                            const int32_t *__restrict__ offsets,
-                                                            const int32_t *__restrict__ items, int G, int C,
-                                                            int32_t *__restrict__ acc)
+// 16-byte asynchronous global -> shared copy; with full == false nothing is
+// read and the 16 bytes are zero-filled.
+__device__ __forceinline__ void cp_async16(uint32_t *dst, const void *src, bool full)
 {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(full ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
+// Group of work item `it`: the last g with first[g] <= it (an empty group has
+// first[g] == first[g + 1], so the last such g is never empty).
+__device__ __forceinline__ int group_of(const int32_t *first, int G, int it)
+{
+    int lo_g = 0, hi_g = G - 1;
+    while (lo_g < hi_g) {
+        const int mid = (lo_g + hi_g + 1) >> 1;
+        if (first[mid] <= it) lo_g = mid;
+        else hi_g = mid - 1;
+    }
+    return lo_g;
+}
+
+// Work item = (group g, chunk of at most CH of its samples); block = TW
+// consecutive words, thread = word.  Grid row y counts the items y,
+// y + gridDim.y, ...; rows arrive through a ring of NST stages of RS rows.
+// Output: partial[it][word][j] = byte lanes of the item's set-bit counts,
+// byte k of lane j = count of dim 32 * word + j + 8k.
+constexpr int SEG_SMEM_G = 1024;  // groups whose offsets are staged in shared memory
+constexpr int RS = 16;            // rows per stage (one carry-save tree)
+constexpr int NST = 4;            // stages in the ring (three in flight while one is counted)
+template <int TW>
+__global__ void __launch_bounds__(TW) count_kernel(const uint32_t *__restrict__ H, int W,
+                                                   const int32_t *__restrict__ perm,
+                                                   const int32_t *__restrict__ offsets,
+                                                   const int32_t *__restrict__ items, int G,
+                                                   uint32_t *__restrict__ partial)
+{
+    constexpr int CPR = TW / 4;   // 16-byte chunks of a row's TW words; RS * CPR = 4 * TW per stage
+    __shared__ __align__(16) uint32_t ring[NST][RS][TW];
+    __shared__ int32_t s_rows[CH];
     __shared__ int32_t s_off[SEG_SMEM_G + 1];
     __shared__ int32_t s_items[SEG_SMEM_G + 1];
-    __shared__ int32_t s_rows[CH];
     const bool small = G <= SEG_SMEM_G;
     if (small)
-        for (int g = threadIdx.x; g <= G; g += blockDim.x) {
+        for (int g = threadIdx.x; g <= G; g += TW) {
             s_off[g] = offsets[g];
             s_items[g] = items[g];
         }
     __syncthreads();
     const int32_t *off = small ? s_off : offsets;
     const int32_t *first = small ? s_items : items;
-    const int word = blockIdx.x * blockDim.x + threadIdx.x;
+    const int wbase = blockIdx.x * TW;
+    const int word = wbase + threadIdx.x;
     const int total = first[G];
     for (int it = blockIdx.y; it < total; it += gridDim.y) {  // uniform across the block
-        // the last g with first[g] <= it owns item it (an empty group has
-        // first[g] == first[g + 1], so the last such g is never empty)
-        int lo_g = 0, hi_g = G - 1;
-        while (lo_g < hi_g) {
-            const int mid = (lo_g + hi_g + 1) >> 1;
-            if (first[mid] <= it) lo_g = mid;
-            else hi_g = mid - 1;
-        }
-        const int g = lo_g;
-        const int c = g < C ? g : g - C;
-        const int sign = g < C ? 1 : -1;
+        const int g = group_of(first, G, it);
         const int r0 = off[g] + (it - first[g]) * CH;
-        const int r1 = min(off[g + 1], r0 + CH);
-        {
-            __syncthreads();
-            for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) s_rows[r - r0] = __ldg(perm + r);
-            __syncthreads();
-            if (word >= W) continue;
-            // CH <= 252: 16 * (carries <= 15) + (planes <= 15) fits a byte lane
-            uint32_t lanes[8];
+        const int n = min(off[g + 1], r0 + CH) - r0;
+        __syncthreads();   // the previous item's last stage has been counted
+        for (int r = threadIdx.x; r < n; r += TW) s_rows[r] = __ldg(perm + r0 + r);
+        __syncthreads();
+        const int nst = (n + RS - 1) / RS;
+        // stage st: rows st*RS .. st*RS + 15 of the item (zero past n and past W)
+        auto issue = [&](int st) {
+            if (st < nst) {
+                uint32_t *slot = &ring[st % NST][0][0];
 #pragma unroll
-            for (int j = 0; j < 8; j++) lanes[j] = 0;
-            uint32_t c1 = 0, c2 = 0, c4 = 0, c8 = 0;
-            const int n = r1 - r0;
-            // sixteen gathered row loads in flight per thread, and the next
-            // sixteen issued before the current ones are counted: the pass is
-            // bound by how many bytes each SM has outstanding.  Rows past n
-            // read as zero words (no bits counted; n enters the sum below).
-            uint32_t nxt[16];
-#pragma unroll
-            for (int u = 0; u < 16; u++) nxt[u] = u < n ? __ldg(H + (int64_t)s_rows[u] * W + word) : 0u;
-            for (int r = 0; r < n; r += 16) {
-                uint32_t w[16];
-#pragma unroll
-                for (int u = 0; u < 16; u++) w[u] = nxt[u];
-                if (r + 16 < n) {
-#pragma unroll
-                    for (int u = 0; u < 16; u++)
-                        nxt[u] = r + 16 + u < n ? __ldg(H + (int64_t)s_rows[r + 16 + u] * W + word) : 0u;
+                for (int k = 0; k < 4; k++) {
+                    const int i = threadIdx.x + k * TW;
+                    const int rr = i / CPR, c4 = (i % CPR) * 4;
+                    const int r = st * RS + rr;
+                    const bool ok = r < n && wbase + c4 < W;
+                    cp_async16(slot + rr * TW + c4, ok ? (const void *)(H + (int64_t)s_rows[r] * W + wbase + c4)
+                                                       : (const void *)H, ok);
                 }
-                const uint32_t e16 = csa16(c1, c2, c4, c8, w);
-#pragma unroll
-                for (int j = 0; j < 8; j++) lanes[j] += (e16 >> j) & 0x01010101u;  // dims j, j+8, j+16, j+24
             }
+            cp_async_commit();   // an empty group past the last stage keeps the count uniform
+        };
+#pragma unroll
+        for (int st = 0; st < NST - 1; st++) issue(st);
+        // CH <= 252: 16 * (carries <= 15) + (planes <= 15) fits a byte lane
+        uint32_t lanes[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) lanes[j] = 0;
+        uint32_t c1 = 0, c2 = 0, c4 = 0, c8 = 0;
+        for (int st = 0; st < nst; st++) {
+            issue(st + NST - 1);
+            cp_async_wait<NST - 1>();   // stage st has landed (this thread's copies)
+            __syncthreads();            // ... and every other thread's
+            uint32_t w[RS];
+#pragma unroll
+            for (int u = 0; u < RS; u++) w[u] = ring[st % NST][u][threadIdx.x];
+            const uint32_t e16 = csa16(c1, c2, c4, c8, w);
+#pragma unroll
+            for (int j = 0; j < 8; j++) lanes[j] += (e16 >> j) & 0x01010101u;  // dims j, j+8, j+16, j+24
+            __syncthreads();            // the slot is refilled by the next iteration's issue
+        }
+        if (word < W) {
 #pragma unroll
             for (int j = 0; j < 8; j++)
                 lanes[j] = (lanes[j] << 4) + ((c1 >> j) & 0x01010101u) + (((c2 >> j) & 0x01010101u) << 1) +
                            (((c4 >> j) & 0x01010101u) << 2) + (((c8 >> j) & 0x01010101u) << 3);
-            int cnt[32];
+            uint4 *dst = reinterpret_cast<uint4 *>(partial + ((int64_t)it * W + word) * 8);
+            dst[0] = make_uint4(lanes[0], lanes[1], lanes[2], lanes[3]);
+            dst[1] = make_uint4(lanes[4], lanes[5], lanes[6], lanes[7]);
+        }
+    }
+    cp_async_wait<0>();
+}
+
+// One thread per (class c, word w): sums |S| - 2 * count over the items of
+// group c (and subtracts those of group C + c when retraining), writes acc
+// (accumulate: adds to it) for the word's dims below D, and, with cls, packs
+// the sign bits of the result (pad bits 0).
+__global__ void reduce_kernel(const uint32_t *__restrict__ partial, int W, int D,
+                              const int32_t *__restrict__ offsets, const int32_t *__restrict__ items, int G, int C,
+                              int accumulate, int32_t *__restrict__ acc, uint32_t *__restrict__ cls)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)C * W) return;
+    const int c = (int)(t / W), w = (int)(t % W);
+    int sum[32];
+#pragma unroll
+    for (int b = 0; b < 32; b++) sum[b] = 0;
+    for (int side = 0; side < (G > C ? 2 : 1); side++) {
+        const int g = side ? C + c : c;
+        const int i0 = items[g], i1 = items[g + 1], o0 = offsets[g], o1 = offsets[g + 1];
+        for (int it = i0; it < i1; it++) {
+            const int r0 = o0 + (it - i0) * CH;
+            const int n = min(o1, r0 + CH) - r0;
+            const uint4 *pp = reinterpret_cast<const uint4 *>(partial + ((int64_t)it * W + w) * 8);
+            const uint4 a = __ldg(pp), b = __ldg(pp + 1);
+            const uint32_t ln[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
             for (int j = 0; j < 8; j++)
 #pragma unroll
-                for (int k = 0; k < 4; k++) cnt[j + 8 * k] = (lanes[j] >> (8 * k)) & 0xffu;
-#pragma unroll
-            for (int b = 0; b < 32; b++) {
-                const int d = word * 32 + b;
-                if (d < D) atomicAdd(acc + (int64_t)c * D + d, sign * (n - 2 * cnt[b]));
-            }
+                for (int k = 0; k < 4; k++) {
+                    const int v = n - 2 * (int)((ln[j] >> (8 * k)) & 0xffu);
+                    sum[j + 8 * k] += side ? -v : v;
+                }
         }
     }
+    uint32_t bits = 0;
+    const int64_t base = (int64_t)c * D + (int64_t)w * 32;
+#pragma unroll
+    for (int b = 0; b < 32; b++) {
+        if (w * 32 + b < D) {
+            const int v = sum[b] + (accumulate ? acc[base + b] : 0);
+            acc[base + b] = v;
+            bits |= (uint32_t)(v < 0) << b;
+        }
+    }
+    if (cls) cls[t] = bits;
 }
 
 // One warp per (class, word): ballot of acc < 0 over the word's 32 dims,
@@ -232,45 +312,74 @@ int sm_count()
     return n > 0 ? n : 152;
 }
 
-// Group the counted samples and add their signed bit counts to acc: G = C
-// groups for bundling, 2C for retraining (one pass for both updates).
+// Group the counted samples (hist already counted when hist_ready), count
+// their bits per item and reduce into acc (and cls): G = C groups for
+// bundling, 2C for retraining (one pass for both updates).
 cudaError_t group_and_count(const uint32_t *H, int W, const int32_t *y, const int32_t *pred, int64_t N, int D, int C,
-                            int mode, int32_t *acc, int32_t *n_updates, const TrainScratch &s, cudaStream_t st)
+                            int mode, bool hist_ready, int accumulate, int32_t *acc, uint32_t *cls,
+                            int32_t *n_updates, const TrainScratch &s, cudaStream_t st)
 {
     const int G = mode == 0 ? C : 2 * C;
-    cudaError_t e = cudaMemsetAsync(s.hist, 0, (size_t)G * sizeof(int32_t), st);
-    if (e != cudaSuccess) return e;
     const int sms = sm_count();
     int64_t blocks = (N + 255) / 256;
     if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
     if (blocks < 1) blocks = 1;
-    const bool in_shared = (size_t)G * sizeof(int32_t) <= 48 * 1024;
-    hist_kernel<<<(unsigned)blocks, 256, in_shared ? (size_t)G * sizeof(int32_t) : 0, st>>>(y, pred, N, C, mode, G,
-                                                                                            in_shared, s.hist);
+    if (!hist_ready) {
+        const bool in_shared = (size_t)G * sizeof(int32_t) <= 48 * 1024;
+        hist_kernel<<<(unsigned)blocks, 256, in_shared ? (size_t)G * sizeof(int32_t) : 0, st>>>(y, pred, N, C, mode,
+                                                                                                G, in_shared, s.hist);
+    }
     scan_kernel<<<1, 32, 0, st>>>(s.hist, G, C, s.offsets, s.items, s.cursor, n_updates);
     scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(y, pred, N, C, mode, s.offsets, s.cursor, s.perm);
-    // items: at most ceil(entries / CH) + G, entries <= (G / C) * N.  A block
-    // spans up to 128 words (narrow rows take a narrower block); about 32
-    // warps per SM, grid rows striding over the items.
-    const int64_t max_items = ((G / C) * N + CH - 1) / CH + G;
-    const int threads = W >= 128 ? 128 : (W + 31) / 32 * 32;
-    const int wblocks = (W + threads - 1) / threads;
-    int64_t rows = (int64_t)sms * (1024 / threads) / wblocks + 1;
-    if (rows > max_items) rows = max_items;
-    if (rows > 65535) rows = 65535;
-    segment_count_kernel<<<dim3(wblocks, (unsigned)rows), threads, 0, st>>>(H, W, D, s.perm, s.offsets, s.items, G,
-                                                                            C, acc);
+    // items: at most ceil(entries / CH) + G, entries <= (G / C) * N; one
+    // block per (item, word block), extra grid rows exit at once
+    const int64_t max_items = train_max_items(N, C);
+    const int wtile = W >= 128 ? 128 : W >= 64 ? 64 : 32;
+    const int wblocks = (W + wtile - 1) / wtile;
+    int64_t rows = max_items < 65535 ? max_items : 65535;
+    const dim3 grid((unsigned)wblocks, (unsigned)rows);
+    if (wtile == 128) count_kernel<128><<<grid, 128, 0, st>>>(H, W, s.perm, s.offsets, s.items, G, s.partial);
+    else if (wtile == 64) count_kernel<64><<<grid, 64, 0, st>>>(H, W, s.perm, s.offsets, s.items, G, s.partial);
+    else count_kernel<32><<<grid, 32, 0, st>>>(H, W, s.perm, s.offsets, s.items, G, s.partial);
+    const int64_t threads = (int64_t)C * W;
+    reduce_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(s.partial, W, D, s.offsets, s.items, G, C,
+                                                                      accumulate, acc, cls);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_train_count(const uint32_t *H, int W, const int32_t *y, const int32_t *pred, int64_t N, int D,
-                               int C, int mode, int32_t *acc, int32_t *n_updates, const TrainScratch &s,
-                               cudaStream_t st)
+int64_t train_max_items(int64_t N, int C)
+{
+    // retraining: up to 2N entries over 2C groups
+    return (2 * N + CH - 1) / CH + 2 * (int64_t)C;
+}
+
+cudaError_t launch_train_pass(const uint32_t *H, int W, const int32_t *y, int64_t N, int D, int C, int mode,
+                              const uint32_t *cls_in, int32_t *pred, int32_t *acc, uint32_t *cls_out,
+                              int32_t *n_updates, const TrainScratch &s, cudaStream_t st)
 {
     if (N <= 0 || D <= 0 || C <= 0) return cudaSuccess;
-    return group_and_count(H, W, y, pred, N, D, C, mode, acc, mode == 0 ? nullptr : n_updates, s, st);
+    const int G = mode == 0 ? C : 2 * C;
+    // the group histogram starts from zero (the scan resets the cursors)
+    cudaError_t e = cudaMemsetAsync(s.hist, 0, (size_t)G * sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    bool hist_ready = false;
+    if (mode != 0) {
+        // prediction with the start-of-epoch classes; for up to 16 classes
+        // the same kernel counts the retraining groups
+        e = launch_argmin_groups(H, N, cls_in, C, W, y, pred, s.hist, st);
+        if (e == cudaSuccess) {
+            hist_ready = true;
+        } else if (e == cudaErrorNotSupported) {
+            e = launch_similarity(H, N, cls_in, C, W, 1, D, nullptr, nullptr, nullptr, pred, nullptr, nullptr, st);
+            if (e != cudaSuccess) return e;
+        } else {
+            return e;
+        }
+    }
+    return group_and_count(H, W, y, pred, N, D, C, mode == 0 ? 0 : 1, hist_ready, mode == 1, acc, cls_out,
+                           mode == 0 ? nullptr : n_updates, s, st);
 }
 
 cudaError_t launch_apply_binarise(const int32_t *delta, int32_t *acc, int C, int D, uint32_t *cls, int W,
