@@ -256,36 +256,52 @@ def train_model(hdc, torch, data, dev, epochs, rank=0, world=1):
     return Bt, acc, ups, time.perf_counter() - t, H, ytr
 
 
-def time_training(hdc, torch, H, y, D, C, reps=5):
-    """Device time of one bundling pass and one retraining epoch over the
-    packed training hypervectors H, with HBM throughput against algorithmic
-    bytes (bundling reads N*W*4; an epoch reads them for the prediction and
-    the misclassified rows twice more for the update)."""
+def time_training(hdc, torch, H, y, D, C, reps=10):
+    """Device time of one bundling pass and one retraining epoch (from the
+    bundle) over the packed training hypervectors H, as CUDA-graph replays (a
+    graph of the bundle and a graph of bundle + epoch; the epoch is their
+    difference), with HBM throughput against algorithmic bytes (bundling
+    reads N*W*4; an epoch reads them for the prediction and the misclassified
+    rows twice more for the update)."""
     N, W = H.shape
     acc = torch.empty((C, D), dtype=torch.int32, device=H.device)
     cls = torch.empty((C, W), dtype=torch.int32, device=H.device)
     nu = torch.zeros(1, dtype=torch.int32, device=H.device)
-    n = __import__("ctypes").c_size_t()
-    hdc._call("hdc_train_workspace_bytes", N, D, C, __import__("ctypes").byref(n))
-    ws = hdc._empty_bytes(n.value, H.device)
-    out = {}
-    for name, mode in (("bundle", 0), ("retrain_epoch", 1)):
-        hdc.train_epoch(H, y, D, C, 0, acc, cls, ws=ws)      # start from the bundle
+    ws = hdc.train_workspace(N, D, C, H.device)
+    bundle = lambda: hdc.train_epoch(H, y, D, C, 0, acc, cls, ws=ws)
+
+    def both():
+        bundle()
+        hdc.train_epoch(H, y, D, C, 1, acc, cls, n_updates=nu, ws=ws)
+
+    def graph_ms(fn):
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        st = torch.cuda.Stream()
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):
+            with torch.cuda.graph(g, stream=st):
+                fn()
+        torch.cuda.current_stream().wait_stream(st)
+        g.replay()
+        torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ts = []
+        a.record()
         for _ in range(reps):
-            if mode == 1:
-                hdc.train_epoch(H, y, D, C, 0, acc, cls, ws=ws)
-            a.record()
-            hdc.train_epoch(H, y, D, C, mode, acc, cls, n_updates=nu, ws=ws)
-            b.record()
-            b.synchronize()
-            ts.append(a.elapsed_time(b) / 1e3)
-        t = sorted(ts)[len(ts) // 2]
-        upd = int(nu.item()) if mode == 1 else 0
-        nbytes = N * W * 4 + 2 * upd * W * 4
-        out[name] = {"ms": t * 1e3, "algorithmic_bytes": nbytes, "gbs": nbytes / t / 1e9,
-                     "updates": upd}
+            g.replay()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / reps / 1e3
+
+    t_b = graph_ms(bundle)
+    t_e = graph_ms(both) - t_b
+    upd = int(nu.item())
+    out = {}
+    for name, t, u in (("bundle", t_b, 0), ("retrain_epoch", t_e, upd)):
+        nbytes = N * W * 4 + 2 * u * W * 4
+        out[name] = {"ms": t * 1e3, "algorithmic_bytes": nbytes, "gbs": nbytes / t / 1e9, "updates": u,
+                     "timing": "CUDA-graph replays"}
     return out
 
 

@@ -11,9 +11,10 @@ Subcommands (one JSON line each):
             product of the rows expanded to +-1.
   training  hdc_train_epoch: one bundling pass and one retraining epoch
             (started from the bundle) over packed samples made of C random
-            prototypes with each bit flipped with probability p, against HBM
-            (bundling reads the N x W words once; an epoch reads them for the
-            prediction and the updated rows twice more).
+            prototypes with each bit flipped with probability p, timed as
+            CUDA-graph replays, against HBM (bundling reads the N x W words
+            once; an epoch reads them for the prediction and the updated rows
+            twice more).
   levelid   hdc_levelid_encode at the Micro-HD-Classification shapes (Sec.
             5.3: F = 617, D = 1024, L = 128) and around them, bound by 32-bit
             integer logic: per query, feature and 32-dim word at least one
@@ -131,7 +132,40 @@ def packed_bernoulli(n: int, D: int, W: int, p: float, g: torch.Generator, dev) 
     return out
 
 
-def training(N: int, D: int, C: int, p: float = 0.48, reps: int = 9, seed: int = 0) -> dict:
+def graph_of(fn):
+    """fn() captured in one CUDA graph (after one eager warm-up call)."""
+    fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            fn()
+    torch.cuda.current_stream().wait_stream(st)
+    torch.cuda.synchronize()
+    return g
+
+
+def replay_ms(g, reps: int) -> float:
+    """Mean device time of one replay of graph g (back to back, CUDA events)."""
+    g.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        g.replay()
+    b.record()
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def training(N: int, D: int, C: int, p: float = 0.48, reps: int = 20, seed: int = 0) -> dict:
+    """Device time of one bundling pass and of one retraining epoch started
+    from the bundle, each as CUDA-graph replays (a graph of the bundle, a
+    graph of bundle + epoch; the epoch is their difference), so the host's
+    launch of the pass's kernels is not in the figure; the eager time of one
+    hdc_train_epoch call from Python is reported beside it."""
     dev = torch.device("cuda")
     g = torch.Generator(device=dev)
     g.manual_seed(seed)
@@ -144,25 +178,36 @@ def training(N: int, D: int, C: int, p: float = 0.48, reps: int = 9, seed: int =
     nu = torch.zeros(1, dtype=torch.int32, device=dev)
     ws = hdc.train_workspace(N, D, C, dev)
     out = {"N": N, "D": D, "C": C, "W": W, "flip_p": p}
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    bundle = lambda: hdc.train_epoch(H, y, D, C, 0, acc, cls, ws=ws)
+    epoch = lambda: hdc.train_epoch(H, y, D, C, 1, acc, cls, n_updates=nu, ws=ws)
+
+    def both():
+        bundle()
+        epoch()
     clk = ClockSampler(torch.cuda.current_device(), period=0.002)
     clk.start()
     clk.mark("t0")
-    for name, mode in (("bundle", 0), ("retrain_epoch", 1)):
+    ga, gb = graph_of(bundle), graph_of(both)
+    t_bundle = replay_ms(ga, reps)
+    t_both = replay_ms(gb, reps)
+    upd = int(nu.item())
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eager = {}
+    for name, fn in (("bundle", bundle), ("retrain_epoch", epoch)):
         ts = []
-        for _ in range(reps):
-            hdc.train_epoch(H, y, D, C, 0, acc, cls, ws=ws)   # an epoch starts from the bundle
+        for _ in range(9):
+            bundle()
             a.record()
-            hdc.train_epoch(H, y, D, C, mode, acc, cls, n_updates=nu, ws=ws)
+            fn()
             b.record()
             b.synchronize()
             ts.append(a.elapsed_time(b))
-        ms = sorted(ts)[len(ts) // 2]
-        upd = int(nu.item()) if mode == 1 else 0
-        nbytes = N * W * 4 + 2 * upd * W * 4
-        out[name] = {"ms": round(ms, 4), "updates": upd, "algorithmic_bytes": nbytes,
-                     "gbs": round(nbytes / (ms / 1e3) / 1e9, 1)}
+        eager[name] = sorted(ts)[len(ts) // 2]
     clk.mark("t1")
+    for name, ms, u in (("bundle", t_bundle, 0), ("retrain_epoch", t_both - t_bundle, upd)):
+        nbytes = N * W * 4 + 2 * u * W * 4
+        out[name] = {"ms": round(ms, 4), "updates": u, "algorithmic_bytes": nbytes,
+                     "gbs": round(nbytes / (ms / 1e3) / 1e9, 1), "eager_call_ms": round(eager[name], 4)}
     out["clocks"] = clk.stop()
     assert hdc.stream_status() == 0
     return out

@@ -346,10 +346,11 @@ TrainLayout train_layout(int64_t N, int D, int C)
     // retraining groups a misclassified sample twice (true and predicted
     // class): 2N permutation entries over 2C groups
     L.perm = off;    off = align_up(off + (size_t)2 * N * 4, kAlign);
-    L.hist = off;    off = align_up(off + (size_t)2 * C * 4, kAlign);
+    // histogram and cursors adjacent: zeroed by one memset
+    L.hist = off;    L.cursor = off + (size_t)2 * C * 4;
+    off = align_up(off + (size_t)4 * C * 4, kAlign);
     L.offsets = off; off = align_up(off + (size_t)(2 * C + 1) * 4, kAlign);
     L.items = off;   off = align_up(off + (size_t)(2 * C + 1) * 4, kAlign);
-    L.cursor = off;  off = align_up(off + (size_t)2 * C * 4, kAlign);
     L.partial = off; off = align_up(off + (size_t)train_max_items(N, C) * words_for(D) * 32, kAlign);
     L.total = off;
     return L;

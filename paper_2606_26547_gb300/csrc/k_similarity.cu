@@ -201,6 +201,23 @@ __global__ void __launch_bounds__(TPB) hamming_reg_kernel(const uint32_t *__rest
     if (s == 0 && row < N) labels[row] = best;
 }
 
+// 16-byte asynchronous global -> shared copy; with full == false nothing is
+// read and the 16 bytes are zero-filled.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool full)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(full ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
+constexpr int QRING = 8;   // query-word slots per thread of the carry-save arg-min
+
 // Kept dims of a perforation (s0, s0 + stride, ... < e0) inside 32-dim word w.
 __device__ __forceinline__ uint32_t perf_word_mask(int64_t w, int64_t s0, int64_t e0, int64_t stride)
 {
@@ -216,7 +233,8 @@ __device__ __forceinline__ uint32_t perf_word_mask(int64_t w, int64_t s0, int64_
 
 // Hamming arg-min for at most 16 binary classes (CM = C rounded up to even).
 // Four threads per query: thread s takes the 16-byte groups of four words
-// 4s, 4s + 16, 4s + 32, ... of its query (a warp reads eight 64-byte runs).
+// 4s, 4s + 16, 4s + 32, ... of its query (a warp reads eight 64-byte runs),
+// streamed through a per-thread ring of QRING shared-memory slots.
 // The class words of a chunk of WC words sit in shared memory (zero past C;
 // both the class words and the query words are ANDed with the kept-dim mask,
 // so (q ^ c) counts only kept dims).  Per class, the four mismatch words
@@ -235,8 +253,9 @@ __global__ void __launch_bounds__(TPB) hamming_csa_kernel(const uint32_t *__rest
                                                           const int32_t *__restrict__ y, int32_t *__restrict__ hist)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t *sc = smem;              // CM x WC
-    uint32_t *mk = smem + CM * WC;    // WC (MASKED)
+    uint4 *qr = reinterpret_cast<uint4 *>(smem);                    // QRING x TPB query slots
+    uint32_t *sc = smem + QRING * TPB * 4;                          // CM x WC
+    uint32_t *mk = sc + CM * WC;                                    // WC (MASKED)
     __shared__ int32_t sh[2 * CM];
     const int tid = threadIdx.x, s = tid & 3;
     const int64_t row = (int64_t)blockIdx.x * (TPB / 4) + (tid >> 2);
@@ -274,17 +293,22 @@ __global__ void __launch_bounds__(TPB) hamming_csa_kernel(const uint32_t *__rest
             *reinterpret_cast<uint4 *>(sc + c * WC + j) = v;
         }
         __syncthreads();
-        // query words three groups ahead of the one counted
-        auto qload = [&](int j) {
-            return (valid && j < nw) ? __ldg(reinterpret_cast<const uint4 *>(q + w0 + j)) : zero;
+        // the thread's query words stream through its own ring of QRING
+        // 16-byte slots (cp.async, QRING - 1 groups ahead of the one counted;
+        // a thread reads back only what it copied, so no block barrier)
+        auto issue = [&](int k) {
+            const int j = k + 4 * s;
+            const bool ok = valid && k < n16 && j < nw;
+            cp_async16(qr + (k >> 4) % QRING * TPB + tid, ok ? (const void *)(q + w0 + j) : (const void *)Q, ok);
+            cp_async_commit();
         };
-        uint4 qa = qload(4 * s), qb = qload(4 * s + 16), qc = qload(4 * s + 32);
+#pragma unroll
+        for (int p = 0; p < QRING - 1; p++) issue(16 * p);
         for (int k = 0; k < n16; k += 16) {
             const int j = k + 4 * s;
-            uint4 qv = qa;
-            qa = qb;
-            qb = qc;
-            qc = qload(j + 48);
+            issue(k + 16 * (QRING - 1));
+            cp_async_wait<QRING - 1>();
+            uint4 qv = qr[(k >> 4) % QRING * TPB + tid];
             if (MASKED) {
                 const uint4 m = *reinterpret_cast<const uint4 *>(mk + j);
                 qv.x &= m.x;
@@ -302,6 +326,7 @@ __global__ void __launch_bounds__(TPB) hamming_csa_kernel(const uint32_t *__rest
                 d4[c] += __popc(e4);
             }
         }
+        cp_async_wait<0>();   // the ring's trailing zero-fills land before the next chunk reuses it
     }
     int best = 0, bv = 0x7fffffff;
 #pragma unroll
@@ -340,7 +365,7 @@ cudaError_t launch_csa_cm(const uint32_t *Q, int64_t N, const uint32_t *cls, int
 {
     const int w16 = (W + 15) & ~15;
     const int WC = w16 < 512 ? w16 : 512;
-    const size_t smem = ((size_t)CM * WC + (MASKED ? WC : 0)) * sizeof(uint32_t);
+    const size_t smem = ((size_t)QRING * TPB * 4 + (size_t)CM * WC + (MASKED ? WC : 0)) * sizeof(uint32_t);
     auto k = hamming_csa_kernel<CM, MASKED, HIST>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

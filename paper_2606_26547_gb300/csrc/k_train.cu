@@ -94,18 +94,97 @@ __global__ void scan_kernel(const int32_t *__restrict__ hist, int G, int C, int3
     if (n_updates) *n_updates += offsets[C < G ? C : G];
 }
 
-// Lanes of a warp with the same group take their slots with one atomic (a
-// few classes would otherwise serialise every sample on a few cursors).
-// blockDim.x is a multiple of 32 and the loop is warp-uniform.
-__global__ void scatter_kernel(const int32_t *__restrict__ y, const int32_t *__restrict__ pred, int64_t N, int C,
-                               int mode, const int32_t *__restrict__ offsets, int32_t *__restrict__ cursor,
-                               int32_t *__restrict__ perm)
+// The scan above for G <= SEG_SMEM_G groups, done by the first warp of a
+// block into shared memory (off[0..G], first[0..G] when first != NULL):
+// lane l scans a run of ceil(G / 32) groups, the run totals are scanned
+// across the warp with shuffles.  The caller synchronises the block after.
+constexpr int SEG_SMEM_G = 1024;  // groups whose offsets are formed in shared memory
+__device__ void warp_scan_groups(const int32_t *__restrict__ hist, int G, int32_t *off, int32_t *first)
 {
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    const int per = (G + 31) / 32;
+    const int g0 = min(G, lane * per), g1 = min(G, g0 + per);
+    int32_t s = 0, it = 0;
+    for (int g = g0; g < g1; g++) {
+        const int32_t h = hist[g];
+        s += h;
+        it += (h + CH - 1) / CH;
+    }
+    int32_t ps = s, pi = it;   // inclusive scans of the run totals
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t a = __shfl_up_sync(0xffffffffu, ps, o), b = __shfl_up_sync(0xffffffffu, pi, o);
+        if (lane >= o) {
+            ps += a;
+            pi += b;
+        }
+    }
+    s = ps - s;
+    it = pi - it;
+    for (int g = g0; g < g1; g++) {
+        const int32_t h = hist[g];
+        off[g] = s;
+        if (first) first[g] = it;
+        s += h;
+        it += (h + CH - 1) / CH;
+    }
+    if (lane == 31) {
+        off[G] = ps;
+        if (first) first[G] = pi;
+    }
+}
+
+// Scatter of the sample indices into their groups.  Each block takes a
+// contiguous run of `run` samples (a multiple of 256 giving about four blocks
+// per SM): it counts the run's entries per group
+// in shared memory, reserves each group's range with one global atomic per
+// group, then places the entries inside its ranges with shared-memory
+// atomics (the order inside a group does not matter: the counts are sums).
+// With hist (G <= SEG_SMEM_G) the group offsets are formed here from the
+// histogram; otherwise they come from the scan kernel, and the per-block
+// counts stay in global memory-backed atomics per warp (large G).
+__global__ void __launch_bounds__(256) scatter_kernel(const int32_t *__restrict__ y, const int32_t *__restrict__ pred,
+                                                      int64_t N, int64_t run, int C, int mode,
+                                                      const int32_t *__restrict__ hist,
+                                                      int G, const int32_t *__restrict__ offsets_in,
+                                                      int32_t *__restrict__ cursor, int32_t *__restrict__ perm)
+{
+    __shared__ int32_t s_off[SEG_SMEM_G + 1];
+    __shared__ int32_t s_cnt[SEG_SMEM_G];
+    __shared__ int32_t s_base[SEG_SMEM_G];
+    const int64_t n0 = (int64_t)blockIdx.x * run;
+    const int64_t n1 = min(N, n0 + run);
+    if (hist) {
+        warp_scan_groups(hist, G, s_off, nullptr);
+        for (int g = threadIdx.x; g < G; g += blockDim.x) s_cnt[g] = 0;
+        __syncthreads();
+        for (int64_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+            int k[2];
+            const int nk = keys_of(y, pred, n, C, mode, k);
+            for (int i = 0; i < nk; i++) atomicAdd(&s_cnt[k[i]], 1);
+        }
+        __syncthreads();
+        for (int g = threadIdx.x; g < G; g += blockDim.x) {
+            const int c = s_cnt[g];
+            s_base[g] = c ? s_off[g] + atomicAdd(&cursor[g], c) : 0;
+            s_cnt[g] = 0;
+        }
+        __syncthreads();
+        for (int64_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+            int k[2];
+            const int nk = keys_of(y, pred, n, C, mode, k);
+            for (int i = 0; i < nk; i++) perm[s_base[k[i]] + atomicAdd(&s_cnt[k[i]], 1)] = (int32_t)n;
+        }
+        return;
+    }
+    // many groups: lanes of a warp with the same group take their slots with
+    // one global atomic (blockDim.x is a multiple of 32, the loop warp-uniform)
     const int lane = threadIdx.x & 31;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < N; base += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t base = n0; base < n1; base += blockDim.x) {
         const int64_t n = base + threadIdx.x;
         int k[2];
-        const int nk = n < N ? keys_of(y, pred, n, C, mode, k) : 0;
+        const int nk = n < n1 ? keys_of(y, pred, n, C, mode, k) : 0;
         for (int i = 0; i < (mode == 0 ? 1 : 2); i++) {
             const int key = i < nk ? k[i] : -1;
             const unsigned peers = __match_any_sync(0xffffffffu, key);
@@ -113,7 +192,7 @@ __global__ void scatter_kernel(const int32_t *__restrict__ y, const int32_t *__r
             int slot = 0;
             if (lane == leader && key >= 0) slot = atomicAdd(&cursor[key], __popc(peers));
             slot = __shfl_sync(0xffffffffu, slot, leader) + __popc(peers & ((1u << lane) - 1u));
-            if (key >= 0) perm[offsets[key] + slot] = (int32_t)n;
+            if (key >= 0) perm[offsets_in[key] + slot] = (int32_t)n;
         }
     }
 }
@@ -151,14 +230,19 @@ __device__ __forceinline__ int group_of(const int32_t *first, int G, int it)
 // y + gridDim.y, ...; rows arrive through a ring of NST stages of RS rows.
 // Output: partial[it][word][j] = byte lanes of the item's set-bit counts,
 // byte k of lane j = count of dim 32 * word + j + 8k.
-constexpr int SEG_SMEM_G = 1024;  // groups whose offsets are staged in shared memory
 constexpr int RS = 16;            // rows per stage (one carry-save tree)
 constexpr int NST = 4;            // stages in the ring (three in flight while one is counted)
+// With G <= SEG_SMEM_G the block forms the offsets and first items from
+// hist itself, and block (0, 0) stores them for the reduce kernel and adds
+// the count of the first C groups (the updated samples of a retraining
+// epoch) to *n_updates; otherwise the scan kernel has done both.
 template <int TW>
 __global__ void __launch_bounds__(TW) count_kernel(const uint32_t *__restrict__ H, int W,
                                                    const int32_t *__restrict__ perm,
-                                                   const int32_t *__restrict__ offsets,
-                                                   const int32_t *__restrict__ items, int G,
+                                                   const int32_t *__restrict__ hist,
+                                                   int32_t *__restrict__ offsets,
+                                                   int32_t *__restrict__ items, int G, int C,
+                                                   int32_t *__restrict__ n_updates,
                                                    uint32_t *__restrict__ partial)
 {
     constexpr int CPR = TW / 4;   // 16-byte chunks of a row's TW words; RS * CPR = 4 * TW per stage
@@ -167,12 +251,17 @@ __global__ void __launch_bounds__(TW) count_kernel(const uint32_t *__restrict__ 
     __shared__ int32_t s_off[SEG_SMEM_G + 1];
     __shared__ int32_t s_items[SEG_SMEM_G + 1];
     const bool small = G <= SEG_SMEM_G;
-    if (small)
-        for (int g = threadIdx.x; g <= G; g += TW) {
-            s_off[g] = offsets[g];
-            s_items[g] = items[g];
+    if (small) {
+        warp_scan_groups(hist, G, s_off, s_items);
+        __syncthreads();
+        if (blockIdx.x == 0 && blockIdx.y == 0) {
+            for (int g = threadIdx.x; g <= G; g += TW) {
+                offsets[g] = s_off[g];
+                items[g] = s_items[g];
+            }
+            if (threadIdx.x == 0 && n_updates) *n_updates += s_off[C < G ? C : G];
         }
-    __syncthreads();
+    }
     const int32_t *off = small ? s_off : offsets;
     const int32_t *first = small ? s_items : items;
     const int wbase = blockIdx.x * TW;
@@ -234,49 +323,70 @@ __global__ void __launch_bounds__(TW) count_kernel(const uint32_t *__restrict__ 
     cp_async_wait<0>();
 }
 
-// One thread per (class c, word w): sums |S| - 2 * count over the items of
-// group c (and subtracts those of group C + c when retraining), writes acc
-// (accumulate: adds to it) for the word's dims below D, and, with cls, packs
-// the sign bits of the result (pad bits 0).
-__global__ void reduce_kernel(const uint32_t *__restrict__ partial, int W, int D,
-                              const int32_t *__restrict__ offsets, const int32_t *__restrict__ items, int G, int C,
-                              int accumulate, int32_t *__restrict__ acc, uint32_t *__restrict__ cls)
+// A block = 32 (class c, word w, byte lane j) slots, i.e. the dims
+// 32w + j + 8k, k = 0..3, times 8 warps that take every eighth counting item
+// of the slot's groups: each sums |S| - 2 * count over its items of group c
+// (and subtracts those of group C + c when retraining); warp 0 adds the 8
+// partial sums, writes acc (accumulate: adds to it) for the dims below D,
+// and, with cls, the eight lanes of a word OR their sign bits into the
+// packed word (pad bits 0).
+constexpr int RED_SLICES = 8;
+__global__ void __launch_bounds__(32 * RED_SLICES) reduce_kernel(const uint32_t *__restrict__ partial, int W, int D,
+                                                                 const int32_t *__restrict__ offsets,
+                                                                 const int32_t *__restrict__ items, int G, int C,
+                                                                 int accumulate, int32_t *__restrict__ acc,
+                                                                 uint32_t *__restrict__ cls)
 {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)C * W) return;
-    const int c = (int)(t / W), w = (int)(t % W);
-    int sum[32];
-#pragma unroll
-    for (int b = 0; b < 32; b++) sum[b] = 0;
-    for (int side = 0; side < (G > C ? 2 : 1); side++) {
-        const int g = side ? C + c : c;
-        const int i0 = items[g], i1 = items[g + 1], o0 = offsets[g], o1 = offsets[g + 1];
-        for (int it = i0; it < i1; it++) {
-            const int r0 = o0 + (it - i0) * CH;
-            const int n = min(o1, r0 + CH) - r0;
-            const uint4 *pp = reinterpret_cast<const uint4 *>(partial + ((int64_t)it * W + w) * 8);
-            const uint4 a = __ldg(pp), b = __ldg(pp + 1);
-            const uint32_t ln[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-            for (int j = 0; j < 8; j++)
+    __shared__ int32_t s_sum[RED_SLICES][4][32];
+    const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+    const int64_t t = (int64_t)blockIdx.x * 32 + lane;
+    const bool live = t < (int64_t)C * W * 8;
+    const int j = (int)(t & 7);
+    const int64_t cw = live ? t >> 3 : 0;
+    const int c = (int)(cw / W), w = (int)(cw % W);
+    int sum[4] = {0, 0, 0, 0};
+    if (live) {
+        for (int side = 0; side < (G > C ? 2 : 1); side++) {
+            const int g = side ? C + c : c;
+            const int i0 = items[g], i1 = items[g + 1], o0 = offsets[g], o1 = offsets[g + 1];
+            for (int it = i0 + slice; it < i1; it += RED_SLICES) {
+                const int r0 = o0 + (it - i0) * CH;
+                const int n = min(o1, r0 + CH) - r0;
+                const uint32_t ln = __ldg(partial + ((int64_t)it * W + w) * 8 + j);
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
-                    const int v = n - 2 * (int)((ln[j] >> (8 * k)) & 0xffu);
-                    sum[j + 8 * k] += side ? -v : v;
+                    const int v = n - 2 * (int)((ln >> (8 * k)) & 0xffu);
+                    sum[k] += side ? -v : v;
                 }
+            }
         }
     }
-    uint32_t bits = 0;
-    const int64_t base = (int64_t)c * D + (int64_t)w * 32;
 #pragma unroll
-    for (int b = 0; b < 32; b++) {
-        if (w * 32 + b < D) {
-            const int v = sum[b] + (accumulate ? acc[base + b] : 0);
-            acc[base + b] = v;
-            bits |= (uint32_t)(v < 0) << b;
+    for (int k = 0; k < 4; k++) s_sum[slice][k][lane] = sum[k];
+    __syncthreads();
+    if (slice != 0) return;
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+        for (int q = 1; q < RED_SLICES; q++) sum[k] += s_sum[q][k][lane];
+    uint32_t bits = 0;
+    if (live) {
+        const int64_t base = (int64_t)c * D;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int d = w * 32 + j + 8 * k;
+            if (d < D) {
+                const int v = sum[k] + (accumulate ? acc[base + d] : 0);
+                acc[base + d] = v;
+                bits |= (uint32_t)(v < 0) << (j + 8 * k);
+            }
         }
     }
-    if (cls) cls[t] = bits;
+    // the eight lanes of one word are lanes 8i .. 8i + 7 of the warp
+    bits |= __shfl_xor_sync(0xffffffffu, bits, 1);
+    bits |= __shfl_xor_sync(0xffffffffu, bits, 2);
+    bits |= __shfl_xor_sync(0xffffffffu, bits, 4);
+    if (live && cls && j == 0) cls[cw] = bits;
 }
 
 // One warp per (class, word): ballot of acc < 0 over the word's 32 dims,
@@ -329,8 +439,14 @@ cudaError_t group_and_count(const uint32_t *H, int W, const int32_t *y, const in
         hist_kernel<<<(unsigned)blocks, 256, in_shared ? (size_t)G * sizeof(int32_t) : 0, st>>>(y, pred, N, C, mode,
                                                                                                 G, in_shared, s.hist);
     }
-    scan_kernel<<<1, 32, 0, st>>>(s.hist, G, C, s.offsets, s.items, s.cursor, n_updates);
-    scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(y, pred, N, C, mode, s.offsets, s.cursor, s.perm);
+    // up to SEG_SMEM_G groups the scatter and counting kernels scan the
+    // histogram themselves; the cursors were zeroed with it
+    const bool small = G <= SEG_SMEM_G;
+    if (!small) scan_kernel<<<1, 32, 0, st>>>(s.hist, G, C, s.offsets, s.items, s.cursor, n_updates);
+    int64_t run = (N + (int64_t)sms * 4 - 1) / ((int64_t)sms * 4);
+    run = (run + 255) / 256 * 256;
+    scatter_kernel<<<(unsigned)((N + run - 1) / run), 256, 0, st>>>(y, pred, N, run, C, mode, small ? s.hist : nullptr,
+                                                                   G, s.offsets, s.cursor, s.perm);
     // items: at most ceil(entries / CH) + G, entries <= (G / C) * N; one
     // block per (item, word block), extra grid rows exit at once
     const int64_t max_items = train_max_items(N, C);
@@ -338,11 +454,15 @@ cudaError_t group_and_count(const uint32_t *H, int W, const int32_t *y, const in
     const int wblocks = (W + wtile - 1) / wtile;
     int64_t rows = max_items < 65535 ? max_items : 65535;
     const dim3 grid((unsigned)wblocks, (unsigned)rows);
-    if (wtile == 128) count_kernel<128><<<grid, 128, 0, st>>>(H, W, s.perm, s.offsets, s.items, G, s.partial);
-    else if (wtile == 64) count_kernel<64><<<grid, 64, 0, st>>>(H, W, s.perm, s.offsets, s.items, G, s.partial);
-    else count_kernel<32><<<grid, 32, 0, st>>>(H, W, s.perm, s.offsets, s.items, G, s.partial);
-    const int64_t threads = (int64_t)C * W;
-    reduce_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(s.partial, W, D, s.offsets, s.items, G, C,
+    int32_t *nu = small ? n_updates : nullptr;
+    if (wtile == 128)
+        count_kernel<128><<<grid, 128, 0, st>>>(H, W, s.perm, s.hist, s.offsets, s.items, G, C, nu, s.partial);
+    else if (wtile == 64)
+        count_kernel<64><<<grid, 64, 0, st>>>(H, W, s.perm, s.hist, s.offsets, s.items, G, C, nu, s.partial);
+    else
+        count_kernel<32><<<grid, 32, 0, st>>>(H, W, s.perm, s.hist, s.offsets, s.items, G, C, nu, s.partial);
+    const int64_t threads = (int64_t)C * W * 8;
+    reduce_kernel<<<(unsigned)((threads + 31) / 32), 32 * RED_SLICES, 0, st>>>(s.partial, W, D, s.offsets, s.items, G, C,
                                                                       accumulate, acc, cls);
     return cudaGetLastError();
 }
@@ -361,8 +481,9 @@ cudaError_t launch_train_pass(const uint32_t *H, int W, const int32_t *y, int64_
 {
     if (N <= 0 || D <= 0 || C <= 0) return cudaSuccess;
     const int G = mode == 0 ? C : 2 * C;
-    // the group histogram starts from zero (the scan resets the cursors)
-    cudaError_t e = cudaMemsetAsync(s.hist, 0, (size_t)G * sizeof(int32_t), st);
+    // the group histogram and the scatter cursors start from zero (adjacent
+    // in the workspace: one memset)
+    cudaError_t e = cudaMemsetAsync(s.hist, 0, (size_t)4 * C * sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     bool hist_ready = false;
     if (mode != 0) {
