@@ -20,6 +20,9 @@ Subcommands (one JSON line each):
             integer logic: per query, feature and 32-dim word at least one
             XOR (binding) and one full adder of the count (two 3-input logic
             operations), 3 LOP3 against 64 LOP3 per clock per SM.
+  classify  hdc_classify of one configuration on a batch of a workload's
+            queries: step time and the encoding kernel's time and FLOP rate
+            against the measured tensor peak (the small cases profiles/ captures).
   cluster   HD-Clustering (encode + hdc_cluster) eagerly and as one CUDA
             graph, with the NMI of each configuration.
 
@@ -233,6 +236,57 @@ def levelid(F: int, D: int, L: int, N: int, stride: int = 1, reps: int = 10, see
             "roofline": lop3_roofline(lops / (ms / 1e3), sms(), clock_of(clk))}
 
 
+# ----------------------------------------------------------------- classify
+
+def classify(workload: str, enc: str, stride: int, class_bits: int, float_query: bool, batch: int,
+             reps: int = 10) -> dict:
+    """hdc_classify on `batch` queries of a workload's mixture with a model
+    trained on its training set (FP32 encode, bundling + one epoch): device
+    time per call and of the library's encoding kernel (hdc_profile_events),
+    with the kernel's FLOP rate against the measured tensor peak."""
+    w = synth.WORKLOADS[workload]
+    d = synth.make(w, n_train=min(w.n_train, 20000), n_query=1)
+    dev = torch.device("cuda")
+    Bt = torch.from_numpy(d["Bt"]).to(dev)
+    H = hdc.encode(torch.from_numpy(d["Xtr"]).to(dev), hdc.Model(Bt, hdc.ApproxConfig(enc="fp32")))
+    acc, _, _ = hdc.train(H, torch.from_numpy(d["ytr"]).to(dev), w.D, w.C, 1)
+    del H
+    m = hdc.Model(Bt, hdc.ApproxConfig(enc=enc, perf_stride=stride, class_bits=class_bits,
+                                       float_query=float_query), acc=acc)
+    X, _ = synth.device_gauss_queries(batch, w, seed=99, device=dev)
+    labels = torch.empty(batch, dtype=torch.int32, device=dev)
+    ws = m.workspace(batch)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in evs:   # torch creates an event's handle on its first record
+        a.record()
+        b.record()
+    it = iter(range(reps))
+
+    def step():
+        i = next(it, None)
+        if i is not None:
+            hdc.profile_events(*evs[i])
+        hdc.classify(X, m, ws=ws, labels=labels)
+        hdc.profile_events(None, None)
+    hdc.classify(X, m, ws=ws, labels=labels)
+    torch.cuda.synchronize()
+    ms, clk = timed_ms(step, reps)
+    kern = statistics.median(a.elapsed_time(b) for a, b in evs)
+    assert hdc.stream_status() == 0
+    flops = 2.0 * batch * w.F * m.Dk
+    pk = {}
+    try:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak = pk.get("bf16_tflops", 1900.0) * (2.0 if enc == "fp8" else 1.0)
+    return {"workload": workload, "enc": enc, "stride": stride, "class_bits": class_bits,
+            "float_query": float_query, "queries": batch, "Dk": m.Dk, "step_ms": round(ms, 4),
+            "queries_per_s": batch / (ms / 1e3), "kernel_ms": round(kern, 4),
+            "kernel_tflops": flops / (kern / 1e3) / 1e12, "frac_of_tensor_peak": flops / (kern / 1e3) / 1e12 / peak,
+            "clocks": clk}
+
+
 # ------------------------------------------------------------------ cluster
 
 def cluster(workload: str) -> dict:
@@ -268,6 +322,13 @@ def main(argv=None):
     t.add_argument("--flip", type=float, default=0.48, help="bit-flip probability of a sample")
     lv = sub.add_parser("levelid")
     lv.add_argument("--queries", type=int, default=262144)
+    cf = sub.add_parser("classify")
+    cf.add_argument("--workload", default="precision_F784_D10000_C10")
+    cf.add_argument("--enc", default="fp8")
+    cf.add_argument("--stride", type=int, default=2)
+    cf.add_argument("--class-bits", type=int, default=1)
+    cf.add_argument("--float-query", action="store_true")
+    cf.add_argument("--batch", type=int, default=1 << 20)
     cl = sub.add_parser("cluster")
     cl.add_argument("--workload", default="cluster_F617_D1024_K26")
     a = ap.parse_args(argv)
@@ -284,6 +345,8 @@ def main(argv=None):
         out = {"encoder": "level-id", "runs": [levelid(617, 1024, 128, q), levelid(617, 512, 128, q),
                                                levelid(617, 1024, 32, q), levelid(617, 2048, 128, q),
                                                levelid(617, 10000, 128, q // 4), levelid(617, 1024, 814, q)]}
+    elif a.cmd == "classify":
+        out = classify(a.workload, a.enc, a.stride, a.class_bits, a.float_query, a.batch)
     else:
         out = cluster(a.workload)
     print(json.dumps(out))

@@ -4,7 +4,7 @@
 
 #include <mutex>
 
-#include "tc_fcos.cuh"
+#include "tc_fcos16.cuh"
 
 namespace hdc {
 namespace {
@@ -170,8 +170,13 @@ cudaError_t launch_tc_fcos(const TcArgs &a, const uint16_t *cv, int ldS, const d
     auto fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
     const int Cp = (a.C + 15) / 16 * 16;
+    // up to 16 classes: 256-dim encode tiles with the cosine partials in the
+    // tile's own accumulator (tc_fcos16.cuh); more: 192-dim tiles and a
+    // cosine accumulator of its own (tc_fcos.cuh)
+    const bool small_c = Cp == tc::F16_CP;
     CUtensorMap ma, mb, mv;
-    if (!make_map(&ma, a.Xq, a.enc, a.F, a.ldx, a.N, tc::BM) || !make_map(&mb, a.Bq, a.enc, a.F, a.ldb, a.Dk, tc::HBN))
+    if (!make_map(&ma, a.Xq, a.enc, a.F, a.ldx, a.N, tc::BM) ||
+        !make_map(&mb, a.Bq, a.enc, a.F, a.ldb, a.Dk, small_c ? tc::BN : tc::HBN))
         return cudaErrorInvalidValue;
     {
         cuuint64_t dims[2] = {(cuuint64_t)ldS, (cuuint64_t)Cp};
@@ -188,7 +193,7 @@ cudaError_t launch_tc_fcos(const TcArgs &a, const uint16_t *cv, int ldS, const d
     p.Dk = a.Dk;
     const int es = a.enc == HDC_ENC_BF16 ? 2 : 1;
     p.num_kb = (a.ldx * es + tc::BKB - 1) / tc::BKB;
-    p.nt = (a.Dk + tc::HBN - 1) / tc::HBN;
+    p.nt = small_c ? (a.Dk + tc::BN - 1) / tc::BN : (a.Dk + tc::HBN - 1) / tc::HBN;
     p.C = a.C;
     p.Cp = Cp;
     p.sb = a.sb;
@@ -199,6 +204,10 @@ cudaError_t launch_tc_fcos(const TcArgs &a, const uint16_t *cv, int ldS, const d
     if (sms <= 0) return cudaErrorNoDevice;
     const int64_t m_tiles = (a.N + tc::BM - 1) / tc::BM;
     const unsigned grid = (unsigned)(m_tiles < sms ? m_tiles : sms);
+    if (small_c) {
+        if (a.enc == HDC_ENC_BF16) return tc::launch_fcos16_bf16(ma, mb, mv, p, grid, st);
+        return tc::launch_fcos16_fp8(ma, mb, mv, p, grid, st);
+    }
     if (a.enc == HDC_ENC_BF16) return tc::launch_fcos_bf16(ma, mb, mv, p, grid, st);
     return tc::launch_fcos_fp8(ma, mb, mv, p, grid, st);
 }

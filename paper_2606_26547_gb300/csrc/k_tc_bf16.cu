@@ -1,5 +1,5 @@
 // Tensor-core encoder instances for BF16 operands (tcgen05.mma kind::f16).
-#include "tc_fcos.cuh"
+#include "tc_fcos16.cuh"
 
 namespace hdc {
 namespace tc {
@@ -23,6 +23,12 @@ cudaError_t launch_fcos_bf16(const CUtensorMap &ma, const CUtensorMap &mb, const
                          const FCParams &p, unsigned grid, cudaStream_t st)
 {
     return launch_fcos_enc<HDC_ENC_BF16>(ma, mb, mv, p, grid, st);
+}
+
+cudaError_t launch_fcos16_bf16(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
+                               const FCParams &p, unsigned grid, cudaStream_t st)
+{
+    return launch_fcos16_enc<HDC_ENC_BF16>(ma, mb, mv, p, grid, st);
 }
 
 }  // namespace tc

@@ -14,8 +14,11 @@
 // reach device memory.
 //
 // Tensor memory: two 192-column encode accumulators and D2 (Cp <= 128).
-// Shared memory: three A/B stages (40 KB each), the 48 KB value tile and the
-// Cp x 384-byte class tile.  Roles as the tensor-core Hamming kernel:
+// Shared memory: three or four A/B stages (40 KB each), the 48 KB value tile
+// and one or two Cp x 384-byte class tiles: with two, the next tile's class
+// values load while the current tile's cosine MMAs run, so the L2 round trip
+// of that load is off the chain MMA2(t) -> value tile free -> epilogue(t + 1).
+// Roles as the tensor-core Hamming kernel:
 // warps 0-11 epilogue (three warpgroups), 12 stage producer, 13 MMA1 issuer,
 // 14 class-tile producer, 15 MMA2 issuer (its own commit chain: 4.65 vs
 // 5.47 ms per 2^20 queries at C = 10 with one issuer); every wait bounded.
@@ -32,17 +35,17 @@ namespace tc {
 constexpr int FC_A2_BYTES = 3 * A2_ATOM;            // 128 rows x 192 BF16 in three 128-byte K atoms
 constexpr int FC_THREADS = (4 * HEWG + 4) * 32;     // + the cosine MMA issuer
 constexpr int FC_CMAX = 128;   // TMEM: 2 x 192 + 128 columns
-// full[S], empty[S], sfull[2], sempty[2], a2full, a2empty, b2full, b2empty,
-// d2full, d2empty, done, merge_full, merge_empty, qfull[2], done2
-__host__ __device__ constexpr int fc_num_bars(int stages) { return 2 * stages + 4 + 6 + 3 + 2 + 1; }
+// full[S], empty[S], sfull[2], sempty[2], a2full, a2empty, b2full[0], b2empty[0],
+// d2full, d2empty, done, merge_full, merge_empty, qfull[2], done2, b2full[1], b2empty[1]
+__host__ __device__ constexpr int fc_num_bars(int stages) { return 2 * stages + 4 + 6 + 3 + 2 + 1 + 2; }
 
-__host__ __device__ constexpr size_t fc_smem_bytes(int stages, int Cp)
+__host__ __device__ constexpr size_t fc_smem_bytes(int stages, int Cp, int b2bufs)
 {
-    return 1024 + (size_t)stages * H_STAGE_BYTES + FC_A2_BYTES + (size_t)3 * Cp * 128 + fc_num_bars(stages) * 8 +
-           16 + (size_t)2 * BM * 8 * (HEWG - 1) + (size_t)2 * HEWG * BM * 4;
+    return 1024 + (size_t)stages * H_STAGE_BYTES + FC_A2_BYTES + (size_t)b2bufs * 3 * Cp * 128 +
+           fc_num_bars(stages) * 8 + 16 + (size_t)2 * BM * 8 * (HEWG - 1) + (size_t)2 * HEWG * BM * 4;
 }
-static_assert(fc_smem_bytes(3, FC_CMAX) <= 232448, "shared memory of the fused float-query kernel");
-static_assert(fc_smem_bytes(4, 16) <= 232448, "shared memory of the four-stage fused float-query kernel");
+static_assert(fc_smem_bytes(3, FC_CMAX, 1) <= 232448, "shared memory of the fused float-query kernel");
+static_assert(fc_smem_bytes(3, 32, 2) <= 232448, "shared memory of the double-buffered class tile");
 
 struct FCParams {
     int64_t N;
@@ -54,7 +57,7 @@ struct FCParams {
     double *scores;          // optional N x C
 };
 
-template <int ENC, int FC_STAGES>
+template <int ENC, int FC_STAGES, int B2BUF>
 __global__ void __launch_bounds__(FC_THREADS, 1)
     tc_fcos_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmV, const FCParams p)
@@ -64,8 +67,9 @@ __global__ void __launch_bounds__(FC_THREADS, 1)
     uint8_t *sA = smem;
     uint8_t *sB = smem + FC_STAGES * HA_BYTES;
     uint8_t *sA2 = smem + FC_STAGES * H_STAGE_BYTES;
-    uint8_t *sB2 = sA2 + FC_A2_BYTES;                               // 3 atoms x Cp rows x 128 B
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sB2 + 3 * p.Cp * 128);
+    uint8_t *sB2 = sA2 + FC_A2_BYTES;                               // B2BUF x 3 atoms x Cp rows x 128 B
+    const int b2_bytes = 3 * p.Cp * 128;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB2 + B2BUF * b2_bytes);
     constexpr int FC_NUM_BARS = fc_num_bars(FC_STAGES);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + FC_NUM_BARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -77,7 +81,8 @@ __global__ void __launch_bounds__(FC_THREADS, 1)
     auto sfull = [&](int a) { return su32(bars + 2 * FC_STAGES + a); };
     auto sempty = [&](int a) { return su32(bars + 2 * FC_STAGES + 2 + a); };
     const uint32_t a2full = su32(bars + 2 * FC_STAGES + 4), a2empty = su32(bars + 2 * FC_STAGES + 5);
-    const uint32_t b2full = su32(bars + 2 * FC_STAGES + 6), b2empty = su32(bars + 2 * FC_STAGES + 7);
+    auto b2full = [&](int b) { return su32(bars + 2 * FC_STAGES + (b ? 16 : 6)); };
+    auto b2empty = [&](int b) { return su32(bars + 2 * FC_STAGES + (b ? 17 : 7)); };
     const uint32_t d2full = su32(bars + 2 * FC_STAGES + 8), d2empty = su32(bars + 2 * FC_STAGES + 9);
     const uint32_t done_bar = su32(bars + 2 * FC_STAGES + 10);
     const uint32_t merge_full = su32(bars + 2 * FC_STAGES + 11), merge_empty = su32(bars + 2 * FC_STAGES + 12);
@@ -102,8 +107,10 @@ __global__ void __launch_bounds__(FC_THREADS, 1)
         }
         mbar_init(a2full, BM * HEWG);
         mbar_init(a2empty, 1);
-        mbar_init(b2full, 1);
-        mbar_init(b2empty, 1);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(b2full(b), 1);
+            mbar_init(b2empty(b), 1);
+        }
         mbar_init(d2full, 1);
         mbar_init(d2empty, BM * HEWG);
         mbar_init(done_bar, 1);
@@ -156,24 +163,29 @@ __global__ void __launch_bounds__(FC_THREADS, 1)
     } else if (warp == CPRODUCER) {
         if (lane == 0) {  // ------------------------------ class-value tile producer
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmV)) : "memory");
-            uint32_t ph = 0, last = 0;
-            bool any = false, ab = false;
+            uint32_t ph[2] = {0, 0}, last[2] = {0, 0};
+            bool any[2] = {false, false}, ab = false;
+            int bi = 0;
             const uint32_t bytes = 3u * (uint32_t)p.Cp * 128u;
             for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
                 for (int t = 0; t < p.nt; t++) {
-                    if (!mbar_wait(b2empty, ph ^ 1, abort_flag)) { ab = true; break; }
-                    mbar_expect_tx(b2full, bytes);
+                    if (!mbar_wait(b2empty(bi), ph[bi] ^ 1, abort_flag)) { ab = true; break; }
+                    mbar_expect_tx(b2full(bi), bytes);
 #pragma unroll
                     for (int a = 0; a < 3; a++)   // 64 BF16 of K per atom
-                        tma_load_2d(su32(sB2 + a * p.Cp * 128), &tmV, t * HBN + a * 64, 0, b2full);
-                    any = true;
-                    last = ph;
-                    ph ^= 1;
+                        tma_load_2d(su32(sB2 + bi * b2_bytes + a * p.Cp * 128), &tmV, t * HBN + a * 64, 0,
+                                    b2full(bi));
+                    any[bi] = true;
+                    last[bi] = ph[bi];
+                    ph[bi] ^= 1;
+                    if (++bi == B2BUF) bi = 0;
                 }
-            if (ab && any) {
-                const unsigned long long t0 = gtimer();
-                while (!mbar_try(b2full, last) && gtimer() - t0 < 100000000ull) {}
-            }
+            if (ab)
+                for (int b = 0; b < B2BUF; b++)
+                    if (any[b]) {
+                        const unsigned long long t0 = gtimer();
+                        while (!mbar_try(b2full(b), last[b]) && gtimer() - t0 < 100000000ull) {}
+                    }
         }
     } else if (warp == ISSUER) {
         if (lane == 0) {  // ------------------------------ MMA1 issuer (encode)
@@ -208,16 +220,17 @@ __global__ void __launch_bounds__(FC_THREADS, 1)
     } else if (warp == ISSUER2) {
         if (lane == 0) {  // ------------------------------ MMA2 issuer (cosine), its own commit chain
             const uint32_t id2 = idesc_n<HDC_ENC_BF16>(p.Cp);
-            uint32_t a2ph = 0, b2ph = 0, d2ph = 0;
+            uint32_t a2ph = 0, b2ph[2] = {0, 0}, d2ph = 0;
+            int bi = 0;
             bool ab = false;
             for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
                 for (int t = 0; t < p.nt; t++) {
                     const bool first = t == 0;
                     if (first && !mbar_wait(d2empty, d2ph ^ 1, abort_flag)) { ab = true; break; }
                     if (!mbar_wait(a2full, a2ph, abort_flag)) { ab = true; break; }
-                    if (!mbar_wait(b2full, b2ph, abort_flag)) { ab = true; break; }
+                    if (!mbar_wait(b2full(bi), b2ph[bi], abort_flag)) { ab = true; break; }
                     tc_fence_after();
-                    const uint32_t a0 = su32(sA2), b0 = su32(sB2);
+                    const uint32_t a0 = su32(sA2), b0 = su32(sB2 + bi * b2_bytes);
 #pragma unroll
                     for (int k = 0; k < 12; k++) {   // three atoms of four 16-element K steps
                         const uint32_t off_a = (uint32_t)((k >> 2) * A2_ATOM) + 32u * (k & 3);
@@ -226,9 +239,10 @@ __global__ void __launch_bounds__(FC_THREADS, 1)
                                           (first && k == 0) ? 0u : 1u);
                     }
                     mma_commit(a2empty);
-                    mma_commit(b2empty);
+                    mma_commit(b2empty(bi));
                     a2ph ^= 1;
-                    b2ph ^= 1;
+                    b2ph[bi] ^= 1;
+                    if (++bi == B2BUF) bi = 0;
                 }
                 if (ab) break;
                 mma_commit(d2full);
@@ -380,12 +394,12 @@ __global__ void __launch_bounds__(FC_THREADS, 1)
     }
 }
 
-template <int ENC, int STAGES>
+template <int ENC, int STAGES, int B2BUF>
 static cudaError_t launch_fcos_stages(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
                                       const FCParams &p, unsigned grid, cudaStream_t st)
 {
-    auto k = tc_fcos_kernel<ENC, STAGES>;
-    const size_t smem = fc_smem_bytes(STAGES, p.Cp);
+    auto k = tc_fcos_kernel<ENC, STAGES, B2BUF>;
+    const size_t smem = fc_smem_bytes(STAGES, p.Cp, B2BUF);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, FC_THREADS, smem, st>>>(ma, mb, mv, p);
@@ -396,8 +410,11 @@ template <int ENC>
 static cudaError_t launch_fcos_enc(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
                                    const FCParams &p, unsigned grid, cudaStream_t st)
 {
-    if (fc_smem_bytes(4, p.Cp) <= 232448) return launch_fcos_stages<ENC, 4>(ma, mb, mv, p, grid, st);
-    return launch_fcos_stages<ENC, 3>(ma, mb, mv, p, grid, st);
+    // a second class tile where it fits (small C), else a fourth A/B stage
+    // where that fits, else three stages and one class tile
+    if (fc_smem_bytes(3, p.Cp, 2) <= 232448) return launch_fcos_stages<ENC, 3, 2>(ma, mb, mv, p, grid, st);
+    if (fc_smem_bytes(4, p.Cp, 1) <= 232448) return launch_fcos_stages<ENC, 4, 1>(ma, mb, mv, p, grid, st);
+    return launch_fcos_stages<ENC, 3, 1>(ma, mb, mv, p, grid, st);
 }
 
 cudaError_t launch_fcos_bf16(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,

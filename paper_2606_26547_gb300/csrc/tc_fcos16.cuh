@@ -1,0 +1,363 @@
+// Fused classify of float (non-binarised) query hypervectors for at most 16
+// classes, on the binary classify's 256-dim encode tiles (Sec. 4.2
+// Algorithmic Choice; the float + cosine form of Sec. 5.2).
+//
+// For each 256-dim tile t of a 128-query block:
+//   S = Xq . Bq^T          (MMA1: M 128, N 256, K = F, BF16 or E4M3) into one
+//                          of two 256-column TMEM accumulators
+//   q = bf16(S * sb_k)     (epilogue: four warpgroups, 64 columns each, into a
+//                          128 x 256 BF16 operand; sum of q^2 kept per row)
+//   P_t = q . Cv_t^T       (MMA2: M 128, N 16, K 256, BF16) written into the
+//                          first 16 columns of tile t's own accumulator, whose
+//                          S values the epilogue has already read
+//   dot += P_t             (warpgroup 0, FP32 registers)
+// After the last tile: score_c = dot_c / (||q|| ||c||) in FP64 (0 for a zero
+// norm), arg-max with the lowest class on ties.  The projections never reach
+// device memory.  Reusing the encode accumulator for the cosine partials is
+// what lets the encode keep 256-dim tiles with both TMEM accumulators: 20
+// tiles of 7 stages per block at D' = 5,000 instead of 27 with 192-dim tiles.
+//
+// Roles: warps 0-15 epilogue, 16 stage producer, 17 MMA1 issuer, 18 class
+// tile producer, 19 MMA2 issuer.  Every wait is bounded as in the encoder.
+#pragma once
+#include "tc_fcos.cuh"
+
+namespace hdc {
+namespace tc {
+
+constexpr int F16_EWG = 4;                             // epilogue warpgroups, 64 columns of a tile each
+constexpr int F16_STAGES = 3;
+constexpr int F16_CP = 16;                             // class rows of MMA2
+constexpr int F16_THREADS = (4 * F16_EWG + 4) * 32;
+constexpr int F16_A2_BYTES = 4 * A2_ATOM;              // 128 rows x 256 BF16: four 128-byte K atoms
+constexpr int F16_B2_BYTES = 4 * F16_CP * 128;         // 16 class rows x 256 BF16: four atoms
+// full[S], empty[S], tfull[2], tempty[2], d2full[2], a2full, a2empty,
+// b2full, b2empty, qfull[2], done, done2
+constexpr int F16_NUM_BARS = 2 * F16_STAGES + 14;
+
+__host__ __device__ constexpr size_t f16_smem_bytes()
+{
+    return 1024 + (size_t)F16_STAGES * STAGE_BYTES + F16_A2_BYTES + F16_B2_BYTES + F16_NUM_BARS * 8 + 16 +
+           (size_t)2 * F16_EWG * BM * 4;
+}
+static_assert(f16_smem_bytes() <= 232448, "shared memory of the 16-class fused float-query kernel");
+
+template <int ENC>
+__global__ void __launch_bounds__(F16_THREADS, 1)
+    tc_fcos16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ CUtensorMap tmV, const FCParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + F16_STAGES * A_BYTES;
+    uint8_t *sA2 = smem + F16_STAGES * STAGE_BYTES;
+    uint8_t *sB2 = sA2 + F16_A2_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB2 + F16_B2_BYTES);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + F16_NUM_BARS);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    float *s_q = reinterpret_cast<float *>(tmem_slot + 4);   // 2 x [F16_EWG][BM] partial squared norms
+    constexpr int S = F16_STAGES;
+    auto full = [&](int s) { return su32(bars + s); };
+    auto empty = [&](int s) { return su32(bars + S + s); };
+    auto tfull = [&](int a) { return su32(bars + 2 * S + a); };
+    auto tempty = [&](int a) { return su32(bars + 2 * S + 2 + a); };
+    auto d2full = [&](int a) { return su32(bars + 2 * S + 4 + a); };
+    const uint32_t a2full = su32(bars + 2 * S + 6), a2empty = su32(bars + 2 * S + 7);
+    const uint32_t b2full = su32(bars + 2 * S + 8), b2empty = su32(bars + 2 * S + 9);
+    auto qfull = [&](int b) { return su32(bars + 2 * S + 10 + b); };
+    const uint32_t done_bar = su32(bars + 2 * S + 12), done2_bar = su32(bars + 2 * S + 13);
+    constexpr int PRODUCER = 4 * F16_EWG, ISSUER = PRODUCER + 1, CPRODUCER = PRODUCER + 2, ISSUER2 = PRODUCER + 3;
+    constexpr int KELEMS = ENC == HDC_ENC_BF16 ? BKB / 2 : BKB;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t num_m_tiles = (p.N + BM - 1) / BM;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; s++) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        for (int a = 0; a < 2; a++) {
+            mbar_init(tfull(a), 1);
+            mbar_init(tempty(a), BM * F16_EWG);
+            mbar_init(d2full(a), 1);
+            mbar_init(qfull(a), BM * F16_EWG);
+        }
+        mbar_init(a2full, BM * F16_EWG);
+        mbar_init(a2empty, 1);
+        mbar_init(b2full, 1);
+        mbar_init(b2empty, 1);
+        mbar_init(done_bar, 1);
+        mbar_init(done2_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == PRODUCER) {
+        if (lane == 0) {  // ------------------------------ A / B stage producer
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+            int stage = 0;
+            uint32_t phase = 0;
+            bool issued[S];
+            uint32_t ipar[S];
+            for (int s = 0; s < S; s++) { issued[s] = false; ipar[s] = 0; }
+            bool ab = false;
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
+                for (int t = 0; t < p.nt && !ab; t++)
+                    for (int kb = 0; kb < p.num_kb; kb++) {
+                        if (!mbar_wait(empty(stage), phase ^ 1, abort_flag)) { ab = true; break; }
+                        mbar_expect_tx(full(stage), STAGE_BYTES);
+                        tma_load_2d(su32(sA + stage * A_BYTES), &tmA, kb * KELEMS, (int)(mt * BM), full(stage));
+                        tma_load_2d(su32(sB + stage * B_BYTES), &tmB, kb * KELEMS, t * BN, full(stage));
+                        issued[stage] = true;
+                        ipar[stage] = phase;
+                        if (++stage == S) { stage = 0; phase ^= 1; }
+                    }
+            if (ab) {  // let our own copies land before the CTA exits
+                for (int s = 0; s < S; s++)
+                    if (issued[s]) {
+                        const unsigned long long t0 = gtimer();
+                        while (!mbar_try(full(s), ipar[s]) && gtimer() - t0 < 100000000ull) {}
+                    }
+            }
+        }
+    } else if (warp == CPRODUCER) {
+        if (lane == 0) {  // ------------------------------ class-value tile producer
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmV)) : "memory");
+            uint32_t ph = 0, last = 0;
+            bool any = false, ab = false;
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
+                for (int t = 0; t < p.nt; t++) {
+                    if (!mbar_wait(b2empty, ph ^ 1, abort_flag)) { ab = true; break; }
+                    mbar_expect_tx(b2full, (uint32_t)F16_B2_BYTES);
+#pragma unroll
+                    for (int a = 0; a < 4; a++)   // 64 BF16 of K per atom
+                        tma_load_2d(su32(sB2 + a * F16_CP * 128), &tmV, t * BN + a * 64, 0, b2full);
+                    any = true;
+                    last = ph;
+                    ph ^= 1;
+                }
+            if (ab && any) {
+                const unsigned long long t0 = gtimer();
+                while (!mbar_try(b2full, last) && gtimer() - t0 < 100000000ull) {}
+            }
+        }
+    } else if (warp == ISSUER) {
+        if (lane == 0) {  // ------------------------------ MMA1 issuer (encode)
+            const uint32_t id1 = idesc_n<ENC>(BN);
+            int stage = 0, acc = 0;
+            uint32_t phase = 0, aphase = 0;
+            bool ab = false;
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
+                for (int t = 0; t < p.nt && !ab; t++) {
+                    if (!mbar_wait(tempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
+                    tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)(acc * BN);
+                    for (int kb = 0; kb < p.num_kb; kb++) {
+                        if (!mbar_wait(full(stage), phase, abort_flag)) { ab = true; break; }
+                        tc_fence_after();
+                        const uint32_t a0 = su32(sA + stage * A_BYTES), b0 = su32(sB + stage * B_BYTES);
+#pragma unroll
+                        for (int k = 0; k < BKB / 32; k++)
+                            mma<ENC>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), id1, (kb | k) != 0);
+                        mma_commit(empty(stage));
+                        if (++stage == S) { stage = 0; phase ^= 1; }
+                    }
+                    if (ab) break;
+                    mma_commit(tfull(acc));
+                    if (++acc == 2) { acc = 0; aphase ^= 1; }
+                }
+            }
+            mma_commit(done_bar);
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try(done_bar, 0) && gtimer() - t0 < 100000000ull) {}
+        }
+    } else if (warp == ISSUER2) {
+        if (lane == 0) {  // ------------------------------ MMA2 issuer (the tile's cosine partials)
+            const uint32_t id2 = idesc_n<HDC_ENC_BF16>(F16_CP);
+            uint32_t a2ph = 0, b2ph = 0;
+            int acc = 0;
+            bool ab = false;
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
+                for (int t = 0; t < p.nt; t++) {
+                    if (!mbar_wait(a2full, a2ph, abort_flag)) { ab = true; break; }
+                    if (!mbar_wait(b2full, b2ph, abort_flag)) { ab = true; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = su32(sA2), b0 = su32(sB2);
+                    // into columns 0..15 of tile t's accumulator (its S values are read)
+                    const uint32_t d2 = tmem + (uint32_t)(acc * BN);
+#pragma unroll
+                    for (int k = 0; k < 16; k++) {   // four atoms of four 16-element K steps
+                        const uint32_t off_a = (uint32_t)((k >> 2) * A2_ATOM) + 32u * (k & 3);
+                        const uint32_t off_b = (uint32_t)((k >> 2) * F16_CP * 128) + 32u * (k & 3);
+                        mma<HDC_ENC_BF16>(d2, sdesc(a0 + off_a), sdesc(b0 + off_b), id2, k == 0 ? 0u : 1u);
+                    }
+                    mma_commit(a2empty);
+                    mma_commit(b2empty);
+                    mma_commit(d2full(acc));
+                    a2ph ^= 1;
+                    b2ph ^= 1;
+                    acc ^= 1;
+                }
+            mma_commit(done2_bar);
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try(done2_bar, 0) && gtimer() - t0 < 100000000ull) {}
+        }
+    } else {  // ------------------------------------------ epilogue warps 0 .. 15
+        const int q = warp & 3, g = warp >> 2;
+        const int r = q * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        uint8_t *a2row = sA2 + g * A2_ATOM + (r >> 3) * 1024 + (r & 7) * 128;   // atom g: this warpgroup's 64 dims
+        int acc = 0, qb = 0;
+        uint32_t aphase = 0, a2ph = 0, qph = 0;
+        bool ab = false;
+        for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
+            const int64_t row = mt * BM + r;
+            const bool valid = row < p.N;
+            float qsum = 0.f;
+            float dot[F16_CP];
+#pragma unroll
+            for (int c = 0; c < F16_CP; c++) dot[c] = 0.f;
+            for (int t = 0; t < p.nt; t++) {
+                const bool ok = mbar_wait(tfull(acc), aphase, abort_flag);
+                if (!__all_sync(0xffffffffu, ok)) { ab = true; break; }
+                tc_fence_after();
+                const int col0 = t * BN + g * 64;
+                bool okh = true;
+#pragma unroll 1
+                for (int h = 0; h < 2; h++) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + lane_base + (uint32_t)(acc * BN + g * 64 + 32 * h), v);
+                    const int c0 = col0 + 32 * h;
+                    uint32_t w[16];
+                    float qa = 0.f, qc = 0.f;   // two chains
+#pragma unroll
+                    for (int i8 = 0; i8 < 4; i8++) {   // eight columns at a time: BF16 of s * sb (zero past Dk)
+                        float sbv[8];
+                        if (c0 + 8 * i8 + 8 <= p.Dk) {
+                            if (p.sb) {
+                                const float4 *s4 = reinterpret_cast<const float4 *>(p.sb + c0 + 8 * i8);
+                                const float4 x0 = s4[0], x1 = s4[1];
+                                sbv[0] = x0.x; sbv[1] = x0.y; sbv[2] = x0.z; sbv[3] = x0.w;
+                                sbv[4] = x1.x; sbv[5] = x1.y; sbv[6] = x1.z; sbv[7] = x1.w;
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 8; i++) sbv[i] = 1.f;
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 8; i++) {
+                                const int c = c0 + 8 * i8 + i;
+                                sbv[i] = c < p.Dk ? (p.sb ? p.sb[c] : 1.f) : 0.f;
+                            }
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; i++) {
+                            const int k = 8 * i8 + 2 * i;
+                            const __nv_bfloat16 b0 = __float2bfloat16_rn(__uint_as_float(v[k]) * sbv[2 * i]);
+                            const __nv_bfloat16 b1 = __float2bfloat16_rn(__uint_as_float(v[k + 1]) * sbv[2 * i + 1]);
+                            const float g0 = __bfloat162float(b0), g1 = __bfloat162float(b1);
+                            qa = fmaf(g0, g0, qa);
+                            qc = fmaf(g1, g1, qc);
+                            w[k / 2] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+                        }
+                    }
+                    qsum += qa + qc;
+                    if (h == 0) {   // MMA2 of the previous tile has read the value tile
+                        const bool oka = mbar_wait(a2empty, a2ph ^ 1, abort_flag);
+                        if (!__all_sync(0xffffffffu, oka)) { okh = false; }
+                    }
+                    if (!okh) break;
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {   // 8 BF16 per 16-byte chunk, 128-byte swizzle
+                        const int ch = 4 * h + i;
+                        *reinterpret_cast<uint4 *>(a2row + ((ch ^ (r & 7)) * 16)) =
+                            make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+                    }
+                }
+                if (!okh) { ab = true; break; }
+                fence_async_smem();
+                tc_fence_before();
+                mbar_arrive(a2full);
+                a2ph ^= 1;
+                if (g == 0) {
+                    // this tile's cosine partials, in columns 0..15 of its accumulator
+                    const bool okd = mbar_wait(d2full(acc), aphase, abort_flag);
+                    if (!__all_sync(0xffffffffu, okd)) { ab = true; break; }
+                    tc_fence_after();
+                    uint32_t v[32];
+                    tmem_ld32(tmem + lane_base + (uint32_t)(acc * BN), v);
+#pragma unroll
+                    for (int c = 0; c < F16_CP; c++) dot[c] += __uint_as_float(v[c]);
+                    tc_fence_before();
+                }
+                mbar_arrive(tempty(acc));
+                if (++acc == 2) { acc = 0; aphase ^= 1; }
+            }
+            if (ab) break;
+            // the row's squared norm: the warpgroups' partial sums in order g = 0 .. 3
+            float *sq = s_q + (size_t)qb * F16_EWG * BM;
+            sq[g * BM + r] = qsum;
+            mbar_arrive(qfull(qb));
+            if (g == 0) {
+                const bool okq = mbar_wait(qfull(qb), qph, abort_flag);
+                if (!__all_sync(0xffffffffu, okq)) { ab = true; break; }
+                float qn = 0.f;
+#pragma unroll
+                for (int h = 0; h < F16_EWG; h++) qn += sq[h * BM + r];
+                const double qnorm = sqrt((double)qn);
+                int best = 0;
+                double bs = 0.0;
+#pragma unroll
+                for (int c = 0; c < F16_CP; c++)
+                    if (c < p.C) {
+                        const double den = qnorm * p.cnorm[c];
+                        const double sc = den == 0.0 ? 0.0 : (double)dot[c] / den;
+                        if (p.scores && valid) p.scores[row * p.C + c] = sc;
+                        if (c == 0 || sc > bs) { bs = sc; best = c; }   // ascending c: lowest on ties
+                    }
+                if (valid) p.labels[row] = best;
+            }
+            if (++qb == 2) { qb = 0; qph ^= 1; }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+template <int ENC>
+static cudaError_t launch_fcos16_enc(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
+                                     const FCParams &p, unsigned grid, cudaStream_t st)
+{
+    auto k = tc_fcos16_kernel<ENC>;
+    constexpr size_t smem = f16_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, F16_THREADS, smem, st>>>(ma, mb, mv, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fcos16_bf16(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
+                               const FCParams &p, unsigned grid, cudaStream_t st);
+cudaError_t launch_fcos16_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
+                              const FCParams &p, unsigned grid, cudaStream_t st);
+
+}  // namespace tc
+}  // namespace hdc
