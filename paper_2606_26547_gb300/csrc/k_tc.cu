@@ -205,8 +205,19 @@ cudaError_t launch_tc_fcos(const TcArgs &a, const uint16_t *cv, int ldS, const d
     const int64_t m_tiles = (a.N + tc::BM - 1) / tc::BM;
     const unsigned grid = (unsigned)(m_tiles < sms ? m_tiles : sms);
     if (small_c) {
-        if (a.enc == HDC_ENC_BF16) return tc::launch_fcos16_bf16(ma, mb, mv, p, grid, st);
-        return tc::launch_fcos16_fp8(ma, mb, mv, p, grid, st);
+        CUtensorMap ms = mv;   // unread without scales (BF16)
+        if (a.sb) {            // the Dk base-row scales as one row, boxes of one tile, zero past Dk
+            cuuint64_t dims[2] = {(cuuint64_t)a.Dk, 1};
+            cuuint64_t strides[1] = {((cuuint64_t)a.Dk * 4 + 15) / 16 * 16};
+            cuuint32_t box[2] = {(cuuint32_t)tc::BN, 1};
+            cuuint32_t estr[2] = {1, 1};
+            if (fn(&ms, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(a.sb), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return cudaErrorInvalidValue;
+        }
+        if (a.enc == HDC_ENC_BF16) return tc::launch_fcos16_bf16(ma, mb, mv, ms, p, grid, st);
+        return tc::launch_fcos16_fp8(ma, mb, mv, ms, p, grid, st);
     }
     if (a.enc == HDC_ENC_BF16) return tc::launch_fcos_bf16(ma, mb, mv, p, grid, st);
     return tc::launch_fcos_fp8(ma, mb, mv, p, grid, st);

@@ -26,9 +26,9 @@ cudaError_t launch_fcos_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const 
 }
 
 cudaError_t launch_fcos16_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
-                               const FCParams &p, unsigned grid, cudaStream_t st)
+                               const CUtensorMap &ms, const FCParams &p, unsigned grid, cudaStream_t st)
 {
-    return launch_fcos16_enc<HDC_ENC_FP8_E4M3>(ma, mb, mv, p, grid, st);
+    return launch_fcos16_enc<HDC_ENC_FP8_E4M3>(ma, mb, mv, ms, p, grid, st);
 }
 
 }  // namespace tc

@@ -6,7 +6,9 @@
 //   S = Xq . Bq^T          (MMA1: M 128, N 256, K = F, BF16 or E4M3) into one
 //                          of two 256-column TMEM accumulators
 //   q = bf16(S * sb_k)     (epilogue: four warpgroups, 64 columns each, into a
-//                          128 x 256 BF16 operand; sum of q^2 kept per row)
+//                          128 x 256 BF16 operand; sum of q^2 kept per row;
+//                          the tile's 256 base-row scales arrive in shared
+//                          memory with its class values, zero past D')
 //   P_t = q . Cv_t^T       (MMA2: M 128, N 16, K 256, BF16) written into the
 //                          first 16 columns of tile t's own accumulator, whose
 //                          S values the epilogue has already read
@@ -31,13 +33,14 @@ constexpr int F16_CP = 16;                             // class rows of MMA2
 constexpr int F16_THREADS = (4 * F16_EWG + 4) * 32;
 constexpr int F16_A2_BYTES = 4 * A2_ATOM;              // 128 rows x 256 BF16: four 128-byte K atoms
 constexpr int F16_B2_BYTES = 4 * F16_CP * 128;         // 16 class rows x 256 BF16: four atoms
+constexpr int F16_SB_BYTES = BN * 4;                   // the tile's base-row scales (FP8)
 // full[S], empty[S], tfull[2], tempty[2], d2full[2], a2full, a2empty,
 // b2full, b2empty, qfull[2], done, done2
 constexpr int F16_NUM_BARS = 2 * F16_STAGES + 14;
 
 __host__ __device__ constexpr size_t f16_smem_bytes()
 {
-    return 1024 + (size_t)F16_STAGES * STAGE_BYTES + F16_A2_BYTES + F16_B2_BYTES + F16_NUM_BARS * 8 + 16 +
+    return 1024 + (size_t)F16_STAGES * STAGE_BYTES + F16_A2_BYTES + F16_B2_BYTES + F16_SB_BYTES + F16_NUM_BARS * 8 + 16 +
            (size_t)2 * F16_EWG * BM * 4;
 }
 static_assert(f16_smem_bytes() <= 232448, "shared memory of the 16-class fused float-query kernel");
@@ -45,7 +48,8 @@ static_assert(f16_smem_bytes() <= 232448, "shared memory of the 16-class fused f
 template <int ENC>
 __global__ void __launch_bounds__(F16_THREADS, 1)
     tc_fcos16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     const __grid_constant__ CUtensorMap tmV, const FCParams p)
+                     const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmS,
+                     const FCParams p)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -53,7 +57,8 @@ __global__ void __launch_bounds__(F16_THREADS, 1)
     uint8_t *sB = smem + F16_STAGES * A_BYTES;
     uint8_t *sA2 = smem + F16_STAGES * STAGE_BYTES;
     uint8_t *sB2 = sA2 + F16_A2_BYTES;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sB2 + F16_B2_BYTES);
+    float *s_sb = reinterpret_cast<float *>(sB2 + F16_B2_BYTES);   // BN scales of the tile (FP8)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB2 + F16_B2_BYTES + F16_SB_BYTES);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + F16_NUM_BARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     float *s_q = reinterpret_cast<float *>(tmem_slot + 4);   // 2 x [F16_EWG][BM] partial squared norms
@@ -136,15 +141,17 @@ __global__ void __launch_bounds__(F16_THREADS, 1)
     } else if (warp == CPRODUCER) {
         if (lane == 0) {  // ------------------------------ class-value tile producer
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmV)) : "memory");
+            const bool has_sb = p.sb != nullptr;
             uint32_t ph = 0, last = 0;
             bool any = false, ab = false;
             for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
                 for (int t = 0; t < p.nt; t++) {
                     if (!mbar_wait(b2empty, ph ^ 1, abort_flag)) { ab = true; break; }
-                    mbar_expect_tx(b2full, (uint32_t)F16_B2_BYTES);
+                    mbar_expect_tx(b2full, (uint32_t)(F16_B2_BYTES + (has_sb ? F16_SB_BYTES : 0)));
 #pragma unroll
                     for (int a = 0; a < 4; a++)   // 64 BF16 of K per atom
                         tma_load_2d(su32(sB2 + a * F16_CP * 128), &tmV, t * BN + a * 64, 0, b2full);
+                    if (has_sb) tma_load_2d(su32(s_sb), &tmS, t * BN, 0, b2full);
                     any = true;
                     last = ph;
                     ph ^= 1;
@@ -221,8 +228,9 @@ __global__ void __launch_bounds__(F16_THREADS, 1)
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         uint8_t *a2row = sA2 + g * A2_ATOM + (r >> 3) * 1024 + (r & 7) * 128;   // atom g: this warpgroup's 64 dims
         int acc = 0, qb = 0;
-        uint32_t aphase = 0, a2ph = 0, qph = 0;
+        uint32_t aphase = 0, a2ph = 0, qph = 0, b2ph = 0;
         bool ab = false;
+        const bool has_sb = p.sb != nullptr;
         for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
             const int64_t row = mt * BM + r;
             const bool valid = row < p.N;
@@ -234,45 +242,37 @@ __global__ void __launch_bounds__(F16_THREADS, 1)
                 const bool ok = mbar_wait(tfull(acc), aphase, abort_flag);
                 if (!__all_sync(0xffffffffu, ok)) { ab = true; break; }
                 tc_fence_after();
-                const int col0 = t * BN + g * 64;
+                if (has_sb) {   // the tile's scales (read before MMA2 of this tile frees the buffer)
+                    const bool oks = mbar_wait(b2full, b2ph, abort_flag);
+                    if (!__all_sync(0xffffffffu, oks)) { ab = true; break; }
+                }
+                b2ph ^= 1;
                 bool okh = true;
 #pragma unroll 1
                 for (int h = 0; h < 2; h++) {
                     uint32_t v[32];
                     tmem_ld32(tmem + lane_base + (uint32_t)(acc * BN + g * 64 + 32 * h), v);
-                    const int c0 = col0 + 32 * h;
+                    // BF16 of s * sb; past D' the projections are zero (zero base rows)
+                    const float4 *s4 = reinterpret_cast<const float4 *>(s_sb + g * 64 + 32 * h);
                     uint32_t w[16];
                     float qa = 0.f, qc = 0.f;   // two chains
 #pragma unroll
-                    for (int i8 = 0; i8 < 4; i8++) {   // eight columns at a time: BF16 of s * sb (zero past Dk)
-                        float sbv[8];
-                        if (c0 + 8 * i8 + 8 <= p.Dk) {
-                            if (p.sb) {
-                                const float4 *s4 = reinterpret_cast<const float4 *>(p.sb + c0 + 8 * i8);
-                                const float4 x0 = s4[0], x1 = s4[1];
-                                sbv[0] = x0.x; sbv[1] = x0.y; sbv[2] = x0.z; sbv[3] = x0.w;
-                                sbv[4] = x1.x; sbv[5] = x1.y; sbv[6] = x1.z; sbv[7] = x1.w;
-                            } else {
-#pragma unroll
-                                for (int i = 0; i < 8; i++) sbv[i] = 1.f;
-                            }
-                        } else {
-#pragma unroll
-                            for (int i = 0; i < 8; i++) {
-                                const int c = c0 + 8 * i8 + i;
-                                sbv[i] = c < p.Dk ? (p.sb ? p.sb[c] : 1.f) : 0.f;
-                            }
-                        }
-#pragma unroll
-                        for (int i = 0; i < 4; i++) {
-                            const int k = 8 * i8 + 2 * i;
-                            const __nv_bfloat16 b0 = __float2bfloat16_rn(__uint_as_float(v[k]) * sbv[2 * i]);
-                            const __nv_bfloat16 b1 = __float2bfloat16_rn(__uint_as_float(v[k + 1]) * sbv[2 * i + 1]);
-                            const float g0 = __bfloat162float(b0), g1 = __bfloat162float(b1);
-                            qa = fmaf(g0, g0, qa);
-                            qc = fmaf(g1, g1, qc);
-                            w[k / 2] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
-                        }
+                    for (int i4 = 0; i4 < 8; i4++) {
+                        const float4 sv = has_sb ? s4[i4] : make_float4(1.f, 1.f, 1.f, 1.f);
+                        const __nv_bfloat162 b01 = __floats2bfloat162_rn(__uint_as_float(v[4 * i4]) * sv.x,
+                                                                         __uint_as_float(v[4 * i4 + 1]) * sv.y);
+                        const __nv_bfloat162 b23 = __floats2bfloat162_rn(__uint_as_float(v[4 * i4 + 2]) * sv.z,
+                                                                         __uint_as_float(v[4 * i4 + 3]) * sv.w);
+                        const uint32_t u01 = *reinterpret_cast<const uint32_t *>(&b01);
+                        const uint32_t u23 = *reinterpret_cast<const uint32_t *>(&b23);
+                        const float g0 = __uint_as_float(u01 << 16), g1 = __uint_as_float(u01 & 0xffff0000u);
+                        const float g2 = __uint_as_float(u23 << 16), g3 = __uint_as_float(u23 & 0xffff0000u);
+                        qa = fmaf(g0, g0, qa);
+                        qc = fmaf(g1, g1, qc);
+                        qa = fmaf(g2, g2, qa);
+                        qc = fmaf(g3, g3, qc);
+                        w[2 * i4] = u01;
+                        w[2 * i4 + 1] = u23;
                     }
                     qsum += qa + qc;
                     if (h == 0) {   // MMA2 of the previous tile has read the value tile
@@ -342,22 +342,24 @@ __global__ void __launch_bounds__(F16_THREADS, 1)
     }
 }
 
+// ms: map of the Dk base-row scales as one row (box BN, zero fill past Dk); any
+// map when p.sb is NULL (BF16), then it is not read.
 template <int ENC>
 static cudaError_t launch_fcos16_enc(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
-                                     const FCParams &p, unsigned grid, cudaStream_t st)
+                                     const CUtensorMap &ms, const FCParams &p, unsigned grid, cudaStream_t st)
 {
     auto k = tc_fcos16_kernel<ENC>;
     constexpr size_t smem = f16_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, F16_THREADS, smem, st>>>(ma, mb, mv, p);
+    k<<<grid, F16_THREADS, smem, st>>>(ma, mb, mv, ms, p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fcos16_bf16(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
-                               const FCParams &p, unsigned grid, cudaStream_t st);
+                               const CUtensorMap &ms, const FCParams &p, unsigned grid, cudaStream_t st);
 cudaError_t launch_fcos16_fp8(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mv,
-                              const FCParams &p, unsigned grid, cudaStream_t st);
+                              const CUtensorMap &ms, const FCParams &p, unsigned grid, cudaStream_t st);
 
 }  // namespace tc
 }  // namespace hdc
