@@ -333,10 +333,10 @@ hdc_status hdc_hamming_argmin(const uint32_t *Q, const uint32_t *Cls, int64_t N,
 namespace {
 // Training workspace: predictions, the class-grouped sample order, the
 // counting-sort histogram / offsets / first work item per group / cursors,
-// and the byte-lane bit counts of every counting item (32 bytes per item and
-// word).
+// the byte-lane bit counts of every counting item (32 bytes per item and
+// word), and for 33..256 classes the class hypervectors expanded to bytes.
 struct TrainLayout {
-    size_t pred, perm, hist, offsets, items, cursor, partial, total;
+    size_t pred, perm, hist, offsets, items, cursor, partial, signs, total;
 };
 TrainLayout train_layout(int64_t N, int D, int C)
 {
@@ -352,6 +352,7 @@ TrainLayout train_layout(int64_t N, int D, int C)
     L.offsets = off; off = align_up(off + (size_t)(2 * C + 1) * 4, kAlign);
     L.items = off;   off = align_up(off + (size_t)(2 * C + 1) * 4, kAlign);
     L.partial = off; off = align_up(off + (size_t)train_max_items(N, C) * words_for(D) * 32, kAlign);
+    L.signs = off;   off = align_up(off + class_sign_bytes(C, words_for(D)), kAlign);
     L.total = off;
     return L;
 }
@@ -391,7 +392,8 @@ hdc_status hdc_train_epoch(const uint32_t *H, const int32_t *y, int64_t N, int32
         return mode == 2 ? HDC_OK : cu(launch_binarise(acc, C, D, cls, W, st));
     }
     TrainScratch sc = {(int32_t *)(w + L.perm), (int32_t *)(w + L.hist), (int32_t *)(w + L.offsets),
-                       (int32_t *)(w + L.items), (int32_t *)(w + L.cursor), (uint32_t *)(w + L.partial)};
+                       (int32_t *)(w + L.items), (int32_t *)(w + L.cursor), (uint32_t *)(w + L.partial),
+                       class_sign_bytes(C, W) ? (uint8_t *)(w + L.signs) : nullptr};
     // mode 2 (a shard's delta) leaves cls as the start-of-epoch classes
     return cu(launch_train_pass(H, W, y, N, D, C, mode, cls, (int32_t *)(w + L.pred), acc,
                                 mode == 2 ? nullptr : cls, n_updates, sc, st));

@@ -99,10 +99,23 @@ cudaError_t launch_argmin_groups(const uint32_t *H, int64_t N, const uint32_t *c
 // Scratch (train_max_items(N, C) counting items): perm (2N int32), hist and
 // cursor (2C int32), offsets and items (2C + 1 int32), partial (max items x
 // W x 8 uint32 byte lanes).
+// signs: for 33..256 classes, Cp x hamming_packed_ldcs(W) bytes for the
+// class hypervectors expanded once per epoch (NULL: the Hamming kernel
+// expands them itself).
 struct TrainScratch {
     int32_t *perm, *hist, *offsets, *items, *cursor;
     uint32_t *partial;
+    uint8_t *signs;
 };
+// Bytes of the expanded class hypervectors the training and clustering
+// workspaces hold (0 outside 33..256 classes).
+size_t class_sign_bytes(int C, int W);
+// Hamming arg-min of N packed rows against C classes over the kept dims
+// (s0, s0 + stride, ... < e0; all of [0, D) for a stride-1 full range): the
+// library's routes, with the class hypervectors expanded into `signs`
+// (class_sign_bytes(C, W), or NULL) for the tensor-core route.
+cudaError_t launch_argmin_ws(const uint32_t *H, int64_t N, const uint32_t *cls, int C, int W, int64_t D,
+                             const Perf *p, int32_t *labels, uint8_t *signs, cudaStream_t st);
 int64_t train_max_items(int64_t N, int C);
 cudaError_t launch_train_pass(const uint32_t *H, int W, const int32_t *y, int64_t N, int D, int C, int mode,
                               const uint32_t *cls_in, int32_t *pred, int32_t *acc, uint32_t *cls_out,
@@ -154,9 +167,13 @@ cudaError_t tc_read_status(cudaStream_t st, int *status);
 // Hamming arg-min of packed rows on the tensor cores (17 <= C <= 256 binary
 // classes, W a multiple of 4 up to 4096): kept dims s0 + k*stride < min(e0, D).
 bool hamming_packed_ok(int C, int W);
+// cls_sign (optional): the class hypervectors already expanded by
+// launch_class_sign(cls, C, W, Dk, Cp, hamming_packed_ldcs(W), cls_sign) --
+// the kernel then streams them instead of expanding the class words itself.
+int hamming_packed_ldcs(int W);
 cudaError_t launch_hamming_packed(const uint32_t *Q, int64_t N, const uint32_t *cls, int C, int W, int64_t D,
                                   int64_t s0, int64_t e0, int64_t stride, int32_t *labels, int32_t *dists,
-                                  cudaStream_t st);
+                                  cudaStream_t st, const uint8_t *cls_sign = nullptr);
 // One block waiting, bounded by limit_ns, on a barrier nothing arrives on
 // (the expiry is reported through tc_read_status).
 cudaError_t launch_wait_selftest(unsigned long long limit_ns, cudaStream_t st);

@@ -29,7 +29,7 @@ __global__ void count_changes_kernel(const int32_t *__restrict__ cur, const int3
 }
 
 struct ClusterLayout {
-    size_t lab0, lab1, train, total;
+    size_t lab0, lab1, signs, train, total;
 };
 
 bool cluster_layout(int64_t N, int D, int K, ClusterLayout *L)
@@ -39,6 +39,8 @@ bool cluster_layout(int64_t N, int D, int K, ClusterLayout *L)
     size_t off = 0;
     L->lab0 = off;  off = align_up(off + (size_t)N * 4, kAlign);
     L->lab1 = off;  off = align_up(off + (size_t)N * 4, kAlign);
+    // the cluster hypervectors expanded to bytes for the assignment (K > 32)
+    L->signs = off; off = align_up(off + class_sign_bytes(K, words_for(D)), kAlign);
     L->train = off; off = align_up(off + tb, kAlign);
     L->total = off;
     return true;
@@ -47,6 +49,13 @@ bool cluster_layout(int64_t N, int D, int K, ClusterLayout *L)
 bool sim_ok(const hdc_approx_config *c)
 {
     return !c || (c->struct_size >= sizeof(hdc_approx_config) && c->class_bits == 1);
+}
+
+// The kept dims of a similarity op (NULL when every dim of D is kept).
+const Perf *perf_or_null(int64_t D, const hdc_approx_config *c, Perf *p)
+{
+    if (!c || !perf_of(D, c, p)) return nullptr;
+    return (p->s0 == 0 && p->e0 == D && p->stride == 1) ? nullptr : p;
 }
 
 }  // namespace
@@ -83,20 +92,24 @@ extern "C" hdc_status hdc_cluster(const uint32_t *H, int64_t N, int32_t D, int32
     cudaStream_t st = (cudaStream_t)stream;
     char *w = (char *)ws;
     int32_t *lab[2] = {(int32_t *)(w + L.lab0), (int32_t *)(w + L.lab1)};
+    uint8_t *signs = class_sign_bytes(K, words_for(D)) ? (uint8_t *)(w + L.signs) : nullptr;
+    const int W = words_for(D);
+    Perf pt, pi;
+    const Perf *ptrain = perf_or_null(D, train_sim, &pt), *pinfer = perf_or_null(D, infer_sim, &pi);
     if (changes && iters > 0 && cudaMemsetAsync(changes, 0, (size_t)iters * sizeof(int32_t), st) != cudaSuccess)
         return HDC_ERR_CUDA;
     if (N == 0) return HDC_OK;
     for (int t = 0; t < iters; t++) {
         int32_t *cur = lab[t & 1], *prev = lab[(t + 1) & 1];
-        hdc_status s = hdc_hamming_argmin(H, cls, N, K, D, train_sim, cur, nullptr, stream);
-        if (s != HDC_OK) return s;
+        if (launch_argmin_ws(H, N, cls, K, W, D, ptrain, cur, signs, st) != cudaSuccess) return HDC_ERR_CUDA;
         if (changes) {
             const int blocks = (int)std::min<int64_t>((N + 255) / 256, 4096);
             count_changes_kernel<<<blocks, 256, 0, st>>>(cur, prev, N, t == 0, changes + t);
             if (cudaGetLastError() != cudaSuccess) return HDC_ERR_CUDA;
         }
-        s = hdc_train_epoch(H, cur, N, D, K, 0, acc, cls, nullptr, w + L.train, ws_bytes - L.train, stream);
+        hdc_status s = hdc_train_epoch(H, cur, N, D, K, 0, acc, cls, nullptr, w + L.train, ws_bytes - L.train,
+                                       stream);
         if (s != HDC_OK) return s;
     }
-    return hdc_hamming_argmin(H, cls, N, K, D, infer_sim, labels, nullptr, stream);
+    return launch_argmin_ws(H, N, cls, K, W, D, pinfer, labels, signs, st) == cudaSuccess ? HDC_OK : HDC_ERR_CUDA;
 }

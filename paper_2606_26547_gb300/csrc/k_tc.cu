@@ -85,6 +85,12 @@ int sm_count()
 
 }  // namespace
 
+// The class-byte map for the other tensor-core translation units.
+bool make_class_sign_map(CUtensorMap *m, const uint8_t *signs, int ldcs, int Cp)
+{
+    return make_sign_map(m, signs, ldcs, Cp);
+}
+
 bool tc_supported(const TcArgs &a)
 {
     if (a.enc != HDC_ENC_BF16 && a.enc != HDC_ENC_FP8_E4M3) return false;

@@ -1,9 +1,15 @@
 // Auxiliary tensor-core kernels in a translation unit of their own (with
 // its own device status word): the Hamming arg-min of packed hypervectors
 // and the failure-detection self-test.
+#include <string.h>
+
 #include "tc_hamming_packed.cuh"
 
 namespace hdc {
+
+// Tensor map of E4M3 class bytes (Cp rows of ldcs bytes, boxes of 128 bytes x
+// Cp rows, 128-byte swizzle), defined with the other map builders.
+bool make_class_sign_map(CUtensorMap *m, const uint8_t *signs, int ldcs, int Cp);
 namespace tc {
 
 // Failure-detection self-test: thread 0 waits, through the bounded-wait
@@ -29,12 +35,18 @@ bool hamming_packed_ok(int C, int W)
     return C > 16 && C <= tc::HP_CMAX && W > 0 && W <= tc::HP_MAX_W && W % 4 == 0;
 }
 
+int hamming_packed_ldcs(int W) { return (W + 7) / 8 * 256; }
+
 cudaError_t launch_hamming_packed(const uint32_t *Q, int64_t N, const uint32_t *cls, int C, int W, int64_t D,
                                   int64_t s0, int64_t e0, int64_t stride, int32_t *labels, int32_t *dists,
-                                  cudaStream_t st)
+                                  cudaStream_t st, const uint8_t *cls_sign)
 {
     if (N <= 0) return cudaSuccess;
     if (!hamming_packed_ok(C, W) || stride < 1) return cudaErrorNotSupported;
+    CUtensorMap mc;
+    memset(&mc, 0, sizeof(mc));
+    if (cls_sign && !make_class_sign_map(&mc, cls_sign, hamming_packed_ldcs(W), (C + 15) / 16 * 16))
+        return cudaErrorInvalidValue;
     tc::HPParams p;
     p.Q = Q;
     p.cls = cls;
@@ -60,13 +72,17 @@ cudaError_t launch_hamming_packed(const uint32_t *Q, int64_t N, const uint32_t *
     const size_t smem2 = tc::hp_smem_bytes(p.Cp, W, 2), smem1 = tc::hp_smem_bytes(p.Cp, W, 1);
     const bool two = fits2(smem2) || fits2(smem1);
     const size_t smem = fits2(smem2) ? smem2 : fits2(smem1) ? smem1 : smem2;
-    auto k = fits2(smem2) ? tc::tc_hamming_packed_kernel<2, 2>
-                          : fits2(smem1) ? tc::tc_hamming_packed_kernel<2, 1> : tc::tc_hamming_packed_kernel<1, 2>;
+    auto k = cls_sign ? (fits2(smem2) ? tc::tc_hamming_packed_kernel<2, 2, true>
+                                      : fits2(smem1) ? tc::tc_hamming_packed_kernel<2, 1, true>
+                                                     : tc::tc_hamming_packed_kernel<1, 2, true>)
+                      : (fits2(smem2) ? tc::tc_hamming_packed_kernel<2, 2, false>
+                                      : fits2(smem1) ? tc::tc_hamming_packed_kernel<2, 1, false>
+                                                     : tc::tc_hamming_packed_kernel<1, 2, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t slots = (int64_t)sms * (two ? 2 : 1);
     const unsigned grid = (unsigned)(tiles < slots ? tiles : slots);
-    k<<<grid, tc::HP_THREADS, smem, st>>>(p);
+    k<<<grid, tc::HP_THREADS, smem, st>>>(p, mc);
     return cudaGetLastError();
 }
 

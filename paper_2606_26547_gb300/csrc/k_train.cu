@@ -493,7 +493,7 @@ cudaError_t launch_train_pass(const uint32_t *H, int W, const int32_t *y, int64_
         if (e == cudaSuccess) {
             hist_ready = true;
         } else if (e == cudaErrorNotSupported) {
-            e = launch_similarity(H, N, cls_in, C, W, 1, D, nullptr, nullptr, nullptr, pred, nullptr, nullptr, st);
+            e = launch_argmin_ws(H, N, cls_in, C, W, D, nullptr, pred, s.signs, st);
             if (e != cudaSuccess) return e;
         } else {
             return e;
@@ -517,6 +517,27 @@ cudaError_t launch_binarise(const int32_t *acc, int C, int D, uint32_t *cls, int
 {
     // without a delta the kernel only reads acc
     return launch_apply_binarise(nullptr, const_cast<int32_t *>(acc), C, D, cls, W, st);
+}
+
+size_t class_sign_bytes(int C, int W)
+{
+    if (C <= 32 || !hamming_packed_ok(C, W)) return 0;
+    return (size_t)((C + 15) / 16 * 16) * hamming_packed_ldcs(W);
+}
+
+cudaError_t launch_argmin_ws(const uint32_t *H, int64_t N, const uint32_t *cls, int C, int W, int64_t D,
+                             const Perf *p, int32_t *labels, uint8_t *signs, cudaStream_t st)
+{
+    if (N <= 0) return cudaSuccess;
+    if (signs && class_sign_bytes(C, W) > 0) {
+        // expand the classes once, then stream them to the tensor-core route
+        const int Cp = (C + 15) / 16 * 16;
+        cudaError_t e = launch_class_sign(cls, C, W, (int)D, Cp, hamming_packed_ldcs(W), signs, st);
+        if (e != cudaSuccess) return e;
+        return launch_hamming_packed(H, N, cls, C, W, D, p ? p->s0 : 0, p ? p->e0 : D, p ? p->stride : 1, labels,
+                                     nullptr, st, signs);
+    }
+    return launch_similarity(H, N, cls, C, W, 1, D, p, nullptr, nullptr, labels, nullptr, nullptr, st);
 }
 
 }  // namespace hdc

@@ -19,6 +19,12 @@
 // half) and the class tile, double buffered, and afterwards read D2 (two
 // warpgroups, alternate 32-class chunks, merged by (distance, class));
 // warp 8 issues the MMAs.  Every wait is bounded as in the encoder.
+//
+// PRE: the class hypervectors come already expanded (E4M3 +-1 bytes, Cp rows
+// of ldcs bytes, from launch_class_sign into the caller's workspace), and
+// thread 0 streams each tile's two class atoms by TMA on a barrier of their
+// own; the expanders then expand only the query rows.  Classes outside the
+// kept dims need no zeros there: the query bytes are zero outside K.
 #pragma once
 #include "tc_hamming.cuh"
 
@@ -31,8 +37,8 @@ constexpr int HP_THREADS = HP_EXP + 32;
 constexpr int HP_CMAX = 256;
 constexpr int HP_A_BYTES = 2 * BM * 128;       // query tile: two atoms of 128 rows x 128 bytes
 constexpr int HP_MAX_W = 4096;                 // words of a packed row (D <= 131072)
-// full[2], empty[2], d2full, d2empty, merge_full, merge_empty, done
-constexpr int HP_NUM_BARS = 9;
+// full[2], empty[2], d2full, d2empty, merge_full, merge_empty, done, cfull[2]
+constexpr int HP_NUM_BARS = 11;
 
 // bbuf: class-tile buffers (2, or 1 so that two CTAs fit per SM)
 __host__ __device__ constexpr size_t hp_smem_bytes(int Cp, int W, int bbuf = 2)
@@ -92,8 +98,9 @@ __device__ __forceinline__ void expand_row(uint8_t *atom, int r, const uint4 w, 
 // MINB = 2: two CTAs per SM, registers capped to fit.  BBUF = 1: one
 // class-tile buffer (so two CTAs fit with larger class tiles): the class rows
 // of tile t are written once the MMAs of tile t - 1 have read them.
-template <int MINB, int BBUF>
-__global__ void __launch_bounds__(HP_THREADS, MINB) tc_hamming_packed_kernel(const HPParams p)
+template <int MINB, int BBUF, bool PRE>
+__global__ void __launch_bounds__(HP_THREADS, MINB)
+    tc_hamming_packed_kernel(const HPParams p, const __grid_constant__ CUtensorMap tmC)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -111,6 +118,7 @@ __global__ void __launch_bounds__(HP_THREADS, MINB) tc_hamming_packed_kernel(con
     auto empty = [&](int b) { return su32(bars + 2 + b); };
     const uint32_t d2full = su32(bars + 4), d2empty = su32(bars + 5);
     const uint32_t merge_full = su32(bars + 6), merge_empty = su32(bars + 7), done_bar = su32(bars + 8);
+    auto cfull = [&](int b) { return su32(bars + 9 + b); };   // PRE: the class atoms of buffer b landed
     constexpr int ISSUER = HP_EXP / 32;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -126,6 +134,7 @@ __global__ void __launch_bounds__(HP_THREADS, MINB) tc_hamming_packed_kernel(con
         mbar_init(merge_full, BM);
         mbar_init(merge_empty, BM);
         mbar_init(done_bar, 1);
+        for (int b = 0; b < 2; b++) mbar_init(cfull(b), 1);
         *abort_flag = 0;
         *s_kept = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -164,12 +173,17 @@ __global__ void __launch_bounds__(HP_THREADS, MINB) tc_hamming_packed_kernel(con
         if (lane == 0) {  // ------------------------------ MMA issuer
             const uint32_t id = idesc_n<HDC_ENC_FP8_E4M3>(p.Cp);
             int buf = 0;
-            uint32_t ph = 0, d2ph = 0;
+            uint32_t ph = 0, d2ph = 0, cph[2] = {0, 0};
             bool ab = false;
             for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
                 if (!mbar_wait(d2empty, d2ph ^ 1, abort_flag)) { ab = true; break; }
                 for (int t = 0; t < p.nt; t++) {
                     if (!mbar_wait(full(buf), ph, abort_flag)) { ab = true; break; }
+                    if (PRE) {
+                        const int cb = BBUF == 2 ? buf : 0;
+                        if (!mbar_wait(cfull(cb), cph[cb], abort_flag)) { ab = true; break; }
+                        cph[cb] ^= 1;
+                    }
                     tc_fence_after();
                     const uint32_t a0 = su32(sA + buf * HP_A_BYTES), b0 = su32(sB + (BBUF == 2 ? buf : 0) * b_bytes);
 #pragma unroll
@@ -197,6 +211,7 @@ __global__ void __launch_bounds__(HP_THREADS, MINB) tc_hamming_packed_kernel(con
         uint32_t ph = 0, d2ph = 0;
         bool ab = false;
         int64_t it = 0, gt = 0;   // gt: tiles expanded by this CTA
+        uint32_t c_issued = 0, c_par = 0, c_ph[2] = {0, 0};   // PRE (thread 0): class copies in flight
         for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++) {
             const int64_t row = mt * BM + r;
             const bool valid = row < p.N;
@@ -216,15 +231,21 @@ __global__ void __launch_bounds__(HP_THREADS, MINB) tc_hamming_packed_kernel(con
                 const int w0 = half * 4;
                 if (valid && w0 < p.W) qn = *reinterpret_cast<const uint4 *>(qrow + w0);
             }
-            uint4 cn0 = class_words(tid, 0), cn1 = class_words(tid + HP_EXP, 0);
+            uint4 cn0 = make_uint4(0, 0, 0, 0), cn1 = cn0;
+            if (!PRE) {
+                cn0 = class_words(tid, 0);
+                cn1 = class_words(tid + HP_EXP, 0);
+            }
             for (int t = 0; t < p.nt; t++) {
                 const uint4 qw = qn, cw0 = cn0, cw1 = cn1;
                 const int w0 = t * 8 + half * 4;                  // this thread's four words
                 const int wn = w0 + 8;
                 if (t + 1 < p.nt) {
                     qn = (valid && wn < p.W) ? *reinterpret_cast<const uint4 *>(qrow + wn) : make_uint4(0, 0, 0, 0);
-                    cn0 = class_words(tid, t + 1);
-                    cn1 = class_words(tid + HP_EXP, t + 1);
+                    if (!PRE) {
+                        cn0 = class_words(tid, t + 1);
+                        cn1 = class_words(tid + HP_EXP, t + 1);
+                    }
                 }
                 const bool oke = mbar_wait(empty(buf), ph ^ 1, abort_flag);   // the MMAs of this buffer's last use
                 if (!__all_sync(0xffffffffu, oke)) { ab = true; break; }
@@ -233,12 +254,21 @@ __global__ void __launch_bounds__(HP_THREADS, MINB) tc_hamming_packed_kernel(con
                     if (!__all_sync(0xffffffffu, okp)) { ab = true; break; }
                 }
                 gt++;
+                uint8_t *bt = sB + (BBUF == 2 ? buf : 0) * b_bytes;
+                if (PRE && tid == 0) {   // the tile's two class atoms, on their own barrier
+                    const int cb = BBUF == 2 ? buf : 0;
+                    mbar_expect_tx(cfull(cb), (uint32_t)b_bytes);
+                    tma_load_2d(su32(bt), &tmC, t * 256, 0, cfull(cb));
+                    tma_load_2d(su32(bt + p.Cp * 128), &tmC, t * 256 + 128, 0, cfull(cb));
+                    c_issued |= 1u << cb;
+                    c_par = (c_par & ~(1u << cb)) | (c_ph[cb] << cb);
+                    c_ph[cb] ^= 1;
+                }
                 const uint4 mq = w0 < p.W ? *reinterpret_cast<const uint4 *>(smask + w0) : make_uint4(0, 0, 0, 0);
                 expand_row(sA + buf * HP_A_BYTES + half * (BM * 128), r, qw, mq);
                 // class rows: items (class c, half h) i = tid, tid + HP_EXP (2 * Cp <= 512)
-                uint8_t *bt = sB + (BBUF == 2 ? buf : 0) * b_bytes;
 #pragma unroll
-                for (int ii = 0; ii < 2; ii++) {
+                for (int ii = 0; ii < (PRE ? 0 : 2); ii++) {
                     const int i = tid + ii * HP_EXP;
                     if (i < 2 * p.Cp) {
                         const int c = i % p.Cp, h = i / p.Cp;
@@ -288,6 +318,12 @@ __global__ void __launch_bounds__(HP_THREADS, MINB) tc_hamming_packed_kernel(con
                 if (valid) p.labels[row] = best;
             }
         }
+        if (PRE && ab && tid == 0)   // let this thread's class copies land before the CTA exits
+            for (int b = 0; b < 2; b++)
+                if (c_issued >> b & 1) {
+                    const unsigned long long t0 = gtimer();
+                    while (!mbar_try(cfull(b), c_par >> b & 1) && gtimer() - t0 < 100000000ull) {}
+                }
     }
 
     tc_fence_before();
