@@ -6,9 +6,9 @@
 // q.c is an exact integer in FP32.  The packed words of a 256-dim tile are
 // expanded in shared memory into E4M3 bytes: +1.0 (0x38) for bit 0, -1.0
 // (0xB8) for bit 1, 0 for a dim outside K (perforated away, or past D).  A
-// nibble of four dims becomes four bytes through one multiply that spreads
-// its bits to the byte boundaries:
-//   ((nib * 0x00204081) & 0x01010101) * 0x80 + 0x38383838
+// nibble of four dims becomes four bytes through one multiply that moves
+// its bits to the byte sign bits:
+//   ((nib * 0x10204080) & 0x80808080) | 0x38383838
 // (the four shifted copies of the nibble occupy disjoint bits, so there are
 // no carries).  Then
 //   D2 += Qtile . Ctile^T     (M 128 queries, N = Cp, K = 256 bytes)
@@ -16,7 +16,8 @@
 // arg-min of (|K| - dot) / 2 with the lowest class on ties.
 //
 // Roles (9 warps): warps 0-7 expand the query tile (thread = row x 128-dim
-// half) and the class tile, double buffered, and afterwards read D2 (two
+// half; its words loaded three tiles ahead) and the class tile, double
+// buffered, and afterwards read D2 (two
 // warpgroups, alternate 32-class chunks, merged by (distance, class));
 // warp 8 issues the MMAs.  Every wait is bounded as in the encoder.
 //
@@ -57,19 +58,33 @@ struct HPParams {
     int32_t *labels, *dists;
 };
 
-// Four dims of a word (bits 4k..4k+3) as four E4M3 bytes, zero where the
-// mask nibble is 0.
-__device__ __forceinline__ uint32_t expand_nibble(uint32_t nib, uint32_t mnib)
+// Four dims as four E4M3 bytes.  t holds the four bits at bits 0..3 (lo) or
+// 4..7 (hi), nothing else: the multiply moves bit i to bit 7 of byte i (its
+// four shifted copies occupy disjoint bits, so no carry reaches a sign
+// bit), the AND keeps the four sign bits and the OR adds 1.0 = 0x38.
+__device__ __forceinline__ uint32_t signs_lo(uint32_t t) { return ((t * 0x10204080u) & 0x80808080u) | 0x38383838u; }
+__device__ __forceinline__ uint32_t signs_hi(uint32_t t) { return ((t * 0x01020408u) & 0x80808080u) | 0x38383838u; }
+
+// The eight words of E4M3 bytes of one packed word (dims 4k..4k+3 in b[k]).
+__device__ __forceinline__ void expand_word(uint32_t w, uint32_t b[8])
 {
-    const uint32_t v = ((nib * 0x00204081u) & 0x01010101u) * 0x80u + 0x38383838u;
-    const uint32_t m = ((mnib * 0x00204081u) & 0x01010101u) * 0xFFu;
-    return v & m;
+    const uint32_t w8 = w >> 8, w16 = w >> 16, w24 = w >> 24;
+    b[0] = signs_lo(w & 0xFu);
+    b[1] = signs_hi(w & 0xF0u);
+    b[2] = signs_lo(w8 & 0xFu);
+    b[3] = signs_hi(w8 & 0xF0u);
+    b[4] = signs_lo(w16 & 0xFu);
+    b[5] = signs_hi(w16 & 0xF0u);
+    b[6] = signs_lo(w24 & 0xFu);
+    b[7] = signs_lo(w >> 28);
 }
 
-// Without a mask (every dim kept).
-__device__ __forceinline__ uint32_t expand_nibble_all(uint32_t nib)
+// Byte masks of the kept dims: 0xFF where kept, 0 elsewhere.
+__device__ __forceinline__ void expand_mask(uint32_t m, uint32_t b[8])
 {
-    return ((nib * 0x00204081u) & 0x01010101u) * 0x80u + 0x38383838u;
+    expand_word(m, b);
+#pragma unroll
+    for (int k = 0; k < 8; k++) b[k] = ((b[k] >> 7) & 0x01010101u) * 0xFFu;
 }
 
 // 128 dims (four words) of one row into its 128-byte row of a K atom
@@ -83,12 +98,12 @@ __device__ __forceinline__ void expand_row(uint8_t *atom, int r, const uint4 w, 
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         uint32_t b[8];
-        if (all) {
+        expand_word(ws[i], b);
+        if (!all) {
+            uint32_t mb[8];
+            expand_mask(ms[i], mb);
 #pragma unroll
-            for (int k = 0; k < 8; k++) b[k] = expand_nibble_all((ws[i] >> (4 * k)) & 0xFu);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 8; k++) b[k] = expand_nibble((ws[i] >> (4 * k)) & 0xFu, (ms[i] >> (4 * k)) & 0xFu);
+            for (int k = 0; k < 8; k++) b[k] &= mb[k];
         }
         *reinterpret_cast<uint4 *>(row + (((2 * i) ^ (r & 7)) * 16)) = make_uint4(b[0], b[1], b[2], b[3]);
         *reinterpret_cast<uint4 *>(row + (((2 * i + 1) ^ (r & 7)) * 16)) = make_uint4(b[4], b[5], b[6], b[7]);
@@ -226,26 +241,26 @@ __global__ void __launch_bounds__(HP_THREADS, MINB)
                            ? *reinterpret_cast<const uint4 *>(p.cls + (int64_t)c * p.W + wc)
                            : make_uint4(0, 0, 0, 0);
             };
-            uint4 qn = make_uint4(0, 0, 0, 0);
-            {
-                const int w0 = half * 4;
-                if (valid && w0 < p.W) qn = *reinterpret_cast<const uint4 *>(qrow + w0);
-            }
+            // this thread's four words of tile t, loaded three tiles ahead
+            auto query_words = [&](int t) {
+                const int w = t * 8 + half * 4;
+                return (valid && w < p.W) ? __ldg(reinterpret_cast<const uint4 *>(qrow + w)) : make_uint4(0, 0, 0, 0);
+            };
+            uint4 q0 = query_words(0), q1 = query_words(1), q2 = query_words(2);
             uint4 cn0 = make_uint4(0, 0, 0, 0), cn1 = cn0;
             if (!PRE) {
                 cn0 = class_words(tid, 0);
                 cn1 = class_words(tid + HP_EXP, 0);
             }
             for (int t = 0; t < p.nt; t++) {
-                const uint4 qw = qn, cw0 = cn0, cw1 = cn1;
+                const uint4 qw = q0, cw0 = cn0, cw1 = cn1;
                 const int w0 = t * 8 + half * 4;                  // this thread's four words
-                const int wn = w0 + 8;
-                if (t + 1 < p.nt) {
-                    qn = (valid && wn < p.W) ? *reinterpret_cast<const uint4 *>(qrow + wn) : make_uint4(0, 0, 0, 0);
-                    if (!PRE) {
-                        cn0 = class_words(tid, t + 1);
-                        cn1 = class_words(tid + HP_EXP, t + 1);
-                    }
+                q0 = q1;
+                q1 = q2;
+                q2 = query_words(t + 3);
+                if (!PRE && t + 1 < p.nt) {
+                    cn0 = class_words(tid, t + 1);
+                    cn1 = class_words(tid + HP_EXP, t + 1);
                 }
                 const bool oke = mbar_wait(empty(buf), ph ^ 1, abort_flag);   // the MMAs of this buffer's last use
                 if (!__all_sync(0xffffffffu, oke)) { ab = true; break; }

@@ -56,6 +56,9 @@ def run_both(hdc, bits, init_idx, iters, tp, ip):
     (26, 1000, 40, 0.3, 4, (0.1, 0.9, 3), (0.0, 0.9, 1)),
     (3, 33, 7, 0.2, 3, (0.0, 0.5, 1), (0.2, 1.0, 2)),
     (100, 2048, 30, 0.35, 6, (0.0, 0.75, 1), (0.0, 1.0, 4)),
+    # 60,000 rows: more 256-row tensor-core tiles than SMs, the class-atom
+    # ring running on across tiles; perforated assignment (masked queries)
+    (40, 512, 1500, 0.3, 2, (0.0, 1.0, 1), (0.1, 0.95, 3)),
 ])
 def test_cluster_matches_oracle(hdc, K, D, per, flip, iters, tp, ip):
     rng = np.random.default_rng(K * 7 + D)

@@ -218,6 +218,23 @@ def test_hamming_argmin_tensor_core_many_tiles(hdc):
     assert np.array_equal(labels.cpu().numpy(), orc.argmin(od))
 
 
+@pytest.mark.parametrize("N,D,C", [(40000, 1024, 120), (39000, 1000, 33)])
+def test_train_tensor_route_many_tiles_bit_exact(hdc, N, D, C):
+    """Retraining whose predictions run on the tensor-core route with the
+    classes expanded once: more 256-row tiles than SMs (CTAs take several,
+    the class-atom ring running on across them), a ragged last tile, 128 and
+    48 padded classes, and D = 1000 (a masked last word).  Accumulators and
+    update counts equal the oracle's."""
+    rng = np.random.default_rng(N + C)
+    protos = rng.integers(0, 2, (C, D)).astype(np.uint8)
+    y = rng.integers(0, C, N).astype(np.int32)
+    bits = protos[y] ^ (rng.random((N, D)) < 0.46).astype(np.uint8)
+    acc, cls, ups = hdc.train(T(pack(bits).view(np.int32)), T(y), D, C, epochs=1)
+    oacc, oups = orc.train(bits, y, C, 1)
+    assert np.array_equal(acc.cpu().numpy().astype(np.int64), oacc)
+    assert ups == oups and oups[0] > 0
+
+
 def test_train_many_classes_bit_exact(hdc):
     """Retraining with 100 classes: its predictions run on the tensor-core
     Hamming kernel; accumulators and update counts equal the oracle's."""
