@@ -79,6 +79,29 @@ def test_float_query_integer_data(hdc, enc, simt, C, bits_, perf):
     assert hdc.stream_status() == 0
 
 
+@pytest.mark.parametrize("enc", ["fp8", "bf16"])
+@pytest.mark.parametrize("D,C", [(100, 3), (240, 16), (480, 7), (481, 16), (1213, 11)])
+def test_float_query_16_class_tiles(hdc, enc, D, C):
+    """The fused kernel for up to 16 classes (240-dim encode tiles, the
+    cosine partials beside each accumulator): kept dims below one tile,
+    exactly one and two tiles, one past, and ragged; more 128-query blocks
+    than SMs.  Sampled rows against the oracle on integer data."""
+    rng = np.random.default_rng(D * 17 + C)
+    F, N = 64, 152 * 128 + 77
+    X = rng.integers(-8, 8, (N, F)).astype(np.float32)
+    Bt = (1 - 2 * rng.integers(0, 2, (D, F))).astype(np.float32)
+    acc = rng.integers(-300, 301, (C, D)).astype(np.int64)
+    m = hdc.Model(T(Bt), hdc.ApproxConfig(enc=enc, class_bits=8, float_query=True), acc=T(acc.astype(np.int32)))
+    lab, sc = hdc.classify(T(X), m, sims=True)
+    lab, sc = lab.cpu().numpy(), sc.cpu().numpy()
+    rows = np.sort(np.concatenate([rng.choice(N - 200, 300, replace=False), np.arange(N - 200, N)]))
+    o_lab, o_sc, q = orc.classify_float(X[rows], Bt, acc, orc.ENC_FP32, 0.0, 1.0, 1, 8, integer=True)
+    chat = orc.gather_cols(orc.class_quantise(acc, 8), orc.kept_dims(D))
+    check(lab[rows], sc[rows], o_lab, o_sc, bound(q, chat))
+    torch.cuda.synchronize()
+    assert hdc.stream_status() == 0
+
+
 def test_float_query_tensor_path_and_ffma_path_on_integers(hdc):
     """More query tiles than SMs through the fused tensor-core kernel and
     through the FFMA encoder + cosine kernel: on sampled rows both agree
