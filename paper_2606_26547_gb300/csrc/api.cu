@@ -416,6 +416,18 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *
     if (ws_bytes < L.total) return HDC_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     const int nb = m->class_bits;
+    if (!float_query(m->flags) && use_tc(m) && m->Fk == m->F && !scores) {
+        // binary classes on the tensor cores: the fused kernel quantises its
+        // own query tiles from X (the quantised operand never reaches HBM),
+        // staging them in the quantised-query region of the workspace
+        TcArgs a = {};
+        a.N = N; a.F = m->Fk; a.ldx = ld_for(m->enc, m->Fk); a.Bq = m->Bq; a.ldb = m->ldb; a.Dk = m->Dk;
+        a.enc = m->enc; a.sb = m->b_scale; a.W = m->W;
+        a.planes = m->cls; a.C = m->C; a.nb = nb; a.csum = m->cls_sum; a.cnorm = m->cls_norm;
+        a.labels = labels; a.dists = dists;
+        a.X = X; a.ldX = m->F; a.stage = (uint8_t *)ws + L.xq;
+        if (tc_qin_ok(a) && tc_stage_bytes(a) <= (size_t)N * a.ldx * esize_for(m->enc)) return cu(timed_tc(a, st));
+    }
     const void *Xop;
     int64_t ldx;
     const float *sx;

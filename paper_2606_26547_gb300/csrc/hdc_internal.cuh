@@ -155,9 +155,21 @@ struct TcArgs {
     const double *cnorm;
     int32_t *labels, *dists;
     double *sims;
+    // classify only: the FP32 query rows (N x ldX) to quantise inside the
+    // kernel, with `stage` (tc_stage_bytes) for its staged query tiles;
+    // Xq is then unused
+    const float *X;
+    int64_t ldX;
+    uint8_t *stage;
 };
 cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st);
 bool tc_supported(const TcArgs &a);
+// Whether the fused classify of a can quantise its own query tiles from the
+// FP32 rows a.X (binary classes, up to 32; 16-byte aligned rows of F % 4 == 0
+// floats; ldx <= 1024; at least two tiles per CTA), and the bytes its staged
+// tiles take (at most N rows of the quantised operand).
+bool tc_qin_ok(const TcArgs &a);
+size_t tc_stage_bytes(const TcArgs &a);
 
 // Reads and clears the streaming quantiser's device status word.
 cudaError_t quant_read_status(cudaStream_t st, int *status);

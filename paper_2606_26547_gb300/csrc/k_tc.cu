@@ -105,10 +105,46 @@ bool tc_supported(const TcArgs &a)
     return true;
 }
 
+namespace {
+unsigned tc_grid(int64_t N, int sms)
+{
+    const int64_t m_tiles = (N + tc::BM - 1) / tc::BM;
+    return (unsigned)(m_tiles < sms ? m_tiles : sms);
+}
+}  // namespace
+
+bool tc_qin_ok(const TcArgs &a)
+{
+    if (!a.X || !a.stage || !a.planes || a.C <= 0 || a.C > 32 || a.nb != 1 || a.H || a.sproj || a.scores || a.sims)
+        return false;
+    if (!tc_supported(a) || a.ldx > tc::QIN_MAX_LD || a.F % 4 != 0 || a.ldX % 4 != 0 || a.ldX < a.F ||
+        (uintptr_t)a.X % 16 != 0 || (uintptr_t)a.stage % 16 != 0)
+        return false;
+    const int sms = sm_count();
+    if (sms <= 0) return false;
+    // two staged tiles per CTA fit in the N rows of the quantised operand
+    return a.N >= (int64_t)2 * tc_grid(a.N, sms) * tc::BM;
+}
+
+size_t tc_stage_bytes(const TcArgs &a)
+{
+    const int sms = sm_count();
+    if (sms <= 0) return 0;
+    return (size_t)2 * tc_grid(a.N, sms) * tc::BM * a.ldx * (a.enc == HDC_ENC_BF16 ? 2 : 1);
+}
+
 cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st)
 {
     CUtensorMap ma, mb;
-    if (!make_map(&ma, a.Xq, a.enc, a.F, a.ldx, a.N, tc::BM) || !make_map(&mb, a.Bq, a.enc, a.F, a.ldb, a.Dk, tc::BN))
+    const bool qin = a.X != nullptr;
+    if (qin && !tc_qin_ok(a)) return cudaErrorNotSupported;
+    const int sms = sm_count();
+    if (sms <= 0) return cudaErrorNoDevice;
+    const unsigned grid = tc_grid(a.N, sms);
+    // QIN: the A operand is the CTAs' staged tiles (2 per CTA)
+    if (!(qin ? make_map(&ma, a.stage, a.enc, a.F, a.ldx, (int64_t)2 * grid * tc::BM, tc::BM)
+              : make_map(&ma, a.Xq, a.enc, a.F, a.ldx, a.N, tc::BM)) ||
+        !make_map(&mb, a.Bq, a.enc, a.F, a.ldb, a.Dk, tc::BN))
         return cudaErrorInvalidValue;
     tc::Params p;
     p.N = a.N;
@@ -129,10 +165,13 @@ cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st)
     p.sproj = a.sproj;
     p.ldS = a.ldS;
     p.qn = a.qn;
-    const int64_t m_tiles = (a.N + tc::BM - 1) / tc::BM;
-    const int sms = sm_count();
-    if (sms <= 0) return cudaErrorNoDevice;
-    const unsigned grid = (unsigned)(m_tiles < sms ? m_tiles : sms);
+    if (qin) {
+        p.X = a.X;
+        p.ldX = a.ldX;
+        p.F = a.F;
+        p.ld = a.ldx;
+        p.stage = a.stage;
+    }
     const bool classify = a.planes != nullptr;
     if (classify && a.cls_sign && a.nb == 1 && a.C > 32 && a.C <= tc::H_CMAX) {
         // binary classes, 33..112 of them: Hamming distances on the tensor

@@ -19,6 +19,12 @@
 //   warp 5 lane 0  MMA issuer: 4 tcgen05.mma (K = 32 bytes each) per stage
 //                  into one of two 128 x 256 FP32 accumulators in TMEM,
 //                  tcgen05.commit frees the stage / publishes the tile;
+//   warps 4*EWG+2, 4*EWG+3 (QIN only)  query quantisers: FP32 rows of the
+//                  CTA's next 128-query tile -> BF16 / E4M3 (the row
+//                  quantisation of Sec. 4.2) into one of two staged tiles
+//                  the CTA owns in global memory, read back by the TMA
+//                  producer; the first tile is quantised by the epilogue
+//                  warps too, before their first accumulator arrives;
 //   warps 0-3      epilogue: tcgen05.ld of the thread's row (TMEM lane),
 //                  32 columns at a time -> one packed word, releases the
 //                  accumulator, then popcounts against the class words
@@ -35,6 +41,7 @@
 #include <cuda_bf16.h>
 
 #include "hdc_internal.cuh"
+#include "quant_math.cuh"
 
 namespace hdc {
 namespace tc {
@@ -50,15 +57,24 @@ constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BKB;            // 16 KB
 constexpr int B_BYTES = BN * BKB;            // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-// threads: 4*EWG epilogue warps (EWG = 1, 2 or 4 warpgroups), a TMA warp, an MMA warp
-__host__ __device__ constexpr int num_threads(int ewg) { return (4 * ewg + 2) * 32; }
+// threads: 4*EWG epilogue warps (EWG = 1, 2 or 4 warpgroups), a TMA warp, an
+// MMA warp and, when the kernel quantises its own query tiles, QWARPS_IN
+// quantiser warps
+constexpr int QWARPS_IN = 2;
+__host__ __device__ constexpr int num_threads(int ewg, bool qin = false)
+{
+    return (4 * ewg + 2 + (qin ? QWARPS_IN : 0)) * 32;
+}
+// elements of a staged query row the quantisers hold in registers (8 x 128)
+constexpr int QIN_MAX_LD = 1024;
 constexpr int TMEM_COLS = 2 * BN;            // two accumulators
 // class-word ring (classify): the 8 words of every class for one 256-dim tile
 constexpr int CBUF = 4, CLS_BYTES = 128 * 32;
 // sign words exchanged between epilogue warpgroups: WXB buffers of [8 words][BM rows]
 constexpr int WXB = 2;
-// full, empty, tfull[2], tempty[2], done, merge_full, merge_empty, cfull[CBUF], cempty[CBUF], wfull[WXB]
-constexpr int NUM_BARS = 2 * STAGES + 7 + 2 * CBUF + WXB;
+// full, empty, tfull[2], tempty[2], done, merge_full, merge_empty, cfull[CBUF], cempty[CBUF], wfull[WXB],
+// a0_ready, a_ready[2], a_free[2] (staged query tiles)
+constexpr int NUM_BARS = 2 * STAGES + 7 + 2 * CBUF + WXB + 5;
 // dynamic shared memory: 1 KB alignment slack, stages, class ring, barriers,
 // TMEM slot + abort flag, per-row minimum and class of warpgroups 1..EWG-1,
 // exchanged words
@@ -82,6 +98,12 @@ struct Params {
     uint16_t *sproj;         // encode-only: BF16 projections s_k * sb_k (N x ldS) or NULL
     int ldS;
     float *qn;               // and the squared norm of each BF16 row
+    // QIN: the FP32 query rows (N x ldX, 16-byte aligned, F % 4 == 0) and the
+    // staged tiles, 2 per CTA of BM rows x ld elements (zeros past F)
+    const float *X = nullptr;
+    int64_t ldX = 0;
+    int F = 0, ld = 0;
+    uint8_t *stage = nullptr;
 };
 
 // ------------------------------------------------------------ PTX wrappers
@@ -235,7 +257,77 @@ __device__ __forceinline__ uint32_t pack_signs(const uint32_t (&r)[32])
     return w;
 }
 
+// Quantise rows of one 128-query tile into a staged tile in global memory
+// (BM rows x p.ld elements; zeros past F and for rows past N).  This warp
+// takes the tile rows w, w + nw, w + 2*nw, ... RQ at a time, issuing all of
+// their loads (streaming, evict-first) before converting the first.  The
+// arithmetic is the row quantiser's: BF16 by round-to-nearest-even, E4M3
+// after the row's power-of-two scale.  The scale itself is not kept: it is
+// positive, and the classify epilogue uses only the signs.
+template <int ENC, int RQ>
+__device__ __forceinline__ void quant_tile(const Params &p, int64_t row0, uint8_t *tile, int w, int nw, int lane)
+{
+    constexpr int ES = ENC == HDC_ENC_BF16 ? 2 : 1;
+    constexpr int MAXIT = QIN_MAX_LD / 128;
+    const int nit = (p.ld + 127) / 128;
+    for (int r = w; r < BM; r += nw * RQ) {
+        float4 v[RQ][MAXIT];
+#pragma unroll
+        for (int q = 0; q < RQ; q++) {
+            const int rr = r + q * nw;
+            const int64_t grow = row0 + rr;
+            const bool live = rr < BM && grow < p.N;
+            const float *src = p.X + (live ? grow : 0) * p.ldX;
+#pragma unroll
+            for (int it = 0; it < MAXIT; it++) {
+                const int f = it * 128 + lane * 4;
+                v[q][it] = live && it < nit && f < p.F ? __ldcs(reinterpret_cast<const float4 *>(src + f))
+                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RQ; q++) {
+            const int rr = r + q * nw;
+            if (rr >= BM) break;   // the same for every lane
+            int k = 0;
+            if (ENC == HDC_ENC_FP8_E4M3) {
+                float amax = 0.f;
+#pragma unroll
+                for (int it = 0; it < MAXIT; it++)
+                    amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v[q][it].x), fabsf(v[q][it].y)),
+                                             fmaxf(fabsf(v[q][it].z), fabsf(v[q][it].w))));
+#pragma unroll
+                for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+                k = pow2_scale_exp(amax);
+            }
+            uint8_t *dst = tile + (size_t)rr * p.ld * ES;
+#pragma unroll
+            for (int it = 0; it < MAXIT; it++) {
+                const int f0 = it * 128 + lane * 4;
+                if (it < nit && f0 < p.ld) {
+                    const float4 x = v[q][it];
+                    if (ENC == HDC_ENC_BF16)
+                        *reinterpret_cast<uint2 *>(dst + (size_t)f0 * 2) = to_bf16x4(x.x, x.y, x.z, x.w);
+                    else
+                        *reinterpret_cast<uint32_t *>(dst + f0) =
+                            to_e4m3x4(scale_pow2(x.x, k), scale_pow2(x.y, k), scale_pow2(x.z, k), scale_pow2(x.w, k));
+                }
+            }
+        }
+    }
+}
+
+// The staged-tile writes of this thread become visible to the TMA (async
+// proxy) reads that follow the barrier it arrives on next.
+__device__ __forceinline__ void fence_to_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
 // ------------------------------------------------------------------ kernel
+// QIN (classify, EWG = 1 or 2): the query operand is quantised inside the
+// kernel from FP32 rows (quant_tile), one tile ahead of the MMAs, into the
+// CTA's two staged tiles; the TMA producer waits for a tile's a_ready (tile
+// 0: a0_ready, written by the epilogue and quantiser warps together) and
+// the MMA issuer frees it (a_free) once the last stage that reads it has
+// landed.
 // EWG = 2 or 4 (classify only): the epilogue warpgroups read the same TMEM
 // lanes, warpgroup g the columns of words [g*8/EWG, (g+1)*8/EWG); every
 // thread publishes its words to shared memory and, after an mbarrier that
@@ -244,8 +336,8 @@ __device__ __forceinline__ uint32_t pack_signs(const uint32_t (&r)[32])
 // and warpgroups 1..EWG-1 hand their per-row minimum to warpgroup 0 through
 // shared memory (an mbarrier pair with bounded waits), which keeps the lower class
 // index on ties.
-template <int ENC, int CMAX, bool CLASSIFY, int EWG>
-__global__ void __launch_bounds__(num_threads(EWG), 1)
+template <int ENC, int CMAX, bool CLASSIFY, int EWG, bool QIN = false>
+__global__ void __launch_bounds__(num_threads(EWG, QIN), 1)
     tc_encode_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmC, const Params p)
 {
@@ -266,6 +358,14 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
     auto cfull = [&](int b) { return su32(bars + 2 * STAGES + 7 + b); };
     auto cempty = [&](int b) { return su32(bars + 2 * STAGES + 7 + CBUF + b); };
     auto wfull = [&](int b) { return su32(bars + 2 * STAGES + 7 + 2 * CBUF + b); };
+    constexpr int QB = 2 * STAGES + 7 + 2 * CBUF + WXB;   // staged query tile barriers
+    const uint32_t a0_ready = su32(bars + QB);
+    auto a_ready = [&](int b) { return su32(bars + QB + 1 + b); };
+    auto a_free = [&](int b) { return su32(bars + QB + 3 + b); };
+    constexpr int QW0 = 4 * EWG + 2;                   // first quantiser warp
+    constexpr int RQ = EWG == 1 ? 4 : 2;               // rows in flight per quantising warp
+    constexpr int QES = ENC == HDC_ENC_BF16 ? 2 : 1;
+    static_assert(!QIN || (CLASSIFY && EWG <= 2), "in-kernel quantisation: classify with one or two warpgroups");
     constexpr int NMRG = EWG > 1 ? EWG - 1 : 1;
     int32_t *s_val = reinterpret_cast<int32_t *>(tmem_slot + 4);  // per-row minimum of warpgroups 1..EWG-1
     int32_t *s_idx = s_val + NMRG * BM;                             // and its class
@@ -296,6 +396,11 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
             mbar_init(cempty(b), BM * EWG);
         }
         for (int b = 0; b < WXB; b++) mbar_init(wfull(b), BM * EWG);
+        mbar_init(a0_ready, (4 * EWG + QWARPS_IN) * 32);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(a_ready(b), QWARPS_IN * 32);
+            mbar_init(a_free(b), 1);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -322,8 +427,15 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
             for (int s = 0; s < STAGES; s++) { issued[s] = false; ipar[s] = 0; }
             uint32_t c_issued = 0, c_par = 0;
             bool ab = false;
-            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
+            int64_t it = 0;
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++)
                 for (int nt = 0; nt < num_n_tiles && !ab; nt++) {
+                    if (QIN && nt == 0) {  // the tile's staged query rows have been written
+                        const bool okq = it == 0 ? mbar_wait(a0_ready, 0, abort_flag)
+                                                 : mbar_wait(a_ready((int)(it & 1)), (uint32_t)(((it - 1) >> 1) & 1),
+                                                             abort_flag);
+                        if (!okq) { ab = true; break; }
+                    }
                     if (CLASSIFY) {  // this dim tile's class words: C rows x 8 words (zeros past W)
                         if (!mbar_wait(cempty(cb), cph ^ 1, abort_flag)) { ab = true; break; }
                         mbar_expect_tx(cfull(cb), (uint32_t)p.C * 32u);
@@ -335,7 +447,8 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
                     for (int kb = 0; kb < p.num_kb; kb++) {
                         if (!mbar_wait(empty(stage), phase ^ 1, abort_flag)) { ab = true; break; }
                         mbar_expect_tx(full(stage), STAGE_BYTES);
-                        tma_load_2d(su32(sA + stage * A_BYTES), &tmA, kb * KELEMS, (int)(mt * BM), full(stage));
+                        const int ay = QIN ? (int)((blockIdx.x * 2 + (it & 1)) * BM) : (int)(mt * BM);
+                        tma_load_2d(su32(sA + stage * A_BYTES), &tmA, kb * KELEMS, ay, full(stage));
                         tma_load_2d(su32(sB + stage * B_BYTES), &tmB, kb * KELEMS, nt * BN, full(stage));
                         issued[stage] = true;
                         ipar[stage] = phase;
@@ -361,7 +474,8 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
             int stage = 0, acc = 0;
             uint32_t phase = 0, aphase = 0;
             bool ab = false;
-            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
+            int64_t it = 0;
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++)
                 for (int nt = 0; nt < num_n_tiles && !ab; nt++) {
                     if (!mbar_wait(tempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
                     tc_fence_after();
@@ -369,6 +483,9 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
                     for (int kb = 0; kb < p.num_kb; kb++) {
                         if (!mbar_wait(full(stage), phase, abort_flag)) { ab = true; break; }
                         tc_fence_after();
+                        // the last copy of the staged query tile has landed:
+                        // its quantisers may overwrite it
+                        if (QIN && nt == num_n_tiles - 1 && kb == p.num_kb - 1) mbar_arrive(a_free((int)(it & 1)));
                         const uint32_t a0 = su32(sA + stage * A_BYTES), b0 = su32(sB + stage * B_BYTES);
 #pragma unroll
                         for (int k = 0; k < BKB / 32; k++)
@@ -385,7 +502,32 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
             const unsigned long long t0 = gtimer();
             while (!mbar_try(done_bar, 0) && gtimer() - t0 < 100000000ull) {}
         }
+    } else if (QIN && warp >= QW0) {  // --------------------- query quantisers
+        const int qw = warp - QW0;
+        uint32_t fph = 0;   // parities of the next completions of a_free[0], a_free[1] (bits 0, 1)
+        int64_t it = 0;
+        for (int64_t mt = blockIdx.x; mt < num_m_tiles && !*abort_flag; mt += gridDim.x, it++) {
+            const int b = (int)(it & 1);
+            uint8_t *tile = p.stage + (size_t)(blockIdx.x * 2 + b) * BM * p.ld * QES;
+            if (it >= 2) {   // tile it - 2 has been read out of this buffer
+                const bool okf = mbar_wait(a_free(b), (fph >> b) & 1u, abort_flag);
+                fph ^= 1u << b;
+                if (!__all_sync(0xffffffffu, okf)) break;
+            }
+            if (it == 0)
+                quant_tile<ENC, RQ>(p, mt * BM, tile, 4 * EWG + qw, 4 * EWG + QWARPS_IN, lane);
+            else
+                quant_tile<ENC, RQ>(p, mt * BM, tile, qw, QWARPS_IN, lane);
+            fence_to_async_global();
+            mbar_arrive(it == 0 ? a0_ready : a_ready(b));
+        }
     } else {  // ------------------------------------ epilogue warps 0 .. 4*EWG-1
+        if (QIN) {  // the first staged tile, with the quantiser warps
+            quant_tile<ENC, RQ>(p, (int64_t)blockIdx.x * BM, p.stage + (size_t)blockIdx.x * 2 * BM * p.ld * QES, warp,
+                                4 * EWG + QWARPS_IN, lane);
+            fence_to_async_global();
+            mbar_arrive(a0_ready);
+        }
         const int q = warp & 3;             // TMEM lane quarter of this warp
         const int g = warp >> 2;            // epilogue warpgroup
         const int r = q * 32 + lane;        // row of the tile (TMEM lane)
@@ -561,15 +703,15 @@ __global__ void __launch_bounds__(num_threads(EWG), 1)
 }
 
 // Launch helpers, instantiated by each encoding's translation unit.
-template <int ENC, int CMAX, bool CLASSIFY, int EWG>
+template <int ENC, int CMAX, bool CLASSIFY, int EWG, bool QIN = false>
 static cudaError_t launch_one(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const Params &p,
                               unsigned grid, cudaStream_t st)
 {
-    auto k = tc_encode_kernel<ENC, CMAX, CLASSIFY, EWG>;
+    auto k = tc_encode_kernel<ENC, CMAX, CLASSIFY, EWG, QIN>;
     constexpr size_t smem = smem_bytes(EWG);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, num_threads(EWG), smem, st>>>(ma, mb, mc, p);
+    k<<<grid, num_threads(EWG, QIN), smem, st>>>(ma, mb, mc, p);
     return cudaGetLastError();
 }
 
@@ -582,6 +724,11 @@ static cudaError_t launch_enc(const CUtensorMap &ma, const CUtensorMap &mb, cons
     if (!classify)
         return p.sproj ? launch_one<ENC, 1, false, 4>(ma, mb, mc, p, grid, st)
                        : launch_one<ENC, 1, false, 1>(ma, mb, mc, p, grid, st);
+    if (p.X) {  // query tiles quantised in the kernel (classify, up to 32 classes)
+        if (p.C <= 16) return launch_one<ENC, 16, true, 1, true>(ma, mb, mc, p, grid, st);
+        if (p.C <= 32) return launch_one<ENC, 16, true, 2, true>(ma, mb, mc, p, grid, st);
+        return cudaErrorNotSupported;
+    }
     // up to 16 classes: one epilogue warpgroup; up to 32: two; more: four,
     // each counting ceil(C / EWG) <= CMAX classes
     if (p.C <= 16) return launch_one<ENC, 16, true, 1>(ma, mb, mc, p, grid, st);
