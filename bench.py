@@ -191,10 +191,12 @@ class ClockSampler:
 # --------------------------------------------------------------- helpers
 
 # DRAM traffic of the fused kernel from one ncu capture (profiles/
-# tc_encode_kernel_fp8_F784_D10000_stride2.md): bytes per query, valid only
-# while the kernel sources hash to the value they had when it was taken.
-PROFILED_TRAFFIC = {"sources_sha1_16": "4306b1b282f7211f", "enc": "fp8", "stride": 2,
-                    "dram_bytes_per_query": (239427072 + 3662080) / 262144}
+# tc_encode_kernel_qin_fp8_F784_D10000_stride2.md: the kernel that quantises
+# its own query tiles, so the FP32 rows are its input): bytes per query,
+# valid only while the kernel sources hash to the value they had when it was
+# taken.
+PROFILED_TRAFFIC = {"sources_sha1_16": "11710a6e3a033075", "enc": "fp8", "stride": 2,
+                    "dram_bytes_per_query": (827032576 + 65636352) / 262144}
 
 
 def tc_sources_sha():
@@ -644,6 +646,9 @@ def run_ours(a):
                      "algorithmic_flops_per_launch": flops,
                      "timed_region_ms": region_s * 1e3,
                      "frac_vs_sustained": achieved / peak_sus,
+                     # the burst peak scaled to this region's median SM clock
+                     "frac_at_region_clock": (achieved / (peak * clocks["sm_mhz"] / pk["sm_max_mhz"])
+                                              if clocks.get("sm_mhz") and pk.get("sm_max_mhz") else None),
                      "clock_note": "burst peak measured with SM clocks up to %s MHz; sustained peak at a median "
                                    "%s MHz under the power cap; this region's median %s MHz"
                                    % (pk.get("sm_max_mhz"), pk.get("clocks_under_load", {}).get("sm_mhz_median"),
