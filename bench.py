@@ -210,14 +210,14 @@ def tc_sources_sha():
 
 def launches_per_step(fused: bool, C: int, F: int, enc: str, B: int) -> int:
     """Kernels one hdc_classify call launches: the fused kernel alone when it
-    quantises its own query tiles (binary classes, up to 32; F % 4 == 0; rows
-    of at most 1,024 quantised elements; two 128-query tiles per SM), the
-    row quantiser first otherwise, and a similarity or cosine kernel after an
-    encode-only launch."""
+    quantises its own query tiles (binary classes, up to 112; F % 4 == 0;
+    rows of at most 1,024 quantised elements; two 128-query tiles per SM),
+    the row quantiser first otherwise, and a similarity or cosine kernel
+    after an encode-only launch."""
     import torch
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     q = 128 if enc == "fp8" else 64
-    if fused and C <= 32 and F % 4 == 0 and (F + q - 1) // q * q <= 1024 and B >= 2 * sms * 128:
+    if fused and C <= 112 and F % 4 == 0 and (F + q - 1) // q * q <= 1024 and B >= 2 * sms * 128:
         return 1
     return 2 if fused else 3
 

@@ -425,6 +425,7 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *
         a.enc = m->enc; a.sb = m->b_scale; a.W = m->W;
         a.planes = m->cls; a.C = m->C; a.nb = nb; a.csum = m->cls_sum; a.cnorm = m->cls_norm;
         a.labels = labels; a.dists = dists;
+        a.cls_sign = m->cls_sign; a.ldcs = m->ldcs;
         a.X = X; a.ldX = m->F; a.stage = (uint8_t *)ws + L.xq;
         if (tc_qin_ok(a) && tc_stage_bytes(a) <= (size_t)N * a.ldx * esize_for(m->enc)) return cu(timed_tc(a, st));
     }

@@ -165,9 +165,10 @@ struct TcArgs {
 cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st);
 bool tc_supported(const TcArgs &a);
 // Whether the fused classify of a can quantise its own query tiles from the
-// FP32 rows a.X (binary classes, up to 32; 16-byte aligned rows of F % 4 == 0
-// floats; ldx <= 1024; at least two tiles per CTA), and the bytes its staged
-// tiles take (at most N rows of the quantised operand).
+// FP32 rows a.X (binary classes: up to 32, or up to 112 with their E4M3
+// signs; 16-byte aligned rows of F % 4 == 0 floats; ldx <= 1024; at least two
+// tiles per CTA), and the bytes its staged tiles take (at most N rows of the
+// quantised operand).
 bool tc_qin_ok(const TcArgs &a);
 size_t tc_stage_bytes(const TcArgs &a);
 

@@ -113,9 +113,18 @@ unsigned tc_grid(int64_t N, int sms)
 }
 }  // namespace
 
+// The fused classify routes that can quantise their own query tiles: the
+// popcount epilogue with one or two warpgroups (up to 32 classes) and the
+// tensor-core Hamming kernel (33..112 classes with their E4M3 signs).
+bool tc_qin_route(const TcArgs &a)
+{
+    return a.C <= 32 || (a.cls_sign && a.C <= tc::H_CMAX);
+}
+
 bool tc_qin_ok(const TcArgs &a)
 {
-    if (!a.X || !a.stage || !a.planes || a.C <= 0 || a.C > 32 || a.nb != 1 || a.H || a.sproj || a.scores || a.sims)
+    if (!a.X || !a.stage || !a.planes || a.C <= 0 || !tc_qin_route(a) || a.nb != 1 || a.H || a.sproj || a.scores ||
+        a.sims)
         return false;
     if (!tc_supported(a) || a.ldx > tc::QIN_MAX_LD || a.F % 4 != 0 || a.ldX % 4 != 0 || a.ldX < a.F ||
         (uintptr_t)a.X % 16 != 0 || (uintptr_t)a.stage % 16 != 0)
@@ -191,6 +200,13 @@ cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st)
         h.Cp = Cp;
         h.labels = a.labels;
         h.dists = a.dists;
+        if (qin) {
+            h.X = a.X;
+            h.ldX = a.ldX;
+            h.F = a.F;
+            h.ld = a.ldx;
+            h.stage = a.stage;
+        }
         if (a.ldcs < h.nt * tc::HBN + 64) return cudaErrorInvalidValue;
         if (a.enc == HDC_ENC_BF16) return tc::launch_hamming_bf16(ma, mb2, ms, h, grid, st);
         return tc::launch_hamming_fp8(ma, mb2, ms, h, grid, st);

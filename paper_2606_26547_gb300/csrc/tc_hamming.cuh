@@ -22,8 +22,10 @@
 // issuer.  The two issuers keep separate commit chains, so the MMA2 of tile t
 // enters the tensor pipe as soon as its sign tile is ready, without holding
 // back the issue of the next tile's MMA1 (a single issuer measured ~2,400
-// cycles of issue and commit latency at each tile boundary).  Every wait is
-// bounded as in the encoder.
+// cycles of issue and commit latency at each tile boundary).  With QIN,
+// warps 16 and 17 quantise the query tiles from FP32 rows one tile ahead into
+// the CTA's two staged tiles, as in the encoder (tc_kernel.cuh).  Every wait
+// is bounded as in the encoder.
 #pragma once
 #include "tc_kernel.cuh"
 
@@ -37,12 +39,13 @@ constexpr int HB_BYTES = HBN * BKB;           // 24 KB
 constexpr int H_STAGE_BYTES = HA_BYTES + HB_BYTES;
 constexpr int HEWG = 3;                       // epilogue warpgroups
 constexpr int H_THREADS = (4 * HEWG + 4) * 32;   // + the MMA2 issuer
+__host__ __device__ constexpr int h_threads(bool qin) { return H_THREADS + (qin ? QWARPS_IN * 32 : 0); }
 constexpr int A2_ATOM = BM * 128;             // one 128-byte K atom of the sign tile
 constexpr int A2_BYTES = 2 * A2_ATOM;         // K = 192 bytes in two atoms
 constexpr int H_CMAX = 112;
 // full[S], empty[S], sfull[2], sempty[2], a2full, a2empty, b2full, b2empty,
-// d2full, d2empty, done, merge_full, merge_empty, done2
-constexpr int H_NUM_BARS = 2 * H_STAGES + 4 + 6 + 3 + 1;
+// d2full, d2empty, done, merge_full, merge_empty, done2, a0_ready, a_ready[2], a_free[2]
+constexpr int H_NUM_BARS = 2 * H_STAGES + 4 + 6 + 3 + 1 + 5;
 
 __host__ __device__ constexpr size_t h_smem_bytes(int Cp)
 {
@@ -56,6 +59,11 @@ struct HParams {
     int Dk, num_kb, nt;     // nt: 192-dim tiles
     int C, Cp;
     int32_t *labels, *dists;
+    // QIN: FP32 query rows and the staged tiles (2 per CTA), as in Params
+    const float *X = nullptr;
+    int64_t ldX = 0;
+    int F = 0, ld = 0;
+    uint8_t *stage = nullptr;
 };
 
 template <int ENC>
@@ -67,8 +75,8 @@ __device__ __forceinline__ uint32_t idesc_n(int n)
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-template <int ENC>
-__global__ void __launch_bounds__(H_THREADS, 1)
+template <int ENC, bool QIN = false>
+__global__ void __launch_bounds__(h_threads(QIN), 1)
     tc_hamming_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const __grid_constant__ CUtensorMap tmS, const HParams p)
 {
@@ -93,6 +101,12 @@ __global__ void __launch_bounds__(H_THREADS, 1)
     const uint32_t done_bar = su32(bars + 2 * H_STAGES + 10);
     const uint32_t merge_full = su32(bars + 2 * H_STAGES + 11), merge_empty = su32(bars + 2 * H_STAGES + 12);
     const uint32_t done2_bar = su32(bars + 2 * H_STAGES + 13);
+    const uint32_t a0_ready = su32(bars + 2 * H_STAGES + 14);
+    auto a_ready = [&](int b) { return su32(bars + 2 * H_STAGES + 15 + b); };
+    auto a_free = [&](int b) { return su32(bars + 2 * H_STAGES + 17 + b); };
+    constexpr int QW0 = 4 * HEWG + 4;                  // first quantiser warp
+    constexpr int QES = ENC == HDC_ENC_BF16 ? 2 : 1;
+    const QinRows qr = {p.X, p.ldX, p.N, p.F, p.ld};
     constexpr int PRODUCER = 4 * HEWG, ISSUER = 4 * HEWG + 1, CPRODUCER = 4 * HEWG + 2, ISSUER2 = 4 * HEWG + 3;
     constexpr int KELEMS = ENC == HDC_ENC_BF16 ? BKB / 2 : BKB;
     constexpr uint32_t D2_COL = 2 * HBN;     // D2 after the two encode accumulators
@@ -119,6 +133,11 @@ __global__ void __launch_bounds__(H_THREADS, 1)
         mbar_init(done2_bar, 1);
         mbar_init(merge_full, BM * (HEWG - 1));
         mbar_init(merge_empty, BM);
+        mbar_init(a0_ready, (4 * HEWG + QWARPS_IN) * 32);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(a_ready(b), QWARPS_IN * 32);
+            mbar_init(a_free(b), 1);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -143,12 +162,20 @@ __global__ void __launch_bounds__(H_THREADS, 1)
             uint32_t ipar[H_STAGES];
             for (int s = 0; s < H_STAGES; s++) { issued[s] = false; ipar[s] = 0; }
             bool ab = false;
-            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
+            int64_t it = 0;
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++)
                 for (int t = 0; t < p.nt && !ab; t++)
                     for (int kb = 0; kb < p.num_kb; kb++) {
+                        if (QIN && t == 0 && kb == 0) {  // the tile's staged query rows have been written
+                            const bool okq = it == 0 ? mbar_wait(a0_ready, 0, abort_flag)
+                                                     : mbar_wait(a_ready((int)(it & 1)),
+                                                                 (uint32_t)(((it - 1) >> 1) & 1), abort_flag);
+                            if (!okq) { ab = true; break; }
+                        }
                         if (!mbar_wait(empty(stage), phase ^ 1, abort_flag)) { ab = true; break; }
                         mbar_expect_tx(full(stage), H_STAGE_BYTES);
-                        tma_load_2d(su32(sA + stage * HA_BYTES), &tmA, kb * KELEMS, (int)(mt * BM), full(stage));
+                        const int ay = QIN ? (int)((blockIdx.x * 2 + (it & 1)) * BM) : (int)(mt * BM);
+                        tma_load_2d(su32(sA + stage * HA_BYTES), &tmA, kb * KELEMS, ay, full(stage));
                         tma_load_2d(su32(sB + stage * HB_BYTES), &tmB, kb * KELEMS, t * HBN, full(stage));
                         issued[stage] = true;
                         ipar[stage] = phase;
@@ -189,7 +216,8 @@ __global__ void __launch_bounds__(H_THREADS, 1)
             int stage = 0, acc = 0;
             uint32_t phase = 0, aphase = 0;
             bool ab = false;
-            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
+            int64_t it = 0;
+            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++) {
                 for (int t = 0; t < p.nt && !ab; t++) {
                     if (!mbar_wait(sempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
                     tc_fence_after();
@@ -197,6 +225,8 @@ __global__ void __launch_bounds__(H_THREADS, 1)
                     for (int kb = 0; kb < p.num_kb; kb++) {
                         if (!mbar_wait(full(stage), phase, abort_flag)) { ab = true; break; }
                         tc_fence_after();
+                        // the last copy of the staged query tile has landed
+                        if (QIN && t == p.nt - 1 && kb == p.num_kb - 1) mbar_arrive(a_free((int)(it & 1)));
                         const uint32_t a0 = su32(sA + stage * HA_BYTES), b0 = su32(sB + stage * HB_BYTES);
 #pragma unroll
                         for (int k = 0; k < BKB / 32; k++)
@@ -246,7 +276,32 @@ __global__ void __launch_bounds__(H_THREADS, 1)
             const unsigned long long t0 = gtimer();
             while (!mbar_try(done2_bar, 0) && gtimer() - t0 < 100000000ull) {}
         }
+    } else if (QIN && warp >= QW0) {  // ----------------------------- query quantisers
+        const int qw = warp - QW0;
+        uint32_t fph = 0;
+        int64_t it = 0;
+        for (int64_t mt = blockIdx.x; mt < num_m_tiles && !*abort_flag; mt += gridDim.x, it++) {
+            const int b = (int)(it & 1);
+            uint8_t *tile = p.stage + (size_t)(blockIdx.x * 2 + b) * BM * p.ld * QES;
+            if (it >= 2) {
+                const bool okf = mbar_wait(a_free(b), (fph >> b) & 1u, abort_flag);
+                fph ^= 1u << b;
+                if (!__all_sync(0xffffffffu, okf)) break;
+            }
+            if (it == 0)
+                quant_tile<ENC, 2>(qr, mt * BM, tile, 4 * HEWG + qw, 4 * HEWG + QWARPS_IN, lane);
+            else
+                quant_tile<ENC, 2>(qr, mt * BM, tile, qw, QWARPS_IN, lane);
+            fence_to_async_global();
+            mbar_arrive(it == 0 ? a0_ready : a_ready(b));
+        }
     } else {  // ------------------------------------------ epilogue warps 0 .. 11
+        if (QIN) {  // the first staged tile, with the quantiser warps
+            quant_tile<ENC, 2>(qr, (int64_t)blockIdx.x * BM, p.stage + (size_t)blockIdx.x * 2 * BM * p.ld * QES, warp,
+                               4 * HEWG + QWARPS_IN, lane);
+            fence_to_async_global();
+            mbar_arrive(a0_ready);
+        }
         const int q = warp & 3, g = warp >> 2;
         const int r = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
@@ -346,16 +401,24 @@ __global__ void __launch_bounds__(H_THREADS, 1)
     }
 }
 
+template <int ENC, bool QIN>
+static cudaError_t launch_hamming_q(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &ms,
+                                    const HParams &p, unsigned grid, cudaStream_t st)
+{
+    auto k = tc_hamming_kernel<ENC, QIN>;
+    const size_t smem = h_smem_bytes(p.Cp);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, h_threads(QIN), smem, st>>>(ma, mb, ms, p);
+    return cudaGetLastError();
+}
+
 template <int ENC>
 static cudaError_t launch_hamming_enc(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &ms,
                                       const HParams &p, unsigned grid, cudaStream_t st)
 {
-    auto k = tc_hamming_kernel<ENC>;
-    const size_t smem = h_smem_bytes(p.Cp);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<grid, H_THREADS, smem, st>>>(ma, mb, ms, p);
-    return cudaGetLastError();
+    return p.X ? launch_hamming_q<ENC, true>(ma, mb, ms, p, grid, st)
+               : launch_hamming_q<ENC, false>(ma, mb, ms, p, grid, st);
 }
 
 cudaError_t launch_hamming_bf16(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &ms,

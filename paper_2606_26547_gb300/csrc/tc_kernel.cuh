@@ -264,8 +264,15 @@ __device__ __forceinline__ uint32_t pack_signs(const uint32_t (&r)[32])
 // arithmetic is the row quantiser's: BF16 by round-to-nearest-even, E4M3
 // after the row's power-of-two scale.  The scale itself is not kept: it is
 // positive, and the classify epilogue uses only the signs.
+// Source and layout of the rows a kernel quantises itself.
+struct QinRows {
+    const float *X;   // N x ldX FP32 rows (16-byte aligned, F % 4 == 0)
+    int64_t ldX, N;
+    int F, ld;        // features, elements per staged row (<= QIN_MAX_LD)
+};
+
 template <int ENC, int RQ>
-__device__ __forceinline__ void quant_tile(const Params &p, int64_t row0, uint8_t *tile, int w, int nw, int lane)
+__device__ __forceinline__ void quant_tile(const QinRows &p, int64_t row0, uint8_t *tile, int w, int nw, int lane)
 {
     constexpr int ES = ENC == HDC_ENC_BF16 ? 2 : 1;
     constexpr int MAXIT = QIN_MAX_LD / 128;
@@ -366,6 +373,7 @@ __global__ void __launch_bounds__(num_threads(EWG, QIN), 1)
     constexpr int RQ = EWG == 1 ? 4 : 2;               // rows in flight per quantising warp
     constexpr int QES = ENC == HDC_ENC_BF16 ? 2 : 1;
     static_assert(!QIN || (CLASSIFY && EWG <= 2), "in-kernel quantisation: classify with one or two warpgroups");
+    const QinRows qr = {p.X, p.ldX, p.N, p.F, p.ld};
     constexpr int NMRG = EWG > 1 ? EWG - 1 : 1;
     int32_t *s_val = reinterpret_cast<int32_t *>(tmem_slot + 4);  // per-row minimum of warpgroups 1..EWG-1
     int32_t *s_idx = s_val + NMRG * BM;                             // and its class
@@ -515,15 +523,15 @@ __global__ void __launch_bounds__(num_threads(EWG, QIN), 1)
                 if (!__all_sync(0xffffffffu, okf)) break;
             }
             if (it == 0)
-                quant_tile<ENC, RQ>(p, mt * BM, tile, 4 * EWG + qw, 4 * EWG + QWARPS_IN, lane);
+                quant_tile<ENC, RQ>(qr, mt * BM, tile, 4 * EWG + qw, 4 * EWG + QWARPS_IN, lane);
             else
-                quant_tile<ENC, RQ>(p, mt * BM, tile, qw, QWARPS_IN, lane);
+                quant_tile<ENC, RQ>(qr, mt * BM, tile, qw, QWARPS_IN, lane);
             fence_to_async_global();
             mbar_arrive(it == 0 ? a0_ready : a_ready(b));
         }
     } else {  // ------------------------------------ epilogue warps 0 .. 4*EWG-1
         if (QIN) {  // the first staged tile, with the quantiser warps
-            quant_tile<ENC, RQ>(p, (int64_t)blockIdx.x * BM, p.stage + (size_t)blockIdx.x * 2 * BM * p.ld * QES, warp,
+            quant_tile<ENC, RQ>(qr, (int64_t)blockIdx.x * BM, p.stage + (size_t)blockIdx.x * 2 * BM * p.ld * QES, warp,
                                 4 * EWG + QWARPS_IN, lane);
             fence_to_async_global();
             mbar_arrive(a0_ready);

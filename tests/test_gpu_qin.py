@@ -1,7 +1,8 @@
 """The fused classify that quantises its own query tiles.
 
-For binary classes (up to 32) on the tensor cores, hdc_classify hands the
-FP32 rows to the fused kernel, which quantises each 128-query tile (BF16 by
+For binary classes on the tensor cores (up to 32 with the popcount
+epilogue, 33..112 with the Hamming distances as a second MMA), hdc_classify
+hands the FP32 rows to the fused kernel, which quantises each 128-query tile (BF16 by
 round-to-nearest-even, E4M3 after the row's power-of-two scale: Sec. 4.2
 "Element Type Representation") one tile ahead of its MMAs, whenever every
 CTA has at least two tiles (N >= 2 x SMs x 128).  Smaller batches quantise
@@ -68,7 +69,7 @@ def gauss_rows(rng, N, F, octaves=True):
 
 
 @pytest.mark.parametrize("enc", ["fp8", "bf16"])
-@pytest.mark.parametrize("C", [10, 26])                 # one and two epilogue warpgroups
+@pytest.mark.parametrize("C", [10, 26, 48, 112])        # one, two epilogue warpgroups; tensor-core Hamming
 @pytest.mark.parametrize("F,extra", [(784, 77), (100, 0), (1024, 1)])
 def test_qin_equals_row_quantiser_route(hdc, enc, C, F, extra):
     rng = np.random.default_rng(C * 1000 + F + extra)
@@ -96,13 +97,13 @@ def test_qin_equals_row_quantiser_route(hdc, enc, C, F, extra):
 
 
 @pytest.mark.parametrize("enc", ["fp8", "bf16"])
-@pytest.mark.parametrize("extra", [0, 1, 128 * 152 + 77])
-def test_qin_integer_data_equals_oracle(hdc, enc, extra):
+@pytest.mark.parametrize("extra,C", [(0, 10), (1, 10), (128 * 152 + 77, 10), (77, 100)])
+def test_qin_integer_data_equals_oracle(hdc, enc, extra, C):
     """Integer features and a +-1 base: every projection is exact in either
     encoding, so every label and distance equals the oracle's (all rows)."""
     from paper_2606_26547_gb300 import synth
     N = threshold() + extra
-    F, D, C = 100, 600, 10
+    F, D = 100, 600
     X, _ = synth.int_mixture(N, F, C, 2.0, 401, 402)
     rng = np.random.default_rng(403)
     Bt = (1 - 2 * rng.integers(0, 2, (D, F))).astype(np.float32)
