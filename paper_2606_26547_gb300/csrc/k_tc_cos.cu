@@ -120,21 +120,23 @@ __global__ void __launch_bounds__(192, 1)
             // BF16 x BF16 -> FP32, K-major A and B, M = 128, N = Cp
             const uint32_t id = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(p.Cp >> 3) << 17) |
                                 ((uint32_t)(BM >> 4) << 24);
+            const uint64_t da0 = sdesc(su32(sA)), db0 = sdesc(su32(sB));
+            const uint32_t full0 = full(0), empty0 = empty(0);   // stage s: + 8 * s
             int stage = 0, acc = 0;
             uint32_t phase = 0, aphase = 0;
             bool ab = false;
             for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
-                if (!mbar_wait(tempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
+                if (!mbar_wait_fast(tempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(acc * CBN);
                 for (int kb = 0; kb < p.num_kb; kb++) {
-                    if (!mbar_wait(full(stage), phase, abort_flag)) { ab = true; break; }
+                    if (!mbar_wait_fast(full0 + 8u * stage, phase, abort_flag)) { ab = true; break; }
                     tc_fence_after();
-                    const uint32_t a0 = su32(sA + stage * CA_BYTES), b0 = su32(sB + stage * CB_MAX);
+                    const uint64_t da = da0 + (uint64_t)(stage * (CA_BYTES >> 4));
+                    const uint64_t db = db0 + (uint64_t)(stage * (CB_MAX >> 4));
 #pragma unroll
-                    for (int k = 0; k < BKB / 32; k++)
-                        mma<HDC_ENC_BF16>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), id, (kb | k) != 0);
-                    mma_commit(empty(stage));
+                    for (int k = 0; k < BKB / 32; k++) mma<HDC_ENC_BF16>(d, da + 2 * k, db + 2 * k, id, (kb | k) != 0);
+                    mma_commit(empty0 + 8u * stage);
                     if (++stage == CSTAGES) { stage = 0; phase ^= 1; }
                 }
                 if (ab) break;

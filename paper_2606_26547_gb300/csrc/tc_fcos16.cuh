@@ -164,22 +164,24 @@ __global__ void __launch_bounds__(F16_THREADS, 1)
     } else if (warp == ISSUER) {
         if (lane == 0) {  // ------------------------------ MMA1 issuer (encode)
             const uint32_t id1 = idesc_n<ENC>(BN);
+            const uint64_t da0 = sdesc(su32(sA)), db0 = sdesc(su32(sB));
+            const uint32_t full0 = full(0), empty0 = empty(0);   // stage s: + 8 * s
             int stage = 0, acc = 0;
             uint32_t phase = 0, aphase = 0;
             bool ab = false;
             for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
                 for (int t = 0; t < p.nt && !ab; t++) {
-                    if (!mbar_wait(tempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
+                    if (!mbar_wait_fast(tempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
                     tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)(acc * BN);
                     for (int kb = 0; kb < p.num_kb; kb++) {
-                        if (!mbar_wait(full(stage), phase, abort_flag)) { ab = true; break; }
+                        if (!mbar_wait_fast(full0 + 8u * stage, phase, abort_flag)) { ab = true; break; }
                         tc_fence_after();
-                        const uint32_t a0 = su32(sA + stage * A_BYTES), b0 = su32(sB + stage * B_BYTES);
+                        const uint64_t da = da0 + (uint64_t)(stage * (A_BYTES >> 4));
+                        const uint64_t db = db0 + (uint64_t)(stage * (B_BYTES >> 4));
 #pragma unroll
-                        for (int k = 0; k < BKB / 32; k++)
-                            mma<ENC>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), id1, (kb | k) != 0);
-                        mma_commit(empty(stage));
+                        for (int k = 0; k < BKB / 32; k++) mma<ENC>(d, da + 2 * k, db + 2 * k, id1, (kb | k) != 0);
+                        mma_commit(empty0 + 8u * stage);
                         if (++stage == S) { stage = 0; phase ^= 1; }
                     }
                     if (ab) break;

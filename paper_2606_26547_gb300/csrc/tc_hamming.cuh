@@ -213,25 +213,27 @@ __global__ void __launch_bounds__(h_threads(QIN), 1)
     } else if (warp == ISSUER) {
         if (lane == 0) {  // ------------------------------ MMA1 issuer (encode)
             const uint32_t id1 = idesc_n<ENC>(HBN);
+            const uint64_t da0 = sdesc(su32(sA)), db0 = sdesc(su32(sB));
+            const uint32_t full0 = full(0), empty0 = empty(0);   // stage s: + 8 * s
             int stage = 0, acc = 0;
             uint32_t phase = 0, aphase = 0;
             bool ab = false;
             int64_t it = 0;
             for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++) {
                 for (int t = 0; t < p.nt && !ab; t++) {
-                    if (!mbar_wait(sempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
+                    if (!mbar_wait_fast(sempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
                     tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)(acc * HBN);
                     for (int kb = 0; kb < p.num_kb; kb++) {
-                        if (!mbar_wait(full(stage), phase, abort_flag)) { ab = true; break; }
+                        if (!mbar_wait_fast(full0 + 8u * stage, phase, abort_flag)) { ab = true; break; }
                         tc_fence_after();
                         // the last copy of the staged query tile has landed
                         if (QIN && t == p.nt - 1 && kb == p.num_kb - 1) mbar_arrive(a_free((int)(it & 1)));
-                        const uint32_t a0 = su32(sA + stage * HA_BYTES), b0 = su32(sB + stage * HB_BYTES);
+                        const uint64_t da = da0 + (uint64_t)(stage * (HA_BYTES >> 4));
+                        const uint64_t db = db0 + (uint64_t)(stage * (HB_BYTES >> 4));
 #pragma unroll
-                        for (int k = 0; k < BKB / 32; k++)
-                            mma<ENC>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), id1, (kb | k) != 0);
-                        mma_commit(empty(stage));
+                        for (int k = 0; k < BKB / 32; k++) mma<ENC>(d, da + 2 * k, db + 2 * k, id1, (kb | k) != 0);
+                        mma_commit(empty0 + 8u * stage);
                         if (++stage == H_STAGES) { stage = 0; phase ^= 1; }
                     }
                     if (ab) break;

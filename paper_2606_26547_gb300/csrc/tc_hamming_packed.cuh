@@ -191,21 +191,23 @@ __global__ void __launch_bounds__(HP_THREADS, MINB)
             uint32_t ph = 0, d2ph = 0, cph[2] = {0, 0};
             bool ab = false;
             for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
-                if (!mbar_wait(d2empty, d2ph ^ 1, abort_flag)) { ab = true; break; }
+                if (!mbar_wait_fast(d2empty, d2ph ^ 1, abort_flag)) { ab = true; break; }
                 for (int t = 0; t < p.nt; t++) {
-                    if (!mbar_wait(full(buf), ph, abort_flag)) { ab = true; break; }
+                    if (!mbar_wait_fast(full(buf), ph, abort_flag)) { ab = true; break; }
                     if (PRE) {
                         const int cb = BBUF == 2 ? buf : 0;
-                        if (!mbar_wait(cfull(cb), cph[cb], abort_flag)) { ab = true; break; }
+                        if (!mbar_wait_fast(cfull(cb), cph[cb], abort_flag)) { ab = true; break; }
                         cph[cb] ^= 1;
                     }
                     tc_fence_after();
-                    const uint32_t a0 = su32(sA + buf * HP_A_BYTES), b0 = su32(sB + (BBUF == 2 ? buf : 0) * b_bytes);
+                    const uint64_t da = sdesc(su32(sA + buf * HP_A_BYTES));
+                    const uint64_t db = sdesc(su32(sB + (BBUF == 2 ? buf : 0) * b_bytes));
+                    const uint32_t atom_b = (uint32_t)(p.Cp * 128) >> 4;   // second K atom of the class tile
 #pragma unroll
                     for (int k = 0; k < 8; k++) {   // two atoms of four 32-byte K steps
-                        const uint32_t oa = (uint32_t)((k >> 2) * (BM * 128)) + 32u * (k & 3);
-                        const uint32_t ob = (uint32_t)((k >> 2) * (p.Cp * 128)) + 32u * (k & 3);
-                        mma<HDC_ENC_FP8_E4M3>(tmem, sdesc(a0 + oa), sdesc(b0 + ob), id, (t | k) != 0);
+                        const uint64_t oa = (uint64_t)((k >> 2) * ((BM * 128) >> 4) + 2 * (k & 3));
+                        const uint64_t ob = (uint64_t)((k >> 2) * atom_b + 2 * (k & 3));
+                        mma<HDC_ENC_FP8_E4M3>(tmem, da + oa, db + ob, id, (t | k) != 0);
                     }
                     mma_commit(empty(buf));
                     if (++buf == 2) { buf = 0; ph ^= 1; }

@@ -154,6 +154,16 @@ static __device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity, volat
     }
 }
 
+// The bounded wait with its common case inline: an MMA or TMA issuing thread
+// that finds the phase already complete spends one try_wait on it.  (Issue
+// overhead in the single MMA-issuing thread sits on the tensor pipe's
+// critical path: a non-inlined wait and descriptor arithmetic per stage held
+// the pipe ~20 % idle in a TMA + MMA pipeline with no epilogue.)
+__device__ __forceinline__ bool mbar_wait_fast(uint32_t a, uint32_t parity, volatile int *abort_flag)
+{
+    return mbar_try(a, parity) || mbar_wait(a, parity, abort_flag);
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t a)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
@@ -177,7 +187,10 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows
-// of 128 bytes, 8-row core groups 1024 bytes apart (SBO), version 1.
+// of 128 bytes, 8-row core groups 1024 bytes apart (SBO), version 1.  The
+// start address sits in bits 0-13 in 16-byte units, so the descriptor of an
+// operand `bytes` further on is sdesc(addr) + bytes / 16 (shared addresses
+// stay below 256 KB: no carry out of the field).
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr)
 {
     uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
@@ -479,26 +492,28 @@ __global__ void __launch_bounds__(num_threads(EWG, QIN), 1)
     } else if (warp == ISSUER) {
         if (lane == 0) {  // ---------------------------------- MMA issuer
             const uint32_t id = idesc<ENC>();
+            const uint64_t da0 = sdesc(su32(sA)), db0 = sdesc(su32(sB));
+            const uint32_t full0 = full(0), empty0 = empty(0);   // stage s: + 8 * s
             int stage = 0, acc = 0;
             uint32_t phase = 0, aphase = 0;
             bool ab = false;
             int64_t it = 0;
             for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++)
                 for (int nt = 0; nt < num_n_tiles && !ab; nt++) {
-                    if (!mbar_wait(tempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
+                    if (!mbar_wait_fast(tempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
                     tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)(acc * BN);
                     for (int kb = 0; kb < p.num_kb; kb++) {
-                        if (!mbar_wait(full(stage), phase, abort_flag)) { ab = true; break; }
+                        if (!mbar_wait_fast(full0 + 8u * stage, phase, abort_flag)) { ab = true; break; }
                         tc_fence_after();
                         // the last copy of the staged query tile has landed:
                         // its quantisers may overwrite it
                         if (QIN && nt == num_n_tiles - 1 && kb == p.num_kb - 1) mbar_arrive(a_free((int)(it & 1)));
-                        const uint32_t a0 = su32(sA + stage * A_BYTES), b0 = su32(sB + stage * B_BYTES);
+                        const uint64_t da = da0 + (uint64_t)(stage * (A_BYTES >> 4));
+                        const uint64_t db = db0 + (uint64_t)(stage * (B_BYTES >> 4));
 #pragma unroll
-                        for (int k = 0; k < BKB / 32; k++)
-                            mma<ENC>(d, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), id, (kb | k) != 0);
-                        mma_commit(empty(stage));
+                        for (int k = 0; k < BKB / 32; k++) mma<ENC>(d, da + 2 * k, db + 2 * k, id, (kb | k) != 0);
+                        mma_commit(empty0 + 8u * stage);
                         if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
                     if (ab) break;
