@@ -158,10 +158,12 @@ cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st)
     tc::Params p;
     p.N = a.N;
     p.Dk = a.Dk;
-    // K blocks of 128 bytes over the padded row (zeros past F); issuing only
-    // the MMAs that reach into [0, F) in the last block measured slower
+    // K blocks of 128 bytes over the padded row (zeros past F); the last
+    // block issues only the 32-byte K steps that reach into [0, F)
     const int es = a.enc == HDC_ENC_BF16 ? 2 : 1;
     p.num_kb = (a.ldx * es + tc::BKB - 1) / tc::BKB;
+    p.last_k = (a.F * es - (p.num_kb - 1) * tc::BKB + 31) / 32;
+    if (p.last_k < 1 || p.last_k > tc::BKB / 32) p.last_k = tc::BKB / 32;
     p.W = a.W;
     p.sx = a.sx;
     p.sb = a.sb;

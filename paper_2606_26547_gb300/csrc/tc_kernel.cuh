@@ -89,6 +89,7 @@ constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
 struct Params {
     int64_t N;
     int Dk, num_kb, W;
+    int last_k = BKB / 32;   // MMA K steps of the last K block that reach into [0, F) (1..4)
     const float *sx, *sb;
     uint32_t *H;
     float *scores;
@@ -511,8 +512,11 @@ __global__ void __launch_bounds__(num_threads(EWG, QIN), 1)
                         if (QIN && nt == num_n_tiles - 1 && kb == p.num_kb - 1) mbar_arrive(a_free((int)(it & 1)));
                         const uint64_t da = da0 + (uint64_t)(stage * (A_BYTES >> 4));
                         const uint64_t db = db0 + (uint64_t)(stage * (B_BYTES >> 4));
+                        // K steps wholly in the zero padding past F add nothing: skipped
+                        const int nk = kb == p.num_kb - 1 ? p.last_k : BKB / 32;
 #pragma unroll
-                        for (int k = 0; k < BKB / 32; k++) mma<ENC>(d, da + 2 * k, db + 2 * k, id, (kb | k) != 0);
+                        for (int k = 0; k < BKB / 32; k++)
+                            if (k < nk) mma<ENC>(d, da + 2 * k, db + 2 * k, id, (kb | k) != 0);
                         mma_commit(empty0 + 8u * stage);
                         if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
