@@ -208,16 +208,20 @@ def tc_sources_sha():
     return h.hexdigest()[:16]
 
 
-def launches_per_step(fused: bool, C: int, F: int, enc: str, B: int) -> int:
+def launches_per_step(fused: bool, C: int, F: int, Dk: int, enc: str, B: int) -> int:
     """Kernels one hdc_classify call launches: the fused kernel alone when it
     quantises its own query tiles (binary classes, up to 112; F % 4 == 0;
-    rows of at most 1,024 quantised elements; two 128-query tiles per SM),
-    the row quantiser first otherwise, and a similarity or cosine kernel
-    after an encode-only launch."""
+    rows of at most 1,024 quantised elements; two 128-query tiles per SM; at
+    least 0.15 * F MMA stages of 128 bytes per query tile), the row quantiser
+    first otherwise, and a similarity or cosine kernel after an encode-only
+    launch."""
     import torch
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     q = 128 if enc == "fp8" else 64
-    if fused and C <= 112 and F % 4 == 0 and (F + q - 1) // q * q <= 1024 and B >= 2 * sms * 128:
+    ld = (F + q - 1) // q * q
+    tile_n = 192 if C > 32 else 256
+    stages = -(-Dk // tile_n) * -(-ld * (128 // q) // 128)
+    if fused and C <= 112 and F % 4 == 0 and ld <= 1024 and B >= 2 * sms * 128 and 20 * stages >= 3 * F:
         return 1
     return 2 if fused else 3
 
@@ -659,7 +663,7 @@ def run_ours(a):
                 "frac_of_copy_bound": e2e_qps / world / copy_qps,
                 "copy_bound": "the same rows and labels, %d chunks, copies only, the faster of one and two "
                               "streams" % nch},
-        "gpu_launches": launches_per_step(fused, w.C, F, a.enc, B) * a.steps,
+        "gpu_launches": launches_per_step(fused, w.C, F, Dk, a.enc, B) * a.steps,
         "clocks": clocks,
         "exact": {"value": exact_qps, "unit": UNIT, "enc": "fp32 (FFMA)", "Dk": w.D,
                   "ms_per_step": el_ex / a.exact_steps * 1e3},

@@ -167,8 +167,9 @@ bool tc_supported(const TcArgs &a);
 // Whether the fused classify of a can quantise its own query tiles from the
 // FP32 rows a.X (binary classes: up to 32, or up to 112 with their E4M3
 // signs; 16-byte aligned rows of F % 4 == 0 floats; ldx <= 1024; at least two
-// tiles per CTA), and the bytes its staged tiles take (at most N rows of the
-// quantised operand).
+// tiles per CTA; at least 0.15 * F 128-byte MMA stages per query tile, below
+// which the row-quantiser pass is faster), and the bytes its staged tiles
+// take (at most N rows of the quantised operand).
 bool tc_qin_ok(const TcArgs &a);
 size_t tc_stage_bytes(const TcArgs &a);
 

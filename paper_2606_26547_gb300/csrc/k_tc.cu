@@ -131,6 +131,17 @@ bool tc_qin_ok(const TcArgs &a)
         return false;
     const int sms = sm_count();
     if (sms <= 0) return false;
+    // The quantiser warps keep a few rows in flight each, so a tile's FP32
+    // rows take about as long as 0.15 * F of its 128-byte MMA stages.  With
+    // fewer stages per tile they set the pace, and the row-quantiser pass
+    // (at the HBM rate) plus the fused kernel is faster.  Measured on GB300
+    // (1,048,576 queries, F = 784, E4M3, two builds alternated): 140 stages
+    // per tile 3.54 vs 3.59 ms, 280 stages 6.26 vs 6.58 ms, 70 stages 2.82
+    // vs 2.11 ms.
+    const int es = a.enc == HDC_ENC_BF16 ? 2 : 1;
+    const int tile_n = a.C > 32 ? tc::HBN : tc::BN;
+    const int64_t stages = (int64_t)((a.Dk + tile_n - 1) / tile_n) * ((a.ldx * es + tc::BKB - 1) / tc::BKB);
+    if (20 * stages < (int64_t)3 * a.F) return false;
     // two staged tiles per CTA fit in the N rows of the quantised operand
     return a.N >= (int64_t)2 * tc_grid(a.N, sms) * tc::BM;
 }

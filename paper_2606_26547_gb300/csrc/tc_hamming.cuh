@@ -23,8 +23,8 @@
 // enters the tensor pipe as soon as its sign tile is ready, without holding
 // back the issue of the next tile's MMA1 (a single issuer measured ~2,400
 // cycles of issue and commit latency at each tile boundary).  With QIN,
-// warps 16 and 17 quantise the query tiles from FP32 rows one tile ahead into
-// the CTA's two staged tiles, as in the encoder (tc_kernel.cuh).  Every wait
+// warps 16-19 quantise the query tiles from FP32 rows one tile ahead into the
+// CTA's two staged tiles, as in the encoder (tc_kernel.cuh).  Every wait
 // is bounded as in the encoder.
 #pragma once
 #include "tc_kernel.cuh"
@@ -39,7 +39,8 @@ constexpr int HB_BYTES = HBN * BKB;           // 24 KB
 constexpr int H_STAGE_BYTES = HA_BYTES + HB_BYTES;
 constexpr int HEWG = 3;                       // epilogue warpgroups
 constexpr int H_THREADS = (4 * HEWG + 4) * 32;   // + the MMA2 issuer
-__host__ __device__ constexpr int h_threads(bool qin) { return H_THREADS + (qin ? QWARPS_IN * 32 : 0); }
+constexpr int H_QW = 4;                          // quantiser warps (QIN): 20 warps at up to 96 registers
+__host__ __device__ constexpr int h_threads(bool qin) { return H_THREADS + (qin ? H_QW * 32 : 0); }
 constexpr int A2_ATOM = BM * 128;             // one 128-byte K atom of the sign tile
 constexpr int A2_BYTES = 2 * A2_ATOM;         // K = 192 bytes in two atoms
 constexpr int H_CMAX = 112;
@@ -133,9 +134,9 @@ __global__ void __launch_bounds__(h_threads(QIN), 1)
         mbar_init(done2_bar, 1);
         mbar_init(merge_full, BM * (HEWG - 1));
         mbar_init(merge_empty, BM);
-        mbar_init(a0_ready, (4 * HEWG + QWARPS_IN) * 32);
+        mbar_init(a0_ready, (4 * HEWG + H_QW) * 32);
         for (int b = 0; b < 2; b++) {
-            mbar_init(a_ready(b), QWARPS_IN * 32);
+            mbar_init(a_ready(b), H_QW * 32);
             mbar_init(a_free(b), 1);
         }
         *abort_flag = 0;
@@ -291,16 +292,16 @@ __global__ void __launch_bounds__(h_threads(QIN), 1)
                 if (!__all_sync(0xffffffffu, okf)) break;
             }
             if (it == 0)
-                quant_tile<ENC, 2>(qr, mt * BM, tile, 4 * HEWG + qw, 4 * HEWG + QWARPS_IN, lane);
+                quant_tile<ENC, 2>(qr, mt * BM, tile, 4 * HEWG + qw, 4 * HEWG + H_QW, lane);
             else
-                quant_tile<ENC, 2>(qr, mt * BM, tile, qw, QWARPS_IN, lane);
+                quant_tile<ENC, 2>(qr, mt * BM, tile, qw, H_QW, lane);
             fence_to_async_global();
             mbar_arrive(it == 0 ? a0_ready : a_ready(b));
         }
     } else {  // ------------------------------------------ epilogue warps 0 .. 11
         if (QIN) {  // the first staged tile, with the quantiser warps
             quant_tile<ENC, 2>(qr, (int64_t)blockIdx.x * BM, p.stage + (size_t)blockIdx.x * 2 * BM * p.ld * QES, warp,
-                               4 * HEWG + QWARPS_IN, lane);
+                               4 * HEWG + H_QW, lane);
             fence_to_async_global();
             mbar_arrive(a0_ready);
         }

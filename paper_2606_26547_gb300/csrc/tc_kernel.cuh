@@ -58,12 +58,15 @@ constexpr int A_BYTES = BM * BKB;            // 16 KB
 constexpr int B_BYTES = BN * BKB;            // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 // threads: 4*EWG epilogue warps (EWG = 1, 2 or 4 warpgroups), a TMA warp, an
-// MMA warp and, when the kernel quantises its own query tiles, QWARPS_IN
-// quantiser warps
-constexpr int QWARPS_IN = 2;
+// MMA warp and, when the kernel quantises its own query tiles, two quantiser
+// warps.  Their loads are latency-bound, so the rows each keeps in flight
+// (quant_tile's RQ) set how fast a tile's FP32 rows arrive: four beside one
+// epilogue warpgroup (eight warps, two per scheduler, up to 255 registers),
+// two beside two (twelve warps, three per scheduler: at most 168 registers).
+__host__ __device__ constexpr int qwarps(int) { return 2; }
 __host__ __device__ constexpr int num_threads(int ewg, bool qin = false)
 {
-    return (4 * ewg + 2 + (qin ? QWARPS_IN : 0)) * 32;
+    return (4 * ewg + 2 + (qin ? qwarps(ewg) : 0)) * 32;
 }
 // elements of a staged query row the quantisers hold in registers (8 x 128)
 constexpr int QIN_MAX_LD = 1024;
@@ -384,6 +387,7 @@ __global__ void __launch_bounds__(num_threads(EWG, QIN), 1)
     auto a_ready = [&](int b) { return su32(bars + QB + 1 + b); };
     auto a_free = [&](int b) { return su32(bars + QB + 3 + b); };
     constexpr int QW0 = 4 * EWG + 2;                   // first quantiser warp
+    constexpr int QW = qwarps(EWG);                    // quantiser warps
     constexpr int RQ = EWG == 1 ? 4 : 2;               // rows in flight per quantising warp
     constexpr int QES = ENC == HDC_ENC_BF16 ? 2 : 1;
     static_assert(!QIN || (CLASSIFY && EWG <= 2), "in-kernel quantisation: classify with one or two warpgroups");
@@ -418,9 +422,9 @@ __global__ void __launch_bounds__(num_threads(EWG, QIN), 1)
             mbar_init(cempty(b), BM * EWG);
         }
         for (int b = 0; b < WXB; b++) mbar_init(wfull(b), BM * EWG);
-        mbar_init(a0_ready, (4 * EWG + QWARPS_IN) * 32);
+        mbar_init(a0_ready, (4 * EWG + QW) * 32);
         for (int b = 0; b < 2; b++) {
-            mbar_init(a_ready(b), QWARPS_IN * 32);
+            mbar_init(a_ready(b), QW * 32);
             mbar_init(a_free(b), 1);
         }
         *abort_flag = 0;
@@ -542,16 +546,16 @@ __global__ void __launch_bounds__(num_threads(EWG, QIN), 1)
                 if (!__all_sync(0xffffffffu, okf)) break;
             }
             if (it == 0)
-                quant_tile<ENC, RQ>(qr, mt * BM, tile, 4 * EWG + qw, 4 * EWG + QWARPS_IN, lane);
+                quant_tile<ENC, RQ>(qr, mt * BM, tile, 4 * EWG + qw, 4 * EWG + QW, lane);
             else
-                quant_tile<ENC, RQ>(qr, mt * BM, tile, qw, QWARPS_IN, lane);
+                quant_tile<ENC, RQ>(qr, mt * BM, tile, qw, QW, lane);
             fence_to_async_global();
             mbar_arrive(it == 0 ? a0_ready : a_ready(b));
         }
     } else {  // ------------------------------------ epilogue warps 0 .. 4*EWG-1
         if (QIN) {  // the first staged tile, with the quantiser warps
             quant_tile<ENC, RQ>(qr, (int64_t)blockIdx.x * BM, p.stage + (size_t)blockIdx.x * 2 * BM * p.ld * QES, warp,
-                                4 * EWG + QWARPS_IN, lane);
+                                4 * EWG + QW, lane);
             fence_to_async_global();
             mbar_arrive(a0_ready);
         }

@@ -5,8 +5,11 @@ epilogue, 33..112 with the Hamming distances as a second MMA), hdc_classify
 hands the FP32 rows to the fused kernel, which quantises each 128-query tile (BF16 by
 round-to-nearest-even, E4M3 after the row's power-of-two scale: Sec. 4.2
 "Element Type Representation") one tile ahead of its MMAs, whenever every
-CTA has at least two tiles (N >= 2 x SMs x 128).  Smaller batches quantise
-all rows first in a kernel of their own.  Both routes feed the same
+CTA has at least two tiles (N >= 2 x SMs x 128) and each tile carries at
+least 0.15 * F MMA stages of 128 bytes (dim tiles x K blocks; below that the
+separate quantiser pass is faster).  Smaller batches quantise all rows first
+in a kernel of their own.  The shapes below (D = 10,000 at stride 2 or 3)
+meet the stage rule.  Both routes feed the same
 operands to the same MMAs, so labels and Hamming distances must agree bit
 for bit: the checks below classify a batch above the threshold once and in
 slices below it, compare with the Hamming distances of the hypervectors
@@ -74,7 +77,7 @@ def gauss_rows(rng, N, F, octaves=True):
 def test_qin_equals_row_quantiser_route(hdc, enc, C, F, extra):
     rng = np.random.default_rng(C * 1000 + F + extra)
     N = threshold() + (3 * 128 + 5 if extra else 0) + extra
-    D = 1000
+    D = 10000
     X = gauss_rows(rng, N, F)
     Bt = rng.standard_normal((D, F)).astype(np.float32)
     acc = rng.integers(-500, 501, (C, D)).astype(np.int32)
@@ -103,7 +106,7 @@ def test_qin_integer_data_equals_oracle(hdc, enc, extra, C):
     encoding, so every label and distance equals the oracle's (all rows)."""
     from paper_2606_26547_gb300 import synth
     N = threshold() + extra
-    F, D = 100, 600
+    F, D = 100, 8000
     X, _ = synth.int_mixture(N, F, C, 2.0, 401, 402)
     rng = np.random.default_rng(403)
     Bt = (1 - 2 * rng.integers(0, 2, (D, F))).astype(np.float32)
@@ -123,7 +126,7 @@ def test_qin_row_scale_edges(hdc, enc):
     whose maximum sits on either side of 448 * 2^k: the in-kernel scale and
     conversion equal the row quantiser's."""
     rng = np.random.default_rng(7)
-    N, F, D, C = threshold() + 300, 128, 520, 16
+    N, F, D, C = threshold() + 300, 128, 10000, 16
     X = gauss_rows(rng, N, F, octaves=False)
     X[0::7] = 0.0
     X[1::7] *= np.float32(2.0 ** -140)                        # subnormal
@@ -149,7 +152,7 @@ def test_qin_row_scale_edges(hdc, enc):
 def test_qin_threshold_edges(hdc, delta):
     """Either side of the route boundary, with ragged query tiles."""
     rng = np.random.default_rng(50 + delta)
-    N, F, D, C = threshold() + delta, 64, 777, 5
+    N, F, D, C = threshold() + delta, 64, 10000, 5
     X = gauss_rows(rng, N, F)
     Bt = rng.standard_normal((D, F)).astype(np.float32)
     acc = rng.integers(-50, 51, (C, D)).astype(np.int32)
