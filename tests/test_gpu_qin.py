@@ -165,3 +165,23 @@ def test_qin_threshold_edges(hdc, delta):
     assert hdc.stream_status() == 0
     assert torch.equal(lab, torch.cat([r[0] for r in ref]))
     assert torch.equal(dist, torch.cat([r[1] for r in ref]))
+
+
+@pytest.mark.parametrize("enc", ["fp8", "bf16"])
+@pytest.mark.parametrize("D", [512, 1536, 2560])
+def test_qin_few_dim_tiles(hdc, enc, D):
+    """Short rows (F = 8, one K block) and 2, 6 or 10 dim tiles per query
+    tile: few MMA stages between consecutive query tiles, so the quantiser
+    warps' tile-ahead hand-off is exercised at its tightest."""
+    rng = np.random.default_rng(D)
+    N, F, C = threshold() + 129, 8, 12
+    X = gauss_rows(rng, N, F)
+    Bt = rng.standard_normal((D, F)).astype(np.float32)
+    acc = rng.integers(-50, 51, (C, D)).astype(np.int32)
+    model = hdc.Model(T(Bt), hdc.ApproxConfig(enc=enc), acc=T(acc))
+    Xd = T(X)
+    lab, dist = hdc.classify(Xd, model, sims=True)
+    l_ref, d_ref = sliced(hdc, Xd, model)
+    torch.cuda.synchronize()
+    assert hdc.stream_status() == 0
+    assert torch.equal(lab, l_ref) and torch.equal(dist, d_ref)
