@@ -195,8 +195,8 @@ class ClockSampler:
 # its own query tiles, so the FP32 rows are its input): bytes per query,
 # valid only while the kernel sources hash to the value they had when it was
 # taken.
-PROFILED_TRAFFIC = {"sources_sha1_16": "11710a6e3a033075", "enc": "fp8", "stride": 2,
-                    "dram_bytes_per_query": (827032576 + 65636352) / 262144}
+PROFILED_TRAFFIC = {"sources_sha1_16": "7989892ed9c97e77", "enc": "fp8", "stride": 2,
+                    "dram_bytes_per_query": (826735104 + 65808128) / 262144}
 
 
 def tc_sources_sha():
@@ -562,21 +562,6 @@ def run_ours(a):
     e2e_streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
     ws_e2e = [m_apx.workspace(bounds[1] - bounds[0] + 1) for _ in e2e_streams]
 
-    def step_e2e(i):
-        for s in e2e_streams:
-            s.wait_stream(stream)
-        for c in range(nch):
-            lo, hi = bounds[c], bounds[c + 1]
-            hdc.classify_host([Xh[lo:hi]], m_apx, Xd[lo:hi], labels[lo:hi], Lh[lo:hi], ws_e2e[c % 2],
-                              stream=e2e_streams[c % 2])
-        for s in e2e_streams:
-            stream.wait_stream(s)
-
-    step_e2e(0)
-    torch.cuda.synchronize()
-    el_e2e = timed_steps(torch, step_e2e, e2e_steps, stream)
-    e2e_qps = world * B * e2e_steps / el_e2e
-
     # the bound that figure meets: the same rows and labels copied in the
     # same chunks with no kernel between them, on the same two streams and on
     # one stream (two host-to-device copies in flight at once can share the
@@ -596,7 +581,27 @@ def run_ours(a):
         torch.cuda.synchronize()
         return timed_steps(torch, step_copy, e2e_steps, stream)
 
-    el_copy2, el_copy1 = copies(2), copies(1)
+    # the host link's rate varies within one process (~160 to ~210 GB/s
+    # measured), so the copies are timed here and again after the e2e leg;
+    # the fastest arrangement and time is the bound
+    el_copy_pre = {2: copies(2), 1: copies(1)}
+
+    def step_e2e(i):
+        for s in e2e_streams:
+            s.wait_stream(stream)
+        for c in range(nch):
+            lo, hi = bounds[c], bounds[c + 1]
+            hdc.classify_host([Xh[lo:hi]], m_apx, Xd[lo:hi], labels[lo:hi], Lh[lo:hi], ws_e2e[c % 2],
+                              stream=e2e_streams[c % 2])
+        for s in e2e_streams:
+            stream.wait_stream(s)
+
+    step_e2e(0)
+    torch.cuda.synchronize()
+    el_e2e = timed_steps(torch, step_e2e, e2e_steps, stream)
+    e2e_qps = world * B * e2e_steps / el_e2e
+
+    el_copy2, el_copy1 = min(copies(2), el_copy_pre[2]), min(copies(1), el_copy_pre[1])
     el_copy = min(el_copy1, el_copy2)
     copy_qps = B * e2e_steps / el_copy
     h2d_gbs = B * w.F * 4 * e2e_steps / el_copy / 1e9
@@ -661,8 +666,8 @@ def run_ours(a):
                 "copy_only_qps": copy_qps * world, "h2d_copy_gbs": h2d_gbs,
                 "h2d_copy_gbs_by_streams": copy_gbs_by_streams,
                 "frac_of_copy_bound": e2e_qps / world / copy_qps,
-                "copy_bound": "the same rows and labels, %d chunks, copies only, the faster of one and two "
-                              "streams" % nch},
+                "copy_bound": "the same rows and labels, %d chunks, copies only, the fastest of one and two "
+                              "streams, timed before and after the e2e leg" % nch},
         "gpu_launches": launches_per_step(fused, w.C, F, Dk, a.enc, B) * a.steps,
         "clocks": clocks,
         "exact": {"value": exact_qps, "unit": UNIT, "enc": "fp32 (FFMA)", "Dk": w.D,
