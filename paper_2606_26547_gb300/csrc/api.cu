@@ -107,7 +107,7 @@ ModelLayout model_layout(int F, int Dk, int C, int enc, int bits, uint32_t flags
 }
 
 struct WsLayout {
-    size_t xq, sx, h, sp, qn, sf, total;
+    size_t xq, sx, h, sp, qn, sf, dacc, total;
 };
 
 bool use_tc(const hdc_model *m);
@@ -128,6 +128,10 @@ WsLayout ws_layout(int64_t N, const hdc_model *m)
     L.sp = off; off = align_up(off + (fq ? (size_t)N * lds_for(m->Dk) * 2 : 0), kAlign);
     L.qn = off; off = align_up(off + (fq ? (size_t)N * 4 : 0), kAlign);
     L.sf = off; off = align_up(off + (fq ? (size_t)N * m->Dk * 4 : 0), kAlign);
+    // a classify of few query tiles splits their dim tiles over CTAs: the
+    // partial distances of at most TC_SPLIT_MAX_TILES tiles and their counters
+    L.dacc = off;
+    off = align_up(off + (m->C > 0 && !fq ? tc_split_bytes(N, m->C) : 0), kAlign);
     L.total = off;
     return L;
 }
@@ -485,8 +489,10 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *
         a.planes = m->cls; a.C = m->C; a.nb = nb; a.csum = m->cls_sum; a.cnorm = m->cls_norm;
         a.labels = labels; a.dists = dists; a.sims = scores;
         a.cls_sign = m->cls_sign; a.ldcs = m->ldcs;
+        a.dacc = (int32_t *)((char *)ws + L.dacc);
         // binary classes: fully fused; otherwise tensor-core encode + K4
         if (tc_supported(a)) return cu(timed_tc(a, st));
+        a.dacc = nullptr;
         TcArgs e = a;
         e.planes = nullptr; e.labels = nullptr; e.dists = nullptr; e.sims = nullptr; e.H = Hb;
         if (tc_supported(e)) {

@@ -161,7 +161,21 @@ struct TcArgs {
     const float *X;
     int64_t ldX;
     uint8_t *stage;
+    // classify (binary classes, the popcount epilogue): scratch of
+    // tc_split_bytes(N, C) zero-filled per launch, so that a batch of few
+    // query tiles can split each tile's dim tiles over several CTAs; NULL
+    // keeps one CTA per query tile
+    int32_t *dacc;
 };
+// Query tiles whose dim tiles a fused classify may split over CTAs, and the
+// scratch that needs: partial distances of those tiles' rows (int32 x C) and
+// one counter per tile.
+constexpr int64_t TC_SPLIT_MAX_TILES = 256;
+inline size_t tc_split_bytes(int64_t N, int C)
+{
+    const int64_t rows = N < TC_SPLIT_MAX_TILES * 128 ? N : TC_SPLIT_MAX_TILES * 128;
+    return (size_t)rows * C * 4 + (size_t)TC_SPLIT_MAX_TILES * 4;
+}
 cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st);
 bool tc_supported(const TcArgs &a);
 // Whether the fused classify of a can quantise its own query tiles from the

@@ -160,7 +160,7 @@ cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st)
     if (qin && !tc_qin_ok(a)) return cudaErrorNotSupported;
     const int sms = sm_count();
     if (sms <= 0) return cudaErrorNoDevice;
-    const unsigned grid = tc_grid(a.N, sms);
+    unsigned grid = tc_grid(a.N, sms);
     // QIN: the A operand is the CTAs' staged tiles (2 per CTA)
     if (!(qin ? make_map(&ma, a.stage, a.enc, a.F, a.ldx, (int64_t)2 * grid * tc::BM, tc::BM)
               : make_map(&ma, a.Xq, a.enc, a.F, a.ldx, a.N, tc::BM)) ||
@@ -226,6 +226,29 @@ cudaError_t launch_tc_encode(const TcArgs &a, cudaStream_t st)
     }
     CUtensorMap mc = mb;  // unused by encode-only launches
     if (classify && !make_cls_map(&mc, a.planes, a.W, a.C)) return cudaErrorInvalidValue;
+    // few query tiles: split each tile's dim tiles over CTAs so that the
+    // batch fills the SMs (non-empty ranges only); partial distances meet
+    // in the zero-filled scratch
+    const int64_t m_tiles = (a.N + tc::BM - 1) / tc::BM;
+    const int n_tiles = (a.Dk + tc::BN - 1) / tc::BN;
+    unsigned g = grid;
+    if (classify && !qin && a.dacc && m_tiles < sms && m_tiles <= TC_SPLIT_MAX_TILES) {
+        int ns = (int)(sms / m_tiles);
+        if (ns > n_tiles) ns = n_tiles;
+        const int per = (n_tiles + ns - 1) / ns;
+        ns = (n_tiles + per - 1) / per;
+        if (ns > 1) {
+            p.nsplit = ns;
+            p.dacc = a.dacc;
+            p.tile_done = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(a.dacc) +
+                                                       (size_t)a.N * a.C * 4);
+            const cudaError_t e = cudaMemsetAsync(a.dacc, 0, (size_t)a.N * a.C * 4 + (size_t)m_tiles * 4, st);
+            if (e != cudaSuccess) return e;
+            const int64_t units = m_tiles * ns;
+            g = (unsigned)(units < sms ? units : sms);
+        }
+    }
+    grid = g;
     if (a.enc == HDC_ENC_BF16) return tc::launch_bf16(ma, mb, mc, p, grid, classify, st);
     return tc::launch_fp8(ma, mb, mc, p, grid, classify, st);
 }

@@ -108,6 +108,13 @@ struct Params {
     int64_t ldX = 0;
     int F = 0, ld = 0;
     uint8_t *stage = nullptr;
+    // classify of few query tiles: each tile's dim tiles split over nsplit
+    // CTAs, which add their partial distances into dacc (N x C, zeroed) and
+    // count themselves in tile_done (one word per query tile, zeroed); the
+    // last contribution takes the arg-min
+    int nsplit = 1;
+    int32_t *dacc = nullptr;
+    unsigned *tile_done = nullptr;
 };
 
 // ------------------------------------------------------------ PTX wrappers
@@ -404,6 +411,11 @@ __global__ void __launch_bounds__(num_threads(EWG, QIN), 1)
     const int64_t num_m_tiles = (p.N + BM - 1) / BM;
     const int num_n_tiles = (p.Dk + BN - 1) / BN;
     constexpr int KELEMS = ENC == HDC_ENC_BF16 ? BKB / 2 : BKB;
+    // work units: (query tile, range of its dim tiles); one range per tile
+    // unless the tile's dim tiles are split over several CTAs (nsplit)
+    const int NS = (CLASSIFY && !QIN) ? p.nsplit : 1;
+    const int ntps = (num_n_tiles + NS - 1) / NS;   // dim tiles per range
+    const int64_t num_units = num_m_tiles * NS;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
@@ -454,8 +466,10 @@ __global__ void __launch_bounds__(num_threads(EWG, QIN), 1)
             uint32_t c_issued = 0, c_par = 0;
             bool ab = false;
             int64_t it = 0;
-            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++)
-                for (int nt = 0; nt < num_n_tiles && !ab; nt++) {
+            for (int64_t u = blockIdx.x; u < num_units && !ab; u += gridDim.x, it++) {
+                const int64_t mt = u / NS;
+                const int nt0 = (int)(u % NS) * ntps, nt1 = min(num_n_tiles, nt0 + ntps);
+                for (int nt = nt0; nt < nt1 && !ab; nt++) {
                     if (QIN && nt == 0) {  // the tile's staged query rows have been written
                         const bool okq = it == 0 ? mbar_wait(a0_ready, 0, abort_flag)
                                                  : mbar_wait(a_ready((int)(it & 1)), (uint32_t)(((it - 1) >> 1) & 1),
@@ -481,6 +495,7 @@ __global__ void __launch_bounds__(num_threads(EWG, QIN), 1)
                         if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
                 }
+            }
             if (ab) {  // let our own copies land before the CTA exits
                 for (int s = 0; s < STAGES; s++)
                     if (issued[s]) {
@@ -503,8 +518,9 @@ __global__ void __launch_bounds__(num_threads(EWG, QIN), 1)
             uint32_t phase = 0, aphase = 0;
             bool ab = false;
             int64_t it = 0;
-            for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++)
-                for (int nt = 0; nt < num_n_tiles && !ab; nt++) {
+            for (int64_t u = blockIdx.x; u < num_units && !ab; u += gridDim.x, it++) {
+                const int nt0 = (int)(u % NS) * ntps, nt1 = min(num_n_tiles, nt0 + ntps);
+                for (int nt = nt0; nt < nt1 && !ab; nt++) {
                     if (!mbar_wait_fast(tempty(acc), aphase ^ 1, abort_flag)) { ab = true; break; }
                     tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)(acc * BN);
@@ -528,6 +544,7 @@ __global__ void __launch_bounds__(num_threads(EWG, QIN), 1)
                     mma_commit(tfull(acc));
                     if (++acc == 2) { acc = 0; aphase ^= 1; }
                 }
+            }
             // all MMAs of this thread complete before TMEM is released
             mma_commit(done_bar);
             const unsigned long long t0 = gtimer();
@@ -569,14 +586,16 @@ __global__ void __launch_bounds__(num_threads(EWG, QIN), 1)
         uint32_t aphase = 0, cph = 0, wph = 0;
         bool ab = false;
         int64_t it = 0;
-        for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++) {
+        for (int64_t u = blockIdx.x; u < num_units && !ab; u += gridDim.x, it++) {
+            const int64_t mt = u / NS;
+            const int nt0 = (int)(u % NS) * ntps, nt1 = min(num_n_tiles, nt0 + ntps);
             const int64_t row = mt * BM + r;
             const bool valid = row < p.N;
             float qsum = 0.f;   // squared norm of the BF16 projections of this row
             int dist[CLASSIFY ? CMAX : 1];
 #pragma unroll
             for (int c = 0; c < (CLASSIFY ? CMAX : 1); c++) dist[c] = 0;
-            for (int nt = 0; nt < num_n_tiles; nt++) {
+            for (int nt = nt0; nt < nt1; nt++) {
                 // warp-uniform outcome: the TMEM loads below are .sync.aligned
                 const bool ok = mbar_wait(tfull(acc), aphase, abort_flag);
                 if (!__all_sync(0xffffffffu, ok)) { ab = true; break; }
@@ -695,7 +714,36 @@ __global__ void __launch_bounds__(num_threads(EWG, QIN), 1)
                     }
                 }
             }
-            if (CLASSIFY && !ab) {  // arg-min over this warpgroup's classes, lowest index on ties
+            if (CLASSIFY && !ab && NS > 1) {
+                // this range's partial distances go into the tile's totals;
+                // the warp whose contribution completes them (all NS ranges x
+                // 4 * EWG warps) takes the arg-min of the whole tile
+                if (valid) {
+#pragma unroll
+                    for (int c = 0; c < CMAX; c++)
+                        if (c0 + c < c1) atomicAdd(p.dacc + row * p.C + c0 + c, dist[c]);
+                }
+                __threadfence();
+                __syncwarp();
+                unsigned prev = 0;
+                if (lane == 0) prev = atomicAdd(p.tile_done + mt, 1u);
+                prev = __shfl_sync(0xffffffffu, prev, 0);
+                if (prev == (unsigned)(NS * 4 * EWG - 1)) {
+                    __threadfence();
+                    for (int rr = lane; rr < BM; rr += 32) {
+                        const int64_t rw = mt * BM + rr;
+                        if (rw >= p.N) break;
+                        const volatile int32_t *dr = p.dacc + rw * p.C;
+                        int best = 0, bv = 0x7fffffff;
+                        for (int c = 0; c < p.C; c++) {   // ascending: ties keep the lowest class
+                            const int v = dr[c];
+                            if (p.dists) p.dists[rw * p.C + c] = v;
+                            if (v < bv) { bv = v; best = c; }
+                        }
+                        p.labels[rw] = best;
+                    }
+                }
+            } else if (CLASSIFY && !ab) {  // arg-min over this warpgroup's classes, lowest index on ties
                 int best = c0, bv = 0x7fffffff;
 #pragma unroll
                 for (int c = 0; c < CMAX; c++)
