@@ -63,10 +63,10 @@ constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 // (quant_tile's RQ) set how fast a tile's FP32 rows arrive: four beside one
 // epilogue warpgroup (eight warps, two per scheduler, up to 255 registers),
 // two beside two (twelve warps, three per scheduler: at most 168 registers).
-__host__ __device__ constexpr int qwarps(int) { return 2; }
+constexpr int QWARPS = 2;
 __host__ __device__ constexpr int num_threads(int ewg, bool qin = false)
 {
-    return (4 * ewg + 2 + (qin ? qwarps(ewg) : 0)) * 32;
+    return (4 * ewg + 2 + (qin ? QWARPS : 0)) * 32;
 }
 // elements of a staged query row the quantisers hold in registers (8 x 128)
 constexpr int QIN_MAX_LD = 1024;
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(num_threads(EWG, QIN), 1)
     auto a_ready = [&](int b) { return su32(bars + QB + 1 + b); };
     auto a_free = [&](int b) { return su32(bars + QB + 3 + b); };
     constexpr int QW0 = 4 * EWG + 2;                   // first quantiser warp
-    constexpr int QW = qwarps(EWG);                    // quantiser warps
+    constexpr int QW = QWARPS;                         // quantiser warps
     constexpr int RQ = EWG == 1 ? 4 : 2;               // rows in flight per quantising warp
     constexpr int QES = ENC == HDC_ENC_BF16 ? 2 : 1;
     static_assert(!QIN || (CLASSIFY && EWG <= 2), "in-kernel quantisation: classify with one or two warpgroups");
