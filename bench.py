@@ -195,8 +195,8 @@ class ClockSampler:
 # its own query tiles, so the FP32 rows are its input): bytes per query,
 # valid only while the kernel sources hash to the value they had when it was
 # taken.
-PROFILED_TRAFFIC = {"sources_sha1_16": "7989892ed9c97e77", "enc": "fp8", "stride": 2,
-                    "dram_bytes_per_query": (826735104 + 65808128) / 262144}
+PROFILED_TRAFFIC = {"sources_sha1_16": "215e9e0c41ddc71a", "enc": "fp8", "stride": 2,
+                    "dram_bytes_per_query": (826851584 + 65014016) / 262144}
 
 
 def tc_sources_sha():
