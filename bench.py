@@ -195,7 +195,7 @@ class ClockSampler:
 # its own query tiles, so the FP32 rows are its input): bytes per query,
 # valid only while the kernel sources hash to the value they had when it was
 # taken.
-PROFILED_TRAFFIC = {"sources_sha1_16": "215e9e0c41ddc71a", "enc": "fp8", "stride": 2,
+PROFILED_TRAFFIC = {"sources_sha1_16": "88333d5419e1a0c4", "enc": "fp8", "stride": 2,
                     "dram_bytes_per_query": (826851584 + 65014016) / 262144}
 
 

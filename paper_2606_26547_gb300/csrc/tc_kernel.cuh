@@ -12,7 +12,8 @@
 // The per-row power-of-two scales of FP8 are positive, so they do not change
 // any bit; they are applied only to the optional projection output.
 //
-// Structure (one CTA per SM, persistent over 128-query tiles):
+// Structure (one CTA per SM, persistent over 128-query tiles, or over
+// (tile, dim-tile range) units for batches of fewer tiles than SMs):
 //   warp 4 lane 0  TMA producer: A tile (128 queries x 128 B of K) and B tile
 //                  (256 dims x 128 B of K) per stage into a 4-stage ring,
 //                  128-byte swizzle, completion on an mbarrier;
@@ -359,6 +360,11 @@ __device__ __forceinline__ void fence_to_async_global() { asm volatile("fence.pr
 // 0: a0_ready, written by the epilogue and quantiser warps together) and
 // the MMA issuer frees it (a_free) once the last stage that reads it has
 // landed.
+// Work units: every role walks the same units, a query tile and a range of
+// its dim tiles (the whole tile unless p.nsplit > 1, a classify of fewer
+// tiles than SMs).  A split range's epilogue warps add their partial
+// distances into p.dacc and count themselves in p.tile_done; the warp whose
+// count completes the tile reads the totals and takes the arg-min.
 // EWG = 2 or 4 (classify only): the epilogue warpgroups read the same TMEM
 // lanes, warpgroup g the columns of words [g*8/EWG, (g+1)*8/EWG); every
 // thread publishes its words to shared memory and, after an mbarrier that
