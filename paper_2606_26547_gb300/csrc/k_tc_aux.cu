@@ -67,17 +67,22 @@ cudaError_t launch_hamming_packed(const uint32_t *Q, int64_t N, const uint32_t *
         sms = 152;
     const int64_t tiles = (N + tc::BM - 1) / tc::BM;
     // two CTAs per SM when both fit in shared memory (TMEM: 2 x 256 columns),
-    // with two class-tile buffers if they fit, else one
+    // with two class-tile buffers if they fit, else one.  Up to 128 padded
+    // classes the query tile lives in tensor memory (no query buffers in
+    // shared memory: two CTAs with two class-tile buffers always fit).
     auto fits2 = [](size_t bytes) { return 2 * (bytes + 1024) <= 228 * 1024; };
-    const size_t smem2 = tc::hp_smem_bytes(p.Cp, W, 2), smem1 = tc::hp_smem_bytes(p.Cp, W, 1);
+    const bool ta = p.Cp <= tc::HP_TA_CMAX;
+    const size_t smem2 = tc::hp_smem_bytes(p.Cp, W, 2, ta), smem1 = tc::hp_smem_bytes(p.Cp, W, 1);
     const bool two = fits2(smem2) || fits2(smem1);
     const size_t smem = fits2(smem2) ? smem2 : fits2(smem1) ? smem1 : smem2;
-    auto k = cls_sign ? (fits2(smem2) ? tc::tc_hamming_packed_kernel<2, 2, true>
-                                      : fits2(smem1) ? tc::tc_hamming_packed_kernel<2, 1, true>
-                                                     : tc::tc_hamming_packed_kernel<1, 2, true>)
-                      : (fits2(smem2) ? tc::tc_hamming_packed_kernel<2, 2, false>
-                                      : fits2(smem1) ? tc::tc_hamming_packed_kernel<2, 1, false>
-                                                     : tc::tc_hamming_packed_kernel<1, 2, false>);
+    auto k = cls_sign ? (ta ? tc::tc_hamming_packed_kernel<2, 2, true, true>
+                            : fits2(smem2) ? tc::tc_hamming_packed_kernel<2, 2, true>
+                                           : fits2(smem1) ? tc::tc_hamming_packed_kernel<2, 1, true>
+                                                          : tc::tc_hamming_packed_kernel<1, 2, true>)
+                      : (ta ? tc::tc_hamming_packed_kernel<2, 2, false, true>
+                            : fits2(smem2) ? tc::tc_hamming_packed_kernel<2, 2, false>
+                                           : fits2(smem1) ? tc::tc_hamming_packed_kernel<2, 1, false>
+                                                          : tc::tc_hamming_packed_kernel<1, 2, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t slots = (int64_t)sms * (two ? 2 : 1);

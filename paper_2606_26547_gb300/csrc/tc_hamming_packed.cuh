@@ -21,6 +21,13 @@
 // warpgroups, alternate 32-class chunks, merged by (distance, class));
 // warp 8 issues the MMAs.  Every wait is bounded as in the encoder.
 //
+// TA (Cp <= 128): the query tile goes to tensor memory instead: each
+// expanding thread writes its row's E4M3 bytes into its own TMEM lane
+// (tcgen05.st, four bytes per column, dims in ascending byte order) and the
+// MMAs take A from there (K-major, row i in lane i), so that shared memory
+// carries only the class operand.  TMEM: D2 in columns 0..127, the two
+// query buffers of 64 columns (256 dims) each in columns 128..255.
+//
 // PRE: the class hypervectors come already expanded (E4M3 +-1 bytes, Cp rows
 // of ldcs bytes, from launch_class_sign into the caller's workspace), and
 // thread 0 streams each tile's two class atoms by TMA on a barrier of their
@@ -41,13 +48,18 @@ constexpr int HP_MAX_W = 4096;                 // words of a packed row (D <= 13
 // full[2], empty[2], d2full, d2empty, merge_full, merge_empty, done, cfull[2]
 constexpr int HP_NUM_BARS = 11;
 
-// bbuf: class-tile buffers (2, or 1 so that two CTAs fit per SM)
-__host__ __device__ constexpr size_t hp_smem_bytes(int Cp, int W, int bbuf = 2)
+constexpr int HP_TA_CMAX = 128;                // TA: largest padded class count
+constexpr int HP_TA_COL = 128;                 // TA: first TMEM column of the query buffers
+
+// bbuf: class-tile buffers (2, or 1 so that two CTAs fit per SM); ta: the
+// query tile in tensor memory (no shared-memory query buffers)
+__host__ __device__ constexpr size_t hp_smem_bytes(int Cp, int W, int bbuf = 2, bool ta = false)
 {
-    return 1024 + (size_t)2 * HP_A_BYTES + (size_t)bbuf * 2 * Cp * 128 + (size_t)(W + 2) * 4 + HP_NUM_BARS * 8 + 16 +
-           (size_t)2 * BM * 4;
+    return 1024 + (ta ? (size_t)0 : (size_t)2 * HP_A_BYTES) + (size_t)bbuf * 2 * Cp * 128 + (size_t)(W + 2) * 4 +
+           HP_NUM_BARS * 8 + 16 + (size_t)2 * BM * 4;
 }
 static_assert(hp_smem_bytes(HP_CMAX, HP_MAX_W) <= 232448, "shared memory of the packed tensor-core Hamming kernel");
+static_assert(2 * (hp_smem_bytes(HP_TA_CMAX, HP_MAX_W, 2, true) + 1024) <= 228 * 1024, "two TA CTAs per SM");
 
 struct HPParams {
     const uint32_t *Q;       // N x W packed rows
@@ -110,17 +122,57 @@ __device__ __forceinline__ void expand_row(uint8_t *atom, int r, const uint4 w, 
     }
 }
 
+// Eight 32-bit TMEM columns of this thread's lane (a warp writes its own
+// 32-lane quarter), and the wait for this thread's stores to land.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// 128 dims (four words) of one row into 32 TMEM columns of its lane: dims
+// 4j..4j+3 of the four words in column taddr + j, lowest dim in the lowest
+// byte.  The mask words are the same for the whole warp (one 128-dim half).
+__device__ __forceinline__ void expand_row_tmem(uint32_t taddr, const uint4 w, const uint4 m)
+{
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w}, ms[4] = {m.x, m.y, m.z, m.w};
+    const bool all = (m.x & m.y & m.z & m.w) == 0xffffffffu;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        uint32_t b[8];
+        expand_word(ws[i], b);
+        if (!all) {
+            uint32_t mb[8];
+            expand_mask(ms[i], mb);
+#pragma unroll
+            for (int k = 0; k < 8; k++) b[k] &= mb[k];
+        }
+        tmem_st8(taddr + 8 * i, b);
+    }
+}
+
+// D += A . B^T with A (128 rows x 32 E4M3 bytes) in tensor memory at column a.
+__device__ __forceinline__ void mma_ts_fp8(uint32_t d, uint32_t a, uint64_t b, uint32_t id, uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "r"(a), "l"(b), "r"(id), "r"(accum));
+}
+
 // MINB = 2: two CTAs per SM, registers capped to fit.  BBUF = 1: one
 // class-tile buffer (so two CTAs fit with larger class tiles): the class rows
 // of tile t are written once the MMAs of tile t - 1 have read them.
-template <int MINB, int BBUF, bool PRE>
+template <int MINB, int BBUF, bool PRE, bool TA = false>
 __global__ void __launch_bounds__(HP_THREADS, MINB)
     tc_hamming_packed_kernel(const HPParams p, const __grid_constant__ CUtensorMap tmC)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *sA = smem;                                          // 2 buffers x HP_A_BYTES
-    uint8_t *sB = sA + 2 * HP_A_BYTES;                           // 2 buffers x two atoms of Cp x 128 bytes
+    uint8_t *sA = smem;                                          // 2 buffers x HP_A_BYTES (none with TA)
+    uint8_t *sB = sA + (TA ? 0 : 2 * HP_A_BYTES);                // 2 buffers x two atoms of Cp x 128 bytes
     const int b_bytes = 2 * p.Cp * 128;
     uint32_t *smask = reinterpret_cast<uint32_t *>(sB + BBUF * b_bytes);   // W mask words
     uint64_t *bars = reinterpret_cast<uint64_t *>(smask + ((p.W + 1) & ~1));
@@ -203,11 +255,16 @@ __global__ void __launch_bounds__(HP_THREADS, MINB)
                     const uint64_t da = sdesc(su32(sA + buf * HP_A_BYTES));
                     const uint64_t db = sdesc(su32(sB + (BBUF == 2 ? buf : 0) * b_bytes));
                     const uint32_t atom_b = (uint32_t)(p.Cp * 128) >> 4;   // second K atom of the class tile
+                    const uint32_t ta = tmem + HP_TA_COL + (uint32_t)(buf * 64);   // TA: this buffer's columns
 #pragma unroll
                     for (int k = 0; k < 8; k++) {   // two atoms of four 32-byte K steps
-                        const uint64_t oa = (uint64_t)((k >> 2) * ((BM * 128) >> 4) + 2 * (k & 3));
                         const uint64_t ob = (uint64_t)((k >> 2) * atom_b + 2 * (k & 3));
-                        mma<HDC_ENC_FP8_E4M3>(tmem, da + oa, db + ob, id, (t | k) != 0);
+                        if (TA) {
+                            mma_ts_fp8(tmem, ta + (uint32_t)(8 * k), db + ob, id, (t | k) != 0);
+                        } else {
+                            const uint64_t oa = (uint64_t)((k >> 2) * ((BM * 128) >> 4) + 2 * (k & 3));
+                            mma<HDC_ENC_FP8_E4M3>(tmem, da + oa, db + ob, id, (t | k) != 0);
+                        }
                     }
                     mma_commit(empty(buf));
                     if (++buf == 2) { buf = 0; ph ^= 1; }
@@ -266,6 +323,7 @@ __global__ void __launch_bounds__(HP_THREADS, MINB)
                 }
                 const bool oke = mbar_wait(empty(buf), ph ^ 1, abort_flag);   // the MMAs of this buffer's last use
                 if (!__all_sync(0xffffffffu, oke)) { ab = true; break; }
+                if (TA) tc_fence_after();   // this thread's TMEM stores after those MMAs
                 if (BBUF == 1 && gt > 0) {   // the single class tile: the previous tile's MMAs have read it
                     const bool okp = mbar_wait(empty(buf ^ 1), buf ? ph : ph ^ 1, abort_flag);
                     if (!__all_sync(0xffffffffu, okp)) { ab = true; break; }
@@ -282,7 +340,12 @@ __global__ void __launch_bounds__(HP_THREADS, MINB)
                     c_ph[cb] ^= 1;
                 }
                 const uint4 mq = w0 < p.W ? *reinterpret_cast<const uint4 *>(smask + w0) : make_uint4(0, 0, 0, 0);
-                expand_row(sA + buf * HP_A_BYTES + half * (BM * 128), r, qw, mq);
+                if (TA) {   // converged for the warp-wide TMEM stores (thread 0 may have issued the class copy)
+                    __syncwarp();
+                    expand_row_tmem(tmem + lane_base + HP_TA_COL + (uint32_t)(buf * 64 + half * 32), qw, mq);
+                } else {
+                    expand_row(sA + buf * HP_A_BYTES + half * (BM * 128), r, qw, mq);
+                }
                 // class rows: items (class c, half h) i = tid, tid + HP_EXP (2 * Cp <= 512)
 #pragma unroll
                 for (int ii = 0; ii < (PRE ? 0 : 2); ii++) {
@@ -294,6 +357,10 @@ __global__ void __launch_bounds__(HP_THREADS, MINB)
                                                                : make_uint4(0, 0, 0, 0);
                         expand_row(bt + h * (p.Cp * 128), c, ii ? cw1 : cw0, mc);
                     }
+                }
+                if (TA) {   // the query columns landed before the MMAs read them
+                    tmem_st_wait();
+                    tc_fence_before();
                 }
                 fence_async_smem();
                 mbar_arrive(full(buf));
