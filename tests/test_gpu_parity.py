@@ -218,6 +218,25 @@ def test_hamming_argmin_tensor_core_many_tiles(hdc):
     assert np.array_equal(labels.cpu().numpy(), orc.argmin(od))
 
 
+@pytest.mark.parametrize("N,C,perf", [(41000, 100, None), (40077, 128, (0.1, 0.9, 3))])
+def test_hamming_argmin_tensor_core_more_tiles_than_ctas(hdc, N, C, perf):
+    """More 128-row tiles than the two CTAs per SM hold, so CTAs take several
+    and the query words stream through the copy ring across m-tiles; a ragged
+    last tile, 100 and 128 classes, with and without perforation."""
+    rng = np.random.default_rng(N + C)
+    D = 1024
+    c = rng.integers(0, 2, (C, D)).astype(np.uint8)
+    c[C - 1] = c[3]
+    y = rng.integers(0, C, N)
+    q = c[y] ^ (rng.random((N, D)) < 0.4).astype(np.uint8)
+    cfg = hdc.ApproxConfig(perf_start=perf[0], perf_end=perf[1], perf_stride=perf[2]) if perf else None
+    labels, dd = hdc.hamming_argmin(T(pack(q).view(np.int32)), T(pack(c).view(np.int32)), D, cfg, dists=True)
+    dims = orc.kept_dims(D, *perf) if perf else orc.kept_dims(D)
+    od = orc.hamming(orc.gather_cols(q, dims), orc.gather_cols(c, dims))
+    assert np.array_equal(dd.cpu().numpy().astype(np.int64), od)
+    assert np.array_equal(labels.cpu().numpy(), orc.argmin(od))
+
+
 @pytest.mark.parametrize("N,D,C", [(40000, 1024, 120), (39000, 1000, 33)])
 def test_train_tensor_route_many_tiles_bit_exact(hdc, N, D, C):
     """Retraining whose predictions run on the tensor-core route with the
