@@ -5,13 +5,18 @@
 // For each 256-dim tile t of a 128-query block:
 //   S = Xq . Bq^T          (MMA1: M 128, N 256, K = F, BF16 or E4M3) into one
 //                          of two 256-column TMEM accumulators
-//   q = bf16(S * sb_k)     (epilogue: four warpgroups, 64 columns each, into a
-//                          128 x 256 BF16 operand; sum of q^2 kept per row;
-//                          the tile's 256 base-row scales arrive in shared
-//                          memory with its class values, zero past D')
-//   P_t = q . Cv_t^T       (MMA2: M 128, N 16, K 256, BF16) written into the
-//                          first 16 columns of tile t's own accumulator, whose
-//                          S values the epilogue has already read
+//   q = bf16(S * sb_k)     (epilogue: four warpgroups, 64 columns each; sum of
+//                          q^2 kept per row; the tile's 256 base-row scales
+//                          arrive in shared memory with its class values, zero
+//                          past D').  Each thread writes the 32 BF16 of every
+//                          32-column half it has read back into the first 16
+//                          of those columns (two per column, lower dim in the
+//                          low half), so the operand never touches shared
+//                          memory
+//   P_t = q . Cv_t^T       (MMA2: M 128, N 16, K 256, BF16, A from tensor
+//                          memory) written into columns 16..31 of tile t's own
+//                          accumulator, S values the epilogue has read and no
+//                          BF16 pair occupies
 //   dot += P_t             (warpgroup 0, FP32 registers)
 // After the last tile: score_c = dot_c / (||q|| ||c||) in FP64 (0 for a zero
 // norm), arg-max with the lowest class on ties.  The projections never reach
@@ -28,22 +33,50 @@ namespace hdc {
 namespace tc {
 
 constexpr int F16_EWG = 4;                             // epilogue warpgroups, 64 columns of a tile each
-constexpr int F16_STAGES = 3;
+// encode stages: three for E4M3, four for BF16 (the shared memory the value
+// tile no longer takes; FP8 measured 1 % slower with four, BF16 5 % faster)
+template <int ENC>
+__host__ __device__ constexpr int f16_stages() { return ENC == HDC_ENC_BF16 ? 4 : 3; }
 constexpr int F16_CP = 16;                             // class rows of MMA2
 constexpr int F16_THREADS = (4 * F16_EWG + 4) * 32;
-constexpr int F16_A2_BYTES = 4 * A2_ATOM;              // 128 rows x 256 BF16: four 128-byte K atoms
 constexpr int F16_B2_BYTES = 4 * F16_CP * 128;         // 16 class rows x 256 BF16: four atoms
 constexpr int F16_SB_BYTES = BN * 4;                   // the tile's base-row scales (FP8)
-// full[S], empty[S], tfull[2], tempty[2], d2full[2], a2full, a2empty,
-// b2full, b2empty, qfull[2], done, done2
-constexpr int F16_NUM_BARS = 2 * F16_STAGES + 14;
+// full[S], empty[S], tfull[2], tempty[2], d2full[2], a2full[2], b2full,
+// b2empty, qfull[2], done, done2.  a2full is per accumulator: epilogue
+// warps that run ahead to the next tile arrive on the other barrier, and
+// tile t + 2's arrivals wait (through tempty) for MMA2 of tile t.
+template <int ENC>
+__host__ __device__ constexpr int f16_num_bars() { return 2 * f16_stages<ENC>() + 14; }
 
+template <int ENC>
 __host__ __device__ constexpr size_t f16_smem_bytes()
 {
-    return 1024 + (size_t)F16_STAGES * STAGE_BYTES + F16_A2_BYTES + F16_B2_BYTES + F16_SB_BYTES + F16_NUM_BARS * 8 + 16 +
-           (size_t)2 * F16_EWG * BM * 4;
+    return 1024 + (size_t)f16_stages<ENC>() * STAGE_BYTES + F16_B2_BYTES + F16_SB_BYTES + f16_num_bars<ENC>() * 8 +
+           16 + (size_t)2 * F16_EWG * BM * 4;
 }
-static_assert(f16_smem_bytes() <= 232448, "shared memory of the 16-class fused float-query kernel");
+
+// Sixteen 32-bit TMEM columns of this thread's lane (the warp's own 32-lane
+// quarter), and the wait for this thread's stores to land.
+__device__ __forceinline__ void f16_tmem_st16(uint32_t taddr, const uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+                 "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+                 "r"(r[15])
+                 : "memory");
+}
+__device__ __forceinline__ void f16_tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// D += A . B^T, BF16, A (128 rows x 16 BF16) in tensor memory at column a.
+__device__ __forceinline__ void f16_mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t id, uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "r"(a), "l"(b), "r"(id), "r"(accum));
+}
+static_assert(f16_smem_bytes<HDC_ENC_BF16>() <= 232448 && f16_smem_bytes<HDC_ENC_FP8_E4M3>() <= 232448,
+              "shared memory of the 16-class fused float-query kernel");
 
 template <int ENC>
 __global__ void __launch_bounds__(F16_THREADS, 1)
@@ -54,21 +87,20 @@ __global__ void __launch_bounds__(F16_THREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;
-    uint8_t *sB = smem + F16_STAGES * A_BYTES;
-    uint8_t *sA2 = smem + F16_STAGES * STAGE_BYTES;
-    uint8_t *sB2 = sA2 + F16_A2_BYTES;
+    constexpr int S = f16_stages<ENC>();
+    uint8_t *sB = smem + S * A_BYTES;
+    uint8_t *sB2 = smem + S * STAGE_BYTES;
     float *s_sb = reinterpret_cast<float *>(sB2 + F16_B2_BYTES);   // BN scales of the tile (FP8)
     uint64_t *bars = reinterpret_cast<uint64_t *>(sB2 + F16_B2_BYTES + F16_SB_BYTES);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + F16_NUM_BARS);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + f16_num_bars<ENC>());
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     float *s_q = reinterpret_cast<float *>(tmem_slot + 4);   // 2 x [F16_EWG][BM] partial squared norms
-    constexpr int S = F16_STAGES;
     auto full = [&](int s) { return su32(bars + s); };
     auto empty = [&](int s) { return su32(bars + S + s); };
     auto tfull = [&](int a) { return su32(bars + 2 * S + a); };
     auto tempty = [&](int a) { return su32(bars + 2 * S + 2 + a); };
     auto d2full = [&](int a) { return su32(bars + 2 * S + 4 + a); };
-    const uint32_t a2full = su32(bars + 2 * S + 6), a2empty = su32(bars + 2 * S + 7);
+    auto a2full = [&](int a) { return su32(bars + 2 * S + 6 + a); };
     const uint32_t b2full = su32(bars + 2 * S + 8), b2empty = su32(bars + 2 * S + 9);
     auto qfull = [&](int b) { return su32(bars + 2 * S + 10 + b); };
     const uint32_t done_bar = su32(bars + 2 * S + 12), done2_bar = su32(bars + 2 * S + 13);
@@ -89,8 +121,7 @@ __global__ void __launch_bounds__(F16_THREADS, 1)
             mbar_init(d2full(a), 1);
             mbar_init(qfull(a), BM * F16_EWG);
         }
-        mbar_init(a2full, BM * F16_EWG);
-        mbar_init(a2empty, 1);
+        for (int a = 0; a < 2; a++) mbar_init(a2full(a), BM * F16_EWG);
         mbar_init(b2full, 1);
         mbar_init(b2empty, 1);
         mbar_init(done_bar, 1);
@@ -196,29 +227,29 @@ __global__ void __launch_bounds__(F16_THREADS, 1)
     } else if (warp == ISSUER2) {
         if (lane == 0) {  // ------------------------------ MMA2 issuer (the tile's cosine partials)
             const uint32_t id2 = idesc_n<HDC_ENC_BF16>(F16_CP);
-            uint32_t a2ph = 0, b2ph = 0;
+            uint32_t a2ph = 0, b2ph = 0;   // a2ph: the parity of both accumulators' a2full, flipped per pair
             int acc = 0;
             bool ab = false;
             for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x)
                 for (int t = 0; t < p.nt; t++) {
-                    if (!mbar_wait(a2full, a2ph, abort_flag)) { ab = true; break; }
+                    if (!mbar_wait(a2full(acc), a2ph, abort_flag)) { ab = true; break; }
                     if (!mbar_wait(b2full, b2ph, abort_flag)) { ab = true; break; }
                     tc_fence_after();
-                    const uint32_t a0 = su32(sA2), b0 = su32(sB2);
-                    // into columns 0..15 of tile t's accumulator (its S values are read)
-                    const uint32_t d2 = tmem + (uint32_t)(acc * BN);
+                    const uint32_t b0 = su32(sB2);
+                    // into columns 16..31 of tile t's accumulator; K step k (dims
+                    // 16k..16k+15): warpgroup k / 4's columns, half (k % 4) / 2,
+                    // eight columns in
+                    const uint32_t tacc = tmem + (uint32_t)(acc * BN), d2 = tacc + 16;
 #pragma unroll
                     for (int k = 0; k < 16; k++) {   // four atoms of four 16-element K steps
-                        const uint32_t off_a = (uint32_t)((k >> 2) * A2_ATOM) + 32u * (k & 3);
+                        const uint32_t col = (uint32_t)((k >> 2) * 64 + ((k & 3) >> 1) * 32 + (k & 1) * 8);
                         const uint32_t off_b = (uint32_t)((k >> 2) * F16_CP * 128) + 32u * (k & 3);
-                        mma<HDC_ENC_BF16>(d2, sdesc(a0 + off_a), sdesc(b0 + off_b), id2, k == 0 ? 0u : 1u);
+                        f16_mma_ts(d2, tacc + col, sdesc(b0 + off_b), id2, k == 0 ? 0u : 1u);
                     }
-                    mma_commit(a2empty);
                     mma_commit(b2empty);
                     mma_commit(d2full(acc));
-                    a2ph ^= 1;
                     b2ph ^= 1;
-                    acc ^= 1;
+                    if (++acc == 2) { acc = 0; a2ph ^= 1; }
                 }
             mma_commit(done2_bar);
             const unsigned long long t0 = gtimer();
@@ -228,9 +259,8 @@ __global__ void __launch_bounds__(F16_THREADS, 1)
         const int q = warp & 3, g = warp >> 2;
         const int r = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        uint8_t *a2row = sA2 + g * A2_ATOM + (r >> 3) * 1024 + (r & 7) * 128;   // atom g: this warpgroup's 64 dims
         int acc = 0, qb = 0;
-        uint32_t aphase = 0, a2ph = 0, qph = 0, b2ph = 0;
+        uint32_t aphase = 0, qph = 0, b2ph = 0;
         bool ab = false;
         const bool has_sb = p.sb != nullptr;
         for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
@@ -249,11 +279,11 @@ __global__ void __launch_bounds__(F16_THREADS, 1)
                     if (!__all_sync(0xffffffffu, oks)) { ab = true; break; }
                 }
                 b2ph ^= 1;
-                bool okh = true;
 #pragma unroll 1
                 for (int h = 0; h < 2; h++) {
+                    const uint32_t col = tmem + lane_base + (uint32_t)(acc * BN + g * 64 + 32 * h);
                     uint32_t v[32];
-                    tmem_ld32(tmem + lane_base + (uint32_t)(acc * BN + g * 64 + 32 * h), v);
+                    tmem_ld32(col, v);
                     // BF16 of s * sb; past D' the projections are zero (zero base rows)
                     const float4 *s4 = reinterpret_cast<const float4 *>(s_sb + g * 64 + 32 * h);
                     uint32_t w[16];
@@ -277,30 +307,18 @@ __global__ void __launch_bounds__(F16_THREADS, 1)
                         w[2 * i4 + 1] = u23;
                     }
                     qsum += qa + qc;
-                    if (h == 0) {   // MMA2 of the previous tile has read the value tile
-                        const bool oka = mbar_wait(a2empty, a2ph ^ 1, abort_flag);
-                        if (!__all_sync(0xffffffffu, oka)) { okh = false; }
-                    }
-                    if (!okh) break;
-#pragma unroll
-                    for (int i = 0; i < 4; i++) {   // 8 BF16 per 16-byte chunk, 128-byte swizzle
-                        const int ch = 4 * h + i;
-                        *reinterpret_cast<uint4 *>(a2row + ((ch ^ (r & 7)) * 16)) =
-                            make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
-                    }
+                    f16_tmem_st16(col, w);   // the half's 32 BF16 into its first 16 columns (read above)
                 }
-                if (!okh) { ab = true; break; }
-                fence_async_smem();
+                f16_tmem_st_wait();
                 tc_fence_before();
-                mbar_arrive(a2full);
-                a2ph ^= 1;
+                mbar_arrive(a2full(acc));
                 if (g == 0) {
                     // this tile's cosine partials, in columns 0..15 of its accumulator
                     const bool okd = mbar_wait(d2full(acc), aphase, abort_flag);
                     if (!__all_sync(0xffffffffu, okd)) { ab = true; break; }
                     tc_fence_after();
                     uint32_t v[32];
-                    tmem_ld32(tmem + lane_base + (uint32_t)(acc * BN), v);
+                    tmem_ld32(tmem + lane_base + (uint32_t)(acc * BN + 16), v);
 #pragma unroll
                     for (int c = 0; c < F16_CP; c++) dot[c] += __uint_as_float(v[c]);
                     tc_fence_before();
@@ -351,7 +369,7 @@ static cudaError_t launch_fcos16_enc(const CUtensorMap &ma, const CUtensorMap &m
                                      const CUtensorMap &ms, const FCParams &p, unsigned grid, cudaStream_t st)
 {
     auto k = tc_fcos16_kernel<ENC>;
-    constexpr size_t smem = f16_smem_bytes();
+    constexpr size_t smem = f16_smem_bytes<ENC>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, F16_THREADS, smem, st>>>(ma, mb, mv, ms, p);
