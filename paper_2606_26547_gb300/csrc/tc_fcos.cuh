@@ -4,20 +4,24 @@
 //
 // For each 192-dim tile t of a 128-query block:
 //   S = Xq . Bq^T                (MMA1: M 128, N 192, K = F, BF16 or E4M3)
-//   q = bf16(S * sb_k)           (the epilogue: one 64-column K atom per
-//                                 warpgroup into a 128 x 192 BF16 operand;
-//                                 sum of q^2 kept per row)
-//   D2 += q . Cv^T               (MMA2: M 128, N = Cp, K = 192, BF16)
+//   q = bf16(S * sb_k)           (the epilogue: 64 columns per warpgroup;
+//                                 sum of q^2 kept per row).  Each thread
+//                                 writes the 32 BF16 of every 32-column
+//                                 half it has read back into the first 16
+//                                 of those columns (two per column, lower
+//                                 dim in the low half)
+//   D2 += q . Cv^T               (MMA2: M 128, N = Cp, K = 192, BF16, A from
+//                                 tensor memory; its commit releases the
+//                                 accumulator to MMA1)
 // with Cv the model's BF16 class values (Cp x ldS; TMA zero fill past ldS).
 // After the last tile: score_c = D2_c / (||q|| ||c||) in FP64 (0 for a zero
 // norm), arg-max with the lowest class on ties.  The projections never
 // reach device memory.
 //
-// Tensor memory: two 192-column encode accumulators and D2 (Cp <= 128).
-// Shared memory: three or four A/B stages (40 KB each), the 48 KB value tile
-// and one or two Cp x 384-byte class tiles: with two, the next tile's class
-// values load while the current tile's cosine MMAs run, so the L2 round trip
-// of that load is off the chain MMA2(t) -> value tile free -> epilogue(t + 1).
+// Tensor memory: two 192-column encode accumulators (each also holding its
+// tile's BF16 values) and D2 (Cp <= 128).  Shared memory: three or four A/B
+// stages (40 KB each) and one or two Cp x 384-byte class tiles: with two, the
+// next tile's class values load while the current tile's cosine MMAs run.
 // Roles as the tensor-core Hamming kernel:
 // warps 0-11 epilogue (three warpgroups), 12 stage producer, 13 MMA1 issuer,
 // 14 class-tile producer, 15 MMA2 issuer (its own commit chain: 4.65 vs
@@ -32,16 +36,18 @@ namespace tc {
 // At N = 192 a stage feeds about 0.2 us of MMA work, so the stages in
 // flight are what covers the L2 latency (36 % tensor activity measured with
 // three stages at C = 10).
-constexpr int FC_A2_BYTES = 3 * A2_ATOM;            // 128 rows x 192 BF16 in three 128-byte K atoms
 constexpr int FC_THREADS = (4 * HEWG + 4) * 32;     // + the cosine MMA issuer
 constexpr int FC_CMAX = 128;   // TMEM: 2 x 192 + 128 columns
-// full[S], empty[S], sfull[2], sempty[2], a2full, a2empty, b2full[0], b2empty[0],
-// d2full, d2empty, done, merge_full, merge_empty, qfull[2], done2, b2full[1], b2empty[1]
+// full[S], empty[S], sfull[2], sempty[2], a2full[2], b2full[0], b2empty[0],
+// d2full, d2empty, done, merge_full, merge_empty, qfull[2], done2, b2full[1], b2empty[1].
+// a2full is per accumulator: epilogue warps that run ahead to the next tile
+// arrive on the other barrier, and tile t + 2's arrivals wait (through
+// sempty and MMA1) for MMA2 of tile t.
 __host__ __device__ constexpr int fc_num_bars(int stages) { return 2 * stages + 4 + 6 + 3 + 2 + 1 + 2; }
 
 __host__ __device__ constexpr size_t fc_smem_bytes(int stages, int Cp, int b2bufs)
 {
-    return 1024 + (size_t)stages * H_STAGE_BYTES + FC_A2_BYTES + (size_t)b2bufs * 3 * Cp * 128 +
+    return 1024 + (size_t)stages * H_STAGE_BYTES + (size_t)b2bufs * 3 * Cp * 128 +
            fc_num_bars(stages) * 8 + 16 + (size_t)2 * BM * 8 * (HEWG - 1) + (size_t)2 * HEWG * BM * 4;
 }
 static_assert(fc_smem_bytes(3, FC_CMAX, 1) <= 232448, "shared memory of the fused float-query kernel");
@@ -57,6 +63,27 @@ struct FCParams {
     double *scores;          // optional N x C
 };
 
+// Sixteen 32-bit TMEM columns of this thread's lane (the warp's own 32-lane
+// quarter), and the wait for this thread's stores to land.
+__device__ __forceinline__ void fc_tmem_st16(uint32_t taddr, const uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+                 "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+                 "r"(r[15])
+                 : "memory");
+}
+__device__ __forceinline__ void fc_tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// D += A . B^T, BF16, A (128 rows x 16 BF16) in tensor memory at column a.
+__device__ __forceinline__ void fc_mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t id, uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "r"(a), "l"(b), "r"(id), "r"(accum));
+}
+
 template <int ENC, int FC_STAGES, int B2BUF>
 __global__ void __launch_bounds__(FC_THREADS, 1)
     tc_fcos_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -66,8 +93,7 @@ __global__ void __launch_bounds__(FC_THREADS, 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;
     uint8_t *sB = smem + FC_STAGES * HA_BYTES;
-    uint8_t *sA2 = smem + FC_STAGES * H_STAGE_BYTES;
-    uint8_t *sB2 = sA2 + FC_A2_BYTES;                               // B2BUF x 3 atoms x Cp rows x 128 B
+    uint8_t *sB2 = smem + FC_STAGES * H_STAGE_BYTES;                // B2BUF x 3 atoms x Cp rows x 128 B
     const int b2_bytes = 3 * p.Cp * 128;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sB2 + B2BUF * b2_bytes);
     constexpr int FC_NUM_BARS = fc_num_bars(FC_STAGES);
@@ -80,7 +106,7 @@ __global__ void __launch_bounds__(FC_THREADS, 1)
     auto empty = [&](int s) { return su32(bars + FC_STAGES + s); };
     auto sfull = [&](int a) { return su32(bars + 2 * FC_STAGES + a); };
     auto sempty = [&](int a) { return su32(bars + 2 * FC_STAGES + 2 + a); };
-    const uint32_t a2full = su32(bars + 2 * FC_STAGES + 4), a2empty = su32(bars + 2 * FC_STAGES + 5);
+    auto a2full = [&](int a) { return su32(bars + 2 * FC_STAGES + 4 + a); };
     auto b2full = [&](int b) { return su32(bars + 2 * FC_STAGES + (b ? 16 : 6)); };
     auto b2empty = [&](int b) { return su32(bars + 2 * FC_STAGES + (b ? 17 : 7)); };
     const uint32_t d2full = su32(bars + 2 * FC_STAGES + 8), d2empty = su32(bars + 2 * FC_STAGES + 9);
@@ -102,11 +128,10 @@ __global__ void __launch_bounds__(FC_THREADS, 1)
         }
         for (int a = 0; a < 2; a++) {
             mbar_init(sfull(a), 1);
-            mbar_init(sempty(a), BM * HEWG);
+            mbar_init(sempty(a), 1);   // the commit of the tile's MMA2
             mbar_init(qfull(a), BM * HEWG);
+            mbar_init(a2full(a), BM * HEWG);
         }
-        mbar_init(a2full, BM * HEWG);
-        mbar_init(a2empty, 1);
         for (int b = 0; b < 2; b++) {
             mbar_init(b2full(b), 1);
             mbar_init(b2empty(b), 1);
@@ -222,27 +247,27 @@ __global__ void __launch_bounds__(FC_THREADS, 1)
     } else if (warp == ISSUER2) {
         if (lane == 0) {  // ------------------------------ MMA2 issuer (cosine), its own commit chain
             const uint32_t id2 = idesc_n<HDC_ENC_BF16>(p.Cp);
-            uint32_t a2ph = 0, b2ph[2] = {0, 0}, d2ph = 0;
-            int bi = 0;
+            uint32_t a2ph = 0, b2ph[2] = {0, 0}, d2ph = 0;   // a2ph: both accumulators' parity, flipped per pair
+            int bi = 0, acc = 0;
             bool ab = false;
             for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
                 for (int t = 0; t < p.nt; t++) {
                     const bool first = t == 0;
                     if (first && !mbar_wait(d2empty, d2ph ^ 1, abort_flag)) { ab = true; break; }
-                    if (!mbar_wait(a2full, a2ph, abort_flag)) { ab = true; break; }
+                    if (!mbar_wait(a2full(acc), a2ph, abort_flag)) { ab = true; break; }
                     if (!mbar_wait(b2full(bi), b2ph[bi], abort_flag)) { ab = true; break; }
                     tc_fence_after();
-                    const uint32_t a0 = su32(sA2), b0 = su32(sB2 + bi * b2_bytes);
+                    const uint32_t b0 = su32(sB2 + bi * b2_bytes), tacc = tmem + (uint32_t)(acc * HBN);
 #pragma unroll
                     for (int k = 0; k < 12; k++) {   // three atoms of four 16-element K steps
-                        const uint32_t off_a = (uint32_t)((k >> 2) * A2_ATOM) + 32u * (k & 3);
+                        // dims 16k..16k+15: warpgroup k / 4's columns, half (k % 4) / 2, eight columns in
+                        const uint32_t col = (uint32_t)((k >> 2) * 64 + ((k & 3) >> 1) * 32 + (k & 1) * 8);
                         const uint32_t off_b = (uint32_t)((k >> 2) * p.Cp * 128) + 32u * (k & 3);
-                        mma<HDC_ENC_BF16>(tmem + D2_COL, sdesc(a0 + off_a), sdesc(b0 + off_b), id2,
-                                          (first && k == 0) ? 0u : 1u);
+                        fc_mma_ts(tmem + D2_COL, tacc + col, sdesc(b0 + off_b), id2, (first && k == 0) ? 0u : 1u);
                     }
-                    mma_commit(a2empty);
+                    mma_commit(sempty(acc));   // the accumulator (and its BF16 values) is free for MMA1
                     mma_commit(b2empty(bi));
-                    a2ph ^= 1;
+                    if (++acc == 2) { acc = 0; a2ph ^= 1; }
                     b2ph[bi] ^= 1;
                     if (++bi == B2BUF) bi = 0;
                 }
@@ -258,9 +283,8 @@ __global__ void __launch_bounds__(FC_THREADS, 1)
         const int q = warp & 3, g = warp >> 2;
         const int r = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        uint8_t *a2row = sA2 + g * A2_ATOM + (r >> 3) * 1024 + (r & 7) * 128;   // atom g: this warpgroup's 64 dims
         int acc = 0, qb = 0;
-        uint32_t aphase = 0, a2ph = 0, d2ph = 0, qph = 0;
+        uint32_t aphase = 0, d2ph = 0, qph = 0;
         bool ab = false;
         int64_t it = 0;
         for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++) {
@@ -272,13 +296,13 @@ __global__ void __launch_bounds__(FC_THREADS, 1)
                 if (!__all_sync(0xffffffffu, ok)) { ab = true; break; }
                 tc_fence_after();
                 // two halves of the warpgroup's 64 columns: BF16 of s * sb (zero
-                // past Dk) into chunks 4h..4h+3 of atom g; squared norm of the BF16 values
+                // past Dk) into the half's first 16 columns; squared norm of the BF16 values
                 const int col0 = t * HBN + g * 64;
-                bool okh = true;
 #pragma unroll 1
                 for (int h = 0; h < 2; h++) {
+                    const uint32_t tcol = tmem + lane_base + (uint32_t)(acc * HBN + g * 64 + 32 * h);
                     uint32_t v[32];
-                    tmem_ld32(tmem + lane_base + (uint32_t)(acc * HBN + g * 64 + 32 * h), v);
+                    tmem_ld32(tcol, v);
                     const int c0 = col0 + 32 * h;
                     float sbv[32];
                     if (c0 + 32 <= p.Dk) {
@@ -309,26 +333,12 @@ __global__ void __launch_bounds__(FC_THREADS, 1)
                         w[i] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
                     }
                     qsum += qa + qb2;
-                    if (h == 1) {   // both halves are in registers: release the accumulator
-                        tc_fence_before();
-                        mbar_arrive(sempty(acc));
-                        if (++acc == 2) { acc = 0; aphase ^= 1; }
-                    } else {        // the MMA2 of the previous tile has read the value tile
-                        const bool oka = mbar_wait(a2empty, a2ph ^ 1, abort_flag);
-                        if (!__all_sync(0xffffffffu, oka)) { okh = false; }
-                    }
-                    if (!okh) break;
-#pragma unroll
-                    for (int i = 0; i < 4; i++) {   // 8 BF16 per 16-byte chunk, 128-byte swizzle
-                        const int ch = 4 * h + i;
-                        *reinterpret_cast<uint4 *>(a2row + ((ch ^ (r & 7)) * 16)) =
-                            make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
-                    }
+                    fc_tmem_st16(tcol, w);   // the half's 32 BF16 into its first 16 columns (read above)
                 }
-                if (!okh) { ab = true; break; }
-                fence_async_smem();
-                mbar_arrive(a2full);
-                a2ph ^= 1;
+                fc_tmem_st_wait();
+                tc_fence_before();
+                mbar_arrive(a2full(acc));
+                if (++acc == 2) { acc = 0; aphase ^= 1; }
             }
             if (ab) break;
             // the row's squared norm: the warpgroups' partial sums in order g = 0, 1, 2
