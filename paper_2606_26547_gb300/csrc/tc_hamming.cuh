@@ -5,8 +5,10 @@
 // q.c is a sum of Dk products +-1 (0 for padding): an exact integer in FP32
 // for Dk < 2^24.  So after the encode GEMM of a 192-dim tile
 //   S = Xq . Bq^T          (MMA1: M 128, N 192, K = F, BF16 or E4M3)
-// the epilogue writes sign(S) as E4M3 +-1 bytes into a 128 x 192 shared
-// operand, and a second GEMM accumulates
+// the epilogue writes sign(S) as E4M3 +-1 bytes back into the accumulator:
+// the 64 bytes of a thread's 64 read columns into the first 16 of them (four
+// per column, lowest dim in the lowest byte), and a second GEMM with its A
+// operand in tensor memory accumulates
 //   D2 += sign(S) . Csign^T  (MMA2: M 128, N = Cp, K = 192, E4M3)
 // over all tiles of the query block, Csign being the class hypervectors as
 // E4M3 +-1 bytes (zero past Dk and for the pad classes up to Cp = C rounded
@@ -14,7 +16,9 @@
 // (Dk - dot) / 2 (lowest class on ties).
 //
 // Tensor memory (512 columns): two 192-column encode accumulators (the
-// encode stays double buffered) and the Cp <= 128 columns of D2.
+// encode stays double buffered; each also holds its tile's sign bytes until
+// MMA2 has read them, MMA2's commit releasing it to MMA1) and the Cp <= 128
+// columns of D2.
 //
 // Roles (16 warps): warps 0-11 epilogue (three warpgroups, 64 columns of a
 // tile each), warp 12 TMA producer of the A / B stages (4 x 40 KB), warp 13
@@ -41,19 +45,41 @@ constexpr int HEWG = 3;                       // epilogue warpgroups
 constexpr int H_THREADS = (4 * HEWG + 4) * 32;   // + the MMA2 issuer
 constexpr int H_QW = 4;                          // quantiser warps (QIN): 20 warps at up to 96 registers
 __host__ __device__ constexpr int h_threads(bool qin) { return H_THREADS + (qin ? H_QW * 32 : 0); }
-constexpr int A2_ATOM = BM * 128;             // one 128-byte K atom of the sign tile
-constexpr int A2_BYTES = 2 * A2_ATOM;         // K = 192 bytes in two atoms
 constexpr int H_CMAX = 112;
-// full[S], empty[S], sfull[2], sempty[2], a2full, a2empty, b2full, b2empty,
-// d2full, d2empty, done, merge_full, merge_empty, done2, a0_ready, a_ready[2], a_free[2]
+// full[S], empty[S], sfull[2], sempty[2], a2full[2], b2full, b2empty,
+// d2full, d2empty, done, merge_full, merge_empty, done2, a0_ready, a_ready[2], a_free[2].
+// a2full is per accumulator: epilogue warps that run ahead to the next tile
+// arrive on the other barrier, and tile t + 2's arrivals wait (through
+// sempty and MMA1) for MMA2 of tile t.
 constexpr int H_NUM_BARS = 2 * H_STAGES + 4 + 6 + 3 + 1 + 5;
 
 __host__ __device__ constexpr size_t h_smem_bytes(int Cp)
 {
-    return 1024 + (size_t)H_STAGES * H_STAGE_BYTES + A2_BYTES + (size_t)2 * Cp * 128 + H_NUM_BARS * 8 + 16 +
+    return 1024 + (size_t)H_STAGES * H_STAGE_BYTES + (size_t)2 * Cp * 128 + H_NUM_BARS * 8 + 16 +
            (size_t)2 * BM * 4 * (HEWG - 1);
 }
 static_assert(h_smem_bytes(H_CMAX) <= 232448, "shared memory of the tensor-core Hamming kernel");
+
+// Sixteen 32-bit TMEM columns of this thread's lane (the warp's own 32-lane
+// quarter), and the wait for this thread's stores to land.
+__device__ __forceinline__ void h_tmem_st16(uint32_t taddr, const uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+                 "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+                 "r"(r[15])
+                 : "memory");
+}
+__device__ __forceinline__ void h_tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// D += A . B^T, E4M3, A (128 rows x 32 bytes) in tensor memory at column a.
+__device__ __forceinline__ void h_mma_ts_fp8(uint32_t d, uint32_t a, uint64_t b, uint32_t id, uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "r"(a), "l"(b), "r"(id), "r"(accum));
+}
 
 struct HParams {
     int64_t N;
@@ -85,8 +111,7 @@ __global__ void __launch_bounds__(h_threads(QIN), 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;
     uint8_t *sB = smem + H_STAGES * HA_BYTES;
-    uint8_t *sA2 = smem + H_STAGES * H_STAGE_BYTES;
-    uint8_t *sB2 = sA2 + A2_BYTES;                                  // 2 atoms x Cp rows x 128 B
+    uint8_t *sB2 = smem + H_STAGES * H_STAGE_BYTES;                 // 2 atoms x Cp rows x 128 B
     uint64_t *bars = reinterpret_cast<uint64_t *>(sB2 + 2 * p.Cp * 128);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + H_NUM_BARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -96,7 +121,7 @@ __global__ void __launch_bounds__(h_threads(QIN), 1)
     auto empty = [&](int s) { return su32(bars + H_STAGES + s); };
     auto sfull = [&](int a) { return su32(bars + 2 * H_STAGES + a); };
     auto sempty = [&](int a) { return su32(bars + 2 * H_STAGES + 2 + a); };
-    const uint32_t a2full = su32(bars + 2 * H_STAGES + 4), a2empty = su32(bars + 2 * H_STAGES + 5);
+    auto a2full = [&](int a) { return su32(bars + 2 * H_STAGES + 4 + a); };
     const uint32_t b2full = su32(bars + 2 * H_STAGES + 6), b2empty = su32(bars + 2 * H_STAGES + 7);
     const uint32_t d2full = su32(bars + 2 * H_STAGES + 8), d2empty = su32(bars + 2 * H_STAGES + 9);
     const uint32_t done_bar = su32(bars + 2 * H_STAGES + 10);
@@ -122,10 +147,9 @@ __global__ void __launch_bounds__(h_threads(QIN), 1)
         }
         for (int a = 0; a < 2; a++) {
             mbar_init(sfull(a), 1);
-            mbar_init(sempty(a), BM * HEWG);
+            mbar_init(sempty(a), 1);   // the commit of the tile's MMA2
+            mbar_init(a2full(a), BM * HEWG);
         }
-        mbar_init(a2full, BM * HEWG);
-        mbar_init(a2empty, 1);
         mbar_init(b2full, 1);
         mbar_init(b2empty, 1);
         mbar_init(d2full, 1);
@@ -249,26 +273,27 @@ __global__ void __launch_bounds__(h_threads(QIN), 1)
     } else if (warp == ISSUER2) {
         if (lane == 0) {  // ------------------------------ MMA2 issuer: D2 (+)= signs . class signs, K = 192
             const uint32_t id2 = idesc_n<HDC_ENC_FP8_E4M3>(p.Cp);
-            uint32_t a2ph = 0, b2ph = 0, d2ph = 0;
+            uint32_t a2ph = 0, b2ph = 0, d2ph = 0;   // a2ph: both accumulators' parity, flipped per pair
+            int acc = 0;
             bool ab = false;
             for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x) {
                 for (int t = 0; t < p.nt; t++) {
                     const bool first = t == 0;
                     if (first && !mbar_wait(d2empty, d2ph ^ 1, abort_flag)) { ab = true; break; }
-                    if (!mbar_wait(a2full, a2ph, abort_flag)) { ab = true; break; }
+                    if (!mbar_wait(a2full(acc), a2ph, abort_flag)) { ab = true; break; }
                     if (!mbar_wait(b2full, b2ph, abort_flag)) { ab = true; break; }
                     tc_fence_after();
-                    const uint32_t a0 = su32(sA2), b0 = su32(sB2);
+                    const uint32_t b0 = su32(sB2), tacc = tmem + (uint32_t)(acc * HBN);
 #pragma unroll
-                    for (int k = 0; k < 6; k++) {   // atom 0: K bytes 0..127, atom 1: 128..191
-                        const uint32_t off_a = (k < 4 ? 0u : (uint32_t)A2_ATOM) + 32u * (k & 3);
+                    for (int k = 0; k < 6; k++) {   // class atom 0: K bytes 0..127, atom 1: 128..191
+                        // dims 32k..32k+31: warpgroup k / 2's first 16 columns, eight in for odd k
+                        const uint32_t col = (uint32_t)((k >> 1) * 64 + (k & 1) * 8);
                         const uint32_t off_b = (k < 4 ? 0u : (uint32_t)(p.Cp * 128)) + 32u * (k & 3);
-                        mma<HDC_ENC_FP8_E4M3>(tmem + D2_COL, sdesc(a0 + off_a), sdesc(b0 + off_b), id2,
-                                              (first && k == 0) ? 0u : 1u);
+                        h_mma_ts_fp8(tmem + D2_COL, tacc + col, sdesc(b0 + off_b), id2, (first && k == 0) ? 0u : 1u);
                     }
-                    mma_commit(a2empty);
+                    mma_commit(sempty(acc));   // the accumulator (and its sign bytes) is free for MMA1
                     mma_commit(b2empty);
-                    a2ph ^= 1;
+                    if (++acc == 2) { acc = 0; a2ph ^= 1; }
                     b2ph ^= 1;
                 }
                 if (ab) break;
@@ -308,11 +333,8 @@ __global__ void __launch_bounds__(h_threads(QIN), 1)
         const int q = warp & 3, g = warp >> 2;
         const int r = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        // this warpgroup's 64 columns of a tile: atom g / 2, 16-byte chunks from (g & 1) * 4
-        uint8_t *a2row = sA2 + (g >> 1) * A2_ATOM + (r >> 3) * 1024 + (r & 7) * 128;
-        const int ch0 = (g & 1) * 4;
         int acc = 0;
-        uint32_t aphase = 0, a2ph = 0, d2ph = 0;
+        uint32_t aphase = 0, d2ph = 0;
         bool ab = false;
         int64_t it = 0;
         for (int64_t mt = blockIdx.x; mt < num_m_tiles && !ab; mt += gridDim.x, it++) {
@@ -322,13 +344,12 @@ __global__ void __launch_bounds__(h_threads(QIN), 1)
                 const bool ok = mbar_wait(sfull(acc), aphase, abort_flag);
                 if (!__all_sync(0xffffffffu, ok)) { ab = true; break; }
                 tc_fence_after();
+                const uint32_t tcol = tmem + lane_base + (uint32_t)(acc * HBN + g * 64);
                 uint32_t v0[32], v1[32];
-                tmem_ld32(tmem + lane_base + (uint32_t)(acc * HBN + g * 64), v0);
-                tmem_ld32(tmem + lane_base + (uint32_t)(acc * HBN + g * 64 + 32), v1);
-                tc_fence_before();
-                mbar_arrive(sempty(acc));
-                if (++acc == 2) { acc = 0; aphase ^= 1; }
-                // E4M3 +1.0 = 0x38, -1.0 = 0xB8 (sign(0) = +1); byte i of a word is column 4w + i
+                tmem_ld32(tcol, v0);
+                tmem_ld32(tcol + 32, v1);
+                // E4M3 +1.0 = 0x38, -1.0 = 0xB8 (sign(0) = +1); byte i of word j is dim 4j + i
+                // of this warpgroup's 64
                 uint32_t w[16];
 #pragma unroll
                 for (int i = 0; i < 8; i++) {
@@ -343,17 +364,11 @@ __global__ void __launch_bounds__(h_threads(QIN), 1)
                         y |= (__uint_as_float(v1[4 * i + b]) < 0.f ? 0xB8u : 0x38u) << (8 * b);
                     w[8 + i] = y;
                 }
-                const bool oka = mbar_wait(a2empty, a2ph ^ 1, abort_flag);   // MMA2 of the previous tile done
-                if (!__all_sync(0xffffffffu, oka)) { ab = true; break; }
-#pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    const int ch = (ch0 + i) ^ (r & 7);   // 128-byte swizzle
-                    *reinterpret_cast<uint4 *>(a2row + ch * 16) = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2],
-                                                                            w[4 * i + 3]);
-                }
-                fence_async_smem();
-                mbar_arrive(a2full);
-                a2ph ^= 1;
+                h_tmem_st16(tcol, w);   // into the first 16 of the 64 columns read above
+                h_tmem_st_wait();
+                tc_fence_before();
+                mbar_arrive(a2full(acc));
+                if (++acc == 2) { acc = 0; aphase ^= 1; }
             }
             if (ab) break;
             // distances of this warpgroup's 32-class chunks (chunk j to warpgroup j % 3)
