@@ -195,6 +195,25 @@ hdc_status hdc_hamming_argmin(const uint32_t *Q, const uint32_t *Cls,
                               const hdc_approx_config *cfg, int32_t *labels,
                               int32_t *dists, hdc_stream_t stream);
 
+/* Workspace bytes for hdc_hamming_argmin_ws: for 33..256 classes and
+ * D <= 131072 (the tensor-core route), the class hypervectors expanded to
+ * one E4M3 +-1 byte per dim (C rounded up to 16 rows of
+ * 256 * ceil(W(D) / 8) bytes); 0 for every other C and D.
+ * HDC_ERR_INVALID_ARG for C <= 0, D <= 0 or a NULL bytes.                  */
+hdc_status hdc_hamming_argmin_workspace_bytes(int32_t C, int32_t D, size_t *bytes);
+
+/* hdc_hamming_argmin (same definition, arguments and results) with a
+ * caller workspace ws of ws_bytes (device, 256-byte aligned, caller-owned,
+ * >= hdc_hamming_argmin_workspace_bytes(C, D); NULL when that is 0).  On
+ * the tensor-core route the class hypervectors are expanded into ws once
+ * per call instead of once per 128-row tile.  HDC_ERR_WORKSPACE when ws is
+ * too small or misaligned; it is overwritten (no result lives in it).     */
+hdc_status hdc_hamming_argmin_ws(const uint32_t *Q, const uint32_t *Cls,
+                                 int64_t N, int32_t C, int32_t D,
+                                 const hdc_approx_config *cfg, int32_t *labels,
+                                 int32_t *dists, void *ws, size_t ws_bytes,
+                                 hdc_stream_t stream);
+
 /* Workspace bytes for hdc_train_epoch (about 12 N + 32 C bytes): the N
  * predictions of a retraining epoch, a 2N-entry permutation grouping the
  * samples (a misclassified sample sits in its true class's group and in its

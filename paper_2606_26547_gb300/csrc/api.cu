@@ -334,6 +334,39 @@ hdc_status hdc_hamming_argmin(const uint32_t *Q, const uint32_t *Cls, int64_t N,
                                 labels, dists, nullptr, (cudaStream_t)stream));
 }
 
+hdc_status hdc_hamming_argmin_workspace_bytes(int32_t C, int32_t D, size_t *bytes)
+{
+    if (!bytes || C <= 0 || D <= 0) return HDC_ERR_INVALID_ARG;
+    *bytes = align_up(class_sign_bytes(C, words_for(D)), kAlign);
+    return HDC_OK;
+}
+
+hdc_status hdc_hamming_argmin_ws(const uint32_t *Q, const uint32_t *Cls, int64_t N, int32_t C, int32_t D,
+                                 const hdc_approx_config *cfg, int32_t *labels, int32_t *dists, void *ws,
+                                 size_t ws_bytes, hdc_stream_t stream)
+{
+    Perf p;
+    if (N < 0 || C <= 0 || D <= 0) return HDC_ERR_INVALID_ARG;
+    if (cfg && (cfg->struct_size < sizeof(hdc_approx_config) || !perf_of(D, cfg, &p))) return HDC_ERR_INVALID_ARG;
+    const int W = words_for(D);
+    const size_t need = class_sign_bytes(C, W);
+    if (need && (!ws || ws_bytes < need || !aligned(ws, kAlign))) return HDC_ERR_WORKSPACE;
+    if (N == 0) return HDC_OK;
+    if (!Q || !Cls || !labels || !aligned(Q, 16) || !aligned(Cls, 16)) return HDC_ERR_INVALID_ARG;
+    const bool perforated = cfg && !(p.s0 == 0 && p.e0 == D && p.stride == 1);
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (!need)
+        return cu(launch_similarity(Q, N, Cls, C, W, 1, D, perforated ? &p : nullptr, nullptr, nullptr, labels, dists,
+                                    nullptr, st));
+    // the classes once into ws (zero past D; the query bytes are zero
+    // outside the kept dims), then the tensor-core route streams them
+    uint8_t *signs = (uint8_t *)ws;
+    hdc_status s = cu(launch_class_sign(Cls, C, W, D, (C + 15) / 16 * 16, hamming_packed_ldcs(W), signs, st));
+    if (s != HDC_OK) return s;
+    return cu(launch_hamming_packed(Q, N, Cls, C, W, D, perforated ? p.s0 : 0, perforated ? p.e0 : D,
+                                    perforated ? p.stride : 1, labels, dists, st, signs));
+}
+
 namespace {
 // Training workspace: predictions, the class-grouped sample order, the
 // counting-sort histogram / offsets / first work item per group / cursors,

@@ -57,6 +57,8 @@ _SIGS = {
     "hdc_workspace_bytes": (_I32, [_I64, _P, _P]),
     "hdc_encode": (_I32, [_P, _I64, _P, _P, _P, _P, _SZ, _P]),
     "hdc_hamming_argmin": (_I32, [_P, _P, _I64, _I32, _I32, _P, _P, _P, _P]),
+    "hdc_hamming_argmin_workspace_bytes": (_I32, [_I32, _I32, _P]),
+    "hdc_hamming_argmin_ws": (_I32, [_P, _P, _I64, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
     "hdc_train_workspace_bytes": (_I32, [_I64, _I32, _I32, _P]),
     "hdc_train_epoch": (_I32, [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
     "hdc_train_apply": (_I32, [_P, _I32, _I32, _P, _P, _P]),
@@ -216,14 +218,29 @@ def encode(X: torch.Tensor, model: Model, scores: bool = False, ws: torch.Tensor
     return (H, S) if scores else H
 
 
+def hamming_workspace(C: int, D: int, device) -> torch.Tensor | None:
+    """Device workspace for hdc_hamming_argmin_ws (None when it needs none)."""
+    n = ctypes.c_size_t()
+    _call("hdc_hamming_argmin_workspace_bytes", C, D, ctypes.byref(n))
+    return _empty_bytes(n.value, device) if n.value else None
+
+
 def hamming_argmin(Q: torch.Tensor, Cls: torch.Tensor, D: int, cfg: ApproxConfig | None = None,
-                   dists: bool = False, stream=None):
+                   dists: bool = False, stream=None, ws: torch.Tensor | None = None, use_ws: bool = True):
+    """Hamming arg-min of packed rows: hdc_hamming_argmin_ws with a workspace
+    (allocated here unless given), or hdc_hamming_argmin with use_ws=False."""
     N, C = Q.shape[0], Cls.shape[0]
     labels = torch.empty(N, dtype=torch.int32, device=Q.device)
     dd = torch.empty((N, C), dtype=torch.int32, device=Q.device) if dists else None
     c = cfg.c() if cfg else None
-    _call("hdc_hamming_argmin", _ptr(Q), _ptr(Cls), N, C, D, ctypes.byref(c) if c else None, _ptr(labels),
-          _ptr(dd), _stream(stream))
+    if use_ws:
+        if ws is None:
+            ws = hamming_workspace(C, D, Q.device)
+        _call("hdc_hamming_argmin_ws", _ptr(Q), _ptr(Cls), N, C, D, ctypes.byref(c) if c else None, _ptr(labels),
+              _ptr(dd), _ptr(ws), ws.numel() if ws is not None else 0, _stream(stream))
+    else:
+        _call("hdc_hamming_argmin", _ptr(Q), _ptr(Cls), N, C, D, ctypes.byref(c) if c else None, _ptr(labels),
+              _ptr(dd), _stream(stream))
     return (labels, dd) if dists else labels
 
 

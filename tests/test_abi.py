@@ -65,6 +65,36 @@ def test_status_strings(lib):
         assert lib.hdc_status_string(code)
 
 
+def test_hamming_workspace_without_gpu(lib):
+    """The Hamming arg-min workspace holds bytes only on the tensor-core
+    route (33..256 classes, D <= 131,072): C rounded up to 16 rows of 256
+    bytes per 8 words (W(D) is padded to 4 words); a missing, short or
+    misaligned workspace is rejected before anything is enqueued."""
+    n = ctypes.c_size_t()
+
+    def nbytes(C, D):
+        assert lib.hdc_hamming_argmin_workspace_bytes(C, D, ctypes.byref(n)) == 0
+        return n.value
+    assert nbytes(10, 1000) == 0 and nbytes(32, 1024) == 0      # popcount routes
+    assert nbytes(33, 1024) == 48 * 1024                       # 48 rows x 4 tiles of 256 bytes
+    assert nbytes(33, 1000) == 48 * 1024                       # W(1000) = 32, as for 1,024 dims
+    assert nbytes(100, 16384) == 112 * 16384
+    assert nbytes(256, 2048) == 256 * 2048
+    assert nbytes(257, 2048) == 0                              # past the tensor-core route
+    assert nbytes(40, 700) == 48 * 768                         # W(700) = 24: three tiles
+    assert nbytes(40, 33) == 48 * 256                          # W(33) = 4: one tile, half of it padding
+    assert nbytes(40, 131072) == 48 * 131072 and nbytes(40, 131073) == 0   # W <= 4,096
+    assert lib.hdc_hamming_argmin_workspace_bytes(0, 10, ctypes.byref(n)) == 1
+    assert lib.hdc_hamming_argmin_workspace_bytes(40, 0, ctypes.byref(n)) == 1
+    assert lib.hdc_hamming_argmin_workspace_bytes(40, 10, None) == 1
+    fake = ctypes.c_void_p(1 << 20)                            # aligned, never dereferenced
+    assert lib.hdc_hamming_argmin_ws(fake, fake, 5, 40, 1024, None, fake, None, None, 0, None) == 3
+    assert lib.hdc_hamming_argmin_ws(fake, fake, 5, 40, 1024, None, fake, None, fake, 48 * 1024 - 1, None) == 3
+    assert lib.hdc_hamming_argmin_ws(fake, fake, 5, 40, 1024, None, fake, None,
+                                     ctypes.c_void_p((1 << 20) + 16), 1 << 20, None) == 3
+    assert lib.hdc_hamming_argmin_ws(None, None, 5, 0, 10, None, None, None, None, 0, None) == 1
+
+
 def test_argument_checks_without_gpu(lib):
     """Invalid arguments are rejected before anything is enqueued."""
     from paper_2606_26547_gb300 import hdc

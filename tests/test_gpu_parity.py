@@ -218,6 +218,33 @@ def test_hamming_argmin_tensor_core_many_tiles(hdc):
     assert np.array_equal(labels.cpu().numpy(), orc.argmin(od))
 
 
+@pytest.mark.parametrize("C,D,perf", [(100, 1000, None), (200, 2048, (0.1, 0.9, 3)), (40, 4096, None), (26, 1024, None)])
+def test_hamming_argmin_workspace_form_and_plain_form(hdc, C, D, perf):
+    """hdc_hamming_argmin_ws (the classes expanded once into the caller's
+    workspace, reused across calls) and hdc_hamming_argmin (expanded per
+    tile) both give the oracle's distances and labels; 26 classes need no
+    workspace."""
+    rng = np.random.default_rng(C * 7 + D)
+    N = 3000
+    q = rng.integers(0, 2, (N, D)).astype(np.uint8)
+    c = rng.integers(0, 2, (C, D)).astype(np.uint8)
+    c[C - 1] = c[1]
+    q[:3] = c[:3]
+    cfg = hdc.ApproxConfig(perf_start=perf[0], perf_end=perf[1], perf_stride=perf[2]) if perf else None
+    Qt, Ct = T(pack(q).view(np.int32)), T(pack(c).view(np.int32))
+    dims = orc.kept_dims(D, *perf) if perf else orc.kept_dims(D)
+    od = orc.hamming(orc.gather_cols(q, dims), orc.gather_cols(c, dims))
+    ws = hdc.hamming_workspace(C, D, Qt.device)
+    assert (ws is None) == (C <= 32)
+    outs = [hdc.hamming_argmin(Qt, Ct, D, cfg, dists=True, ws=ws) for _ in range(2)]
+    outs.append(hdc.hamming_argmin(Qt, Ct, D, cfg, dists=True, use_ws=False))
+    for labels, dd in outs:
+        assert np.array_equal(dd.cpu().numpy().astype(np.int64), od)
+        assert np.array_equal(labels.cpu().numpy(), orc.argmin(od))
+    torch.cuda.synchronize()
+    assert hdc.stream_status() == 0
+
+
 @pytest.mark.parametrize("N,C,perf", [(41000, 100, None), (40077, 128, (0.1, 0.9, 3))])
 def test_hamming_argmin_tensor_core_more_tiles_than_ctas(hdc, N, C, perf):
     """More 128-row tiles than the two CTAs per SM hold, so CTAs take several
