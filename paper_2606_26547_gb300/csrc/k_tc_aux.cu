@@ -66,23 +66,31 @@ cudaError_t launch_hamming_packed(const uint32_t *Q, int64_t N, const uint32_t *
                                                      cudaSuccess || sms <= 0)
         sms = 152;
     const int64_t tiles = (N + tc::BM - 1) / tc::BM;
-    // two CTAs per SM when both fit in shared memory (TMEM: 2 x 256 columns),
-    // with two class-tile buffers if they fit, else one.  Up to 128 padded
-    // classes the query tile lives in tensor memory (no query buffers in
-    // shared memory: two CTAs with two class-tile buffers always fit).
+    // Up to 128 padded classes the query tile lives in tensor memory, two
+    // CTAs per SM (256 TMEM columns each, two class-tile buffers).  Above,
+    // two CTAs per SM with the query tile in shared memory where they fit
+    // (two class-tile buffers, else one), else one CTA with the query tile in
+    // tensor memory and all 512 columns: measured, the two-CTA forms win up
+    // to ~176 classes (10^5 x 16,384 dims, 144 classes: 0.339 vs 0.377 ms)
+    // and the one-CTA tensor-memory form above (256 classes: 0.397 vs 0.459
+    // ms with the one-CTA shared-memory form).  The one-CTA form asks for at
+    // least 120 KB of shared memory, so that no second CTA shares the SM and
+    // waits for its 512 columns.
     auto fits2 = [](size_t bytes) { return 2 * (bytes + 1024) <= 228 * 1024; };
-    const bool ta = p.Cp <= tc::HP_TA_CMAX;
-    const size_t smem2 = tc::hp_smem_bytes(p.Cp, W, 2, ta), smem1 = tc::hp_smem_bytes(p.Cp, W, 1);
-    const bool two = fits2(smem2) || fits2(smem1);
-    const size_t smem = fits2(smem2) ? smem2 : fits2(smem1) ? smem1 : smem2;
-    auto k = cls_sign ? (ta ? tc::tc_hamming_packed_kernel<2, 2, true, true>
-                            : fits2(smem2) ? tc::tc_hamming_packed_kernel<2, 2, true>
-                                           : fits2(smem1) ? tc::tc_hamming_packed_kernel<2, 1, true>
-                                                          : tc::tc_hamming_packed_kernel<1, 2, true>)
-                      : (ta ? tc::tc_hamming_packed_kernel<2, 2, false, true>
-                            : fits2(smem2) ? tc::tc_hamming_packed_kernel<2, 2, false>
-                                           : fits2(smem1) ? tc::tc_hamming_packed_kernel<2, 1, false>
-                                                          : tc::tc_hamming_packed_kernel<1, 2, false>);
+    const size_t smem2 = tc::hp_smem_bytes(p.Cp, W, 2), smem1 = tc::hp_smem_bytes(p.Cp, W, 1);
+    const size_t smta = tc::hp_smem_bytes(p.Cp, W, 2, true);
+    const int form = p.Cp <= tc::HP_TA_CMAX ? 0 : fits2(smem2) ? 1 : fits2(smem1) ? 2 : 3;
+    const bool two = form < 3;
+    const size_t smem = form == 0 ? smta : form == 1 ? smem2 : form == 2 ? smem1
+                      : (smta >= (size_t)120 * 1024 ? smta : (size_t)120 * 1024);
+    auto k = cls_sign ? (form == 0   ? tc::tc_hamming_packed_kernel<2, 2, true, true>
+                         : form == 1 ? tc::tc_hamming_packed_kernel<2, 2, true>
+                         : form == 2 ? tc::tc_hamming_packed_kernel<2, 1, true>
+                                     : tc::tc_hamming_packed_kernel<1, 2, true, true>)
+                      : (form == 0   ? tc::tc_hamming_packed_kernel<2, 2, false, true>
+                         : form == 1 ? tc::tc_hamming_packed_kernel<2, 2, false>
+                         : form == 2 ? tc::tc_hamming_packed_kernel<2, 1, false>
+                                     : tc::tc_hamming_packed_kernel<1, 2, false, true>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t slots = (int64_t)sms * (two ? 2 : 1);

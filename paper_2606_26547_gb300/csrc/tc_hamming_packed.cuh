@@ -21,12 +21,14 @@
 // warpgroups, alternate 32-class chunks, merged by (distance, class));
 // warp 8 issues the MMAs.  Every wait is bounded as in the encoder.
 //
-// TA (Cp <= 128): the query tile goes to tensor memory instead: each
-// expanding thread writes its row's E4M3 bytes into its own TMEM lane
-// (tcgen05.st, four bytes per column, dims in ascending byte order) and the
-// MMAs take A from there (K-major, row i in lane i), so that shared memory
-// carries only the class operand.  TMEM: D2 in columns 0..127, the two
-// query buffers of 64 columns (256 dims) each in columns 128..255.
+// TA: the query tile goes to tensor memory instead: each expanding thread
+// writes its row's E4M3 bytes into its own TMEM lane (tcgen05.st, four bytes
+// per column, dims in ascending byte order) and the MMAs take A from there
+// (K-major, row i in lane i), so that shared memory carries only the class
+// operand.  TMEM: with two CTAs per SM (Cp <= 128) D2 in columns 0..127 and
+// the two query buffers of 64 columns (256 dims) each in columns 128..255 of
+// 256; with one (Cp <= 256) D2 in columns 0..255 and the buffers in
+// 256..383 of 512.
 //
 // PRE: the class hypervectors come already expanded (E4M3 +-1 bytes, Cp rows
 // of ldcs bytes, from launch_class_sign into the caller's workspace), and
@@ -48,8 +50,7 @@ constexpr int HP_MAX_W = 4096;                 // words of a packed row (D <= 13
 // full[2], empty[2], d2full, d2empty, merge_full, merge_empty, done, cfull[2]
 constexpr int HP_NUM_BARS = 11;
 
-constexpr int HP_TA_CMAX = 128;                // TA: largest padded class count
-constexpr int HP_TA_COL = 128;                 // TA: first TMEM column of the query buffers
+constexpr int HP_TA_CMAX = 128;                // TA: largest padded class count with two CTAs per SM
 
 // bbuf: class-tile buffers (2, or 1 so that two CTAs fit per SM); ta: the
 // query tile in tensor memory (no shared-memory query buffers)
@@ -60,6 +61,7 @@ __host__ __device__ constexpr size_t hp_smem_bytes(int Cp, int W, int bbuf = 2, 
 }
 static_assert(hp_smem_bytes(HP_CMAX, HP_MAX_W) <= 232448, "shared memory of the packed tensor-core Hamming kernel");
 static_assert(2 * (hp_smem_bytes(HP_TA_CMAX, HP_MAX_W, 2, true) + 1024) <= 228 * 1024, "two TA CTAs per SM");
+static_assert(hp_smem_bytes(HP_CMAX, HP_MAX_W, 2, true) <= 232448, "one TA CTA per SM");
 
 struct HPParams {
     const uint32_t *Q;       // N x W packed rows
@@ -187,6 +189,9 @@ __global__ void __launch_bounds__(HP_THREADS, MINB)
     const uint32_t merge_full = su32(bars + 6), merge_empty = su32(bars + 7), done_bar = su32(bars + 8);
     auto cfull = [&](int b) { return su32(bars + 9 + b); };   // PRE: the class atoms of buffer b landed
     constexpr int ISSUER = HP_EXP / 32;
+    // TMEM columns of the CTA and the first column of its TA query buffers
+    constexpr int TCOLS = TA && MINB == 1 ? 512 : 256;
+    constexpr uint32_t TA_COL = MINB == 1 ? 256 : 128;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t num_m_tiles = (p.N + BM - 1) / BM;
@@ -226,7 +231,7 @@ __global__ void __launch_bounds__(HP_THREADS, MINB)
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                     "r"(256)
+                     "r"(TCOLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -255,7 +260,7 @@ __global__ void __launch_bounds__(HP_THREADS, MINB)
                     const uint64_t da = sdesc(su32(sA + buf * HP_A_BYTES));
                     const uint64_t db = sdesc(su32(sB + (BBUF == 2 ? buf : 0) * b_bytes));
                     const uint32_t atom_b = (uint32_t)(p.Cp * 128) >> 4;   // second K atom of the class tile
-                    const uint32_t ta = tmem + HP_TA_COL + (uint32_t)(buf * 64);   // TA: this buffer's columns
+                    const uint32_t ta = tmem + TA_COL + (uint32_t)(buf * 64);   // TA: this buffer's columns
 #pragma unroll
                     for (int k = 0; k < 8; k++) {   // two atoms of four 32-byte K steps
                         const uint64_t ob = (uint64_t)((k >> 2) * atom_b + 2 * (k & 3));
@@ -342,7 +347,7 @@ __global__ void __launch_bounds__(HP_THREADS, MINB)
                 const uint4 mq = w0 < p.W ? *reinterpret_cast<const uint4 *>(smask + w0) : make_uint4(0, 0, 0, 0);
                 if (TA) {   // converged for the warp-wide TMEM stores (thread 0 may have issued the class copy)
                     __syncwarp();
-                    expand_row_tmem(tmem + lane_base + HP_TA_COL + (uint32_t)(buf * 64 + half * 32), qw, mq);
+                    expand_row_tmem(tmem + lane_base + TA_COL + (uint32_t)(buf * 64 + half * 32), qw, mq);
                 } else {
                     expand_row(sA + buf * HP_A_BYTES + half * (BM * 128), r, qw, mq);
                 }
@@ -414,7 +419,7 @@ __global__ void __launch_bounds__(HP_THREADS, MINB)
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
     }
 }
 
