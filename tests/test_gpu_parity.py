@@ -245,6 +245,33 @@ def test_hamming_argmin_workspace_form_and_plain_form(hdc, C, D, perf):
     assert hdc.stream_status() == 0
 
 
+@pytest.mark.parametrize("D,C,perf", [(131072, 256, None), (131072, 40, (0.02, 0.99, 5)), (131073, 256, None)])
+def test_hamming_argmin_largest_rows(hdc, D, C, perf):
+    """The tensor-core route's largest rows (4,096 words: the whole kept-dim
+    mask in shared memory), with 256 classes (one CTA per SM, all 512 TMEM
+    columns) and 40 (two CTAs), and one dim past it (4,100 words: the
+    popcount route, which needs no workspace); two 128-row tiles, the second
+    ragged.  Rows 0-2, 64 and 127-129 against the oracle."""
+    rng = np.random.default_rng(D + C)
+    N = 130
+    q = rng.integers(0, 2, (N, D)).astype(np.uint8)
+    c = rng.integers(0, 2, (C, D)).astype(np.uint8)
+    c[C - 1] = c[0]
+    q[:2] = c[:2]
+    cfg = hdc.ApproxConfig(perf_start=perf[0], perf_end=perf[1], perf_stride=perf[2]) if perf else None
+    assert (hdc.hamming_workspace(C, D, torch.device("cuda:0")) is None) == (D > 131072)
+    Qt, Ct = T(pack(q).view(np.int32)), T(pack(c).view(np.int32))
+    rows = np.array([0, 1, 2, 64, 127, 128, 129])
+    dims = orc.kept_dims(D, *perf) if perf else orc.kept_dims(D)
+    od = orc.hamming(orc.gather_cols(q[rows], dims), orc.gather_cols(c, dims))
+    for use_ws in (True, False):
+        labels, dd = hdc.hamming_argmin(Qt, Ct, D, cfg, dists=True, use_ws=use_ws)
+        assert np.array_equal(dd.cpu().numpy()[rows].astype(np.int64), od)
+        assert np.array_equal(labels.cpu().numpy()[rows], orc.argmin(od))
+    torch.cuda.synchronize()
+    assert hdc.stream_status() == 0
+
+
 @pytest.mark.parametrize("N,C,perf", [(41000, 100, None), (40077, 128, (0.1, 0.9, 3))])
 def test_hamming_argmin_tensor_core_more_tiles_than_ctas(hdc, N, C, perf):
     """More 128-row tiles than the two CTAs per SM hold, so CTAs take several
