@@ -107,8 +107,17 @@ ModelLayout model_layout(int F, int Dk, int C, int enc, int bits, uint32_t flags
 }
 
 struct WsLayout {
-    size_t xq, sx, h, sp, qn, sf, dacc, total;
+    size_t xq, sx, h, sp, qn, sf, dacc, csign, total;
 };
+
+// Binary classes past the fused kernels (129..256): the classify's Hamming
+// step expands the class hypervectors once per call into the workspace for
+// the tensor-core route (0 bytes where that route does not apply).
+size_t classify_sign_bytes(const hdc_model *m)
+{
+    if (m->class_bits != 1 || m->C <= 128 || float_query(m->flags)) return 0;
+    return class_sign_bytes(m->C, m->W);
+}
 
 bool use_tc(const hdc_model *m);
 
@@ -132,6 +141,7 @@ WsLayout ws_layout(int64_t N, const hdc_model *m)
     // partial distances of at most TC_SPLIT_MAX_TILES tiles and their counters
     L.dacc = off;
     off = align_up(off + (m->C > 0 && !fq ? tc_split_bytes(N, m->C) : 0), kAlign);
+    L.csign = off; off = align_up(off + classify_sign_bytes(m), kAlign);
     L.total = off;
     return L;
 }
@@ -538,6 +548,13 @@ hdc_status hdc_classify(const float *X, int64_t N, const hdc_model *m, int32_t *
         s = cu(timed_simt(Xop, ldx, N, m->Fk, m->Bq, m->ldb, m->Dk, m->enc, sx, m->b_scale, Hb, m->W,
                                   nullptr, st));
         if (s != HDC_OK) return s;
+    }
+    if (classify_sign_bytes(m)) {   // 129..256 binary classes: the classes expanded once, then the tensor cores
+        uint8_t *signs = (uint8_t *)ws + L.csign;
+        s = cu(launch_class_sign(m->cls, m->C, m->W, m->Dk, (m->C + 15) / 16 * 16, hamming_packed_ldcs(m->W), signs,
+                                 st));
+        if (s != HDC_OK) return s;
+        return cu(launch_hamming_packed(Hb, N, m->cls, m->C, m->W, m->Dk, 0, m->Dk, 1, labels, dists, st, signs));
     }
     return cu(launch_similarity(Hb, N, m->cls, m->C, m->W, nb, m->Dk, nullptr, m->cls_sum, m->cls_norm, labels,
                                 dists, scores, st));

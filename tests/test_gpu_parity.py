@@ -482,6 +482,27 @@ def test_tc_classify_matches_oracle_many_classes(hdc, enc, C, bits_):
         assert np.array_equal(sims.cpu().numpy(), osim)
 
 
+@pytest.mark.parametrize("enc", ["bf16", "fp8"])
+@pytest.mark.parametrize("C", [129, 200, 256, 257])
+def test_classify_binary_classes_past_the_fused_kernels(hdc, enc, C):
+    """129..256 binary classes: encode, then the classes expanded once into
+    the workspace and the tensor-core Hamming (257: the popcount route);
+    labels and distances equal the oracle's, ties across class chunks."""
+    rng = np.random.default_rng(C * 3 + len(enc))
+    F, D, N = 200, 1300, 300
+    X = rng.integers(-8, 8, (N, F)).astype(np.float32)
+    Bt = (1 - 2 * rng.integers(0, 2, (D, F))).astype(np.float32)
+    acc = rng.integers(-300, 301, (C, D)).astype(np.int64)
+    acc[C - 1] = acc[2]
+    model = hdc.Model(T(Bt), hdc.ApproxConfig(enc=enc), acc=T(acc.astype(np.int32)))
+    labels, dist = hdc.classify(T(X), model, sims=True)
+    ol, od = orc.classify(X, Bt, acc, orc.ENC_FP32, 0.0, 1.0, 1, 1, integer=True)
+    assert np.array_equal(labels.cpu().numpy(), ol)
+    assert np.array_equal(dist.cpu().numpy().astype(np.int64), od)
+    torch.cuda.synchronize()
+    assert hdc.stream_status() == 0
+
+
 @pytest.mark.parametrize("C", [20, 50, 100])
 def test_tc_classify_ties_across_warpgroups(hdc, C):
     """Equal class hypervectors in every warpgroup's class range: each query
