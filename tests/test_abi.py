@@ -95,6 +95,31 @@ def test_hamming_workspace_without_gpu(lib):
     assert lib.hdc_hamming_argmin_ws(None, None, 5, 0, 10, None, None, None, None, 0, None) == 1
 
 
+def test_classify_workspace_holds_expanded_classes_without_gpu(lib):
+    """hdc_workspace_bytes of a binary model past the fused kernels (129..256
+    classes) exceeds that of the same model with 8-bit classes by the
+    classes expanded to E4M3 bytes (C rounded up to 16 rows of 256 bytes
+    per 8 words); at 128 and 257 classes the two are equal.  A model
+    descriptor with placeholder pointers: the size query reads its fields
+    only."""
+    from paper_2606_26547_gb300 import hdc
+    words = lambda d: ((d + 31) // 32 + 3) // 4 * 4
+
+    def ws(C, bits=1, D=10000, N=4096):
+        m = hdc.ModelC()
+        m.struct_size = ctypes.sizeof(m)
+        m.F, m.D, m.Dk, m.C, m.enc, m.ldb, m.class_bits = 784, D, D, C, 1, 784, bits
+        m.W, m.flags, m.Fk, m.fs0, m.fstride = words(D), 0, 784, 0, 1
+        m.Bq = m.cls = m.cls_sum = m.cls_norm = 1 << 20
+        n = ctypes.c_size_t()
+        assert lib.hdc_workspace_bytes(N, ctypes.byref(m), ctypes.byref(n)) == 0
+        return n.value
+    ldcs = (words(10000) + 7) // 8 * 256
+    for C, Cp in ((129, 144), (200, 208), (256, 256)):
+        assert ws(C) - ws(C, bits=8) == Cp * ldcs
+    assert ws(128) == ws(128, bits=8) and ws(257) == ws(257, bits=8)
+
+
 def test_argument_checks_without_gpu(lib):
     """Invalid arguments are rejected before anything is enqueued."""
     from paper_2606_26547_gb300 import hdc
